@@ -1,0 +1,393 @@
+/*
+ * safegpu.h -- C ABI of the GB300 (sm_103a) SafeGPU library.
+ *
+ * The library implements the data-parallel collection operations and the
+ * on-device design-by-contract checks of Kolesnichenko, Poskitt, Nanz, Meyer,
+ * "Contract-Based General-Purpose GPU Programming" (SafeGPU):
+ *   - collections, vectors and matrices held in device memory (Sec. 3.1-3.4,
+ *     Table 1 CUDA_DATA_HANDLE, Table 2 collection API);
+ *   - deferred execution: calls are queued and run at a trigger -- a scalar
+ *     query, a read back to the host, or an explicit flush (Sec. 5, the
+ *     three triggers) -- after an optimizer merges the queued calls into
+ *     fewer kernels (Sec. 5, Fig. 2 map+reduce merge, Fig. 3 expression
+ *     rewrite);
+ *   - pre- and postconditions evaluated on the GPU, scalar ones on the host
+ *     and range ones (for_all, exists, is_sorted, ...) on the device
+ *     (Sec. 4; contract modes of Sec. 6.3).
+ *
+ * Conventions for every call:
+ *   - Every function returns an sg_status; results come back through
+ *     out-parameters, which are written only on SG_OK.
+ *   - Sizes and indices are int64_t.  Vectors are contiguous 1-D arrays;
+ *     matrices are row-major (Sec. 3.4: "a single-dimensional array with
+ *     row-wise alignment").
+ *   - Handles returned through an out-parameter are owned by the caller, who
+ *     releases them with the matching *_release call.  Releasing a handle
+ *     whose value is still pending is allowed: the queued work keeps what it
+ *     needs alive, and an unread intermediate whose handle was released is
+ *     never materialised when the optimizer can fuse it away.
+ *   - Device pointers passed to *_wrap are borrowed: the caller keeps the
+ *     memory alive and unmodified until the next sg_flush returns.
+ *   - Shape and dtype errors (the paper's scalar contracts) are detected on
+ *     the host at the call and nothing is queued.  Range contracts are
+ *     evaluated on the device at the flush: the flush then returns
+ *     SG_ERR_PRECONDITION / SG_ERR_POSTCONDITION, the checked value and its
+ *     dependants are poisoned (reading them returns SG_ERR_POISONED) and
+ *     sg_last_violation() reports the first (smallest) violating index.
+ *   - No call falls back to the CPU.  A context needs a CUDA device; the one
+ *     exception is a planning-only context (device = -1), on which handles
+ *     carry shapes only and sg_plan_describe() shows what a flush would
+ *     launch.
+ *   - All work of a context runs in order on the stream given to sg_init.
+ *     A context is not thread-safe; use one per host thread.
+ */
+#ifndef SAFEGPU_H
+#define SAFEGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SG_ABI_VERSION 1
+
+typedef enum {
+  SG_OK = 0,
+  SG_ERR_INVALID_ARG = 1,   /* null handle, bad enum, malformed expression   */
+  SG_ERR_SHAPE = 2,         /* count / rows / columns mismatch (scalar contract) */
+  SG_ERR_DTYPE = 3,         /* element type not supported by the operation   */
+  SG_ERR_OOM = 4,           /* device allocation failed                      */
+  SG_ERR_CUDA = 5,          /* a CUDA runtime call failed                    */
+  SG_ERR_PRECONDITION = 6,  /* a `require` range contract failed on device   */
+  SG_ERR_POSTCONDITION = 7, /* an `ensure` range contract failed on device   */
+  SG_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up            */
+  SG_ERR_NOT_CONVERGED = 9, /* iterative refinement hit its iteration limit  */
+  SG_ERR_POISONED = 10,     /* value depends on a failed contract            */
+  SG_ERR_UNSUPPORTED = 11,  /* e.g. compute on a planning-only context       */
+  SG_ERR_SINGULAR = 12      /* exactly zero pivot in elimination             */
+} sg_status;
+
+typedef enum {
+  SG_F32 = 0, SG_F64 = 1, SG_BF16 = 2, SG_F16 = 3, SG_I32 = 4, SG_I64 = 5
+} sg_dtype;
+
+typedef struct sg_ctx sg_ctx;
+typedef struct sg_vector sg_vector;   /* collection / vector (Sec. 3.2-3.3) */
+typedef struct sg_matrix sg_matrix;   /* row-major matrix (Sec. 3.4)        */
+typedef struct sg_scalar sg_scalar;   /* deferred scalar result             */
+
+/* ------------------------------------------------------------------------ */
+/* Expressions: the agents of Sec. 3.2 (functions and predicates applied to
+ * every element).  A postfix program over a stack of IEEE binary32 values,
+ * evaluated per element index i.  Booleans are 1.0f / 0.0f and a value is
+ * true when it compares unequal to 0.0f (NaN is true).  Every operation is
+ * one IEEE operation rounded to nearest-even; nothing is contracted into an
+ * FMA unless SG_OP_FMA says so.  At most SG_MAX_EXPR_OPS ops and a stack
+ * depth of at most SG_MAX_EXPR_DEPTH.                                       */
+
+#define SG_MAX_EXPR_OPS 24
+#define SG_MAX_EXPR_DEPTH 6
+
+typedef enum {
+  SG_OP_LOAD = 1,   /* arg = input slot k: push in_k[i]                   */
+  SG_OP_CONST,      /* push `value`                                       */
+  SG_OP_ADD, SG_OP_SUB, SG_OP_MUL, SG_OP_DIV,   /* pop b, a; push a op b  */
+  SG_OP_FMA,        /* pop c, b, a; push a*b+c with one rounding          */
+  SG_OP_MIN, SG_OP_MAX, /* NaN if either is NaN, else a<b?a:b / a>b?a:b   */
+  SG_OP_NEG, SG_OP_ABS, SG_OP_SQRT,
+  SG_OP_LT, SG_OP_LE, SG_OP_GT, SG_OP_GE, SG_OP_EQ, SG_OP_NE,
+  SG_OP_AND, SG_OP_OR, SG_OP_NOT,
+  SG_OP_SELECT,     /* pop f, t, c; push c ? t : f                        */
+  SG_OP_DUP, SG_OP_SWAP,
+  SG_OP_INDEX       /* push (float)i                                      */
+} sg_opcode;
+
+typedef struct {
+  int32_t op;      /* sg_opcode                      */
+  int32_t arg;     /* input slot for SG_OP_LOAD      */
+  float value;     /* constant for SG_OP_CONST       */
+} sg_expr_op;
+
+typedef struct {
+  int32_t nops;
+  sg_expr_op ops[SG_MAX_EXPR_OPS];
+} sg_expr;
+
+/* ------------------------------------------------------------------------ */
+/* Context (Table 1, CUDA_INTEROP: initialisation and device handling).
+ * device  : CUDA ordinal, or -1 for a planning-only context (no GPU needed).
+ * stream  : a cudaStream_t (as void*), or NULL for the legacy default stream.
+ *           All kernels and copies of this context are issued on it.
+ * Errors  : SG_ERR_INVALID_ARG (out is NULL), SG_ERR_CUDA (no such device). */
+sg_status sg_init(int device, void* stream, sg_ctx** out);
+/* Waits for the stream, frees every device allocation the context made.
+ * Handles still alive become invalid. */
+sg_status sg_destroy(sg_ctx* ctx);
+/* Message of the last error on this context (static storage until the next
+ * call on it). */
+const char* sg_last_error(sg_ctx* ctx);
+const char* sg_status_name(sg_status s);
+
+/* ------------------------------------------------------------------------ */
+/* Vectors (Table 2: from_array, count, item; Table 1 CUDA_DATA_HANDLE).      */
+
+/* from_array: allocates n elements on the device (owned by the handle) and,
+ * when host is not NULL, copies n elements from host memory (one memcpy,
+ * Sec. 3.2).  host == NULL leaves the contents undefined. */
+sg_status sg_vector_create(sg_ctx* ctx, sg_dtype dt, int64_t n,
+                           const void* host, sg_vector** out);
+/* Borrows n elements at dev_ptr (e.g. a torch tensor's storage). */
+sg_status sg_vector_wrap(sg_ctx* ctx, sg_dtype dt, int64_t n, void* dev_ptr,
+                         sg_vector** out);
+/* to_array: flushes the work the vector depends on (trigger 2 of Sec. 5),
+ * then copies n == count elements into host memory and waits for them.
+ * SG_ERR_POISONED if the value depends on a failed contract. */
+sg_status sg_vector_read(sg_vector* v, void* host, int64_t n);
+/* count (Table 2): scalar query, no flush.  May be called on a pending
+ * filter result only after a flush (its count is data-dependent); before
+ * that it flushes. */
+sg_status sg_vector_count(sg_vector* v, int64_t* n);
+/* Device address of the vector's storage after flushing it (for interop). */
+sg_status sg_vector_device_ptr(sg_vector* v, void** dev_ptr);
+sg_status sg_vector_release(sg_vector* v);
+
+/* Matrices (Sec. 3.4): rows x cols, row-major, same ownership rules. */
+sg_status sg_matrix_create(sg_ctx* ctx, sg_dtype dt, int64_t rows, int64_t cols,
+                           const void* host, sg_matrix** out);
+sg_status sg_matrix_wrap(sg_ctx* ctx, sg_dtype dt, int64_t rows, int64_t cols,
+                         void* dev_ptr, sg_matrix** out);
+sg_status sg_matrix_read(sg_matrix* m, void* host, int64_t count);
+sg_status sg_matrix_shape(sg_matrix* m, int64_t* rows, int64_t* cols);
+sg_status sg_matrix_device_ptr(sg_matrix* m, void** dev_ptr);
+sg_status sg_matrix_release(sg_matrix* m);
+/* A vector view of all rows*cols elements (the matrix stays valid). */
+sg_status sg_matrix_as_vector(sg_matrix* m, sg_vector** out);
+
+/* ------------------------------------------------------------------------ */
+/* Collection operations (Table 2, Sec. 3.2-3.3).  All are deferred.
+ * Element type: SG_F32.  Every input must have the same count (scalar
+ * contract, else SG_ERR_SHAPE).                                             */
+
+/* project (Table 2): out[i] = f(x[i]); input slot 0 = x.  New vector. */
+sg_status sg_map(sg_ctx* ctx, const sg_expr* f, sg_vector* x, sg_vector** out);
+/* Component-wise vector arithmetic (Sec. 3.3 plus/minus/compwise_*):
+ * out[i] = f(x[i], y[i]); slots 0 = x, 1 = y. */
+sg_status sg_zip(sg_ctx* ctx, const sg_expr* f, sg_vector* x, sg_vector* y,
+                 sg_vector** out);
+/* General n-ary form (1..4 inputs in slots 0..nin-1). */
+sg_status sg_mapn(sg_ctx* ctx, const sg_expr* f, int nin, sg_vector* const* ins,
+                  sg_vector** out);
+/* for_each (Table 2): x[i] = f(x[i]) in place. */
+sg_status sg_for_each(sg_ctx* ctx, const sg_expr* f, sg_vector* x);
+/* filter (Table 2): a new vector of the x[i] for which pred(x[i]) holds, in
+ * index order (stable).  Its count is known after the flush. */
+sg_status sg_filter(sg_ctx* ctx, const sg_expr* pred, sg_vector* x,
+                    sg_vector** out);
+
+typedef enum {
+  SG_REDUCE_SUM = 0,  /* binary64 value of the sum of the elements (an empty
+                         sum is 0)                                          */
+  SG_REDUCE_MIN = 1,  /* NaN if any element is NaN; count must be > 0       */
+  SG_REDUCE_MAX = 2,
+  SG_REDUCE_AVG = 3,  /* sum / count; count must be > 0                     */
+  SG_REDUCE_COUNT = 4
+} sg_reduce_op;
+
+/* sum / avg / min / max (Sec. 3.3): a deferred scalar. */
+sg_status sg_reduce(sg_ctx* ctx, sg_reduce_op op, sg_vector* x, sg_scalar** out);
+/* for_all / exists (Table 2): deferred Boolean; pred over slots 0..nin-1
+ * (slot 0 = x).  sg_scalar_index gives the first failing (for_all) or first
+ * witnessing (exists) index, -1 if none. */
+sg_status sg_for_all(sg_ctx* ctx, const sg_expr* pred, int nin,
+                     sg_vector* const* ins, sg_scalar** out);
+sg_status sg_exists(sg_ctx* ctx, const sg_expr* pred, int nin,
+                    sg_vector* const* ins, sg_scalar** out);
+/* Trigger 1 of Sec. 5: reading a scalar flushes what it depends on. */
+sg_status sg_scalar_get(sg_scalar* s, double* value);
+sg_status sg_scalar_index(sg_scalar* s, int64_t* index);
+sg_status sg_scalar_release(sg_scalar* s);
+
+/* ------------------------------------------------------------------------ */
+/* Sorting (Listing 4: ascending, left < mid = right >).  Keys SG_I32, signed
+ * order.  With contract mode >= SG_CONTRACTS_PRE_POST the built-in
+ * postconditions `Result.is_sorted` and `Result is a permutation of keys`
+ * (Listing 4 `Result.count = a.count`, strengthened to multiset equality)
+ * are evaluated inside the sort's last pass.  n < 2^30. */
+sg_status sg_sort(sg_ctx* ctx, sg_vector* keys, sg_vector** out);
+
+/* ------------------------------------------------------------------------ */
+/* Matrix product (Sec. 3.4 `multiply`): C = A B.  A: M x K, B: K x N, SG_F32
+ * storage; C: M x N SG_F32.  `precision` selects binary32 SIMT arithmetic or
+ * bf16 / fp16 operands (rounded to nearest even) on the tensor cores with
+ * binary32 accumulation.  Built-in postcondition (mode >= PRE_POST):
+ * Freivalds' check with 4 Rademacher vectors (see sg_contract). */
+typedef enum {
+  SG_PREC_F32_SIMT = 0,
+  SG_PREC_BF16_TC = 1,
+  SG_PREC_F16_TC = 2
+} sg_precision;
+sg_status sg_matmul(sg_ctx* ctx, sg_matrix* A, sg_matrix* B, sg_precision p,
+                    sg_matrix** C);
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian elimination (Sec. 5, Listing 6; read as elimination with partial
+ * pivoting) and solve.  A: n x n SG_F32, b: n SG_F64; x: n SG_F64.
+ * The factorisation runs with `precision` operands for the trailing update
+ * (binary32 accumulation), then iterative refinement with the residual
+ * r = b - A x in binary64 until max|d| <= refine_tol * max|x| or max_iter.
+ * Built-in postcondition (mode >= PRE_POST): max|b - A x| /
+ * (|A|_inf |x|_inf + |b|_inf) <= residual_tol, evaluated in binary64. */
+typedef struct {
+  sg_precision precision;  /* trailing-update operands                */
+  int32_t max_iter;        /* refinement iterations (default 30)      */
+  double refine_tol;       /* default 1e-14                           */
+  double residual_tol;     /* default 1e-12                           */
+  int32_t block;           /* panel width nb (0 = library choice)     */
+} sg_solve_opts;
+
+typedef struct {
+  int32_t iterations;      /* refinement steps taken                  */
+  int32_t info;            /* 0, or k+1 for an exactly zero pivot     */
+  double residual;         /* final normwise backward error           */
+  double last_correction;  /* max|d| / max|x| of the last step        */
+} sg_solve_info;
+
+sg_status sg_solve(sg_ctx* ctx, sg_matrix* A, sg_vector* b,
+                   const sg_solve_opts* opts, sg_vector** x,
+                   sg_solve_info* info);
+
+/* ------------------------------------------------------------------------ */
+/* Contracts (Sec. 4).  sg_require attaches a precondition, sg_ensure a
+ * postcondition, to the current (possibly pending) value of `target`.  They
+ * are evaluated at the next flush, fused into the pass that produces the
+ * target whenever possible.  Scalar parts (counts, shapes) are checked at
+ * the call.  Returns an id in *contract_id (may be NULL) that
+ * sg_last_violation() reports.                                              */
+typedef enum {
+  SG_C_FOR_ALL = 0,     /* expr over slots: 0 = target, 1.. = other[]   */
+  SG_C_EXISTS = 1,
+  SG_C_SORTED = 2,      /* target ascending; first i with t[i] > t[i+1]   */
+  SG_C_PERMUTATION = 3, /* target is a permutation of other[0]            */
+  SG_C_FREIVALDS = 4,   /* target C = other[0] (A) x other[1] (B), matrices */
+  SG_C_RESIDUAL = 5     /* target x solves other[0] (A) x = other[1] (b)    */
+} sg_contract_kind;
+
+typedef struct {
+  int32_t kind;          /* sg_contract_kind                              */
+  sg_expr expr;          /* FOR_ALL / EXISTS predicate                    */
+  int32_t nother;        /* number of entries used in other[]             */
+  void* other[3];        /* sg_vector* (or sg_matrix* for FREIVALDS,
+                            RESIDUAL's A)                                 */
+  uint64_t seed;         /* FREIVALDS: Rademacher stream seed             */
+  int32_t nvec;          /* FREIVALDS: number of vectors (default 4)      */
+  double tol;            /* FREIVALDS: c in tau = c u sigma (default 8);
+                            RESIDUAL: bound (default 1e-12)               */
+} sg_contract;
+
+sg_status sg_require(sg_ctx* ctx, void* target, const sg_contract* c,
+                     int32_t* contract_id);
+sg_status sg_ensure(sg_ctx* ctx, void* target, const sg_contract* c,
+                    int32_t* contract_id);
+
+typedef enum { SG_PRE = 0, SG_POST = 1 } sg_contract_role;
+
+typedef struct {
+  int32_t contract_id;   /* id from sg_require / sg_ensure, or -1 for a
+                            built-in contract of an operation             */
+  int32_t role;          /* sg_contract_role                              */
+  int32_t kind;          /* sg_contract_kind                              */
+  int32_t op_id;         /* sequence number of the checked operation      */
+  int64_t first_index;   /* smallest violating index (row for FREIVALDS), -1
+                            when the contract has no index (PERMUTATION)  */
+  double observed;       /* e.g. the residual or |z_i - w_i| / tau_i      */
+} sg_violation;
+
+/* The first violation found by the last flush; SG_ERR_INVALID_ARG if none. */
+sg_status sg_last_violation(sg_ctx* ctx, sg_violation* out);
+
+/* ------------------------------------------------------------------------ */
+/* Execution (Sec. 5).                                                       */
+
+/* update (Table 2): run every pending operation of the context, merged by
+ * the optimizer, and wait for it.  Returns the first failure. */
+sg_status sg_flush(sg_ctx* ctx);
+
+typedef enum {
+  SG_CONTRACTS_OFF = 0,
+  SG_CONTRACTS_PRE = 1,       /* preconditions only        (Sec. 6.3 mode 1) */
+  SG_CONTRACTS_PRE_POST = 2,  /* pre- and postconditions   (mode 2)          */
+  SG_CONTRACTS_FULL = 3       /* plus handle invariants    (mode 3)          */
+} sg_contract_mode;
+sg_status sg_set_contract_mode(sg_ctx* ctx, sg_contract_mode m);
+
+/* Fusion of queued calls (Sec. 5): SG_FUSE_ON merges map chains, map+reduce
+ * and contract predicates into single passes; SG_FUSE_OFF launches one
+ * kernel per queued call (the plain unfused schedule). */
+typedef enum { SG_FUSE_OFF = 0, SG_FUSE_ON = 1 } sg_fusion;
+sg_status sg_set_fusion(sg_ctx* ctx, sg_fusion f);
+
+/* Schedule choice for launch shapes (blocks per SM, items per thread, sort
+ * tile): the autotuned plain table, or the learned MLP cost model. */
+typedef enum { SG_SCHED_AUTOTUNE = 0, SG_SCHED_LEARNED = 1 } sg_sched;
+sg_status sg_set_scheduler(sg_ctx* ctx, sg_sched s);
+
+/* Writes a one-line-per-kernel description of what sg_flush would launch
+ * for the currently queued work (no execution; works on a planning-only
+ * context).  *len receives the length needed, including the terminator. */
+sg_status sg_plan_describe(sg_ctx* ctx, char* buf, size_t cap, size_t* len);
+
+/* Number of kernels this context has launched so far. */
+sg_status sg_kernel_count(sg_ctx* ctx, int64_t* count);
+
+/* Tracing.  With `on` != 0 every kernel this context launches is bracketed
+ * by two CUDA events recorded on its stream (a few microseconds per launch;
+ * off by default).  sg_profile_report writes one line per kernel name,
+ * "name launches total_ms", accumulated since the last reset (reset != 0
+ * clears the totals after writing); *len receives the size needed. */
+sg_status sg_profile_enable(sg_ctx* ctx, int on);
+sg_status sg_profile_report(sg_ctx* ctx, char* buf, size_t cap, size_t* len,
+                            int reset);
+
+/* Contract testing (Sec. 4 contracts must be seen to fire): plant a fault
+ * in the NEXT sort of this context, on the host side, between its third and
+ * its last pass: the host copies into the intermediate buffer (which holds
+ * the keys ordered by their low 24 bits) either
+ *   SG_INJECT_SWAP:      positions i and j exchanged, or
+ *   SG_INJECT_OVERWRITE: position i set to the int32 value j.
+ * Nothing is planted on the device side; the fused postconditions of the
+ * last pass then report what they see.  mode SG_INJECT_NONE cancels.
+ * Errors: SG_ERR_INVALID_ARG for a bad mode or negative index. */
+typedef enum { SG_INJECT_NONE = 0, SG_INJECT_SWAP = 1, SG_INJECT_OVERWRITE = 2 } sg_inject_mode;
+sg_status sg_debug_inject_sort(sg_ctx* ctx, sg_inject_mode mode, int64_t i, int64_t j);
+
+/* ------------------------------------------------------------------------ */
+/* Batched collections: one persistent launch over many collections of uneven
+ * size, each running the chain
+ *     y = map(x);  require for_all(pre(y));  s = sum(filter(y, keep))
+ * (Sec. 3.2-3.3 operations per collection; the filter output is consumed only
+ * by the sum, so it is never materialised).  Captured once into a CUDA graph
+ * per (context, chain, nseg) and replayed.  Device pointers, caller-owned:
+ *   data     : concatenated SG_F32 elements
+ *   offsets  : nseg+1 int64, offsets[0] = 0, non-decreasing
+ *   sums     : nseg binary64 sums of the kept y
+ *   first_viol: nseg int64, first index (within the collection) where pre
+ *               fails, -1 if none
+ *   kept     : nseg int64 counts of kept elements
+ * Returns SG_ERR_PRECONDITION if any collection violated `pre` (outputs are
+ * still written). */
+typedef struct {
+  sg_expr map;
+  sg_expr pre;
+  sg_expr keep;
+} sg_chain;
+
+sg_status sg_batch_run(sg_ctx* ctx, const sg_chain* chain, const float* data,
+                       const int64_t* offsets, int64_t nseg, double* sums,
+                       int64_t* first_viol, int64_t* kept);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAFEGPU_H */

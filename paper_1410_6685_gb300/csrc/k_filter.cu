@@ -1,0 +1,190 @@
+// k_filter.cu -- `filter` of Table 2 (sm_103a): the items for which the
+// predicate holds, in index order (a stable stream compaction).
+//
+// One CTA per 4096-element tile, tiles taken in launch order from a global
+// ticket.  The tile is staged through shared memory with 128-bit loads, each
+// thread evaluates the predicate on 16 consecutive items, a block scan gives
+// every kept item its rank inside the tile, and a decoupled look-back over
+// the tile counts of earlier tiles (bounded waits) gives the tile's global
+// output offset.  Kept items are packed in shared memory and written out
+// contiguously, so both the read and the write are coalesced: 4n bytes read,
+// 4m bytes written for m kept items.
+#include "sg_eval.cuh"
+
+namespace sgk {
+namespace {
+
+constexpr int kFB = 256;
+constexpr int kFK = 16;
+constexpr int kFTile = kFB * kFK;
+constexpr unsigned long long kFAgg = 1ull << 62;
+constexpr unsigned long long kFPre = 2ull << 62;
+constexpr unsigned long long kFCnt = (1ull << 62) - 1;
+constexpr unsigned kFSpin = 1u << 22;
+
+struct FilterHdr {
+  unsigned tile_ctr;
+  unsigned pad[63];
+};
+
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <int DEPTH>
+__global__ void __launch_bounds__(kFB) k_filter(const float* __restrict__ x,
+                                                float* __restrict__ out, long long n,
+                                                const StreamArgs a, unsigned long long* st,
+                                                FilterHdr* h, FilterResult* res) {
+  __shared__ float s_v[kFTile];
+  __shared__ unsigned s_warp[kFB / 32];
+  __shared__ unsigned s_tile;
+  __shared__ unsigned s_total;
+  __shared__ unsigned long long s_excl;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(&h->tile_ctr, 1u);
+  __syncthreads();
+  const unsigned tile = s_tile;
+  const long long base = (long long)tile * kFTile;
+  const int valid = (int)(n - base < kFTile ? n - base : kFTile);
+
+  // stage the tile (coalesced)
+  if (valid == kFTile && (((uintptr_t)(x + base)) & 15) == 0) {
+#pragma unroll
+    for (int q = 0; q < kFK / 4; ++q) {
+      const int i4 = tid + q * kFB;
+      const float4 t = __ldcs(reinterpret_cast<const float4*>(x + base) + i4);
+      reinterpret_cast<float4*>(s_v)[i4] = t;
+    }
+  } else {
+    for (int i = tid; i < valid; i += kFB) s_v[i] = __ldcs(x + base + i);
+  }
+  __syncthreads();
+
+  // predicate on 16 consecutive items per thread
+  float v[kFK];
+  unsigned keep = 0;
+#pragma unroll
+  for (int g = 0; g < kFK / 4; ++g) {
+    float xx[1][4];
+    const int i0 = tid * kFK + g * 4;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      xx[0][l] = (i0 + l < valid) ? s_v[i0 + l] : 0.0f;
+      v[g * 4 + l] = xx[0][l];
+    }
+    float r[4];
+    ev::eval_value<4, 1, DEPTH>(a, xx, base + i0, r);
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+      if (i0 + l < valid && r[l] != 0.0f) keep |= 1u << (g * 4 + l);
+  }
+  const unsigned cnt = __popc(keep);
+
+  // block exclusive scan of the counts
+  const int lane = tid & 31, w = tid >> 5;
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    unsigned t = lane < kFB / 32 ? s_warp[lane] : 0;
+    unsigned ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += y;
+    }
+    if (lane < kFB / 32) s_warp[lane] = ti - t;
+    if (lane == kFB / 32 - 1) s_total = ti;
+  }
+  __syncthreads();
+  const unsigned excl_tile = incl - cnt + s_warp[w];
+  const unsigned total = s_total;
+
+  // decoupled look-back over earlier tiles' counts
+  if (tid == 0) {
+    unsigned long long excl = 0;
+    if (tile == 0) {
+      st_relaxed64(&st[0], kFPre | total);
+    } else {
+      st_relaxed64(&st[tile], kFAgg | total);
+      long long j = (long long)tile - 1;
+      unsigned spins = 0;
+      while (j >= 0) {
+        const unsigned long long s = ld_relaxed64(&st[j]);
+        const unsigned long long flag = s & ~kFCnt;
+        if (flag == 0) {
+          if (++spins > kFSpin) {
+            atomicExch(&res->timeout, 1);
+            break;
+          }
+          if (spins > 32) __nanosleep(64);
+          continue;
+        }
+        excl += s & kFCnt;
+        if (flag == kFPre) break;
+        --j;
+      }
+      st_relaxed64(&st[tile], kFPre | (excl + total));
+    }
+    s_excl = excl;
+    if (tile == gridDim.x - 1) res->count = (long long)(excl + total);
+  }
+  __syncthreads();   // everyone has read s_v into registers
+
+  // pack the kept items in shared memory, then write them out contiguously
+  unsigned r = excl_tile;
+#pragma unroll
+  for (int k = 0; k < kFK; ++k)
+    if (keep & (1u << k)) s_v[r++] = v[k];
+  __syncthreads();
+  const unsigned long long gb = s_excl;
+  for (unsigned i = tid; i < total; i += kFB) {
+    const unsigned long long pos = gb + i;
+    if (pos < (unsigned long long)n) out[pos] = s_v[i];
+  }
+}
+
+}  // namespace
+
+size_t filter_scratch_bytes(long long n) {
+  const size_t ntiles = (size_t)((n + kFTile - 1) / kFTile);
+  return sizeof(FilterHdr) + ntiles * sizeof(unsigned long long) + 256;
+}
+
+cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& pred,
+                          int pred_depth, void* scratch, FilterResult* res, cudaStream_t s,
+                          int num_sms, int64_t* kernels, Prof* prof) {
+  (void)num_sms;
+  if (n <= 0) return cudaSuccess;   // count stays 0 (result record was zeroed)
+  const unsigned ntiles = (unsigned)((n + kFTile - 1) / kFTile);
+  FilterHdr* h = static_cast<FilterHdr*>(scratch);
+  unsigned long long* st = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) +
+                                                                 sizeof(FilterHdr));
+  cudaError_t e = cudaMemsetAsync(scratch, 0, filter_scratch_bytes(n), s);
+  if (e != cudaSuccess) return e;
+  StreamArgs a{};
+  a.prog = pred;
+  a.nin = 1;
+  a.depth = pred_depth;
+  prof_begin(prof, "filter", s);
+  if (pred_depth > 4)
+    k_filter<8><<<ntiles, kFB, 0, s>>>(x, out, n, a, st, h, res);
+  else
+    k_filter<4><<<ntiles, kFB, 0, s>>>(x, out, n, a, st, h, res);
+  prof_end(prof, s);
+  *kernels += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace sgk

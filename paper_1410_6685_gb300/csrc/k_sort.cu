@@ -1,0 +1,503 @@
+// k_sort.cu -- ascending sort of signed int32 keys (sm_103a) with the
+// postconditions of Listing 4 (`Result.is_sorted`, and `Result.count =
+// a.count` strengthened to "Result is a permutation of a") fused into the
+// last pass.
+//
+// Method: least-significant-digit radix sort with 8-bit digits.
+//   1. k_radix_hist: one read of the input builds the four 256-bin digit
+//      histograms and the input's multiset fingerprint; its last block turns
+//      the histograms into per-digit global start offsets.
+//   2. k_onesweep x4: each CTA takes the next tile (a global atomic ticket,
+//      so tiles start in order), ranks its keys stably inside the tile
+//      (warp-private counters with match_any), publishes its per-digit tile
+//      counts, finds the exclusive prefix of each digit over the preceding
+//      tiles by a decoupled look-back (bounded waits), sorts the tile in
+//      shared memory by digit and writes it out in digit runs.
+//   The last pass flips the sign bit (signed order) and, when the contracts
+//   are on, (a) checks every adjacent pair inside each tile-local digit run,
+//   (b) carries the last key of every digit run through the look-back words
+//   so each run's first key is compared with its predecessor in the output,
+//   and (c) accumulates the output's multiset fingerprint
+//   (sum of mix(k), sum of mix(k)^2 mod 2^64, count; mix = SplitMix64's
+//   output function) for comparison with the input's.  No extra pass over
+//   the keys is needed.
+#include <stdint.h>
+
+#include "sg_internal.h"
+
+namespace sgk {
+namespace {
+
+constexpr int kSortBlock = 256;
+constexpr int kKpt = 16;
+constexpr int kTile = kSortBlock * kKpt;   // 4096 keys
+constexpr int kRadix = 256;
+constexpr int kWarps = kSortBlock / 32;
+constexpr int kWarpKeys = 32 * kKpt;
+constexpr unsigned kSpinLimit = 1u << 22;
+
+constexpr unsigned kCntMask = (1u << 30) - 1;
+constexpr unsigned kAgg = 1u;
+constexpr unsigned kPre = 2u;
+
+static_assert(kSortBlock == kRadix, "one thread per digit in the look-back");
+
+struct SortHdr {
+  unsigned hist[4][kRadix];
+  unsigned offs[4][kRadix];
+  unsigned tile_ctr[4];
+  unsigned done_ctr;
+  unsigned pad[59];
+};
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <bool LAST>
+__device__ __forceinline__ unsigned digit_of(int k, int shift) {
+  const unsigned u = (unsigned)k;
+  return LAST ? ((u >> 24) ^ 0x80u) : ((u >> shift) & 0xFFu);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Exclusive scan of one value per thread over the 256-thread block.
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* s_warp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned t = lane < kWarps ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kWarps) s_warp[lane] = t - s_warp[lane];   // exclusive warp offsets
+  }
+  __syncthreads();
+  return x - v + s_warp[w];
+}
+
+__device__ __forceinline__ void fp_add(unsigned long long& f1, unsigned long long& f2, int k) {
+  const unsigned long long m = mix64((unsigned long long)(unsigned)k);
+  f1 += m;
+  f2 += m * m;
+}
+
+__device__ __forceinline__ void fp_flush(unsigned long long f1, unsigned long long f2,
+                                         unsigned long long* dst) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+    f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(dst, f1);
+    atomicAdd(dst + 1, f2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, long long n,
+                                                    SortHdr* h, SortResult* res) {
+  __shared__ unsigned sh[4][kRadix];
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  unsigned long long f1 = 0, f2 = 0;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long start = 0;
+  auto count = [&](int k) {
+    const unsigned u = (unsigned)k;
+    atomicAdd(&sh[0][u & 0xFFu], 1u);
+    atomicAdd(&sh[1][(u >> 8) & 0xFFu], 1u);
+    atomicAdd(&sh[2][(u >> 16) & 0xFFu], 1u);
+    atomicAdd(&sh[3][(u >> 24) ^ 0x80u], 1u);
+    fp_add(f1, f2, k);
+  };
+  if (((uintptr_t)in & 15) == 0) {
+    const long long nv = n >> 2;
+    start = nv << 2;
+    for (long long v = tid; v < nv; v += stride) {
+      const int4 q = __ldg(reinterpret_cast<const int4*>(in) + v);
+      count(q.x);
+      count(q.y);
+      count(q.z);
+      count(q.w);
+    }
+  }
+  for (long long i = start + tid; i < n; i += stride) count(in[i]);
+  fp_flush(f1, f2, res->fp_in);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
+    const unsigned c = (&sh[0][0])[i];
+    if (c) atomicAdd(&(&h->hist[0][0])[i], c);
+  }
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(&h->done_ctr, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (threadIdx.x < 4) {
+    const int p = threadIdx.x;
+    unsigned run = 0;
+    for (int d = 0; d < kRadix; ++d) {
+      h->offs[p][d] = run;
+      run += __ldcg(&h->hist[p][d]);
+    }
+  }
+  if (threadIdx.x == 0) res->cnt_in = n;
+}
+
+// ---------------------------------------------------------------------------
+template <bool LAST, bool CHECK>
+__global__ void __launch_bounds__(kSortBlock) k_onesweep(
+    const int* __restrict__ in, int* __restrict__ out, long long n, int pass, SortHdr* h,
+    unsigned* st32, unsigned long long* st64, SortResult* res) {
+  __shared__ int s_keys[kTile];
+  __shared__ unsigned s_whist[kWarps][kRadix];
+  __shared__ unsigned s_start[kRadix];
+  __shared__ long long s_gbase[kRadix];
+  __shared__ unsigned s_warp[kWarps];
+  __shared__ unsigned s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(&h->tile_ctr[pass], 1u);
+  for (int i = tid; i < kWarps * kRadix; i += kSortBlock) (&s_whist[0][0])[i] = 0;
+  __syncthreads();
+  const unsigned tile = s_tile;
+  const long long base = (long long)tile * kTile;
+  const int shift = pass * 8;
+  const int valid_cnt = (int)(n - base < kTile ? n - base : kTile);
+
+  // load: warp w owns keys [w*512, (w+1)*512) of the tile, 32 consecutive per round
+  int key[kKpt];
+  unsigned dig[kKpt];
+  const long long wbase = base + (long long)w * kWarpKeys + lane;
+#pragma unroll
+  for (int r = 0; r < kKpt; ++r) {
+    const long long idx = wbase + r * 32;
+    const bool ok = idx < n;
+    key[r] = ok ? __ldcs(in + idx) : 0;
+    dig[r] = ok ? digit_of<LAST>(key[r], shift) : (unsigned)kRadix;
+  }
+
+  // stable rank of each key among the warp's keys of the same digit
+  unsigned rank[kKpt];
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int r = 0; r < kKpt; ++r) {
+    const unsigned d = dig[r];
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned before = __popc(peers & lt);
+    const unsigned prev = d < kRadix ? s_whist[w][d] : 0u;
+    __syncwarp();
+    if (d < kRadix && before == 0) s_whist[w][d] = prev + __popc(peers);
+    __syncwarp();
+    rank[r] = prev + before;
+  }
+  __syncthreads();
+
+  // per digit: tile count and exclusive offsets of the warps
+  unsigned cnt = 0;
+  {
+    const int d = tid;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+      const unsigned t = s_whist[ww][d];
+      s_whist[ww][d] = cnt;
+      cnt += t;
+    }
+  }
+  // publish the tile aggregate as early as possible
+  if (!(LAST && CHECK)) st_relaxed(&st32[(size_t)tile * kRadix + tid], ((tile == 0 ? kPre : kAgg) << 30) | cnt);
+  const unsigned start = block_excl_scan(cnt, s_warp);
+  s_start[tid] = start;
+  __syncthreads();
+
+  // sort the tile in shared memory by digit (stable)
+#pragma unroll
+  for (int r = 0; r < kKpt; ++r) {
+    const unsigned d = dig[r];
+    if (d < kRadix) s_keys[s_start[d] + s_whist[w][d] + rank[r]] = key[r];
+  }
+  __syncthreads();
+
+  // decoupled look-back: exclusive prefix of digit `tid` over earlier tiles
+  const int d = tid;
+  unsigned long long excl = 0;
+  bool timeout = false;
+  if (!(LAST && CHECK)) {
+    if (tile > 0) {
+      long long j = (long long)tile - 1;
+      unsigned spins = 0;
+      while (j >= 0) {
+        const unsigned v = ld_relaxed(&st32[(size_t)j * kRadix + d]);
+        const unsigned flag = v >> 30;
+        if (flag == 0) {
+          if (++spins > kSpinLimit) { timeout = true; break; }
+          if (spins > 32) __nanosleep(64);
+          continue;
+        }
+        excl += v & kCntMask;
+        if (flag == kPre) break;
+        --j;
+      }
+      st_relaxed(&st32[(size_t)tile * kRadix + d], (kPre << 30) | (unsigned)(excl + cnt));
+    }
+  } else {
+    // 64-bit words: flag(2) | count(30) | last key of the digit run (32)
+    const int first_key = cnt ? s_keys[start] : 0;
+    const int last_key = cnt ? s_keys[start + cnt - 1] : 0;
+    auto word = [](unsigned flag, unsigned c, int k) {
+      return ((unsigned long long)((flag << 30) | c) << 32) | (unsigned)k;
+    };
+    bool found = false;
+    int pred_last = 0;
+    if (tile == 0) {
+      st_relaxed64(&st64[d], word(kPre, cnt, last_key));
+    } else {
+      st_relaxed64(&st64[(size_t)tile * kRadix + d], word(kAgg, cnt, last_key));
+      long long j = (long long)tile - 1;
+      unsigned spins = 0;
+      while (j >= 0) {
+        const unsigned long long v = ld_relaxed64(&st64[(size_t)j * kRadix + d]);
+        const unsigned hi = (unsigned)(v >> 32);
+        const unsigned flag = hi >> 30;
+        if (flag == 0) {
+          if (++spins > kSpinLimit) { timeout = true; break; }
+          if (spins > 32) __nanosleep(64);
+          continue;
+        }
+        const unsigned c = hi & kCntMask;
+        if (!found && c > 0) {
+          found = true;
+          pred_last = (int)(unsigned)v;
+        }
+        excl += c;
+        if (flag == kPre) break;
+        --j;
+      }
+      const int carry = cnt ? last_key : pred_last;
+      st_relaxed64(&st64[(size_t)tile * kRadix + d], word(kPre, (unsigned)(excl + cnt), carry));
+    }
+    // the first key of this run must not be below the last key before it
+    if (cnt && found && first_key < pred_last) {
+      const long long pos = (long long)h->offs[pass][d] + (long long)excl - 1;
+      atomicMax(&res->unsorted_enc, ~(unsigned long long)pos);
+    }
+  }
+  if (timeout) atomicExch(&res->timeout, 1);
+  s_gbase[d] = (long long)h->offs[pass][d] + (long long)excl - (long long)start;
+  __syncthreads();
+
+  // write the tile out in digit runs
+  unsigned long long f1 = 0, f2 = 0;
+  long long bad = -1;
+  for (int i = tid; i < valid_cnt; i += kSortBlock) {
+    const int k = s_keys[i];
+    const unsigned dk = digit_of<LAST>(k, shift);
+    const long long pos = s_gbase[dk] + i;
+    if (pos >= 0 && pos < n) __stcs(out + pos, k);   // only a timed-out look-back can miss
+    if (LAST && CHECK) {
+      fp_add(f1, f2, k);
+      if (i + 1 < valid_cnt) {
+        const int k2 = s_keys[i + 1];
+        if (digit_of<LAST>(k2, shift) == dk && k > k2 && bad < 0) bad = pos;
+      }
+    }
+  }
+  if (LAST && CHECK) {
+    fp_flush(f1, f2, res->fp_out);
+    unsigned long long enc = bad >= 0 ? ~(unsigned long long)bad : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long e2 = __shfl_xor_sync(0xffffffffu, enc, o);
+      enc = e2 > enc ? e2 : enc;
+    }
+    if (lane == 0 && enc) atomicMax(&res->unsorted_enc, enc);
+    if (tid == 0) {
+      atomicAdd((unsigned long long*)&res->cnt_out, (unsigned long long)valid_cnt);
+      res->checked = 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stand-alone checks (re-read the vector).
+
+__global__ void __launch_bounds__(256) k_check_sorted(const int* __restrict__ x, long long n,
+                                                      SortResult* res) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long bad = -1;
+  for (long long i = tid; i + 1 < n && bad < 0; i += stride)
+    if (__ldg(x + i) > __ldg(x + i + 1)) bad = i;
+  unsigned long long enc = bad >= 0 ? ~(unsigned long long)bad : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long e2 = __shfl_xor_sync(0xffffffffu, enc, o);
+    enc = e2 > enc ? e2 : enc;
+  }
+  if ((threadIdx.x & 31) == 0 && enc) atomicMax(&res->unsorted_enc, enc);
+}
+
+__global__ void __launch_bounds__(256) k_fingerprint(const int* __restrict__ x, long long n,
+                                                     unsigned long long* fp, long long* cnt) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long f1 = 0, f2 = 0;
+  for (long long i = tid; i < n; i += stride) fp_add(f1, f2, __ldg(x + i));
+  fp_flush(f1, f2, fp);
+  if (tid == 0) *cnt = n;
+}
+
+struct Layout {
+  size_t st32[3];
+  size_t st64;
+  size_t zero_bytes;
+  size_t tmp;
+  size_t total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout layout(long long n) {
+  Layout L;
+  const size_t ntiles = (size_t)((n + kTile - 1) / kTile);
+  size_t off = align256(sizeof(SortHdr));
+  for (int p = 0; p < 3; ++p) {
+    L.st32[p] = off;
+    off = align256(off + ntiles * kRadix * sizeof(unsigned));
+  }
+  L.st64 = off;
+  off = align256(off + ntiles * kRadix * sizeof(unsigned long long));
+  L.zero_bytes = off;
+  L.tmp = off;
+  off = align256(off + (size_t)n * sizeof(int));
+  L.total = off;
+  return L;
+}
+
+int grid_for(long long units, int num_sms, int per_sm) {
+  long long g = (units + 255) / 256;
+  long long cap = (long long)num_sms * per_sm;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+size_t sort_scratch_bytes(long long n) { return layout(n).total; }
+
+cudaError_t launch_sort(const int32_t* in, int32_t* out, long long n, bool contracts,
+                        void* scratch, SortResult* res, cudaStream_t s, int num_sms,
+                        int64_t* kernels, const SortInject* inject, Prof* prof) {
+  if (n <= 0) return cudaSuccess;
+  const Layout L = layout(n);
+  char* base = static_cast<char*>(scratch);
+  SortHdr* h = reinterpret_cast<SortHdr*>(base);
+  unsigned* st32[3];
+  for (int p = 0; p < 3; ++p) st32[p] = reinterpret_cast<unsigned*>(base + L.st32[p]);
+  unsigned long long* st64 = reinterpret_cast<unsigned long long*>(base + L.st64);
+  int* tmp = reinterpret_cast<int*>(base + L.tmp);
+  cudaError_t e = cudaMemsetAsync(base, 0, L.zero_bytes, s);
+  if (e != cudaSuccess) return e;
+  prof_begin(prof, "radix_hist", s);
+  k_radix_hist<<<grid_for((n + 3) / 4 / 8, num_sms, 4), 256, 0, s>>>(in, n, h, res);
+  prof_end(prof, s);
+  const unsigned ntiles = (unsigned)((n + kTile - 1) / kTile);
+  prof_begin(prof, "onesweep", s);
+  k_onesweep<false, false><<<ntiles, kSortBlock, 0, s>>>(in, tmp, n, 0, h, st32[0], st64, res);
+  prof_end(prof, s);
+  prof_begin(prof, "onesweep", s);
+  k_onesweep<false, false><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 1, h, st32[1], st64, res);
+  prof_end(prof, s);
+  prof_begin(prof, "onesweep", s);
+  k_onesweep<false, false><<<ntiles, kSortBlock, 0, s>>>(out, tmp, n, 2, h, st32[2], st64, res);
+  prof_end(prof, s);
+  if (inject && inject->mode == 1 && inject->i < n && inject->j < n) {
+    // swap through the (now free) output buffer: stream-ordered host copies
+    e = cudaMemcpyAsync(out, tmp + inject->i, sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp + inject->i, tmp + inject->j, sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp + inject->j, out, sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  } else if (inject && inject->mode == 2 && inject->i < n) {
+    static int value;   // pageable source: the copy is staged before it returns
+    value = (int)inject->j;
+    e = cudaMemcpyAsync(tmp + inject->i, &value, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  // the last pass uses the (zeroed) 64-bit area; without contracts only its
+  // first half, as 32-bit words
+  unsigned* st_last = reinterpret_cast<unsigned*>(st64);
+  prof_begin(prof, contracts ? "onesweep_last_checked" : "onesweep", s);
+  if (contracts)
+    k_onesweep<true, true><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res);
+  else
+    k_onesweep<true, false><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res);
+  prof_end(prof, s);
+  *kernels += 5;
+  return cudaGetLastError();
+}
+
+size_t check_scratch_bytes() { return 0; }
+
+cudaError_t launch_check_sorted(const int32_t* x, long long n, SortResult* res, void*,
+                                cudaStream_t s, int num_sms, int64_t* kernels, Prof* prof) {
+  if (n <= 1) return cudaSuccess;
+  prof_begin(prof, "check_sorted", s);
+  k_check_sorted<<<grid_for(n, num_sms, 8), 256, 0, s>>>(x, n, res);
+  prof_end(prof, s);
+  *kernels += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_perm(const int32_t* x, const int32_t* ref, long long n,
+                              SortResult* res, void*, cudaStream_t s, int num_sms,
+                              int64_t* kernels, Prof* prof) {
+  if (n <= 0) return cudaSuccess;
+  prof_begin(prof, "fingerprint", s);
+  k_fingerprint<<<grid_for(n, num_sms, 8), 256, 0, s>>>(x, n, res->fp_out, &res->cnt_out);
+  k_fingerprint<<<grid_for(n, num_sms, 8), 256, 0, s>>>(ref, n, res->fp_in, &res->cnt_in);
+  prof_end(prof, s);
+  *kernels += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace sgk

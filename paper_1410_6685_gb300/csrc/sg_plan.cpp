@@ -1,0 +1,805 @@
+// sg_plan.cpp -- the optimizer and executor of the deferred queue (Sec. 5).
+//
+// The queue of one context is a DAG of data nodes (values) and kernel nodes
+// (the queued calls), in a valid topological order.  The optimizer walks it
+// in order and merges element-wise calls over collections of one count into
+// passes of the fused streaming kernel:
+//   * map chains become one expression (Fig. 3: X[i]+Y[i] -> a*X[i]+Y[i]):
+//     a value produced earlier in the pass is substituted into its consumer;
+//   * a map and the reduction that consumes it share the pass (Fig. 2);
+//   * for_all / exists queries and range contracts on values of the pass are
+//     evaluated in the same pass (Sec. 4, range contracts on the device);
+//   * a filter whose result is only summed becomes a masked reduction, so
+//     the filtered collection is never built;
+//   * an intermediate is written to memory only if a handle still refers to
+//     it or a later pass needs it ("collapsing intermediate dependencies").
+// Sort, filter, matrix product and their contracts become their own kernel
+// groups; the sort's built-in postconditions ride in its last pass.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+
+#include "sg_internal.h"
+#include "sg_plan.h"
+
+namespace {
+
+using sgk::Prog;
+
+struct Op {
+  uint8_t op;
+  int8_t arg;
+  float cst;
+};
+
+enum class PK { STREAM, FILTER, SORT, CHECK_SORTED, CHECK_PERM, MATMUL, FREIVALDS };
+
+struct Pass {
+  PK kind = PK::STREAM;
+  int64_t n = 0;
+  std::vector<Node*> nodes;
+  // STREAM
+  std::vector<Value*> inputs;                  // loaded values, slot = index
+  std::map<Value*, std::vector<Op>> inl;       // values produced in the pass
+  std::map<Value*, std::vector<Op>> mask;      // masked (filtered) values
+  std::map<Value*, Value*> mask_base;          // masked value -> filtered input
+  std::vector<Value*> stores;                  // materialised outputs
+  std::vector<Op> prog;
+  std::vector<Node*> preds;                    // slot = index
+  Value* reduce_of = nullptr;
+  std::vector<Node*> reduces;
+  int est_ops = 0;
+  int depth = 0;
+  // SORT (+ its fused checks), FILTER, CHECK_*, MATMUL, FREIVALDS
+  Node* main = nullptr;
+  Node* chk_sorted = nullptr;
+  Node* chk_perm = nullptr;
+};
+
+bool is_f32_stream_node(const Node* n) {
+  switch (n->kind) {
+    case NK::MAP:
+    case NK::REDUCE:
+    case NK::QUANT:
+      return true;
+    case NK::CHECK:
+      return n->ckind == SG_C_FOR_ALL || n->ckind == SG_C_EXISTS;
+    default:
+      return false;
+  }
+}
+
+int64_t node_len(const Node* n) { return n->in[0] ? n->in[0]->n : 0; }
+
+// Depth bookkeeping of a finished program: depth before each op, max depth.
+bool program_depths(const std::vector<Op>& ops, std::vector<uint8_t>* before, int* maxd) {
+  int d = 0, mx = 0;
+  if (before) before->clear();
+  for (const Op& o : ops) {
+    if (before) before->push_back((uint8_t)d);
+    int need = 0, delta = 0;
+    switch (o.op) {
+      case SG_OP_LOAD: case SG_OP_CONST: case SG_OP_INDEX: delta = 1; break;
+      case SG_OP_FMA: case SG_OP_SELECT: need = 3; delta = -2; break;
+      case SG_OP_NEG: case SG_OP_ABS: case SG_OP_SQRT: case SG_OP_NOT: need = 1; break;
+      case SG_OP_DUP: need = 1; delta = 1; break;
+      case SG_OP_SWAP: need = 2; break;
+      case sgk::K_STORE: need = 1; break;
+      case sgk::K_PRED: case sgk::K_MASK: case sgk::K_REDUCE: case sgk::K_POP:
+        need = 1; delta = -1; break;
+      default: need = 2; delta = -1; break;   // binary arithmetic / comparison
+    }
+    if (d < need) return false;
+    d += delta;
+    mx = std::max(mx, d);
+  }
+  if (d != 0) return false;
+  *maxd = mx;
+  return mx <= sgk::kMaxDepth;
+}
+
+struct Planner {
+  sg_ctx* c;
+  std::vector<Node*> nodes;
+  std::set<Node*> unmaskable;   // filters that must be compacted
+  std::vector<Pass> passes;
+  std::map<Value*, std::vector<Node*>> consumers;
+
+  explicit Planner(sg_ctx* ctx) : c(ctx) {
+    for (auto& n : c->pending) nodes.push_back(n.get());
+    for (Node* n : nodes)
+      for (int k = 0; k < n->nin; ++k)
+        if (n->in[k]) consumers[n->in[k].get()].push_back(n);
+  }
+
+  // A filter can become a mask when only reductions consume its result and
+  // no handle refers to it.
+  bool maskable(Node* f) {
+    if (c->fusion != SG_FUSE_ON || unmaskable.count(f)) return false;
+    Value* y = f->out.get();
+    if (y->handles > 0) return false;
+    auto it = consumers.find(y);
+    if (it == consumers.end()) return true;
+    for (Node* u : it->second)
+      if (u->kind != NK::REDUCE) return false;
+    return true;
+  }
+
+  bool dead(Node* n) {
+    // a map whose result nobody will ever see is not computed
+    if (n->kind != NK::MAP || n->inplace) return false;
+    Value* v = n->out.get();
+    return v->handles == 0 && consumers.find(v) == consumers.end();
+  }
+
+  int slot_of(Pass& P, Value* v, bool add) {
+    for (size_t i = 0; i < P.inputs.size(); ++i)
+      if (P.inputs[i] == v) return (int)i;
+    if (!add || P.inputs.size() >= (size_t)sgk::kMaxIn) return -1;
+    P.inputs.push_back(v);
+    return (int)P.inputs.size() - 1;
+  }
+
+  // Ops computing value v inside pass P (a load, or the substituted
+  // expression of a value produced earlier in P).
+  bool value_ops(Pass& P, Value* v, std::vector<Op>* out) {
+    if (P.mask.count(v)) return false;   // a masked value is only reducible
+    auto it = P.inl.find(v);
+    if (it != P.inl.end()) {
+      out->insert(out->end(), it->second.begin(), it->second.end());
+      return true;
+    }
+    int s = slot_of(P, v, true);
+    if (s < 0) return false;
+    out->push_back(Op{SG_OP_LOAD, (int8_t)s, 0.0f});
+    return true;
+  }
+
+  bool expand(Pass& P, const sg_expr& e, Node* n, std::vector<Op>* out) {
+    for (int p = 0; p < e.nops; ++p) {
+      const sg_expr_op& o = e.ops[p];
+      if (o.op == SG_OP_LOAD) {
+        if (!value_ops(P, n->in[o.arg].get(), out)) return false;
+      } else {
+        out->push_back(Op{(uint8_t)o.op, 0, o.value});
+      }
+    }
+    return true;
+  }
+
+  // Try to add node n to the open stream pass; all-or-nothing.
+  bool try_add(Pass& P, Node* n) {
+    Pass T = P;   // tentative copy (small)
+    std::vector<Op> ops;
+    int extra = 0;
+    switch (n->kind) {
+      case NK::MAP: {
+        if (!expand(T, n->expr, n, &ops)) return false;
+        extra = 2;   // a possible STORE + POP
+        T.inl[n->out.get()] = ops;
+        break;
+      }
+      case NK::FILTER: {
+        // masked value: y = x where pred(x)
+        std::vector<Op> xo, mo;
+        Value* x = n->in[0].get();
+        if (!value_ops(T, x, &xo)) return false;
+        for (int p = 0; p < n->expr.nops; ++p) {
+          const sg_expr_op& o = n->expr.ops[p];
+          if (o.op == SG_OP_LOAD) mo.insert(mo.end(), xo.begin(), xo.end());
+          else mo.push_back(Op{(uint8_t)o.op, 0, o.value});
+        }
+        T.mask[n->out.get()] = mo;
+        T.inl[n->out.get()] = xo;
+        ops = {};
+        break;
+      }
+      case NK::REDUCE: {
+        Value* v = n->in[0].get();
+        if (T.reduce_of && T.reduce_of != v) return false;
+        if (!T.reduce_of) {
+          std::vector<Op> r;
+          auto mk = T.mask.find(v);
+          if (mk != T.mask.end()) {
+            r = mk->second;
+            r.push_back(Op{sgk::K_MASK, 0, 0.0f});
+            auto vi = T.inl.find(v);
+            r.insert(r.end(), vi->second.begin(), vi->second.end());
+          } else if (!value_ops(T, v, &r)) {
+            return false;
+          }
+          r.push_back(Op{sgk::K_REDUCE, 0, 0.0f});
+          ops = r;
+          T.reduce_of = v;
+        }
+        T.reduces.push_back(n);
+        break;
+      }
+      case NK::QUANT:
+      case NK::CHECK: {
+        if ((int)T.preds.size() >= sgk::kMaxPred) return false;
+        if (!expand(T, n->expr, n, &ops)) return false;
+        ops.push_back(Op{sgk::K_PRED, (int8_t)T.preds.size(), 0.0f});
+        T.preds.push_back(n);
+        break;
+      }
+      default:
+        return false;
+    }
+    if (T.est_ops + (int)ops.size() + extra > sgk::kMaxProg) return false;
+    if (n->kind != NK::MAP && n->kind != NK::FILTER) {
+      int d = 0;
+      std::vector<Op> chk = ops;
+      if (!program_depths(chk, nullptr, &d)) return false;
+    } else if (n->kind == NK::MAP) {
+      std::vector<Op> chk = T.inl[n->out.get()];
+      chk.push_back(Op{sgk::K_POP, 0, 0.0f});
+      int d = 0;
+      if (!program_depths(chk, nullptr, &d)) return false;
+    }
+    T.est_ops += (int)ops.size() + extra;
+    T.nodes.push_back(n);
+    P = std::move(T);
+    return true;
+  }
+
+  void group() {
+    passes.clear();
+    bool open = false;
+    for (Node* n : nodes) {
+      if (dead(n)) continue;
+      const bool streamable = is_f32_stream_node(n) || (n->kind == NK::FILTER && maskable(n));
+      if (streamable) {
+        const int64_t len = node_len(n);
+        if (open && c->fusion == SG_FUSE_ON && passes.back().n == len && try_add(passes.back(), n))
+          continue;
+        Pass P;
+        P.kind = PK::STREAM;
+        P.n = len;
+        if (!try_add(P, n)) {
+          // cannot fail for a lone node with loaded inputs unless the node
+          // consumes a masked value produced in a closed pass
+          if (n->kind == NK::REDUCE) unmaskable.insert(n->in[0]->producer);
+          P = Pass{};
+          P.kind = PK::STREAM;
+          P.n = len;
+          try_add(P, n);
+        }
+        passes.push_back(std::move(P));
+        open = true;
+        continue;
+      }
+      open = false;
+      Pass P;
+      P.n = node_len(n);
+      P.main = n;
+      P.nodes.push_back(n);
+      switch (n->kind) {
+        case NK::FILTER: P.kind = PK::FILTER; break;
+        case NK::SORT: P.kind = PK::SORT; break;
+        case NK::MATMUL: P.kind = PK::MATMUL; break;
+        case NK::CHECK:
+          if (n->ckind == SG_C_SORTED) {
+            // fuse into the sort that produced the checked value
+            if (c->fusion == SG_FUSE_ON && !passes.empty() && passes.back().kind == PK::SORT &&
+                passes.back().main->out.get() == n->in[0].get() && !passes.back().chk_sorted) {
+              passes.back().chk_sorted = n;
+              passes.back().nodes.push_back(n);
+              continue;
+            }
+            P.kind = PK::CHECK_SORTED;
+          } else if (n->ckind == SG_C_PERMUTATION) {
+            if (c->fusion == SG_FUSE_ON && !passes.empty() && passes.back().kind == PK::SORT &&
+                passes.back().main->out.get() == n->in[0].get() &&
+                passes.back().main->in[0].get() == n->in[1].get() && !passes.back().chk_perm) {
+              passes.back().chk_perm = n;
+              passes.back().nodes.push_back(n);
+              continue;
+            }
+            P.kind = PK::CHECK_PERM;
+          } else {
+            P.kind = PK::FREIVALDS;
+          }
+          break;
+        default:
+          break;
+      }
+      passes.push_back(std::move(P));
+    }
+  }
+
+  // Masked filters whose reductions ended up in another pass are compacted.
+  bool validate() {
+    bool ok = true;
+    for (Pass& P : passes) {
+      if (P.kind != PK::STREAM) continue;
+      for (auto& kv : P.mask) {
+        Value* y = kv.first;
+        for (Node* u : consumers[y]) {
+          if (std::find(P.nodes.begin(), P.nodes.end(), u) == P.nodes.end()) {
+            unmaskable.insert(y->producer);
+            ok = false;
+          }
+        }
+      }
+    }
+    return ok;
+  }
+
+  int pass_of_node(Node* n) {
+    for (size_t i = 0; i < passes.size(); ++i)
+      if (std::find(passes[i].nodes.begin(), passes[i].nodes.end(), n) != passes[i].nodes.end())
+        return (int)i;
+    return -1;
+  }
+
+  bool must_store(const Pass& P, Node* n) {
+    Value* v = n->out.get();
+    if (n->inplace || v->handles > 0) return true;
+    for (Node* u : consumers[v])
+      if (std::find(P.nodes.begin(), P.nodes.end(), u) == P.nodes.end()) return true;
+    return false;
+  }
+
+  // Emit the program of every stream pass (after grouping is final).
+  void emit() {
+    for (Pass& P : passes) {
+      if (P.kind != PK::STREAM) continue;
+      // rebuild inline expressions in node order and emit ops
+      Pass E;
+      E.kind = PK::STREAM;
+      E.n = P.n;
+      E.nodes = P.nodes;
+      for (Node* n : P.nodes) {
+        switch (n->kind) {
+          case NK::MAP: {
+            std::vector<Op> ops;
+            expand(E, n->expr, n, &ops);
+            E.inl[n->out.get()] = ops;
+            if (must_store(P, n)) {
+              int slot = (int)E.stores.size();
+              E.stores.push_back(n->out.get());
+              E.prog.insert(E.prog.end(), ops.begin(), ops.end());
+              E.prog.push_back(Op{sgk::K_STORE, (int8_t)slot, 0.0f});
+              E.prog.push_back(Op{sgk::K_POP, 0, 0.0f});
+            }
+            break;
+          }
+          case NK::FILTER: {
+            std::vector<Op> xo, mo;
+            value_ops(E, n->in[0].get(), &xo);
+            for (int p = 0; p < n->expr.nops; ++p) {
+              const sg_expr_op& o = n->expr.ops[p];
+              if (o.op == SG_OP_LOAD) mo.insert(mo.end(), xo.begin(), xo.end());
+              else mo.push_back(Op{(uint8_t)o.op, 0, o.value});
+            }
+            E.mask[n->out.get()] = mo;
+            E.inl[n->out.get()] = xo;
+            break;
+          }
+          case NK::REDUCE: {
+            Value* v = n->in[0].get();
+            E.reduces.push_back(n);
+            if (E.reduce_of) break;
+            E.reduce_of = v;
+            auto mk = E.mask.find(v);
+            if (mk != E.mask.end()) {
+              E.prog.insert(E.prog.end(), mk->second.begin(), mk->second.end());
+              E.prog.push_back(Op{sgk::K_MASK, 0, 0.0f});
+              auto& vi = E.inl[v];
+              E.prog.insert(E.prog.end(), vi.begin(), vi.end());
+            } else {
+              value_ops(E, v, &E.prog);
+            }
+            E.prog.push_back(Op{sgk::K_REDUCE, 0, 0.0f});
+            break;
+          }
+          default: {  // QUANT / CHECK
+            std::vector<Op> ops;
+            expand(E, n->expr, n, &ops);
+            E.prog.insert(E.prog.end(), ops.begin(), ops.end());
+            E.prog.push_back(Op{sgk::K_PRED, (int8_t)E.preds.size(), 0.0f});
+            E.preds.push_back(n);
+            break;
+          }
+        }
+      }
+      program_depths(E.prog, nullptr, &E.depth);
+      P = std::move(E);
+    }
+  }
+
+  void plan() {
+    for (int it = 0; it < 8; ++it) {
+      group();
+      if (validate()) break;
+    }
+    emit();
+  }
+};
+
+
+// ---------------------------------------------------------------------------
+// execution
+
+constexpr int kStreamBlock = 256;
+constexpr long long kNone = 0x7fffffffffffffffLL;
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+sg_status cuda_fail(sg_ctx* c, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  c->err = buf;
+  return SG_ERR_CUDA;
+}
+
+sg_status ensure_storage(sg_ctx* c, Value* v) {
+  if (v->st) return SG_OK;
+  size_t es = (v->dt == SG_F64 || v->dt == SG_I64) ? 8 : (v->dt == SG_BF16 || v->dt == SG_F16) ? 2 : 4;
+  auto st = std::make_shared<Storage>();
+  st->bytes = (size_t)v->n * es;
+  st->stream = c->stream;
+  if (st->bytes) {
+    cudaError_t e = cudaMallocAsync(&st->ptr, st->bytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "output allocation");
+    st->owned = true;
+  }
+  v->st = std::move(st);
+  return SG_OK;
+}
+
+sg_status ensure_scratch(sg_ctx* c, size_t bytes) {
+  if (c->scratch_bytes >= bytes) return SG_OK;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream sync");
+  if (c->scratch) cudaFree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_bytes = 0;
+  size_t nb = round_up(std::max(bytes, (size_t)1 << 20), (size_t)1 << 20);
+  e = cudaMalloc(&c->scratch, nb);
+  if (e != cudaSuccess) return cuda_fail(c, e, "scratch allocation");
+  c->scratch_bytes = nb;
+  return SG_OK;
+}
+
+sg_status ensure_host_res(sg_ctx* c, size_t bytes) {
+  if (c->host_res_bytes >= bytes) return SG_OK;
+  if (c->host_res) cudaFreeHost(c->host_res);
+  c->host_res = nullptr;
+  size_t nb = round_up(std::max(bytes, (size_t)4096), 4096);
+  cudaError_t e = cudaMallocHost(&c->host_res, nb);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pinned result buffer");
+  c->host_res_bytes = nb;
+  return SG_OK;
+}
+
+int stream_grid(sg_ctx* c, const Pass& P) {
+  const long long units = std::max<long long>(1, (P.n + 3) / 4);
+  const long long want = (units + kStreamBlock - 1) / kStreamBlock;
+  const int occ = sgk::stream_max_blocks_per_sm((int)P.inputs.size(), P.depth, kStreamBlock);
+  const long long cap = (long long)c->num_sms * occ;
+  return (int)std::max<long long>(1, std::min(want, cap));
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+void record_violation(sg_ctx* c, Node* n, int64_t first, double observed, bool* have,
+                      sg_status* status) {
+  n->failed = true;
+  n->first = first;
+  n->observed = observed;
+  if (*have) return;
+  *have = true;
+  c->has_violation = true;
+  c->last_violation.contract_id = n->builtin ? -1 : n->cid;
+  c->last_violation.role = n->role;
+  c->last_violation.kind = n->ckind;
+  c->last_violation.op_id = n->in[0] && n->in[0]->producer ? n->in[0]->producer->id : -1;
+  c->last_violation.first_index = first;
+  c->last_violation.observed = observed;
+  *status = n->role == SG_PRE ? SG_ERR_PRECONDITION : SG_ERR_POSTCONDITION;
+}
+
+}  // namespace
+
+sg_status sg_execute_pending(sg_ctx* c) {
+  Planner pl(c);
+  pl.plan();
+  std::vector<Pass>& passes = pl.passes;
+  c->has_violation = false;
+
+  // scratch: result records, then the largest per-pass work area
+  const size_t res_bytes = round_up(std::max<size_t>(1, passes.size()) * sgk::kResultBytes, 256);
+  size_t work = 0;
+  for (Pass& P : passes) {
+    switch (P.kind) {
+      case PK::STREAM:
+        work = std::max(work, (size_t)stream_grid(c, P) * sizeof(sgk::PassResult));
+        break;
+      case PK::SORT: work = std::max(work, sgk::sort_scratch_bytes(P.n)); break;
+      case PK::FILTER: work = std::max(work, sgk::filter_scratch_bytes(P.n)); break;
+      case PK::CHECK_SORTED:
+      case PK::CHECK_PERM: work = std::max(work, sgk::check_scratch_bytes()); break;
+      default: break;
+    }
+  }
+  sg_status st = ensure_scratch(c, res_bytes + work);
+  if (!st) st = ensure_host_res(c, res_bytes);
+  if (st) {
+    c->pending.clear();
+    return st;
+  }
+  char* dres = static_cast<char*>(c->scratch);
+  void* dwork = dres + res_bytes;
+  cudaError_t e = cudaMemsetAsync(dres, 0, res_bytes, c->stream);
+  sg_status status = SG_OK;
+
+  for (size_t i = 0; i < passes.size() && e == cudaSuccess && !status; ++i) {
+    Pass& P = passes[i];
+    void* rec = dres + i * sgk::kResultBytes;
+    switch (P.kind) {
+      case PK::STREAM: {
+        if (P.prog.empty()) break;
+        sgk::StreamArgs a{};
+        bool vec = true;
+        for (size_t k = 0; k < P.inputs.size(); ++k) {
+          Value* v = P.inputs[k];
+          if (!v->st) { status = SG_ERR_INVALID_ARG; c->err = "internal: unmaterialised input"; break; }
+          a.in[k] = static_cast<const float*>(v->st->ptr);
+          vec &= aligned16(a.in[k]);
+        }
+        for (size_t k = 0; k < P.stores.size() && !status; ++k) {
+          status = ensure_storage(c, P.stores[k]);
+          if (!status) {
+            a.out[k] = static_cast<float*>(P.stores[k]->st->ptr);
+            vec &= aligned16(a.out[k]);
+          }
+        }
+        if (status) break;
+        a.n = P.n;
+        a.prog.nops = (int)P.prog.size();
+        std::vector<uint8_t> before;
+        int md = 0;
+        program_depths(P.prog, &before, &md);
+        for (size_t p = 0; p < P.prog.size(); ++p) {
+          a.prog.op[p] = P.prog[p].op;
+          a.prog.arg[p] = P.prog[p].arg;
+          a.prog.cst[p] = P.prog[p].cst;
+          a.prog.depth[p] = before[p];
+        }
+        a.nin = (int)P.inputs.size();
+        a.depth = md;
+        a.has_reduce = P.reduce_of != nullptr;
+        a.npred = (int)P.preds.size();
+        a.pred_exists = 0;
+        for (size_t p = 0; p < P.preds.size(); ++p) {
+          Node* q = P.preds[p];
+          const bool ex = q->kind == NK::QUANT ? q->exists : q->ckind == SG_C_EXISTS;
+          if (ex) a.pred_exists |= 1u << p;
+        }
+        a.partials = static_cast<sgk::PassResult*>(dwork);
+        a.counter = c->counter;
+        a.result = static_cast<sgk::PassResult*>(rec);
+        a.vec4 = vec ? 1 : 0;
+        e = sgk::launch_stream(a, stream_grid(c, P), kStreamBlock, c->stream, &c->prof);
+        c->kernels++;
+        break;
+      }
+      case PK::FILTER: {
+        Node* n = P.main;
+        Value* x = n->in[0].get();
+        status = ensure_storage(c, n->out.get());
+        if (status) break;
+        sgk::Prog pr{};
+        std::vector<Op> ops;
+        for (int p = 0; p < n->expr.nops; ++p)
+          ops.push_back(Op{(uint8_t)n->expr.ops[p].op, 0, n->expr.ops[p].value});
+        // the predicate's value is read off the stack (no sink): depths are
+        // computed with a trailing pop that is not executed
+        ops.push_back(Op{sgk::K_POP, 0, 0.0f});
+        std::vector<uint8_t> before;
+        int md = 0;
+        program_depths(ops, &before, &md);
+        ops.pop_back();
+        pr.nops = (int)ops.size();
+        for (size_t p = 0; p < ops.size(); ++p) {
+          pr.op[p] = ops[p].op;
+          pr.arg[p] = ops[p].arg;
+          pr.cst[p] = ops[p].cst;
+          pr.depth[p] = before[p];
+        }
+        e = sgk::launch_filter(static_cast<const float*>(x->st->ptr),
+                               static_cast<float*>(n->out->st->ptr), P.n, pr, md, dwork,
+                               static_cast<sgk::FilterResult*>(rec), c->stream, c->num_sms,
+                               &c->kernels, &c->prof);
+        break;
+      }
+      case PK::SORT: {
+        Node* n = P.main;
+        status = ensure_storage(c, n->out.get());
+        if (status) break;
+        e = sgk::launch_sort(static_cast<const int32_t*>(n->in[0]->st->ptr),
+                             static_cast<int32_t*>(n->out->st->ptr), P.n,
+                             P.chk_sorted || P.chk_perm, dwork,
+                             static_cast<sgk::SortResult*>(rec), c->stream, c->num_sms,
+                             &c->kernels, &c->inject, &c->prof);
+        c->inject = sgk::SortInject{};
+        break;
+      }
+      case PK::CHECK_SORTED: {
+        Node* n = P.main;
+        e = sgk::launch_check_sorted(static_cast<const int32_t*>(n->in[0]->st->ptr), P.n,
+                                     static_cast<sgk::SortResult*>(rec), dwork, c->stream,
+                                     c->num_sms, &c->kernels, &c->prof);
+        break;
+      }
+      case PK::CHECK_PERM: {
+        Node* n = P.main;
+        e = sgk::launch_check_perm(static_cast<const int32_t*>(n->in[0]->st->ptr),
+                                   static_cast<const int32_t*>(n->in[1]->st->ptr), P.n,
+                                   static_cast<sgk::SortResult*>(rec), dwork, c->stream,
+                                   c->num_sms, &c->kernels, &c->prof);
+        break;
+      }
+      case PK::MATMUL:
+      case PK::FREIVALDS:
+        status = sg_exec_linalg(c, P.main, rec, dwork, &e);
+        break;
+    }
+  }
+  if (e == cudaSuccess && !status)
+    e = cudaMemcpyAsync(c->host_res, dres, passes.size() * sgk::kResultBytes,
+                        cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && !status) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess && !status) status = cuda_fail(c, e, "kernel execution");
+  if (e == cudaSuccess) c->prof.collect();
+
+  bool have = false;
+  sg_status cstatus = SG_OK;
+  if (!status) {
+    const char* hres = static_cast<const char*>(c->host_res);
+    for (size_t i = 0; i < passes.size(); ++i) {
+      Pass& P = passes[i];
+      const char* rec = hres + i * sgk::kResultBytes;
+      switch (P.kind) {
+        case PK::STREAM: {
+          if (P.prog.empty()) break;
+          sgk::PassResult r;
+          memcpy(&r, rec, sizeof r);
+          for (Node* n : P.reduces) {
+            const bool empty = r.count == 0;
+            double v = 0.0;
+            switch (n->rop) {
+              case SG_REDUCE_SUM: v = r.sum; break;
+              case SG_REDUCE_COUNT: v = (double)r.count; break;
+              case SG_REDUCE_MIN: v = (r.nan_seen || empty) ? NAN : (double)r.mn; break;
+              case SG_REDUCE_MAX: v = (r.nan_seen || empty) ? NAN : (double)r.mx; break;
+              case SG_REDUCE_AVG: v = empty ? NAN : r.sum / (double)r.count; break;
+            }
+            n->sout->value = v;
+            n->sout->index = -1;
+          }
+          for (size_t p = 0; p < P.preds.size(); ++p) {
+            Node* q = P.preds[p];
+            const long long f = r.first[p];
+            const bool hit = f != kNone;
+            if (q->kind == NK::QUANT) {
+              q->sout->value = q->exists ? (hit ? 1.0 : 0.0) : (hit ? 0.0 : 1.0);
+              q->sout->index = hit ? f : -1;
+            } else if (q->ckind == SG_C_FOR_ALL ? hit : !hit) {
+              record_violation(c, q, q->ckind == SG_C_FOR_ALL ? f : -1, 0.0, &have, &cstatus);
+            }
+          }
+          break;
+        }
+        case PK::FILTER: {
+          sgk::FilterResult r;
+          memcpy(&r, rec, sizeof r);
+          if (r.timeout) {
+            status = SG_ERR_TIMEOUT;
+            c->err = "filter look-back wait gave up";
+          }
+          P.main->out->n = r.count;
+          P.main->out->rows = r.count;
+          P.main->out->count_known = true;
+          break;
+        }
+        case PK::SORT:
+        case PK::CHECK_SORTED:
+        case PK::CHECK_PERM: {
+          sgk::SortResult r;
+          memcpy(&r, rec, sizeof r);
+          if (r.timeout) {
+            status = SG_ERR_TIMEOUT;
+            c->err = "sort look-back wait gave up";
+          }
+          Node* ks = P.kind == PK::SORT ? P.chk_sorted : P.kind == PK::CHECK_SORTED ? P.main : nullptr;
+          Node* kp = P.kind == PK::SORT ? P.chk_perm : P.kind == PK::CHECK_PERM ? P.main : nullptr;
+          if (ks && r.unsorted_enc != 0)
+            record_violation(c, ks, (int64_t)~r.unsorted_enc, 0.0, &have, &cstatus);
+          if (kp && (r.fp_in[0] != r.fp_out[0] || r.fp_in[1] != r.fp_out[1] ||
+                     r.cnt_in != r.cnt_out))
+            record_violation(c, kp, -1, 0.0, &have, &cstatus);
+          break;
+        }
+        case PK::MATMUL:
+        case PK::FREIVALDS: {
+          double observed = 0.0;
+          long long row = -1;
+          if (sg_linalg_result(c, P.main, rec, &row, &observed))
+            record_violation(c, P.main, row, observed, &have, &cstatus);
+          break;
+        }
+      }
+    }
+  }
+
+  // poison: a failed contract poisons its target and everything computed
+  // from it (queue order is a topological order)
+  for (Node* n : pl.nodes)
+    if (n->failed && n->in[0]) n->in[0]->poisoned = true;
+  for (Node* n : pl.nodes) {
+    bool p = false;
+    for (int k = 0; k < n->nin; ++k) p |= n->in[k] && n->in[k]->poisoned;
+    if (n->kind == NK::CHECK) continue;
+    if (p && n->out) n->out->poisoned = true;
+    if (p && n->sout) n->sout->poisoned = true;
+  }
+  for (Node* n : pl.nodes) {
+    if (n->out) {
+      n->out->producer = nullptr;
+      if (!n->out->count_known && status) n->out->count_known = true, n->out->n = 0;
+    }
+    if (n->sout) {
+      n->sout->producer = nullptr;
+      n->sout->done = true;
+      if (status) n->sout->poisoned = true;
+    }
+  }
+  c->pending.clear();
+  if (status) return status;
+  return cstatus;
+}
+
+sg_status sg_describe_pending(sg_ctx* c, std::string* out) {
+  Planner pl(c);
+  pl.plan();
+  std::string s;
+  char buf[256];
+  for (Pass& P : pl.passes) {
+    switch (P.kind) {
+      case PK::STREAM:
+        if (P.prog.empty()) continue;
+        snprintf(buf, sizeof buf, "stream n=%lld in=%zu store=%zu pred=%zu reduce=%d ops=%zu\n",
+                 (long long)P.n, P.inputs.size(), P.stores.size(), P.preds.size(),
+                 P.reduce_of ? 1 : 0, P.prog.size());
+        break;
+      case PK::FILTER: snprintf(buf, sizeof buf, "filter n=%lld\n", (long long)P.n); break;
+      case PK::SORT:
+        snprintf(buf, sizeof buf, "sort n=%lld sorted=%d perm=%d\n", (long long)P.n,
+                 P.chk_sorted ? 1 : 0, P.chk_perm ? 1 : 0);
+        break;
+      case PK::CHECK_SORTED: snprintf(buf, sizeof buf, "check_sorted n=%lld\n", (long long)P.n); break;
+      case PK::CHECK_PERM: snprintf(buf, sizeof buf, "check_perm n=%lld\n", (long long)P.n); break;
+      case PK::MATMUL:
+        snprintf(buf, sizeof buf, "matmul %lldx%lldx%lld prec=%d\n", (long long)P.main->in[0]->rows,
+                 (long long)P.main->in[0]->cols, (long long)P.main->in[1]->cols, P.main->prec);
+        break;
+      case PK::FREIVALDS:
+        snprintf(buf, sizeof buf, "freivalds n=%lld nvec=%d\n", (long long)P.main->in[0]->rows,
+                 P.main->nvec);
+        break;
+    }
+    s += buf;
+  }
+  *out = std::move(s);
+  return SG_OK;
+}

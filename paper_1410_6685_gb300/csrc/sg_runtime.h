@@ -1,0 +1,109 @@
+// sg_runtime.h -- host-side objects of the library: values, handles, the
+// deferred-execution graph (Sec. 5) and the context.  Internal.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "safegpu.h"
+#include "sg_internal.h"
+
+struct Node;
+
+// Device storage shared by the values that alias it (for_each writes in place).
+struct Storage {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  bool owned = false;
+  cudaStream_t stream = nullptr;
+  ~Storage();
+};
+
+// One value of a collection / vector / matrix (an SSA value of the graph).
+struct Value {
+  sg_dtype dt = SG_F32;
+  int64_t n = 0;          // element count (capacity for a pending filter)
+  int64_t rows = 0, cols = 1;
+  std::shared_ptr<Storage> st;   // null until materialised
+  Node* producer = nullptr;      // pending producer (valid until the flush)
+  bool poisoned = false;
+  bool count_known = true;       // false for a filter result before its flush
+  int handles = 0;               // user handles that point at this value
+  int pending_uses = 0;          // uses by queued nodes
+};
+using ValueP = std::shared_ptr<Value>;
+
+struct ScalarVal {
+  bool done = false;
+  bool poisoned = false;
+  double value = 0.0;
+  int64_t index = -1;
+  Node* producer = nullptr;
+};
+using ScalarP = std::shared_ptr<ScalarVal>;
+
+enum class NK { MAP, REDUCE, QUANT, CHECK, FILTER, SORT, MATMUL };
+
+struct Node {
+  int id = 0;
+  NK kind = NK::MAP;
+  sg_expr expr{};                // MAP / QUANT / CHECK(for_all, exists) / FILTER
+  int nin = 0;
+  ValueP in[4];
+  ValueP out;
+  bool inplace = false;          // MAP as for_each
+  ScalarP sout;                  // REDUCE / QUANT
+  int rop = 0;                   // sg_reduce_op
+  bool exists = false;           // QUANT: exists (else for_all)
+  // CHECK
+  int ckind = 0, role = 0, cid = -1;
+  bool builtin = false;
+  uint64_t seed = 0;
+  int nvec = 4;
+  double tol = 0.0;
+  int prec = 0;                  // MATMUL precision
+  // results filled at execution
+  int64_t first = -1;
+  double observed = 0.0;
+  bool failed = false;
+};
+using NodeP = std::shared_ptr<Node>;
+
+struct sg_ctx {
+  int device = -1;
+  bool planning_only = true;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int mode = SG_CONTRACTS_PRE_POST;
+  int fusion = SG_FUSE_ON;
+  int sched = SG_SCHED_AUTOTUNE;
+  std::vector<NodeP> pending;
+  int next_node = 0;
+  int next_contract = 0;
+  std::string err;
+  bool has_violation = false;
+  sg_violation last_violation{};
+  int64_t kernels = 0;
+  // device resources
+  unsigned int* counter = nullptr;     // last-block-done counter (stays zero)
+  void* scratch = nullptr;             // per-flush scratch arena
+  size_t scratch_bytes = 0;
+  void* host_res = nullptr;            // pinned host copy of pass results
+  size_t host_res_bytes = 0;
+  sgk::SortInject inject{};            // contract-test fault for the next sort
+  sgk::Prof prof;                      // per-kernel event tracing
+};
+
+struct sg_vector {
+  sg_ctx* ctx = nullptr;
+  ValueP v;
+  bool matrix = false;
+};
+
+struct sg_scalar {
+  sg_ctx* ctx = nullptr;
+  ScalarP s;
+};

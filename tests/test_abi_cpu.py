@@ -1,0 +1,181 @@
+"""CPU checks of the boundary: the library loads without a GPU, exports every
+function include/safegpu.h declares, and the host planner (Sec. 5 optimizer)
+makes the plans the paper describes, on a planning-only context (device -1).
+No compute call is made."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "safegpu.h")
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1410_6685_gb300 import safegpu
+    return safegpu
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:sg_status|const char\*)\s+(sg_\w+)\s*\(", text, re.M)))
+
+
+def test_every_declared_symbol_is_exported(sg):
+    names = declared_functions()
+    assert len(names) >= 40
+    out = subprocess.run(["nm", "-D", "--defined-only", sg.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (sg_\w+)$", out, re.M))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert getattr(sg.lib, n) is not None
+
+
+def test_no_cpu_fallback_symbols(sg):
+    # the library links no oracle code
+    out = subprocess.run(["nm", "-D", sg.LIB_PATH], capture_output=True, text=True).stdout
+    assert "or_" + "map" not in out and "or_sort" not in out
+
+
+def test_status_names(sg):
+    for i, name in enumerate(sg.STATUS):
+        assert sg.lib.sg_status_name(i).decode() == name
+
+
+@pytest.fixture
+def pctx(sg):
+    ctx = sg.sg_init(-1)
+    yield ctx
+    sg.sg_destroy(ctx)
+
+
+ADD = [("x", 0), ("x", 1), ("add",)]
+MUL = [("x", 0), ("x", 1), ("mul",)]
+
+
+def vec(sg, ctx, n, dt=None):
+    return sg.sg_vector_create(ctx, sg.SG_F32 if dt is None else dt, n)
+
+
+def lines(sg, ctx):
+    return [l for l in sg.sg_plan_describe(ctx).splitlines() if l]
+
+
+def test_dot_product_plans_to_one_kernel(sg, pctx):
+    # Listing 5 / Fig. 2: compwise_multiply then sum -> one kernel, the
+    # product is never stored
+    a, b = vec(sg, pctx, 1000), vec(sg, pctx, 1000)
+    t = sg.sg_zip(pctx, MUL, a, b)
+    s = sg.sg_reduce(pctx, sg.SG_REDUCE_SUM, t)
+    sg.sg_vector_release(t)
+    L = lines(sg, pctx)
+    assert len(L) == 1 and "store=0" in L[0] and "reduce=1" in L[0] and "in=2" in L[0], L
+    sg.sg_scalar_release(s)
+
+
+def test_axpy_rewrite_is_one_kernel(sg, pctx):
+    # Fig. 3: smult then plus -> one kernel computing a*X[i] + Y[i]
+    x, y = vec(sg, pctx, 4096), vec(sg, pctx, 4096)
+    ax = sg.sg_map(pctx, [("c", 2.5), ("x", 0), ("mul",)], x)
+    r = sg.sg_zip(pctx, ADD, ax, y)
+    sg.sg_vector_release(ax)
+    L = lines(sg, pctx)
+    assert len(L) == 1 and "store=1" in L[0] and "in=2" in L[0], L
+    sg.sg_set_fusion(pctx, sg.SG_FUSE_OFF)
+    assert len(lines(sg, pctx)) == 2
+    sg.sg_vector_release(r)
+
+
+def test_vadd_sum_post_fused_and_unfused(sg, pctx):
+    a, b = vec(sg, pctx, 1 << 20), vec(sg, pctx, 1 << 20)
+    z = sg.sg_zip(pctx, ADD, a, b)
+    sg.sg_ensure(pctx, z, sg.contract(sg.SG_C_FOR_ALL,
+                                      [("x", 0), ("x", 1), ("x", 2), ("add",), ("eq",)],
+                                      other=[a, b]))
+    s = sg.sg_reduce(pctx, sg.SG_REDUCE_SUM, z)
+    L = lines(sg, pctx)
+    assert L == ["stream n=1048576 in=2 store=1 pred=1 reduce=1 ops=17"], L
+    sg.sg_set_fusion(pctx, sg.SG_FUSE_OFF)
+    L = lines(sg, pctx)
+    assert len(L) == 3 and all(l.startswith("stream") for l in L), L
+    sg.sg_scalar_release(s)
+
+
+def test_filter_then_sum_becomes_masked_reduce(sg, pctx):
+    x = vec(sg, pctx, 10000)
+    y = sg.sg_map(pctx, [("x", 0), ("x", 0), ("c", 1.0), ("fma",)], x)
+    k = sg.sg_filter(pctx, [("x", 0), ("c", 1.5), ("gt",)], y)
+    sg.sg_vector_release(y)
+    s = sg.sg_reduce(pctx, sg.SG_REDUCE_SUM, k)
+    sg.sg_vector_release(k)
+    L = lines(sg, pctx)
+    assert len(L) == 1 and "reduce=1" in L[0] and "store=0" in L[0], L
+    sg.sg_scalar_release(s)
+
+
+def test_filter_kept_by_handle_is_compacted(sg, pctx):
+    x = vec(sg, pctx, 10000)
+    k = sg.sg_filter(pctx, [("x", 0), ("c", 0.0), ("gt",)], x)
+    s = sg.sg_reduce(pctx, sg.SG_REDUCE_SUM, k)
+    L = lines(sg, pctx)
+    assert L[0].startswith("filter n=10000") and L[1].startswith("stream"), L
+    sg.sg_scalar_release(s)
+
+
+def test_contract_mode_off_plans_no_check(sg, pctx):
+    a = vec(sg, pctx, 100)
+    sg.sg_set_contract_mode(pctx, sg.SG_CONTRACTS_OFF)
+    sg.sg_require(pctx, a, sg.contract(sg.SG_C_FOR_ALL, [("x", 0), ("c", 0.0), ("ne",)]))
+    assert lines(sg, pctx) == []
+    sg.sg_set_contract_mode(pctx, sg.SG_CONTRACTS_PRE)
+    sg.sg_ensure(pctx, a, sg.contract(sg.SG_C_FOR_ALL, [("x", 0), ("c", 0.0), ("ne",)]))
+    assert lines(sg, pctx) == []
+    sg.sg_require(pctx, a, sg.contract(sg.SG_C_FOR_ALL, [("x", 0), ("c", 0.0), ("ne",)]))
+    assert len(lines(sg, pctx)) == 1
+
+
+def test_sort_plans_fused_postconditions(sg, pctx):
+    k = vec(sg, pctx, 1 << 20, sg.SG_I32)
+    out = sg.sg_sort(pctx, k)
+    assert lines(sg, pctx) == ["sort n=1048576 sorted=1 perm=1"]
+    sg.sg_set_fusion(pctx, sg.SG_FUSE_OFF)
+    assert lines(sg, pctx) == ["sort n=1048576 sorted=0 perm=0", "check_sorted n=1048576",
+                               "check_perm n=1048576"]
+    sg.sg_vector_release(out)
+
+
+def test_scalar_contracts_on_host(sg, pctx):
+    a, b = vec(sg, pctx, 10), vec(sg, pctx, 11)
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_zip(pctx, ADD, a, b)
+    assert e.value.status == sg.SG_ERR_SHAPE
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_map(pctx, [("x", 0), ("add",)], a)
+    assert e.value.status == sg.SG_ERR_INVALID_ARG
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_map(pctx, [("x", 1)], a)
+    assert e.value.status == sg.SG_ERR_INVALID_ARG
+    i = vec(sg, pctx, 10, sg.SG_I32)
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_map(pctx, [("x", 0)], i)
+    assert e.value.status == sg.SG_ERR_DTYPE
+    m1 = sg.sg_matrix_create(pctx, sg.SG_F32, 3, 4)
+    m2 = sg.sg_matrix_create(pctx, sg.SG_F32, 5, 3)
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_matmul(pctx, m1, m2)
+    assert e.value.status == sg.SG_ERR_SHAPE
+
+
+def test_planning_only_context_cannot_execute(sg, pctx):
+    a = vec(sg, pctx, 10)
+    s = sg.sg_reduce(pctx, sg.SG_REDUCE_SUM, a)
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_flush(pctx)
+    assert e.value.status == sg.SG_ERR_UNSUPPORTED

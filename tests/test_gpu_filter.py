@@ -1,0 +1,93 @@
+"""GPU parity of `filter` (Table 2; Sec. 3.2 example `a < 5`): the kept items
+in index order, bit-identical to the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_6685_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+f32 = np.float32
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1410_6685_gb300 import safegpu as sg
+    ctx = sg.sg_init(0, torch.cuda.current_stream().cuda_stream)
+    yield sg, ctx, torch
+    sg.sg_destroy(ctx)
+
+
+def run_filter(env, x, pred):
+    sg, ctx, torch = env
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=f32)).cuda()
+    v = sg.sg_vector_wrap(ctx, sg.SG_F32, len(x), t.data_ptr())
+    k = sg.sg_filter(ctx, pred, v)
+    m = sg.sg_vector_count(ctx, k)
+    out = sg.sg_vector_read(ctx, k, np.empty(m, f32))
+    return out, t
+
+
+PREDS = [
+    [("x", 0), ("c", 0.25), ("gt",)],
+    [("x", 0), ("c", 5.0), ("lt",)],
+    [("x", 0), ("abs",), ("c", 0.5), ("lt",), ("x", 0), ("c", -0.9), ("lt",), ("or",)],
+    [("index",), ("c", 3.0), ("div",), ("dup",), ("c", 0.5), ("add",), ("c", 0.0), ("add",),
+     ("swap",), ("sub",), ("c", 0.4), ("gt",)],
+]
+
+
+@pytest.mark.parametrize("n", [1, 2, 4095, 4096, 4097, 3 * 4096 + 5, 1_000_003])
+@pytest.mark.parametrize("k", range(len(PREDS)))
+def test_filter_bit_exact(env, n, k):
+    x = inputs.uniform_pm1(inputs.rng(n + k), n)
+    got, _ = run_filter(env, x, PREDS[k])
+    ref = oracle.filter(PREDS[k], x)
+    assert len(got) == len(ref)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_filter_none_and_all(env):
+    x = inputs.uniform_pm1(inputs.rng(5), 100_000)
+    none, _ = run_filter(env, x, [("x", 0), ("c", 2.0), ("gt",)])
+    every, _ = run_filter(env, x, [("x", 0), ("c", 2.0), ("lt",)])
+    assert len(none) == 0
+    assert np.array_equal(every, x)
+
+
+def test_filter_paper_example(env):
+    c = np.array([7, 1, 9, 4, 5, 3, 0], f32)
+    got, _ = run_filter(env, c, [("x", 0), ("c", 5.0), ("lt",)])
+    assert got.tolist() == [1, 4, 3, 0]
+
+
+def test_filter_large_full_size(env):
+    n = 1 << 26
+    x = inputs.batch_data(n, seed=21)
+    pred = [("x", 0), ("x", 0), ("mul",), ("c", 0.5), ("gt",)]
+    got, _ = run_filter(env, x, pred)
+    ref = oracle.filter(pred, x)
+    assert np.array_equal(got, ref)
+
+
+def test_filter_then_chain(env):
+    """A filtered collection feeds further deferred operations."""
+    sg, ctx, torch = env
+    n = 300_007
+    x = inputs.uniform_pm1(inputs.rng(9), n)
+    t = torch.from_numpy(x).cuda()
+    v = sg.sg_vector_wrap(ctx, sg.SG_F32, n, t.data_ptr())
+    y = sg.sg_map(ctx, [("x", 0), ("c", 3.0), ("mul",)], v)
+    k = sg.sg_filter(ctx, [("x", 0), ("c", 1.0), ("gt",)], y)
+    s = sg.sg_reduce(ctx, sg.SG_REDUCE_MAX, k)
+    m = sg.sg_vector_count(ctx, k)
+    kept = oracle.filter([("x", 0), ("c", 1.0), ("gt",)],
+                         oracle.map([("x", 0), ("c", 3.0), ("mul",)], x))
+    assert m == len(kept)
+    assert sg.sg_scalar_get(ctx, s) == oracle.max(kept)
+    z = sg.sg_map(ctx, [("x", 0), ("neg",)], k)
+    out = sg.sg_vector_read(ctx, z, np.empty(m, f32))
+    assert np.array_equal(out, -kept)
