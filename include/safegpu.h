@@ -333,6 +333,18 @@ sg_status sg_set_fusion(sg_ctx* ctx, sg_fusion f);
 typedef enum { SG_SCHED_AUTOTUNE = 0, SG_SCHED_LEARNED = 1 } sg_sched;
 sg_status sg_set_scheduler(sg_ctx* ctx, sg_sched s);
 
+/* Code generation for fused element-wise passes (Sec. 5 generates a kernel
+ * per plan).  SG_CODEGEN_SPECIALIZE (default): the fused program is compiled
+ * once per program structure into straight-line code inside the streaming
+ * kernel template (NVRTC, sm_103a) and cached for the process;
+ * SG_CODEGEN_INTERPRET: the precompiled streaming kernel evaluates the
+ * program.  Both give identical results.  SG_ERR_UNSUPPORTED if
+ * specialisation was requested but NVRTC cannot be loaded (the context keeps
+ * interpreting).  The environment variable SG_CODEGEN=interpret sets the
+ * default of new contexts. */
+typedef enum { SG_CODEGEN_INTERPRET = 0, SG_CODEGEN_SPECIALIZE = 1 } sg_codegen;
+sg_status sg_set_codegen(sg_ctx* ctx, sg_codegen g);
+
 /* Writes a one-line-per-kernel description of what sg_flush would launch
  * for the currently queued work (no execution; works on a planning-only
  * context).  *len receives the length needed, including the terminator. */

@@ -434,19 +434,24 @@ int or_batch_chain(int nm, const int* mop, const int* marg, const float* mcst,
                    const float* x, const int64_t* off, int64_t nseg,
                    double* sums, int64_t* first_viol, int64_t* kept) {
   for (int64_t s = 0; s < nseg; ++s) {
-    int64_t b = off[s], e = off[s + 1];
+    const int64_t b = off[s], L = off[s + 1] - off[s];
     double acc = 0.0;
     int64_t cnt = 0, fv = -1;
-    for (int64_t i = b; i < e; ++i) {
-      const float* xin[1] = {x + i};
-      float y, pr, fr;
-      if (eval_at(nm, mop, marg, mcst, 1, xin, 0, &y)) return OR_ERR_EXPR;
-      const float* yin[1] = {&y};
-      if (eval_at(np, pop, parg, pcst, 1, yin, 0, &pr)) return OR_ERR_EXPR;
-      if (eval_at(nf, fop, farg, fcst, 1, yin, 0, &fr)) return OR_ERR_EXPR;
-      if (!is_true(pr) && fv < 0) fv = i - b;
-      if (is_true(fr)) { acc += (double)y; ++cnt; }
+    float* y = (float*)malloc((size_t)(L > 0 ? L : 1) * sizeof(float));
+    if (!y) return OR_ERR_ARG;
+    /* each agent sees the collection's own elements and index k = 0..L-1 */
+    const float* xin[1] = {x + b};
+    const float* yin[1] = {y};
+    for (int64_t k = 0; k < L; ++k)
+      if (eval_at(nm, mop, marg, mcst, 1, xin, k, &y[k])) { free(y); return OR_ERR_EXPR; }
+    for (int64_t k = 0; k < L; ++k) {
+      float pr, fr;
+      if (eval_at(np, pop, parg, pcst, 1, yin, k, &pr) ||
+          eval_at(nf, fop, farg, fcst, 1, yin, k, &fr)) { free(y); return OR_ERR_EXPR; }
+      if (!is_true(pr) && fv < 0) fv = k;
+      if (is_true(fr)) { acc += (double)y[k]; ++cnt; }
     }
+    free(y);
     sums[s] = acc;
     first_viol[s] = fv;
     kept[s] = cnt;

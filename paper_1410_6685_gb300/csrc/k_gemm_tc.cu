@@ -1,0 +1,376 @@
+// k_gemm_tc.cu -- matrix `multiply` of Sec. 3.4 on the 5th-generation tensor
+// cores (sm_103a): C = A B (or C = C - A B for the elimination update) with
+// bf16 or fp16 operands, rounded to nearest even from binary32, and binary32
+// accumulation in tensor memory.
+//
+// Operands are first cast (and B transposed) into K-major 16-bit copies whose
+// K extent is padded to a multiple of 64.  Each CTA computes a 128 x 256 tile
+// of C with 128 threads:
+//   warp 0, one lane : TMA producer -- 2-D tiled bulk-tensor loads of a 128x64
+//                      A slice and a 256x64 B slice per stage (128-byte
+//                      swizzle, no multicast), completion on a "full" mbarrier;
+//   warp 1, one lane : MMA issuer -- four tcgen05.mma (M=128, N=256, K=16) per
+//                      stage, accumulator in 256 TMEM columns, tcgen05.commit
+//                      to the stage's "empty" mbarrier, and to "done" at the end;
+//   warp 2           : allocates / frees the tensor memory;
+//   all four warps   : epilogue -- tcgen05.ld of their 32 TMEM lanes (rows),
+//                      binary32 stores (or read-modify-write for C - A B).
+// Four pipeline stages of 48 KB.  Every mbarrier wait is bounded: on a
+// timeout the kernel raises an error flag and finishes without hanging.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "sg_linalg_kernels.h"
+
+namespace sgk {
+namespace {
+
+constexpr int TM = 128, TN = 256, TK = 64, STAGES = 4;
+constexpr int A_BYTES = TM * TK * 2;            // 16 KB
+constexpr int B_BYTES = TN * TK * 2;            // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr unsigned kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  for (unsigned i = 0; i < kWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major tile in the 128-byte swizzle
+// layout (rows of 128 B, 8-row groups 1024 B apart).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address >> 4
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor, kind::f16: D f32, A/B bf16 or f16, both K-major
+__host__ __device__ constexpr uint32_t idesc(bool fp16) {
+  return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) |
+         ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id,
+                                     uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(id), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ma,
+                                                    const __grid_constant__ CUtensorMap mb,
+                                                    float* __restrict__ C, int ldc, int M,
+                                                    int N, int KB, uint32_t id, int subtract,
+                                                    int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars[0..S): full, bars[S..2S): empty, bars[2S]: done; then the TMEM slot
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t done_bar = smem_u32(&bars[2 * STAGES]);
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (kb >= STAGES && !mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1u, err)) break;
+      const uint32_t full = smem_u32(&bars[s]);
+      mbar_expect_tx(full, STAGE_BYTES);
+      const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
+      tma_load_2d(a_dst, &ma, kb * TK, m0, full);
+      tma_load_2d(a_dst + A_BYTES, &mb, kb * TK, n0, full);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    bool ok = true;
+    for (int kb = 0; kb < KB && ok; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      ok = mbar_wait(smem_u32(&bars[s]), ph, err);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_base = smem_u32(smem + s * STAGE_BYTES);
+      const uint64_t da = sdesc(a_base), db = sdesc(a_base + A_BYTES);
+#pragma unroll
+      for (int k = 0; k < TK / 16; ++k) {
+        // advance 16 elements (32 bytes) along K inside the swizzled rows
+        umma(tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), id, (kb | k) != 0);
+      }
+      umma_commit(smem_u32(&bars[STAGES + s]));
+    }
+    umma_commit(done_bar);
+  }
+  __syncwarp();
+
+  // epilogue: wait for the accumulator, then rows 32*warp + lane
+  const bool ready = mbar_wait(done_bar, 0, err);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0 + warp * 32 + lane;
+  if (ready) {
+#pragma unroll 1
+    for (int c = 0; c < TN / 32; ++c) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+      const int col0 = n0 + c * 32;
+      if (row < M) {
+        float* cp = C + (size_t)row * ldc + col0;
+        if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+            if (subtract) {
+              const float4 o = *reinterpret_cast<const float4*>(cp + j);
+              v = make_float4(o.x - v.x, o.y - v.y, o.z - v.z, o.w - v.w);
+            }
+            *reinterpret_cast<float4*>(cp + j) = v;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (col0 + j < N) {
+              const float v = __uint_as_float(r[j]);
+              cp[j] = subtract ? cp[j] - v : v;
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN)
+                 : "memory");
+  }
+}
+
+// binary32 (rows x cols, leading dim ld) -> 16-bit rows x Kp, zero padded
+template <bool FP16>
+__global__ void k_cast_rows(const float* __restrict__ A, int lda, int rows, int cols, int Kp,
+                            void* out) {
+  const long long total = (long long)rows * (Kp / 8);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / (Kp / 8));
+    const int c0 = (int)(t % (Kp / 8)) * 8;
+    const float* src = A + (size_t)r * lda + c0;
+    uint16_t h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float v = (c0 + j < cols) ? src[j] : 0.0f;
+      if (FP16) {
+        const __half x = __float2half_rn(v);
+        h[j] = *reinterpret_cast<const uint16_t*>(&x);
+      } else {
+        const __nv_bfloat16 x = __float2bfloat16_rn(v);
+        h[j] = *reinterpret_cast<const uint16_t*>(&x);
+      }
+    }
+    uint4 pk;
+    pk.x = h[0] | ((uint32_t)h[1] << 16);
+    pk.y = h[2] | ((uint32_t)h[3] << 16);
+    pk.z = h[4] | ((uint32_t)h[5] << 16);
+    pk.w = h[6] | ((uint32_t)h[7] << 16);
+    reinterpret_cast<uint4*>(out)[t] = pk;
+  }
+}
+
+// B (K x N, leading dim ldb) -> Bt (N x Kp) 16-bit, transposed via 32x32 tiles
+template <bool FP16>
+__global__ void k_cast_transpose(const float* __restrict__ B, int ldb, int K, int N, int Kp,
+                                 uint16_t* out) {
+  __shared__ float t[32][33];
+  const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int k = k0 + i, n = n0 + threadIdx.x;
+    t[i][threadIdx.x] = (k < K && n < N) ? B[(size_t)k * ldb + n] : 0.0f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int n = n0 + i, k = k0 + threadIdx.x;
+    if (n < N && k < Kp) {
+      const float v = t[threadIdx.x][i];
+      uint16_t h;
+      if (FP16) {
+        const __half x = __float2half_rn(v);
+        h = *reinterpret_cast<const uint16_t*>(&x);
+      } else {
+        const __nv_bfloat16 x = __float2bfloat16_rn(v);
+        h = *reinterpret_cast<const uint16_t*>(&x);
+      }
+      out[(size_t)n * Kp + k] = h;
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int rows, int Kp, int box_rows, bool fp16) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t gemm_tc_scratch_bytes(int M, int N, int K) {
+  const size_t Kp = (size_t)((K + TK - 1) / TK) * TK;
+  return 256 + align256((size_t)M * Kp * 2) + align256((size_t)N * Kp * 2);
+}
+
+cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                           int M, int N, int K, bool fp16, bool subtract, void* scratch,
+                           cudaStream_t s, Prof* prof, int64_t* kernels) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K <= 0) {   // empty inner dimension: C = 0 (or C unchanged for C - A B)
+    if (subtract) return cudaSuccess;
+    return cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)N * 4, M, s);
+  }
+  const int Kp = ((K + TK - 1) / TK) * TK;
+  char* p = static_cast<char*>(scratch);
+  int* err = reinterpret_cast<int*>(p);
+  uint16_t* a16 = reinterpret_cast<uint16_t*>(p + 256);
+  uint16_t* bt16 = reinterpret_cast<uint16_t*>(p + 256 + align256((size_t)M * Kp * 2));
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  prof_begin(prof, "cast_operands", s);
+  const long long ca = (long long)M * (Kp / 8);
+  const int ga = (int)std::min<long long>((ca + 255) / 256, 65535LL * 8);
+  dim3 gt((N + 31) / 32, (Kp + 31) / 32), bt(32, 8);
+  if (fp16) {
+    k_cast_rows<true><<<ga, 256, 0, s>>>(A, lda, M, K, Kp, a16);
+    k_cast_transpose<true><<<gt, bt, 0, s>>>(B, ldb, K, N, Kp, bt16);
+  } else {
+    k_cast_rows<false><<<ga, 256, 0, s>>>(A, lda, M, K, Kp, a16);
+    k_cast_transpose<false><<<gt, bt, 0, s>>>(B, ldb, K, N, Kp, bt16);
+  }
+  prof_end(prof, s);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a16, M, Kp, TM, fp16) || !make_map(&mb, bt16, N, Kp, TN, fp16))
+    return cudaErrorInvalidValue;
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+  prof_begin(prof, fp16 ? "gemm_tc_f16" : "gemm_tc_bf16", s);
+  k_gemm_tc<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, Kp / TK, idesc(fp16),
+                                          subtract ? 1 : 0, err);
+  prof_end(prof, s);
+  *kernels += 3;
+  return cudaGetLastError();
+}
+
+}  // namespace sgk

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
 
 // ---------------------------------------------------------------------------
 template <bool LAST, bool CHECK>
-__global__ void __launch_bounds__(kSortBlock) k_onesweep(
+__global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
     const int* __restrict__ in, int* __restrict__ out, long long n, int pass, SortHdr* h,
     unsigned* st32, unsigned long long* st64, SortResult* res) {
   __shared__ int s_keys[kTile];
@@ -205,29 +205,40 @@ __global__ void __launch_bounds__(kSortBlock) k_onesweep(
 
   // load: warp w owns keys [w*512, (w+1)*512) of the tile, 32 consecutive per round
   int key[kKpt];
-  unsigned dig[kKpt];
   const long long wbase = base + (long long)w * kWarpKeys + lane;
+  const bool full = valid_cnt == kTile;
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
     const long long idx = wbase + r * 32;
-    const bool ok = idx < n;
-    key[r] = ok ? __ldcs(in + idx) : 0;
-    dig[r] = ok ? digit_of<LAST>(key[r], shift) : (unsigned)kRadix;
+    key[r] = (full || idx < n) ? __ldcs(in + idx) : 0;
   }
 
-  // stable rank of each key among the warp's keys of the same digit
-  unsigned rank[kKpt];
+  // stable rank of each key among the warp's keys of the same digit; the
+  // lanes holding the same digit are found with eight ballots (one per digit
+  // bit), a ninth separates the padding lanes of a partial tile
+  unsigned short rank[kKpt];
   const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
-    const unsigned d = dig[r];
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const bool ok = full || (wbase + r * 32) < n;
+    const unsigned d = digit_of<LAST>(key[r], shift);
+    unsigned peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const unsigned bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
+    if (!full) {
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      peers &= ok ? bal : ~bal;
+    }
     const unsigned before = __popc(peers & lt);
-    const unsigned prev = d < kRadix ? s_whist[w][d] : 0u;
+    const unsigned prev = ok ? s_whist[w][d] : 0u;
     __syncwarp();
-    if (d < kRadix && before == 0) s_whist[w][d] = prev + __popc(peers);
+    if (ok && before == 0) s_whist[w][d] = prev + __popc(peers);
     __syncwarp();
-    rank[r] = prev + before;
+    rank[r] = (unsigned short)(prev + before);
   }
   __syncthreads();
 
@@ -251,8 +262,10 @@ __global__ void __launch_bounds__(kSortBlock) k_onesweep(
   // sort the tile in shared memory by digit (stable)
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
-    const unsigned d = dig[r];
-    if (d < kRadix) s_keys[s_start[d] + s_whist[w][d] + rank[r]] = key[r];
+    if (full || (wbase + r * 32) < n) {
+      const unsigned d = digit_of<LAST>(key[r], shift);
+      s_keys[s_start[d] + s_whist[w][d] + rank[r]] = key[r];
+    }
   }
   __syncthreads();
 

@@ -42,14 +42,16 @@ __global__ void __launch_bounds__(256) k_stream(const StreamArgs a) {
           x[k][0] = x[k][1] = x[k][2] = x[k][3] = 0.0f;
         }
       }
-      run_prog<4, NX, DEPTH>(a, x, v << 2, acc);
+      const bool vm[4] = {true, true, true, true};
+      run_prog<4, NX, DEPTH>(a, x, v << 2, vm, acc);
     }
   }
   for (long long i = tail_start + tid; i < n; i += stride) {
     float x[NX][1];
 #pragma unroll
     for (int k = 0; k < NX; ++k) x[k][0] = (k < NIN) ? a.in[k][i] : 0.0f;
-    run_prog<1, NX, DEPTH>(a, x, i, acc);
+    const bool vm[1] = {true};
+    run_prog<1, NX, DEPTH>(a, x, i, vm, acc);
   }
 
   if (!a.has_reduce && a.npred == 0) return;

@@ -10,9 +10,11 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
+#include "sg_jit.h"
 #include "sg_plan.h"
 #include "sg_runtime.h"
 
@@ -195,6 +197,8 @@ sg_status sg_init(int device, void* stream, sg_ctx** out) {
   if (!out) return SG_ERR_INVALID_ARG;
   auto* c = new sg_ctx;
   c->device = device;
+  if (const char* g = getenv("SG_CODEGEN"))
+    if (strcmp(g, "interpret") == 0) c->codegen = SG_CODEGEN_INTERPRET;
   c->stream = static_cast<cudaStream_t>(stream);
   if (device >= 0) {
     c->planning_only = false;
@@ -717,6 +721,16 @@ sg_status sg_set_contract_mode(sg_ctx* c, sg_contract_mode m) {
 sg_status sg_set_fusion(sg_ctx* c, sg_fusion f) {
   if (!c || (f != SG_FUSE_OFF && f != SG_FUSE_ON)) return SG_ERR_INVALID_ARG;
   c->fusion = f;
+  return SG_OK;
+}
+
+sg_status sg_set_codegen(sg_ctx* c, sg_codegen g) {
+  if (!c || (g != SG_CODEGEN_INTERPRET && g != SG_CODEGEN_SPECIALIZE)) return SG_ERR_INVALID_ARG;
+  if (g == SG_CODEGEN_SPECIALIZE && !sgk::jit_available()) {
+    c->codegen = SG_CODEGEN_INTERPRET;
+    return fail(c, SG_ERR_UNSUPPORTED, "NVRTC is not available; fused passes are interpreted");
+  }
+  c->codegen = g;
   return SG_OK;
 }
 

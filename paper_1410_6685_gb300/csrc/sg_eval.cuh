@@ -75,8 +75,8 @@ __device__ __forceinline__ void exec_at(int op, int arg, float cst,
                                         const StreamArgs& a,
                                         float (&s)[DEPTH][L],
                                         const float (&x)[NX][L],
-                                        float (&mask)[L], long long i0,
-                                        Acc& acc) {
+                                        float (&mask)[L], const bool (&vm)[L],
+                                        long long i0, Acc& acc) {
   if constexpr (D > DEPTH) {
     return;
   } else {
@@ -196,7 +196,7 @@ __device__ __forceinline__ void exec_at(int op, int arg, float cst,
 #pragma unroll
         for (int l = L - 1; l >= 0; --l) {
           const bool t = truthy(s[D - 1][l]);
-          if (ex ? t : !t) hit = i0 + l;
+          if (vm[l] && (ex ? t : !t)) hit = i0 + l;
         }
 #pragma unroll
         for (int p = 0; p < kMaxPred; ++p)
@@ -206,7 +206,7 @@ __device__ __forceinline__ void exec_at(int op, int arg, float cst,
     case K_MASK:
       if constexpr (D >= 1) {
 #pragma unroll
-        for (int l = 0; l < L; ++l) mask[l] = b2f(truthy(s[D - 1][l]));
+        for (int l = 0; l < L; ++l) mask[l] = b2f(vm[l] && truthy(s[D - 1][l]));
       }
       break;
     case K_REDUCE:
@@ -216,7 +216,7 @@ __device__ __forceinline__ void exec_at(int op, int arg, float cst,
         for (int l = 0; l < L; ++l) v[l] = s[D - 1][l];
         acc_reduce<L>(acc, v, mask);
 #pragma unroll
-        for (int l = 0; l < L; ++l) mask[l] = 1.0f;
+        for (int l = 0; l < L; ++l) mask[l] = b2f(vm[l]);
       }
       break;
     default:  // K_POP: the host's depth bookkeeping already dropped the value
@@ -225,29 +225,30 @@ __device__ __forceinline__ void exec_at(int op, int arg, float cst,
   }
 }
 
+// vm: lanes that hold a real element (sinks ignore the others)
 template <int L, int NX, int DEPTH>
 __device__ __forceinline__ void run_prog(const StreamArgs& a,
                                          const float (&x)[NX][L], long long i0,
-                                         Acc& acc) {
+                                         const bool (&vm)[L], Acc& acc) {
   float s[DEPTH][L];
   float mask[L];
 #pragma unroll
-  for (int l = 0; l < L; ++l) mask[l] = 1.0f;
+  for (int l = 0; l < L; ++l) mask[l] = b2f(vm[l]);
   const int nops = a.prog.nops;
   for (int pc = 0; pc < nops; ++pc) {
     const int op = a.prog.op[pc];
     const int arg = a.prog.arg[pc];
     const float c = a.prog.cst[pc];
     switch (a.prog.depth[pc]) {
-      case 0: exec_at<0, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 1: exec_at<1, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 2: exec_at<2, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 3: exec_at<3, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 4: exec_at<4, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 5: exec_at<5, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 6: exec_at<6, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 7: exec_at<7, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      default: exec_at<8, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
+      case 0: exec_at<0, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 1: exec_at<1, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 2: exec_at<2, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 3: exec_at<3, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 4: exec_at<4, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 5: exec_at<5, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 6: exec_at<6, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 7: exec_at<7, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      default: exec_at<8, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
     }
   }
 }
@@ -333,24 +334,28 @@ __device__ __forceinline__ void eval_value(const StreamArgs& a, const float (&x)
                                            long long i0, float (&v)[L]) {
   float s[DEPTH][L];
   float mask[L];
+  bool vm[L];
   Acc acc;
 #pragma unroll
-  for (int l = 0; l < L; ++l) mask[l] = 1.0f;
+  for (int l = 0; l < L; ++l) {
+    mask[l] = 1.0f;
+    vm[l] = true;
+  }
   const int nops = a.prog.nops;
   for (int pc = 0; pc < nops; ++pc) {
     const int op = a.prog.op[pc];
     const int arg = a.prog.arg[pc];
     const float c = a.prog.cst[pc];
     switch (a.prog.depth[pc]) {
-      case 0: exec_at<0, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 1: exec_at<1, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 2: exec_at<2, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 3: exec_at<3, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 4: exec_at<4, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 5: exec_at<5, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 6: exec_at<6, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      case 7: exec_at<7, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
-      default: exec_at<8, L, NX, DEPTH>(op, arg, c, a, s, x, mask, i0, acc); break;
+      case 0: exec_at<0, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 1: exec_at<1, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 2: exec_at<2, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 3: exec_at<3, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 4: exec_at<4, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 5: exec_at<5, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 6: exec_at<6, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      case 7: exec_at<7, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
+      default: exec_at<8, L, NX, DEPTH>(op, arg, c, a, s, x, mask, vm, i0, acc); break;
     }
   }
 #pragma unroll

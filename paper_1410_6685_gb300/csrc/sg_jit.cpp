@@ -1,0 +1,455 @@
+// sg_jit.cpp -- run-time specialisation of fused element-wise passes.
+//
+// Sec. 5 of the paper instantiates a kernel template per library call and
+// compiles it at run time.  Here the template is the hand-written streaming
+// kernel below; what is instantiated is the body: the optimizer's fused
+// postfix program (map chains, predicates, masked reduction) is turned into
+// straight-line SSA code by symbolic execution of its stack, and compiled
+// once per program structure with NVRTC for sm_103a (constants stay kernel
+// arguments, so programs that differ only in constants share a kernel).
+// The result record and the deterministic block / last-block combine are the
+// same as those of the interpreting kernel (k_stream.cu), which remains the
+// fallback when NVRTC is unavailable or specialisation is switched off.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "sg_internal.h"
+#include "sg_jit.h"
+
+namespace sgk {
+namespace {
+
+// ---- NVRTC, loaded on first use ------------------------------------------
+typedef int nvrtcResult_t;
+struct Nvrtc {
+  void* h = nullptr;
+  nvrtcResult_t (*create)(void**, const char*, const char*, int, const char* const*,
+                          const char* const*) = nullptr;
+  nvrtcResult_t (*compile)(void*, int, const char* const*) = nullptr;
+  nvrtcResult_t (*cubin_size)(void*, size_t*) = nullptr;
+  nvrtcResult_t (*cubin)(void*, char*) = nullptr;
+  nvrtcResult_t (*log_size)(void*, size_t*) = nullptr;
+  nvrtcResult_t (*log)(void*, char*) = nullptr;
+  nvrtcResult_t (*destroy)(void**) = nullptr;
+  bool ok = false;
+};
+
+Nvrtc& nvrtc() {
+  static Nvrtc n;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                           "/usr/local/cuda/lib64/libnvrtc.so"};
+    for (const char* nm : names) {
+      n.h = dlopen(nm, RTLD_NOW | RTLD_LOCAL);
+      if (n.h) break;
+    }
+    if (!n.h) return;
+    n.create = (decltype(n.create))dlsym(n.h, "nvrtcCreateProgram");
+    n.compile = (decltype(n.compile))dlsym(n.h, "nvrtcCompileProgram");
+    n.cubin_size = (decltype(n.cubin_size))dlsym(n.h, "nvrtcGetCUBINSize");
+    n.cubin = (decltype(n.cubin))dlsym(n.h, "nvrtcGetCUBIN");
+    n.log_size = (decltype(n.log_size))dlsym(n.h, "nvrtcGetProgramLogSize");
+    n.log = (decltype(n.log))dlsym(n.h, "nvrtcGetProgramLog");
+    n.destroy = (decltype(n.destroy))dlsym(n.h, "nvrtcDestroyProgram");
+    n.ok = n.create && n.compile && n.cubin_size && n.cubin && n.log_size && n.log && n.destroy;
+  });
+  return n;
+}
+
+// ---- the kernel template ---------------------------------------------------
+// Layouts below must match PassResult (sg_internal.h) and JitArgs (sg_jit.h).
+const char* kTemplateHead = R"SGJIT(
+struct PassResult {
+  double sum; long long count; float mn, mx; int nan_seen; int pad; long long first[4];
+};
+struct JitArgs {
+  const float* in[4]; float* out[4]; long long n; float cst[48];
+  PassResult* partials; unsigned* counter; PassResult* result; int vec4; int pad;
+};
+#define SG_NONE 0x7fffffffffffffffLL
+__device__ __forceinline__ bool sg_nan(float v) { return v != v; }
+__device__ __forceinline__ float sg_min(float a, float b) {
+  return (sg_nan(a) || sg_nan(b)) ? __int_as_float(0x7fffffff) : (a < b ? a : b);
+}
+__device__ __forceinline__ float sg_max(float a, float b) {
+  return (sg_nan(a) || sg_nan(b)) ? __int_as_float(0x7fffffff) : (a > b ? a : b);
+}
+__device__ __forceinline__ float sg_b(bool v) { return v ? 1.0f : 0.0f; }
+struct Acc { double sum; long long cnt; float mn, mx; int nan_seen; long long first[4]; };
+__device__ __forceinline__ void acc_init(Acc& a) {
+  a.sum = 0.0; a.cnt = 0; a.mn = __int_as_float(0x7f800000); a.mx = __int_as_float(0xff800000);
+  a.nan_seen = 0;
+  for (int p = 0; p < 4; ++p) a.first[p] = SG_NONE;
+}
+__device__ __forceinline__ void acc_merge(Acc& a, const Acc& b) {
+  a.sum += b.sum; a.cnt += b.cnt;
+  a.mn = b.mn < a.mn ? b.mn : a.mn; a.mx = b.mx > a.mx ? b.mx : a.mx;
+  a.nan_seen |= b.nan_seen;
+  for (int p = 0; p < 4; ++p) a.first[p] = b.first[p] < a.first[p] ? b.first[p] : a.first[p];
+}
+__device__ __forceinline__ void warp_reduce(Acc& a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    Acc b;
+    b.sum = __shfl_xor_sync(0xffffffffu, a.sum, o);
+    b.cnt = __shfl_xor_sync(0xffffffffu, a.cnt, o);
+    b.mn = __shfl_xor_sync(0xffffffffu, a.mn, o);
+    b.mx = __shfl_xor_sync(0xffffffffu, a.mx, o);
+    b.nan_seen = __shfl_xor_sync(0xffffffffu, a.nan_seen, o);
+    for (int p = 0; p < 4; ++p) b.first[p] = __shfl_xor_sync(0xffffffffu, a.first[p], o);
+    acc_merge(a, b);
+  }
+}
+__device__ __forceinline__ void block_reduce(Acc& a) {
+  __shared__ Acc sh[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  warp_reduce(a);
+  if (lane == 0) sh[w] = a;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane < nw) a = sh[lane]; else acc_init(a);
+    warp_reduce(a);
+  }
+  __syncthreads();
+}
+// one masked value into the reduction (mn/mx skip NaN, which sets nan_seen)
+__device__ __forceinline__ void acc_one(Acc& a, float v, bool m) {
+  if (!m) return;
+  a.cnt += 1;
+  if (sg_nan(v)) a.nan_seen = 1;
+  else { a.mn = v < a.mn ? v : a.mn; a.mx = v > a.mx ? v : a.mx; }
+}
+)SGJIT";
+
+const char* kTemplateKernel = R"SGJIT(
+extern "C" __global__ void __launch_bounds__(256) sg_fused(const JitArgs a) {
+  Acc acc;
+  acc_init(acc);
+  const long long n = a.n;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long tail = 0;
+  if (a.vec4) {
+    const long long nv = n >> 2;
+    tail = nv << 2;
+    for (long long v = tid; v < nv; v += stride) {
+      float xs[SG_NX][4];
+#pragma unroll
+      for (int k = 0; k < SG_NIN; ++k) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(a.in[k]) + v);
+        xs[k][0] = t.x; xs[k][1] = t.y; xs[k][2] = t.z; xs[k][3] = t.w;
+      }
+      float os[SG_NO][4];
+      float rv[4];
+      bool rm[4];
+      unsigned hit[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        float x[SG_NX], o[SG_NO];
+#pragma unroll
+        for (int k = 0; k < SG_NIN; ++k) x[k] = xs[k][l];
+        hit[l] = 0u; rv[l] = 0.0f; rm[l] = false;
+        sg_body(a, x, (v << 2) + l, o, hit[l], rv[l], rm[l]);
+#pragma unroll
+        for (int k = 0; k < SG_NOUT; ++k) os[k][l] = o[k];
+      }
+#pragma unroll
+      for (int k = 0; k < SG_NOUT; ++k)
+        reinterpret_cast<float4*>(a.out[k])[v] = make_float4(os[k][0], os[k][1], os[k][2], os[k][3]);
+#if SG_NPRED > 0
+#pragma unroll
+      for (int l = 3; l >= 0; --l)
+#pragma unroll
+        for (int p = 0; p < SG_NPRED; ++p)
+          if ((hit[l] >> p) & 1u) acc.first[p] = (v << 2) + l < acc.first[p] ? (v << 2) + l : acc.first[p];
+#endif
+#if SG_RED
+      {
+        // binary32 pairs, one binary64 add per four elements (redone in
+        // binary64 if a pair sum of finite terms overflowed)
+        float t[4];
+        bool inf = false;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          t[l] = rm[l] ? rv[l] : 0.0f;
+          inf |= fabsf(t[l]) == __int_as_float(0x7f800000);
+          acc_one(acc, rv[l], rm[l]);
+        }
+        const float p = __fadd_rn(__fadd_rn(t[0], t[1]), __fadd_rn(t[2], t[3]));
+        if (fabsf(p) == __int_as_float(0x7f800000) && !inf)
+          acc.sum += ((double)t[0] + (double)t[1]) + ((double)t[2] + (double)t[3]);
+        else
+          acc.sum += (double)p;
+      }
+#endif
+    }
+  }
+  for (long long i = tail + tid; i < n; i += stride) {
+    float x[SG_NX], o[SG_NO];
+#pragma unroll
+    for (int k = 0; k < SG_NIN; ++k) x[k] = a.in[k][i];
+    unsigned hit = 0u;
+    float rv = 0.0f;
+    bool rm = false;
+    sg_body(a, x, i, o, hit, rv, rm);
+#pragma unroll
+    for (int k = 0; k < SG_NOUT; ++k) a.out[k][i] = o[k];
+#if SG_NPRED > 0
+#pragma unroll
+    for (int p = 0; p < SG_NPRED; ++p)
+      if ((hit >> p) & 1u) acc.first[p] = i < acc.first[p] ? i : acc.first[p];
+#endif
+#if SG_RED
+    acc_one(acc, rv, rm);
+    if (rm) acc.sum += (double)rv;
+#endif
+  }
+#if SG_RED || SG_NPRED > 0
+  block_reduce(acc);
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    PassResult r;
+    r.sum = acc.sum; r.count = acc.cnt; r.mn = acc.mn; r.mx = acc.mx; r.nan_seen = acc.nan_seen;
+    r.pad = 0;
+    for (int p = 0; p < 4; ++p) r.first[p] = acc.first[p];
+    a.partials[blockIdx.x] = r;
+    __threadfence();
+    am_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  Acc tot;
+  acc_init(tot);
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    const PassResult* q = &a.partials[b];
+    Acc p;
+    p.sum = __ldcg(&q->sum); p.cnt = __ldcg(&q->count); p.mn = __ldcg(&q->mn);
+    p.mx = __ldcg(&q->mx); p.nan_seen = __ldcg(&q->nan_seen);
+    for (int k = 0; k < 4; ++k) p.first[k] = __ldcg(&q->first[k]);
+    acc_merge(tot, p);
+  }
+  block_reduce(tot);
+  if (threadIdx.x == 0) {
+    PassResult r;
+    r.sum = tot.sum; r.count = tot.cnt; r.mn = tot.mn; r.mx = tot.mx; r.nan_seen = tot.nan_seen;
+    r.pad = 0;
+    for (int p = 0; p < 4; ++p) r.first[p] = tot.first[p];
+    *a.result = r;
+    *a.counter = 0u;
+  }
+#endif
+}
+)SGJIT";
+
+// ---- body generation: symbolic execution of the postfix program -----------
+bool gen_body(const Prog& pr, uint32_t pred_exists, std::string* body) {
+  std::vector<std::string> st;
+  std::string b;
+  int t = 0;
+  auto tmp = [&](const std::string& expr) {
+    std::string nm = "t" + std::to_string(t++);
+    b += "  const float " + nm + " = " + expr + ";\n";
+    return nm;
+  };
+  auto pop = [&](std::string* v) {
+    if (st.empty()) return false;
+    *v = st.back();
+    st.pop_back();
+    return true;
+  };
+  char buf[64];
+  for (int pc = 0; pc < pr.nops; ++pc) {
+    const int op = pr.op[pc];
+    std::string x, y, z;
+    switch (op) {
+      case SG_OP_LOAD:
+        snprintf(buf, sizeof buf, "x[%d]", (int)pr.arg[pc]);
+        st.push_back(buf);
+        break;
+      case SG_OP_CONST:
+        snprintf(buf, sizeof buf, "a.cst[%d]", pc);
+        st.push_back(buf);
+        break;
+      case SG_OP_INDEX: st.push_back(tmp("__ll2float_rn(i)")); break;
+      case SG_OP_DUP:
+        if (st.empty()) return false;
+        st.push_back(st.back());
+        break;
+      case SG_OP_SWAP:
+        if (st.size() < 2) return false;
+        std::swap(st[st.size() - 1], st[st.size() - 2]);
+        break;
+      case SG_OP_NEG: case SG_OP_ABS: case SG_OP_SQRT: case SG_OP_NOT: {
+        if (!pop(&x)) return false;
+        const char* f = op == SG_OP_NEG ? "(-%s)" : op == SG_OP_ABS ? "fabsf(%s)"
+                        : op == SG_OP_SQRT ? "__fsqrt_rn(%s)" : "sg_b(!(%s != 0.0f))";
+        snprintf(buf, sizeof buf, f, x.c_str());
+        st.push_back(tmp(buf));
+        break;
+      }
+      case SG_OP_FMA: case SG_OP_SELECT: {
+        if (!pop(&z) || !pop(&y) || !pop(&x)) return false;
+        std::string e = op == SG_OP_FMA
+                            ? "__fmaf_rn(" + x + ", " + y + ", " + z + ")"
+                            : "((" + x + " != 0.0f) ? " + y + " : " + z + ")";
+        st.push_back(tmp(e));
+        break;
+      }
+      case K_STORE:
+        if (st.empty()) return false;
+        b += "  o[" + std::to_string((int)pr.arg[pc]) + "] = " + st.back() + ";\n";
+        break;
+      case K_PRED: {
+        if (!pop(&x)) return false;
+        const int p = pr.arg[pc];
+        const bool ex = (pred_exists >> p) & 1u;
+        b += std::string("  if (") + (ex ? "" : "!") + "(" + x + " != 0.0f)) hit |= " +
+             std::to_string(1u << p) + "u;\n";
+        break;
+      }
+      case K_MASK:
+        if (!pop(&x)) return false;
+        b += "  mask = (" + x + " != 0.0f);\n";
+        break;
+      case K_REDUCE:
+        if (!pop(&x)) return false;
+        b += "  rv = " + x + "; rm = mask; mask = true;\n";
+        break;
+      case K_POP:
+        if (!pop(&x)) return false;
+        break;
+      default: {  // binary
+        if (!pop(&y) || !pop(&x)) return false;
+        std::string e;
+        switch (op) {
+          case SG_OP_ADD: e = "__fadd_rn(" + x + ", " + y + ")"; break;
+          case SG_OP_SUB: e = "__fsub_rn(" + x + ", " + y + ")"; break;
+          case SG_OP_MUL: e = "__fmul_rn(" + x + ", " + y + ")"; break;
+          case SG_OP_DIV: e = "__fdiv_rn(" + x + ", " + y + ")"; break;
+          case SG_OP_MIN: e = "sg_min(" + x + ", " + y + ")"; break;
+          case SG_OP_MAX: e = "sg_max(" + x + ", " + y + ")"; break;
+          case SG_OP_LT: e = "sg_b(" + x + " < " + y + ")"; break;
+          case SG_OP_LE: e = "sg_b(" + x + " <= " + y + ")"; break;
+          case SG_OP_GT: e = "sg_b(" + x + " > " + y + ")"; break;
+          case SG_OP_GE: e = "sg_b(" + x + " >= " + y + ")"; break;
+          case SG_OP_EQ: e = "sg_b(" + x + " == " + y + ")"; break;
+          case SG_OP_NE: e = "sg_b(" + x + " != " + y + ")"; break;
+          case SG_OP_AND: e = "sg_b(" + x + " != 0.0f && " + y + " != 0.0f)"; break;
+          case SG_OP_OR: e = "sg_b(" + x + " != 0.0f || " + y + " != 0.0f)"; break;
+          default: return false;
+        }
+        st.push_back(tmp(e));
+      }
+    }
+  }
+  *body = b;
+  return true;
+}
+
+struct Cache {
+  std::mutex mu;
+  std::unordered_map<std::string, cudaKernel_t> kernels;
+  std::unordered_map<std::string, bool> failed;
+};
+Cache& cache() {
+  static Cache c;
+  return c;
+}
+
+}  // namespace
+
+bool jit_available() { return nvrtc().ok; }
+
+// Returns the specialised kernel, compiling it on first use; nullptr when it
+// cannot be built (then the caller uses the interpreting kernel).
+cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, bool reduce,
+                               uint32_t pred_exists, std::string* log) {
+  Nvrtc& nv = nvrtc();
+  if (!nv.ok) {
+    if (log) *log = "NVRTC library not found";
+    return nullptr;
+  }
+  std::string body;
+  if (!gen_body(pr, pred_exists, &body)) {
+    if (log) *log = "program could not be specialised";
+    return nullptr;
+  }
+  char defs[256];
+  snprintf(defs, sizeof defs,
+           "#define SG_NIN %d\n#define SG_NX %d\n#define SG_NOUT %d\n#define SG_NO %d\n"
+           "#define SG_NPRED %d\n#define SG_RED %d\n",
+           nin, nin > 0 ? nin : 1, nout, nout > 0 ? nout : 1, npred, reduce ? 1 : 0);
+  std::string src = std::string(defs) + kTemplateHead +
+                    "__device__ __forceinline__ void sg_body(const JitArgs& a, const float* x, "
+                    "long long i, float* o, unsigned& hit, float& rv, bool& rm) {\n"
+                    "  bool mask = true;\n  (void)x; (void)i; (void)o; (void)hit; (void)rv; "
+                    "(void)rm; (void)a;\n" +
+                    body + "  (void)mask;\n}\n" + kTemplateKernel;
+  Cache& c = cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  auto it = c.kernels.find(src);
+  if (it != c.kernels.end()) return it->second;
+  if (c.failed.count(src)) return nullptr;
+  void* prog = nullptr;
+  cudaKernel_t k = nullptr;
+  if (nv.create(&prog, src.c_str(), "sg_fused.cu", 0, nullptr, nullptr) == 0) {
+    const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-default-device",
+                          "-fmad=false"};
+    const int rc = nv.compile(prog, 4, opts);
+    if (rc == 0) {
+      size_t sz = 0;
+      nv.cubin_size(prog, &sz);
+      std::vector<char> cubin(sz);
+      nv.cubin(prog, cubin.data());
+      cudaLibrary_t lib = nullptr;
+      if (cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) ==
+              cudaSuccess &&
+          cudaLibraryGetKernel(&k, lib, "sg_fused") == cudaSuccess) {
+        // the library stays loaded for the life of the process (cached kernel)
+      } else {
+        cudaGetLastError();
+        k = nullptr;
+        if (log) *log = "loading the specialised kernel failed";
+      }
+    } else if (log) {
+      size_t ls = 0;
+      nv.log_size(prog, &ls);
+      std::string l(ls, '\0');
+      nv.log(prog, &l[0]);
+      *log = l;
+    }
+    nv.destroy(&prog);
+  }
+  if (k) c.kernels[src] = k;
+  else c.failed[src] = true;
+  return k;
+}
+
+cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,
+                              cudaStream_t st, Prof* prof) {
+  JitArgs a{};
+  for (int i = 0; i < kMaxIn; ++i) a.in[i] = s.in[i];
+  for (int i = 0; i < kMaxOut; ++i) a.out[i] = s.out[i];
+  a.n = s.n;
+  for (int i = 0; i < kMaxProg; ++i) a.cst[i] = s.prog.cst[i];
+  a.partials = s.partials;
+  a.counter = s.counter;
+  a.result = s.result;
+  a.vec4 = s.vec4;
+  void* args[] = {&a};
+  prof_begin(prof, "stream_jit", st);
+  cudaError_t e = cudaLaunchKernel((const void*)k, dim3(grid), dim3(block), args, 0, st);
+  prof_end(prof, st);
+  return e;
+}
+
+}  // namespace sgk

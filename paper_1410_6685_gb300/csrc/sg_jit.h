@@ -1,0 +1,32 @@
+// sg_jit.h -- run-time specialised fused passes (sg_jit.cpp).  Internal.
+#pragma once
+#include <string>
+
+#include "sg_internal.h"
+
+namespace sgk {
+
+// Kernel argument block of the specialised kernel; its layout is repeated
+// verbatim in the kernel template source inside sg_jit.cpp.
+struct JitArgs {
+  const float* in[kMaxIn];
+  float* out[kMaxOut];
+  long long n;
+  float cst[kMaxProg];
+  PassResult* partials;
+  unsigned* counter;
+  PassResult* result;
+  int vec4;
+  int pad;
+};
+static_assert(kMaxIn == 4 && kMaxOut == 4 && kMaxProg == 48 && kMaxPred == 4,
+              "the kernel template hard-codes these sizes");
+static_assert(sizeof(JitArgs) == 296, "JitArgs layout changed: update the template");
+
+bool jit_available();
+cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, bool reduce,
+                               uint32_t pred_exists, std::string* log);
+cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,
+                              cudaStream_t st, Prof* prof);
+
+}  // namespace sgk

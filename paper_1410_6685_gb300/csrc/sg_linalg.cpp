@@ -1,24 +1,95 @@
-// sg_linalg.cpp -- matrix product and its Freivalds postcondition (Sec. 3.4
-// `multiply`), dispatched from the executor.
+// sg_linalg.cpp -- matrix product (Sec. 3.4 `multiply`) and its Freivalds
+// postcondition, dispatched from the executor.
+#include <cmath>
+#include <cstring>
+
+#include "sg_linalg_kernels.h"
 #include "sg_plan.h"
 
-size_t sg_linalg_scratch(sg_ctx*, Node*) { return 0; }
+namespace {
 
-sg_status sg_exec_linalg(sg_ctx* c, Node*, void*, void*, cudaError_t*) {
-  c->err = "matrix product not built yet";
-  return SG_ERR_UNSUPPORTED;
+// effective unit roundoff of a product: operand rounding (two operands) plus
+// binary32 accumulation over n terms
+float u_eff_for(int prec, long long n) {
+  const double acc = std::ldexp(1.0, -24) * std::sqrt((double)n);
+  switch (prec) {
+    case SG_PREC_BF16_TC: return (float)(std::ldexp(1.0, -8) + acc);
+    case SG_PREC_F16_TC: return (float)(std::ldexp(1.0, -10) + acc);
+    default: return (float)acc;
+  }
 }
 
-bool sg_linalg_result(sg_ctx*, Node*, const void*, long long*, double*) { return false; }
+}  // namespace
+
+size_t sg_linalg_scratch(sg_ctx*, Node* n) {
+  if (n->kind == NK::MATMUL) {
+    if (n->prec == SG_PREC_F32_SIMT) return 0;
+    return sgk::gemm_tc_scratch_bytes((int)n->in[0]->rows, (int)n->in[1]->cols,
+                                      (int)n->in[0]->cols);
+  }
+  return sgk::freivalds_scratch_bytes((int)n->in[0]->rows, n->nvec);
+}
+
+sg_status sg_exec_linalg(sg_ctx* c, Node* n, void* rec, void* work, cudaError_t* e) {
+  if (n->kind == NK::MATMUL) {
+    Value* A = n->in[0].get();
+    Value* B = n->in[1].get();
+    Value* Cv = n->out.get();
+    if (!Cv->st) {
+      auto st = std::make_shared<Storage>();
+      st->bytes = (size_t)Cv->n * 4;
+      st->stream = c->stream;
+      if (st->bytes) {
+        cudaError_t ae = cudaMallocAsync(&st->ptr, st->bytes, c->stream);
+        if (ae != cudaSuccess) {
+          cudaGetLastError();
+          c->err = "matrix allocation failed";
+          return SG_ERR_OOM;
+        }
+        st->owned = true;
+      }
+      Cv->st = std::move(st);
+    }
+    const int M = (int)A->rows, K = (int)A->cols, N = (int)B->cols;
+    const float* a = static_cast<const float*>(A->st->ptr);
+    const float* b = static_cast<const float*>(B->st->ptr);
+    float* cc = static_cast<float*>(Cv->st->ptr);
+    if (n->prec == SG_PREC_F32_SIMT) {
+      *e = sgk::launch_gemm_f32(a, b, cc, M, N, K, c->stream, &c->prof);
+      c->kernels += 1;
+    } else {
+      *e = sgk::launch_gemm_tc(a, K, b, N, cc, N, M, N, K, n->prec == SG_PREC_F16_TC, false,
+                               work, c->stream, &c->prof, &c->kernels);
+    }
+    return SG_OK;
+  }
+  // Freivalds: in[0] = C (target), in[1] = A, in[2] = B
+  const int N = (int)n->in[0]->rows;
+  // the precision of the product that produced C, when the check is built in
+  const int prec = n->in[0]->producer && n->in[0]->producer->kind == NK::MATMUL
+                       ? n->in[0]->producer->prec
+                       : n->prec;
+  *e = sgk::launch_freivalds(static_cast<const float*>(n->in[1]->st->ptr),
+                             static_cast<const float*>(n->in[2]->st->ptr),
+                             static_cast<const float*>(n->in[0]->st->ptr), N, n->seed, n->nvec,
+                             (float)n->tol, u_eff_for(prec, N), work,
+                             static_cast<sgk::FreivaldsResult*>(rec), c->stream, &c->prof,
+                             &c->kernels);
+  return SG_OK;
+}
+
+bool sg_linalg_result(sg_ctx*, Node* n, const void* rec, long long* row, double* observed) {
+  if (n->kind != NK::CHECK) return false;
+  sgk::FreivaldsResult r;
+  memcpy(&r, rec, sizeof r);
+  *observed = r.max_ratio;
+  if (!r.viol_enc) return false;
+  *row = (long long)~r.viol_enc;
+  return true;
+}
 
 extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix*, sg_vector*, const sg_solve_opts*,
                               sg_vector**, sg_solve_info*) {
   if (c) c->err = "solve not built yet";
-  return SG_ERR_UNSUPPORTED;
-}
-
-extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain*, const float*, const int64_t*,
-                                  int64_t, double*, int64_t*, int64_t*) {
-  if (c) c->err = "batch not built yet";
   return SG_ERR_UNSUPPORTED;
 }

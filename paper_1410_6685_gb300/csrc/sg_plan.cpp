@@ -26,6 +26,7 @@
 #include <string>
 
 #include "sg_internal.h"
+#include "sg_jit.h"
 #include "sg_plan.h"
 
 namespace {
@@ -522,13 +523,15 @@ sg_status sg_execute_pending(sg_ctx* c) {
   for (Pass& P : passes) {
     switch (P.kind) {
       case PK::STREAM:
-        work = std::max(work, (size_t)stream_grid(c, P) * sizeof(sgk::PassResult));
+        work = std::max(work, (size_t)std::max(stream_grid(c, P), c->num_sms * 8) *
+                                  sizeof(sgk::PassResult));
         break;
       case PK::SORT: work = std::max(work, sgk::sort_scratch_bytes(P.n)); break;
       case PK::FILTER: work = std::max(work, sgk::filter_scratch_bytes(P.n)); break;
       case PK::CHECK_SORTED:
       case PK::CHECK_PERM: work = std::max(work, sgk::check_scratch_bytes()); break;
-      default: break;
+      case PK::MATMUL:
+      case PK::FREIVALDS: work = std::max(work, sg_linalg_scratch(c, P.main)); break;
     }
   }
   sg_status st = ensure_scratch(c, res_bytes + work);
@@ -589,7 +592,19 @@ sg_status sg_execute_pending(sg_ctx* c) {
         a.counter = c->counter;
         a.result = static_cast<sgk::PassResult*>(rec);
         a.vec4 = vec ? 1 : 0;
-        e = sgk::launch_stream(a, stream_grid(c, P), kStreamBlock, c->stream, &c->prof);
+        cudaKernel_t jk = nullptr;
+        if (c->codegen == SG_CODEGEN_SPECIALIZE)
+          jk = sgk::jit_stream_kernel(a.prog, a.nin, (int)P.stores.size(), a.npred,
+                                      a.has_reduce != 0, a.pred_exists, nullptr);
+        if (jk) {
+          const long long units = std::max<long long>(1, (P.n + 3) / 4);
+          const long long want = (units + kStreamBlock - 1) / kStreamBlock;
+          const int grid = (int)std::max<long long>(
+              1, std::min<long long>(want, (long long)c->num_sms * 8));
+          e = sgk::launch_jit_stream(jk, a, grid, kStreamBlock, c->stream, &c->prof);
+        } else {
+          e = sgk::launch_stream(a, stream_grid(c, P), kStreamBlock, c->stream, &c->prof);
+        }
         c->kernels++;
         break;
       }

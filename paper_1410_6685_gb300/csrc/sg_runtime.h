@@ -72,6 +72,34 @@ struct Node {
 };
 using NodeP = std::shared_ptr<Node>;
 
+// Captured batched-collections launches, keyed by everything baked into
+// the CUDA graph.
+struct BatchKey {
+  sg_chain chain;
+  const float* data;
+  const int64_t* offsets;
+  int64_t nseg;
+  double* sums;
+  int64_t* first;
+  int64_t* kept;
+  long long chunk;
+  int grid_per_sm;
+  int pad;
+};
+
+struct BatchPlan {
+  cudaGraphExec_t exec = nullptr;
+  void* scratch = nullptr;
+  unsigned* host_flag = nullptr;
+  long long capacity = 0;
+};
+
+struct BatchPlanCache {
+  std::vector<std::pair<BatchKey, BatchPlan>> plans;
+  cudaStream_t capture_stream = nullptr;
+  ~BatchPlanCache();
+};
+
 struct sg_ctx {
   int device = -1;
   bool planning_only = true;
@@ -80,6 +108,7 @@ struct sg_ctx {
   int mode = SG_CONTRACTS_PRE_POST;
   int fusion = SG_FUSE_ON;
   int sched = SG_SCHED_AUTOTUNE;
+  int codegen = SG_CODEGEN_SPECIALIZE;
   std::vector<NodeP> pending;
   int next_node = 0;
   int next_contract = 0;
@@ -95,6 +124,7 @@ struct sg_ctx {
   size_t host_res_bytes = 0;
   sgk::SortInject inject{};            // contract-test fault for the next sort
   sgk::Prof prof;                      // per-kernel event tracing
+  BatchPlanCache batch;                // captured batched launches
 };
 
 struct sg_vector {

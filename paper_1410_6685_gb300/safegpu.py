@@ -113,7 +113,7 @@ def _load():
         "sg_ensure": [vp, vp, P(SgContract), P(C.c_int32)],
         "sg_last_violation": [vp, P(SgViolation)], "sg_flush": [vp],
         "sg_set_contract_mode": [vp, i32], "sg_set_fusion": [vp, i32],
-        "sg_set_scheduler": [vp, i32], "sg_plan_describe": [vp, C.c_char_p, sz, P(sz)],
+        "sg_set_scheduler": [vp, i32], "sg_set_codegen": [vp, i32], "sg_plan_describe": [vp, C.c_char_p, sz, P(sz)],
         "sg_kernel_count": [vp, P(i64)], "sg_profile_enable": [vp, i32], "sg_profile_report": [vp, C.c_char_p, sz, P(sz), i32], "sg_debug_inject_sort": [vp, i32, i64, i64],
         "sg_batch_run": [vp, P(SgChain), vp, vp, i64, vp, vp, vp],
     }
@@ -426,3 +426,10 @@ def sg_profile_report(ctx, reset=False) -> dict:
         name, cnt, ms = line.split()
         out[name] = (int(cnt), float(ms))
     return out
+
+
+SG_CODEGEN_INTERPRET, SG_CODEGEN_SPECIALIZE = 0, 1
+
+
+def sg_set_codegen(ctx, g):
+    _check(lib.sg_set_codegen(ctx, g), ctx)

@@ -15,14 +15,18 @@ SIZES = [1, 3, 4, 5, 255, 1024 + 3, 256 * 4 * 37 + 1, (1 << 20) + 7]
 ADD = [("x", 0), ("x", 1), ("add",)]
 
 
-@pytest.fixture(scope="module")
-def env():
+@pytest.fixture(scope="module", params=["specialize", "interpret"])
+def env(request):
+    """Every test runs with the run-time specialised kernels and with the
+    interpreting kernel: both must match the oracle."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1410_6685_gb300 import safegpu as sg
     assert torch.cuda.is_available()
     ctx = sg.sg_init(0, torch.cuda.current_stream().cuda_stream)
+    sg.sg_set_codegen(ctx, sg.SG_CODEGEN_SPECIALIZE if request.param == "specialize"
+                      else sg.SG_CODEGEN_INTERPRET)
     yield sg, ctx, torch
     sg.sg_destroy(ctx)
 
