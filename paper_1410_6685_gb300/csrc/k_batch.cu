@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kBB) k_batch(const float* __restrict__ data,
       }
     }
     // block reduction (fixed order)
+    ev::acc_fold(acc);
     ev::warp_reduce(acc);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) s_acc[w] = acc;

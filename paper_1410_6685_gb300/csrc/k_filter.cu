@@ -187,4 +187,6 @@ cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& p
   return cudaGetLastError();
 }
 
+
+
 }  // namespace sgk

@@ -14,9 +14,10 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 8;
 
 template <bool VEC>
-__global__ void __launch_bounds__(256) k_gemm_f32(const float* __restrict__ A,
-                                                  const float* __restrict__ B,
-                                                  float* __restrict__ C, int M, int N, int K) {
+__global__ void __launch_bounds__(256) k_gemm_f32(const float* __restrict__ A, int lda,
+                                                  const float* __restrict__ B, int ldb,
+                                                  float* __restrict__ C, int ldc, int M, int N,
+                                                  int K, int subtract) {
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const int tid = threadIdx.x;
@@ -32,22 +33,22 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float* __restrict__ A,
     const int gm = m0 + a_row;
     const int gk = k0 + a_k;
     if (VEC && gm < M && gk + 3 < K) {
-      const float4 t = *reinterpret_cast<const float4*>(A + (size_t)gm * K + gk);
+      const float4 t = *reinterpret_cast<const float4*>(A + (size_t)gm * lda + gk);
       ra[0] = t.x; ra[1] = t.y; ra[2] = t.z; ra[3] = t.w;
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        ra[j] = (gm < M && gk + j < K) ? A[(size_t)gm * K + gk + j] : 0.0f;
+        ra[j] = (gm < M && gk + j < K) ? A[(size_t)gm * lda + gk + j] : 0.0f;
     }
     const int gkb = k0 + b_k;
     const int gn = n0 + b_n;
     if (VEC && gkb < K && gn + 3 < N) {
-      const float4 t = *reinterpret_cast<const float4*>(B + (size_t)gkb * N + gn);
+      const float4 t = *reinterpret_cast<const float4*>(B + (size_t)gkb * ldb + gn);
       rb[0] = t.x; rb[1] = t.y; rb[2] = t.z; rb[3] = t.w;
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        rb[j] = (gkb < K && gn + j < N) ? B[(size_t)gkb * N + gn + j] : 0.0f;
+        rb[j] = (gkb < K && gn + j < N) ? B[(size_t)gkb * ldb + gn + j] : 0.0f;
     }
   };
   auto store = [&](int buf) {
@@ -95,14 +96,19 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float* __restrict__ A,
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int gn = n0 + h * 64 + tx * 4;
-      float* c = C + (size_t)gm * N + gn;
+      float* c = C + (size_t)gm * ldc + gn;
       if (VEC && gn + 3 < N) {
-        *reinterpret_cast<float4*>(c) =
-            make_float4(acc[i][h * 4], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]);
+        float4 v = make_float4(acc[i][h * 4], acc[i][h * 4 + 1], acc[i][h * 4 + 2],
+                               acc[i][h * 4 + 3]);
+        if (subtract) {
+          const float4 o = *reinterpret_cast<const float4*>(c);
+          v = make_float4(o.x - v.x, o.y - v.y, o.z - v.z, o.w - v.w);
+        }
+        *reinterpret_cast<float4*>(c) = v;
       } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (gn + j < N) c[j] = acc[i][h * 4 + j];
+          if (gn + j < N) c[j] = subtract ? c[j] - acc[i][h * 4 + j] : acc[i][h * 4 + j];
       }
     }
   }
@@ -110,16 +116,18 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float* __restrict__ A,
 
 }  // namespace
 
-cudaError_t launch_gemm_f32(const float* A, const float* B, float* C, int M, int N, int K,
-                            cudaStream_t s, Prof* prof) {
-  const bool vec = (K % 4 == 0) && (N % 4 == 0) && ((uintptr_t)A % 16 == 0) &&
-                   ((uintptr_t)B % 16 == 0) && ((uintptr_t)C % 16 == 0);
+cudaError_t launch_gemm_f32(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                            int M, int N, int K, bool subtract, cudaStream_t s, Prof* prof) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  const bool vec = (lda % 4 == 0) && (ldb % 4 == 0) && (ldc % 4 == 0) &&
+                   ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) &&
+                   ((uintptr_t)C % 16 == 0);
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
   prof_begin(prof, "gemm_f32_simt", s);
   if (vec)
-    k_gemm_f32<true><<<grid, 256, 0, s>>>(A, B, C, M, N, K);
+    k_gemm_f32<true><<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, subtract ? 1 : 0);
   else
-    k_gemm_f32<false><<<grid, 256, 0, s>>>(A, B, C, M, N, K);
+    k_gemm_f32<false><<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, subtract ? 1 : 0);
   prof_end(prof, s);
   return cudaGetLastError();
 }

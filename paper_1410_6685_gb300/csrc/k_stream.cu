@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(256) k_stream(const StreamArgs a) {
 
   if (!a.has_reduce && a.npred == 0) return;
 
+  acc_fold(acc);
   block_reduce(acc);
   __shared__ bool am_last;
   if (threadIdx.x == 0) {

@@ -13,6 +13,7 @@ constexpr long long kNoIndex = 0x7fffffffffffffffLL;
 
 struct Acc {
   double sum;
+  float hi, lo;   // per-thread double-float partial sum (folded into sum)
   long long cnt;
   float mn, mx;
   int nan_seen;
@@ -51,22 +52,16 @@ __device__ __forceinline__ void acc_reduce(Acc& acc, const float (&v)[L],
     }
   }
   acc.cnt += c;
-  if (L == 4) {
-    // pairwise in binary32, one binary64 add per four elements; redone in
-    // binary64 if the binary32 pair sum overflowed from finite terms
-    float p = __fadd_rn(__fadd_rn(t[0], t[1 % L]), __fadd_rn(t[2 % L], t[3 % L]));
-    if (isinf(p) && !any_inf) {
-      double q = 0.0;
+  // Knuth's TwoSum per element into a binary32 double-float accumulator
 #pragma unroll
-      for (int l = 0; l < L; ++l) q += (double)t[l];
-      acc.sum += q;
-    } else {
-      acc.sum += (double)p;
-    }
-  } else {
-#pragma unroll
-    for (int l = 0; l < L; ++l) acc.sum += (double)t[l];
+  for (int l = 0; l < L; ++l) {
+    const float s = __fadd_rn(acc.hi, t[l]);
+    const float bp = __fsub_rn(s, acc.hi);
+    const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bp)), __fsub_rn(t[l], bp));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, e);
   }
+  (void)any_inf;
 }
 
 // Execute op `op` with the stack holding D values before it.
@@ -253,8 +248,14 @@ __device__ __forceinline__ void run_prog(const StreamArgs& a,
   }
 }
 
+__device__ __forceinline__ void acc_fold(Acc& a) {
+  a.sum += (double)a.hi + (double)a.lo;
+  a.hi = 0.0f;
+  a.lo = 0.0f;
+}
+
 __device__ __forceinline__ void acc_merge(Acc& a, const Acc& b) {
-  a.sum += b.sum;
+  a.sum += b.sum + ((double)b.hi + (double)b.lo);
   a.cnt += b.cnt;
   a.mn = b.mn < a.mn ? b.mn : a.mn;
   a.mx = b.mx > a.mx ? b.mx : a.mx;
@@ -268,6 +269,8 @@ __device__ __forceinline__ void warp_reduce(Acc& a) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     Acc b;
+    b.hi = 0.0f;
+    b.lo = 0.0f;
     b.sum = __shfl_xor_sync(0xffffffffu, a.sum, o);
     b.cnt = __shfl_xor_sync(0xffffffffu, a.cnt, o);
     b.mn = __shfl_xor_sync(0xffffffffu, a.mn, o);
@@ -293,6 +296,8 @@ __device__ __forceinline__ void to_rec(const Acc& a, PassResult& r) {
 
 __device__ __forceinline__ void from_rec(const PassResult* r, Acc& a) {
   a.sum = __ldcg(&r->sum);
+  a.hi = 0.0f;
+  a.lo = 0.0f;
   a.cnt = __ldcg(&r->count);
   a.mn = __ldcg(&r->mn);
   a.mx = __ldcg(&r->mx);
@@ -303,6 +308,8 @@ __device__ __forceinline__ void from_rec(const PassResult* r, Acc& a) {
 
 __device__ __forceinline__ void acc_init(Acc& a) {
   a.sum = 0.0;
+  a.hi = 0.0f;
+  a.lo = 0.0f;
   a.cnt = 0;
   a.mn = CUDART_INF_F;
   a.mx = -CUDART_INF_F;

@@ -83,11 +83,24 @@ __device__ __forceinline__ float sg_max(float a, float b) {
   return (sg_nan(a) || sg_nan(b)) ? __int_as_float(0x7fffffff) : (a > b ? a : b);
 }
 __device__ __forceinline__ float sg_b(bool v) { return v ? 1.0f : 0.0f; }
-struct Acc { double sum; long long cnt; float mn, mx; int nan_seen; long long first[4]; };
+struct Acc { double sum; float hi, lo; long long cnt; float mn, mx; int nan_seen; long long first[4]; };
 __device__ __forceinline__ void acc_init(Acc& a) {
-  a.sum = 0.0; a.cnt = 0; a.mn = __int_as_float(0x7f800000); a.mx = __int_as_float(0xff800000);
+  a.sum = 0.0; a.hi = 0.0f; a.lo = 0.0f; a.cnt = 0;
+  a.mn = __int_as_float(0x7f800000); a.mx = __int_as_float(0xff800000);
   a.nan_seen = 0;
   for (int p = 0; p < 4; ++p) a.first[p] = SG_NONE;
+}
+// Knuth's TwoSum: hi + v = s + e exactly; the error terms gather in lo
+__device__ __forceinline__ void acc_add(Acc& a, float v) {
+  const float s = __fadd_rn(a.hi, v);
+  const float bp = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, e);
+}
+__device__ __forceinline__ void acc_fold(Acc& a) {
+  a.sum += (double)a.hi + (double)a.lo;
+  a.hi = 0.0f; a.lo = 0.0f;
 }
 __device__ __forceinline__ void acc_merge(Acc& a, const Acc& b) {
   a.sum += b.sum; a.cnt += b.cnt;
@@ -124,8 +137,11 @@ __device__ __forceinline__ void block_reduce(Acc& a) {
 __device__ __forceinline__ void acc_one(Acc& a, float v, bool m) {
   if (!m) return;
   a.cnt += 1;
+  acc_add(a, v);
+#if SG_MINMAX
   if (sg_nan(v)) a.nan_seen = 1;
   else { a.mn = v < a.mn ? v : a.mn; a.mx = v > a.mx ? v : a.mx; }
+#endif
 }
 )SGJIT";
 
@@ -172,23 +188,8 @@ extern "C" __global__ void __launch_bounds__(256) sg_fused(const JitArgs a) {
           if ((hit[l] >> p) & 1u) acc.first[p] = (v << 2) + l < acc.first[p] ? (v << 2) + l : acc.first[p];
 #endif
 #if SG_RED
-      {
-        // binary32 pairs, one binary64 add per four elements (redone in
-        // binary64 if a pair sum of finite terms overflowed)
-        float t[4];
-        bool inf = false;
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          t[l] = rm[l] ? rv[l] : 0.0f;
-          inf |= fabsf(t[l]) == __int_as_float(0x7f800000);
-          acc_one(acc, rv[l], rm[l]);
-        }
-        const float p = __fadd_rn(__fadd_rn(t[0], t[1]), __fadd_rn(t[2], t[3]));
-        if (fabsf(p) == __int_as_float(0x7f800000) && !inf)
-          acc.sum += ((double)t[0] + (double)t[1]) + ((double)t[2] + (double)t[3]);
-        else
-          acc.sum += (double)p;
-      }
+      for (int l = 0; l < 4; ++l) acc_one(acc, rv[l], rm[l]);
 #endif
     }
   }
@@ -209,10 +210,10 @@ extern "C" __global__ void __launch_bounds__(256) sg_fused(const JitArgs a) {
 #endif
 #if SG_RED
     acc_one(acc, rv, rm);
-    if (rm) acc.sum += (double)rv;
 #endif
   }
 #if SG_RED || SG_NPRED > 0
+  acc_fold(acc);
   block_reduce(acc);
   __shared__ bool am_last;
   if (threadIdx.x == 0) {
@@ -232,6 +233,7 @@ extern "C" __global__ void __launch_bounds__(256) sg_fused(const JitArgs a) {
   for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
     const PassResult* q = &a.partials[b];
     Acc p;
+    p.hi = 0.0f; p.lo = 0.0f;
     p.sum = __ldcg(&q->sum); p.cnt = __ldcg(&q->count); p.mn = __ldcg(&q->mn);
     p.mx = __ldcg(&q->mx); p.nan_seen = __ldcg(&q->nan_seen);
     for (int k = 0; k < 4; ++k) p.first[k] = __ldcg(&q->first[k]);
@@ -372,7 +374,7 @@ bool jit_available() { return nvrtc().ok; }
 // Returns the specialised kernel, compiling it on first use; nullptr when it
 // cannot be built (then the caller uses the interpreting kernel).
 cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, bool reduce,
-                               uint32_t pred_exists, std::string* log) {
+                               bool minmax, uint32_t pred_exists, std::string* log) {
   Nvrtc& nv = nvrtc();
   if (!nv.ok) {
     if (log) *log = "NVRTC library not found";
@@ -383,11 +385,12 @@ cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, boo
     if (log) *log = "program could not be specialised";
     return nullptr;
   }
-  char defs[256];
+  char defs[320];
   snprintf(defs, sizeof defs,
            "#define SG_NIN %d\n#define SG_NX %d\n#define SG_NOUT %d\n#define SG_NO %d\n"
-           "#define SG_NPRED %d\n#define SG_RED %d\n",
-           nin, nin > 0 ? nin : 1, nout, nout > 0 ? nout : 1, npred, reduce ? 1 : 0);
+           "#define SG_NPRED %d\n#define SG_RED %d\n#define SG_MINMAX %d\n",
+           nin, nin > 0 ? nin : 1, nout, nout > 0 ? nout : 1, npred, reduce ? 1 : 0,
+           minmax ? 1 : 0);
   std::string src = std::string(defs) + kTemplateHead +
                     "__device__ __forceinline__ void sg_body(const JitArgs& a, const float* x, "
                     "long long i, float* o, unsigned& hit, float& rv, bool& rm) {\n"

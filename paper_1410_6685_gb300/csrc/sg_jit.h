@@ -24,8 +24,9 @@ static_assert(kMaxIn == 4 && kMaxOut == 4 && kMaxProg == 48 && kMaxPred == 4,
 static_assert(sizeof(JitArgs) == 296, "JitArgs layout changed: update the template");
 
 bool jit_available();
+// minmax: the pass also tracks min / max / NaN (a min, max or avg is asked)
 cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, bool reduce,
-                               uint32_t pred_exists, std::string* log);
+                               bool minmax, uint32_t pred_exists, std::string* log);
 cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,
                               cudaStream_t st, Prof* prof);
 

@@ -55,7 +55,7 @@ sg_status sg_exec_linalg(sg_ctx* c, Node* n, void* rec, void* work, cudaError_t*
     const float* b = static_cast<const float*>(B->st->ptr);
     float* cc = static_cast<float*>(Cv->st->ptr);
     if (n->prec == SG_PREC_F32_SIMT) {
-      *e = sgk::launch_gemm_f32(a, b, cc, M, N, K, c->stream, &c->prof);
+      *e = sgk::launch_gemm_f32(a, K, b, N, cc, N, M, N, K, false, c->stream, &c->prof);
       c->kernels += 1;
     } else {
       *e = sgk::launch_gemm_tc(a, K, b, N, cc, N, M, N, K, n->prec == SG_PREC_F16_TC, false,
@@ -88,8 +88,3 @@ bool sg_linalg_result(sg_ctx*, Node* n, const void* rec, long long* row, double*
   return true;
 }
 
-extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix*, sg_vector*, const sg_solve_opts*,
-                              sg_vector**, sg_solve_info*) {
-  if (c) c->err = "solve not built yet";
-  return SG_ERR_UNSUPPORTED;
-}

@@ -5,9 +5,10 @@
 
 namespace sgk {
 
-// binary32 SIMT product C = A B (row-major M x K, K x N).
-cudaError_t launch_gemm_f32(const float* A, const float* B, float* C, int M, int N, int K,
-                            cudaStream_t s, Prof* prof);
+// binary32 SIMT product C = A B (or C = C - A B), row-major with leading
+// dimensions (M x K, K x N, M x N).
+cudaError_t launch_gemm_f32(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                            int M, int N, int K, bool subtract, cudaStream_t s, Prof* prof);
 
 // Tensor-core product: operands rounded (nearest even) to bf16 or fp16,
 // binary32 accumulation in tensor memory.  beta = 0: C = A B; beta = 1:

@@ -1,0 +1,30 @@
+// sg_lu.h -- elimination and solve kernels (k_lu.cu).  Internal.
+#pragma once
+#include "sg_internal.h"
+
+namespace sgk {
+
+constexpr int kLuPanel = 32;      // panel width of the blocked factorisation
+constexpr int kLuMaxN = 9216;     // the panel must fit the cluster's shared memory
+
+size_t lu_panel_max_smem(int n);
+cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info, cudaStream_t s,
+                            Prof* prof);
+cudaError_t launch_lu_laswp_trsm(float* LU, int n, int k, int jb, const int* piv, cudaStream_t s,
+                                 Prof* prof);
+// y = U^-1 L^-1 P rhs in binary32; rhs_is_residual only changes the trace
+// name.  flags: 2*ceil(n/32) words that never hold `epoch` before the call.
+cudaError_t launch_lu_solve(const float* LU, int n, const int* piv, const double* rhs,
+                            bool rhs_is_residual, float* y, unsigned* flags, unsigned epoch,
+                            unsigned* tickets, int* err, cudaStream_t s, Prof* prof);
+// r = b - A x in binary64; norms[0] = max|r|; rows with |r_i| > thresh
+// (or NaN) raise ~i into *viol (when viol is not null).
+cudaError_t launch_residual(const float* A, int n, const double* b, const double* x, double* r,
+                            double* norms, double thresh, unsigned long long* viol,
+                            cudaStream_t s, Prof* prof);
+cudaError_t launch_anorm(const float* A, int n, double* norms, cudaStream_t s);   // norms[3]
+// x = d (init) or x += d; norms[1] = max|d|, norms[2] = max|x|, norms[4] = max|b|
+cudaError_t launch_update(double* x, const float* d, const double* b, int n, bool init,
+                          double* norms, cudaStream_t s);
+
+}  // namespace sgk

@@ -593,9 +593,11 @@ sg_status sg_execute_pending(sg_ctx* c) {
         a.result = static_cast<sgk::PassResult*>(rec);
         a.vec4 = vec ? 1 : 0;
         cudaKernel_t jk = nullptr;
+        bool minmax = false;
+        for (Node* q : P.reduces) minmax |= q->rop == SG_REDUCE_MIN || q->rop == SG_REDUCE_MAX;
         if (c->codegen == SG_CODEGEN_SPECIALIZE)
           jk = sgk::jit_stream_kernel(a.prog, a.nin, (int)P.stores.size(), a.npred,
-                                      a.has_reduce != 0, a.pred_exists, nullptr);
+                                      a.has_reduce != 0, minmax, a.pred_exists, nullptr);
         if (jk) {
           const long long units = std::max<long long>(1, (P.n + 3) / 4);
           const long long want = (units + kStreamBlock - 1) / kStreamBlock;

@@ -433,3 +433,4 @@ SG_CODEGEN_INTERPRET, SG_CODEGEN_SPECIALIZE = 0, 1
 
 def sg_set_codegen(ctx, g):
     _check(lib.sg_set_codegen(ctx, g), ctx)
+
