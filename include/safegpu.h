@@ -399,6 +399,40 @@ sg_status sg_batch_run(sg_ctx* ctx, const sg_chain* chain, const float* data,
                        const int64_t* offsets, int64_t nseg, double* sums,
                        int64_t* first_viol, int64_t* kept);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free filter (the paper has no counterpart).  Some callers
+ * cannot allocate device memory: a serving runtime that reserves all of HBM
+ * in its own pool at start-up and forbids later allocations, a
+ * latency-critical path that cannot afford the device-wide synchronisation
+ * an allocation may imply, a plugin host that only hands out the input and
+ * output buffers.  This call runs the filter of sg_filter on caller-owned
+ * device buffers, needs no context, and keeps its scratch (the look-back
+ * words of the stream compaction) in one fixed array of
+ * SG_FILTER_NOALLOC_SCRATCH_BYTES (about 513 KB) in the library's device
+ * memory, which every GPU that loads the library holds until the process
+ * exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   pred      : predicate over slot 0, as for sg_filter
+ *   dev_x     : n binary32 inputs (device memory)
+ *   dev_out   : room for n binary32 outputs (device memory); the kept items,
+ *               in index order, are written to its start
+ *   dev_count : one int64 in device memory, receives the number kept
+ *   stream    : a cudaStream_t, or NULL for the legacy default stream; the
+ *               call waits for the stream before it returns
+ * Errors: n > SG_FILTER_NOALLOC_MAX_N (2^28) gives SG_ERR_SHAPE; a malformed
+ * predicate or a null buffer SG_ERR_INVALID_ARG; a look-back wait that gave
+ * up SG_ERR_TIMEOUT; a CUDA failure SG_ERR_CUDA.
+ * The first call on each device looks up the array's device address, with
+ * that device current: make that first call before any stream capture.
+ * All calls on a device share the one array, which keeps the last call's
+ * contents (each call clears what it needs first): calls whose GPU work
+ * overlaps -- from several host threads or streams -- race on it, so the
+ * caller must serialise them. */
+#define SG_FILTER_NOALLOC_MAX_N (1LL << 28)
+#define SG_FILTER_NOALLOC_SCRATCH_BYTES \
+  (768 + ((SG_FILTER_NOALLOC_MAX_N + 4095) / 4096) * 8)
+sg_status sg_filter_noalloc(const sg_expr* pred, const float* dev_x, int64_t n,
+                            float* dev_out, int64_t* dev_count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

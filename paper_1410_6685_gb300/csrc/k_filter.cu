@@ -9,6 +9,9 @@
 // output offset.  Kept items are packed in shared memory and written out
 // contiguously, so both the read and the write are coalesced: 4n bytes read,
 // 4m bytes written for m kept items.
+#include <cstring>
+#include <mutex>
+
 #include "sg_eval.cuh"
 
 namespace sgk {
@@ -188,5 +191,114 @@ cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& p
 }
 
 
+// ---------------------------------------------------------------------------
+// Allocation-free filter.  Some callers cannot allocate device memory: a
+// serving runtime that reserves all of HBM in its own pool at start-up and
+// forbids later allocations, a latency-critical path that cannot afford the
+// device-wide synchronisation cudaMalloc may imply, or a plugin host that
+// hands out only the input and output buffers.  For them the look-back
+// scratch of the filter lives in this fixed device array instead of memory
+// the library allocates.  Every GPU that loads the library holds the array
+// until the process exits.  There is no counterpart in the paper.
 
+static_assert(SG_FILTER_NOALLOC_SCRATCH_BYTES >=
+                  256 + sizeof(FilterHdr) +
+                      ((SG_FILTER_NOALLOC_MAX_N + kFTile - 1) / kFTile) * sizeof(unsigned long long) +
+                      256,
+              "the fixed scratch must hold the result record and the filter scratch");
+
+static __device__ __align__(256) unsigned char sg_filter_noalloc_scratch[SG_FILTER_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices];   // device address of the array, per device
+
+}  // namespace
 }  // namespace sgk
+
+extern "C" sg_status sg_filter_noalloc(const sg_expr* pred, const float* dev_x, int64_t n,
+                                       float* dev_out, int64_t* dev_count, void* stream) {
+  using namespace sgk;
+  if (!pred || n < 0 || (n > 0 && (!dev_x || !dev_out)) || !dev_count) return SG_ERR_INVALID_ARG;
+  if (n > SG_FILTER_NOALLOC_MAX_N) return SG_ERR_SHAPE;
+  // the predicate: one input slot, checked and given its stack depths here
+  if (pred->nops <= 0 || pred->nops > SG_MAX_EXPR_OPS) return SG_ERR_INVALID_ARG;
+  Prog pr;
+  memset(&pr, 0, sizeof pr);
+  int d = 0, md = 0;
+  for (int p = 0; p < pred->nops; ++p) {
+    const int op = pred->ops[p].op;
+    int need = 0, delta = 0;
+    switch (op) {
+      case SG_OP_LOAD:
+        if (pred->ops[p].arg != 0) return SG_ERR_INVALID_ARG;
+        delta = 1;
+        break;
+      case SG_OP_CONST: case SG_OP_INDEX: delta = 1; break;
+      case SG_OP_FMA: case SG_OP_SELECT: need = 3; delta = -2; break;
+      case SG_OP_NEG: case SG_OP_ABS: case SG_OP_SQRT: case SG_OP_NOT: need = 1; break;
+      case SG_OP_DUP: need = 1; delta = 1; break;
+      case SG_OP_SWAP: need = 2; break;
+      default:
+        if (op < SG_OP_ADD || op > SG_OP_INDEX) return SG_ERR_INVALID_ARG;
+        need = 2;
+        delta = -1;
+    }
+    if (d < need) return SG_ERR_INVALID_ARG;
+    pr.op[p] = (uint8_t)op;
+    pr.arg[p] = 0;
+    pr.cst[p] = pred->ops[p].value;
+    pr.depth[p] = (uint8_t)d;
+    d += delta;
+    md = d > md ? d : md;
+    if (md > SG_MAX_EXPR_DEPTH) return SG_ERR_INVALID_ARG;
+  }
+  if (d != 1) return SG_ERR_INVALID_ARG;
+  pr.nops = pred->nops;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // set-up, once per device, with that device current: the array's device
+  // address (the host-side symbol is only a stand-in, never a device pointer)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return SG_ERR_UNSUPPORTED;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, sg_filter_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return SG_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = p;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  FilterResult* res = static_cast<FilterResult*>(base);
+  void* scratch = static_cast<char*>(base) + 256;
+
+  // the array keeps the previous call's contents: clear the result record
+  // and the look-back words this call uses
+  cudaError_t e = cudaMemsetAsync(res, 0, sizeof(FilterResult), s);
+  if (e == cudaSuccess && n > 0) {
+    int64_t kernels = 0;
+    e = launch_filter(dev_x, dev_out, n, pr, md, scratch, res, s, 0, &kernels, nullptr);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dev_count, &res->count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  FilterResult h{};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h, res, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  return h.timeout ? SG_ERR_TIMEOUT : SG_OK;
+}

@@ -116,6 +116,7 @@ def _load():
         "sg_set_scheduler": [vp, i32], "sg_set_codegen": [vp, i32], "sg_plan_describe": [vp, C.c_char_p, sz, P(sz)],
         "sg_kernel_count": [vp, P(i64)], "sg_profile_enable": [vp, i32], "sg_profile_report": [vp, C.c_char_p, sz, P(sz), i32], "sg_debug_inject_sort": [vp, i32, i64, i64],
         "sg_batch_run": [vp, P(SgChain), vp, vp, i64, vp, vp, vp],
+        "sg_filter_noalloc": [P(SgExpr), vp, i64, vp, vp, vp],
     }
     for name, args in protos.items():
         f = getattr(L, name)
@@ -434,3 +435,12 @@ SG_CODEGEN_INTERPRET, SG_CODEGEN_SPECIALIZE = 0, 1
 def sg_set_codegen(ctx, g):
     _check(lib.sg_set_codegen(ctx, g), ctx)
 
+
+SG_FILTER_NOALLOC_MAX_N = 1 << 28
+
+
+def sg_filter_noalloc(pred, dev_x, n, dev_out, dev_count, stream=None):
+    """Allocation-free filter on caller-owned device buffers (no context)."""
+    e = expr(pred)
+    _check(lib.sg_filter_noalloc(C.byref(e), C.c_void_p(dev_x), n, C.c_void_p(dev_out),
+                                 C.c_void_p(dev_count), C.c_void_p(stream or 0)))
