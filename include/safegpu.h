@@ -400,6 +400,58 @@ sg_status sg_batch_run(sg_ctx* ctx, const sg_chain* chain, const float* data,
                        int64_t* first_viol, int64_t* kept);
 
 /* ------------------------------------------------------------------------ */
+/* Schedule choice for the batched launch: a schedule is (elements per work
+ * item, CTAs per SM).  SG_SCHED_AUTOTUNE measures every candidate the first
+ * time a workload (offsets pointer, count, chain) is seen and keeps the
+ * fastest; SG_SCHED_LEARNED runs the schedule the trained 2x64 MLP cost
+ * model predicts fastest, without measuring (while no model is trained it
+ * behaves as SG_SCHED_AUTOTUNE).  Every batched run is timed with CUDA events
+ * and logged as (12 features, log microseconds); sg_sched_train fits the
+ * model to that log on the GPU with the kernels below.                      */
+#define SG_SCHED_MAX_CANDIDATES 32
+typedef struct {
+  int32_t ncand;          /* candidates measured                               */
+  int32_t best_index;     /* fastest measured (the autotuner's choice)         */
+  int32_t default_index;  /* the plain table's choice                          */
+  int32_t learned_index;  /* the model's choice, -1 when no model is trained   */
+  int64_t chunk[SG_SCHED_MAX_CANDIDATES];
+  int32_t ctas_per_sm[SG_SCHED_MAX_CANDIDATES];
+  double measured_us[SG_SCHED_MAX_CANDIDATES];
+  double predicted_us[SG_SCHED_MAX_CANDIDATES];
+} sg_sched_report;
+
+/* Runs the batch once under every candidate schedule (the outputs hold the
+ * last run's results) and reports the measured times, the plain table's,
+ * the autotuner's and the learned model's choices.  For regret studies. */
+sg_status sg_batch_report(sg_ctx* ctx, const sg_chain* chain, const float* data,
+                          const int64_t* offsets, int64_t nseg, double* sums,
+                          int64_t* first_viol, int64_t* kept, sg_sched_report* out);
+/* Trains the cost model on the context's log (at least 8 records): features
+ * and targets standardised, minibatches of up to 512, Adam(lr), `epochs`
+ * passes, initial weights from `seed`.  *final_loss: mean squared error on
+ * the standardised log-time. */
+sg_status sg_sched_train(sg_ctx* ctx, int32_t epochs, float lr, uint64_t seed,
+                         float* final_loss);
+sg_status sg_sched_log_size(sg_ctx* ctx, int64_t* records, int32_t* features);
+sg_status sg_sched_log_read(sg_ctx* ctx, float* features, float* log_us,
+                            int64_t records);
+
+/* The cost model's network on caller device buffers (binary32), stream of
+ * ctx: yhat = W3 relu(W2 relu(W1 x + b1) + b2) + b3, hidden width 64, flat
+ * parameters [W1 (64 x d_in), b1, W2 (64 x 64), b2, W3 (64), b3];
+ * loss = mean (yhat - y)^2, gradient in the same layout; Adam with bias
+ * correction at step `step` (1-based).  X is B x d_in row-major, 1 <= d_in
+ * <= 32.  The calls wait for the stream. */
+sg_status sg_mlp_forward(sg_ctx* ctx, const float* params, int32_t d_in,
+                         const float* X, int64_t B, float* yhat);
+sg_status sg_mlp_loss_grad(sg_ctx* ctx, const float* params, int32_t d_in,
+                           const float* X, const float* y, int64_t B,
+                           float* grad, float* loss);
+sg_status sg_mlp_adam(sg_ctx* ctx, float* params, const float* grad, float* m,
+                      float* v, int64_t nparams, int64_t step, float lr,
+                      float beta1, float beta2, float eps);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free filter (the paper has no counterpart).  Some callers
  * cannot allocate device memory: a serving runtime that reserves all of HBM
  * in its own pool at start-up and forbids later allocations, a

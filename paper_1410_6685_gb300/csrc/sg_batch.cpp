@@ -1,8 +1,10 @@
 // sg_batch.cpp -- sg_batch_run: the batched-collections chain, captured once
-// into a CUDA graph per (chain, pointers, sizes, schedule) and replayed.
+// into a CUDA graph per (chain, pointers, sizes, schedule) and replayed, with
+// the schedule from the plain table, the autotuner or the learned model.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
 
@@ -41,46 +43,70 @@ bool expr_ok(const sg_expr& e) {
   return d == 1;
 }
 
-}  // namespace
-
-BatchPlanCache::~BatchPlanCache() {
-  for (auto& kv : plans) {
-    BatchPlan& p = kv.second;
-    if (p.exec) cudaGraphExecDestroy(p.exec);
-    if (p.scratch) cudaFree(p.scratch);
-    if (p.host_flag) cudaFreeHost(p.host_flag);
-  }
-  if (capture_stream) cudaStreamDestroy(capture_stream);
+uint64_t chain_hash(const sg_chain& ch) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(&ch);
+  uint64_t h = 1469598103934665603ull;   // FNV-1a
+  for (size_t i = 0; i < sizeof ch; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
 }
 
-extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* data,
-                                  const int64_t* offsets, int64_t nseg, double* sums,
-                                  int64_t* first_viol, int64_t* kept) {
-  if (!c || !ch || nseg < 0) return bad(c, SG_ERR_INVALID_ARG, "bad batch arguments");
-  if (c->planning_only) return bad(c, SG_ERR_UNSUPPORTED, "planning-only context");
-  if (nseg > 0 && (!data || !offsets || !sums || !first_viol || !kept))
-    return bad(c, SG_ERR_INVALID_ARG, "null device pointer");
-  if (!expr_ok(ch->map) || !expr_ok(ch->pre) || !expr_ok(ch->keep))
-    return bad(c, SG_ERR_INVALID_ARG, "chain expressions must be 1-input programs");
-  if (nseg == 0) return SG_OK;
+struct Job {
+  const sg_chain* ch;
+  const float* data;
+  const int64_t* offsets;
+  int64_t nseg;
+  double* sums;
+  int64_t* first;
+  int64_t* kept;
   sgk::Prog prog;
-  int depth = 0;
-  if (!sgk::build_chain_prog(*ch, &prog, &depth))
-    return bad(c, SG_ERR_INVALID_ARG, "chain program too long or too deep");
+  int depth;
+  BatchStats stats;
+};
 
-  // everything queued before runs first (same stream order as a flush)
-  sg_status st = sg_flush(c);
-  if (st && st != SG_ERR_PRECONDITION && st != SG_ERR_POSTCONDITION) return st;
+sg_status read_stats(sg_ctx* c, Job& j) {
+  std::vector<int64_t> off(j.nseg + 1);
+  cudaError_t e = cudaMemcpyAsync(off.data(), j.offsets, off.size() * 8, cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bad(c, SG_ERR_CUDA, cudaGetErrorString(e));
+  }
+  BatchStats& w = j.stats;
+  w.nseg = j.nseg;
+  w.total = off[j.nseg] - off[0];
+  double s = 0, s2 = 0, mn = 1e300, mx = -1e300;
+  for (int64_t i = 0; i < j.nseg; ++i) {
+    const int64_t L = off[i + 1] - off[i];
+    if (L < 0) return bad(c, SG_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    const double l = std::log2((double)L + 1.0);
+    s += l;
+    s2 += l * l;
+    mn = std::min(mn, l);
+    mx = std::max(mx, l);
+  }
+  w.mean_log = s / (double)j.nseg;
+  w.std_log = std::sqrt(std::max(0.0, s2 / (double)j.nseg - w.mean_log * w.mean_log));
+  w.min_log = mn;
+  w.max_log = mx;
+  w.ops = j.prog.nops;
+  w.depth = j.depth;
+  return SG_OK;
+}
 
-  const sg_sched_choice sch = sg_choose_batch_schedule(c, nseg, depth);
+// Runs the batch once with schedule `sch` (capturing its graph on first use),
+// times it with CUDA events, logs it.  *violated: a precondition failed.
+sg_status run_with(sg_ctx* c, const Job& j, const sg_sched_choice& sch, double* us,
+                   bool* violated) {
   BatchKey key;
-  memcpy(&key.chain, ch, sizeof *ch);
-  key.data = data;
-  key.offsets = offsets;
-  key.nseg = nseg;
-  key.sums = sums;
-  key.first = first_viol;
-  key.kept = kept;
+  memset(&key, 0, sizeof key);
+  memcpy(&key.chain, j.ch, sizeof *j.ch);
+  key.data = j.data;
+  key.offsets = j.offsets;
+  key.nseg = j.nseg;
+  key.sums = j.sums;
+  key.first = j.first;
+  key.kept = j.kept;
   key.chunk = sch.chunk;
   key.grid_per_sm = sch.blocks_per_sm;
   BatchPlanCache& cache = c->batch;
@@ -90,44 +116,40 @@ extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* da
       return bad(c, SG_ERR_CUDA, "capture stream creation failed");
     }
   }
+  if (!cache.ev[0]) {
+    cudaEventCreate(&cache.ev[0]);
+    cudaEventCreate(&cache.ev[1]);
+  }
   for (int attempt = 0; attempt < 3; ++attempt) {
     BatchPlan* plan = nullptr;
     for (auto& kv : cache.plans)
       if (memcmp(&kv.first, &key, sizeof key) == 0) plan = &kv.second;
     if (!plan) {
-      // capacity: one chunk per collection plus the chunks the elements need
-      // (the total is read once; the kernel reports an overflow if the
-      // offsets change under the same pointers)
-      int64_t total = 0;
-      cudaError_t e = cudaMemcpyAsync(&total, offsets + nseg, sizeof total,
-                                      cudaMemcpyDeviceToHost, c->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-      if (e != cudaSuccess) return bad(c, SG_ERR_CUDA, cudaGetErrorString(e));
       BatchPlan p;
-      p.capacity = nseg + total / sch.chunk + 1 + (attempt ? 2 * nseg : 0);
-      if (cudaMalloc(&p.scratch, sgk::batch_scratch_bytes(nseg, p.capacity)) != cudaSuccess ||
+      p.capacity = j.nseg + j.stats.total / sch.chunk + 1 + (attempt ? 4 * j.nseg + 1024 : 0);
+      if (cudaMalloc(&p.scratch, sgk::batch_scratch_bytes(j.nseg, p.capacity)) != cudaSuccess ||
           cudaMallocHost((void**)&p.host_flag, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         return bad(c, SG_ERR_OOM, "batch scratch allocation failed");
       }
       // the per-collection counters start at zero and return to zero
-      cudaMemset(p.scratch, 0, sgk::batch_scratch_bytes(nseg, p.capacity));
+      cudaMemset(p.scratch, 0, sgk::batch_scratch_bytes(j.nseg, p.capacity));
       sgk::BatchLaunch L{};
-      L.data = data;
-      L.offsets = reinterpret_cast<const long long*>(offsets);
-      L.nseg = nseg;
+      L.data = j.data;
+      L.offsets = reinterpret_cast<const long long*>(j.offsets);
+      L.nseg = j.nseg;
       L.chunk = sch.chunk;
       L.capacity = p.capacity;
       L.grid = std::max(1, c->num_sms * sch.blocks_per_sm);
-      L.prog = prog;
-      L.depth = depth;
+      L.prog = j.prog;
+      L.depth = j.depth;
       L.scratch = p.scratch;
-      L.sums = sums;
-      L.first_viol = reinterpret_cast<long long*>(first_viol);
-      L.kept = reinterpret_cast<long long*>(kept);
+      L.sums = j.sums;
+      L.first_viol = reinterpret_cast<long long*>(j.first);
+      L.kept = reinterpret_cast<long long*>(j.kept);
       L.host_flag = p.host_flag;
       cudaGraph_t g = nullptr;
-      e = cudaStreamBeginCapture(cache.capture_stream, cudaStreamCaptureModeThreadLocal);
+      cudaError_t e = cudaStreamBeginCapture(cache.capture_stream, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
         cudaError_t le = sgk::launch_batch(L, cache.capture_stream, nullptr);
         e = cudaStreamEndCapture(cache.capture_stream, &g);
@@ -146,15 +168,19 @@ extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* da
     }
     const bool prof = c->prof.on;
     if (prof) sgk::prof_begin(&c->prof, "batch_graph", c->stream);
+    cudaEventRecord(cache.ev[0], c->stream);
     cudaError_t e = cudaGraphLaunch(plan->exec, c->stream);
+    cudaEventRecord(cache.ev[1], c->stream);
     if (prof) sgk::prof_end(&c->prof, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bad(c, SG_ERR_CUDA, cudaGetErrorString(e));
     if (prof) c->prof.collect();
     c->kernels += 2;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, cache.ev[0], cache.ev[1]);
     const unsigned flag = *plan->host_flag;
     if (flag & 2u) {
-      // offsets changed under the same pointers: rebuild with more room
+      // the offsets changed under the same pointers: rebuild with more room
       cudaGraphExecDestroy(plan->exec);
       cudaFree(plan->scratch);
       cudaFreeHost(plan->host_flag);
@@ -165,12 +191,169 @@ extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* da
         }
       continue;
     }
-    sg_record_batch_timing(c, nseg, sch);
-    if (flag & 1u) {
-      c->err = "a collection violated the batch precondition";
-      return SG_ERR_PRECONDITION;
-    }
+    float f[kSchedFeatures];
+    sg_batch_features(j.stats, sch, c->num_sms, f);
+    sg_sched_log_add(c, f, ms * 1000.0);
+    if (us) *us = ms * 1000.0;
+    *violated = (flag & 1u) != 0;
     return SG_OK;
   }
   return bad(c, SG_ERR_CUDA, "batch work list overflowed twice");
+}
+
+sg_status prepare(sg_ctx* c, const sg_chain* ch, const float* data, const int64_t* offsets,
+                  int64_t nseg, double* sums, int64_t* first, int64_t* kept, Job* j) {
+  if (!c || !ch || nseg < 0) return bad(c, SG_ERR_INVALID_ARG, "bad batch arguments");
+  if (c->planning_only) return bad(c, SG_ERR_UNSUPPORTED, "planning-only context");
+  if (nseg > 0 && (!data || !offsets || !sums || !first || !kept))
+    return bad(c, SG_ERR_INVALID_ARG, "null device pointer");
+  if (!expr_ok(ch->map) || !expr_ok(ch->pre) || !expr_ok(ch->keep))
+    return bad(c, SG_ERR_INVALID_ARG, "chain expressions must be 1-input programs");
+  j->ch = ch;
+  j->data = data;
+  j->offsets = offsets;
+  j->nseg = nseg;
+  j->sums = sums;
+  j->first = first;
+  j->kept = kept;
+  if (!sgk::build_chain_prog(*ch, &j->prog, &j->depth))
+    return bad(c, SG_ERR_INVALID_ARG, "chain program too long or too deep");
+  if (nseg == 0) return SG_OK;
+  // everything queued before runs first (same stream order as a flush)
+  sg_status st = sg_flush(c);
+  if (st && st != SG_ERR_PRECONDITION && st != SG_ERR_POSTCONDITION) return st;
+  return read_stats(c, *j);
+}
+
+// Autotune: measure every candidate (each twice, the second run counts).
+sg_status autotune(sg_ctx* c, const Job& j, std::vector<double>* times, int* best) {
+  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.depth);
+  times->assign(cand.size(), 0.0);
+  double bt = 1e300;
+  *best = 0;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    bool viol = false;
+    double us = 0.0;
+    sg_status st = run_with(c, j, cand[i], &us, &viol);
+    if (!st) st = run_with(c, j, cand[i], &us, &viol);
+    if (st) return st;
+    (*times)[i] = us;
+    if (us < bt) {
+      bt = us;
+      *best = (int)i;
+    }
+  }
+  return SG_OK;
+}
+
+}  // namespace
+
+BatchPlanCache::~BatchPlanCache() {
+  for (auto& kv : plans) {
+    BatchPlan& p = kv.second;
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    if (p.scratch) cudaFree(p.scratch);
+    if (p.host_flag) cudaFreeHost(p.host_flag);
+  }
+  if (capture_stream) cudaStreamDestroy(capture_stream);
+  if (ev[0]) cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+}
+
+extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* data,
+                                  const int64_t* offsets, int64_t nseg, double* sums,
+                                  int64_t* first_viol, int64_t* kept) {
+  Job j;
+  sg_status st = prepare(c, ch, data, offsets, nseg, sums, first_viol, kept, &j);
+  if (st || nseg == 0) return st;
+  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.depth);
+  sg_sched_choice pick = sg_batch_default(j.depth);
+  bool chosen = false;
+  if (c->sched == SG_SCHED_LEARNED) {
+    std::vector<float> pred;
+    if (sg_sched_predict(c, j.stats, cand, &pred)) {
+      pick = cand[std::min_element(pred.begin(), pred.end()) - pred.begin()];
+      chosen = true;
+    }
+  }
+  if (!chosen) {
+    // the autotuned table (measured once per workload and chain)
+    auto wkey = std::make_pair((const void*)offsets, (long long)nseg);
+    const uint64_t h = chain_hash(*ch);
+    int idx = -1;
+    for (auto& t : c->schedst.tuned)
+      if (t.first == wkey && t.second.first == h) idx = t.second.second;
+    if (idx < 0) {
+      std::vector<double> times;
+      st = autotune(c, j, &times, &idx);
+      if (st) return st;
+      c->schedst.tuned.push_back({wkey, {h, idx}});
+    }
+    pick = cand[idx];
+  }
+  bool viol = false;
+  st = run_with(c, j, pick, nullptr, &viol);
+  if (st) return st;
+  if (viol) {
+    c->err = "a collection violated the batch precondition";
+    return SG_ERR_PRECONDITION;
+  }
+  return SG_OK;
+}
+
+extern "C" sg_status sg_batch_report(sg_ctx* c, const sg_chain* ch, const float* data,
+                                     const int64_t* offsets, int64_t nseg, double* sums,
+                                     int64_t* first_viol, int64_t* kept, sg_sched_report* out) {
+  if (!out) return bad(c, SG_ERR_INVALID_ARG, "null report");
+  Job j;
+  sg_status st = prepare(c, ch, data, offsets, nseg, sums, first_viol, kept, &j);
+  if (st) return st;
+  if (nseg == 0) return bad(c, SG_ERR_INVALID_ARG, "empty batch");
+  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.depth);
+  memset(out, 0, sizeof *out);
+  out->ncand = (int32_t)std::min<size_t>(cand.size(), SG_SCHED_MAX_CANDIDATES);
+  std::vector<double> times;
+  int best = 0;
+  st = autotune(c, j, &times, &best);
+  if (st) return st;
+  const sg_sched_choice def = sg_batch_default(j.depth);
+  out->default_index = -1;
+  for (int i = 0; i < out->ncand; ++i) {
+    out->chunk[i] = cand[i].chunk;
+    out->ctas_per_sm[i] = cand[i].blocks_per_sm;
+    out->measured_us[i] = times[i];
+    if (cand[i].chunk == def.chunk && cand[i].blocks_per_sm == def.blocks_per_sm)
+      out->default_index = i;
+  }
+  out->best_index = best;
+  out->learned_index = -1;
+  std::vector<float> pred;
+  if (sg_sched_predict(c, j.stats, cand, &pred)) {
+    out->learned_index = (int32_t)(std::min_element(pred.begin(), pred.end()) - pred.begin());
+    for (int i = 0; i < out->ncand; ++i)
+      out->predicted_us[i] = std::exp((double)pred[i] * c->schedst.ysd + c->schedst.ymu);
+  }
+  return SG_OK;
+}
+
+extern "C" sg_status sg_sched_train(sg_ctx* c, int32_t epochs, float lr, uint64_t seed,
+                                    float* final_loss) {
+  if (!c || epochs <= 0 || !(lr > 0.0f)) return bad(c, SG_ERR_INVALID_ARG, "bad training arguments");
+  if (c->planning_only) return bad(c, SG_ERR_UNSUPPORTED, "planning-only context");
+  return sg_sched_train_impl(c, epochs, lr, seed, final_loss);
+}
+
+extern "C" sg_status sg_sched_log_size(sg_ctx* c, int64_t* records, int32_t* features) {
+  if (!c || !records || !features) return SG_ERR_INVALID_ARG;
+  *records = (int64_t)c->schedst.log_y.size();
+  *features = kSchedFeatures;
+  return SG_OK;
+}
+
+extern "C" sg_status sg_sched_log_read(sg_ctx* c, float* features, float* log_us, int64_t records) {
+  if (!c || records < 0 || records > (int64_t)c->schedst.log_y.size()) return SG_ERR_INVALID_ARG;
+  if (records && (!features || !log_us)) return SG_ERR_INVALID_ARG;
+  memcpy(features, c->schedst.log_x.data(), (size_t)records * kSchedFeatures * 4);
+  memcpy(log_us, c->schedst.log_y.data(), (size_t)records * 4);
+  return SG_OK;
 }

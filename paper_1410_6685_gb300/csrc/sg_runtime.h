@@ -97,7 +97,25 @@ struct BatchPlan {
 struct BatchPlanCache {
   std::vector<std::pair<BatchKey, BatchPlan>> plans;
   cudaStream_t capture_stream = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};   // timing of each batched run
   ~BatchPlanCache();
+};
+
+// Timing log and learned cost model of the schedule chooser.
+constexpr int kSchedFeatures = 12;
+constexpr int kSchedMaxCand = 64;
+struct SchedState {
+  std::vector<float> log_x;   // records x kSchedFeatures
+  std::vector<float> log_y;   // log microseconds
+  bool trained = false;
+  std::vector<float> mu, sd;  // feature normalisation
+  float ymu = 0.0f, ysd = 1.0f;
+  void* dev = nullptr;        // params, grads, Adam moments, data (device)
+  float* params = nullptr;
+  float* pred = nullptr;
+  // autotuned choices: (offsets, nseg, chain hash) -> candidate index
+  std::vector<std::pair<std::pair<const void*, long long>, std::pair<uint64_t, int>>> tuned;
+  ~SchedState();
 };
 
 struct sg_ctx {
@@ -125,6 +143,7 @@ struct sg_ctx {
   sgk::SortInject inject{};            // contract-test fault for the next sort
   sgk::Prof prof;                      // per-kernel event tracing
   BatchPlanCache batch;                // captured batched launches
+  SchedState schedst;                  // schedule log and cost model
 };
 
 struct sg_vector {

@@ -1,7 +1,8 @@
-// sg_sched.h -- schedule choice for launch shapes: the autotuned plain table
-// or the learned cost model (sg_set_scheduler).  Internal.
+// sg_sched.h -- schedule choice for launch shapes: the plain table, the
+// autotuner and the learned cost model (sg_set_scheduler).  Internal.
 #pragma once
 #include <cstdint>
+#include <vector>
 
 #include "sg_runtime.h"
 
@@ -10,5 +11,17 @@ struct sg_sched_choice {
   int blocks_per_sm;    // persistent CTAs per SM
 };
 
-sg_sched_choice sg_choose_batch_schedule(sg_ctx* c, int64_t nseg, int depth);
-void sg_record_batch_timing(sg_ctx* c, int64_t nseg, const sg_sched_choice& ch);
+// Length statistics of a batched workload (from its offsets) and program size
+struct BatchStats {
+  long long nseg = 0, total = 0;
+  double mean_log = 0, std_log = 0, min_log = 0, max_log = 0;
+  int ops = 0, depth = 0;
+};
+
+std::vector<sg_sched_choice> sg_batch_candidates(int depth);
+sg_sched_choice sg_batch_default(int depth);
+void sg_batch_features(const BatchStats& w, const sg_sched_choice& ch, int num_sms, float* f);
+void sg_sched_log_add(sg_ctx* c, const float* f, double us);
+sg_status sg_sched_train_impl(sg_ctx* c, int epochs, float lr, uint64_t seed, float* final_loss);
+bool sg_sched_predict(sg_ctx* c, const BatchStats& w, const std::vector<sg_sched_choice>& cand,
+                      std::vector<float>* pred);

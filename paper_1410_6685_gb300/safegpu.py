@@ -71,6 +71,17 @@ class SgSolveInfo(C.Structure):
                 ("last_correction", C.c_double)]
 
 
+SG_SCHED_MAX_CANDIDATES = 32
+
+
+class SgSchedReport(C.Structure):
+    _fields_ = [("ncand", C.c_int32), ("best_index", C.c_int32), ("default_index", C.c_int32),
+                ("learned_index", C.c_int32), ("chunk", C.c_int64 * SG_SCHED_MAX_CANDIDATES),
+                ("ctas_per_sm", C.c_int32 * SG_SCHED_MAX_CANDIDATES),
+                ("measured_us", C.c_double * SG_SCHED_MAX_CANDIDATES),
+                ("predicted_us", C.c_double * SG_SCHED_MAX_CANDIDATES)]
+
+
 class SgChain(C.Structure):
     _fields_ = [("map", SgExpr), ("pre", SgExpr), ("keep", SgExpr)]
 
@@ -117,6 +128,13 @@ def _load():
         "sg_kernel_count": [vp, P(i64)], "sg_profile_enable": [vp, i32], "sg_profile_report": [vp, C.c_char_p, sz, P(sz), i32], "sg_debug_inject_sort": [vp, i32, i64, i64],
         "sg_batch_run": [vp, P(SgChain), vp, vp, i64, vp, vp, vp],
         "sg_filter_noalloc": [P(SgExpr), vp, i64, vp, vp, vp],
+        "sg_batch_report": [vp, P(SgChain), vp, vp, i64, vp, vp, vp, P(SgSchedReport)],
+        "sg_sched_train": [vp, i32, C.c_float, C.c_uint64, P(C.c_float)],
+        "sg_sched_log_size": [vp, P(i64), P(C.c_int32)],
+        "sg_sched_log_read": [vp, vp, vp, i64],
+        "sg_mlp_forward": [vp, vp, i32, vp, i64, vp],
+        "sg_mlp_loss_grad": [vp, vp, i32, vp, vp, i64, vp, vp],
+        "sg_mlp_adam": [vp, vp, vp, vp, vp, i64, i64, C.c_float, C.c_float, C.c_float, C.c_float],
     }
     for name, args in protos.items():
         f = getattr(L, name)
@@ -444,3 +462,46 @@ def sg_filter_noalloc(pred, dev_x, n, dev_out, dev_count, stream=None):
     e = expr(pred)
     _check(lib.sg_filter_noalloc(C.byref(e), C.c_void_p(dev_x), n, C.c_void_p(dev_out),
                                  C.c_void_p(dev_count), C.c_void_p(stream or 0)))
+
+
+def sg_batch_report(ctx, chain: SgChain, data_ptr, offsets_ptr, nseg, sums_ptr, first_ptr,
+                    kept_ptr) -> SgSchedReport:
+    r = SgSchedReport()
+    _check(lib.sg_batch_report(ctx, C.byref(chain), C.c_void_p(data_ptr), C.c_void_p(offsets_ptr),
+                               nseg, C.c_void_p(sums_ptr), C.c_void_p(first_ptr),
+                               C.c_void_p(kept_ptr), C.byref(r)), ctx)
+    return r
+
+
+def sg_sched_train(ctx, epochs=200, lr=1e-3, seed=1) -> float:
+    loss = C.c_float()
+    _check(lib.sg_sched_train(ctx, epochs, lr, seed, C.byref(loss)), ctx)
+    return loss.value
+
+
+def sg_sched_log(ctx):
+    import numpy as np
+    n, d = C.c_int64(), C.c_int32()
+    _check(lib.sg_sched_log_size(ctx, C.byref(n), C.byref(d)), ctx)
+    X = np.empty((n.value, d.value), np.float32)
+    y = np.empty(n.value, np.float32)
+    _check(lib.sg_sched_log_read(ctx, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data),
+                                 n.value), ctx)
+    return X, y
+
+
+def sg_mlp_forward(ctx, p_ptr, d_in, x_ptr, B, yhat_ptr):
+    _check(lib.sg_mlp_forward(ctx, C.c_void_p(p_ptr), d_in, C.c_void_p(x_ptr), B,
+                              C.c_void_p(yhat_ptr)), ctx)
+
+
+def sg_mlp_loss_grad(ctx, p_ptr, d_in, x_ptr, y_ptr, B, g_ptr, loss_ptr):
+    _check(lib.sg_mlp_loss_grad(ctx, C.c_void_p(p_ptr), d_in, C.c_void_p(x_ptr),
+                                C.c_void_p(y_ptr), B, C.c_void_p(g_ptr),
+                                C.c_void_p(loss_ptr)), ctx)
+
+
+def sg_mlp_adam(ctx, p_ptr, g_ptr, m_ptr, v_ptr, nparams, step, lr=1e-3, b1=0.9, b2=0.999,
+                eps=1e-8):
+    _check(lib.sg_mlp_adam(ctx, C.c_void_p(p_ptr), C.c_void_p(g_ptr), C.c_void_p(m_ptr),
+                           C.c_void_p(v_ptr), nparams, step, lr, b1, b2, eps), ctx)

@@ -1,0 +1,131 @@
+"""GPU tests of the learned schedule chooser: the 2x64 MLP's forward,
+backward and Adam kernels against the binary64 oracle, and what the trained
+cost model gains over the plain schedule table on held-out batched workloads
+(regret = measured time of the chosen schedule / fastest measured - 1)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_6685_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+D_IN = 12
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1410_6685_gb300 import safegpu as sg
+    ctx = sg.sg_init(0, torch.cuda.current_stream().cuda_stream)
+    yield sg, ctx, torch
+    sg.sg_destroy(ctx)
+
+
+def dev(torch, a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).cuda()
+
+
+def test_forward_and_gradient_vs_oracle(env):
+    sg, ctx, torch = env
+    g = np.random.default_rng(1)
+    P = inputs.mlp_init(D_IN, 64, seed=4)
+    B = 300
+    X = g.standard_normal((B, D_IN))
+    y = g.standard_normal(B)
+    P32, X32, y32 = (x.astype(np.float32) for x in (P, X, y))
+    tP, tX, ty = dev(torch, P32, np.float32), dev(torch, X32, np.float32), dev(torch, y32, np.float32)
+    yhat = torch.empty(B, device="cuda")
+    sg.sg_mlp_forward(ctx, tP.data_ptr(), D_IN, tX.data_ptr(), B, yhat.data_ptr())
+    ref = oracle.mlp_forward(P32.astype(np.float64), X32.astype(np.float64), D_IN)
+    assert np.max(np.abs(yhat.cpu().numpy() - ref)) <= 1e-5 * (1 + np.max(np.abs(ref)))
+    G = torch.empty(len(P), device="cuda")
+    loss = torch.empty(1, device="cuda")
+    sg.sg_mlp_loss_grad(ctx, tP.data_ptr(), D_IN, tX.data_ptr(), ty.data_ptr(), B, G.data_ptr(),
+                        loss.data_ptr())
+    rl, rG = oracle.mlp_loss_grad(P32.astype(np.float64), X32.astype(np.float64),
+                                  y32.astype(np.float64), D_IN)
+    assert abs(loss.item() - rl) <= 1e-5 * rl
+    Gg = G.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(Gg - rG) <= 1e-4 * np.linalg.norm(rG)
+
+
+def test_adam_step_vs_oracle(env):
+    sg, ctx, torch = env
+    g = np.random.default_rng(2)
+    n = 1000
+    P = g.standard_normal(n)
+    G = g.standard_normal(n)
+    m = g.standard_normal(n) * 0.1
+    v = np.abs(g.standard_normal(n)) * 0.1
+    tP, tG, tm, tv = (dev(torch, x, np.float32) for x in (P, G, m, v))
+    sg.sg_mlp_adam(ctx, tP.data_ptr(), tG.data_ptr(), tm.data_ptr(), tv.data_ptr(), n, 7, lr=1e-2)
+    P64, G64, m64, v64 = (x.astype(np.float32).astype(np.float64) for x in (P, G, m, v))
+    oracle.adam_step(P64, G64, m64, v64, 7, lr=1e-2)
+    assert np.max(np.abs(tP.cpu().numpy() - P64)) <= 1e-6 * (1 + np.max(np.abs(P64)))
+    assert np.max(np.abs(tm.cpu().numpy() - m64)) <= 1e-6
+    assert np.max(np.abs(tv.cpu().numpy() - v64)) <= 1e-6
+
+
+def make_workload(torch, rng, nseg, lo, hi):
+    u = rng.random(nseg)
+    L = np.floor(2.0 ** (lo + (hi - lo) * u)).astype(np.int64)
+    off = inputs.batch_offsets(L)
+    total = int(off[-1])
+    x = torch.rand(max(total, 1), device="cuda") * 2 - 1
+    to = torch.from_numpy(off).cuda()
+    outs = (torch.empty(nseg, dtype=torch.float64, device="cuda"),
+            torch.empty(nseg, dtype=torch.int64, device="cuda"),
+            torch.empty(nseg, dtype=torch.int64, device="cuda"))
+    return x, to, outs, nseg
+
+
+def test_learned_schedule_gain_over_plain_table(env):
+    sg, ctx, torch = env
+    chain = sg.chain([("x", 0), ("x", 0), ("c", 1.0), ("fma",)], [("x", 0), ("c", 1.0), ("ge",)],
+                     [("x", 0), ("c", 1.5), ("gt",)])
+    rng = np.random.default_rng(12)
+
+    def spec(r):
+        lo = int(r.integers(4, 9))
+        hi = int(r.integers(lo + 2, 19))
+        nseg = int(r.integers(100, 3000))
+        while nseg * 2.0 ** ((lo + hi) / 2) > 2.5e7:
+            nseg //= 2
+        return max(nseg, 16), lo, hi
+
+    # training: the autotuner measures every candidate of each workload
+    sg.sg_set_scheduler(ctx, sg.SG_SCHED_AUTOTUNE)
+    for _ in range(28):
+        x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
+        sg.sg_batch_run(ctx, chain, x.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
+    Xlog, ylog = sg.sg_sched_log(ctx)
+    assert len(ylog) >= 28 * 2 * 8
+    loss = sg.sg_sched_train(ctx, epochs=400, lr=3e-3, seed=7)
+    assert loss < 0.5          # standardised log-time: well below the variance (1.0)
+    # held-out workloads
+    reg_l, reg_d = [], []
+    for _ in range(8):
+        x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
+        r = sg.sg_batch_report(ctx, chain, x.data_ptr(), to.data_ptr(), nseg,
+                               *(t.data_ptr() for t in outs))
+        t = np.array(r.measured_us[:r.ncand])
+        best = t.min()
+        assert r.learned_index >= 0 and r.default_index >= 0
+        reg_l.append(t[r.learned_index] / best - 1)
+        reg_d.append(t[r.default_index] / best - 1)
+    ml, md = float(np.mean(reg_l)), float(np.mean(reg_d))
+    print("\nmean regret learned %.3f, plain table %.3f, per workload learned %s plain %s"
+          % (ml, md, np.round(reg_l, 3).tolist(), np.round(reg_d, 3).tolist()))
+    assert ml <= md + 0.05
+    assert ml <= 0.30
+    # the learned chooser runs once, without measuring candidates
+    sg.sg_set_scheduler(ctx, sg.SG_SCHED_LEARNED)
+    x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
+    k0 = sg.sg_kernel_count(ctx)
+    sg.sg_batch_run(ctx, chain, x.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
+    assert sg.sg_kernel_count(ctx) - k0 <= 2 + 1
+    sg.sg_set_scheduler(ctx, sg.SG_SCHED_AUTOTUNE)
