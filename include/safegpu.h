@@ -281,7 +281,7 @@ typedef struct {
   void* other[3];        /* sg_vector* (or sg_matrix* for FREIVALDS,
                             RESIDUAL's A)                                 */
   uint64_t seed;         /* FREIVALDS: Rademacher stream seed             */
-  int32_t nvec;          /* FREIVALDS: number of vectors (default 4)      */
+  int32_t nvec;          /* FREIVALDS: number of vectors, 1..4 (0 = 4)    */
   double tol;            /* FREIVALDS: c in tau = c u sigma (default 8);
                             RESIDUAL: bound (default 1e-12)               */
 } sg_contract;

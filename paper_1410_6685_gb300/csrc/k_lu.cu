@@ -38,37 +38,17 @@ constexpr int kPT = 256;      // threads per CTA
 constexpr int kStride = kPB + 1;
 constexpr unsigned kSpin = 1u << 24;
 
-__device__ __forceinline__ unsigned long long key_of(float v, int pos) {
-  // larger |v| wins, then the lower position; NaN sorts above everything
-  return ((unsigned long long)__float_as_uint(fabsf(v)) << 32) | (0xFFFFFFFFu - (unsigned)pos);
+// Pivot candidate: larger |v| wins, then the lower current position; the
+// low 16 bits carry the candidate's row within the panel so one 64-bit max
+// says who won.  NaN magnitudes sort above everything.
+__device__ __forceinline__ unsigned long long key_of(float v, int pos, int row) {
+  return ((unsigned long long)__float_as_uint(fabsf(v)) << 32) |
+         ((unsigned long long)(0xFFFFu - (unsigned)pos) << 16) | (unsigned)row;
 }
 
-__device__ __forceinline__ unsigned long long block_max(unsigned long long v,
-                                                        unsigned long long* sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
-    v = u > v ? u : v;
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    v = lane < kPT / 32 ? sh[lane] : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
-      v = u > v ? u : v;
-    }
-    if (lane == 0) sh[0] = v;
-  }
-  __syncthreads();
-  return sh[0];
-}
+constexpr int kMaxRowsPerThread = 5;   // ceil(ceil(9216 / 8) / 256)
 
-// smem: slab[rs][33] floats, pos[m] ints, inv[m] ints, cand[2][8] u64,
-// prow[32] floats, red[8] u64
+// smem: slab[rs][33] floats, cand[2][8] u64, best[2] u64, prow[32] floats
 __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     k_lu_panel(float* __restrict__ LU, int n, int k, int jb, int* __restrict__ piv,
                int* __restrict__ info) {
@@ -80,68 +60,74 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
   const int r0 = rank * rs;
   const int r1 = min(m, r0 + rs);
   float* slab = reinterpret_cast<float*>(smem);
-  int* pos = reinterpret_cast<int*>(slab + (size_t)rs * kStride);
-  int* inv = pos + m;
   unsigned long long* cand = reinterpret_cast<unsigned long long*>(
-      (reinterpret_cast<uintptr_t>(inv + m) + 15) & ~(uintptr_t)15);
-  float* prow = reinterpret_cast<float*>(cand + 2 * kPC);
-  unsigned long long* red = reinterpret_cast<unsigned long long*>(prow + kPB);
+      (reinterpret_cast<uintptr_t>(slab + (size_t)rs * kStride) + 15) & ~(uintptr_t)15);
+  unsigned long long* best = cand + 2 * kPC;
+  float* prow = reinterpret_cast<float*>(best + 2);
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
 
-  // load my rows of the panel, initialise the position tables
+  // my rows: r = r0 + tid + i*kPT; their current positions live in registers
+  int lp[kMaxRowsPerThread];
+#pragma unroll
+  for (int i = 0; i < kMaxRowsPerThread; ++i) lp[i] = r0 + tid + i * kPT;
   for (int t = tid; t < (r1 - r0) * kPB; t += kPT) {
     const int r = t / kPB, c = t % kPB;
     slab[r * kStride + c] = c < jb ? LU[(size_t)(k + r0 + r) * n + k + c] : 0.0f;
   }
-  for (int i = tid; i < m; i += kPT) {
-    pos[i] = i;
-    inv[i] = i;
-  }
+  if (tid < 2) best[tid] = 0ull;
   __syncthreads();
-  // first column's candidate
-  unsigned long long best = 0ull;
-  for (int r = r0 + tid; r < r1; r += kPT) {
-    const unsigned long long kk = key_of(slab[(r - r0) * kStride], r);
-    best = kk > best ? kk : best;
+  // the first column's candidate
+  unsigned long long mine = 0ull;
+#pragma unroll
+  for (int i = 0; i < kMaxRowsPerThread; ++i) {
+    const int r = r0 + tid + i * kPT;
+    if (r < r1) {
+      const unsigned long long kk = key_of(slab[(r - r0) * kStride], lp[i], r);
+      mine = kk > mine ? kk : mine;
+    }
   }
-  best = block_max(best, red);
   int my_info = 0;
   for (int j = 0; j < jb; ++j) {
     const int par = j & 1;
-    if (tid < kPC) {
-      unsigned long long* dst = cluster.map_shared_rank(&cand[par * kPC + rank], tid);
-      *dst = best;
+    // this CTA's best candidate for column j
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, mine, o);
+      mine = u > mine ? u : mine;
     }
+    if (lane == 0 && mine) atomicMax(&best[par], mine);
+    __syncthreads();
+    if (tid < kPC) *cluster.map_shared_rank(&cand[par * kPC + rank], tid) = best[par];
+    if (tid == kPC) best[par ^ 1] = 0ull;   // next column's slot (its last reader is done)
     cluster.sync();
     unsigned long long g = 0ull;
 #pragma unroll
     for (int q = 0; q < kPC; ++q) g = cand[par * kPC + q] > g ? cand[par * kPC + q] : g;
-    const int p = (int)(0xFFFFFFFFu - (unsigned)(g & 0xFFFFFFFFull));   // position
-    const int gp = pos[p];                                               // physical row
+    const int p = (int)(0xFFFFu - (unsigned)((g >> 16) & 0xFFFFu));   // winning position
+    const int gp = (int)(g & 0xFFFFu);                                // its row in the panel
     const int owner = gp / rs;
-    // read the pivot row (columns j..jb-1) from its owner's shared memory
     if (tid < kPB) {
       const float* src = cluster.map_shared_rank(slab, owner);
       prow[tid] = (tid >= j && tid < jb) ? src[(gp - owner * rs) * kStride + tid] : 0.0f;
     }
-    // replicated interchange of positions j and p
-    __syncthreads();
-    if (tid == 0) {
-      const int gj = pos[j];
-      pos[j] = gp;
-      pos[p] = gj;
-      inv[gp] = j;
-      inv[gj] = p;
+    // interchange of positions j and p (each thread for its own rows)
+#pragma unroll
+    for (int i = 0; i < kMaxRowsPerThread; ++i) {
+      const int r = r0 + tid + i * kPT;
+      if (lp[i] == j) lp[i] = p;
+      if (r == gp) lp[i] = j;
     }
     __syncthreads();
     const float d = prow[j];
     const bool zero = d == 0.0f;
     if (zero && my_info == 0) my_info = k + j + 1;
     // eliminate below the pivot; find the next column's candidate
-    best = 0ull;
-    for (int r = r0 + tid; r < r1; r += kPT) {
-      const int lp = inv[r];
-      if (lp <= j) continue;
+    mine = 0ull;
+#pragma unroll
+    for (int i = 0; i < kMaxRowsPerThread; ++i) {
+      const int r = r0 + tid + i * kPT;
+      if (r >= r1 || lp[i] <= j) continue;
       float* row = slab + (r - r0) * kStride;
       if (!zero) {
         const float l = row[j] / d;
@@ -149,18 +135,21 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
         for (int c = j + 1; c < jb; ++c) row[c] = fmaf(-l, prow[c], row[c]);
       }
       if (j + 1 < jb) {
-        const unsigned long long kk = key_of(row[j + 1], lp);
-        best = kk > best ? kk : best;
+        const unsigned long long kk = key_of(row[j + 1], lp[i], r);
+        mine = kk > mine ? kk : mine;
       }
     }
     if (tid == 0 && rank == 0) piv[k + j] = k + p;
-    best = block_max(best, red);
   }
   cluster.sync();   // no CTA reads another's shared memory after this
   // write the panel back in its final row order
-  for (int t = tid; t < (r1 - r0) * kPB; t += kPT) {
-    const int r = t / kPB, c = t % kPB;
-    if (c < jb) LU[(size_t)(k + inv[r0 + r]) * n + k + c] = slab[r * kStride + c];
+#pragma unroll
+  for (int i = 0; i < kMaxRowsPerThread; ++i) {
+    const int r = r0 + tid + i * kPT;
+    if (r >= r1) continue;
+    float* dst = LU + (size_t)(k + lp[i]) * n + k;
+    const float* row = slab + (r - r0) * kStride;
+    for (int c = 0; c < jb; ++c) dst[c] = row[c];
   }
   if (tid == 0 && rank == 0 && my_info) atomicCAS(info, 0, my_info);
   cluster.sync();
@@ -183,14 +172,14 @@ __global__ void k_lu_laswp(float* LU, int n, int k, int jb, const int* __restric
   }
 }
 
-// U12 = L11^-1 A12: one thread per column of A12
-__global__ void k_lu_trsm(float* LU, int n, int k, int jb) {
+// U12 = L11^-1 A12 for the columns [c0, c1): one thread per column
+__global__ void k_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1) {
   __shared__ float L[kPB][kPB + 1];
   for (int t = threadIdx.x; t < jb * jb; t += blockDim.x)
     L[t / jb][t % jb] = LU[(size_t)(k + t / jb) * n + k + t % jb];
   __syncthreads();
-  const int c = k + jb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
   float x[kPB];
 #pragma unroll
   for (int i = 0; i < kPB; ++i) x[i] = i < jb ? LU[(size_t)(k + i) * n + c] : 0.0f;
@@ -229,14 +218,16 @@ __global__ void k_apply_piv(const double* __restrict__ rhs, float* y, int n,
 
 // Triangular solve by 32-row blocks.  LOWER: unit lower L, blocks in
 // increasing order; else upper U with its diagonal, blocks in decreasing
-// order.  Block b waits for the flags of the blocks it depends on.
+// order.  Block b's eight warps share its dependencies (warp w takes every
+// eighth one); each waits, with a bounded spin, for that block's flag and
+// adds its 32x32 product, one row per lane.  Warp 0 then solves the
+// diagonal block and publishes the flag.
 template <bool LOWER>
 __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int n, float* y,
                                               unsigned* flags, unsigned epoch, unsigned* ticket,
                                               int* err) {
   __shared__ unsigned s_b;
   __shared__ float part[8][32];
-  __shared__ float yb[32];
   const int nb = (n + 31) / 32;
   if (threadIdx.x == 0) s_b = atomicAdd(ticket, 1u);
   __syncthreads();
@@ -245,60 +236,58 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int 
   const int row0 = b * 32;
   const int rows = min(32, n - row0);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  // contributions of the finished blocks, in dependency order
-  for (int q = 0; q < nb; ++q) {
+  const int row = row0 + lane;
+  const float* lrow = LU + (size_t)min(row, n - 1) * n;
+  float acc = 0.0f;
+  const int ndep = LOWER ? b : nb - 1 - b;
+  for (int q = w; q < ndep; q += 8) {
     const int c = LOWER ? q : nb - 1 - q;
-    if (c == b) break;
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       unsigned spins = 0;
-      while (atomicAdd(&flags[c], 0u) != epoch) {
+      for (;;) {
+        unsigned f;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&flags[c]) : "memory");
+        if (f == epoch) break;
         if (++spins > kSpin) {
           atomicExch(err, 1);
           break;
         }
         if (spins > 64) __nanosleep(100);
       }
-      __threadfence();
     }
-    __syncthreads();
-    const int col = c * 32 + lane;
-    const float yc = col < n ? __ldcg(&y[col]) : 0.0f;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int row = row0 + w * 4 + r;
-      if (row < n && col < n) acc[r] = fmaf(LU[(size_t)row * n + col], yc, acc[r]);
+    __syncwarp();
+    const int cb = c * 32;
+    const float yc = cb + lane < n ? __ldcg(&y[cb + lane]) : 0.0f;
+    const int cols = min(32, n - cb);
+    for (int j = 0; j < cols; ++j) {
+      const float yj = __shfl_sync(0xffffffffu, yc, j);
+      if (row < n) acc = fmaf(lrow[cb + j], yj, acc);
     }
   }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    float v = acc[r];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) part[w][r] = v;
-  }
+  part[w][lane] = acc;
   __syncthreads();
-  // the diagonal block, by one warp
   if (w == 0) {
     float v = 0.0f;
-    if (lane < rows) v = __ldcg(&y[row0 + lane]) - part[lane >> 2][lane & 3];
+    if (lane < rows) {
+      float sacc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sacc += part[k][lane];
+      v = __ldcg(&y[row0 + lane]) - sacc;
+    }
     if (LOWER) {
       for (int i = 0; i < rows; ++i) {
         const float yi = __shfl_sync(0xffffffffu, v, i);
-        if (lane > i && lane < rows) v = fmaf(-LU[(size_t)(row0 + lane) * n + row0 + i], yi, v);
+        if (lane > i && lane < rows) v = fmaf(-lrow[row0 + i], yi, v);
       }
     } else {
+      const float dii = lane < rows ? lrow[row0 + lane] : 1.0f;   // my row's diagonal
       for (int i = rows - 1; i >= 0; --i) {
-        float vi = __shfl_sync(0xffffffffu, v, i);
-        const float dii = LU[(size_t)(row0 + i) * n + row0 + i];
-        vi = vi / dii;
-        if (lane == i) v = vi;
-        if (lane < i) v = fmaf(-LU[(size_t)(row0 + lane) * n + row0 + i], vi, v);
+        if (lane == i) v = v / dii;
+        const float vi = __shfl_sync(0xffffffffu, v, i);
+        if (lane < i) v = fmaf(-lrow[row0 + i], vi, v);
       }
     }
-    if (lane < rows) yb[lane] = v;
-    __syncwarp();
-    if (lane < rows) y[row0 + lane] = yb[lane];
+    if (lane < rows) y[row0 + lane] = v;
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicExch(&flags[b], epoch);
@@ -396,7 +385,7 @@ __global__ void k_residual_to_f32(const double* __restrict__ r, float* y, int n,
 size_t panel_smem(int n, int k) {
   const int m = n - k;
   const int rs = (m + kPC - 1) / kPC;
-  return (size_t)rs * kStride * 4 + (size_t)m * 8 + 16 + 2 * kPC * 8 + kPB * 4 + 8 * 8 + 64;
+  return (size_t)rs * kStride * 4 + 16 + 2 * kPC * 8 + 2 * 8 + kPB * 4 + 64;
 }
 
 }  // namespace
@@ -419,15 +408,21 @@ cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info
   return cudaGetLastError();
 }
 
-cudaError_t launch_lu_laswp_trsm(float* LU, int n, int k, int jb, const int* piv, cudaStream_t s,
-                                 Prof* prof) {
-  prof_begin(prof, "lu_laswp_trsm", s);
+cudaError_t launch_lu_laswp(float* LU, int n, int k, int jb, const int* piv, cudaStream_t s,
+                            Prof* prof) {
+  prof_begin(prof, "lu_laswp", s);
   if (k > 0) k_lu_laswp<<<(k + 255) / 256, 256, 0, s>>>(LU, n, k, jb, piv, 0, k);
   const int rest = n - k - jb;
-  if (rest > 0) {
-    k_lu_laswp<<<(rest + 255) / 256, 256, 0, s>>>(LU, n, k, jb, piv, k + jb, n);
-    k_lu_trsm<<<(rest + 127) / 128, 128, 0, s>>>(LU, n, k, jb);
-  }
+  if (rest > 0) k_lu_laswp<<<(rest + 255) / 256, 256, 0, s>>>(LU, n, k, jb, piv, k + jb, n);
+  prof_end(prof, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1, cudaStream_t s,
+                           Prof* prof) {
+  if (c1 <= c0) return cudaSuccess;
+  prof_begin(prof, "lu_trsm", s);
+  k_lu_trsm<<<(c1 - c0 + 127) / 128, 128, 0, s>>>(LU, n, k, jb, c0, c1);
   prof_end(prof, s);
   return cudaGetLastError();
 }

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
   __shared__ int s_keys[kTile];
   __shared__ unsigned s_whist[kWarps][kRadix];
   __shared__ unsigned s_start[kRadix];
-  __shared__ long long s_gbase[kRadix];
+  __shared__ int s_gbase[kRadix];
   __shared__ unsigned s_warp[kWarps];
   __shared__ unsigned s_tile;
 
@@ -225,9 +225,9 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
     unsigned peers = 0xffffffffu;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-      const bool bit = (d >> b) & 1u;
+      const unsigned bit = (d >> b) & 1u;
       const unsigned bal = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? bal : ~bal;
+      peers &= bal ^ (bit - 1u);          // lanes whose bit b equals mine
     }
     if (!full) {
       const unsigned bal = __ballot_sync(0xffffffffu, ok);
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
     }
   }
   if (timeout) atomicExch(&res->timeout, 1);
-  s_gbase[d] = (long long)h->offs[pass][d] + (long long)excl - (long long)start;
+  s_gbase[d] = (int)h->offs[pass][d] + (int)excl - (int)start;
   __syncthreads();
 
   // write the tile out in digit runs
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
   for (int i = tid; i < valid_cnt; i += kSortBlock) {
     const int k = s_keys[i];
     const unsigned dk = digit_of<LAST>(k, shift);
-    const long long pos = s_gbase[dk] + i;
+    const int pos = s_gbase[dk] + i;
     if (pos >= 0 && pos < n) __stcs(out + pos, k);   // only a timed-out look-back can miss
     if (LAST && CHECK) {
       fp_add(f1, f2, k);

@@ -673,6 +673,7 @@ static sg_status attach(sg_ctx* c, void* target, const sg_contract* k, int32_t* 
       n->nin = 3;
       n->seed = k->seed;
       n->nvec = k->nvec > 0 ? k->nvec : 4;
+      if (n->nvec > 4) return fail(c, SG_ERR_INVALID_ARG, "Freivalds uses at most 4 vectors");
       n->tol = k->tol > 0 ? k->tol : 8.0;
       n->prec = SG_PREC_F32_SIMT;
       use(n.get(), 0, t->v);

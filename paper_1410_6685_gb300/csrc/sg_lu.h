@@ -5,13 +5,18 @@
 namespace sgk {
 
 constexpr int kLuPanel = 32;      // panel width of the blocked factorisation
+constexpr int kLuOuter = 128;     // outer block: one tensor-core update per 128 columns
 constexpr int kLuMaxN = 9216;     // the panel must fit the cluster's shared memory
 
 size_t lu_panel_max_smem(int n);
 cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info, cudaStream_t s,
                             Prof* prof);
-cudaError_t launch_lu_laswp_trsm(float* LU, int n, int k, int jb, const int* piv, cudaStream_t s,
-                                 Prof* prof);
+// the interchanges of piv[k..k+jb) on every column outside the panel
+cudaError_t launch_lu_laswp(float* LU, int n, int k, int jb, const int* piv, cudaStream_t s,
+                            Prof* prof);
+// rows k..k+jb of columns [c0, c1) := L11^-1 (them), L11 = unit lower at (k, k)
+cudaError_t launch_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1, cudaStream_t s,
+                           Prof* prof);
 // y = U^-1 L^-1 P rhs in binary32; rhs_is_residual only changes the trace
 // name.  flags: 2*ceil(n/32) words that never hold `epoch` before the call.
 cudaError_t launch_lu_solve(const float* LU, int n, const int* piv, const double* rhs,

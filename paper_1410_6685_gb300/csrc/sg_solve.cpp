@@ -172,23 +172,46 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
   if (e == cudaSuccess) e = cudaMemsetAsync(base + o_flags, 0, o_norms + 64 - o_flags, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.viol, 0, 8, s);
   if (e == cudaSuccess) e = sgk::launch_anorm(a, n, w.norms, s);
-  for (int k = 0; k < n && e == cudaSuccess; k += sgk::kLuPanel) {
-    const int jb = std::min(sgk::kLuPanel, n - k);
-    e = sgk::launch_lu_panel(w.lu, n, k, jb, w.piv, w.info, s, prof);
-    if (e == cudaSuccess) e = sgk::launch_lu_laswp_trsm(w.lu, n, k, jb, w.piv, s, prof);
-    c->kernels += 4;
-    const int rest = n - k - jb;
-    if (rest > 0 && e == cudaSuccess) {
-      float* l21 = w.lu + (size_t)(k + jb) * n + k;
-      float* u12 = w.lu + (size_t)k * n + k + jb;
-      float* a22 = w.lu + (size_t)(k + jb) * n + k + jb;
-      if (o.precision == SG_PREC_F32_SIMT) {
-        e = sgk::launch_gemm_f32(l21, n, u12, n, a22, n, rest, rest, jb, true, s, prof);
+  // two levels: 32-column panels inside 128-column outer blocks; inside an
+  // outer block only its own columns are updated (binary32 SIMT, narrow);
+  // the trailing matrix is updated once per outer block with K = 128
+  const bool tc = o.precision != SG_PREC_F32_SIMT;
+  auto gemm_sub = [&](float* a_, float* b_, float* c_, int M, int N, int K, bool big) {
+    if (M <= 0 || N <= 0 || K <= 0 || e != cudaSuccess) return;
+    if (big && tc) {
+      e = sgk::launch_gemm_tc(a_, n, b_, n, c_, n, M, N, K, o.precision == SG_PREC_F16_TC, true,
+                              w.gemm, s, prof, &c->kernels);
+    } else {
+      e = sgk::launch_gemm_f32(a_, n, b_, n, c_, n, M, N, K, true, s, prof);
+      c->kernels += 1;
+    }
+  };
+  auto at = [&](int r, int col) { return w.lu + (size_t)r * n + col; };
+  for (int K = 0; K < n && e == cudaSuccess; K += sgk::kLuOuter) {
+    const int KB = std::min(sgk::kLuOuter, n - K);
+    for (int j = K; j < K + KB && e == cudaSuccess; j += sgk::kLuPanel) {
+      const int jb = std::min(sgk::kLuPanel, K + KB - j);
+      e = sgk::launch_lu_panel(w.lu, n, j, jb, w.piv, w.info, s, prof);
+      if (e == cudaSuccess) e = sgk::launch_lu_laswp(w.lu, n, j, jb, w.piv, s, prof);
+      c->kernels += 3;
+      const int right = K + KB - (j + jb);   // columns of this outer block to the right
+      if (right > 0 && e == cudaSuccess) {
+        e = sgk::launch_lu_trsm(w.lu, n, j, jb, j + jb, K + KB, s, prof);
         c->kernels += 1;
-      } else {
-        e = sgk::launch_gemm_tc(l21, n, u12, n, a22, n, rest, rest, jb,
-                                o.precision == SG_PREC_F16_TC, true, w.gemm, s, prof, &c->kernels);
+        gemm_sub(at(j + jb, j), at(j, j + jb), at(j + jb, j + jb), n - j - jb, right, jb, false);
       }
+    }
+    const int rest = n - K - KB;
+    if (rest > 0 && e == cudaSuccess) {
+      // U12 = L11^-1 A12 for the outer block, 32 rows at a time
+      for (int i = 0; i < KB && e == cudaSuccess; i += sgk::kLuPanel) {
+        const int ib = std::min(sgk::kLuPanel, KB - i);
+        e = sgk::launch_lu_trsm(w.lu, n, K + i, ib, K + KB, n, s, prof);
+        c->kernels += 1;
+        gemm_sub(at(K + i + ib, K + i), at(K + i, K + KB), at(K + i + ib, K + KB), KB - i - ib, rest,
+                 ib, false);
+      }
+      gemm_sub(at(K + KB, K), at(K, K + KB), at(K + KB, K + KB), rest, rest, KB, true);
     }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hinfo, w.info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
