@@ -7,7 +7,10 @@
 //   tau_i = c * u_eff * sqrt( sum_k a_ik^2 ((B r)_k^2 + s_k) ),  s_k = sum_j b_kj^2,
 // a c-sigma bound on the rounding noise of a product whose operand rounding
 // and accumulation have unit roundoff u_eff.  Three streaming passes, one
-// warp per row: r, then B (B r and s), then A and C together.
+// column stripe per CTA (8 warps side by side along 8 rows), each lane holding its columns' vector entries in
+// registers while the rows stream by (their loads issued together); partial
+// sums per stripe are then added in a fixed order: r, then B (B r and
+// |B_k|^2), then A and C together, then the per-row test.
 #include <math.h>
 
 #include "sg_linalg_kernels.h"
@@ -15,7 +18,7 @@
 namespace sgk {
 namespace {
 
-constexpr int kMaxVec = 8;
+constexpr int kMaxVec = 4;
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -23,12 +26,18 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
-__global__ void k_frv_r(float* r, int N, int nvec, unsigned long long seed) {
-  const long long total = (long long)N * nvec;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const unsigned long long z = mix64(seed + (unsigned long long)(t + 1) * 0x9E3779B97F4A7C15ull);
-    r[t] = (z >> 63) ? -1.0f : 1.0f;   // r[v*N + j]
+// r4[j] = (r_0(j), r_1(j), r_2(j), r_3(j)); unused vectors are 0
+__global__ void k_frv_r(float4* r4, int N, int nvec, unsigned long long seed) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
+       j += (long long)gridDim.x * blockDim.x) {
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const unsigned long long t = (unsigned long long)q * N + j + 1;
+      const unsigned long long z = mix64(seed + t * 0x9E3779B97F4A7C15ull);
+      v[q] = q < nvec ? ((z >> 63) ? -1.0f : 1.0f) : 0.0f;
+    }
+    r4[j] = make_float4(v[0], v[1], v[2], v[3]);
   }
 }
 
@@ -38,81 +47,187 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// br[v*N + k] = sum_j B[k][j] r[v][j];  s[k] = sum_j B[k][j]^2
-template <int NV>
-__global__ void __launch_bounds__(256) k_frv_b(const float* __restrict__ B, int N,
-                                               const float* __restrict__ r, float* br, float* s) {
-  const int lane = threadIdx.x & 31;
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long k = warp; k < N; k += nwarps) {
-    const float* row = B + k * (long long)N;
-    float acc[NV], sq = 0.0f;
+constexpr int kRows = 8;            // rows per CTA (their loads issued together)
+constexpr int kWarps = 8;           // warps per CTA, side by side along a row
+constexpr int kWB = 256;            // columns per warp in the B pass (8 per lane)
+constexpr int kWAC = 128;           // columns per warp in the A/C pass (4 per lane)
+constexpr int kSwB = kWarps * kWB;  // stripe width of a CTA, B pass
+constexpr int kSwAC = kWarps * kWAC;
+
+__device__ __forceinline__ float4 ldv(const float* row, long long col, int N, bool vec) {
+  if (vec && col + 3 < N) return __ldcs(reinterpret_cast<const float4*>(row + col));
+  float v[4];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0.0f;
-    for (int j = lane; j < N; j += 32) {
-      const float b = __ldcs(row + j);
-      sq = fmaf(b, b, sq);
+  for (int q = 0; q < 4; ++q) v[q] = col + q < N ? __ldcs(row + col + q) : 0.0f;
+  return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+__device__ __forceinline__ float4 ldvec(const float4* p, long long j, int N) {
+  return j < N ? p[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// partials over column stripes of B:  pb[s][k] = (sum_j B[k][j] r_v[j] for v<4,
+// sum_j B[k][j]^2), j in stripe s; the warps' shares are added in warp order
+__global__ void __launch_bounds__(256, 2) k_frv_b(const float* __restrict__ B, int N,
+                                                  const float4* __restrict__ r4, float* pb) {
+  __shared__ float red[kWarps][kRows][5];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int stripe = blockIdx.x;
+  const long long c0 = (long long)stripe * kSwB + w * kWB + lane * 8;
+  const long long row0 = (long long)blockIdx.y * kRows;
+  const bool vec = (N % 4) == 0 && ((uintptr_t)B % 16) == 0;
+  float4 r[8];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = fmaf(b, __ldg(r + (long long)v * N + j), acc[v]);
+  for (int e = 0; e < 8; ++e) r[e] = ldvec(r4, c0 + e, N);
+  float4 b[kRows][2];
+#pragma unroll
+  for (int i = 0; i < kRows; ++i) {
+    const long long row = row0 + i;
+    const float* rp = B + (row < N ? row : 0) * (long long)N;
+    b[i][0] = row < N ? ldv(rp, c0, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+    b[i][1] = row < N ? ldv(rp, c0 + 4, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < kRows; ++i) {
+    const float bv[8] = {b[i][0].x, b[i][0].y, b[i][0].z, b[i][0].w,
+                         b[i][1].x, b[i][1].y, b[i][1].z, b[i][1].w};
+    float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      o[0] = fmaf(bv[e], r[e].x, o[0]);
+      o[1] = fmaf(bv[e], r[e].y, o[1]);
+      o[2] = fmaf(bv[e], r[e].z, o[2]);
+      o[3] = fmaf(bv[e], r[e].w, o[3]);
+      o[4] = fmaf(bv[e], bv[e], o[4]);
     }
-    sq = warp_sum(sq);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = warp_sum(acc[v]);
+    for (int t = 0; t < 5; ++t) o[t] = warp_sum(o[t]);
     if (lane == 0) {
-      s[k] = sq;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) br[(long long)v * N + k] = acc[v];
+      for (int t = 0; t < 5; ++t) red[w][i][t] = o[t];
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < kRows * 5) {
+    const int i = threadIdx.x / 5, t = threadIdx.x % 5;
+    const long long row = row0 + i;
+    float acc = 0.0f;
+#pragma unroll
+    for (int v = 0; v < kWarps; ++v) acc += red[v][i][t];
+    if (row < N) pb[((long long)stripe * N + row) * 5 + t] = acc;
   }
 }
 
-template <int NV>
-__global__ void __launch_bounds__(256) k_frv_ac(const float* __restrict__ A,
-                                                const float* __restrict__ C, int N,
-                                                const float* __restrict__ r,
-                                                const float* __restrict__ br,
-                                                const float* __restrict__ s, float c, float u_eff,
-                                                FreivaldsResult* res) {
-  const int lane = threadIdx.x & 31;
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long i = warp; i < N; i += nwarps) {
-    const float* arow = A + i * (long long)N;
-    const float* crow = C + i * (long long)N;
-    float z[NV], q[NV], w[NV];
+// br4[k] = sum over stripes (fixed order), t4[k] = br4[k]^2 + |B_k|^2
+__global__ void k_frv_b_reduce(const float* __restrict__ pb, int N, int nstripes, float4* br4,
+                               float4* t4) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int s = 0; s < nstripes; ++s) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) z[v] = q[v] = w[v] = 0.0f;
-    for (int k = lane; k < N; k += 32) {
-      const float a = __ldcs(arow + k);
-      const float cc = __ldcs(crow + k);
-      const float a2 = a * a;
-      const float sk = __ldg(s + k);
+    for (int t = 0; t < 5; ++t) o[t] += pb[((long long)s * N + k) * 5 + t];
+  }
+  br4[k] = make_float4(o[0], o[1], o[2], o[3]);
+  t4[k] = make_float4(fmaf(o[0], o[0], o[4]), fmaf(o[1], o[1], o[4]), fmaf(o[2], o[2], o[4]),
+                      fmaf(o[3], o[3], o[4]));
+}
+
+// partials over column stripes of A and C: z = A br, q = (A.A) t, w = C r
+__global__ void __launch_bounds__(256, 2) k_frv_ac(const float* __restrict__ A,
+                                                   const float* __restrict__ C, int N,
+                                                   const float4* __restrict__ r4,
+                                                   const float4* __restrict__ br4,
+                                                   const float4* __restrict__ t4, float* pac) {
+  __shared__ float red[kWarps][kRows][12];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int stripe = blockIdx.x;
+  const long long c0 = (long long)stripe * kSwAC + w * kWAC + lane * 4;
+  const long long row0 = (long long)blockIdx.y * kRows;
+  const bool vec = (N % 4) == 0 && ((uintptr_t)A % 16) == 0 && ((uintptr_t)C % 16) == 0;
+  float4 vb[4], vt[4], vr[4];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float b = __ldg(br + (long long)v * N + k);
-        z[v] = fmaf(a, b, z[v]);
-        q[v] = fmaf(a2, fmaf(b, b, sk), q[v]);
-        w[v] = fmaf(cc, __ldg(r + (long long)v * N + k), w[v]);
+  for (int e = 0; e < 4; ++e) {
+    vb[e] = ldvec(br4, c0 + e, N);
+    vt[e] = ldvec(t4, c0 + e, N);
+    vr[e] = ldvec(r4, c0 + e, N);
+  }
+  float4 av[kRows], cv[kRows];
+#pragma unroll
+  for (int i = 0; i < kRows; ++i) {
+    const long long row = row0 + i;
+    const long long rr = row < N ? row : 0;
+    av[i] = row < N ? ldv(A + rr * (long long)N, c0, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+    cv[i] = row < N ? ldv(C + rr * (long long)N, c0, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < kRows; ++i) {
+    const float a[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
+    const float c[4] = {cv[i].x, cv[i].y, cv[i].z, cv[i].w};
+    float o[12];
+#pragma unroll
+    for (int t = 0; t < 12; ++t) o[t] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float a2 = a[e] * a[e];
+      o[0] = fmaf(a[e], vb[e].x, o[0]); o[1] = fmaf(a[e], vb[e].y, o[1]);
+      o[2] = fmaf(a[e], vb[e].z, o[2]); o[3] = fmaf(a[e], vb[e].w, o[3]);
+      o[4] = fmaf(a2, vt[e].x, o[4]); o[5] = fmaf(a2, vt[e].y, o[5]);
+      o[6] = fmaf(a2, vt[e].z, o[6]); o[7] = fmaf(a2, vt[e].w, o[7]);
+      o[8] = fmaf(c[e], vr[e].x, o[8]); o[9] = fmaf(c[e], vr[e].y, o[9]);
+      o[10] = fmaf(c[e], vr[e].z, o[10]); o[11] = fmaf(c[e], vr[e].w, o[11]);
+    }
+#pragma unroll
+    for (int t = 0; t < 12; ++t) o[t] = warp_sum(o[t]);
+    if (lane == 0) {
+#pragma unroll
+      for (int t = 0; t < 12; ++t) red[w][i][t] = o[t];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kRows * 12) {
+    const int i = threadIdx.x / 12, t = threadIdx.x % 12;
+    const long long row = row0 + i;
+    float acc = 0.0f;
+#pragma unroll
+    for (int v = 0; v < kWarps; ++v) acc += red[v][i][t];
+    if (row < N) pac[((long long)stripe * N + row) * 12 + t] = acc;
+  }
+}
+
+// per row: sum the partials (fixed order), compare |z - w| with tau
+__global__ void k_frv_check(const float* __restrict__ pac, int N, int nstripes, int nvec,
+                            float c, float u_eff, FreivaldsResult* res) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  float worst = 0.0f;
+  bool bad = false;
+  if (i < N) {
+    float o[12];
+#pragma unroll
+    for (int t = 0; t < 12; ++t) o[t] = 0.0f;
+    for (int s = 0; s < nstripes; ++s) {
+      const float* p = pac + ((long long)s * N + i) * 12;
+#pragma unroll
+      for (int t = 0; t < 12; t += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p + t);
+        o[t] += v.x; o[t + 1] += v.y; o[t + 2] += v.z; o[t + 3] += v.w;
       }
     }
-    float worst = 0.0f;
-    bool bad = false;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const float zz = warp_sum(z[v]), qq = warp_sum(q[v]), ww = warp_sum(w[v]);
-      const float tau = c * u_eff * sqrtf(qq);
-      const float gap = fabsf(zz - ww);
+    for (int v = 0; v < 4; ++v) {
+      if (v >= nvec) continue;
+      const float tau = c * u_eff * sqrtf(o[4 + v]);
+      const float gap = fabsf(o[v] - o[8 + v]);
       const float ratio = tau > 0.0f ? gap / tau : (gap > 0.0f ? INFINITY : 0.0f);
       worst = fmaxf(worst, ratio);
       bad |= !(gap <= tau);
     }
-    if (lane == 0) {
-      if (bad) atomicMax(&res->viol_enc, ~(unsigned long long)i);
-      // ratios are non-negative: their float bits order like unsigned ints
-      atomicMax(reinterpret_cast<unsigned*>(&res->max_ratio), __float_as_uint(worst));
-    }
+    if (bad) atomicMax(&res->viol_enc, ~(unsigned long long)i);
   }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o2));
+  // ratios are non-negative: their float bits order like unsigned ints
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned*>(&res->max_ratio), __float_as_uint(worst));
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -120,7 +235,10 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 
 size_t freivalds_scratch_bytes(int N, int nvec) {
-  return 2 * align256((size_t)N * nvec * sizeof(float)) + align256((size_t)N * sizeof(float));
+  (void)nvec;
+  const size_t nsb = (size_t)((N + kSwB - 1) / kSwB), nsa = (size_t)((N + kSwAC - 1) / kSwAC);
+  return 3 * align256((size_t)N * sizeof(float4)) + align256(nsb * N * 5 * sizeof(float)) +
+         align256(nsa * N * 12 * sizeof(float));
 }
 
 cudaError_t launch_freivalds(const float* A, const float* B, const float* C, int N,
@@ -129,29 +247,25 @@ cudaError_t launch_freivalds(const float* A, const float* B, const float* C, int
                              int64_t* kernels) {
   if (N <= 0) return cudaSuccess;
   if (nvec < 1 || nvec > kMaxVec) return cudaErrorInvalidValue;
+  const int nsb = (N + kSwB - 1) / kSwB, nsa = (N + kSwAC - 1) / kSwAC;
   char* p = static_cast<char*>(scratch);
-  float* r = reinterpret_cast<float*>(p);
-  float* br = reinterpret_cast<float*>(p + align256((size_t)N * nvec * sizeof(float)));
-  float* s = reinterpret_cast<float*>(p + 2 * align256((size_t)N * nvec * sizeof(float)));
-  const int rows_grid = (N + 7) / 8;   // 8 warps per block, one row per warp
+  const size_t one = align256((size_t)N * sizeof(float4));
+  float4* r4 = reinterpret_cast<float4*>(p);
+  float4* br4 = reinterpret_cast<float4*>(p + one);
+  float4* t4 = reinterpret_cast<float4*>(p + 2 * one);
+  char* q = p + 3 * one;
+  float* pb = reinterpret_cast<float*>(q);
+  q += align256((size_t)nsb * N * 5 * sizeof(float));
+  float* pac = reinterpret_cast<float*>(q);
+  const int rowblocks = (N + kRows - 1) / kRows;
   prof_begin(prof, "freivalds", st);
-  k_frv_r<<<(N * nvec + 255) / 256, 256, 0, st>>>(r, N, nvec, seed);
-#define SG_FRV(NV)                                                                      \
-  k_frv_b<NV><<<rows_grid, 256, 0, st>>>(B, N, r, br, s);                               \
-  k_frv_ac<NV><<<rows_grid, 256, 0, st>>>(A, C, N, r, br, s, c, u_eff, res)
-  switch (nvec) {
-    case 1: SG_FRV(1); break;
-    case 2: SG_FRV(2); break;
-    case 3: SG_FRV(3); break;
-    case 4: SG_FRV(4); break;
-    case 5: SG_FRV(5); break;
-    case 6: SG_FRV(6); break;
-    case 7: SG_FRV(7); break;
-    default: SG_FRV(8); break;
-  }
-#undef SG_FRV
+  k_frv_r<<<(N + 255) / 256, 256, 0, st>>>(r4, N, nvec, seed);
+  k_frv_b<<<dim3(nsb, rowblocks), 256, 0, st>>>(B, N, r4, pb);
+  k_frv_b_reduce<<<(N + 255) / 256, 256, 0, st>>>(pb, N, nsb, br4, t4);
+  k_frv_ac<<<dim3(nsa, rowblocks), 256, 0, st>>>(A, C, N, r4, br4, t4, pac);
+  k_frv_check<<<(N + 255) / 256, 256, 0, st>>>(pac, N, nsa, nvec, c, u_eff, res);
   prof_end(prof, st);
-  *kernels += 3;
+  *kernels += 5;
   return cudaGetLastError();
 }
 
