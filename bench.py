@@ -15,6 +15,13 @@ four read+write passes).  Inputs are resident in HBM and larger than L2
 For N > 1 run under torch.distributed.run: each rank sorts its own keys (weak
 scaling, no data-path collective; a barrier and a max over ranks frame the
 timed region).  `--impl reference` times the CPU oracle on a bounded sample.
+
+After the headline, rank 0 also reports the other parts of the metric under
+`extras.secondary` (skip with --no-extras): the fused zip + for_all + sum
+stream at n = 2^28 (GB/s, fraction of HBM, contract overhead), the bf16
+tcgen05 GEMM at 8192^2 with its Freivalds postcondition (TFLOP/s, contract
+overhead), GEPP at n = 8192 with refinement, and the batch of 10,000
+collections.
 """
 from __future__ import annotations
 
@@ -38,12 +45,14 @@ WORKLOAD = ("sort int32 n=2^26 uniform full range, postconditions sorted + permu
 
 
 def peaks():
+    """(HBM GB/s, bf16 TFLOP/s burst, kind): the measured copy bandwidth and
+    cuBLAS bf16 rate of this GPU model, else the fallback figures."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 1900.0, "fallback"
 
 
 def dist_env():
@@ -147,6 +156,138 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(torch, stream, step, k):
+    """Mean device milliseconds of `step` over k calls (CUDA events on `stream`)."""
+    step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
+def with_contracts_off(sg, ctx, fn):
+    sg.sg_set_contract_mode(ctx, sg.SG_CONTRACTS_OFF)
+    try:
+        return fn()
+    finally:
+        sg.sg_set_contract_mode(ctx, sg.SG_CONTRACTS_PRE_POST)
+
+
+def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
+    """The other rows of the metric, each on its own synthetic workload:
+    the fused zip+reduce+for_all stream, the bf16 tensor-core GEMM with its
+    Freivalds postcondition, GEPP with iterative refinement, and the batched
+    chain.  Every figure is device time from CUDA events; the overhead of
+    contract checking is the ratio of the same steps with checking on and off."""
+    import numpy as np
+    from paper_1410_6685_gb300 import inputs
+    out = {}
+    g = torch.Generator(device="cuda")
+
+    # 1. zip(+) -> ensure for_all(z = x + y) -> reduce(sum), n = 2^28, one fused pass
+    n = 1 << 28
+    g.manual_seed(0)
+    x = torch.rand(n, device="cuda", generator=g) * 2 - 1
+    y = torch.rand(n, device="cuda", generator=g) * 2 - 1
+    vx, vy = sg.wrap_tensor(ctx, x), sg.wrap_tensor(ctx, y)
+    add = [("x", 0), ("x", 1), ("add",)]
+    post = sg.contract(sg.SG_C_FOR_ALL, [("x", 0), ("x", 1), ("x", 2), ("add",), ("eq",)],
+                       other=[vx, vy])
+
+    def s_stream():
+        z = sg.sg_zip(ctx, add, vx, vy)
+        sg.sg_ensure(ctx, z, post)
+        r = sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, z)
+        sg.sg_scalar_get(ctx, r)
+        sg.sg_vector_release(z)
+        sg.sg_scalar_release(r)
+    ms = time_steps(torch, stream, s_stream, k)
+    ms_off = with_contracts_off(sg, ctx, lambda: time_steps(torch, stream, s_stream, k))
+    gbs = 12.0 * n / (ms / 1e3) / 1e9     # read x, y; write z
+    out["stream_zip_sum_forall"] = {
+        "n": n, "ms": round(ms, 4), "GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4),
+        "bytes_per_elem": 12, "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2)}
+    sg.sg_vector_release(vx)
+    sg.sg_vector_release(vy)
+    del x, y
+
+    # 2. matmul 8192^2, bf16 operands on tcgen05, f32 accumulate, Freivalds (4 vectors)
+    N = 8192
+    g.manual_seed(4)
+    A = torch.randn(N, N, device="cuda", generator=g)
+    B = torch.randn(N, N, device="cuda", generator=g)
+    ma, mb = sg.wrap_tensor(ctx, A), sg.wrap_tensor(ctx, B)
+
+    def s_mm():
+        c = sg.sg_matmul(ctx, ma, mb, sg.SG_PREC_BF16_TC)
+        sg.sg_flush(ctx)
+        sg.sg_matrix_release(c)
+    sg.sg_profile_enable(ctx, True)
+    sg.sg_profile_report(ctx, reset=True)
+    ms = time_steps(torch, stream, s_mm, k)
+    prof = sg.sg_profile_report(ctx, reset=True)
+    sg.sg_profile_enable(ctx, False)
+    ms_off = with_contracts_off(sg, ctx, lambda: time_steps(torch, stream, s_mm, k))
+    kern = {kk: round(v[1] / v[0], 4) for kk, v in prof.items()}
+    g_ms = kern.get("gemm_tc_bf16")
+    out["gemm_bf16_8192"] = {
+        "ms_step": round(ms, 4), "TFLOPs_step": round(2 * N ** 3 / (ms / 1e3) / 1e12, 1),
+        "TFLOPs_gemm_kernel": round(2 * N ** 3 / (g_ms / 1e3) / 1e12, 1) if g_ms else None,
+        "frac_tensor_gemm_kernel": round(2 * N ** 3 / (g_ms / 1e3) / 1e12 / tc_peak, 4)
+        if g_ms else None,
+        "per_kernel_ms": kern, "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2)}
+    sg.sg_matrix_release(ma)
+    sg.sg_matrix_release(mb)
+    del A, B
+
+    # 3. GEPP n = 8192, bf16 trailing updates, binary64 refinement + residual check
+    n = 8192
+    An, bn = inputs.gepp_inputs(n)
+    ta, tb = torch.from_numpy(An).cuda(), torch.from_numpy(bn).cuda()
+    mA, vb = sg.wrap_tensor(ctx, ta), sg.wrap_tensor(ctx, tb)
+    o = sg.SgSolveOpts()
+    o.precision, o.max_iter, o.refine_tol, o.residual_tol = sg.SG_PREC_BF16_TC, 30, 1e-14, 1e-12
+    info_box = {}
+
+    def s_solve():
+        xs, info = sg.sg_solve(ctx, mA, vb, o)
+        info_box["it"] = info.iterations
+        sg.sg_vector_release(xs)
+    ms = time_steps(torch, stream, s_solve, 2)
+    out["solve_gepp_8192"] = {"ms": round(ms, 3), "iterations": info_box.get("it"),
+                              "GFLOPs": round(2 / 3 * n ** 3 / (ms / 1e3) / 1e9, 1)}
+    sg.sg_matrix_release(mA)
+    sg.sg_vector_release(vb)
+    del ta, tb
+
+    # 4. 10,000 collections (log-uniform lengths), map -> filter -> sum, one launch
+    L = inputs.batch_lengths()
+    off = inputs.batch_offsets(L)
+    total = int(off[-1])
+    g.manual_seed(9)
+    xb = torch.rand(total, device="cuda", generator=g) * 2 - 1
+    to = torch.from_numpy(off).cuda()
+    nseg = len(L)
+    outs = (torch.empty(nseg, dtype=torch.float64, device="cuda"),
+            torch.empty(nseg, dtype=torch.int64, device="cuda"),
+            torch.empty(nseg, dtype=torch.int64, device="cuda"))
+    ch = sg.chain([("x", 0), ("x", 0), ("c", 1.0), ("fma",)], [("x", 0), ("c", 1.0), ("ge",)],
+                  [("x", 0), ("c", 1.5), ("gt",)])
+
+    def s_batch():
+        sg.sg_batch_run(ctx, ch, xb.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
+    ms = time_steps(torch, stream, s_batch, k)
+    gbs = (4.0 * total + 24 * nseg) / (ms / 1e3) / 1e9
+    out["batch_10000"] = {"elements": total, "ms": round(ms, 4), "GBps": round(gbs, 1),
+                          "frac_hbm": round(gbs / hbm_peak, 4)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,6 +295,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_KEYS)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the stream / GEMM / solve / batch figures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -261,7 +404,7 @@ def main():
         sg.sg_destroy(ctx)
         return
 
-    peak, peak_kind = peaks()
+    peak, tc_peak, peak_kind = peaks()
     value = world * BYTES_PER_KEY * n / (ms / 1e3) / 1e9
     roof = None
     if "onesweep" in prof:
@@ -272,19 +415,23 @@ def main():
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "kernel": "k_onesweep (passes 1-3; 8 bytes/key read+write)",
                 "peak_kind": peak_kind + " hbm_gbs (copy bandwidth)"}
+    extras = None
+    if not args.no_extras:
+        extras = secondary_workloads(torch, sg, ctx, stream, max(3, min(args.steps, 10)), peak,
+                                     tc_peak)
     cpu = None
     if world == 1:
         import oracle
         oracle.build()
-        sample = 1 << 24
+        sample = min(n, 1 << 26)
         sk = keys[:sample].copy()
         t0 = time.perf_counter()
         oracle_step(sk)
         dt = time.perf_counter() - t0
         cpu = {"value": round(BYTES_PER_KEY * sample / dt / 1e9, 4), "unit": "GB/s", "cores": 1,
                "kind": "oracle",
-               "sample": "first 2^24 keys of the same workload, one step: C qsort + is_sorted + "
-                         "multiset equality, single thread"}
+               "sample": "first %d keys of the same workload, one step: C qsort + is_sorted + "
+                         "multiset equality, single thread" % sample}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -306,6 +453,7 @@ def main():
             "ms_per_step_contracts_off": round(ms_off, 4),
             "per_kernel_ms": {k: round(v[1] / v[0], 5) for k, v in prof.items()},
             "per_kernel_launches": {k: v[0] for k, v in prof.items()},
+            "secondary": extras,
         },
     }
     print(json.dumps(line), flush=True)

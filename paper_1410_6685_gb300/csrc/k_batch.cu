@@ -7,14 +7,17 @@
 //
 // Work list: every collection is cut into chunks of `chunk` elements (an
 // empty collection still gets one chunk).  A one-block prep kernel scans the
-// chunk counts; the persistent kernel's CTAs then take chunks from a global
-// ticket, locate the chunk's collection by binary search, evaluate the fused
-// program and leave a per-chunk partial.  The CTA that finishes a
+// chunk counts and a second kernel writes each chunk's collection; the
+// persistent kernel's CTAs then take chunks from a global ticket, evaluate
+// the fused program and leave a per-chunk partial.  The program is either
+// interpreted (this file) or compiled at run time into straight-line code
+// (the same kernel, specialised by sg_jit.cpp).  The CTA that finishes a
 // collection's last chunk (per-collection counter) combines the partials in
 // chunk order, so results do not depend on scheduling.  All counters return
 // to zero, so the captured CUDA graph can be replayed as is.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -22,6 +25,7 @@
 
 #include "sg_batch.h"
 #include "sg_eval.cuh"
+#include "sg_jit.h"
 
 namespace sgk {
 namespace {
@@ -94,11 +98,23 @@ __global__ void __launch_bounds__(1024) k_batch_prep(const long long* __restrict
   }
 }
 
+// chunk_seg[chunk_start[s] + c] = s for every chunk c of collection s
+__global__ void k_batch_map(const long long* __restrict__ chunk_start, long long nseg,
+                            long long capacity, int* chunk_seg) {
+  if (chunk_start[nseg] > capacity) return;   // overflow: the batch kernel does nothing
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nseg;
+       s += (long long)gridDim.x * blockDim.x) {
+    const long long c0 = chunk_start[s], c1 = chunk_start[s + 1];
+    for (long long c = c0; c < c1; ++c) chunk_seg[c] = (int)s;
+  }
+}
+
 template <int DEPTH, bool VEC>
 __global__ void __launch_bounds__(kBB) k_batch(const float* __restrict__ data,
                                                const long long* __restrict__ off, long long nseg,
                                                long long chunk, const StreamArgs a,
                                                const long long* __restrict__ chunk_start,
+                                               const int* __restrict__ chunk_seg,
                                                ChunkPartial* partials, unsigned* seg_done,
                                                BatchHdr* h, double* sums, long long* first_viol,
                                                long long* kept) {
@@ -112,13 +128,7 @@ __global__ void __launch_bounds__(kBB) k_batch(const float* __restrict__ data,
     const unsigned long long item = s_item;
     __syncthreads();
     if (item >= total) break;
-    // collection of this chunk: last s with chunk_start[s] <= item
-    long long lo = 0, hi = nseg - 1;
-    while (lo < hi) {
-      const long long mid = (lo + hi + 1) >> 1;
-      if ((unsigned long long)chunk_start[mid] <= item) lo = mid; else hi = mid - 1;
-    }
-    const long long s = lo;
+    const long long s = chunk_seg[item];
     const long long c = (long long)item - chunk_start[s];
     const long long nch = chunk_start[s + 1] - chunk_start[s];
     const long long sb = off[s], se = off[s + 1];
@@ -254,7 +264,8 @@ bool build_chain_prog(const sg_chain& ch, Prog* pr, int* depth) {
 
 size_t batch_scratch_bytes(long long nseg, long long capacity) {
   return sizeof(BatchHdr) + (size_t)(nseg + 1) * sizeof(long long) +
-         (size_t)nseg * sizeof(unsigned) + (size_t)capacity * sizeof(ChunkPartial) + 1024;
+         (size_t)nseg * sizeof(unsigned) + (size_t)capacity * sizeof(ChunkPartial) +
+         (size_t)capacity * sizeof(int) + 1280;
 }
 
 cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, Prof* prof) {
@@ -266,6 +277,8 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, Prof* prof) {
   unsigned* seg_done = reinterpret_cast<unsigned*>(base + o);
   o = (o + (size_t)L.nseg * sizeof(unsigned) + 255) & ~(size_t)255;
   ChunkPartial* partials = reinterpret_cast<ChunkPartial*>(base + o);
+  o = (o + (size_t)L.capacity * sizeof(ChunkPartial) + 255) & ~(size_t)255;
+  int* chunk_seg = reinterpret_cast<int*>(base + o);
 
   StreamArgs a{};
   a.prog = L.prog;
@@ -278,12 +291,39 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, Prof* prof) {
   if (L.nseg == 0) return cudaSuccess;
   prof_begin(prof, "batch_prep", s);
   k_batch_prep<<<1, 1024, 0, s>>>(L.offsets, L.nseg, L.chunk, L.capacity, chunk_start, h);
+  k_batch_map<<<(int)std::min<long long>((L.nseg + 255) / 256, 1024), 256, 0, s>>>(
+      chunk_start, L.nseg, L.capacity, chunk_seg);
   prof_end(prof, s);
-  prof_begin(prof, "batch", s);
   const bool vec = ((uintptr_t)L.data & 15) == 0;
+  if (L.jit) {
+    BatchJitArgs ja{};
+    ja.data = L.data;
+    ja.off = L.offsets;
+    ja.nseg = L.nseg;
+    ja.chunk = L.chunk;
+    for (int i = 0; i < kMaxProg; ++i) ja.cst[i] = L.prog.cst[i];
+    ja.chunk_start = chunk_start;
+    ja.chunk_seg = chunk_seg;
+    ja.partials = partials;
+    ja.seg_done = seg_done;
+    ja.hdr = h;
+    ja.sums = L.sums;
+    ja.first_viol = L.first_viol;
+    ja.kept = L.kept;
+    ja.vec4 = vec ? 1 : 0;
+    void* args[] = {&ja};
+    prof_begin(prof, "batch_jit", s);
+    e = cudaLaunchKernel((const void*)L.jit, dim3(L.grid), dim3(kBB), args, 0, s);
+    prof_end(prof, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(L.host_flag, &h->any_violation, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        s);
+    return e == cudaSuccess ? cudaGetLastError() : e;
+  }
+  prof_begin(prof, "batch", s);
 #define SG_BATCH(D, V)                                                                  \
   k_batch<D, V><<<L.grid, kBB, 0, s>>>(L.data, L.offsets, L.nseg, L.chunk, a, chunk_start, \
-                                       partials, seg_done, h, L.sums, L.first_viol, L.kept)
+                                       chunk_seg, partials, seg_done, h, L.sums, L.first_viol, L.kept)
   if (L.depth > 4) {
     if (vec) SG_BATCH(8, true); else SG_BATCH(8, false);
   } else {

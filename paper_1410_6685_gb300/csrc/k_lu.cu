@@ -219,9 +219,10 @@ __global__ void k_apply_piv(const double* __restrict__ rhs, float* y, int n,
 // Triangular solve by 32-row blocks.  LOWER: unit lower L, blocks in
 // increasing order; else upper U with its diagonal, blocks in decreasing
 // order.  Block b's eight warps share its dependencies (warp w takes every
-// eighth one); each waits, with a bounded spin, for that block's flag and
-// adds its 32x32 product, one row per lane.  Warp 0 then solves the
-// diagonal block and publishes the flag.
+// eighth one); each loads that 32x32 block into registers, waits, with a
+// bounded spin, for the block's flag and adds its product, one row per
+// lane.  Warp 0 then solves the diagonal block (held in registers from the
+// start) and publishes the flag with a release store.
 template <bool LOWER>
 __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int n, float* y,
                                               unsigned* flags, unsigned epoch, unsigned* ticket,
@@ -240,8 +241,19 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int 
   const float* lrow = LU + (size_t)min(row, n - 1) * n;
   float acc = 0.0f;
   const int ndep = LOWER ? b : nb - 1 - b;
+  // warp 0 keeps its diagonal block's row in registers for the final solve
+  float dg[32];
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) dg[j] = (row < n && row0 + j < n) ? lrow[row0 + j] : 0.0f;
+  }
   for (int q = w; q < ndep; q += 8) {
     const int c = LOWER ? q : nb - 1 - q;
+    const int cb = c * 32;
+    // the 32x32 block does not depend on the flag: load it before waiting
+    float m[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) m[j] = (row < n && cb + j < n) ? lrow[cb + j] : 0.0f;
     if (lane == 0) {
       unsigned spins = 0;
       for (;;) {
@@ -256,13 +268,9 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int 
       }
     }
     __syncwarp();
-    const int cb = c * 32;
     const float yc = cb + lane < n ? __ldcg(&y[cb + lane]) : 0.0f;
-    const int cols = min(32, n - cb);
-    for (int j = 0; j < cols; ++j) {
-      const float yj = __shfl_sync(0xffffffffu, yc, j);
-      if (row < n) acc = fmaf(lrow[cb + j], yj, acc);
-    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc = fmaf(m[j], __shfl_sync(0xffffffffu, yc, j), acc);
   }
   part[w][lane] = acc;
   __syncthreads();
@@ -275,22 +283,30 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int 
       v = __ldcg(&y[row0 + lane]) - sacc;
     }
     if (LOWER) {
-      for (int i = 0; i < rows; ++i) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
         const float yi = __shfl_sync(0xffffffffu, v, i);
-        if (lane > i && lane < rows) v = fmaf(-lrow[row0 + i], yi, v);
+        if (lane > i && lane < rows) v = fmaf(-dg[i], yi, v);
       }
     } else {
-      const float dii = lane < rows ? lrow[row0 + lane] : 1.0f;   // my row's diagonal
-      for (int i = rows - 1; i >= 0; --i) {
-        if (lane == i) v = v / dii;
-        const float vi = __shfl_sync(0xffffffffu, v, i);
-        if (lane < i) v = fmaf(-lrow[row0 + i], vi, v);
+      // my row's diagonal entry is dg[lane]: select it without dynamic indexing
+      float dii = 1.0f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) dii = lane == j && lane < rows ? dg[j] : dii;
+#pragma unroll
+      for (int i = 31; i >= 0; --i) {
+        if (i < rows) {
+          if (lane == i) v = v / dii;
+          const float vi = __shfl_sync(0xffffffffu, v, i);
+          if (lane < i) v = fmaf(-dg[i], vi, v);
+        }
       }
     }
     if (lane < rows) y[row0 + lane] = v;
     __threadfence();
     __syncwarp();
-    if (lane == 0) atomicExch(&flags[b], epoch);
+    if (lane == 0)
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&flags[b]), "r"(epoch) : "memory");
   }
 }
 

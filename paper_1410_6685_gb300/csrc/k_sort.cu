@@ -8,8 +8,9 @@
 //      histograms and the input's multiset fingerprint; its last block turns
 //      the histograms into per-digit global start offsets.
 //   2. k_onesweep x4: each CTA takes the next tile (a global atomic ticket,
-//      so tiles start in order), ranks its keys stably inside the tile
-//      (warp-private counters with match_any), publishes its per-digit tile
+//      so tiles start in order; 6144 keys, 24 per thread), ranks its keys
+//      stably inside the tile (warp-private counters; the lanes sharing a
+//      digit are found by match_any or by ballots), publishes its per-digit tile
 //      counts, finds the exclusive prefix of each digit over the preceding
 //      tiles by a decoupled look-back (bounded waits), sorts the tile in
 //      shared memory by digit and writes it out in digit runs.
@@ -29,8 +30,9 @@ namespace sgk {
 namespace {
 
 constexpr int kSortBlock = 256;
-constexpr int kKpt = 16;
-constexpr int kTile = kSortBlock * kKpt;   // 4096 keys
+constexpr int kKpt = 24;
+constexpr int kTile = kSortBlock * kKpt;   // 6144 keys
+constexpr int kMatchEvery = 4;
 constexpr int kRadix = 256;
 constexpr int kWarps = kSortBlock / 32;
 constexpr int kWarpKeys = 32 * kKpt;
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
   __shared__ int s_gbase[kRadix];
   __shared__ unsigned s_warp[kWarps];
   __shared__ unsigned s_tile;
+  __shared__ unsigned short s_rank[kTile];
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (tid == 0) s_tile = atomicAdd(&h->tile_ctr[pass], 1u);
@@ -214,31 +217,38 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
   }
 
   // stable rank of each key among the warp's keys of the same digit; the
-  // lanes holding the same digit are found with eight ballots (one per digit
-  // bit), a ninth separates the padding lanes of a partial tile
-  unsigned short rank[kKpt];
+  // lanes holding the same digit are found with match_any, or with eight
+  // ballots (one per digit bit) and a ninth that separates the padding lanes
+  // of a partial tile
   const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
     const bool ok = full || (wbase + r * 32) < n;
     const unsigned d = digit_of<LAST>(key[r], shift);
-    unsigned peers = 0xffffffffu;
+    unsigned peers;
+    if (r % kMatchEvery == 0) {
+      // one round in kMatchEvery on the match unit, the others on ballots,
+      // so that the two kinds of instruction overlap
+      peers = __match_any_sync(0xffffffffu, ok ? d : 0x1000u);
+    } else {
+      peers = 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const unsigned bit = (d >> b) & 1u;
-      const unsigned bal = __ballot_sync(0xffffffffu, bit);
-      peers &= bal ^ (bit - 1u);          // lanes whose bit b equals mine
-    }
-    if (!full) {
-      const unsigned bal = __ballot_sync(0xffffffffu, ok);
-      peers &= ok ? bal : ~bal;
+      for (int b = 0; b < 8; ++b) {
+        const unsigned bit = (d >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bal ^ (bit - 1u);        // lanes whose bit b equals mine
+      }
+      if (!full) {
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        peers &= ok ? bal : ~bal;
+      }
     }
     const unsigned before = __popc(peers & lt);
     const unsigned prev = ok ? s_whist[w][d] : 0u;
     __syncwarp();
     if (ok && before == 0) s_whist[w][d] = prev + __popc(peers);
     __syncwarp();
-    rank[r] = (unsigned short)(prev + before);
+    s_rank[w * kWarpKeys + r * 32 + lane] = (unsigned short)(prev + before);
   }
   __syncthreads();
 
@@ -264,7 +274,7 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
   for (int r = 0; r < kKpt; ++r) {
     if (full || (wbase + r * 32) < n) {
       const unsigned d = digit_of<LAST>(key[r], shift);
-      s_keys[s_start[d] + s_whist[w][d] + rank[r]] = key[r];
+      s_keys[s_start[d] + s_whist[w][d] + s_rank[w * kWarpKeys + r * 32 + lane]] = key[r];
     }
   }
   __syncthreads();

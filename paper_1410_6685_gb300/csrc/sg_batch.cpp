@@ -9,6 +9,7 @@
 #include <string>
 
 #include "sg_batch.h"
+#include "sg_jit.h"
 #include "sg_runtime.h"
 #include "sg_sched.h"
 
@@ -109,6 +110,7 @@ sg_status run_with(sg_ctx* c, const Job& j, const sg_sched_choice& sch, double* 
   key.kept = j.kept;
   key.chunk = sch.chunk;
   key.grid_per_sm = sch.blocks_per_sm;
+  key.pad = c->codegen;
   BatchPlanCache& cache = c->batch;
   if (!cache.capture_stream) {
     if (cudaStreamCreateWithFlags(&cache.capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -148,6 +150,8 @@ sg_status run_with(sg_ctx* c, const Job& j, const sg_sched_choice& sch, double* 
       L.first_viol = reinterpret_cast<long long*>(j.first);
       L.kept = reinterpret_cast<long long*>(j.kept);
       L.host_flag = p.host_flag;
+      L.jit = c->codegen == SG_CODEGEN_SPECIALIZE ? sgk::jit_batch_kernel(j.prog, nullptr)
+                                                  : nullptr;
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(cache.capture_stream, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {

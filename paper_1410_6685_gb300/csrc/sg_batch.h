@@ -19,6 +19,7 @@ struct BatchLaunch {
   long long* first_viol;
   long long* kept;
   unsigned* host_flag;      // pinned: bit 0 violation, bit 1 capacity overflow
+  cudaKernel_t jit;         // run-time specialised kernel, or nullptr (interpreter)
 };
 
 bool build_chain_prog(const sg_chain& ch, Prog* pr, int* depth);

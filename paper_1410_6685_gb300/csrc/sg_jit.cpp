@@ -252,6 +252,107 @@ extern "C" __global__ void __launch_bounds__(256) sg_fused(const JitArgs a) {
 }
 )SGJIT";
 
+const char* kTemplateBatch = R"SGJIT(
+struct ChunkPartial { double sum; long long cnt; long long first; };
+struct BatchHdr { unsigned ticket; unsigned any_violation; unsigned long long total_chunks; unsigned pad[60]; };
+struct BatchJitArgs {
+  const float* data; const long long* off; long long nseg; long long chunk; float cst[48];
+  const long long* chunk_start; const int* chunk_seg; ChunkPartial* partials; unsigned* seg_done;
+  BatchHdr* hdr; double* sums; long long* first_viol; long long* kept; int vec4; int pad;
+};
+__device__ __forceinline__ void sg_elem(const BatchJitArgs& a, float v, long long i, Acc& acc) {
+  float x[1] = {v};
+  float o[1];
+  unsigned hit = 0u;
+  float rv = 0.0f;
+  bool rm = false;
+  sg_body(a, x, i, o, hit, rv, rm);
+  if (hit & 1u) acc.first[0] = i < acc.first[0] ? i : acc.first[0];
+  acc_one(acc, rv, rm);
+}
+extern "C" __global__ void __launch_bounds__(256) sg_batch(const BatchJitArgs a) {
+  __shared__ unsigned long long s_item;
+  __shared__ Acc s_acc[8];
+  __shared__ bool s_last;
+  const unsigned long long total = a.hdr->total_chunks;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.hdr->ticket, 1u);
+    __syncthreads();
+    const unsigned long long item = s_item;
+    __syncthreads();
+    if (item >= total) break;
+    const long long s = a.chunk_seg[item];
+    const long long cs = a.chunk_start[s];
+    const long long c = (long long)item - cs;
+    const long long nch = a.chunk_start[s + 1] - cs;
+    const long long sb = a.off[s], se = a.off[s + 1];
+    const long long b = sb + c * a.chunk;
+    const long long e = b + a.chunk < se ? b + a.chunk : se;
+    Acc acc;
+    acc_init(acc);
+    if (a.vec4) {
+      const long long q0 = b >> 2, q1 = (e + 3) >> 2;
+      for (long long q = q0 + threadIdx.x; q < q1; q += 256) {
+        const float4 t = __ldcs(reinterpret_cast<const float4*>(a.data) + q);
+        const float xv[4] = {t.x, t.y, t.z, t.w};
+        const long long j0 = q << 2;
+        if (j0 >= b && j0 + 3 < e) {
+#pragma unroll
+          for (int l = 0; l < 4; ++l) sg_elem(a, xv[l], j0 + l - sb, acc);
+        } else {
+#pragma unroll
+          for (int l = 0; l < 4; ++l)
+            if (j0 + l >= b && j0 + l < e) sg_elem(a, xv[l], j0 + l - sb, acc);
+        }
+      }
+    } else {
+      for (long long i = b + threadIdx.x; i < e; i += 256) sg_elem(a, __ldcs(a.data + i), i - sb, acc);
+    }
+    acc_fold(acc);
+    warp_reduce(acc);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s_acc[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Acc tot = s_acc[0];
+      for (int k = 1; k < 8; ++k) acc_merge(tot, s_acc[k]);
+      if (nch == 1) {
+        a.sums[s] = tot.sum;
+        a.kept[s] = tot.cnt;
+        a.first_viol[s] = tot.first[0] == SG_NONE ? -1 : tot.first[0];
+        if (tot.first[0] != SG_NONE) atomicOr(&a.hdr->any_violation, 1u);
+        s_last = false;
+      } else {
+        ChunkPartial p;
+        p.sum = tot.sum; p.cnt = tot.cnt; p.first = tot.first[0];
+        a.partials[cs + c] = p;
+        __threadfence();
+        s_last = atomicAdd(&a.seg_done[s], 1u) == (unsigned)(nch - 1);
+      }
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+      __threadfence();
+      double sum = 0.0;
+      long long cnt = 0, first = SG_NONE;
+      for (long long k = 0; k < nch; ++k) {
+        const ChunkPartial* p = &a.partials[cs + k];
+        sum += __ldcg(&p->sum);
+        cnt += __ldcg(&p->cnt);
+        const long long f = __ldcg(&p->first);
+        first = f < first ? f : first;
+      }
+      a.sums[s] = sum;
+      a.kept[s] = cnt;
+      a.first_viol[s] = first == SG_NONE ? -1 : first;
+      if (first != SG_NONE) atomicOr(&a.hdr->any_violation, 1u);
+      a.seg_done[s] = 0;
+    }
+    __syncthreads();
+  }
+}
+)SGJIT";
+
 // ---- body generation: symbolic execution of the postfix program -----------
 bool gen_body(const Prog& pr, uint32_t pred_exists, std::string* body) {
   std::vector<std::string> st;
@@ -367,36 +468,10 @@ Cache& cache() {
   return c;
 }
 
-}  // namespace
-
-bool jit_available() { return nvrtc().ok; }
-
-// Returns the specialised kernel, compiling it on first use; nullptr when it
-// cannot be built (then the caller uses the interpreting kernel).
-cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, bool reduce,
-                               bool minmax, uint32_t pred_exists, std::string* log) {
+// Compiles `src` (once; cached by source text) and returns its kernel `name`,
+// or nullptr when it cannot be built.
+cudaKernel_t compile_cached(const std::string& src, const char* name, std::string* log) {
   Nvrtc& nv = nvrtc();
-  if (!nv.ok) {
-    if (log) *log = "NVRTC library not found";
-    return nullptr;
-  }
-  std::string body;
-  if (!gen_body(pr, pred_exists, &body)) {
-    if (log) *log = "program could not be specialised";
-    return nullptr;
-  }
-  char defs[320];
-  snprintf(defs, sizeof defs,
-           "#define SG_NIN %d\n#define SG_NX %d\n#define SG_NOUT %d\n#define SG_NO %d\n"
-           "#define SG_NPRED %d\n#define SG_RED %d\n#define SG_MINMAX %d\n",
-           nin, nin > 0 ? nin : 1, nout, nout > 0 ? nout : 1, npred, reduce ? 1 : 0,
-           minmax ? 1 : 0);
-  std::string src = std::string(defs) + kTemplateHead +
-                    "__device__ __forceinline__ void sg_body(const JitArgs& a, const float* x, "
-                    "long long i, float* o, unsigned& hit, float& rv, bool& rm) {\n"
-                    "  bool mask = true;\n  (void)x; (void)i; (void)o; (void)hit; (void)rv; "
-                    "(void)rm; (void)a;\n" +
-                    body + "  (void)mask;\n}\n" + kTemplateKernel;
   Cache& c = cache();
   std::lock_guard<std::mutex> lk(c.mu);
   auto it = c.kernels.find(src);
@@ -416,7 +491,7 @@ cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, boo
       cudaLibrary_t lib = nullptr;
       if (cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) ==
               cudaSuccess &&
-          cudaLibraryGetKernel(&k, lib, "sg_fused") == cudaSuccess) {
+          cudaLibraryGetKernel(&k, lib, name) == cudaSuccess) {
         // the library stays loaded for the life of the process (cached kernel)
       } else {
         cudaGetLastError();
@@ -435,6 +510,56 @@ cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, boo
   if (k) c.kernels[src] = k;
   else c.failed[src] = true;
   return k;
+}
+
+std::string body_fn(const std::string& body) {
+  return "template <class A> __device__ __forceinline__ void sg_body(const A& a, const float* x, "
+         "long long i, float* o, unsigned& hit, float& rv, bool& rm) {\n"
+         "  bool mask = true;\n  (void)x; (void)i; (void)o; (void)hit; (void)rv; "
+         "(void)rm; (void)a;\n" +
+         body + "  (void)mask;\n}\n";
+}
+
+}  // namespace
+
+bool jit_available() { return nvrtc().ok; }
+
+// Returns the specialised kernel, compiling it on first use; nullptr when it
+// cannot be built (then the caller uses the interpreting kernel).
+cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, bool reduce,
+                               bool minmax, uint32_t pred_exists, std::string* log) {
+  if (!nvrtc().ok) {
+    if (log) *log = "NVRTC library not found";
+    return nullptr;
+  }
+  std::string body;
+  if (!gen_body(pr, pred_exists, &body)) {
+    if (log) *log = "program could not be specialised";
+    return nullptr;
+  }
+  char defs[320];
+  snprintf(defs, sizeof defs,
+           "#define SG_NIN %d\n#define SG_NX %d\n#define SG_NOUT %d\n#define SG_NO %d\n"
+           "#define SG_NPRED %d\n#define SG_RED %d\n#define SG_MINMAX %d\n",
+           nin, nin > 0 ? nin : 1, nout, nout > 0 ? nout : 1, npred, reduce ? 1 : 0,
+           minmax ? 1 : 0);
+  const std::string src = std::string(defs) + kTemplateHead + body_fn(body) + kTemplateKernel;
+  return compile_cached(src, "sg_fused", log);
+}
+
+cudaKernel_t jit_batch_kernel(const Prog& pr, std::string* log) {
+  if (!nvrtc().ok) {
+    if (log) *log = "NVRTC library not found";
+    return nullptr;
+  }
+  std::string body;
+  if (!gen_body(pr, 0u, &body)) {
+    if (log) *log = "program could not be specialised";
+    return nullptr;
+  }
+  const std::string src =
+      std::string("#define SG_MINMAX 0\n") + kTemplateHead + body_fn(body) + kTemplateBatch;
+  return compile_cached(src, "sg_batch", log);
 }
 
 cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,

@@ -23,10 +23,33 @@ static_assert(kMaxIn == 4 && kMaxOut == 4 && kMaxProg == 48 && kMaxPred == 4,
               "the kernel template hard-codes these sizes");
 static_assert(sizeof(JitArgs) == 296, "JitArgs layout changed: update the template");
 
+// Kernel argument block of the specialised batch kernel (k_batch.cu holds the
+// interpreting twin); repeated verbatim in the template source.
+struct BatchJitArgs {
+  const float* data;
+  const long long* off;
+  long long nseg;
+  long long chunk;
+  float cst[kMaxProg];
+  const long long* chunk_start;
+  const int* chunk_seg;
+  void* partials;
+  unsigned* seg_done;
+  void* hdr;
+  double* sums;
+  long long* first_viol;
+  long long* kept;
+  int vec4;
+  int pad;
+};
+static_assert(sizeof(BatchJitArgs) == 296, "BatchJitArgs layout changed: update the template");
+
 bool jit_available();
 // minmax: the pass also tracks min / max / NaN (a min, max or avg is asked)
 cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, bool reduce,
                                bool minmax, uint32_t pred_exists, std::string* log);
+// the batched map -> for_all -> masked sum chain of one program (k_batch.cu)
+cudaKernel_t jit_batch_kernel(const Prog& pr, std::string* log);
 cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,
                               cudaStream_t st, Prof* prof);
 

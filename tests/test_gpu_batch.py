@@ -16,13 +16,17 @@ PRE = [("x", 0), ("c", 1.0), ("ge",)]
 KEEP = [("x", 0), ("c", 1.5), ("gt",)]
 
 
-@pytest.fixture(scope="module")
-def env():
+@pytest.fixture(scope="module", params=["specialize", "interpret"])
+def env(request):
+    """Both forms of the batch kernel: the program compiled at run time into
+    straight-line code, and the interpreting kernel."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1410_6685_gb300 import safegpu as sg
     ctx = sg.sg_init(0, torch.cuda.current_stream().cuda_stream)
+    sg.sg_set_codegen(ctx, sg.SG_CODEGEN_SPECIALIZE if request.param == "specialize"
+                      else sg.SG_CODEGEN_INTERPRET)
     yield sg, ctx, torch
     sg.sg_destroy(ctx)
 
