@@ -374,6 +374,17 @@ sg_status sg_profile_report(sg_ctx* ctx, char* buf, size_t cap, size_t* len,
 typedef enum { SG_INJECT_NONE = 0, SG_INJECT_SWAP = 1, SG_INJECT_OVERWRITE = 2 } sg_inject_mode;
 sg_status sg_debug_inject_sort(sg_ctx* ctx, sg_inject_mode mode, int64_t i, int64_t j);
 
+/* Contract testing of `multiply` (Sec. 3.4): plant an error in the NEXT
+ * tensor-core product (SG_PREC_BF16_TC / SG_PREC_F16_TC) of this context:
+ * `delta` is added to element (row, col) of the product as the kernel's
+ * epilogue stores it, so every later reader -- the Freivalds
+ * postcondition, fused into the product or not -- sees the wrong value.
+ * The planted value is a kernel argument; nothing faults.  row = col = -1
+ * cancels; an index outside the product plants nothing.  Binary32 products
+ * ignore it.  Errors: SG_ERR_INVALID_ARG for indices below -1, one of them
+ * negative, or above INT32_MAX. */
+sg_status sg_debug_inject_matmul(sg_ctx* ctx, int64_t row, int64_t col, float delta);
+
 /* ------------------------------------------------------------------------ */
 /* Batched collections: one persistent launch over many collections of uneven
  * size, each running the chain

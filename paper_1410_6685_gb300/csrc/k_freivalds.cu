@@ -13,10 +13,15 @@
 // |B_k|^2), then A and C together, then the per-row test.
 #include <math.h>
 
+#include "sg_frv.cuh"
 #include "sg_linalg_kernels.h"
 
 namespace sgk {
 namespace {
+
+using frv::ldv;
+using frv::ldvec;
+using frv::warp_sum_spread;
 
 constexpr int kMaxVec = 4;
 
@@ -54,67 +59,58 @@ constexpr int kWAC = 128;           // columns per warp in the A/C pass (4 per l
 constexpr int kSwB = kWarps * kWB;  // stripe width of a CTA, B pass
 constexpr int kSwAC = kWarps * kWAC;
 
-__device__ __forceinline__ float4 ldv(const float* row, long long col, int N, bool vec) {
-  if (vec && col + 3 < N) return __ldcs(reinterpret_cast<const float4*>(row + col));
-  float v[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) v[q] = col + q < N ? __ldcs(row + col + q) : 0.0f;
-  return make_float4(v[0], v[1], v[2], v[3]);
-}
-
-__device__ __forceinline__ float4 ldvec(const float4* p, long long j, int N) {
-  return j < N ? p[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-}
+constexpr int kIters = 4;   // row groups of kRows per CTA (vectors loaded once)
 
 // partials over column stripes of B:  pb[s][k] = (sum_j B[k][j] r_v[j] for v<4,
 // sum_j B[k][j]^2), j in stripe s; the warps' shares are added in warp order
 __global__ void __launch_bounds__(256, 2) k_frv_b(const float* __restrict__ B, int N,
                                                   const float4* __restrict__ r4, float* pb) {
-  __shared__ float red[kWarps][kRows][5];
+  __shared__ float red[2][kWarps][kRows][5];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int stripe = blockIdx.x;
   const long long c0 = (long long)stripe * kSwB + w * kWB + lane * 8;
-  const long long row0 = (long long)blockIdx.y * kRows;
   const bool vec = (N % 4) == 0 && ((uintptr_t)B % 16) == 0;
   float4 r[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) r[e] = ldvec(r4, c0 + e, N);
-  float4 b[kRows][2];
+  const int slot = (lane >> 2) & 7;
+#pragma unroll 1
+  for (int it = 0; it < kIters; ++it) {
+    const long long row0 = ((long long)blockIdx.y * kIters + it) * kRows;
+    if (row0 >= N) break;
+    float4 b[kRows][2];
 #pragma unroll
-  for (int i = 0; i < kRows; ++i) {
-    const long long row = row0 + i;
-    const float* rp = B + (row < N ? row : 0) * (long long)N;
-    b[i][0] = row < N ? ldv(rp, c0, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
-    b[i][1] = row < N ? ldv(rp, c0 + 4, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int i = 0; i < kRows; ++i) {
-    const float bv[8] = {b[i][0].x, b[i][0].y, b[i][0].z, b[i][0].w,
-                         b[i][1].x, b[i][1].y, b[i][1].z, b[i][1].w};
-    float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      o[0] = fmaf(bv[e], r[e].x, o[0]);
-      o[1] = fmaf(bv[e], r[e].y, o[1]);
-      o[2] = fmaf(bv[e], r[e].z, o[2]);
-      o[3] = fmaf(bv[e], r[e].w, o[3]);
-      o[4] = fmaf(bv[e], bv[e], o[4]);
+    for (int i = 0; i < kRows; ++i) {
+      const long long row = row0 + i;
+      const float* rp = B + (row < N ? row : 0) * (long long)N;
+      b[i][0] = row < N ? ldv(rp, c0, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+      b[i][1] = row < N ? ldv(rp, c0 + 4, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int t = 0; t < 5; ++t) o[t] = warp_sum(o[t]);
-    if (lane == 0) {
+    for (int i = 0; i < kRows; ++i) {
+      const float bv[8] = {b[i][0].x, b[i][0].y, b[i][0].z, b[i][0].w,
+                           b[i][1].x, b[i][1].y, b[i][1].z, b[i][1].w};
+      float o[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int t = 0; t < 5; ++t) red[w][i][t] = o[t];
+      for (int e = 0; e < 8; ++e) {
+        o[0] = fmaf(bv[e], r[e].x, o[0]);
+        o[1] = fmaf(bv[e], r[e].y, o[1]);
+        o[2] = fmaf(bv[e], r[e].z, o[2]);
+        o[3] = fmaf(bv[e], r[e].w, o[3]);
+        o[4] = fmaf(bv[e], bv[e], o[4]);
+      }
+      const float v = warp_sum_spread<8>(o, lane);
+      if ((lane & 3) == 0 && slot < 5) red[it & 1][w][i][slot] = v;
     }
-  }
-  __syncthreads();
-  if (threadIdx.x < kRows * 5) {
-    const int i = threadIdx.x / 5, t = threadIdx.x % 5;
-    const long long row = row0 + i;
-    float acc = 0.0f;
+    __syncthreads();
+    if (threadIdx.x < kRows * 5) {
+      const int i = threadIdx.x / 5, t = threadIdx.x % 5;
+      const long long row = row0 + i;
+      float acc = 0.0f;
 #pragma unroll
-    for (int v = 0; v < kWarps; ++v) acc += red[v][i][t];
-    if (row < N) pb[((long long)stripe * N + row) * 5 + t] = acc;
+      for (int q = 0; q < kWarps; ++q) acc += red[it & 1][q][i][t];
+      if (row < N) pb[((long long)stripe * N + row) * 5 + t] = acc;
+    }
   }
 }
 
@@ -139,11 +135,10 @@ __global__ void __launch_bounds__(256, 2) k_frv_ac(const float* __restrict__ A,
                                                    const float4* __restrict__ r4,
                                                    const float4* __restrict__ br4,
                                                    const float4* __restrict__ t4, float* pac) {
-  __shared__ float red[kWarps][kRows][12];
+  __shared__ float red[2][kWarps][kRows][12];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int stripe = blockIdx.x;
   const long long c0 = (long long)stripe * kSwAC + w * kWAC + lane * 4;
-  const long long row0 = (long long)blockIdx.y * kRows;
   const bool vec = (N % 4) == 0 && ((uintptr_t)A % 16) == 0 && ((uintptr_t)C % 16) == 0;
   float4 vb[4], vt[4], vr[4];
 #pragma unroll
@@ -152,46 +147,48 @@ __global__ void __launch_bounds__(256, 2) k_frv_ac(const float* __restrict__ A,
     vt[e] = ldvec(t4, c0 + e, N);
     vr[e] = ldvec(r4, c0 + e, N);
   }
-  float4 av[kRows], cv[kRows];
+  const int slot = (lane >> 1) & 15;
+#pragma unroll 1
+  for (int it = 0; it < kIters; ++it) {
+    const long long row0 = ((long long)blockIdx.y * kIters + it) * kRows;
+    if (row0 >= N) break;
+    float4 av[kRows], cv[kRows];
 #pragma unroll
-  for (int i = 0; i < kRows; ++i) {
-    const long long row = row0 + i;
-    const long long rr = row < N ? row : 0;
-    av[i] = row < N ? ldv(A + rr * (long long)N, c0, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
-    cv[i] = row < N ? ldv(C + rr * (long long)N, c0, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int i = 0; i < kRows; ++i) {
-    const float a[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
-    const float c[4] = {cv[i].x, cv[i].y, cv[i].z, cv[i].w};
-    float o[12];
-#pragma unroll
-    for (int t = 0; t < 12; ++t) o[t] = 0.0f;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float a2 = a[e] * a[e];
-      o[0] = fmaf(a[e], vb[e].x, o[0]); o[1] = fmaf(a[e], vb[e].y, o[1]);
-      o[2] = fmaf(a[e], vb[e].z, o[2]); o[3] = fmaf(a[e], vb[e].w, o[3]);
-      o[4] = fmaf(a2, vt[e].x, o[4]); o[5] = fmaf(a2, vt[e].y, o[5]);
-      o[6] = fmaf(a2, vt[e].z, o[6]); o[7] = fmaf(a2, vt[e].w, o[7]);
-      o[8] = fmaf(c[e], vr[e].x, o[8]); o[9] = fmaf(c[e], vr[e].y, o[9]);
-      o[10] = fmaf(c[e], vr[e].z, o[10]); o[11] = fmaf(c[e], vr[e].w, o[11]);
+    for (int i = 0; i < kRows; ++i) {
+      const long long row = row0 + i;
+      const long long rr = row < N ? row : 0;
+      av[i] = row < N ? ldv(A + rr * (long long)N, c0, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+      cv[i] = row < N ? ldv(C + rr * (long long)N, c0, N, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int t = 0; t < 12; ++t) o[t] = warp_sum(o[t]);
-    if (lane == 0) {
+    for (int i = 0; i < kRows; ++i) {
+      const float a[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
+      const float c[4] = {cv[i].x, cv[i].y, cv[i].z, cv[i].w};
+      float o[16];
 #pragma unroll
-      for (int t = 0; t < 12; ++t) red[w][i][t] = o[t];
+      for (int t = 0; t < 16; ++t) o[t] = 0.0f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float a2 = a[e] * a[e];
+        o[0] = fmaf(a[e], vb[e].x, o[0]); o[1] = fmaf(a[e], vb[e].y, o[1]);
+        o[2] = fmaf(a[e], vb[e].z, o[2]); o[3] = fmaf(a[e], vb[e].w, o[3]);
+        o[4] = fmaf(a2, vt[e].x, o[4]); o[5] = fmaf(a2, vt[e].y, o[5]);
+        o[6] = fmaf(a2, vt[e].z, o[6]); o[7] = fmaf(a2, vt[e].w, o[7]);
+        o[8] = fmaf(c[e], vr[e].x, o[8]); o[9] = fmaf(c[e], vr[e].y, o[9]);
+        o[10] = fmaf(c[e], vr[e].z, o[10]); o[11] = fmaf(c[e], vr[e].w, o[11]);
+      }
+      const float v = warp_sum_spread<16>(o, lane);
+      if ((lane & 1) == 0 && slot < 12) red[it & 1][w][i][slot] = v;
     }
-  }
-  __syncthreads();
-  if (threadIdx.x < kRows * 12) {
-    const int i = threadIdx.x / 12, t = threadIdx.x % 12;
-    const long long row = row0 + i;
-    float acc = 0.0f;
+    __syncthreads();
+    if (threadIdx.x < kRows * 12) {
+      const int i = threadIdx.x / 12, t = threadIdx.x % 12;
+      const long long row = row0 + i;
+      float acc = 0.0f;
 #pragma unroll
-    for (int v = 0; v < kWarps; ++v) acc += red[v][i][t];
-    if (row < N) pac[((long long)stripe * N + row) * 12 + t] = acc;
+      for (int q = 0; q < kWarps; ++q) acc += red[it & 1][q][i][t];
+      if (row < N) pac[((long long)stripe * N + row) * 12 + t] = acc;
+    }
   }
 }
 
@@ -230,6 +227,45 @@ __global__ void k_frv_check(const float* __restrict__ pac, int N, int nstripes, 
   if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned*>(&res->max_ratio), __float_as_uint(worst));
 }
 
+// The same test when the partial sums come from the fused product (the cast
+// kernels and the GEMM epilogue): pzq[s][i] = (z_0..3, q_0..3) over column
+// stripe s of A, pw[t][i] = (C r)_i over column tile t of C.
+__global__ void k_frv_check_fused(const float* __restrict__ pzq, int nsa,
+                                  const float4* __restrict__ pw, int nsc, int N, int nvec,
+                                  float c, float u_eff, FreivaldsResult* res) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  float worst = 0.0f;
+  bool bad = false;
+  if (i < N) {
+    float o[12];
+#pragma unroll
+    for (int t = 0; t < 12; ++t) o[t] = 0.0f;
+    for (int s = 0; s < nsa; ++s) {
+      const float4* p = reinterpret_cast<const float4*>(pzq + ((long long)s * N + i) * 8);
+      const float4 z = p[0], q = p[1];
+      o[0] += z.x; o[1] += z.y; o[2] += z.z; o[3] += z.w;
+      o[4] += q.x; o[5] += q.y; o[6] += q.z; o[7] += q.w;
+    }
+    for (int t = 0; t < nsc; ++t) {
+      const float4 w = pw[(long long)t * N + i];
+      o[8] += w.x; o[9] += w.y; o[10] += w.z; o[11] += w.w;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (v >= nvec) continue;
+      const float tau = c * u_eff * sqrtf(o[4 + v]);
+      const float gap = fabsf(o[v] - o[8 + v]);
+      const float ratio = tau > 0.0f ? gap / tau : (gap > 0.0f ? INFINITY : 0.0f);
+      worst = fmaxf(worst, ratio);
+      bad |= !(gap <= tau);
+    }
+    if (bad) atomicMax(&res->viol_enc, ~(unsigned long long)i);
+  }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o2));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned*>(&res->max_ratio), __float_as_uint(worst));
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -257,7 +293,7 @@ cudaError_t launch_freivalds(const float* A, const float* B, const float* C, int
   float* pb = reinterpret_cast<float*>(q);
   q += align256((size_t)nsb * N * 5 * sizeof(float));
   float* pac = reinterpret_cast<float*>(q);
-  const int rowblocks = (N + kRows - 1) / kRows;
+  const int rowblocks = (N + kRows * kIters - 1) / (kRows * kIters);
   prof_begin(prof, "freivalds", st);
   k_frv_r<<<(N + 255) / 256, 256, 0, st>>>(r4, N, nvec, seed);
   k_frv_b<<<dim3(nsb, rowblocks), 256, 0, st>>>(B, N, r4, pb);
@@ -266,6 +302,48 @@ cudaError_t launch_freivalds(const float* A, const float* B, const float* C, int
   k_frv_check<<<(N + 255) / 256, 256, 0, st>>>(pac, N, nsa, nvec, c, u_eff, res);
   prof_end(prof, st);
   *kernels += 5;
+  return cudaGetLastError();
+}
+
+FrvFused frv_fused_layout(void* scratch, int N) {
+  FrvFused f;
+  char* p = static_cast<char*>(scratch);
+  const size_t one = align256((size_t)N * sizeof(float4));
+  f.r4 = reinterpret_cast<float4*>(p);
+  f.br4 = reinterpret_cast<float4*>(p + one);
+  f.t4 = reinterpret_cast<float4*>(p + 2 * one);
+  p += 3 * one;
+  f.nsb = (N + kFrvStripeB - 1) / kFrvStripeB;
+  f.nsa = (N + kFrvStripeA - 1) / kFrvStripeA;
+  f.nsc = (N + kFrvTileC - 1) / kFrvTileC;
+  f.pb = reinterpret_cast<float*>(p);
+  p += align256((size_t)f.nsb * N * 5 * sizeof(float));
+  f.pzq = reinterpret_cast<float*>(p);
+  p += align256((size_t)f.nsa * N * 8 * sizeof(float));
+  f.pw = reinterpret_cast<float4*>(p);
+  p += align256((size_t)f.nsc * N * sizeof(float4));
+  f.bytes = (size_t)(p - static_cast<char*>(scratch));
+  return f;
+}
+
+size_t frv_fused_scratch_bytes(int N) { return frv_fused_layout(nullptr, N).bytes; }
+
+cudaError_t launch_frv_vectors(const FrvFused& f, int N, int nvec, unsigned long long seed,
+                               cudaStream_t st) {
+  if (nvec < 1 || nvec > kMaxVec) return cudaErrorInvalidValue;
+  k_frv_r<<<(N + 255) / 256, 256, 0, st>>>(f.r4, N, nvec, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frv_b_reduce(const FrvFused& f, int N, cudaStream_t st) {
+  k_frv_b_reduce<<<(N + 255) / 256, 256, 0, st>>>(f.pb, N, f.nsb, f.br4, f.t4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frv_check_fused(const FrvFused& f, int N, int nvec, float c, float u_eff,
+                                   FreivaldsResult* res, cudaStream_t st) {
+  k_frv_check_fused<<<(N + 255) / 256, 256, 0, st>>>(f.pzq, f.nsa, f.pw, f.nsc, N, nvec, c, u_eff,
+                                                     res);
   return cudaGetLastError();
 }
 

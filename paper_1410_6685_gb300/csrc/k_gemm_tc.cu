@@ -24,16 +24,19 @@
 
 #include <algorithm>
 
+#include "sg_frv.cuh"
 #include "sg_linalg_kernels.h"
 
 namespace sgk {
 namespace {
 
 constexpr int TM = 128, TN = 256, TK = 64, STAGES = 4;
+static_assert(kFrvTileC == TN, "the fused check keeps one C r partial per column tile");
 constexpr int A_BYTES = TM * TK * 2;            // 16 KB
 constexpr int B_BYTES = TN * TK * 2;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int R_BYTES = TN * 16;                // the fused check's r entries of the tile
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + R_BYTES;
 constexpr unsigned kWaitLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -129,13 +132,16 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
                                                     const __grid_constant__ CUtensorMap mb,
                                                     float* __restrict__ C, int ldc, int M,
                                                     int N, int KB, uint32_t id, int subtract,
-                                                    int* err) {
+                                                    int* err, const float4* __restrict__ frv_r,
+                                                    float4* __restrict__ frv_pw, int inj_row,
+                                                    int inj_col, float inj_delta) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   // bars[0..S): full, bars[S..2S): empty, bars[2S]: done; then the TMEM slot
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  float4* s_r = reinterpret_cast<float4*>(smem + STAGES * STAGE_BYTES + 256);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
 
@@ -143,6 +149,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (frv_r) {
+    for (int j = threadIdx.x; j < TN; j += blockDim.x)
+      s_r[j] = n0 + j < N ? frv_r[n0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -196,11 +206,32 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int row = m0 + warp * 32 + lane;
   if (ready) {
+    // fused Freivalds check: this row's partial C r over the tile's columns
+    float4 wacc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
     for (int c = 0; c < TN / 32; ++c) {
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
       const int col0 = n0 + c * 32;
+      // contract testing: a planted error in one product element, applied
+      // before it is stored (and before the fused check sees it)
+      if (row == inj_row && inj_col >= col0 && inj_col < col0 + 32) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (col0 + j == inj_col) r[j] = __float_as_uint(__uint_as_float(r[j]) + inj_delta);
+      }
+      if (frv_r) {
+        // r of columns past N is zero in s_r (their accumulator entries are too)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float4 rj = s_r[c * 32 + j];
+          const float v = __uint_as_float(r[j]);
+          wacc.x = fmaf(v, rj.x, wacc.x);
+          wacc.y = fmaf(v, rj.y, wacc.y);
+          wacc.z = fmaf(v, rj.z, wacc.z);
+          wacc.w = fmaf(v, rj.w, wacc.w);
+        }
+      }
       if (row < M) {
         float* cp = C + (size_t)row * ldc + col0;
         if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
@@ -225,6 +256,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
         }
       }
     }
+    if (frv_r && row < M) frv_pw[(size_t)blockIdx.x * M + row] = wacc;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -294,6 +326,166 @@ __global__ void k_cast_transpose(const float* __restrict__ B, int ldb, int K, in
   }
 }
 
+__device__ __forceinline__ uint16_t to16(float v, bool fp16) {
+  if (fp16) {
+    const __half x = __float2half_rn(v);
+    return *reinterpret_cast<const uint16_t*>(&x);
+  }
+  const __nv_bfloat16 x = __float2bfloat16_rn(v);
+  return *reinterpret_cast<const uint16_t*>(&x);
+}
+
+// Square B (N x N) -> Bt (N x Kp) 16-bit, with the fused Freivalds partial
+// sums of row k over this CTA's stripe of kFrvStripeB columns:
+// pb[stripe][k] = (sum_j B[k][j] r_v[j], v < 4;  sum_j B[k][j]^2).
+// CTA: 64 rows of B, eight 64-column sub-tiles in turn, each staged in
+// shared memory and written out transposed in 16-byte runs along k.
+template <bool FP16>
+__global__ void __launch_bounds__(256) k_cast_bt_frv(const float* __restrict__ B, int N, int Kp,
+                                                     uint16_t* __restrict__ out,
+                                                     const float4* __restrict__ r4,
+                                                     float* __restrict__ pb) {
+  __shared__ float t[64][65];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k0 = blockIdx.y * 64;
+  const bool vec2 = (N % 2) == 0 && ((uintptr_t)B % 8) == 0;
+  float acc[8][5];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[i][q] = 0.0f;
+#pragma unroll 1
+  for (int st = 0; st < kFrvStripeB / 64; ++st) {
+    const int n0 = blockIdx.x * kFrvStripeB + st * 64;
+    if (n0 >= N) break;   // the same for the whole CTA
+    const int nc = n0 + 2 * lane;
+    const float4 r0 = frv::ldvec(r4, nc, N), r1 = frv::ldvec(r4, nc + 1, N);
+    float b0[8], b1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = k0 + w * 8 + i;
+      b0[i] = 0.0f;
+      b1[i] = 0.0f;
+      if (k < N) {
+        const float* rp = B + (size_t)k * N;
+        if (vec2 && nc + 1 < N) {
+          const float2 v = __ldcs(reinterpret_cast<const float2*>(rp + nc));
+          b0[i] = v.x;
+          b1[i] = v.y;
+        } else {
+          if (nc < N) b0[i] = __ldcs(rp + nc);
+          if (nc + 1 < N) b1[i] = __ldcs(rp + nc + 1);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      acc[i][0] = fmaf(b1[i], r1.x, fmaf(b0[i], r0.x, acc[i][0]));
+      acc[i][1] = fmaf(b1[i], r1.y, fmaf(b0[i], r0.y, acc[i][1]));
+      acc[i][2] = fmaf(b1[i], r1.z, fmaf(b0[i], r0.z, acc[i][2]));
+      acc[i][3] = fmaf(b1[i], r1.w, fmaf(b0[i], r0.w, acc[i][3]));
+      acc[i][4] = fmaf(b1[i], b1[i], fmaf(b0[i], b0[i], acc[i][4]));
+      t[w * 8 + i][2 * lane] = b0[i];
+      t[w * 8 + i][2 * lane + 1] = b1[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = threadIdx.x; u < 512; u += 256) {
+      const int nn = u >> 3, kc = u & 7;
+      const int n = n0 + nn;
+      if (n < N) {
+        uint32_t h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = to16(t[kc * 8 + j][nn], FP16);
+        uint4 pk;
+        pk.x = h[0] | (h[1] << 16);
+        pk.y = h[2] | (h[3] << 16);
+        pk.z = h[4] | (h[5] << 16);
+        pk.w = h[6] | (h[7] << 16);
+        *reinterpret_cast<uint4*>(out + (size_t)n * Kp + k0 + kc * 8) = pk;
+      }
+    }
+    __syncthreads();
+  }
+  const int slot = (lane >> 2) & 7;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    float o[8] = {acc[i][0], acc[i][1], acc[i][2], acc[i][3], acc[i][4], 0.0f, 0.0f, 0.0f};
+    const float v = frv::warp_sum_spread<8>(o, lane);
+    const int k = k0 + w * 8 + i;
+    if ((lane & 3) == 0 && slot < 5 && k < N) pb[((size_t)blockIdx.x * N + k) * 5 + slot] = v;
+  }
+}
+
+// Square A (N x N) -> A16 (N x Kp) 16-bit (zero padded), with the fused
+// partial sums of row i over this CTA's stripe of kFrvStripeA columns:
+// pzq[stripe][i] = (sum_k a_ik br_v[k], v < 4;  sum_k a_ik^2 t_v[k], v < 4).
+// Eight warps side by side along the row (4 columns per lane), 8 rows per
+// step, 4 steps per CTA.
+template <bool FP16>
+__global__ void __launch_bounds__(256, 2) k_cast_a_frv(const float* __restrict__ A, int N, int Kp,
+                                                       uint16_t* __restrict__ out,
+                                                       const float4* __restrict__ br4,
+                                                       const float4* __restrict__ t4,
+                                                       float* __restrict__ pzq) {
+  __shared__ float red[2][8][8][8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long c0 = (long long)blockIdx.x * kFrvStripeA + w * 128 + lane * 4;
+  const bool vec = (N % 4) == 0 && ((uintptr_t)A % 16) == 0;
+  float4 vb[4], vt[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    vb[e] = frv::ldvec(br4, c0 + e, N);
+    vt[e] = frv::ldvec(t4, c0 + e, N);
+  }
+  const int slot = (lane >> 2) & 7;
+#pragma unroll 1
+  for (int it = 0; it < 4; ++it) {
+    const long long row0 = ((long long)blockIdx.y * 4 + it) * 8;
+    if (row0 >= N) break;
+    float4 av[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const long long row = row0 + i;
+      av[i] = row < N ? frv::ldv(A + row * (long long)N, c0, N, vec)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const long long row = row0 + i;
+      const float a[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
+      if (row < N && c0 < Kp) {
+        uint2 pk;
+        pk.x = (uint32_t)to16(a[0], FP16) | ((uint32_t)to16(a[1], FP16) << 16);
+        pk.y = (uint32_t)to16(a[2], FP16) | ((uint32_t)to16(a[3], FP16) << 16);
+        *reinterpret_cast<uint2*>(out + row * Kp + c0) = pk;
+      }
+      float o[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) o[q] = 0.0f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float a2 = a[e] * a[e];
+        o[0] = fmaf(a[e], vb[e].x, o[0]); o[1] = fmaf(a[e], vb[e].y, o[1]);
+        o[2] = fmaf(a[e], vb[e].z, o[2]); o[3] = fmaf(a[e], vb[e].w, o[3]);
+        o[4] = fmaf(a2, vt[e].x, o[4]); o[5] = fmaf(a2, vt[e].y, o[5]);
+        o[6] = fmaf(a2, vt[e].z, o[6]); o[7] = fmaf(a2, vt[e].w, o[7]);
+      }
+      const float v = frv::warp_sum_spread<8>(o, lane);
+      if ((lane & 3) == 0) red[it & 1][w][i][slot] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      const int i = threadIdx.x >> 3, q = threadIdx.x & 7;
+      const long long row = row0 + i;
+      float s = 0.0f;
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) s += red[it & 1][ww][i][q];
+      if (row < N) pzq[((size_t)blockIdx.x * N + row) * 8 + q] = s;
+    }
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -331,7 +523,8 @@ size_t gemm_tc_scratch_bytes(int M, int N, int K) {
 
 cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
                            int M, int N, int K, bool fp16, bool subtract, void* scratch,
-                           cudaStream_t s, Prof* prof, int64_t* kernels) {
+                           cudaStream_t s, Prof* prof, int64_t* kernels, int inj_row,
+                           int inj_col, float inj_delta) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (K <= 0) {   // empty inner dimension: C = 0 (or C unchanged for C - A B)
     if (subtract) return cudaSuccess;
@@ -367,10 +560,57 @@ cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, flo
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
   prof_begin(prof, fp16 ? "gemm_tc_f16" : "gemm_tc_bf16", s);
   k_gemm_tc<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, Kp / TK, idesc(fp16),
-                                          subtract ? 1 : 0, err);
+                                          subtract ? 1 : 0, err, nullptr, nullptr, inj_row,
+                                          inj_col, inj_delta);
   prof_end(prof, s);
   *kernels += 3;
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int N, bool fp16,
+                                   unsigned long long seed, int nvec, float c, float u_eff,
+                                   void* scratch, FreivaldsResult* res, cudaStream_t s,
+                                   Prof* prof, int64_t* kernels, int inj_row, int inj_col,
+                                   float inj_delta) {
+  if (N <= 0) return cudaSuccess;
+  const int Kp = ((N + TK - 1) / TK) * TK;
+  char* p = static_cast<char*>(scratch);
+  int* err = reinterpret_cast<int*>(p);
+  uint16_t* a16 = reinterpret_cast<uint16_t*>(p + 256);
+  uint16_t* bt16 = reinterpret_cast<uint16_t*>(p + 256 + align256((size_t)N * Kp * 2));
+  const FrvFused f = frv_fused_layout(p + gemm_tc_scratch_bytes(N, N, N), N);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  prof_begin(prof, "cast_operands", s);
+  cudaError_t e = launch_frv_vectors(f, N, nvec, seed, s);
+  if (e != cudaSuccess) return e;
+  const dim3 gb((N + kFrvStripeB - 1) / kFrvStripeB, Kp / 64);
+  const dim3 ga(f.nsa, (N + 31) / 32);
+  if (fp16) k_cast_bt_frv<true><<<gb, 256, 0, s>>>(B, N, Kp, bt16, f.r4, f.pb);
+  else k_cast_bt_frv<false><<<gb, 256, 0, s>>>(B, N, Kp, bt16, f.r4, f.pb);
+  e = launch_frv_b_reduce(f, N, s);
+  if (e != cudaSuccess) return e;
+  if (fp16) k_cast_a_frv<true><<<ga, 256, 0, s>>>(A, N, Kp, a16, f.br4, f.t4, f.pzq);
+  else k_cast_a_frv<false><<<ga, 256, 0, s>>>(A, N, Kp, a16, f.br4, f.t4, f.pzq);
+  prof_end(prof, s);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a16, N, Kp, TM, fp16) || !make_map(&mb, bt16, N, Kp, TN, fp16))
+    return cudaErrorInvalidValue;
+  dim3 grid((N + TN - 1) / TN, (N + TM - 1) / TM);
+  prof_begin(prof, fp16 ? "gemm_tc_f16" : "gemm_tc_bf16", s);
+  k_gemm_tc<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, C, N, N, N, Kp / TK, idesc(fp16), 0, err, f.r4,
+                                          f.pw, inj_row, inj_col, inj_delta);
+  prof_end(prof, s);
+  prof_begin(prof, "freivalds_fused", s);
+  e = launch_frv_check_fused(f, N, nvec, c, u_eff, res, s);
+  prof_end(prof, s);
+  *kernels += 6;
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace sgk

@@ -185,31 +185,40 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
 }
 
 // ---------------------------------------------------------------------------
-template <bool LAST, bool CHECK>
-__global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
-    const int* __restrict__ in, int* __restrict__ out, long long n, int pass, SortHdr* h,
-    unsigned* st32, unsigned long long* st64, SortResult* res) {
-  __shared__ int s_keys[kTile];
-  __shared__ unsigned s_whist[kWarps][kRadix];
-  __shared__ unsigned s_start[kRadix];
-  __shared__ int s_gbase[kRadix];
-  __shared__ unsigned s_warp[kWarps];
-  __shared__ unsigned s_tile;
-  __shared__ unsigned short s_rank[kTile];
+struct SortSmem {
+  int keys[kTile];
+  unsigned whist[kWarps][kRadix];
+  unsigned start[kRadix];
+  int gbase[kRadix];
+  unsigned warp[kWarps];
+  unsigned tile;
+  int timeout;
+  unsigned short rank[kTile];
+};
 
+// One tile of one pass.  FULL: the tile holds kTile keys (every tile but the
+// last), so no index is checked against n.
+template <bool LAST, bool CHECK, bool FULL>
+__device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restrict__ in,
+                                              int* __restrict__ out, long long n, int pass,
+                                              SortHdr* h, unsigned* st32,
+                                              unsigned long long* st64, SortResult* res,
+                                              unsigned tile) {
+  int* const s_keys = sm.keys;
+  unsigned (*const s_whist)[kRadix] = sm.whist;
+  unsigned* const s_start = sm.start;
+  int* const s_gbase = sm.gbase;
+  unsigned short* const s_rank = sm.rank;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(&h->tile_ctr[pass], 1u);
-  for (int i = tid; i < kWarps * kRadix; i += kSortBlock) (&s_whist[0][0])[i] = 0;
-  __syncthreads();
-  const unsigned tile = s_tile;
   const long long base = (long long)tile * kTile;
   const int shift = pass * 8;
-  const int valid_cnt = (int)(n - base < kTile ? n - base : kTile);
+  const int valid_cnt = FULL ? kTile : (int)(n - base < kTile ? n - base : kTile);
 
-  // load: warp w owns keys [w*512, (w+1)*512) of the tile, 32 consecutive per round
+  // load: warp w owns keys [w*kWarpKeys, (w+1)*kWarpKeys) of the tile, 32
+  // consecutive per round
   int key[kKpt];
   const long long wbase = base + (long long)w * kWarpKeys + lane;
-  const bool full = valid_cnt == kTile;
+  constexpr bool full = FULL;
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
     const long long idx = wbase + r * 32;
@@ -265,7 +274,7 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
   }
   // publish the tile aggregate as early as possible
   if (!(LAST && CHECK)) st_relaxed(&st32[(size_t)tile * kRadix + tid], ((tile == 0 ? kPre : kAgg) << 30) | cnt);
-  const unsigned start = block_excl_scan(cnt, s_warp);
+  const unsigned start = block_excl_scan(cnt, sm.warp);
   s_start[tid] = start;
   __syncthreads();
 
@@ -343,18 +352,24 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
       atomicMax(&res->unsorted_enc, ~(unsigned long long)pos);
     }
   }
-  if (timeout) atomicExch(&res->timeout, 1);
+  if (timeout) {
+    atomicExch(&res->timeout, 1);
+    sm.timeout = 1;
+  }
   s_gbase[d] = (int)h->offs[pass][d] + (int)excl - (int)start;
   __syncthreads();
+  // a look-back that gave up leaves this tile's offsets unknown: write nothing
+  const bool write = sm.timeout == 0;
 
   // write the tile out in digit runs
   unsigned long long f1 = 0, f2 = 0;
   long long bad = -1;
+#pragma unroll 4
   for (int i = tid; i < valid_cnt; i += kSortBlock) {
     const int k = s_keys[i];
     const unsigned dk = digit_of<LAST>(k, shift);
     const int pos = s_gbase[dk] + i;
-    if (pos >= 0 && pos < n) __stcs(out + pos, k);   // only a timed-out look-back can miss
+    if (write) __stcs(out + pos, k);
     if (LAST && CHECK) {
       fp_add(f1, f2, k);
       if (i + 1 < valid_cnt) {
@@ -377,6 +392,25 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
       res->checked = 1;
     }
   }
+}
+
+template <bool LAST, bool CHECK>
+__global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
+    const int* __restrict__ in, int* __restrict__ out, long long n, int pass, SortHdr* h,
+    unsigned* st32, unsigned long long* st64, SortResult* res) {
+  __shared__ SortSmem sm;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    sm.tile = atomicAdd(&h->tile_ctr[pass], 1u);
+    sm.timeout = 0;
+  }
+  for (int i = tid; i < kWarps * kRadix; i += kSortBlock) (&sm.whist[0][0])[i] = 0;
+  __syncthreads();
+  const unsigned tile = sm.tile;
+  if ((long long)(tile + 1) * kTile <= n)
+    onesweep_tile<LAST, CHECK, true>(sm, in, out, n, pass, h, st32, st64, res, tile);
+  else
+    onesweep_tile<LAST, CHECK, false>(sm, in, out, n, pass, h, st32, st64, res, tile);
 }
 
 // ---------------------------------------------------------------------------

@@ -765,6 +765,15 @@ sg_status sg_debug_inject_sort(sg_ctx* c, sg_inject_mode mode, int64_t i, int64_
   return SG_OK;
 }
 
+sg_status sg_debug_inject_matmul(sg_ctx* c, int64_t row, int64_t col, float delta) {
+  if (!c || row < -1 || col < -1 || (row < 0) != (col < 0) || row > INT32_MAX || col > INT32_MAX)
+    return SG_ERR_INVALID_ARG;
+  c->mm_inject.row = row;
+  c->mm_inject.col = col;
+  c->mm_inject.delta = delta;
+  return SG_OK;
+}
+
 sg_status sg_kernel_count(sg_ctx* c, int64_t* count) {
   if (!c || !count) return SG_ERR_INVALID_ARG;
   *count = c->kernels;

@@ -270,11 +270,36 @@ __device__ __forceinline__ void sg_elem(const BatchJitArgs& a, float v, long lon
   if (hit & 1u) acc.first[0] = i < acc.first[0] ? i : acc.first[0];
   acc_one(acc, rv, rm);
 }
+__device__ __forceinline__ void sg_quad(const BatchJitArgs& a, float4 t, long long j0,
+                                        long long b, long long e, long long sb, Acc& acc) {
+  const float xv[4] = {t.x, t.y, t.z, t.w};
+  if (j0 >= b && j0 + 3 < e) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) sg_elem(a, xv[l], j0 + l - sb, acc);
+  } else {
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+      if (j0 + l >= b && j0 + l < e) sg_elem(a, xv[l], j0 + l - sb, acc);
+  }
+}
+// the three fields a chunk's result needs, combined like acc_merge
+__device__ __forceinline__ void batch_warp_reduce(double& sum, long long& cnt, long long& first) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_xor_sync(0xffffffffu, sum, o);
+    const long long c2 = __shfl_xor_sync(0xffffffffu, cnt, o);
+    const long long f2 = __shfl_xor_sync(0xffffffffu, first, o);
+    sum += s2;
+    cnt += c2;
+    first = f2 < first ? f2 : first;
+  }
+}
 extern "C" __global__ void __launch_bounds__(256) sg_batch(const BatchJitArgs a) {
   __shared__ unsigned long long s_item;
-  __shared__ Acc s_acc[8];
+  __shared__ double s_sum[8];
+  __shared__ long long s_cnt[8], s_first[8];
   __shared__ bool s_last;
   const unsigned long long total = a.hdr->total_chunks;
+  const float4* d4 = reinterpret_cast<const float4*>(a.data);
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&a.hdr->ticket, 1u);
     __syncthreads();
@@ -291,40 +316,49 @@ extern "C" __global__ void __launch_bounds__(256) sg_batch(const BatchJitArgs a)
     Acc acc;
     acc_init(acc);
     if (a.vec4) {
-      const long long q0 = b >> 2, q1 = (e + 3) >> 2;
-      for (long long q = q0 + threadIdx.x; q < q1; q += 256) {
-        const float4 t = __ldcs(reinterpret_cast<const float4*>(a.data) + q);
-        const float xv[4] = {t.x, t.y, t.z, t.w};
-        const long long j0 = q << 2;
-        if (j0 >= b && j0 + 3 < e) {
+      // each thread visits quads q, q + 256, q + 512, ... in that order; four
+      // loads are issued before the four are evaluated
+      const long long q1 = (e + 3) >> 2;
+      long long q = (b >> 2) + threadIdx.x;
+      for (; q + 768 < q1; q += 1024) {
+        float4 t[4];
 #pragma unroll
-          for (int l = 0; l < 4; ++l) sg_elem(a, xv[l], j0 + l - sb, acc);
-        } else {
+        for (int u = 0; u < 4; ++u) t[u] = __ldcs(d4 + q + u * 256);
 #pragma unroll
-          for (int l = 0; l < 4; ++l)
-            if (j0 + l >= b && j0 + l < e) sg_elem(a, xv[l], j0 + l - sb, acc);
-        }
+        for (int u = 0; u < 4; ++u) sg_quad(a, t[u], (q + u * 256) << 2, b, e, sb, acc);
       }
+      for (; q < q1; q += 256) sg_quad(a, __ldcs(d4 + q), q << 2, b, e, sb, acc);
     } else {
       for (long long i = b + threadIdx.x; i < e; i += 256) sg_elem(a, __ldcs(a.data + i), i - sb, acc);
     }
     acc_fold(acc);
-    warp_reduce(acc);
+    double sum = acc.sum;
+    long long cnt = acc.cnt, first = acc.first[0];
+    batch_warp_reduce(sum, cnt, first);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) s_acc[w] = acc;
+    if (lane == 0) {
+      s_sum[w] = sum;
+      s_cnt[w] = cnt;
+      s_first[w] = first;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      Acc tot = s_acc[0];
-      for (int k = 1; k < 8; ++k) acc_merge(tot, s_acc[k]);
+      double tsum = s_sum[0];
+      long long tcnt = s_cnt[0], tfirst = s_first[0];
+      for (int k = 1; k < 8; ++k) {
+        tsum += s_sum[k];
+        tcnt += s_cnt[k];
+        tfirst = s_first[k] < tfirst ? s_first[k] : tfirst;
+      }
       if (nch == 1) {
-        a.sums[s] = tot.sum;
-        a.kept[s] = tot.cnt;
-        a.first_viol[s] = tot.first[0] == SG_NONE ? -1 : tot.first[0];
-        if (tot.first[0] != SG_NONE) atomicOr(&a.hdr->any_violation, 1u);
+        a.sums[s] = tsum;
+        a.kept[s] = tcnt;
+        a.first_viol[s] = tfirst == SG_NONE ? -1 : tfirst;
+        if (tfirst != SG_NONE) atomicOr(&a.hdr->any_violation, 1u);
         s_last = false;
       } else {
         ChunkPartial p;
-        p.sum = tot.sum; p.cnt = tot.cnt; p.first = tot.first[0];
+        p.sum = tsum; p.cnt = tcnt; p.first = tfirst;
         a.partials[cs + c] = p;
         __threadfence();
         s_last = atomicAdd(&a.seg_done[s], 1u) == (unsigned)(nch - 1);
@@ -333,19 +367,19 @@ extern "C" __global__ void __launch_bounds__(256) sg_batch(const BatchJitArgs a)
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
       __threadfence();
-      double sum = 0.0;
-      long long cnt = 0, first = SG_NONE;
+      double sum2 = 0.0;
+      long long cnt2 = 0, first2 = SG_NONE;
       for (long long k = 0; k < nch; ++k) {
         const ChunkPartial* p = &a.partials[cs + k];
-        sum += __ldcg(&p->sum);
-        cnt += __ldcg(&p->cnt);
+        sum2 += __ldcg(&p->sum);
+        cnt2 += __ldcg(&p->cnt);
         const long long f = __ldcg(&p->first);
-        first = f < first ? f : first;
+        first2 = f < first2 ? f : first2;
       }
-      a.sums[s] = sum;
-      a.kept[s] = cnt;
-      a.first_viol[s] = first == SG_NONE ? -1 : first;
-      if (first != SG_NONE) atomicOr(&a.hdr->any_violation, 1u);
+      a.sums[s] = sum2;
+      a.kept[s] = cnt2;
+      a.first_viol[s] = first2 == SG_NONE ? -1 : first2;
+      if (first2 != SG_NONE) atomicOr(&a.hdr->any_violation, 1u);
       a.seg_done[s] = 0;
     }
     __syncthreads();

@@ -5,6 +5,7 @@
 
 #include "sg_linalg_kernels.h"
 #include "sg_plan.h"
+#include "sg_runtime.h"
 
 namespace {
 
@@ -21,16 +22,26 @@ float u_eff_for(int prec, long long n) {
 
 }  // namespace
 
-size_t sg_linalg_scratch(sg_ctx*, Node* n) {
+bool sg_linalg_can_fuse(const Node* mm, const Node* chk) {
+  return mm->kind == NK::MATMUL && chk->kind == NK::CHECK && chk->ckind == SG_C_FREIVALDS &&
+         mm->prec != SG_PREC_F32_SIMT && chk->nvec >= 1 && chk->nvec <= 4 &&
+         mm->out.get() == chk->in[0].get() && mm->in[0].get() == chk->in[1].get() &&
+         mm->in[1].get() == chk->in[2].get() && mm->in[0]->rows == mm->in[0]->cols &&
+         mm->in[1]->rows == mm->in[1]->cols && mm->in[0]->rows == mm->in[1]->rows &&
+         mm->in[0]->rows > 0;
+}
+
+size_t sg_linalg_scratch(sg_ctx*, Node* n, Node* fused) {
   if (n->kind == NK::MATMUL) {
     if (n->prec == SG_PREC_F32_SIMT) return 0;
-    return sgk::gemm_tc_scratch_bytes((int)n->in[0]->rows, (int)n->in[1]->cols,
-                                      (int)n->in[0]->cols);
+    const size_t g = sgk::gemm_tc_scratch_bytes((int)n->in[0]->rows, (int)n->in[1]->cols,
+                                                (int)n->in[0]->cols);
+    return fused ? g + sgk::frv_fused_scratch_bytes((int)n->in[0]->rows) : g;
   }
   return sgk::freivalds_scratch_bytes((int)n->in[0]->rows, n->nvec);
 }
 
-sg_status sg_exec_linalg(sg_ctx* c, Node* n, void* rec, void* work, cudaError_t* e) {
+sg_status sg_exec_linalg(sg_ctx* c, Node* n, Node* fused, void* rec, void* work, cudaError_t* e) {
   if (n->kind == NK::MATMUL) {
     Value* A = n->in[0].get();
     Value* B = n->in[1].get();
@@ -54,12 +65,23 @@ sg_status sg_exec_linalg(sg_ctx* c, Node* n, void* rec, void* work, cudaError_t*
     const float* a = static_cast<const float*>(A->st->ptr);
     const float* b = static_cast<const float*>(B->st->ptr);
     float* cc = static_cast<float*>(Cv->st->ptr);
+    // a planted element error (contract testing) goes to the next tc product
+    const int ir = (int)c->mm_inject.row, ic = (int)c->mm_inject.col;
+    const float id = c->mm_inject.delta;
+    if (n->prec != SG_PREC_F32_SIMT) c->mm_inject.row = c->mm_inject.col = -1;
+    if (fused) {
+      *e = sgk::launch_gemm_tc_checked(a, b, cc, N, n->prec == SG_PREC_F16_TC, fused->seed,
+                                       fused->nvec, (float)fused->tol, u_eff_for(n->prec, N),
+                                       work, static_cast<sgk::FreivaldsResult*>(rec), c->stream,
+                                       &c->prof, &c->kernels, ir, ic, id);
+      return SG_OK;
+    }
     if (n->prec == SG_PREC_F32_SIMT) {
       *e = sgk::launch_gemm_f32(a, K, b, N, cc, N, M, N, K, false, c->stream, &c->prof);
       c->kernels += 1;
     } else {
       *e = sgk::launch_gemm_tc(a, K, b, N, cc, N, M, N, K, n->prec == SG_PREC_F16_TC, false,
-                               work, c->stream, &c->prof, &c->kernels);
+                               work, c->stream, &c->prof, &c->kernels, ir, ic, id);
     }
     return SG_OK;
   }
@@ -78,8 +100,9 @@ sg_status sg_exec_linalg(sg_ctx* c, Node* n, void* rec, void* work, cudaError_t*
   return SG_OK;
 }
 
-bool sg_linalg_result(sg_ctx*, Node* n, const void* rec, long long* row, double* observed) {
-  if (n->kind != NK::CHECK) return false;
+bool sg_linalg_result(sg_ctx*, Node* n, Node* fused, const void* rec, long long* row,
+                      double* observed) {
+  if (n->kind != NK::CHECK && !fused) return false;
   sgk::FreivaldsResult r;
   memcpy(&r, rec, sizeof r);
   *observed = r.max_ratio;

@@ -14,10 +14,13 @@ cudaError_t launch_gemm_f32(const float* A, int lda, const float* B, int ldb, fl
 // binary32 accumulation in tensor memory.  beta = 0: C = A B; beta = 1:
 // C = C - A B (the elimination update).  a16 / bt16 are scratch operand
 // copies (M x Kp and N x Kp, K-major, Kp = K rounded up to 64).
+// inj_row / inj_col >= 0: contract testing, inj_delta is added to that
+// product element before it is stored.
 size_t gemm_tc_scratch_bytes(int M, int N, int K);
 cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
                            int M, int N, int K, bool fp16, bool subtract, void* scratch,
-                           cudaStream_t s, Prof* prof, int64_t* kernels);
+                           cudaStream_t s, Prof* prof, int64_t* kernels, int inj_row = -1,
+                           int inj_col = -1, float inj_delta = 0.0f);
 
 // Freivalds' check of C = A B for square N x N matrices with `nvec`
 // Rademacher vectors drawn from SplitMix64 (seed); tau_i = c u_eff sigma_i.
@@ -31,5 +34,39 @@ cudaError_t launch_freivalds(const float* A, const float* B, const float* C, int
                              unsigned long long seed, int nvec, float c, float u_eff,
                              void* scratch, FreivaldsResult* res, cudaStream_t s,
                              Prof* prof, int64_t* kernels);
+
+// Freivalds' check fused into the tensor-core product of square N x N
+// matrices: the cast of B also forms the partial sums of B r and |B_k|^2,
+// the cast of A those of A (B r) and (A.A) t, and the GEMM epilogue those of
+// C r, so the check reads no matrix a second time.  Partial sums are over
+// column stripes (kFrvStripeB of B, kFrvStripeA of A, kFrvTileC of C) and are
+// added in a fixed order by the final per-row test.
+constexpr int kFrvStripeB = 512;
+constexpr int kFrvStripeA = 1024;
+constexpr int kFrvTileC = 256;
+struct FrvFused {
+  float4* r4;      // [N] the nvec Rademacher vectors, entry j of each
+  float4* br4;     // [N] B r
+  float4* t4;      // [N] (B r)_k^2 + |B_k|^2
+  float* pb;       // [nsb][N][5] partial B r and |B_k|^2
+  float* pzq;      // [nsa][N][8] partial A (B r) and (A.A) t
+  float4* pw;      // [nsc][N] partial C r
+  int nsb, nsa, nsc;
+  size_t bytes;
+};
+FrvFused frv_fused_layout(void* scratch, int N);
+size_t frv_fused_scratch_bytes(int N);
+cudaError_t launch_frv_vectors(const FrvFused& f, int N, int nvec, unsigned long long seed,
+                               cudaStream_t st);
+cudaError_t launch_frv_b_reduce(const FrvFused& f, int N, cudaStream_t st);
+cudaError_t launch_frv_check_fused(const FrvFused& f, int N, int nvec, float c, float u_eff,
+                                   FreivaldsResult* res, cudaStream_t st);
+// C = A B on the tensor cores with the fused check (scratch: gemm_tc_scratch_bytes
+// followed by frv_fused_scratch_bytes)
+cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int N, bool fp16,
+                                   unsigned long long seed, int nvec, float c, float u_eff,
+                                   void* scratch, FreivaldsResult* res, cudaStream_t s,
+                                   Prof* prof, int64_t* kernels, int inj_row = -1,
+                                   int inj_col = -1, float inj_delta = 0.0f);
 
 }  // namespace sgk

@@ -61,6 +61,7 @@ struct Pass {
   Node* main = nullptr;
   Node* chk_sorted = nullptr;
   Node* chk_perm = nullptr;
+  Node* chk_frv = nullptr;    // MATMUL: built-in Freivalds check folded in
 };
 
 bool is_f32_stream_node(const Node* n) {
@@ -305,6 +306,13 @@ struct Planner {
             }
             P.kind = PK::CHECK_PERM;
           } else {
+            // fold into the tensor-core product that produced the checked value
+            if (c->fusion == SG_FUSE_ON && !passes.empty() && passes.back().kind == PK::MATMUL &&
+                !passes.back().chk_frv && sg_linalg_can_fuse(passes.back().main, n)) {
+              passes.back().chk_frv = n;
+              passes.back().nodes.push_back(n);
+              continue;
+            }
             P.kind = PK::FREIVALDS;
           }
           break;
@@ -531,7 +539,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
       case PK::CHECK_SORTED:
       case PK::CHECK_PERM: work = std::max(work, sgk::check_scratch_bytes()); break;
       case PK::MATMUL:
-      case PK::FREIVALDS: work = std::max(work, sg_linalg_scratch(c, P.main)); break;
+      case PK::FREIVALDS: work = std::max(work, sg_linalg_scratch(c, P.main, P.chk_frv)); break;
     }
   }
   sg_status st = ensure_scratch(c, res_bytes + work);
@@ -668,7 +676,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
       }
       case PK::MATMUL:
       case PK::FREIVALDS:
-        status = sg_exec_linalg(c, P.main, rec, dwork, &e);
+        status = sg_exec_linalg(c, P.main, P.chk_frv, rec, dwork, &e);
         break;
     }
   }
@@ -751,8 +759,8 @@ sg_status sg_execute_pending(sg_ctx* c) {
         case PK::FREIVALDS: {
           double observed = 0.0;
           long long row = -1;
-          if (sg_linalg_result(c, P.main, rec, &row, &observed))
-            record_violation(c, P.main, row, observed, &have, &cstatus);
+          if (sg_linalg_result(c, P.main, P.chk_frv, rec, &row, &observed))
+            record_violation(c, P.chk_frv ? P.chk_frv : P.main, row, observed, &have, &cstatus);
           break;
         }
       }
@@ -807,8 +815,10 @@ sg_status sg_describe_pending(sg_ctx* c, std::string* out) {
       case PK::CHECK_SORTED: snprintf(buf, sizeof buf, "check_sorted n=%lld\n", (long long)P.n); break;
       case PK::CHECK_PERM: snprintf(buf, sizeof buf, "check_perm n=%lld\n", (long long)P.n); break;
       case PK::MATMUL:
-        snprintf(buf, sizeof buf, "matmul %lldx%lldx%lld prec=%d\n", (long long)P.main->in[0]->rows,
-                 (long long)P.main->in[0]->cols, (long long)P.main->in[1]->cols, P.main->prec);
+        snprintf(buf, sizeof buf, "matmul %lldx%lldx%lld prec=%d%s\n",
+                 (long long)P.main->in[0]->rows, (long long)P.main->in[0]->cols,
+                 (long long)P.main->in[1]->cols, P.main->prec,
+                 P.chk_frv ? " +freivalds(fused)" : "");
         break;
       case PK::FREIVALDS:
         snprintf(buf, sizeof buf, "freivalds n=%lld nvec=%d\n", (long long)P.main->in[0]->rows,

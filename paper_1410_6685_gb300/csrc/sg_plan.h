@@ -13,8 +13,12 @@ sg_status sg_execute_pending(sg_ctx* c);
 sg_status sg_describe_pending(sg_ctx* c, std::string* out);
 
 // Matrix product and Freivalds check kernels (sg_linalg.cpp).
-size_t sg_linalg_scratch(sg_ctx* c, Node* n);
-sg_status sg_exec_linalg(sg_ctx* c, Node* n, void* rec, void* work, cudaError_t* e);
+// fused: a built-in Freivalds check folded into the product `n` (or nullptr)
+size_t sg_linalg_scratch(sg_ctx* c, Node* n, Node* fused);
+sg_status sg_exec_linalg(sg_ctx* c, Node* n, Node* fused, void* rec, void* work, cudaError_t* e);
+// a product whose Freivalds check can be folded into it
+bool sg_linalg_can_fuse(const Node* mm, const Node* chk);
 // True when the node's check failed; fills the violating row and the
 // observed |z_i - w_i| / tau_i.
-bool sg_linalg_result(sg_ctx* c, Node* n, const void* rec, long long* row, double* observed);
+bool sg_linalg_result(sg_ctx* c, Node* n, Node* fused, const void* rec, long long* row,
+                      double* observed);

@@ -141,6 +141,10 @@ struct sg_ctx {
   void* host_res = nullptr;            // pinned host copy of pass results
   size_t host_res_bytes = 0;
   sgk::SortInject inject{};            // contract-test fault for the next sort
+  struct {
+    int64_t row = -1, col = -1;
+    float delta = 0.0f;
+  } mm_inject;                          // contract-test fault for the next tc product
   sgk::Prof prof;                      // per-kernel event tracing
   BatchPlanCache batch;                // captured batched launches
   SchedState schedst;                  // schedule log and cost model

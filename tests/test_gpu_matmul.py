@@ -150,3 +150,60 @@ def test_contract_modes_matmul(env):
     mc, keep = gemm(env, A, B, 1, flush=False)
     assert "freivalds" in sg.sg_plan_describe(ctx)
     sg.sg_flush(ctx)
+
+
+def test_fused_check_in_plan(env):
+    """The built-in Freivalds check of a square tensor-core product is folded
+    into the product (casts + epilogue); the binary32 product keeps the
+    stand-alone check, and so does a product with fusion switched off."""
+    sg, ctx, _ = env
+    A, B = inputs.matmul_inputs(256)
+    for prec, fused in [(1, True), (2, True), (0, False)]:
+        mc, keep = gemm(env, A, B, prec, flush=False)
+        d = sg.sg_plan_describe(ctx)
+        assert ("+freivalds(fused)" in d) == fused, d
+        assert ("freivalds n=256" in d) == (not fused), d
+        sg.sg_flush(ctx)
+    sg.sg_set_fusion(ctx, sg.SG_FUSE_OFF)
+    try:
+        mc, keep = gemm(env, A, B, 1, flush=False)
+        assert "freivalds n=256" in sg.sg_plan_describe(ctx)
+        sg.sg_flush(ctx)
+    finally:
+        sg.sg_set_fusion(ctx, sg.SG_FUSE_ON)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n", [512, 1000])
+@pytest.mark.parametrize("fusion", [True, False])
+def test_builtin_check_flags_planted_element(env, prec, n, fusion):
+    """An error planted in one product element (host-chosen, applied by the
+    kernel's epilogue before the store) is reported by the built-in
+    postcondition at its row, in the fused and the stand-alone forms; the
+    oracle, given the product read back, names the same row."""
+    sg, ctx, _ = env
+    A, B = inputs.matmul_inputs(n)
+    u_eff = (2.0 ** -8 if prec == 1 else 2.0 ** -10) + 2.0 ** -24 * math.sqrt(n)
+    mc, keep = gemm(env, A, B, prec)
+    C0 = read(env, mc, n, n)
+    first, gap, tau = oracle.freivalds(A, B, C0, seed=6, nvec=4, c=8.0, u_eff=u_eff)
+    assert first == -1
+    sg.sg_set_fusion(ctx, sg.SG_FUSE_ON if fusion else sg.SG_FUSE_OFF)
+    try:
+        for row, col in [(0, 0), (n // 3, n - 1), (n - 1, 17)]:
+            delta = np.float32(4 * tau[row])
+            sg.sg_debug_inject_matmul(ctx, row, col, float(delta))
+            mc, keep = gemm(env, A, B, prec, flush=False)
+            with pytest.raises(sg.SgError) as e:
+                sg.sg_flush(ctx)
+            assert e.value.status == sg.SG_ERR_POSTCONDITION
+            v = sg.sg_last_violation(ctx)
+            assert v.kind == sg.SG_C_FREIVALDS and v.first_index == row
+            assert oracle.freivalds(A, B, C0 + np.where(
+                (np.arange(n)[:, None] == row) & (np.arange(n)[None, :] == col), delta,
+                np.float32(0)), seed=6, nvec=4, c=8.0, u_eff=u_eff)[0] == row
+    finally:
+        sg.sg_set_fusion(ctx, sg.SG_FUSE_ON)
+    # the injection is consumed: the next product is clean again
+    mc, keep = gemm(env, A, B, prec)
+    assert np.array_equal(read(env, mc, n, n), C0)
