@@ -35,7 +35,7 @@ static_assert(kFrvTileC == TN, "the fused check keeps one C r partial per column
 constexpr int A_BYTES = TM * TK * 2;            // 16 KB
 constexpr int B_BYTES = TN * TK * 2;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
-constexpr int R_BYTES = TN * 16;                // the fused check's r entries of the tile
+constexpr int R_BYTES = 4 * TN * 16;            // the fused check's r entries, one copy per epilogue warp
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + R_BYTES;
 constexpr unsigned kWaitLimit = 1u << 26;
 
@@ -128,7 +128,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ma,
+// bounded wait that also gives up as soon as another role of the CTA has
+// raised the abort flag (so one failed wait cannot leave the others spinning
+// through every remaining tile)
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, int* err,
+                                             volatile int* abort_flag) {
+  for (unsigned i = 0; i < kWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 255) == 255 && *abort_flag) return false;
+  }
+  atomicExch(err, 1);
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent kernel, one CTA per SM, tiles t = blockIdx.x + i * gridDim.x
+// (row-block t / nN, column-block t % nN):
+//   warp 0, one lane : TMA producer over all of the CTA's tiles;
+//   warp 1, one lane : MMA issuer; accumulators alternate between two
+//                      256-column halves of the 512 TMEM columns, so the
+//                      epilogue of one tile overlaps the main loop of the next;
+//   warps 2..5       : epilogue, warp w reads TMEM lanes 32 (w % 4) .. + 31;
+//                      after draining an accumulator they release it to the
+//                      MMA issuer through an mbarrier.
+__global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ma,
                                                     const __grid_constant__ CUtensorMap mb,
                                                     float* __restrict__ C, int ldc, int M,
                                                     int N, int KB, uint32_t id, int subtract,
@@ -139,25 +174,33 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars[0..S): full, bars[S..2S): empty, bars[2S]: done; then the TMEM slot
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  // bars[0..S): full, [S..2S): empty, [2S, 2S+2): accumulator full,
+  // [2S+2, 2S+4): accumulator empty, [2S+4]: drain; then the TMEM slot and
+  // the abort flag
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float4* s_r = reinterpret_cast<float4*>(smem + STAGES * STAGE_BYTES + 256);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int nN = (N + TN - 1) / TN, nM = (M + TM - 1) / TM;
+  const int ntiles = nN * nM;
+  const uint32_t tfull0 = smem_u32(&bars[2 * STAGES]), tempty0 = smem_u32(&bars[2 * STAGES + 2]);
+  const uint32_t drain_bar = smem_u32(&bars[2 * STAGES + 4]);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < 2 * STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    mbar_init(tfull0, 1);
+    mbar_init(tfull0 + 8, 1);
+    mbar_init(tempty0, 4);
+    mbar_init(tempty0 + 8, 4);
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  if (frv_r) {
-    for (int j = threadIdx.x; j < TN; j += blockDim.x)
-      s_r[j] = n0 + j < N ? frv_r[n0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(TN)
+                 "r"(2 * TN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -165,104 +208,146 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t done_bar = smem_u32(&bars[2 * STAGES]);
 
-  if (warp == 0 && lane == 0) {
-    // producer
-    for (int kb = 0; kb < KB; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (kb >= STAGES && !mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1u, err)) break;
-      const uint32_t full = smem_u32(&bars[s]);
-      mbar_expect_tx(full, STAGE_BYTES);
-      const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
-      tma_load_2d(a_dst, &ma, kb * TK, m0, full);
-      tma_load_2d(a_dst + A_BYTES, &mb, kb * TK, n0, full);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    bool ok = true;
-    for (int kb = 0; kb < KB && ok; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      ok = mbar_wait(smem_u32(&bars[s]), ph, err);
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_base = smem_u32(smem + s * STAGE_BYTES);
-      const uint64_t da = sdesc(a_base), db = sdesc(a_base + A_BYTES);
-#pragma unroll
-      for (int k = 0; k < TK / 16; ++k) {
-        // advance 16 elements (32 bytes) along K inside the swizzled rows
-        umma(tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), id, (kb | k) != 0);
-      }
-      umma_commit(smem_u32(&bars[STAGES + s]));
-    }
-    umma_commit(done_bar);
-  }
-  __syncwarp();
-
-  // epilogue: wait for the accumulator, then rows 32*warp + lane
-  const bool ready = mbar_wait(done_bar, 0, err);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int row = m0 + warp * 32 + lane;
-  if (ready) {
-    // fused Freivalds check: this row's partial C r over the tile's columns
-    float4 wacc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 1
-    for (int c = 0; c < TN / 32; ++c) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-      const int col0 = n0 + c * 32;
-      // contract testing: a planted error in one product element, applied
-      // before it is stored (and before the fused check sees it)
-      if (row == inj_row && inj_col >= col0 && inj_col < col0 + 32) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (col0 + j == inj_col) r[j] = __float_as_uint(__uint_as_float(r[j]) + inj_delta);
-      }
-      if (frv_r) {
-        // r of columns past N is zero in s_r (their accumulator entries are too)
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float4 rj = s_r[c * 32 + j];
-          const float v = __uint_as_float(r[j]);
-          wacc.x = fmaf(v, rj.x, wacc.x);
-          wacc.y = fmaf(v, rj.y, wacc.y);
-          wacc.z = fmaf(v, rj.z, wacc.z);
-          wacc.w = fmaf(v, rj.w, wacc.w);
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int m0 = (t / nN) * TM, n0 = (t % nN) * TN;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (it >= STAGES &&
+              !mbar_wait_ab(smem_u32(&bars[STAGES + s]), ph ^ 1u, err, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t full = smem_u32(&bars[s]);
+          mbar_expect_tx(full, STAGE_BYTES);
+          const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
+          tma_load_2d(a_dst, &ma, kb * TK, m0, full);
+          tma_load_2d(a_dst + A_BYTES, &mb, kb * TK, n0, full);
         }
       }
-      if (row < M) {
-        float* cp = C + (size_t)row * ldc + col0;
-        if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-            if (subtract) {
-              const float4 o = *reinterpret_cast<const float4*>(cp + j);
-              v = make_float4(o.x - v.x, o.y - v.y, o.z - v.z, o.w - v.w);
-            }
-            *reinterpret_cast<float4*>(cp + j) = v;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      int it = 0, tl = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+        const int acc = tl & 1;
+        if (tl >= 2 && !mbar_wait_ab(tempty0 + 8 * acc, (uint32_t)((tl >> 1) - 1) & 1u, err,
+                                     abort_flag))
+          break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(acc * TN);
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (!mbar_wait_ab(smem_u32(&bars[s]), ph, err, abort_flag)) {
+            ok = false;
+            break;
           }
-        } else {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_base = smem_u32(smem + s * STAGE_BYTES);
+          const uint64_t da = sdesc(a_base), db = sdesc(a_base + A_BYTES);
+#pragma unroll
+          for (int k = 0; k < TK / 16; ++k) {
+            // advance 16 elements (32 bytes) along K inside the swizzled rows
+            umma(dacc, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), id, (kb | k) != 0);
+          }
+          umma_commit(smem_u32(&bars[STAGES + s]));
+        }
+        if (ok) umma_commit(tfull0 + 8 * acc);
+      }
+      // completes when every MMA issued above has finished
+      umma_commit(drain_bar);
+    }
+  } else {
+    // epilogue warps 2..5
+    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    float4* s_rw = s_r + (warp - 2) * TN;
+    int tl = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+      const int m0 = (t / nN) * TM, n0 = (t % nN) * TN;
+      const int acc = tl & 1;
+      if (frv_r) {
+        // each epilogue warp keeps its own copy, so no barrier spans the warps
+        __syncwarp();
+        for (int j = lane; j < TN; j += 32)
+          s_rw[j] = n0 + j < N ? frv_r[n0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+      }
+      if (!mbar_wait_ab(tfull0 + 8 * acc, (uint32_t)(tl >> 1) & 1u, err, abort_flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = m0 + q * 32 + lane;
+      float4 wacc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+      for (int c = 0; c < TN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TN + c * 32), r);
+        if (c == TN / 32 - 1) {
+          // the accumulator is drained: hand it back to the MMA issuer
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
+        }
+        const int col0 = n0 + c * 32;
+        // contract testing: a planted error in one product element, applied
+        // before it is stored (and before the fused check sees it)
+        if (row == inj_row && inj_col >= col0 && inj_col < col0 + 32) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j == inj_col) r[j] = __float_as_uint(__uint_as_float(r[j]) + inj_delta);
+        }
+        if (frv_r) {
+          // r of columns past N is zero in s_r (their accumulator entries are too)
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            if (col0 + j < N) {
-              const float v = __uint_as_float(r[j]);
-              cp[j] = subtract ? cp[j] - v : v;
+            const float4 rj = s_rw[c * 32 + j];
+            const float v = __uint_as_float(r[j]);
+            wacc.x = fmaf(v, rj.x, wacc.x);
+            wacc.y = fmaf(v, rj.y, wacc.y);
+            wacc.z = fmaf(v, rj.z, wacc.z);
+            wacc.w = fmaf(v, rj.w, wacc.w);
+          }
+        }
+        if (row < M) {
+          float* cp = C + (size_t)row * ldc + col0;
+          if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                     __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+              if (subtract) {
+                const float4 o = *reinterpret_cast<const float4*>(cp + j);
+                v = make_float4(o.x - v.x, o.y - v.y, o.z - v.z, o.w - v.w);
+              }
+              *reinterpret_cast<float4*>(cp + j) = v;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (col0 + j < N) {
+                const float v = __uint_as_float(r[j]);
+                cp[j] = subtract ? cp[j] - v : v;
+              }
             }
           }
         }
       }
+      if (frv_r && row < M) frv_pw[(size_t)(t % nN) * M + row] = wacc;
     }
-    if (frv_r && row < M) frv_pw[(size_t)blockIdx.x * M + row] = wacc;
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 2) {
+    // every MMA has completed before the tensor memory is released
+    mbar_wait(drain_bar, 0, err);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN)
                  : "memory");
   }
 }
@@ -514,6 +599,21 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int Kp, int box_rows, 
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// one CTA per SM (the pipeline's shared memory allows no second), at most
+// one per tile
+int persistent_grid(int M, int N) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+      sms = 1;
+  }
+  const long long tiles = (long long)((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+  return (int)std::max<long long>(1, std::min<long long>(tiles, sms));
+}
+
 }  // namespace
 
 size_t gemm_tc_scratch_bytes(int M, int N, int K) {
@@ -557,9 +657,9 @@ cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, flo
   CUtensorMap ma, mb;
   if (!make_map(&ma, a16, M, Kp, TM, fp16) || !make_map(&mb, bt16, N, Kp, TN, fp16))
     return cudaErrorInvalidValue;
-  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+  const int grid = persistent_grid(M, N);
   prof_begin(prof, fp16 ? "gemm_tc_f16" : "gemm_tc_bf16", s);
-  k_gemm_tc<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, Kp / TK, idesc(fp16),
+  k_gemm_tc<<<grid, 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, Kp / TK, idesc(fp16),
                                           subtract ? 1 : 0, err, nullptr, nullptr, inj_row,
                                           inj_col, inj_delta);
   prof_end(prof, s);
@@ -601,9 +701,9 @@ cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int
   CUtensorMap ma, mb;
   if (!make_map(&ma, a16, N, Kp, TM, fp16) || !make_map(&mb, bt16, N, Kp, TN, fp16))
     return cudaErrorInvalidValue;
-  dim3 grid((N + TN - 1) / TN, (N + TM - 1) / TM);
+  const int grid = persistent_grid(N, N);
   prof_begin(prof, fp16 ? "gemm_tc_f16" : "gemm_tc_bf16", s);
-  k_gemm_tc<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, C, N, N, N, Kp / TK, idesc(fp16), 0, err, f.r4,
+  k_gemm_tc<<<grid, 192, SMEM_BYTES, s>>>(ma, mb, C, N, N, N, Kp / TK, idesc(fp16), 0, err, f.r4,
                                           f.pw, inj_row, inj_col, inj_delta);
   prof_end(prof, s);
   prof_begin(prof, "freivalds_fused", s);

@@ -151,12 +151,17 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
   if (((uintptr_t)in & 15) == 0) {
     const long long nv = n >> 2;
     start = nv << 2;
-    for (long long v = tid; v < nv; v += stride) {
-      const int4 q = __ldg(reinterpret_cast<const int4*>(in) + v);
-      count(q.x);
-      count(q.y);
-      count(q.z);
-      count(q.w);
+    const int4* in4 = reinterpret_cast<const int4*>(in);
+    long long v = tid;
+    // two 16-byte loads in flight per thread before their keys are counted
+    for (; v + stride < nv; v += 2 * stride) {
+      const int4 q0 = __ldcs(in4 + v), q1 = __ldcs(in4 + v + stride);
+      count(q0.x); count(q0.y); count(q0.z); count(q0.w);
+      count(q1.x); count(q1.y); count(q1.z); count(q1.w);
+    }
+    for (; v < nv; v += stride) {
+      const int4 q = __ldcs(in4 + v);
+      count(q.x); count(q.y); count(q.z); count(q.w);
     }
   }
   for (long long i = start + tid; i < n; i += stride) count(in[i]);
@@ -219,6 +224,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   int key[kKpt];
   const long long wbase = base + (long long)w * kWarpKeys + lane;
   constexpr bool full = FULL;
+  const int lbase = w * kWarpKeys + lane;   // this thread's keys: s_keys[lbase + 32 r]
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
     const long long idx = wbase + r * 32;
@@ -257,7 +263,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
     __syncwarp();
     if (ok && before == 0) s_whist[w][d] = prev + __popc(peers);
     __syncwarp();
-    s_rank[w * kWarpKeys + r * 32 + lane] = (unsigned short)(prev + before);
+    s_rank[lbase + r * 32] = (unsigned short)(prev + before);
   }
   __syncthreads();
 
@@ -283,7 +289,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   for (int r = 0; r < kKpt; ++r) {
     if (full || (wbase + r * 32) < n) {
       const unsigned d = digit_of<LAST>(key[r], shift);
-      s_keys[s_start[d] + s_whist[w][d] + s_rank[w * kWarpKeys + r * 32 + lane]] = key[r];
+      s_keys[s_start[d] + s_whist[w][d] + s_rank[lbase + r * 32]] = key[r];
     }
   }
   __syncthreads();
@@ -494,7 +500,7 @@ cudaError_t launch_sort(const int32_t* in, int32_t* out, long long n, bool contr
   cudaError_t e = cudaMemsetAsync(base, 0, L.zero_bytes, s);
   if (e != cudaSuccess) return e;
   prof_begin(prof, "radix_hist", s);
-  k_radix_hist<<<grid_for((n + 3) / 4 / 8, num_sms, 4), 256, 0, s>>>(in, n, h, res);
+  k_radix_hist<<<grid_for((n + 3) / 4 / 8, num_sms, 8), 256, 0, s>>>(in, n, h, res);
   prof_end(prof, s);
   const unsigned ntiles = (unsigned)((n + kTile - 1) / kTile);
   prof_begin(prof, "onesweep", s);
