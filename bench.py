@@ -63,31 +63,105 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region.
+
+    NVML through ctypes every ~2 ms when libnvidia-ml is loadable (the timed
+    region lasts milliseconds), else nvidia-smi every 200 ms from just before
+    to just after the region."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, local_rank):
+    def __init__(self, local_rank, torch=None):
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         ids = [v for v in vis.split(",") if v.strip()]
         self.gpu = ids[local_rank] if local_rank < len(ids) and ids[local_rank].isdigit() \
             else str(local_rank)
-        self.proc = None
-        self.f = None
+        self.local_rank = local_rank
+        self.torch = torch
+        self.samples, self.mx, self.reasons = [], 0.0, set()
+        self.nvml = self._nvml_handle()
+        self.proc = self.f = self.thread = None
+        self.running = False
+
+    def _nvml_handle(self):
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            dev = ctypes.c_void_p()
+            bus = None
+            if self.torch is not None:
+                pr = self.torch.cuda.get_device_properties(self.local_rank)
+                if all(hasattr(pr, k) for k in ("pci_domain_id", "pci_bus_id", "pci_device_id")):
+                    bus = "%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+            if bus is not None:
+                rc = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(dev))
+            else:
+                rc = lib.nvmlDeviceGetHandleByIndex_v2(int(self.gpu), ctypes.byref(dev))
+            if rc != 0:
+                return None
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) == 0:
+                self.mx = float(mx.value)
+            fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            return (lib, dev, fn)
+        except Exception:
+            return None
+
+    def _poll(self):
+        import ctypes
+        lib, dev, fn = self.nvml
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while self.running:
+            if lib.nvmlDeviceGetClockInfo(dev, 1, ctypes.byref(clk)) == 0:
+                self.samples.append(float(clk.value))
+            if fn(dev, ctypes.byref(rs)) == 0:
+                for bit, name in self.REASONS.items():
+                    if rs.value & bit:
+                        self.reasons.add(name)
+            time.sleep(0.002)
 
     def start(self):
+        if self.nvml:
+            import threading
+            self.running = True
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            while not self.samples and self.thread.is_alive():
+                time.sleep(0.001)
+            return
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
                  "-i", self.gpu, "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and os.path.getsize(self.f.name) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            time.sleep(0.004)
+            self.running = False
+            self.thread.join()
+            if not self.samples:
+                return None
+            return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.mx,
+                    "reasons": sorted(self.reasons), "samples": len(self.samples),
+                    "source": "nvml"}
         if not self.proc:
             return None
+        size0 = os.path.getsize(self.f.name)
+        t0 = time.time()
+        while time.time() - t0 < 1.0 and os.path.getsize(self.f.name) == size0:
+            time.sleep(0.02)   # one sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(5)
@@ -111,7 +185,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms, from just before to just after"}
 
 
 def oracle_step(keys):
@@ -354,7 +428,7 @@ def main():
     for _ in range(args.warmup):
         step()
     # timed region (kernel tracing on: events bracket each launch on `stream`)
-    clocks = Clocks(local)
+    clocks = Clocks(local, torch)
     sg.sg_profile_enable(ctx, True)
     sg.sg_profile_report(ctx, reset=True)
     k0 = sg.sg_kernel_count(ctx)
