@@ -73,6 +73,9 @@ def lib():
             "or_first_unsorted_i32": (i64, [vp, i64]),
             "or_same_multiset_i32": (i32, [vp, vp, i64]),
             "or_matmul_f64": (None, [vp, vp, i64, i64, i64, vp]),
+            "or_transpose_f32": (None, [vp, i64, i64, vp]),
+            "or_matvec_f64": (None, [vp, i64, i64, vp, vp]),
+            "or_vecmat_f64": (None, [vp, vp, i64, i64, vp]),
             "or_matmul_rows_f64": (None, [vp, vp, i64, i64, i64, vp, i64, vp]),
             "or_splitmix64": (u64, [u64]),
             "or_rademacher": (dbl, [u64, i64, i64, i64]),
@@ -211,6 +214,37 @@ def same_multiset_i32(a, b) -> bool:
     if r < 0:
         raise MemoryError
     return bool(r)
+
+
+def transpose_f32(A) -> np.ndarray:
+    """Sec. 3.4 `transpose` (Listing 1): At[j][i] = A[i][j]."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    r, c = A.shape
+    At = np.empty((c, r), dtype=np.float32)
+    lib().or_transpose_f32(_p(A), r, c, _p(At))
+    return At
+
+
+def matvec_f64(A, x) -> np.ndarray:
+    """Sec. 3.4 `right_multiply` (Listing 1): y = A x in binary64."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    r, c = A.shape
+    assert x.shape == (c,)
+    y = np.empty(r, dtype=np.float64)
+    lib().or_matvec_f64(_p(A), r, c, _p(x), _p(y))
+    return y
+
+
+def vecmat_f64(x, A) -> np.ndarray:
+    """Sec. 3.4 `left_multiply`: y = x^T A in binary64."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    r, c = A.shape
+    assert x.shape == (r,)
+    y = np.empty(c, dtype=np.float64)
+    lib().or_vecmat_f64(_p(x), _p(A), r, c, _p(y))
+    return y
 
 
 def matmul_f64(A, B) -> np.ndarray:

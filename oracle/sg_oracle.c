@@ -234,6 +234,35 @@ int or_same_multiset_i32(const int32_t* a, const int32_t* b, int64_t n) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Matrix `transpose` (Sec. 3.4; Listing 1): At[j][i] = A[i][j], row-major,
+ * rows x cols in, cols x rows out.                                          */
+
+void or_transpose_f32(const float* A, int64_t rows, int64_t cols, float* At) {
+  for (int64_t i = 0; i < rows; ++i)
+    for (int64_t j = 0; j < cols; ++j) At[j * rows + i] = A[i * cols + j];
+}
+
+/* `right_multiply` (Sec. 3.4; Listing 1): y = A x, y[i] = sum_j A[i][j] x[j];
+ * `left_multiply`: y = x^T A, y[j] = sum_i x[i] A[i][j].  Binary32 inputs
+ * widened exactly, products and sums in binary64, index ascending.          */
+
+void or_matvec_f64(const float* A, int64_t rows, int64_t cols, const float* x, double* y) {
+  for (int64_t i = 0; i < rows; ++i) {
+    double s = 0.0;
+    for (int64_t j = 0; j < cols; ++j) s += (double)A[i * cols + j] * (double)x[j];
+    y[i] = s;
+  }
+}
+
+void or_vecmat_f64(const float* x, const float* A, int64_t rows, int64_t cols, double* y) {
+  for (int64_t j = 0; j < cols; ++j) {
+    double s = 0.0;
+    for (int64_t i = 0; i < rows; ++i) s += (double)x[i] * (double)A[i * cols + j];
+    y[j] = s;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Matrix `multiply` (Sec. 3.4): C = A B, row-major, binary32 inputs widened
  * exactly to binary64, products and sums in binary64, k ascending.          */
 

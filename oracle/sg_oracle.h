@@ -62,6 +62,13 @@ void    or_matmul_f64(const float* A, const float* B, int64_t M, int64_t K,
 void    or_matmul_rows_f64(const float* A, const float* B, int64_t M, int64_t K,
                            int64_t N, const int64_t* rows, int64_t nrows,
                            double* C);
+/* ---- transpose and matrix-vector products (Sec. 3.4 `transpose`,
+ *      `right_multiply`, `left_multiply`; Listing 1) ---- */
+void    or_transpose_f32(const float* A, int64_t rows, int64_t cols, float* At);
+void    or_matvec_f64(const float* A, int64_t rows, int64_t cols, const float* x,
+                      double* y);
+void    or_vecmat_f64(const float* x, const float* A, int64_t rows, int64_t cols,
+                      double* y);
 uint64_t or_splitmix64(uint64_t state_after_increment);
 double  or_rademacher(uint64_t seed, int64_t v, int64_t n, int64_t j);
 int64_t or_freivalds(const float* A, const float* B, const float* C, int64_t N,

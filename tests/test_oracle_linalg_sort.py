@@ -346,3 +346,50 @@ def test_adam_first_step_hand_computed():
     # bias-corrected first step moves each weight by lr * g / (|g| + eps')
     assert np.allclose(P, [0.9, -1.9], atol=1e-6)
     assert np.allclose(m, [0.05, -0.025]) and np.allclose(v, [0.00025, 0.0000625])
+
+
+# ---- transpose and matrix-vector products (Sec. 3.4, Listing 1) ----
+
+def test_transpose_brute_force_and_involution():
+    g = np.random.default_rng(21)
+    for r, c in [(1, 1), (1, 7), (7, 1), (3, 5), (16, 9)]:
+        A = g.standard_normal((r, c)).astype(np.float32)
+        At = oracle.transpose_f32(A)
+        assert At.shape == (c, r)
+        for i in range(r):
+            for j in range(c):
+                assert At[j, i] == A[i, j]
+        assert np.array_equal(oracle.transpose_f32(At), A)   # (A^T)^T = A
+
+
+def test_matvec_closed_forms():
+    g = np.random.default_rng(22)
+    n = 37
+    x = g.standard_normal(n).astype(np.float32)
+    # identity: y = x exactly; permutation P: y = P x exactly
+    assert np.array_equal(oracle.matvec_f64(np.eye(n, dtype=np.float32), x), x.astype(np.float64))
+    p = g.permutation(n)
+    P = np.eye(n, dtype=np.float32)[p]
+    assert np.array_equal(oracle.matvec_f64(P, x), x[p].astype(np.float64))
+    # all-ones vector: y_i = row sums (small integers: exact)
+    A = g.integers(-9, 10, (5, 8)).astype(np.float32)
+    assert np.array_equal(oracle.matvec_f64(A, np.ones(8, np.float32)), A.sum(axis=1))
+    assert np.array_equal(oracle.vecmat_f64(np.ones(5, np.float32), A), A.sum(axis=0))
+    # e_k picks row k (left) / column k (right)
+    ek = np.zeros(8, np.float32); ek[3] = 1
+    assert np.array_equal(oracle.matvec_f64(A, ek), A[:, 3])
+    e2 = np.zeros(5, np.float32); e2[2] = 1
+    assert np.array_equal(oracle.vecmat_f64(e2, A), A[2])
+
+
+def test_matvec_vecmat_vs_numpy_and_duality():
+    g = np.random.default_rng(23)
+    A = g.standard_normal((50, 70)).astype(np.float32)
+    x = g.standard_normal(70).astype(np.float32)
+    v = g.standard_normal(50).astype(np.float32)
+    assert np.allclose(oracle.matvec_f64(A, x), A.astype(np.float64) @ x.astype(np.float64),
+                       rtol=1e-12, atol=1e-12)
+    assert np.allclose(oracle.vecmat_f64(v, A), v.astype(np.float64) @ A.astype(np.float64),
+                       rtol=1e-12, atol=1e-12)
+    # x^T A = (A^T x)^T: the left product equals the right product of the transpose
+    assert np.array_equal(oracle.vecmat_f64(v, A), oracle.matvec_f64(oracle.transpose_f32(A), v))
