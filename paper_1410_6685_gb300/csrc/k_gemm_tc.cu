@@ -154,8 +154,23 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Persistent kernel, one CTA per SM, tiles t = blockIdx.x + i * gridDim.x
-// (row-block t / nN, column-block t % nN):
+// Tile t of the persistent order: groups of kGroupM row blocks; inside a
+// group the row block varies fastest.  The CTAs' concurrent tiles then span
+// about 16 row blocks x 10 column blocks, whose A and B slices (some 70 MB
+// at K = 8192) stay in L2 instead of all of B.
+constexpr int kGroupM = 16;
+__device__ __forceinline__ void tile_coords(int t, int nM, int nN, int* mb, int* nb) {
+  const int per_group = kGroupM * nN;
+  const int g = t / per_group;
+  const int first = g * kGroupM;
+  const int gm = min(kGroupM, nM - first);
+  const int r = t - g * per_group;
+  *mb = first + r % gm;
+  *nb = r / gm;
+}
+
+// Persistent kernel, one CTA per SM, tiles t = blockIdx.x + i * gridDim.x in
+// the grouped order of tile_coords:
 //   warp 0, one lane : TMA producer over all of the CTA's tiles;
 //   warp 1, one lane : MMA issuer; accumulators alternate between two
 //                      256-column halves of the 512 TMEM columns, so the
@@ -215,7 +230,9 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUte
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int m0 = (t / nN) * TM, n0 = (t % nN) * TN;
+        int bm, bn;
+        tile_coords(t, nM, nN, &bm, &bn);
+        const int m0 = bm * TM, n0 = bn * TN;
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -272,7 +289,9 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUte
     float4* s_rw = s_r + (warp - 2) * TN;
     int tl = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
-      const int m0 = (t / nN) * TM, n0 = (t % nN) * TN;
+      int bm, bn;
+      tile_coords(t, nM, nN, &bm, &bn);
+      const int m0 = bm * TM, n0 = bn * TN;
       const int acc = tl & 1;
       if (frv_r) {
         // each epilogue warp keeps its own copy, so no barrier spans the warps
@@ -339,7 +358,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUte
           }
         }
       }
-      if (frv_r && row < M) frv_pw[(size_t)(t % nN) * M + row] = wacc;
+      if (frv_r && row < M) frv_pw[(size_t)bn * M + row] = wacc;
     }
   }
   __syncthreads();

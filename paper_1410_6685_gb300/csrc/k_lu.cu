@@ -337,6 +337,42 @@ __global__ void __launch_bounds__(256) k_residual(const float* __restrict__ A, i
                            (unsigned long long)__double_as_longlong(rmax));
 }
 
+// The determinant from the factors (the intent of Listing 6): det A =
+// (-1)^(number of interchanges) * prod_i u_ii.  One block; every thread adds
+// log|u_ii| of its diagonal entries in binary64, then a tree in a fixed
+// order.  out[0] = sign (+1, -1, or 0 when some u_ii is zero), out[1] =
+// log |det A| (-inf when zero).
+__global__ void __launch_bounds__(1024) k_lu_det(const float* __restrict__ LU, int n,
+                                                 const int* __restrict__ piv, double* out) {
+  __shared__ double s_log[1024];
+  __shared__ int s_neg[1024], s_zero[1024];
+  double lg = 0.0;
+  int neg = 0, zero = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float u = LU[(size_t)i * n + i];
+    if (u == 0.0f) zero = 1;
+    else lg += log(fabs((double)u));
+    neg ^= (u < 0.0f) ? 1 : 0;
+    neg ^= (piv[i] != i) ? 1 : 0;
+  }
+  s_log[threadIdx.x] = lg;
+  s_neg[threadIdx.x] = neg;
+  s_zero[threadIdx.x] = zero;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_log[threadIdx.x] += s_log[threadIdx.x + o];
+      s_neg[threadIdx.x] ^= s_neg[threadIdx.x + o];
+      s_zero[threadIdx.x] |= s_zero[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s_zero[0] ? 0.0 : (s_neg[0] ? -1.0 : 1.0);
+    out[1] = s_zero[0] ? -INFINITY : s_log[0];
+  }
+}
+
 // |A|_inf (binary64) once per solve
 __global__ void __launch_bounds__(256) k_anorm(const float* __restrict__ A, int n, double* norms) {
   const int lane = threadIdx.x & 31;
@@ -477,6 +513,14 @@ cudaError_t launch_update(double* x, const float* d, const double* b, int n, boo
                           double* norms, cudaStream_t s) {
   k_update<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(x, d, b, n,
                                                                             init ? 1 : 0, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_det(const float* LU, int n, const int* piv, double* out, cudaStream_t s,
+                          Prof* prof) {
+  prof_begin(prof, "lu_det", s);
+  k_lu_det<<<1, 1024, 0, s>>>(LU, n, piv, out);
+  prof_end(prof, s);
   return cudaGetLastError();
 }
 

@@ -75,10 +75,13 @@ __device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned lon
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// digit of a key in a pass.  sel = 0x4440 | pass: one byte permute moves
+// byte `pass` of the key to the low byte and zeroes the rest.  The last pass
+// flips the sign bit (signed order).
 template <bool LAST>
-__device__ __forceinline__ unsigned digit_of(int k, int shift) {
+__device__ __forceinline__ unsigned digit_of(int k, unsigned sel) {
   const unsigned u = (unsigned)k;
-  return LAST ? ((u >> 24) ^ 0x80u) : ((u >> shift) & 0xFFu);
+  return LAST ? ((u >> 24) ^ 0x80u) : __byte_perm(u, 0u, sel);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -216,7 +219,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   unsigned short* const s_rank = sm.rank;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const long long base = (long long)tile * kTile;
-  const int shift = pass * 8;
+  const unsigned dsel = 0x4440u | (unsigned)pass;   // digit selector of this pass
   const int valid_cnt = FULL ? kTile : (int)(n - base < kTile ? n - base : kTile);
 
   // load: warp w owns keys [w*kWarpKeys, (w+1)*kWarpKeys) of the tile, 32
@@ -239,7 +242,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
     const bool ok = full || (wbase + r * 32) < n;
-    const unsigned d = digit_of<LAST>(key[r], shift);
+    const unsigned d = digit_of<LAST>(key[r], dsel);
     unsigned peers;
     if (r % kMatchEvery == 0) {
       // one round in kMatchEvery on the match unit, the others on ballots,
@@ -288,7 +291,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
     if (full || (wbase + r * 32) < n) {
-      const unsigned d = digit_of<LAST>(key[r], shift);
+      const unsigned d = digit_of<LAST>(key[r], dsel);
       s_keys[s_start[d] + s_whist[w][d] + s_rank[lbase + r * 32]] = key[r];
     }
   }
@@ -373,14 +376,14 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 #pragma unroll 4
   for (int i = tid; i < valid_cnt; i += kSortBlock) {
     const int k = s_keys[i];
-    const unsigned dk = digit_of<LAST>(k, shift);
+    const unsigned dk = digit_of<LAST>(k, dsel);
     const int pos = s_gbase[dk] + i;
     if (write) __stcs(out + pos, k);
     if (LAST && CHECK) {
       fp_add(f1, f2, k);
       if (i + 1 < valid_cnt) {
         const int k2 = s_keys[i + 1];
-        if (digit_of<LAST>(k2, shift) == dk && k > k2 && bad < 0) bad = pos;
+        if (digit_of<LAST>(k2, dsel) == dk && k > k2 && bad < 0) bad = pos;
       }
     }
   }

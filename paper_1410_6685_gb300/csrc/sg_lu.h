@@ -28,6 +28,9 @@ cudaError_t launch_residual(const float* A, int n, const double* b, const double
                             double* norms, double thresh, unsigned long long* viol,
                             cudaStream_t s, Prof* prof);
 cudaError_t launch_anorm(const float* A, int n, double* norms, cudaStream_t s);   // norms[3]
+// out[0] = sign of det A (0 if singular), out[1] = log |det A|, from the factors
+cudaError_t launch_lu_det(const float* LU, int n, const int* piv, double* out, cudaStream_t s,
+                          Prof* prof);
 // x = d (init) or x += d; norms[1] = max|d|, norms[2] = max|x|, norms[4] = max|b|
 cudaError_t launch_update(double* x, const float* d, const double* b, int n, bool init,
                           double* norms, cudaStream_t s);

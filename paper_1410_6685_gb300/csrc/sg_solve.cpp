@@ -50,6 +50,61 @@ struct SolveWork {
   void* gemm;
 };
 
+// Blocked elimination with partial pivoting of the n x n binary32 matrix in
+// `lu` (row-major), in place: L (unit lower) and U overwrite it, piv[k] is
+// the row interchanged with row k at step k, *info = k+1 at an exactly zero
+// pivot.  gemm: tensor-core scratch (gemm_tc_scratch_bytes(n, n, kLuOuter)),
+// unused for binary32 updates.
+cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* info, void* gemm,
+                            sg_precision prec) {
+  cudaError_t e = cudaSuccess;
+  sgk::Prof* prof = &c->prof;
+  cudaStream_t s = c->stream;
+  // two levels: 32-column panels inside 128-column outer blocks; inside an
+  // outer block only its own columns are updated (binary32 SIMT, narrow);
+  // the trailing matrix is updated once per outer block with K = 128
+  const bool tc = prec != SG_PREC_F32_SIMT;
+  auto gemm_sub = [&](float* a_, float* b_, float* c_, int M, int N, int K, bool big) {
+    if (M <= 0 || N <= 0 || K <= 0 || e != cudaSuccess) return;
+    if (big && tc) {
+      e = sgk::launch_gemm_tc(a_, n, b_, n, c_, n, M, N, K, prec == SG_PREC_F16_TC, true,
+                              gemm, s, prof, &c->kernels);
+    } else {
+      e = sgk::launch_gemm_f32(a_, n, b_, n, c_, n, M, N, K, true, s, prof);
+      c->kernels += 1;
+    }
+  };
+  auto at = [&](int r, int col) { return lu + (size_t)r * n + col; };
+  for (int K = 0; K < n && e == cudaSuccess; K += sgk::kLuOuter) {
+    const int KB = std::min(sgk::kLuOuter, n - K);
+    for (int j = K; j < K + KB && e == cudaSuccess; j += sgk::kLuPanel) {
+      const int jb = std::min(sgk::kLuPanel, K + KB - j);
+      e = sgk::launch_lu_panel(lu, n, j, jb, piv, info, s, prof);
+      if (e == cudaSuccess) e = sgk::launch_lu_laswp(lu, n, j, jb, piv, s, prof);
+      c->kernels += 3;
+      const int right = K + KB - (j + jb);   // columns of this outer block to the right
+      if (right > 0 && e == cudaSuccess) {
+        e = sgk::launch_lu_trsm(lu, n, j, jb, j + jb, K + KB, s, prof);
+        c->kernels += 1;
+        gemm_sub(at(j + jb, j), at(j, j + jb), at(j + jb, j + jb), n - j - jb, right, jb, false);
+      }
+    }
+    const int rest = n - K - KB;
+    if (rest > 0 && e == cudaSuccess) {
+      // U12 = L11^-1 A12 for the outer block, 32 rows at a time
+      for (int i = 0; i < KB && e == cudaSuccess; i += sgk::kLuPanel) {
+        const int ib = std::min(sgk::kLuPanel, KB - i);
+        e = sgk::launch_lu_trsm(lu, n, K + i, ib, K + KB, n, s, prof);
+        c->kernels += 1;
+        gemm_sub(at(K + i + ib, K + i), at(K + i, K + KB), at(K + i + ib, K + KB), KB - i - ib, rest,
+                 ib, false);
+      }
+      gemm_sub(at(K + KB, K), at(K, K + KB), at(K + KB, K + KB), rest, rest, KB, true);
+    }
+  }
+  return e;
+}
+
 }  // namespace
 
 extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_solve_opts* opts,
@@ -111,7 +166,7 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
   const size_t o_viol = take(8);
   const size_t gemm_bytes = o.precision == SG_PREC_F32_SIMT
                                 ? 0
-                                : sgk::gemm_tc_scratch_bytes(n, n, sgk::kLuPanel);
+                                : sgk::gemm_tc_scratch_bytes(n, n, sgk::kLuOuter);
   const size_t o_gemm = take(gemm_bytes + 256);
   char* base = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&base, off, c->stream);
@@ -172,48 +227,7 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
   if (e == cudaSuccess) e = cudaMemsetAsync(base + o_flags, 0, o_norms + 64 - o_flags, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.viol, 0, 8, s);
   if (e == cudaSuccess) e = sgk::launch_anorm(a, n, w.norms, s);
-  // two levels: 32-column panels inside 128-column outer blocks; inside an
-  // outer block only its own columns are updated (binary32 SIMT, narrow);
-  // the trailing matrix is updated once per outer block with K = 128
-  const bool tc = o.precision != SG_PREC_F32_SIMT;
-  auto gemm_sub = [&](float* a_, float* b_, float* c_, int M, int N, int K, bool big) {
-    if (M <= 0 || N <= 0 || K <= 0 || e != cudaSuccess) return;
-    if (big && tc) {
-      e = sgk::launch_gemm_tc(a_, n, b_, n, c_, n, M, N, K, o.precision == SG_PREC_F16_TC, true,
-                              w.gemm, s, prof, &c->kernels);
-    } else {
-      e = sgk::launch_gemm_f32(a_, n, b_, n, c_, n, M, N, K, true, s, prof);
-      c->kernels += 1;
-    }
-  };
-  auto at = [&](int r, int col) { return w.lu + (size_t)r * n + col; };
-  for (int K = 0; K < n && e == cudaSuccess; K += sgk::kLuOuter) {
-    const int KB = std::min(sgk::kLuOuter, n - K);
-    for (int j = K; j < K + KB && e == cudaSuccess; j += sgk::kLuPanel) {
-      const int jb = std::min(sgk::kLuPanel, K + KB - j);
-      e = sgk::launch_lu_panel(w.lu, n, j, jb, w.piv, w.info, s, prof);
-      if (e == cudaSuccess) e = sgk::launch_lu_laswp(w.lu, n, j, jb, w.piv, s, prof);
-      c->kernels += 3;
-      const int right = K + KB - (j + jb);   // columns of this outer block to the right
-      if (right > 0 && e == cudaSuccess) {
-        e = sgk::launch_lu_trsm(w.lu, n, j, jb, j + jb, K + KB, s, prof);
-        c->kernels += 1;
-        gemm_sub(at(j + jb, j), at(j, j + jb), at(j + jb, j + jb), n - j - jb, right, jb, false);
-      }
-    }
-    const int rest = n - K - KB;
-    if (rest > 0 && e == cudaSuccess) {
-      // U12 = L11^-1 A12 for the outer block, 32 rows at a time
-      for (int i = 0; i < KB && e == cudaSuccess; i += sgk::kLuPanel) {
-        const int ib = std::min(sgk::kLuPanel, KB - i);
-        e = sgk::launch_lu_trsm(w.lu, n, K + i, ib, K + KB, n, s, prof);
-        c->kernels += 1;
-        gemm_sub(at(K + i + ib, K + i), at(K + i, K + KB), at(K + i + ib, K + KB), KB - i - ib, rest,
-                 ib, false);
-      }
-      gemm_sub(at(K + KB, K), at(K, K + KB), at(K + KB, K + KB), rest, rest, KB, true);
-    }
-  }
+  if (e == cudaSuccess) e = factor_in_place(c, w.lu, n, w.piv, w.info, w.gemm, o.precision);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hinfo, w.info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -307,4 +321,76 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
     *xout = h;
   }
   return status;
+}
+
+extern "C" sg_status sg_det(sg_ctx* c, sg_matrix* A, sg_precision prec, sg_det_result* out) {
+  if (!c || !A || !A->v || !out) return err(c, SG_ERR_INVALID_ARG, "bad det arguments");
+  if (c->planning_only) return err(c, SG_ERR_UNSUPPORTED, "planning-only context");
+  if (prec < SG_PREC_F32_SIMT || prec > SG_PREC_F16_TC)
+    return err(c, SG_ERR_INVALID_ARG, "bad precision");
+  const int64_t n64 = A->v->rows;
+  if (A->v->cols != n64) return err(c, SG_ERR_SHAPE, "det needs a square matrix");
+  if (A->v->dt != SG_F32) return err(c, SG_ERR_DTYPE, "det needs SG_F32");
+  if (n64 > sgk::kLuMaxN) return err(c, SG_ERR_SHAPE, "det supports n <= 9216");
+  sg_status st = sg_flush(c);
+  if (st && st != SG_ERR_PRECONDITION && st != SG_ERR_POSTCONDITION) return st;
+  if (A->v->poisoned) return err(c, SG_ERR_POISONED, "input depends on a failed contract");
+  const int n = (int)n64;
+  if (n == 0) {   // the empty product
+    *out = sg_det_result{1, 0, 0.0, 1.0};
+    return SG_OK;
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o2 = off;
+    off = al(off + bytes);
+    return o2;
+  };
+  const size_t o_lu = take((size_t)n * n * 4);
+  const size_t o_piv = take((size_t)n * 4);
+  const size_t o_info = take(64);
+  const size_t o_out = take(64);
+  const size_t gemm_bytes =
+      prec == SG_PREC_F32_SIMT ? 0 : sgk::gemm_tc_scratch_bytes(n, n, sgk::kLuOuter);
+  const size_t o_gemm = take(gemm_bytes + 256);
+  char* base = nullptr;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMallocAsync((void**)&base, off, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return err(c, SG_ERR_OOM, "det workspace allocation failed");
+  }
+  float* lu = reinterpret_cast<float*>(base + o_lu);
+  int* piv = reinterpret_cast<int*>(base + o_piv);
+  int* info = reinterpret_cast<int*>(base + o_info);
+  double* dout = reinterpret_cast<double*>(base + o_out);
+  e = cudaMemcpyAsync(lu, A->v->st->ptr, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, 64, s);
+  if (e == cudaSuccess) e = factor_in_place(c, lu, n, piv, info, base + o_gemm, prec);
+  if (e == cudaSuccess) e = sgk::launch_lu_det(lu, n, piv, dout, s, &c->prof);
+  c->kernels += 1;
+  double h[2] = {0.0, 0.0};
+  int hinfo = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (c->prof.on) c->prof.collect();
+  cudaFreeAsync(base, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return err(c, SG_ERR_CUDA, cudaGetErrorString(e));
+  }
+  sg_det_result r;
+  r.info = hinfo;
+  if (hinfo) {   // the elimination stopped at an exactly zero pivot
+    r.sign = 0;
+    r.log_abs = -INFINITY;
+    r.det = 0.0;
+  } else {
+    r.sign = (int32_t)h[0];
+    r.log_abs = h[1];
+    r.det = r.sign == 0 ? 0.0 : (double)r.sign * std::exp(h[1]);
+  }
+  *out = r;
+  return SG_OK;
 }

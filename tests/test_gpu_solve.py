@@ -122,3 +122,64 @@ def test_not_converged(env):
     A, b = inputs.gepp_inputs(256)
     solve(env, A, b, prec=1, max_iter=1, refine_tol=1e-300, expect=sg.SG_ERR_NOT_CONVERGED)
     # one step cannot show stagnation, so the limit is what stops it
+
+
+def leibniz(A):
+    """det by the Leibniz sum over all permutations (exact for integers)."""
+    import itertools
+    n = len(A)
+    tot = 0
+    for p in itertools.permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if p[i] > p[j])
+        prod = 1
+        for i in range(n):
+            prod *= int(A[i][p[i]])
+        tot += -prod if inv % 2 else prod
+    return tot
+
+
+def det(env, A, prec=0):
+    sg, ctx, torch = env
+    ta = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)).cuda()
+    r = sg.sg_det(ctx, sg.wrap_tensor(ctx, ta), prec)
+    return r
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_det_vs_leibniz(env, n, seed):
+    """The determinant from the GPU factors (Listing 6's intent) against the
+    exact Leibniz sum on small integer matrices (pivoting exercised)."""
+    A = np.random.default_rng(100 * n + seed).integers(-5, 6, (n, n))
+    ref = leibniz(A.tolist())
+    r = det(env, A)
+    if ref == 0:
+        assert abs(r.det) <= 1e-4 * float(np.prod(np.abs(A).max(axis=1) + 1))
+        return
+    assert r.sign == (1 if ref > 0 else -1) and r.info == 0
+    assert abs(r.det - ref) <= 1e-4 * abs(ref)
+    assert abs(r.log_abs - np.log(abs(ref))) <= 1e-4
+
+
+def test_det_exactly_singular_and_empty(env):
+    r = det(env, np.array([[1.0, 2.0], [2.0, 4.0]]))
+    assert r.sign == 0 and r.info == 2 and r.det == 0.0 and r.log_abs == -np.inf
+    r = det(env, np.zeros((0, 0), np.float32))
+    assert r.sign == 1 and r.det == 1.0 and r.log_abs == 0.0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_det_diag_dominant_2048(env, prec):
+    """log |det| of the n = 2048 elimination workload against the binary64
+    oracle's factors (the determinant itself overflows binary64); binary32
+    updates to n 2^-20, bf16 tensor-core updates to n 2^-12 in the log."""
+    n = 2048
+    A, _ = inputs.gepp_inputs(n)
+    LU, piv, info = oracle.gepp_f64(A.astype(np.float64))
+    assert info == 0
+    ref = float(np.sum(np.log(np.abs(np.diag(LU)))))
+    sign = (-1) ** int(np.sum(piv != np.arange(n))) * int(np.prod(np.sign(np.diag(LU))))
+    r = det(env, A, prec)
+    assert r.sign == sign and r.info == 0
+    assert abs(r.log_abs - ref) <= n * (2.0 ** -20 if prec == 0 else 2.0 ** -12)
+    assert r.det == np.inf    # |det| far above the binary64 range
