@@ -231,6 +231,23 @@ typedef enum {
 sg_status sg_matmul(sg_ctx* ctx, sg_matrix* A, sg_matrix* B, sg_precision p,
                     sg_matrix** C);
 
+/* Matrix `transpose` and the matrix-vector products `right_multiply` and
+ * `left_multiply` of Sec. 3.4 (Listing 1 chains the first two).  SG_F32,
+ * row-major; all three are deferred like the collection operations.
+ *   sg_transpose: At = A^T (cols x rows, a new matrix owned by the caller).
+ *   sg_matvec:    y = A x; A rows x cols, x of cols elements (Listing 1's
+ *                 precondition: checked at the call, SG_ERR_SHAPE), y of rows.
+ *   sg_vecmat:    y = x^T A; x of rows elements, y of cols.
+ * Sums are binary32 (FMA per lane, then fixed-order trees and stripe sums):
+ * |y_i - y*_i| <= (terms + 8) 2^-24 sum |a x| with terms = cols (matvec) or
+ * rows (vecmat).  With fusion on, sg_matvec on the pending transpose of A
+ * whose handle has been released reads A once as sg_vecmat does and never
+ * materialises A^T.
+ * Errors: SG_ERR_INVALID_ARG, SG_ERR_DTYPE, SG_ERR_SHAPE. */
+sg_status sg_transpose(sg_ctx* ctx, sg_matrix* A, sg_matrix** At);
+sg_status sg_matvec(sg_ctx* ctx, sg_matrix* A, sg_vector* x, sg_vector** y);
+sg_status sg_vecmat(sg_ctx* ctx, sg_vector* x, sg_matrix* A, sg_vector** y);
+
 /* ------------------------------------------------------------------------ */
 /* Gaussian elimination (Sec. 5, Listing 6; read as elimination with partial
  * pivoting) and solve.  A: n x n SG_F32, b: n SG_F64; x: n SG_F64.
@@ -257,6 +274,25 @@ typedef struct {
 sg_status sg_solve(sg_ctx* ctx, sg_matrix* A, sg_vector* b,
                    const sg_solve_opts* opts, sg_vector** x,
                    sg_solve_info* info);
+
+/* The determinant (the intent of Listing 6, Sec. 5: elimination that returns
+ * the product of the pivots), from the same elimination with partial
+ * pivoting: det A = (-1)^(row interchanges) * prod_i u_ii.  A: n x n SG_F32
+ * (n <= 9216), factored in a workspace copy with `precision` operands for
+ * the trailing updates (SG_PREC_F32_SIMT keeps every update in binary32).
+ * The log of |det| is summed in binary64, so it neither overflows nor
+ * underflows; `det` = sign * exp(log_abs) may be +-inf or 0 in binary64.
+ * An exactly singular A (a zero pivot) is not an error: sign = 0,
+ * det = 0, log_abs = -inf, info = k+1 for the first zero pivot at step k.
+ * Errors: SG_ERR_SHAPE (not square, n too large), SG_ERR_DTYPE,
+ * SG_ERR_POISONED, SG_ERR_OOM, SG_ERR_CUDA. */
+typedef struct {
+  int32_t sign;        /* +1, -1, or 0 for an exactly singular A            */
+  int32_t info;        /* 0, or k+1 for the first exactly zero pivot        */
+  double log_abs;      /* natural log of |det A| (-inf when singular)       */
+  double det;          /* sign * exp(log_abs) in binary64                   */
+} sg_det_result;
+sg_status sg_det(sg_ctx* ctx, sg_matrix* A, sg_precision precision, sg_det_result* out);
 
 /* ------------------------------------------------------------------------ */
 /* Contracts (Sec. 4).  sg_require attaches a precondition, sg_ensure a

@@ -567,6 +567,62 @@ sg_status sg_sort(sg_ctx* c, sg_vector* keys, sg_vector** out) {
   return SG_OK;
 }
 
+sg_status sg_transpose(sg_ctx* c, sg_matrix* A, sg_matrix** At) {
+  if (!c || check_vec(A) || A->ctx != c || !At) return fail(c, SG_ERR_INVALID_ARG, "bad transpose");
+  if (A->v->dt != SG_F32) return fail(c, SG_ERR_DTYPE, "transpose needs SG_F32");
+  NodeP n = new_node(c, NK::TRANSPOSE);
+  n->nin = 1;
+  use(n.get(), 0, A->v);
+  make_out(c, SG_F32, A->v->n, A->v->cols, A->v->rows, &n->out);
+  sg_vector* h = new_handle(c, n->out, true);
+  enqueue(c, std::move(n));
+  *At = static_cast<sg_matrix*>(h);
+  return SG_OK;
+}
+
+sg_status sg_matvec(sg_ctx* c, sg_matrix* A, sg_vector* x, sg_vector** y) {
+  if (!c || check_vec(A) || check_vec(x) || A->ctx != c || x->ctx != c || !y)
+    return fail(c, SG_ERR_INVALID_ARG, "bad matvec");
+  if (A->v->dt != SG_F32 || x->v->dt != SG_F32) return fail(c, SG_ERR_DTYPE, "matvec needs SG_F32");
+  sg_status ks = known_count(x);
+  if (ks && ks != SG_ERR_PRECONDITION && ks != SG_ERR_POSTCONDITION) return ks;
+  // precondition of Listing 1: the vector's count matches the matrix
+  if (x->v->n != A->v->cols)
+    return fail(c, SG_ERR_SHAPE, "A is %lldx%lld, x has %lld elements", (long long)A->v->rows,
+                (long long)A->v->cols, (long long)x->v->n);
+  NodeP n = new_node(c, NK::MATVEC);
+  n->nin = 2;
+  n->left = false;
+  use(n.get(), 0, A->v);
+  use(n.get(), 1, x->v);
+  make_out(c, SG_F32, A->v->rows, A->v->rows, 1, &n->out);
+  sg_vector* h = new_handle(c, n->out, false);
+  enqueue(c, std::move(n));
+  *y = h;
+  return SG_OK;
+}
+
+sg_status sg_vecmat(sg_ctx* c, sg_vector* x, sg_matrix* A, sg_vector** y) {
+  if (!c || check_vec(A) || check_vec(x) || A->ctx != c || x->ctx != c || !y)
+    return fail(c, SG_ERR_INVALID_ARG, "bad vecmat");
+  if (A->v->dt != SG_F32 || x->v->dt != SG_F32) return fail(c, SG_ERR_DTYPE, "vecmat needs SG_F32");
+  sg_status ks = known_count(x);
+  if (ks && ks != SG_ERR_PRECONDITION && ks != SG_ERR_POSTCONDITION) return ks;
+  if (x->v->n != A->v->rows)
+    return fail(c, SG_ERR_SHAPE, "x has %lld elements, A is %lldx%lld", (long long)x->v->n,
+                (long long)A->v->rows, (long long)A->v->cols);
+  NodeP n = new_node(c, NK::MATVEC);
+  n->nin = 2;
+  n->left = true;
+  use(n.get(), 0, x->v);
+  use(n.get(), 1, A->v);
+  make_out(c, SG_F32, A->v->cols, A->v->cols, 1, &n->out);
+  sg_vector* h = new_handle(c, n->out, false);
+  enqueue(c, std::move(n));
+  *y = h;
+  return SG_OK;
+}
+
 sg_status sg_matmul(sg_ctx* c, sg_matrix* A, sg_matrix* B, sg_precision p, sg_matrix** C) {
   if (!c || check_vec(A) || check_vec(B) || !C || p < SG_PREC_F32_SIMT || p > SG_PREC_F16_TC)
     return fail(c, SG_ERR_INVALID_ARG, "bad matmul");

@@ -69,4 +69,15 @@ cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int
                                    Prof* prof, int64_t* kernels, int inj_row = -1,
                                    int inj_col = -1, float inj_delta = 0.0f);
 
+// Sec. 3.4 `transpose`, `right_multiply`, `left_multiply` (binary32,
+// row-major).  At: cols x rows.  matvec: y = A x (x: cols, y: rows); vecmat:
+// y = x^T A (x: rows, y: cols), scratch of vecmat_scratch_bytes(rows, cols).
+cudaError_t launch_transpose(const float* A, int rows, int cols, float* At, cudaStream_t s,
+                             Prof* prof);
+cudaError_t launch_matvec(const float* A, int rows, int cols, const float* x, float* y,
+                          cudaStream_t s, Prof* prof);
+size_t vecmat_scratch_bytes(int rows, int cols);
+cudaError_t launch_vecmat(const float* x, const float* A, int rows, int cols, float* y,
+                          void* scratch, cudaStream_t s, Prof* prof);
+
 }  // namespace sgk

@@ -27,6 +27,7 @@
 
 #include "sg_internal.h"
 #include "sg_jit.h"
+#include "sg_linalg_kernels.h"
 #include "sg_plan.h"
 
 namespace {
@@ -39,7 +40,7 @@ struct Op {
   float cst;
 };
 
-enum class PK { STREAM, FILTER, SORT, CHECK_SORTED, CHECK_PERM, MATMUL, FREIVALDS };
+enum class PK { STREAM, FILTER, SORT, CHECK_SORTED, CHECK_PERM, MATMUL, FREIVALDS, TRANSPOSE, MATVEC };
 
 struct Pass {
   PK kind = PK::STREAM;
@@ -62,6 +63,7 @@ struct Pass {
   Node* chk_sorted = nullptr;
   Node* chk_perm = nullptr;
   Node* chk_frv = nullptr;    // MATMUL: built-in Freivalds check folded in
+  Node* vtrans = nullptr;     // MATVEC y = A x with A the pending transpose of vtrans->in[0]
 };
 
 bool is_f32_stream_node(const Node* n) {
@@ -134,10 +136,27 @@ struct Planner {
   }
 
   bool dead(Node* n) {
-    // a map whose result nobody will ever see is not computed
-    if (n->kind != NK::MAP || n->inplace) return false;
+    // a map / transpose / product whose result nobody will ever see is not computed
+    const bool pure = (n->kind == NK::MAP && !n->inplace) || n->kind == NK::TRANSPOSE ||
+                      n->kind == NK::MATVEC;
+    if (!pure) return false;
     Value* v = n->out.get();
     return v->handles == 0 && consumers.find(v) == consumers.end();
+  }
+
+  // A transpose that only right-multiplies vectors (and has no handle) is
+  // never materialised: y = A^T x is computed as x^T A on the source.
+  std::set<Node*> virtual_t;
+  bool virtual_transpose(Node* n) {
+    if (c->fusion != SG_FUSE_ON || n->kind != NK::TRANSPOSE) return false;
+    Value* v = n->out.get();
+    if (v->handles > 0) return false;
+    auto it = consumers.find(v);
+    if (it == consumers.end()) return false;
+    for (Node* u : it->second)
+      if (u->kind != NK::MATVEC || u->left || u->in[0].get() != v || u->in[1].get() == v)
+        return false;
+    return true;
   }
 
   int slot_of(Pass& P, Value* v, bool add) {
@@ -253,6 +272,7 @@ struct Planner {
 
   void group() {
     passes.clear();
+    virtual_t.clear();
     bool open = false;
     for (Node* n : nodes) {
       if (dead(n)) continue;
@@ -286,6 +306,18 @@ struct Planner {
         case NK::FILTER: P.kind = PK::FILTER; break;
         case NK::SORT: P.kind = PK::SORT; break;
         case NK::MATMUL: P.kind = PK::MATMUL; break;
+        case NK::TRANSPOSE:
+          if (virtual_transpose(n)) {
+            virtual_t.insert(n);
+            continue;
+          }
+          P.kind = PK::TRANSPOSE;
+          break;
+        case NK::MATVEC:
+          P.kind = PK::MATVEC;
+          if (!n->left && n->in[0]->producer && virtual_t.count(n->in[0]->producer))
+            P.vtrans = n->in[0]->producer;
+          break;
         case NK::CHECK:
           if (n->ckind == SG_C_SORTED) {
             // fuse into the sort that produced the checked value
@@ -540,6 +572,13 @@ sg_status sg_execute_pending(sg_ctx* c) {
       case PK::CHECK_PERM: work = std::max(work, sgk::check_scratch_bytes()); break;
       case PK::MATMUL:
       case PK::FREIVALDS: work = std::max(work, sg_linalg_scratch(c, P.main, P.chk_frv)); break;
+      case PK::TRANSPOSE: break;
+      case PK::MATVEC: {
+        const Node* n = P.main;
+        const Value* A = P.vtrans ? P.vtrans->in[0].get() : n->left ? n->in[1].get() : nullptr;
+        if (A) work = std::max(work, sgk::vecmat_scratch_bytes((int)A->rows, (int)A->cols));
+        break;
+      }
     }
   }
   sg_status st = ensure_scratch(c, res_bytes + work);
@@ -678,6 +717,39 @@ sg_status sg_execute_pending(sg_ctx* c) {
       case PK::FREIVALDS:
         status = sg_exec_linalg(c, P.main, P.chk_frv, rec, dwork, &e);
         break;
+      case PK::TRANSPOSE: {
+        Node* n = P.main;
+        status = ensure_storage(c, n->out.get());
+        if (status) break;
+        const Value* A = n->in[0].get();
+        e = sgk::launch_transpose(static_cast<const float*>(A->st->ptr), (int)A->rows,
+                                  (int)A->cols, static_cast<float*>(n->out->st->ptr), c->stream,
+                                  &c->prof);
+        c->kernels += 1;
+        break;
+      }
+      case PK::MATVEC: {
+        Node* n = P.main;
+        status = ensure_storage(c, n->out.get());
+        if (status) break;
+        float* y = static_cast<float*>(n->out->st->ptr);
+        if (n->left || P.vtrans) {
+          // y = x^T A; for a folded transpose, A is the transpose's source
+          const Value* x = n->left ? n->in[0].get() : n->in[1].get();
+          const Value* A = n->left ? n->in[1].get() : P.vtrans->in[0].get();
+          e = sgk::launch_vecmat(static_cast<const float*>(x->st->ptr),
+                                 static_cast<const float*>(A->st->ptr), (int)A->rows,
+                                 (int)A->cols, y, dwork, c->stream, &c->prof);
+          c->kernels += 2;
+        } else {
+          const Value* A = n->in[0].get();
+          e = sgk::launch_matvec(static_cast<const float*>(A->st->ptr), (int)A->rows,
+                                 (int)A->cols, static_cast<const float*>(n->in[1]->st->ptr), y,
+                                 c->stream, &c->prof);
+          c->kernels += 1;
+        }
+        break;
+      }
     }
   }
   if (e == cudaSuccess && !status)
@@ -755,6 +827,9 @@ sg_status sg_execute_pending(sg_ctx* c) {
             record_violation(c, kp, -1, 0.0, &have, &cstatus);
           break;
         }
+        case PK::TRANSPOSE:
+        case PK::MATVEC:
+          break;
         case PK::MATMUL:
         case PK::FREIVALDS: {
           double observed = 0.0;
@@ -824,6 +899,17 @@ sg_status sg_describe_pending(sg_ctx* c, std::string* out) {
         snprintf(buf, sizeof buf, "freivalds n=%lld nvec=%d\n", (long long)P.main->in[0]->rows,
                  P.main->nvec);
         break;
+      case PK::TRANSPOSE:
+        snprintf(buf, sizeof buf, "transpose %lldx%lld\n", (long long)P.main->in[0]->rows,
+                 (long long)P.main->in[0]->cols);
+        break;
+      case PK::MATVEC: {
+        const Node* n = P.main;
+        const Value* A = P.vtrans ? P.vtrans->in[0].get() : n->left ? n->in[1].get() : n->in[0].get();
+        snprintf(buf, sizeof buf, "%s %lldx%lld%s\n", (n->left || P.vtrans) ? "vecmat" : "matvec",
+                 (long long)A->rows, (long long)A->cols, P.vtrans ? " (transpose folded)" : "");
+        break;
+      }
     }
     s += buf;
   }

@@ -45,7 +45,7 @@ struct ScalarVal {
 };
 using ScalarP = std::shared_ptr<ScalarVal>;
 
-enum class NK { MAP, REDUCE, QUANT, CHECK, FILTER, SORT, MATMUL };
+enum class NK { MAP, REDUCE, QUANT, CHECK, FILTER, SORT, MATMUL, TRANSPOSE, MATVEC };
 
 struct Node {
   int id = 0;
@@ -65,6 +65,7 @@ struct Node {
   int nvec = 4;
   double tol = 0.0;
   int prec = 0;                  // MATMUL precision
+  bool left = false;             // MATVEC: y = x^T A (in[0] = x, in[1] = A), else y = A x
   // results filled at execution
   int64_t first = -1;
   double observed = 0.0;

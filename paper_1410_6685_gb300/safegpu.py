@@ -71,6 +71,11 @@ class SgSolveInfo(C.Structure):
                 ("last_correction", C.c_double)]
 
 
+class SgDetResult(C.Structure):
+    _fields_ = [("sign", C.c_int32), ("info", C.c_int32), ("log_abs", C.c_double),
+                ("det", C.c_double)]
+
+
 SG_SCHED_MAX_CANDIDATES = 32
 
 
@@ -119,7 +124,10 @@ def _load():
         "sg_scalar_get": [vp, P(dbl)], "sg_scalar_index": [vp, P(i64)],
         "sg_scalar_release": [vp], "sg_sort": [vp, vp, P(vp)],
         "sg_matmul": [vp, vp, vp, i32, P(vp)],
+        "sg_transpose": [vp, vp, P(vp)], "sg_matvec": [vp, vp, vp, P(vp)],
+        "sg_vecmat": [vp, vp, vp, P(vp)],
         "sg_solve": [vp, vp, vp, P(SgSolveOpts), P(vp), P(SgSolveInfo)],
+        "sg_det": [vp, vp, i32, P(SgDetResult)],
         "sg_require": [vp, vp, P(SgContract), P(C.c_int32)],
         "sg_ensure": [vp, vp, P(SgContract), P(C.c_int32)],
         "sg_last_violation": [vp, P(SgViolation)], "sg_flush": [vp],
@@ -358,6 +366,18 @@ def sg_matmul(ctx, A, B, precision=SG_PREC_F32_SIMT):
     return _out(lib.sg_matmul, ctx, ctx, A, B, precision)
 
 
+def sg_transpose(ctx, A):
+    return _out(lib.sg_transpose, ctx, ctx, A)
+
+
+def sg_matvec(ctx, A, x):
+    return _out(lib.sg_matvec, ctx, ctx, A, x)
+
+
+def sg_vecmat(ctx, x, A):
+    return _out(lib.sg_vecmat, ctx, ctx, x, A)
+
+
 def sg_solve(ctx, A, b, opts: SgSolveOpts | None = None):
     x = C.c_void_p()
     info = SgSolveInfo()
@@ -365,6 +385,12 @@ def sg_solve(ctx, A, b, opts: SgSolveOpts | None = None):
                       C.byref(info))
     _check(rc, ctx)
     return x, info
+
+
+def sg_det(ctx, A, precision=SG_PREC_F32_SIMT) -> SgDetResult:
+    out = SgDetResult()
+    _check(lib.sg_det(ctx, A, precision, C.byref(out)), ctx)
+    return out
 
 
 def contract(kind, expr_ops=None, other=(), seed=0, nvec=4, tol=0.0) -> SgContract:
