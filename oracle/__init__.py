@@ -73,6 +73,8 @@ def lib():
             "or_first_unsorted_i32": (i64, [vp, i64]),
             "or_same_multiset_i32": (i32, [vp, vp, i64]),
             "or_matmul_f64": (None, [vp, vp, i64, i64, i64, vp]),
+            "or_sort_f32": (None, [vp, i64, vp]),
+            "or_first_unsorted_f32": (i64, [vp, i64]),
             "or_transpose_f32": (None, [vp, i64, i64, vp]),
             "or_matvec_f64": (None, [vp, i64, i64, vp, vp]),
             "or_vecmat_f64": (None, [vp, vp, i64, i64, vp]),
@@ -203,6 +205,20 @@ def sort_i32(x) -> np.ndarray:
 def first_unsorted_i32(x) -> int:
     x = np.ascontiguousarray(x, dtype=np.int32)
     return int(lib().or_first_unsorted_i32(_p(x), len(x)))
+
+
+def sort_f32(x) -> np.ndarray:
+    """Listing 4's REAL_32 sort: ascending in IEEE 754 totalOrder."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty_like(x)
+    lib().or_sort_f32(_p(x), len(x), _p(out))
+    return out
+
+
+def first_unsorted_f32(x) -> int:
+    """is_sorted in the IEEE comparison: first i with x[i] > x[i+1], else -1."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    return int(lib().or_first_unsorted_f32(_p(x), len(x)))
 
 
 def same_multiset_i32(a, b) -> bool:

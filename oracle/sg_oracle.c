@@ -212,6 +212,43 @@ void or_sort_i32(const int32_t* x, int64_t n, int32_t* out) {
 
 /* `is_sorted` (Sec. 3.3; Listing 4 postcondition): the smallest i with
  * x[i] > x[i+1], or -1. */
+/* IEEE 754 totalOrder written out by classes: negative NaNs (larger payload
+ * first), negative numbers and -inf, -0, +0, positive numbers and +inf,
+ * positive NaNs (smaller payload first).                                    */
+static int f32_class(float v, uint32_t bits) {
+  const int neg = (int)(bits >> 31);
+  if (v != v) return neg ? 0 : 5;
+  if (v == 0.0f) return neg ? 2 : 3;
+  return neg ? 1 : 4;
+}
+
+static int cmp_f32_total(const void* a, const void* b) {
+  float x, y;
+  uint32_t bx, by;
+  memcpy(&x, a, 4);
+  memcpy(&y, b, 4);
+  memcpy(&bx, a, 4);
+  memcpy(&by, b, 4);
+  const int cx = f32_class(x, bx), cy = f32_class(y, by);
+  if (cx != cy) return (cx > cy) - (cx < cy);
+  if (cx == 1 || cx == 4) return (x > y) - (x < y);
+  const uint32_t px = bx & 0x7fffffffu, py = by & 0x7fffffffu;
+  if (cx == 0) return (px < py) - (px > py);   /* negative NaNs: larger payload first */
+  return (px > py) - (px < py);                /* positive NaNs (and the zeros) */
+}
+
+void or_sort_f32(const float* x, int64_t n, float* out) {
+  if (n <= 0) return;
+  memcpy(out, x, (size_t)n * sizeof(float));
+  qsort(out, (size_t)n, sizeof(float), cmp_f32_total);
+}
+
+int64_t or_first_unsorted_f32(const float* x, int64_t n) {
+  for (int64_t i = 0; i + 1 < n; ++i)
+    if (x[i] > x[i + 1]) return i;
+  return -1;
+}
+
 int64_t or_first_unsorted_i32(const int32_t* x, int64_t n) {
   for (int64_t i = 0; i + 1 < n; ++i)
     if (x[i] > x[i + 1]) return i;

@@ -55,6 +55,11 @@ float   or_max_f32(const float* x, int64_t n);
 void    or_sort_i32(const int32_t* x, int64_t n, int32_t* out);
 int64_t or_first_unsorted_i32(const int32_t* x, int64_t n);
 int     or_same_multiset_i32(const int32_t* a, const int32_t* b, int64_t n);
+/* binary32 keys (Listing 4 sorts REAL_32): ascending in IEEE 754 totalOrder
+ * (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN); is_sorted in the
+ * IEEE comparison: first i with x[i] > x[i+1] (NaN compares false)        */
+void    or_sort_f32(const float* x, int64_t n, float* out);
+int64_t or_first_unsorted_f32(const float* x, int64_t n);
 
 /* ---- matrix product and its check (Sec. 3.4 `multiply`) ---- */
 void    or_matmul_f64(const float* A, const float* B, int64_t M, int64_t K,

@@ -393,3 +393,55 @@ def test_matvec_vecmat_vs_numpy_and_duality():
                        rtol=1e-12, atol=1e-12)
     # x^T A = (A^T x)^T: the left product equals the right product of the transpose
     assert np.array_equal(oracle.vecmat_f64(v, A), oracle.matvec_f64(oracle.transpose_f32(A), v))
+
+
+# ---- binary32 keys (Listing 4 sorts REAL_32) ----
+
+def _f32(bits):
+    return np.array(bits, dtype=np.uint32).view(np.float32)
+
+
+# the totalOrder of IEEE 754 (Sec. 5.10) on these bit patterns, written out
+# by hand: -NaN(big payload), -NaN(small), -inf, -2.5, -tiny, -0, +0, +tiny,
+# 1.0, +inf, +NaN(small), +NaN(big)
+TOTAL_ORDER = [0xFFC00005, 0xFFC00001, 0xFF800000, 0xC0200000, 0x80000001, 0x80000000,
+               0x00000000, 0x00000001, 0x3F800000, 0x7F800000, 0x7FC00001, 0x7FC00005]
+
+
+def test_sort_f32_total_order_special_values():
+    want = _f32(TOTAL_ORDER).view(np.uint32)
+    g = np.random.default_rng(31)
+    for _ in range(200):
+        x = _f32(TOTAL_ORDER)[g.permutation(len(TOTAL_ORDER))]
+        assert np.array_equal(oracle.sort_f32(x).view(np.uint32), want)
+
+
+def test_sort_f32_brute_force_small():
+    # all permutations of 7 keys with repeats and both zeros: one output
+    base = _f32([0x80000000, 0x00000000, 0x3F800000, 0x3F800000, 0xBF800000, 0x7F800000,
+                 0x7FC00000])
+    want = None
+    for p in itertools.permutations(range(7)):
+        got = oracle.sort_f32(base[list(p)]).view(np.uint32)
+        if want is None:
+            want = got
+            assert list(got) == [0xBF800000, 0x80000000, 0x00000000, 0x3F800000, 0x3F800000,
+                                 0x7F800000, 0x7FC00000]
+        assert np.array_equal(got, want)
+
+
+def test_sort_f32_matches_numpy_on_finite_nonzero():
+    g = np.random.default_rng(32)
+    x = (g.standard_normal(100000) * 1e3).astype(np.float32)
+    x[x == 0] = 1.0
+    assert np.array_equal(oracle.sort_f32(x), np.sort(x))
+    assert oracle.first_unsorted_f32(oracle.sort_f32(x)) == -1
+
+
+def test_first_unsorted_f32_ieee():
+    x = np.array([1.0, 2.0, 2.0, 5.0, 3.0, 4.0], np.float32)
+    assert oracle.first_unsorted_f32(x) == 3
+    # NaN compares false and +0 / -0 compare equal: neither is a violation
+    assert oracle.first_unsorted_f32(np.array([1.0, np.nan, 0.5], np.float32)) == -1
+    assert oracle.first_unsorted_f32(_f32([0x00000000, 0x80000000])) == -1
+    assert oracle.first_unsorted_f32(np.array([], np.float32)) == -1
