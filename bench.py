@@ -20,7 +20,8 @@ After the headline, rank 0 also reports the other parts of the metric under
 `extras.secondary` (skip with --no-extras): the fused zip + for_all + sum
 stream at n = 2^28 (GB/s, fraction of HBM, contract overhead), the bf16
 tcgen05 GEMM at 8192^2 with its Freivalds postcondition (TFLOP/s, contract
-overhead), GEPP at n = 8192 with refinement, and the batch of 10,000
+overhead), GEPP at n = 8192 with refinement, the transpose of 8192^2 and
+the transposed matrix-vector product of Listing 1, and the batch of 10,000
 collections.
 """
 from __future__ import annotations
@@ -339,7 +340,39 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
     sg.sg_vector_release(vb)
     del ta, tb
 
-    # 4. 10,000 collections (log-uniform lengths), map -> filter -> sum, one launch
+    # 4. Listing 1: transpose of 8192^2 (materialised), and A^T x with the
+    #    transpose folded into the left product (A read once)
+    n = 8192
+    g.manual_seed(12)
+    tA = torch.randn(n, n, device="cuda", generator=g)
+    tx = torch.randn(n, device="cuda", generator=g)
+    mA, vx = sg.wrap_tensor(ctx, tA), sg.wrap_tensor(ctx, tx)
+
+    def s_transpose():
+        t = sg.sg_transpose(ctx, mA)
+        sg.sg_flush(ctx)
+        sg.sg_matrix_release(t)
+
+    def s_listing1():
+        t = sg.sg_transpose(ctx, mA)
+        y = sg.sg_matvec(ctx, t, vx)
+        sg.sg_matrix_release(t)
+        sg.sg_flush(ctx)
+        sg.sg_vector_release(y)
+    ms_t = time_steps(torch, stream, s_transpose, k)
+    ms_l = time_steps(torch, stream, s_listing1, k)
+    out["transpose_8192"] = {"ms": round(ms_t, 4), "GBps": round(8.0 * n * n / (ms_t / 1e3) / 1e9, 1),
+                             "frac_hbm": round(8.0 * n * n / (ms_t / 1e3) / 1e9 / hbm_peak, 4),
+                             "bytes_per_elem": 8}
+    out["listing1_transpose_matvec_8192"] = {
+        "ms": round(ms_l, 4), "GBps": round(4.0 * n * n / (ms_l / 1e3) / 1e9, 1),
+        "frac_hbm": round(4.0 * n * n / (ms_l / 1e3) / 1e9 / hbm_peak, 4), "bytes_per_elem": 4,
+        "plan": "transpose folded into x^T A (never materialised)"}
+    sg.sg_matrix_release(mA)
+    sg.sg_vector_release(vx)
+    del tA, tx
+
+    # 5. 10,000 collections (log-uniform lengths), map -> filter -> sum, one launch
     L = inputs.batch_lengths()
     off = inputs.batch_offsets(L)
     total = int(off[-1])

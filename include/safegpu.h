@@ -210,11 +210,16 @@ sg_status sg_scalar_index(sg_scalar* s, int64_t* index);
 sg_status sg_scalar_release(sg_scalar* s);
 
 /* ------------------------------------------------------------------------ */
-/* Sorting (Listing 4: ascending, left < mid = right >).  Keys SG_I32, signed
- * order.  With contract mode >= SG_CONTRACTS_PRE_POST the built-in
- * postconditions `Result.is_sorted` and `Result is a permutation of keys`
- * (Listing 4 `Result.count = a.count`, strengthened to multiset equality)
- * are evaluated inside the sort's last pass.  n < 2^30. */
+/* Sorting (Listing 4: ascending, left < mid = right >).  Keys SG_I32 in
+ * signed order, or SG_F32 (Listing 4 sorts REAL_32) in IEEE 754 totalOrder:
+ * -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN, equal bit patterns being
+ * indistinguishable, so the output is unique.  With contract mode >=
+ * SG_CONTRACTS_PRE_POST the built-in postconditions `Result.is_sorted` and
+ * `Result is a permutation of keys` (Listing 4 `Result.count = a.count`,
+ * strengthened to multiset equality of the bit patterns) are evaluated
+ * inside the sort's last pass; there `is_sorted` is checked in the sort's
+ * own order.  A stand-alone SG_C_SORTED contract on SG_F32 uses the IEEE
+ * comparison (x[i] > x[i+1] is a violation; NaN never is).  n < 2^30. */
 sg_status sg_sort(sg_ctx* ctx, sg_vector* keys, sg_vector** out);
 
 /* ------------------------------------------------------------------------ */

@@ -75,11 +75,21 @@ __device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned lon
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// digit of a key in a pass.  sel = 0x4440 | pass: one byte permute moves
-// byte `pass` of the key to the low byte and zeroes the rest.  The last pass
-// flips the sign bit (signed order).
-template <bool LAST>
+// Order-preserving unsigned image of a key: signed int32 order (flip the
+// sign bit), or for binary32 bit patterns the IEEE totalOrder (negative
+// patterns: flip every bit; positive: flip the sign bit).
+template <bool FLT>
+__device__ __forceinline__ unsigned okey(int k) {
+  const unsigned u = (unsigned)k;
+  return FLT ? (u ^ ((unsigned)(k >> 31) | 0x80000000u)) : (u ^ 0x80000000u);
+}
+
+// digit of a key in a pass: byte `pass` of okey.  sel = 0x4440 | pass: one
+// byte permute moves that byte to the low byte and zeroes the rest.  For
+// int32 keys only the last pass's byte differs from the raw key's.
+template <bool LAST, bool FLT>
 __device__ __forceinline__ unsigned digit_of(int k, unsigned sel) {
+  if (FLT) return __byte_perm(okey<true>(k), 0u, sel);
   const unsigned u = (unsigned)k;
   return LAST ? ((u >> 24) ^ 0x80u) : __byte_perm(u, 0u, sel);
 }
@@ -134,6 +144,7 @@ __device__ __forceinline__ void fp_flush(unsigned long long f1, unsigned long lo
 }
 
 // ---------------------------------------------------------------------------
+template <bool FLT>
 __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, long long n,
                                                     SortHdr* h, SortResult* res) {
   __shared__ unsigned sh[4][kRadix];
@@ -144,11 +155,11 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long start = 0;
   auto count = [&](int k) {
-    const unsigned u = (unsigned)k;
+    const unsigned u = okey<FLT>(k);
     atomicAdd(&sh[0][u & 0xFFu], 1u);
     atomicAdd(&sh[1][(u >> 8) & 0xFFu], 1u);
     atomicAdd(&sh[2][(u >> 16) & 0xFFu], 1u);
-    atomicAdd(&sh[3][(u >> 24) ^ 0x80u], 1u);
+    atomicAdd(&sh[3][u >> 24], 1u);
     fp_add(f1, f2, k);
   };
   if (((uintptr_t)in & 15) == 0) {
@@ -206,7 +217,7 @@ struct SortSmem {
 
 // One tile of one pass.  FULL: the tile holds kTile keys (every tile but the
 // last), so no index is checked against n.
-template <bool LAST, bool CHECK, bool FULL>
+template <bool LAST, bool CHECK, bool FULL, bool FLT>
 __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restrict__ in,
                                               int* __restrict__ out, long long n, int pass,
                                               SortHdr* h, unsigned* st32,
@@ -242,7 +253,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
     const bool ok = full || (wbase + r * 32) < n;
-    const unsigned d = digit_of<LAST>(key[r], dsel);
+    const unsigned d = digit_of<LAST, FLT>(key[r], dsel);
     unsigned peers;
     if (r % kMatchEvery == 0) {
       // one round in kMatchEvery on the match unit, the others on ballots,
@@ -291,7 +302,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
     if (full || (wbase + r * 32) < n) {
-      const unsigned d = digit_of<LAST>(key[r], dsel);
+      const unsigned d = digit_of<LAST, FLT>(key[r], dsel);
       s_keys[s_start[d] + s_whist[w][d] + s_rank[lbase + r * 32]] = key[r];
     }
   }
@@ -356,7 +367,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
       st_relaxed64(&st64[(size_t)tile * kRadix + d], word(kPre, (unsigned)(excl + cnt), carry));
     }
     // the first key of this run must not be below the last key before it
-    if (cnt && found && first_key < pred_last) {
+    if (cnt && found && okey<FLT>(first_key) < okey<FLT>(pred_last)) {
       const long long pos = (long long)h->offs[pass][d] + (long long)excl - 1;
       atomicMax(&res->unsorted_enc, ~(unsigned long long)pos);
     }
@@ -376,14 +387,15 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 #pragma unroll 4
   for (int i = tid; i < valid_cnt; i += kSortBlock) {
     const int k = s_keys[i];
-    const unsigned dk = digit_of<LAST>(k, dsel);
+    const unsigned dk = digit_of<LAST, FLT>(k, dsel);
     const int pos = s_gbase[dk] + i;
     if (write) __stcs(out + pos, k);
     if (LAST && CHECK) {
       fp_add(f1, f2, k);
       if (i + 1 < valid_cnt) {
         const int k2 = s_keys[i + 1];
-        if (digit_of<LAST>(k2, dsel) == dk && k > k2 && bad < 0) bad = pos;
+        if (digit_of<LAST, FLT>(k2, dsel) == dk && okey<FLT>(k) > okey<FLT>(k2) && bad < 0)
+          bad = pos;
       }
     }
   }
@@ -403,7 +415,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   }
 }
 
-template <bool LAST, bool CHECK>
+template <bool LAST, bool CHECK, bool FLT>
 __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
     const int* __restrict__ in, int* __restrict__ out, long long n, int pass, SortHdr* h,
     unsigned* st32, unsigned long long* st64, SortResult* res) {
@@ -417,21 +429,29 @@ __global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
   __syncthreads();
   const unsigned tile = sm.tile;
   if ((long long)(tile + 1) * kTile <= n)
-    onesweep_tile<LAST, CHECK, true>(sm, in, out, n, pass, h, st32, st64, res, tile);
+    onesweep_tile<LAST, CHECK, true, FLT>(sm, in, out, n, pass, h, st32, st64, res, tile);
   else
-    onesweep_tile<LAST, CHECK, false>(sm, in, out, n, pass, h, st32, st64, res, tile);
+    onesweep_tile<LAST, CHECK, false, FLT>(sm, in, out, n, pass, h, st32, st64, res, tile);
 }
 
 // ---------------------------------------------------------------------------
 // Stand-alone checks (re-read the vector).
 
+// is_sorted: first i with x[i] > x[i+1]; signed int32, or the IEEE
+// comparison of binary32 values (NaN compares false)
+template <bool FLT>
+__device__ __forceinline__ bool gt_key(int a, int b) {
+  return FLT ? (__int_as_float(a) > __int_as_float(b)) : (a > b);
+}
+
+template <bool FLT>
 __global__ void __launch_bounds__(256) k_check_sorted(const int* __restrict__ x, long long n,
                                                       SortResult* res) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long bad = -1;
   for (long long i = tid; i + 1 < n && bad < 0; i += stride)
-    if (__ldg(x + i) > __ldg(x + i + 1)) bad = i;
+    if (gt_key<FLT>(__ldg(x + i), __ldg(x + i + 1))) bad = i;
   unsigned long long enc = bad >= 0 ? ~(unsigned long long)bad : 0ull;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -489,7 +509,10 @@ int grid_for(long long units, int num_sms, int per_sm) {
 
 size_t sort_scratch_bytes(long long n) { return layout(n).total; }
 
-cudaError_t launch_sort(const int32_t* in, int32_t* out, long long n, bool contracts,
+namespace {
+
+template <bool FLT>
+cudaError_t sort_impl(const int32_t* in, int32_t* out, long long n, bool contracts,
                         void* scratch, SortResult* res, cudaStream_t s, int num_sms,
                         int64_t* kernels, const SortInject* inject, Prof* prof) {
   if (n <= 0) return cudaSuccess;
@@ -503,17 +526,17 @@ cudaError_t launch_sort(const int32_t* in, int32_t* out, long long n, bool contr
   cudaError_t e = cudaMemsetAsync(base, 0, L.zero_bytes, s);
   if (e != cudaSuccess) return e;
   prof_begin(prof, "radix_hist", s);
-  k_radix_hist<<<grid_for((n + 3) / 4 / 8, num_sms, 8), 256, 0, s>>>(in, n, h, res);
+  k_radix_hist<FLT><<<grid_for((n + 3) / 4 / 8, num_sms, 8), 256, 0, s>>>(in, n, h, res);
   prof_end(prof, s);
   const unsigned ntiles = (unsigned)((n + kTile - 1) / kTile);
   prof_begin(prof, "onesweep", s);
-  k_onesweep<false, false><<<ntiles, kSortBlock, 0, s>>>(in, tmp, n, 0, h, st32[0], st64, res);
+  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(in, tmp, n, 0, h, st32[0], st64, res);
   prof_end(prof, s);
   prof_begin(prof, "onesweep", s);
-  k_onesweep<false, false><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 1, h, st32[1], st64, res);
+  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 1, h, st32[1], st64, res);
   prof_end(prof, s);
   prof_begin(prof, "onesweep", s);
-  k_onesweep<false, false><<<ntiles, kSortBlock, 0, s>>>(out, tmp, n, 2, h, st32[2], st64, res);
+  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(out, tmp, n, 2, h, st32[2], st64, res);
   prof_end(prof, s);
   if (inject && inject->mode == 1 && inject->i < n && inject->j < n) {
     // swap through the (now free) output buffer: stream-ordered host copies
@@ -534,21 +557,34 @@ cudaError_t launch_sort(const int32_t* in, int32_t* out, long long n, bool contr
   unsigned* st_last = reinterpret_cast<unsigned*>(st64);
   prof_begin(prof, contracts ? "onesweep_last_checked" : "onesweep", s);
   if (contracts)
-    k_onesweep<true, true><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res);
+    k_onesweep<true, true, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res);
   else
-    k_onesweep<true, false><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res);
+    k_onesweep<true, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res);
   prof_end(prof, s);
   *kernels += 5;
   return cudaGetLastError();
 }
 
+}  // namespace
+
+cudaError_t launch_sort(const int32_t* in, int32_t* out, long long n, bool contracts,
+                        void* scratch, SortResult* res, cudaStream_t s, int num_sms,
+                        int64_t* kernels, const SortInject* inject, Prof* prof, bool flt) {
+  return flt ? sort_impl<true>(in, out, n, contracts, scratch, res, s, num_sms, kernels, inject,
+                               prof)
+             : sort_impl<false>(in, out, n, contracts, scratch, res, s, num_sms, kernels, inject,
+                                prof);
+}
+
 size_t check_scratch_bytes() { return 0; }
 
 cudaError_t launch_check_sorted(const int32_t* x, long long n, SortResult* res, void*,
-                                cudaStream_t s, int num_sms, int64_t* kernels, Prof* prof) {
+                                cudaStream_t s, int num_sms, int64_t* kernels, Prof* prof,
+                                bool flt) {
   if (n <= 1) return cudaSuccess;
   prof_begin(prof, "check_sorted", s);
-  k_check_sorted<<<grid_for(n, num_sms, 8), 256, 0, s>>>(x, n, res);
+  if (flt) k_check_sorted<true><<<grid_for(n, num_sms, 8), 256, 0, s>>>(x, n, res);
+  else k_check_sorted<false><<<grid_for(n, num_sms, 8), 256, 0, s>>>(x, n, res);
   prof_end(prof, s);
   *kernels += 1;
   return cudaGetLastError();

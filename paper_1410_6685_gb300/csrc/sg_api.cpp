@@ -538,14 +538,15 @@ sg_status sg_scalar_release(sg_scalar* s) {
 
 sg_status sg_sort(sg_ctx* c, sg_vector* keys, sg_vector** out) {
   if (!c || check_vec(keys) || !out || keys->ctx != c) return fail(c, SG_ERR_INVALID_ARG, "bad sort");
-  if (keys->v->dt != SG_I32) return fail(c, SG_ERR_DTYPE, "sort keys must be SG_I32");
+  if (keys->v->dt != SG_I32 && keys->v->dt != SG_F32)
+    return fail(c, SG_ERR_DTYPE, "sort keys must be SG_I32 or SG_F32");
   sg_status s = known_count(keys);
   if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
   if (keys->v->n >= (int64_t(1) << 30)) return fail(c, SG_ERR_SHAPE, "sort supports n < 2^30");
   NodeP n = new_node(c, NK::SORT);
   n->nin = 1;
   use(n.get(), 0, keys->v);
-  make_out(c, SG_I32, keys->v->n, keys->v->n, 1, &n->out);
+  make_out(c, keys->v->dt, keys->v->n, keys->v->n, 1, &n->out);
   ValueP outv = n->out, inv = keys->v;
   sg_vector* h = new_handle(c, n->out, false);
   enqueue(c, std::move(n));
@@ -696,7 +697,8 @@ static sg_status attach(sg_ctx* c, void* target, const sg_contract* k, int32_t* 
       break;
     }
     case SG_C_SORTED:
-      if (t->v->dt != SG_I32) return fail(c, SG_ERR_DTYPE, "sortedness contract needs SG_I32");
+      if (t->v->dt != SG_I32 && t->v->dt != SG_F32)
+        return fail(c, SG_ERR_DTYPE, "sortedness contract needs SG_I32 or SG_F32");
       if (!active) return SG_OK;
       n->nin = 1;
       use(n.get(), 0, t->v);
@@ -704,8 +706,8 @@ static sg_status attach(sg_ctx* c, void* target, const sg_contract* k, int32_t* 
     case SG_C_PERMUTATION: {
       if (k->nother != 1) return fail(c, SG_ERR_INVALID_ARG, "permutation needs other[0]");
       sg_vector* o = static_cast<sg_vector*>(k->other[0]);
-      if (t->v->dt != SG_I32 || o->v->dt != SG_I32)
-        return fail(c, SG_ERR_DTYPE, "permutation contract needs SG_I32");
+      if ((t->v->dt != SG_I32 && t->v->dt != SG_F32) || o->v->dt != t->v->dt)
+        return fail(c, SG_ERR_DTYPE, "permutation contract needs two SG_I32 or two SG_F32 vectors");
       sg_status s = known_count(t);
       if (!s) s = known_count(o);
       if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;

@@ -119,16 +119,19 @@ struct SortInject {
   long long i, j;
 };
 // in -> out (distinct buffers).  Scratch must hold sort_scratch_bytes(n).
+// flt: the 32-bit keys are binary32 patterns sorted in IEEE totalOrder
+// (else signed int32 order).
 cudaError_t launch_sort(const int32_t* in, int32_t* out, long long n,
                         bool contracts, void* scratch, SortResult* res,
                         cudaStream_t s, int num_sms, int64_t* kernels,
-                        const SortInject* inject, Prof* prof);
-// Stand-alone checks on any int32 vector (re-read).  `res` must be zeroed
+                        const SortInject* inject, Prof* prof, bool flt);
+// Stand-alone checks on any 32-bit vector (re-read).  `res` must be zeroed
 // by the caller's conventions: these kernels set only their own fields.
 size_t check_scratch_bytes();
+// flt: binary32 values in the IEEE comparison (NaN never out of order)
 cudaError_t launch_check_sorted(const int32_t* x, long long n, SortResult* res,
                                 void* scratch, cudaStream_t s, int num_sms,
-                                int64_t* kernels, Prof* prof);
+                                int64_t* kernels, Prof* prof, bool flt);
 cudaError_t launch_check_perm(const int32_t* x, const int32_t* ref, long long n,
                               SortResult* res, void* scratch, cudaStream_t s,
                               int num_sms, int64_t* kernels, Prof* prof);

@@ -694,7 +694,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
                              static_cast<int32_t*>(n->out->st->ptr), P.n,
                              P.chk_sorted || P.chk_perm, dwork,
                              static_cast<sgk::SortResult*>(rec), c->stream, c->num_sms,
-                             &c->kernels, &c->inject, &c->prof);
+                             &c->kernels, &c->inject, &c->prof, n->in[0]->dt == SG_F32);
         c->inject = sgk::SortInject{};
         break;
       }
@@ -702,7 +702,8 @@ sg_status sg_execute_pending(sg_ctx* c) {
         Node* n = P.main;
         e = sgk::launch_check_sorted(static_cast<const int32_t*>(n->in[0]->st->ptr), P.n,
                                      static_cast<sgk::SortResult*>(rec), dwork, c->stream,
-                                     c->num_sms, &c->kernels, &c->prof);
+                                     c->num_sms, &c->kernels, &c->prof,
+                                     n->in[0]->dt == SG_F32);
         break;
       }
       case PK::CHECK_PERM: {

@@ -8,6 +8,7 @@ A small command-line driver for measuring and profiling single kernels:
     python -m paper_1410_6685_gb300.workloads solve  [--n N] [--reps R] [--prec 0|1|2]
     python -m paper_1410_6685_gb300.workloads batch  [--reps R]
     python -m paper_1410_6685_gb300.workloads filter [--n N] [--reps R]
+    python -m paper_1410_6685_gb300.workloads transpose [--n N] [--reps R]
 
 Each prints one JSON line: per kernel name, launches and mean milliseconds
 (CUDA events bracketing each launch on the context's stream), plus the
@@ -26,7 +27,8 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["sort", "stream", "gemm", "solve", "batch", "filter"])
+    ap.add_argument("case", choices=["sort", "stream", "gemm", "solve", "batch", "filter",
+                                     "transpose"])
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--prec", type=int, default=1)
@@ -145,6 +147,30 @@ def main(argv=None):
                             *(t.data_ptr() for t in outs))
         out["kernels"] = run(step)
         out["bytes_per_launch"] = 4 * total + 24 * nseg
+    elif a.case == "transpose":
+        # Listing 1: transpose (materialised), then A^T x with the transpose
+        # folded into the left product, then the right product A x
+        n = a.n or 8192
+        g = torch.Generator(device="cuda").manual_seed(12)
+        A = torch.randn(n, n, device="cuda", generator=g)
+        x = torch.randn(n, device="cuda", generator=g)
+        mA, vx = sg.wrap_tensor(ctx, A), sg.wrap_tensor(ctx, x)
+        keep += [A, x]
+
+        def step():
+            t = sg.sg_transpose(ctx, mA)
+            sg.sg_flush(ctx)
+            sg.sg_matrix_release(t)
+            t = sg.sg_transpose(ctx, mA)
+            y = sg.sg_matvec(ctx, t, vx)
+            sg.sg_matrix_release(t)
+            z = sg.sg_matvec(ctx, mA, vx)
+            sg.sg_flush(ctx)
+            sg.sg_vector_release(y)
+            sg.sg_vector_release(z)
+        out["kernels"] = run(step)
+        out["bytes_per_transpose"] = 8 * n * n
+        out["bytes_per_product"] = 4 * n * n
     torch.cuda.synchronize()
     sg.sg_destroy(ctx)
     print(json.dumps(out), flush=True)

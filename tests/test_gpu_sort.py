@@ -10,7 +10,7 @@ from paper_1410_6685_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TILE = 4096
+TILE = 6144   # keys per tile of the onesweep kernel
 
 
 @pytest.fixture(scope="module")
@@ -185,3 +185,81 @@ def test_contracts_off_sort(env):
         assert np.array_equal(got, last_pass(bad))
     finally:
         sg.sg_set_contract_mode(ctx, sg.SG_CONTRACTS_PRE_POST)
+
+
+# ---- binary32 keys (Listing 4 sorts REAL_32), IEEE totalOrder ----
+
+SPECIAL = np.array([0xFFC00005, 0xFFC00001, 0xFF800000, 0xC0200000, 0x80000001, 0x80000000,
+                    0x00000000, 0x00000001, 0x3F800000, 0x7F800000, 0x7FC00001, 0x7FC00005],
+                   dtype=np.uint32).view(np.float32)
+
+
+def float_keys(n, seed):
+    g = np.random.default_rng(seed)
+    x = (g.standard_normal(n) * np.float32(1e3)).astype(np.float32)
+    if n >= 64:
+        idx = g.choice(n, min(n // 8, 4096), replace=False)
+        x[idx] = SPECIAL[g.integers(0, len(SPECIAL), len(idx))]
+    return x
+
+
+def run_sort_f32(env, keys, flush_ok=True):
+    sg, ctx, torch = env
+    t = torch.from_numpy(np.ascontiguousarray(keys, dtype=np.float32)).cuda()
+    v = sg.sg_vector_wrap(ctx, sg.SG_F32, len(keys), t.data_ptr())
+    out = sg.sg_sort(ctx, v)
+    if flush_ok:
+        sg.sg_flush(ctx)
+    return v, out, t
+
+
+@pytest.mark.parametrize("n", [1, 2, 12, 100, TILE - 1, TILE + 1, 3 * TILE + 17, 1 << 20])
+def test_sort_f32_total_order_bit_exact(env, n):
+    keys = float_keys(n, 2000 + n) if n != 12 else SPECIAL[::-1].copy()
+    v, out, t = run_sort_f32(env, keys)
+    sg, ctx, _ = env
+    got = sg.sg_vector_read(ctx, out, np.empty(n, np.float32))
+    assert np.array_equal(got.view(np.uint32), oracle.sort_f32(keys).view(np.uint32))
+    assert oracle.first_unsorted_f32(got) == -1
+
+
+def test_sort_f32_full_size(env):
+    """2^26 binary32 keys (N(0,1e3) with special values planted)."""
+    n = 1 << 26
+    keys = float_keys(n, 5)
+    v, out, t = run_sort_f32(env, keys)
+    sg, ctx, _ = env
+    got = sg.sg_vector_read(ctx, out, np.empty(n, np.float32))
+    assert np.array_equal(got.view(np.uint32), oracle.sort_f32(keys).view(np.uint32))
+
+
+def test_sort_f32_fused_checks_catch_planted_swap(env):
+    sg, ctx, _ = env
+    n = 3 * TILE + 17
+    keys = float_keys(n, 9)
+    sg.sg_debug_inject_sort(ctx, sg.SG_INJECT_SWAP, 3, n - 2)
+    v, out, t = run_sort_f32(env, keys, flush_ok=False)
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_flush(ctx)
+    assert e.value.status == sg.SG_ERR_POSTCONDITION
+    assert sg.sg_last_violation(ctx).kind == sg.SG_C_SORTED
+
+
+def test_sorted_contract_f32_ieee_comparison(env):
+    """A user-attached sortedness contract on binary32 data uses the IEEE
+    comparison: +0 before -0 and NaNs are not violations; 2 > 1 is."""
+    sg, ctx, torch = env
+    for data, first in [(np.array([1.0, 2.0, np.nan, 0.5, 3.0], np.float32), -1),
+                        (np.array([0.0, -0.0, 1.0], np.float32), -1),
+                        (np.array([0.0, 1.0, 2.0, 1.0, 5.0], np.float32), 2)]:
+        assert oracle.first_unsorted_f32(data) == first
+        t = torch.from_numpy(data).cuda()
+        v = sg.sg_vector_wrap(ctx, sg.SG_F32, len(data), t.data_ptr())
+        sg.sg_ensure(ctx, v, sg.contract(sg.SG_C_SORTED))
+        if first < 0:
+            sg.sg_flush(ctx)
+        else:
+            with pytest.raises(sg.SgError):
+                sg.sg_flush(ctx)
+            assert sg.sg_last_violation(ctx).first_index == first
+        sg.sg_vector_release(v)
