@@ -152,6 +152,20 @@ sg_status sg_vector_count(sg_vector* v, int64_t* n);
 /* Device address of the vector's storage after flushing it (for interop). */
 sg_status sg_vector_device_ptr(sg_vector* v, void** dev_ptr);
 sg_status sg_vector_release(sg_vector* v);
+/* item (Table 2): element i (0-based) into *value (dtype-sized); flushes the
+ * work the vector depends on.  SG_ERR_SHAPE for i outside [0, count),
+ * SG_ERR_POISONED as sg_vector_read. */
+sg_status sg_vector_item(sg_vector* v, int64_t i, void* value);
+/* concatenate (Table 2): a new vector, a's elements then b's (same dtype),
+ * deferred; counts must be known, so a pending filter operand is flushed
+ * first (its count is data-dependent).  Errors: SG_ERR_DTYPE. */
+sg_status sg_concat(sg_ctx* ctx, sg_vector* a, sg_vector* b, sg_vector** out);
+/* subset (Table 2): elements [start, finish) of v (0-based, half-open) as a
+ * vector that shares v's memory: writes through either are seen by both.
+ * v is flushed first if pending.  Errors: SG_ERR_SHAPE unless
+ * 0 <= start <= finish <= count. */
+sg_status sg_subset(sg_ctx* ctx, sg_vector* v, int64_t start, int64_t finish,
+                    sg_vector** out);
 
 /* Matrices (Sec. 3.4): rows x cols, row-major, same ownership rules. */
 sg_status sg_matrix_create(sg_ctx* ctx, sg_dtype dt, int64_t rows, int64_t cols,

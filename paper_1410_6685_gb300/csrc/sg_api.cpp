@@ -122,6 +122,14 @@ sg_status known_count(sg_vector* v) {
   return sg_flush(v->ctx);
 }
 
+// A queued in-place write (for_each) lands in memory that v shares (v
+// itself, or a subset view of the same allocation): reading v must flush.
+bool pending_write_to(sg_ctx* c, const Value* v) {
+  for (auto& n : c->pending)
+    if (n->inplace && n->out && storage_related(n->out->st.get(), v->st.get())) return true;
+  return false;
+}
+
 sg_vector* new_handle(sg_ctx* c, ValueP v, bool matrix) {
   sg_vector* h = matrix ? static_cast<sg_vector*>(new sg_matrix) : new sg_vector;
   h->ctx = c;
@@ -282,7 +290,7 @@ sg_status sg_vector_wrap(sg_ctx* c, sg_dtype dt, int64_t n, void* p, sg_vector**
 static sg_status read_common(sg_vector* h, void* host, int64_t n) {
   if (check_vec(h) || (!host && n > 0)) return SG_ERR_INVALID_ARG;
   sg_ctx* c = h->ctx;
-  if (h->v->producer || !h->v->count_known) {
+  if (h->v->producer || !h->v->count_known || pending_write_to(c, h->v.get())) {
     sg_status s = sg_flush(c);
     if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
   }
@@ -311,7 +319,7 @@ sg_status sg_vector_count(sg_vector* h, int64_t* n) {
 
 static sg_status devptr_common(sg_vector* h, void** p) {
   if (check_vec(h) || !p) return SG_ERR_INVALID_ARG;
-  if (h->v->producer || !h->v->count_known) {
+  if (h->v->producer || !h->v->count_known || pending_write_to(h->ctx, h->v.get())) {
     sg_status s = sg_flush(h->ctx);
     if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
   }
@@ -321,6 +329,67 @@ static sg_status devptr_common(sg_vector* h, void** p) {
 }
 
 sg_status sg_vector_device_ptr(sg_vector* h, void** p) { return devptr_common(h, p); }
+
+sg_status sg_vector_item(sg_vector* h, int64_t i, void* value) {
+  if (check_vec(h) || !value) return SG_ERR_INVALID_ARG;
+  sg_ctx* c = h->ctx;
+  if (h->v->producer || !h->v->count_known || pending_write_to(c, h->v.get())) {
+    sg_status s = sg_flush(c);
+    if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
+  }
+  if (h->v->poisoned) return fail(c, SG_ERR_POISONED, "value depends on a failed contract");
+  if (i < 0 || i >= h->v->n)
+    return fail(c, SG_ERR_SHAPE, "item %lld of a vector of %lld", (long long)i, (long long)h->v->n);
+  if (c->planning_only) return fail(c, SG_ERR_UNSUPPORTED, "planning-only context");
+  const size_t es = dtype_size(h->v->dt);
+  cudaError_t e = cudaMemcpyAsync(value, static_cast<const char*>(h->v->st->ptr) + (size_t)i * es,
+                                  es, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, SG_ERR_CUDA, "item copy failed: %s", cudaGetErrorString(e));
+  return SG_OK;
+}
+
+sg_status sg_concat(sg_ctx* c, sg_vector* a, sg_vector* b, sg_vector** out) {
+  if (!c || check_vec(a) || check_vec(b) || a->ctx != c || b->ctx != c || !out)
+    return fail(c, SG_ERR_INVALID_ARG, "bad concatenate");
+  if (a->v->dt != b->v->dt) return fail(c, SG_ERR_DTYPE, "concatenate of different dtypes");
+  sg_status s = known_count(a);
+  if (!s) s = known_count(b);
+  if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
+  NodeP n = new_node(c, NK::CONCAT);
+  n->nin = 2;
+  use(n.get(), 0, a->v);
+  use(n.get(), 1, b->v);
+  const int64_t len = a->v->n + b->v->n;
+  make_out(c, a->v->dt, len, len, 1, &n->out);
+  sg_vector* h = new_handle(c, n->out, false);
+  enqueue(c, std::move(n));
+  *out = h;
+  return SG_OK;
+}
+
+sg_status sg_subset(sg_ctx* c, sg_vector* v, int64_t start, int64_t finish, sg_vector** out) {
+  if (!c || check_vec(v) || v->ctx != c || !out) return fail(c, SG_ERR_INVALID_ARG, "bad subset");
+  if (v->v->producer || !v->v->count_known) {
+    sg_status s = sg_flush(c);
+    if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
+  }
+  if (v->v->poisoned) return fail(c, SG_ERR_POISONED, "value depends on a failed contract");
+  if (start < 0 || start > finish || finish > v->v->n)
+    return fail(c, SG_ERR_SHAPE, "subset [%lld, %lld) of a vector of %lld", (long long)start,
+                (long long)finish, (long long)v->v->n);
+  const size_t es = dtype_size(v->v->dt);
+  auto view = std::make_shared<Storage>();
+  view->ptr = v->v->st ? static_cast<char*>(v->v->st->ptr) + (size_t)start * es : nullptr;
+  view->bytes = (size_t)(finish - start) * es;
+  view->owned = false;
+  view->parent = v->v->st;
+  ValueP nv;
+  make_out(c, v->v->dt, finish - start, finish - start, 1, &nv);
+  nv->st = std::move(view);
+  *out = new_handle(c, nv, false);
+  return SG_OK;
+}
 
 sg_status sg_vector_release(sg_vector* h) {
   if (!h) return SG_ERR_INVALID_ARG;

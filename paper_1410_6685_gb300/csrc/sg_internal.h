@@ -112,6 +112,9 @@ struct SortResult {
 };
 static_assert(sizeof(SortResult) <= kResultBytes, "result too large");
 
+// bytes from src to dst (no overlap), on stream s
+cudaError_t launch_copy(void* dst, const void* src, size_t bytes, int num_sms, cudaStream_t s);
+
 size_t sort_scratch_bytes(long long n);
 // Host-side fault planted before the last pass (contract tests only).
 struct SortInject {

@@ -40,7 +40,8 @@ struct Op {
   float cst;
 };
 
-enum class PK { STREAM, FILTER, SORT, CHECK_SORTED, CHECK_PERM, MATMUL, FREIVALDS, TRANSPOSE, MATVEC };
+enum class PK { STREAM, FILTER, SORT, CHECK_SORTED, CHECK_PERM, MATMUL, FREIVALDS, TRANSPOSE, MATVEC,
+                CONCAT };
 
 struct Pass {
   PK kind = PK::STREAM;
@@ -138,7 +139,7 @@ struct Planner {
   bool dead(Node* n) {
     // a map / transpose / product whose result nobody will ever see is not computed
     const bool pure = (n->kind == NK::MAP && !n->inplace) || n->kind == NK::TRANSPOSE ||
-                      n->kind == NK::MATVEC;
+                      n->kind == NK::MATVEC || n->kind == NK::CONCAT;
     if (!pure) return false;
     Value* v = n->out.get();
     return v->handles == 0 && consumers.find(v) == consumers.end();
@@ -196,6 +197,17 @@ struct Planner {
 
   // Try to add node n to the open stream pass; all-or-nothing.
   bool try_add(Pass& P, Node* n) {
+    // memory written in place earlier in this pass is only read through the
+    // written value itself (a subset view of it starts a new pass)
+    for (Node* m : P.nodes) {
+      if (!m->inplace) continue;
+      for (int k = 0; k < n->nin; ++k) {
+        Value* v = n->in[k].get();
+        if (v && v != m->out.get() && v != m->in[0].get() &&
+            storage_related(v->st.get(), m->out->st.get()))
+          return false;
+      }
+    }
     Pass T = P;   // tentative copy (small)
     std::vector<Op> ops;
     int extra = 0;
@@ -313,6 +325,7 @@ struct Planner {
           }
           P.kind = PK::TRANSPOSE;
           break;
+        case NK::CONCAT: P.kind = PK::CONCAT; break;
         case NK::MATVEC:
           P.kind = PK::MATVEC;
           if (!n->left && n->in[0]->producer && virtual_t.count(n->in[0]->producer))
@@ -572,7 +585,8 @@ sg_status sg_execute_pending(sg_ctx* c) {
       case PK::CHECK_PERM: work = std::max(work, sgk::check_scratch_bytes()); break;
       case PK::MATMUL:
       case PK::FREIVALDS: work = std::max(work, sg_linalg_scratch(c, P.main, P.chk_frv)); break;
-      case PK::TRANSPOSE: break;
+      case PK::TRANSPOSE:
+      case PK::CONCAT: break;
       case PK::MATVEC: {
         const Node* n = P.main;
         const Value* A = P.vtrans ? P.vtrans->in[0].get() : n->left ? n->in[1].get() : nullptr;
@@ -589,7 +603,24 @@ sg_status sg_execute_pending(sg_ctx* c) {
   }
   char* dres = static_cast<char*>(c->scratch);
   void* dwork = dres + res_bytes;
-  cudaError_t e = cudaMemsetAsync(dres, 0, res_bytes, c->stream);
+  // Passes that leave nothing for the host (pure maps, transposes, products,
+  // concatenations) need no result records: then the flush neither clears
+  // nor reads them back and does not wait for the device -- stream order
+  // keeps every later use correct, and reads synchronise.
+  bool need_records = false;
+  for (Pass& P : passes) {
+    switch (P.kind) {
+      case PK::STREAM:
+        need_records |= !P.prog.empty() && (P.reduce_of != nullptr || !P.preds.empty());
+        break;
+      case PK::MATMUL: need_records |= P.chk_frv != nullptr; break;
+      case PK::TRANSPOSE:
+      case PK::MATVEC:
+      case PK::CONCAT: break;
+      default: need_records = true; break;
+    }
+  }
+  cudaError_t e = need_records ? cudaMemsetAsync(dres, 0, res_bytes, c->stream) : cudaSuccess;
   sg_status status = SG_OK;
 
   for (size_t i = 0; i < passes.size() && e == cudaSuccess && !status; ++i) {
@@ -718,6 +749,22 @@ sg_status sg_execute_pending(sg_ctx* c) {
       case PK::FREIVALDS:
         status = sg_exec_linalg(c, P.main, P.chk_frv, rec, dwork, &e);
         break;
+      case PK::CONCAT: {
+        Node* n = P.main;
+        status = ensure_storage(c, n->out.get());
+        if (status) break;
+        const Value* a = n->in[0].get();
+        const Value* b = n->in[1].get();
+        const size_t es = (a->dt == SG_F64 || a->dt == SG_I64) ? 8
+                          : (a->dt == SG_BF16 || a->dt == SG_F16) ? 2 : 4;
+        char* dst = static_cast<char*>(n->out->st->ptr);
+        if (a->n) e = sgk::launch_copy(dst, a->st->ptr, (size_t)a->n * es, c->num_sms, c->stream);
+        if (e == cudaSuccess && b->n)
+          e = sgk::launch_copy(dst + (size_t)a->n * es, b->st->ptr, (size_t)b->n * es, c->num_sms,
+                               c->stream);
+        c->kernels += 2;
+        break;
+      }
       case PK::TRANSPOSE: {
         Node* n = P.main;
         status = ensure_storage(c, n->out.get());
@@ -753,10 +800,11 @@ sg_status sg_execute_pending(sg_ctx* c) {
       }
     }
   }
-  if (e == cudaSuccess && !status)
+  if (e == cudaSuccess && !status && need_records)
     e = cudaMemcpyAsync(c->host_res, dres, passes.size() * sgk::kResultBytes,
                         cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess && !status) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && !status && need_records) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && !status && !need_records) e = cudaGetLastError();
   if (e != cudaSuccess && !status) status = cuda_fail(c, e, "kernel execution");
   if (e == cudaSuccess) c->prof.collect();
 
@@ -830,6 +878,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
         }
         case PK::TRANSPOSE:
         case PK::MATVEC:
+        case PK::CONCAT:
           break;
         case PK::MATMUL:
         case PK::FREIVALDS: {
@@ -903,6 +952,10 @@ sg_status sg_describe_pending(sg_ctx* c, std::string* out) {
       case PK::TRANSPOSE:
         snprintf(buf, sizeof buf, "transpose %lldx%lld\n", (long long)P.main->in[0]->rows,
                  (long long)P.main->in[0]->cols);
+        break;
+      case PK::CONCAT:
+        snprintf(buf, sizeof buf, "concat %lld+%lld\n", (long long)P.main->in[0]->n,
+                 (long long)P.main->in[1]->n);
         break;
       case PK::MATVEC: {
         const Node* n = P.main;

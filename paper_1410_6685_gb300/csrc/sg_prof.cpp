@@ -32,6 +32,8 @@ void Prof::end(cudaStream_t s) {
 void Prof::collect() {
   for (Rec& r : open) {
     float ms = 0.0f;
+    // a flush that leaves no results does not wait for the device itself
+    cudaEventSynchronize(r.b);
     if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       auto& a = agg[r.name];
       a.first += 1;

@@ -19,6 +19,7 @@ struct Storage {
   size_t bytes = 0;
   bool owned = false;
   cudaStream_t stream = nullptr;
+  std::shared_ptr<Storage> parent;   // a subset's view keeps its source alive
   ~Storage();
 };
 
@@ -36,6 +37,14 @@ struct Value {
 };
 using ValueP = std::shared_ptr<Value>;
 
+// Two storages share memory: the same allocation, or subset views of one.
+inline bool storage_related(const Storage* a, const Storage* b) {
+  if (!a || !b) return false;
+  while (a->parent) a = a->parent.get();
+  while (b->parent) b = b->parent.get();
+  return a == b;
+}
+
 struct ScalarVal {
   bool done = false;
   bool poisoned = false;
@@ -45,7 +54,7 @@ struct ScalarVal {
 };
 using ScalarP = std::shared_ptr<ScalarVal>;
 
-enum class NK { MAP, REDUCE, QUANT, CHECK, FILTER, SORT, MATMUL, TRANSPOSE, MATVEC };
+enum class NK { MAP, REDUCE, QUANT, CHECK, FILTER, SORT, MATMUL, TRANSPOSE, MATVEC, CONCAT };
 
 struct Node {
   int id = 0;

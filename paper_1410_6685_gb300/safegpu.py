@@ -14,6 +14,8 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsafegpu.so")
 
@@ -125,6 +127,8 @@ def _load():
         "sg_scalar_release": [vp], "sg_sort": [vp, vp, P(vp)],
         "sg_matmul": [vp, vp, vp, i32, P(vp)],
         "sg_transpose": [vp, vp, P(vp)], "sg_matvec": [vp, vp, vp, P(vp)],
+        "sg_vector_item": [vp, i64, vp], "sg_concat": [vp, vp, vp, P(vp)],
+        "sg_subset": [vp, vp, i64, i64, P(vp)],
         "sg_vecmat": [vp, vp, vp, P(vp)],
         "sg_solve": [vp, vp, vp, P(SgSolveOpts), P(vp), P(SgSolveInfo)],
         "sg_det": [vp, vp, i32, P(SgDetResult)],
@@ -364,6 +368,20 @@ def sg_sort(ctx, keys):
 
 def sg_matmul(ctx, A, B, precision=SG_PREC_F32_SIMT):
     return _out(lib.sg_matmul, ctx, ctx, A, B, precision)
+
+
+def sg_vector_item(ctx, v, i, dtype=np.float32):
+    out = np.zeros(1, dtype=dtype)
+    _check(lib.sg_vector_item(v, i, C.c_void_p(out.ctypes.data)), ctx)
+    return out[0]
+
+
+def sg_concat(ctx, a, b):
+    return _out(lib.sg_concat, ctx, ctx, a, b)
+
+
+def sg_subset(ctx, v, start, finish):
+    return _out(lib.sg_subset, ctx, ctx, v, start, finish)
 
 
 def sg_transpose(ctx, A):
