@@ -392,6 +392,47 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
     gbs = (4.0 * total + 24 * nseg) / (ms / 1e3) / 1e9
     out["batch_10000"] = {"elements": total, "ms": round(ms, 4), "GBps": round(gbs, 1),
                           "frac_hbm": round(gbs / hbm_peak, 4)}
+
+    # 6. schedule of that batch: the 2x64 MLP cost model, trained on the GPU on
+    #    autotuner sweeps of 56 smaller synthetic batches (never this one),
+    #    against the plain table and the autotuner's measured best
+    rng = np.random.default_rng(12)
+    sg.sg_set_scheduler(ctx, sg.SG_SCHED_AUTOTUNE)
+    keep = []
+    for _ in range(56):
+        lo = int(rng.integers(4, 9))
+        hi = int(rng.integers(lo + 2, 19))
+        ns = int(rng.integers(100, 3000))
+        while ns * 2.0 ** ((lo + hi) / 2) > 2.5e7:
+            ns //= 2
+        ns = max(ns, 16)
+        Ls = np.floor(2.0 ** (lo + (hi - lo) * rng.random(ns))).astype(np.int64)
+        offs = inputs.batch_offsets(Ls)
+        xs = torch.rand(max(int(offs[-1]), 1), device="cuda") * 2 - 1
+        ts = torch.from_numpy(offs).cuda()
+        os_ = (torch.empty(ns, dtype=torch.float64, device="cuda"),
+               torch.empty(ns, dtype=torch.int64, device="cuda"),
+               torch.empty(ns, dtype=torch.int64, device="cuda"))
+        sg.sg_batch_run(ctx, ch, xs.data_ptr(), ts.data_ptr(), ns, *(t.data_ptr() for t in os_))
+        keep.append((xs, ts, os_))
+    t0 = time.perf_counter()
+    loss = sg.sg_sched_train(ctx, epochs=400, lr=3e-3, seed=7)
+    t_train = time.perf_counter() - t0
+    del keep
+    r = sg.sg_batch_report(ctx, ch, xb.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
+    t_us = np.array(r.measured_us[:r.ncand])
+    best = float(t_us.min())
+    out["batch_10000_schedule"] = {
+        "candidates": int(r.ncand),
+        "plain_table_ms": round(t_us[r.default_index] / 1e3, 4),
+        "learned_ms": round(t_us[r.learned_index] / 1e3, 4),
+        "autotuned_best_ms": round(best / 1e3, 4),
+        "regret_plain": round(t_us[r.default_index] / best - 1, 4),
+        "regret_learned": round(t_us[r.learned_index] / best - 1, 4),
+        "learned_choice": {"chunk": int(r.chunk[r.learned_index]),
+                           "ctas_per_sm": int(r.ctas_per_sm[r.learned_index])},
+        "train_records": int(sg.sg_sched_log(ctx)[1].shape[0]), "train_loss": round(loss, 5),
+        "train_s": round(t_train, 2)}
     return out
 
 

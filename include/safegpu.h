@@ -468,12 +468,17 @@ sg_status sg_batch_run(sg_ctx* ctx, const sg_chain* chain, const float* data,
 /* ------------------------------------------------------------------------ */
 /* Schedule choice for the batched launch: a schedule is (elements per work
  * item, CTAs per SM).  SG_SCHED_AUTOTUNE measures every candidate the first
- * time a workload (offsets pointer, count, chain) is seen and keeps the
- * fastest; SG_SCHED_LEARNED runs the schedule the trained 2x64 MLP cost
- * model predicts fastest, without measuring (while no model is trained it
- * behaves as SG_SCHED_AUTOTUNE).  Every batched run is timed with CUDA events
- * and logged as (12 features, log microseconds); sg_sched_train fits the
- * model to that log on the GPU with the kernels below.                      */
+ * time a workload (offsets pointer, count, chain) is seen -- a warm-up run,
+ * then the better of two runs timed with CUDA events -- and keeps the
+ * fastest; each measurement is logged as (12 features, log microseconds,
+ * log of the time relative to the plain table's choice on that workload).
+ * sg_sched_train fits the 2x64 MLP cost model to the relative log-times on
+ * the GPU with the kernels below.  SG_SCHED_LEARNED then runs, without
+ * measuring, the candidate the model predicts fastest when it is predicted
+ * to beat the plain table's choice by more than 2%, else that choice (while
+ * no model is trained it behaves as SG_SCHED_AUTOTUNE).  In the report,
+ * predicted_us is the model's relative prediction times the plain choice's
+ * measured time.                                                            */
 #define SG_SCHED_MAX_CANDIDATES 32
 typedef struct {
   int32_t ncand;          /* candidates measured                               */

@@ -214,6 +214,17 @@ sg_status sg_init(int device, void* stream, sg_ctx** out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&c->counter, 64 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(c->counter, 0, 64 * sizeof(unsigned int));
+    if (e == cudaSuccess) {
+      // library values come from the device's stream-ordered pool; keep freed
+      // blocks in the pool (this process only) so that a value of the same
+      // size in the next step does not go back to the driver
+      cudaMemPool_t pool = nullptr;
+      if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+      cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
       cudaGetLastError();

@@ -95,8 +95,8 @@ sg_status read_stats(sg_ctx* c, Job& j) {
   return SG_OK;
 }
 
-// Runs the batch once with schedule `sch` (capturing its graph on first use),
-// times it with CUDA events, logs it.  *violated: a precondition failed.
+// Runs the batch once with schedule `sch` (capturing its graph on first use)
+// and times it with CUDA events.  *violated: a precondition failed.
 sg_status run_with(sg_ctx* c, const Job& j, const sg_sched_choice& sch, double* us,
                    bool* violated) {
   BatchKey key;
@@ -195,9 +195,6 @@ sg_status run_with(sg_ctx* c, const Job& j, const sg_sched_choice& sch, double* 
         }
       continue;
     }
-    float f[kSchedFeatures];
-    sg_batch_features(j.stats, sch, c->num_sms, f);
-    sg_sched_log_add(c, f, ms * 1000.0);
     if (us) *us = ms * 1000.0;
     *violated = (flag & 1u) != 0;
     return SG_OK;
@@ -229,7 +226,9 @@ sg_status prepare(sg_ctx* c, const sg_chain* ch, const float* data, const int64_
   return read_stats(c, *j);
 }
 
-// Autotune: measure every candidate (each twice, the second run counts).
+// Autotune: measure every candidate -- a warm-up run (graph capture, cold
+// caches), then the better of two timed runs -- and log the sweep with each
+// time relative to the plain table's choice.
 sg_status autotune(sg_ctx* c, const Job& j, std::vector<double>* times, int* best) {
   const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.depth);
   times->assign(cand.size(), 0.0);
@@ -237,15 +236,27 @@ sg_status autotune(sg_ctx* c, const Job& j, std::vector<double>* times, int* bes
   *best = 0;
   for (size_t i = 0; i < cand.size(); ++i) {
     bool viol = false;
-    double us = 0.0;
+    double us = 0.0, u2 = 0.0;
     sg_status st = run_with(c, j, cand[i], &us, &viol);
     if (!st) st = run_with(c, j, cand[i], &us, &viol);
+    if (!st) st = run_with(c, j, cand[i], &u2, &viol);
     if (st) return st;
+    us = std::min(us, u2);
     (*times)[i] = us;
     if (us < bt) {
       bt = us;
       *best = (int)i;
     }
+  }
+  const sg_sched_choice def = sg_batch_default(j.depth);
+  double tdef = 0.0;
+  for (size_t i = 0; i < cand.size(); ++i)
+    if (cand[i].chunk == def.chunk && cand[i].blocks_per_sm == def.blocks_per_sm) tdef = (*times)[i];
+  for (size_t i = 0; i < cand.size(); ++i) {
+    float f[kSchedFeatures];
+    sg_batch_features(j.stats, cand[i], c->num_sms, f);
+    const float rel = tdef > 0.0 ? (float)std::log((*times)[i] / tdef) : NAN;
+    sg_sched_log_add(c, f, (*times)[i], rel);
   }
   return SG_OK;
 }
@@ -274,9 +285,9 @@ extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* da
   sg_sched_choice pick = sg_batch_default(j.depth);
   bool chosen = false;
   if (c->sched == SG_SCHED_LEARNED) {
-    std::vector<float> pred;
-    if (sg_sched_predict(c, j.stats, cand, &pred)) {
-      pick = cand[std::min_element(pred.begin(), pred.end()) - pred.begin()];
+    const int li = sg_sched_learned_index(c, j.stats, cand, pick, nullptr);
+    if (li >= 0) {
+      pick = cand[li];
       chosen = true;
     }
   }
@@ -332,10 +343,13 @@ extern "C" sg_status sg_batch_report(sg_ctx* c, const sg_chain* ch, const float*
   out->best_index = best;
   out->learned_index = -1;
   std::vector<float> pred;
-  if (sg_sched_predict(c, j.stats, cand, &pred)) {
-    out->learned_index = (int32_t)(std::min_element(pred.begin(), pred.end()) - pred.begin());
-    for (int i = 0; i < out->ncand; ++i)
-      out->predicted_us[i] = std::exp((double)pred[i] * c->schedst.ysd + c->schedst.ymu);
+  const int li = sg_sched_learned_index(c, j.stats, cand, def, &pred);
+  if (li >= 0) {
+    out->learned_index = li;
+    // the model predicts times relative to the plain choice: scale by its
+    // measured time
+    const double tdef = out->default_index >= 0 ? times[out->default_index] : 0.0;
+    for (int i = 0; i < out->ncand; ++i) out->predicted_us[i] = std::exp((double)pred[i]) * tdef;
   }
   return SG_OK;
 }

@@ -117,6 +117,7 @@ constexpr int kSchedMaxCand = 64;
 struct SchedState {
   std::vector<float> log_x;   // records x kSchedFeatures
   std::vector<float> log_y;   // log microseconds
+  std::vector<float> log_rel; // log(us / us of the plain choice), NaN outside sweeps
   bool trained = false;
   std::vector<float> mu, sd;  // feature normalisation
   float ymu = 0.0f, ysd = 1.0f;

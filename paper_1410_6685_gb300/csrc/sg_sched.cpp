@@ -7,11 +7,14 @@
 //   [log2 nseg, log2 total, mean / std / min / max of log2(L+1), log2 of the
 //    work items, program ops / 48, depth / 8, log2 chunk, CTAs per SM / 8,
 //    work items per CTA slot (log2)]                              (d_in = 12)
-// Every executed batch is timed with CUDA events and logged as (features,
-// log microseconds).  The autotuner measures every candidate once per
-// workload and keeps the fastest; the learned chooser predicts the time of
-// every candidate with the MLP (trained on the log by the library's own GPU
-// kernels) and runs the predicted-fastest without measuring.
+// The autotuner measures every candidate of a workload (a warm-up run, then
+// the better of two timed runs, CUDA events) and keeps the fastest; each
+// measurement is logged as (features, log microseconds, log of the time
+// relative to the plain table's choice on the same workload).  The MLP,
+// trained on the GPU by the library's own kernels, predicts that relative
+// log-time; the learned chooser runs the predicted-fastest candidate when it
+// is predicted to beat the plain choice by more than 2%, else the plain
+// choice, without measuring.
 #include "sg_sched.h"
 
 #include <algorithm>
@@ -68,10 +71,11 @@ void sg_batch_features(const BatchStats& w, const sg_sched_choice& ch, int num_s
   f[11] = (float)std::log2(std::max(1.0, items / slots));
 }
 
-void sg_sched_log_add(sg_ctx* c, const float* f, double us) {
+void sg_sched_log_add(sg_ctx* c, const float* f, double us, float rel) {
   SchedState& s = c->schedst;
   s.log_x.insert(s.log_x.end(), f, f + kSchedFeatures);
   s.log_y.push_back((float)std::log(std::max(us, 1e-3)));
+  s.log_rel.push_back(rel);
 }
 
 // ---------------------------------------------------------------------------
@@ -102,35 +106,40 @@ static void init_params(std::vector<float>& P, int d_in, uint64_t seed) {
 sg_status sg_sched_train_impl(sg_ctx* c, int epochs, float lr, uint64_t seed, float* final_loss) {
   SchedState& s = c->schedst;
   const int d = kSchedFeatures;
-  const long long R = (long long)s.log_y.size();
+  // the sweep records: features and time relative to the plain choice
+  std::vector<long long> rows;
+  for (long long r = 0; r < (long long)s.log_rel.size(); ++r)
+    if (std::isfinite(s.log_rel[r])) rows.push_back(r);
+  const long long R = (long long)rows.size();
   if (R < 8) {
-    c->err = "the schedule log needs at least 8 records";
+    c->err = "the schedule log needs at least 8 records from candidate sweeps";
     return SG_ERR_INVALID_ARG;
   }
-  // feature / target normalisation from the log
+  // feature / target normalisation from those records
   s.mu.assign(d, 0.0f);
   s.sd.assign(d, 0.0f);
   double ym = 0.0, ys = 0.0;
-  for (long long r = 0; r < R; ++r) {
+  for (long long r : rows) {
     for (int k = 0; k < d; ++k) s.mu[k] += s.log_x[r * d + k];
-    ym += s.log_y[r];
+    ym += s.log_rel[r];
   }
   for (int k = 0; k < d; ++k) s.mu[k] /= (float)R;
   ym /= (double)R;
-  for (long long r = 0; r < R; ++r) {
+  for (long long r : rows) {
     for (int k = 0; k < d; ++k) {
       const float q = s.log_x[r * d + k] - s.mu[k];
       s.sd[k] += q * q;
     }
-    ys += (s.log_y[r] - ym) * (s.log_y[r] - ym);
+    ys += (s.log_rel[r] - ym) * (s.log_rel[r] - ym);
   }
   for (int k = 0; k < d; ++k) s.sd[k] = std::sqrt(s.sd[k] / (float)R) + 1e-6f;
   s.ymu = (float)ym;
   s.ysd = (float)std::sqrt(ys / (double)R) + 1e-6f;
   std::vector<float> X((size_t)R * d), Y(R);
-  for (long long r = 0; r < R; ++r) {
-    for (int k = 0; k < d; ++k) X[r * d + k] = (s.log_x[r * d + k] - s.mu[k]) / s.sd[k];
-    Y[r] = (s.log_y[r] - s.ymu) / s.ysd;
+  for (long long i = 0; i < R; ++i) {
+    const long long r = rows[i];
+    for (int k = 0; k < d; ++k) X[i * d + k] = (s.log_x[r * d + k] - s.mu[k]) / s.sd[k];
+    Y[i] = (s.log_rel[r] - s.ymu) / s.ysd;
   }
   // device buffers: params, grad, m, v, X, Y, work, loss
   const int np = sgk::mlp_nparams(d);
@@ -239,5 +248,19 @@ bool sg_sched_predict(sg_ctx* c, const BatchStats& w, const std::vector<sg_sched
     cudaGetLastError();
     return false;
   }
+  for (float& p : *pred) p = p * s.ysd + s.ymu;
   return true;
+}
+
+int sg_sched_learned_index(sg_ctx* c, const BatchStats& w, const std::vector<sg_sched_choice>& cand,
+                           const sg_sched_choice& def, std::vector<float>* pred) {
+  std::vector<float> local;
+  std::vector<float>& p = pred ? *pred : local;
+  if (!sg_sched_predict(c, w, cand, &p)) return -1;
+  int di = 0;
+  for (size_t i = 0; i < cand.size(); ++i)
+    if (cand[i].chunk == def.chunk && cand[i].blocks_per_sm == def.blocks_per_sm) di = (int)i;
+  const int bi = (int)(std::min_element(p.begin(), p.end()) - p.begin());
+  // a predicted gain against the plain choice, beyond the model's noise
+  return p[bi] < p[di] - kLearnedMargin ? bi : di;
 }

@@ -84,6 +84,12 @@ def make_workload(torch, rng, nseg, lo, hi):
 
 
 def test_learned_schedule_gain_over_plain_table(env):
+    """Train the cost model on autotuner sweeps of 56 synthetic workloads, then
+    compare, on 12 held-out workloads, the regret of the learned choice and
+    of the plain table's choice (time / fastest - 1, each candidate measured
+    twice more and the better time kept, so that measurement noise does not
+    decide).  The learned chooser must not lose to the table and must stay
+    near the fastest; it must also run without measuring."""
     sg, ctx, torch = env
     chain = sg.chain([("x", 0), ("x", 0), ("c", 1.0), ("fma",)], [("x", 0), ("c", 1.0), ("ge",)],
                      [("x", 0), ("c", 1.5), ("gt",)])
@@ -99,29 +105,30 @@ def test_learned_schedule_gain_over_plain_table(env):
 
     # training: the autotuner measures every candidate of each workload
     sg.sg_set_scheduler(ctx, sg.SG_SCHED_AUTOTUNE)
-    for _ in range(28):
+    for _ in range(56):
         x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
         sg.sg_batch_run(ctx, chain, x.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
     Xlog, ylog = sg.sg_sched_log(ctx)
-    assert len(ylog) >= 28 * 2 * 8
+    assert len(ylog) >= 56 * 8 and Xlog.shape == (len(ylog), D_IN)
     loss = sg.sg_sched_train(ctx, epochs=400, lr=3e-3, seed=7)
-    assert loss < 0.5          # standardised log-time: well below the variance (1.0)
+    assert loss < 0.5          # standardised relative log-time: well below its variance (1.0)
     # held-out workloads
     reg_l, reg_d = [], []
-    for _ in range(8):
+    for _ in range(12):
         x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
-        r = sg.sg_batch_report(ctx, chain, x.data_ptr(), to.data_ptr(), nseg,
-                               *(t.data_ptr() for t in outs))
-        t = np.array(r.measured_us[:r.ncand])
+        args = (ctx, chain, x.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
+        r1 = sg.sg_batch_report(*args)
+        r2 = sg.sg_batch_report(*args)
+        t = np.minimum(np.array(r1.measured_us[:r1.ncand]), np.array(r2.measured_us[:r2.ncand]))
         best = t.min()
-        assert r.learned_index >= 0 and r.default_index >= 0
-        reg_l.append(t[r.learned_index] / best - 1)
-        reg_d.append(t[r.default_index] / best - 1)
+        assert r1.learned_index >= 0 and r1.default_index >= 0
+        reg_l.append(t[r1.learned_index] / best - 1)
+        reg_d.append(t[r1.default_index] / best - 1)
     ml, md = float(np.mean(reg_l)), float(np.mean(reg_d))
     print("\nmean regret learned %.3f, plain table %.3f, per workload learned %s plain %s"
           % (ml, md, np.round(reg_l, 3).tolist(), np.round(reg_d, 3).tolist()))
-    assert ml <= md + 0.05
-    assert ml <= 0.30
+    assert ml <= md + 0.01
+    assert ml <= 0.10
     # the learned chooser runs once, without measuring candidates
     sg.sg_set_scheduler(ctx, sg.SG_SCHED_LEARNED)
     x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
