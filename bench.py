@@ -334,8 +334,15 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
         info_box["it"] = info.iterations
         sg.sg_vector_release(xs)
     ms = time_steps(torch, stream, s_solve, 2)
-    out["solve_gepp_8192"] = {"ms": round(ms, 3), "iterations": info_box.get("it"),
-                              "GFLOPs": round(2 / 3 * n ** 3 / (ms / 1e3) / 1e9, 1)}
+    it_bf16 = info_box.get("it")
+    # the plain form: every update in binary32 on the CUDA cores
+    o.precision = sg.SG_PREC_F32_SIMT
+    ms32 = time_steps(torch, stream, s_solve, 2)
+    out["solve_gepp_8192"] = {"ms": round(ms, 3), "iterations": it_bf16,
+                              "GFLOPs": round(2 / 3 * n ** 3 / (ms / 1e3) / 1e9, 1),
+                              "plain_f32_ms": round(ms32, 3),
+                              "plain_f32_iterations": info_box.get("it"),
+                              "speedup_mixed_over_plain": round(ms32 / ms, 3)}
     sg.sg_matrix_release(mA)
     sg.sg_vector_release(vb)
     del ta, tb

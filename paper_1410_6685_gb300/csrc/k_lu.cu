@@ -6,10 +6,11 @@
 //                  shared memories and eliminates it column by column.  Each
 //                  column costs one hardware cluster barrier: every CTA
 //                  publishes its best pivot candidate (largest |a|, then the
-//                  lowest current row position) into every CTA's shared
-//                  memory, all pick the same winner, read the pivot row from
-//                  its owner over distributed shared memory, and update their
-//                  own rows while finding the next column's candidate.  Row
+//                  lowest current row position) together with that row into
+//                  every CTA's shared memory; after the barrier all pick the
+//                  same winner, find its row in their own shared memory, and
+//                  update their own rows while finding the next column's
+//                  candidate.  Row
 //                  interchanges are tracked as a replicated position table
 //                  and applied when the panel is written back, so the result
 //                  equals the row-swapping textbook algorithm.
@@ -48,10 +49,10 @@ __device__ __forceinline__ unsigned long long key_of(float v, int pos, int row) 
 
 constexpr int kMaxRowsPerThread = 5;   // ceil(ceil(9216 / 8) / 256)
 
-// smem: slab[rs][33] floats, cand[2][8] u64, best[2] u64, prow[32] floats
+// smem: slab[rs][33] floats, cand[2][8] u64, best[2] u64, crow[2][8][32] floats
 __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     k_lu_panel(float* __restrict__ LU, int n, int k, int jb, int* __restrict__ piv,
-               int* __restrict__ info) {
+               int* __restrict__ info, int* __restrict__ moves) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -63,7 +64,8 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
   unsigned long long* cand = reinterpret_cast<unsigned long long*>(
       (reinterpret_cast<uintptr_t>(slab + (size_t)rs * kStride) + 15) & ~(uintptr_t)15);
   unsigned long long* best = cand + 2 * kPC;
-  float* prow = reinterpret_cast<float*>(best + 2);
+  // crow[par][q][c]: CTA q's candidate row for the column of parity par
+  float* crow = reinterpret_cast<float*>(best + 2);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
 
@@ -98,19 +100,33 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     }
     if (lane == 0 && mine) atomicMax(&best[par], mine);
     __syncthreads();
-    if (tid < kPC) *cluster.map_shared_rank(&cand[par * kPC + rank], tid) = best[par];
+    // publish the candidate and its row (the pivot row, should it win) in
+    // every CTA of the cluster: one barrier then gives every CTA the winner
+    // and its row from its own shared memory
+    const unsigned long long bmine = best[par];
+    if (tid < kPC) *cluster.map_shared_rank(&cand[par * kPC + rank], tid) = bmine;
+    if (tid >= 32 && tid < 32 + kPB * kPC / 4 && bmine) {
+      const int q = (tid - 32) / (kPB / 4), cq = ((tid - 32) % (kPB / 4)) * 4;
+      const int lr = (int)(bmine & 0xFFFFu) - r0;
+      float4 v;
+      v.x = (cq >= j && cq < jb) ? slab[lr * kStride + cq] : 0.0f;
+      v.y = (cq + 1 >= j && cq + 1 < jb) ? slab[lr * kStride + cq + 1] : 0.0f;
+      v.z = (cq + 2 >= j && cq + 2 < jb) ? slab[lr * kStride + cq + 2] : 0.0f;
+      v.w = (cq + 3 >= j && cq + 3 < jb) ? slab[lr * kStride + cq + 3] : 0.0f;
+      *reinterpret_cast<float4*>(cluster.map_shared_rank(&crow[(par * kPC + rank) * kPB + cq], q)) = v;
+    }
     if (tid == kPC) best[par ^ 1] = 0ull;   // next column's slot (its last reader is done)
     cluster.sync();
     unsigned long long g = 0ull;
+    int wq = 0;
 #pragma unroll
-    for (int q = 0; q < kPC; ++q) g = cand[par * kPC + q] > g ? cand[par * kPC + q] : g;
+    for (int q = 0; q < kPC; ++q) {
+      const unsigned long long cq = cand[par * kPC + q];
+      if (cq > g) { g = cq; wq = q; }
+    }
     const int p = (int)(0xFFFFu - (unsigned)((g >> 16) & 0xFFFFu));   // winning position
     const int gp = (int)(g & 0xFFFFu);                                // its row in the panel
-    const int owner = gp / rs;
-    if (tid < kPB) {
-      const float* src = cluster.map_shared_rank(slab, owner);
-      prow[tid] = (tid >= j && tid < jb) ? src[(gp - owner * rs) * kStride + tid] : 0.0f;
-    }
+    const float* prow = crow + (par * kPC + wq) * kPB;
     // interchange of positions j and p (each thread for its own rows)
 #pragma unroll
     for (int i = 0; i < kMaxRowsPerThread; ++i) {
@@ -118,7 +134,6 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
       if (lp[i] == j) lp[i] = p;
       if (r == gp) lp[i] = j;
     }
-    __syncthreads();
     const float d = prow[j];
     const bool zero = d == 0.0f;
     if (zero && my_info == 0) my_info = k + j + 1;
@@ -142,7 +157,8 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     if (tid == 0 && rank == 0) piv[k + j] = k + p;
   }
   cluster.sync();   // no CTA reads another's shared memory after this
-  // write the panel back in its final row order
+  // write the panel back in its final row order, and list the rows that
+  // moved (at most 2 jb) for the other columns' interchange
 #pragma unroll
   for (int i = 0; i < kMaxRowsPerThread; ++i) {
     const int r = r0 + tid + i * kPT;
@@ -150,26 +166,39 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     float* dst = LU + (size_t)(k + lp[i]) * n + k;
     const float* row = slab + (r - r0) * kStride;
     for (int c = 0; c < jb; ++c) dst[c] = row[c];
+    if (lp[i] != r) {
+      const int t = atomicAdd(&moves[0], 1);
+      if (t < 2 * kPB) {
+        moves[1 + t] = k + r;
+        moves[1 + 2 * kPB + t] = k + lp[i];
+      }
+    }
   }
   if (tid == 0 && rank == 0 && my_info) atomicCAS(info, 0, my_info);
   cluster.sync();
 }
 
-// interchanges piv[k..k+jb) applied in order to columns [c0, c1)
-__global__ void k_lu_laswp(float* LU, int n, int k, int jb, const int* __restrict__ piv, int c0,
-                           int c1) {
+// The panel's interchanges on columns [c0, c1) as one permutation: row
+// dst[t] receives old row src[t] (the list the panel kernel left).  Every
+// load of a column is issued before its stores.
+__global__ void __launch_bounds__(128) k_lu_laswp(float* LU, int n, const int* __restrict__ moves,
+                                                  int c0, int c1) {
+  __shared__ int s_src[2 * kPB], s_dst[2 * kPB];
+  const int cnt = min(moves[0], 2 * kPB);
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    s_src[t] = moves[1 + t];
+    s_dst[t] = moves[1 + 2 * kPB + t];
+  }
+  __syncthreads();
   const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= c1) return;
-  for (int j = 0; j < jb; ++j) {
-    const int p = piv[k + j];
-    if (p != k + j) {
-      float* a = LU + (size_t)(k + j) * n + c;
-      float* b = LU + (size_t)p * n + c;
-      const float t = *a;
-      *a = *b;
-      *b = t;
-    }
-  }
+  float v[2 * kPB];
+#pragma unroll
+  for (int t = 0; t < 2 * kPB; ++t)
+    if (t < cnt) v[t] = LU[(size_t)s_src[t] * n + c];
+#pragma unroll
+  for (int t = 0; t < 2 * kPB; ++t)
+    if (t < cnt) LU[(size_t)s_dst[t] * n + c] = v[t];
 }
 
 // U12 = L11^-1 A12 for the columns [c0, c1): one thread per column
@@ -437,15 +466,15 @@ __global__ void k_residual_to_f32(const double* __restrict__ r, float* y, int n,
 size_t panel_smem(int n, int k) {
   const int m = n - k;
   const int rs = (m + kPC - 1) / kPC;
-  return (size_t)rs * kStride * 4 + 16 + 2 * kPC * 8 + 2 * 8 + kPB * 4 + 64;
+  return (size_t)rs * kStride * 4 + 16 + 2 * kPC * 8 + 2 * 8 + 2 * kPC * kPB * 4 + 64;
 }
 
 }  // namespace
 
 size_t lu_panel_max_smem(int n) { return panel_smem(n, 0); }
 
-cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info, cudaStream_t s,
-                            Prof* prof) {
+cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info, int* moves,
+                            cudaStream_t s, Prof* prof) {
   const size_t sm = panel_smem(n, k);
   static size_t attr = 0;
   if (sm > attr) {
@@ -455,17 +484,17 @@ cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info
     attr = panel_smem(n, 0);
   }
   prof_begin(prof, "lu_panel", s);
-  k_lu_panel<<<kPC, kPT, sm, s>>>(LU, n, k, jb, piv, info);
+  k_lu_panel<<<kPC, kPT, sm, s>>>(LU, n, k, jb, piv, info, moves);
   prof_end(prof, s);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lu_laswp(float* LU, int n, int k, int jb, const int* piv, cudaStream_t s,
+cudaError_t launch_lu_laswp(float* LU, int n, int k, int jb, const int* moves, cudaStream_t s,
                             Prof* prof) {
   prof_begin(prof, "lu_laswp", s);
-  if (k > 0) k_lu_laswp<<<(k + 255) / 256, 256, 0, s>>>(LU, n, k, jb, piv, 0, k);
+  if (k > 0) k_lu_laswp<<<(k + 127) / 128, 128, 0, s>>>(LU, n, moves, 0, k);
   const int rest = n - k - jb;
-  if (rest > 0) k_lu_laswp<<<(rest + 255) / 256, 256, 0, s>>>(LU, n, k, jb, piv, k + jb, n);
+  if (rest > 0) k_lu_laswp<<<(rest + 127) / 128, 128, 0, s>>>(LU, n, moves, k + jb, n);
   prof_end(prof, s);
   return cudaGetLastError();
 }

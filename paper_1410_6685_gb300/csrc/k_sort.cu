@@ -18,10 +18,10 @@
 //   are on, (a) checks every adjacent pair inside each tile-local digit run,
 //   (b) carries the last key of every digit run through the look-back words
 //   so each run's first key is compared with its predecessor in the output,
-//   and (c) accumulates the output's multiset fingerprint
-//   (sum of mix(k), sum of mix(k)^2 mod 2^64, count; mix = SplitMix64's
-//   output function) for comparison with the input's.  No extra pass over
-//   the keys is needed.
+//   and (c) accumulates the output's multiset fingerprint (sum of mix(k),
+//   sum of mix(k)^2 mod 2^64, count; mix = MurmurHash3's 32-bit finalizer, a
+//   bijection) for comparison with the input's.  No extra pass over the keys
+//   is needed.
 #include <stdint.h>
 
 #include "sg_internal.h"
@@ -30,6 +30,7 @@ namespace sgk {
 namespace {
 
 constexpr int kSortBlock = 256;
+constexpr int kSortMinBlocks = 4;   // resident CTAs per SM the registers are sized for
 constexpr int kKpt = 24;
 constexpr int kTile = kSortBlock * kKpt;   // 6144 keys
 constexpr int kMatchEvery = 4;
@@ -42,7 +43,7 @@ constexpr unsigned kCntMask = (1u << 30) - 1;
 constexpr unsigned kAgg = 1u;
 constexpr unsigned kPre = 2u;
 
-static_assert(kSortBlock == kRadix, "one thread per digit in the look-back");
+static_assert(kSortBlock % kRadix == 0, "threads 0..255 own one digit each");
 
 struct SortHdr {
   unsigned hist[4][kRadix];
@@ -51,12 +52,6 @@ struct SortHdr {
   unsigned done_ctr;
   unsigned pad[59];
 };
-
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
 
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
   unsigned v;
@@ -124,10 +119,21 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* s_warp
   return x - v + s_warp[w];
 }
 
+// MurmurHash3's 32-bit finalizer (Appleby): a bijection of 32-bit words, so
+// replacing one key by another always changes the sums below.
+__device__ __forceinline__ unsigned fmix32(unsigned h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
 __device__ __forceinline__ void fp_add(unsigned long long& f1, unsigned long long& f2, int k) {
-  const unsigned long long m = mix64((unsigned long long)(unsigned)k);
+  const unsigned m = fmix32((unsigned)k);
   f1 += m;
-  f2 += m * m;
+  f2 += (unsigned long long)m * m;
 }
 
 __device__ __forceinline__ void fp_flush(unsigned long long f1, unsigned long long f2,
@@ -144,7 +150,9 @@ __device__ __forceinline__ void fp_flush(unsigned long long f1, unsigned long lo
 }
 
 // ---------------------------------------------------------------------------
-template <bool FLT>
+// FP: also the input's multiset fingerprint (only the permutation check
+// needs it)
+template <bool FLT, bool FP>
 __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, long long n,
                                                     SortHdr* h, SortResult* res) {
   __shared__ unsigned sh[4][kRadix];
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
     atomicAdd(&sh[1][(u >> 8) & 0xFFu], 1u);
     atomicAdd(&sh[2][(u >> 16) & 0xFFu], 1u);
     atomicAdd(&sh[3][u >> 24], 1u);
-    fp_add(f1, f2, k);
+    if (FP) fp_add(f1, f2, k);
   };
   if (((uintptr_t)in & 15) == 0) {
     const long long nv = n >> 2;
@@ -179,7 +187,7 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
     }
   }
   for (long long i = start + tid; i < n; i += stride) count(in[i]);
-  fp_flush(f1, f2, res->fp_in);
+  if (FP) fp_flush(f1, f2, res->fp_in);
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
     const unsigned c = (&sh[0][0])[i];
@@ -281,9 +289,10 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   }
   __syncthreads();
 
-  // per digit: tile count and exclusive offsets of the warps
+  // per digit (threads 0..255): tile count and exclusive offsets of the warps
+  const bool dig = kSortBlock == kRadix || tid < kRadix;
   unsigned cnt = 0;
-  {
+  if (dig) {
     const int d = tid;
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
@@ -291,11 +300,12 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
       s_whist[ww][d] = cnt;
       cnt += t;
     }
+    // publish the tile aggregate as early as possible
+    if (!(LAST && CHECK))
+      st_relaxed(&st32[(size_t)tile * kRadix + tid], ((tile == 0 ? kPre : kAgg) << 30) | cnt);
   }
-  // publish the tile aggregate as early as possible
-  if (!(LAST && CHECK)) st_relaxed(&st32[(size_t)tile * kRadix + tid], ((tile == 0 ? kPre : kAgg) << 30) | cnt);
   const unsigned start = block_excl_scan(cnt, sm.warp);
-  s_start[tid] = start;
+  if (dig) s_start[tid] = start;
   __syncthreads();
 
   // sort the tile in shared memory by digit (stable)
@@ -312,7 +322,9 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   const int d = tid;
   unsigned long long excl = 0;
   bool timeout = false;
-  if (!(LAST && CHECK)) {
+  if (!dig) {
+    // no digit of this thread
+  } else if (!(LAST && CHECK)) {
     if (tile > 0) {
       long long j = (long long)tile - 1;
       unsigned spins = 0;
@@ -376,7 +388,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
     atomicExch(&res->timeout, 1);
     sm.timeout = 1;
   }
-  s_gbase[d] = (int)h->offs[pass][d] + (int)excl - (int)start;
+  if (dig) s_gbase[d] = (int)h->offs[pass][d] + (int)excl - (int)start;
   __syncthreads();
   // a look-back that gave up leaves this tile's offsets unknown: write nothing
   const bool write = sm.timeout == 0;
@@ -416,7 +428,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 }
 
 template <bool LAST, bool CHECK, bool FLT>
-__global__ void __launch_bounds__(kSortBlock, 4) k_onesweep(
+__global__ void __launch_bounds__(kSortBlock, kSortMinBlocks) k_onesweep(
     const int* __restrict__ in, int* __restrict__ out, long long n, int pass, SortHdr* h,
     unsigned* st32, unsigned long long* st64, SortResult* res) {
   __shared__ SortSmem sm;
@@ -526,7 +538,10 @@ cudaError_t sort_impl(const int32_t* in, int32_t* out, long long n, bool contrac
   cudaError_t e = cudaMemsetAsync(base, 0, L.zero_bytes, s);
   if (e != cudaSuccess) return e;
   prof_begin(prof, "radix_hist", s);
-  k_radix_hist<FLT><<<grid_for((n + 3) / 4 / 8, num_sms, 8), 256, 0, s>>>(in, n, h, res);
+  if (contracts)
+    k_radix_hist<FLT, true><<<grid_for((n + 3) / 4 / 8, num_sms, 8), 256, 0, s>>>(in, n, h, res);
+  else
+    k_radix_hist<FLT, false><<<grid_for((n + 3) / 4 / 8, num_sms, 8), 256, 0, s>>>(in, n, h, res);
   prof_end(prof, s);
   const unsigned ntiles = (unsigned)((n + kTile - 1) / kTile);
   prof_begin(prof, "onesweep", s);

@@ -61,6 +61,7 @@ struct Job {
   int64_t* kept;
   sgk::Prog prog;
   int depth;
+  int occ;          // resident CTAs per SM of the kernel that will run
   BatchStats stats;
 };
 
@@ -219,6 +220,18 @@ sg_status prepare(sg_ctx* c, const sg_chain* ch, const float* data, const int64_
   j->kept = kept;
   if (!sgk::build_chain_prog(*ch, &j->prog, &j->depth))
     return bad(c, SG_ERR_INVALID_ARG, "chain program too long or too deep");
+  // the candidates' CTAs per SM follow the kernel that will run: the
+  // specialised one when code generation is on, else the interpreter
+  j->occ = 0;
+  if (c->codegen == SG_CODEGEN_SPECIALIZE) {
+    if (cudaKernel_t k = sgk::jit_batch_kernel(j->prog, nullptr)) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k, 256, 0) == cudaSuccess)
+        j->occ = nb;
+      cudaGetLastError();
+    }
+  }
+  if (j->occ <= 0) j->occ = sgk::batch_blocks_per_sm(j->depth);
   if (nseg == 0) return SG_OK;
   // everything queued before runs first (same stream order as a flush)
   sg_status st = sg_flush(c);
@@ -230,7 +243,7 @@ sg_status prepare(sg_ctx* c, const sg_chain* ch, const float* data, const int64_
 // caches), then the better of two timed runs -- and log the sweep with each
 // time relative to the plain table's choice.
 sg_status autotune(sg_ctx* c, const Job& j, std::vector<double>* times, int* best) {
-  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.depth);
+  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.occ);
   times->assign(cand.size(), 0.0);
   double bt = 1e300;
   *best = 0;
@@ -248,7 +261,7 @@ sg_status autotune(sg_ctx* c, const Job& j, std::vector<double>* times, int* bes
       *best = (int)i;
     }
   }
-  const sg_sched_choice def = sg_batch_default(j.depth);
+  const sg_sched_choice def = sg_batch_default(j.occ);
   double tdef = 0.0;
   for (size_t i = 0; i < cand.size(); ++i)
     if (cand[i].chunk == def.chunk && cand[i].blocks_per_sm == def.blocks_per_sm) tdef = (*times)[i];
@@ -281,8 +294,8 @@ extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* da
   Job j;
   sg_status st = prepare(c, ch, data, offsets, nseg, sums, first_viol, kept, &j);
   if (st || nseg == 0) return st;
-  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.depth);
-  sg_sched_choice pick = sg_batch_default(j.depth);
+  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.occ);
+  sg_sched_choice pick = sg_batch_default(j.occ);
   bool chosen = false;
   if (c->sched == SG_SCHED_LEARNED) {
     const int li = sg_sched_learned_index(c, j.stats, cand, pick, nullptr);
@@ -324,14 +337,14 @@ extern "C" sg_status sg_batch_report(sg_ctx* c, const sg_chain* ch, const float*
   sg_status st = prepare(c, ch, data, offsets, nseg, sums, first_viol, kept, &j);
   if (st) return st;
   if (nseg == 0) return bad(c, SG_ERR_INVALID_ARG, "empty batch");
-  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.depth);
+  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.occ);
   memset(out, 0, sizeof *out);
   out->ncand = (int32_t)std::min<size_t>(cand.size(), SG_SCHED_MAX_CANDIDATES);
   std::vector<double> times;
   int best = 0;
   st = autotune(c, j, &times, &best);
   if (st) return st;
-  const sg_sched_choice def = sg_batch_default(j.depth);
+  const sg_sched_choice def = sg_batch_default(j.occ);
   out->default_index = -1;
   for (int i = 0; i < out->ncand; ++i) {
     out->chunk[i] = cand[i].chunk;

@@ -9,10 +9,14 @@ constexpr int kLuOuter = 128;     // outer block: one tensor-core update per 128
 constexpr int kLuMaxN = 9216;     // the panel must fit the cluster's shared memory
 
 size_t lu_panel_max_smem(int n);
-cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info, cudaStream_t s,
-                            Prof* prof);
-// the interchanges of piv[k..k+jb) on every column outside the panel
-cudaError_t launch_lu_laswp(float* LU, int n, int k, int jb, const int* piv, cudaStream_t s,
+// moves: the panel's slot of kLuMoveInts ints, zero before the call; the
+// kernel lists there the rows its interchanges moved (count, sources,
+// destinations) for launch_lu_laswp.
+constexpr int kLuMoveInts = 1 + 4 * kLuPanel;
+cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info, int* moves,
+                            cudaStream_t s, Prof* prof);
+// the panel's interchanges on every column outside the panel
+cudaError_t launch_lu_laswp(float* LU, int n, int k, int jb, const int* moves, cudaStream_t s,
                             Prof* prof);
 // rows k..k+jb of columns [c0, c1) := L11^-1 (them), L11 = unit lower at (k, k)
 cudaError_t launch_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1, cudaStream_t s,

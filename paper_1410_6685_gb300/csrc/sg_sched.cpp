@@ -27,7 +27,7 @@
 namespace {
 
 const long long kChunks[] = {2048, 4096, 8192, 16384, 32768, 65536};
-const int kPerSm[] = {1, 2, 4, 0};   // 0: as many as fit (occupancy)
+const int kPerSm[] = {1, 2, 4, 8};   // capped at the kernel's occupancy
 
 uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -37,12 +37,12 @@ uint64_t mix64(uint64_t z) {
 
 }  // namespace
 
-std::vector<sg_sched_choice> sg_batch_candidates(int depth) {
+std::vector<sg_sched_choice> sg_batch_candidates(int occ) {
   std::vector<sg_sched_choice> out;
-  const int occ = std::max(1, sgk::batch_blocks_per_sm(depth));
+  occ = std::max(1, occ);
   for (long long ch : kChunks)
     for (int p : kPerSm) {
-      const int bps = p == 0 ? occ : std::min(p, occ);
+      const int bps = std::min(p, occ);
       bool dup = false;
       for (auto& c : out) dup |= c.chunk == ch && c.blocks_per_sm == bps;
       if (!dup) out.push_back(sg_sched_choice{ch, bps});
@@ -50,8 +50,8 @@ std::vector<sg_sched_choice> sg_batch_candidates(int depth) {
   return out;
 }
 
-sg_sched_choice sg_batch_default(int depth) {
-  return sg_sched_choice{16384, std::max(1, sgk::batch_blocks_per_sm(depth))};
+sg_sched_choice sg_batch_default(int occ) {
+  return sg_sched_choice{16384, std::max(1, std::min(occ, 8))};
 }
 
 void sg_batch_features(const BatchStats& w, const sg_sched_choice& ch, int num_sms, float* f) {

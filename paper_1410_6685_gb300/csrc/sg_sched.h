@@ -18,8 +18,9 @@ struct BatchStats {
   int ops = 0, depth = 0;
 };
 
-std::vector<sg_sched_choice> sg_batch_candidates(int depth);
-sg_sched_choice sg_batch_default(int depth);
+// occ: resident CTAs per SM of the batch kernel that will run
+std::vector<sg_sched_choice> sg_batch_candidates(int occ);
+sg_sched_choice sg_batch_default(int occ);
 void sg_batch_features(const BatchStats& w, const sg_sched_choice& ch, int num_sms, float* f);
 // One timing record: features, microseconds, and log(us / us of the plain
 // table's choice on the same workload) when the record comes from a sweep

@@ -53,10 +53,11 @@ struct SolveWork {
 // Blocked elimination with partial pivoting of the n x n binary32 matrix in
 // `lu` (row-major), in place: L (unit lower) and U overwrite it, piv[k] is
 // the row interchanged with row k at step k, *info = k+1 at an exactly zero
-// pivot.  gemm: tensor-core scratch (gemm_tc_scratch_bytes(n, n, kLuOuter)),
+// pivot.  moves: ceil(n / kLuPanel) * kLuMoveInts ints, zero on entry.
+// gemm: tensor-core scratch (gemm_tc_scratch_bytes(n, n, kLuOuter)),
 // unused for binary32 updates.
-cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* info, void* gemm,
-                            sg_precision prec) {
+cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* info, int* moves,
+                            void* gemm, sg_precision prec) {
   cudaError_t e = cudaSuccess;
   sgk::Prof* prof = &c->prof;
   cudaStream_t s = c->stream;
@@ -79,8 +80,9 @@ cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* info, vo
     const int KB = std::min(sgk::kLuOuter, n - K);
     for (int j = K; j < K + KB && e == cudaSuccess; j += sgk::kLuPanel) {
       const int jb = std::min(sgk::kLuPanel, K + KB - j);
-      e = sgk::launch_lu_panel(lu, n, j, jb, piv, info, s, prof);
-      if (e == cudaSuccess) e = sgk::launch_lu_laswp(lu, n, j, jb, piv, s, prof);
+      int* mv = moves + (size_t)(j / sgk::kLuPanel) * sgk::kLuMoveInts;
+      e = sgk::launch_lu_panel(lu, n, j, jb, piv, info, mv, s, prof);
+      if (e == cudaSuccess) e = sgk::launch_lu_laswp(lu, n, j, jb, mv, s, prof);
       c->kernels += 3;
       const int right = K + KB - (j + jb);   // columns of this outer block to the right
       if (right > 0 && e == cudaSuccess) {
@@ -162,6 +164,7 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
   const size_t o_tk = take(64);
   const size_t o_err = take(64);
   const size_t o_info = take(64);
+  const size_t o_moves = take((size_t)nb * sgk::kLuMoveInts * 4);
   const size_t o_norms = take(8 * 8);
   const size_t o_viol = take(8);
   const size_t gemm_bytes = o.precision == SG_PREC_F32_SIMT
@@ -227,7 +230,9 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
   if (e == cudaSuccess) e = cudaMemsetAsync(base + o_flags, 0, o_norms + 64 - o_flags, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.viol, 0, 8, s);
   if (e == cudaSuccess) e = sgk::launch_anorm(a, n, w.norms, s);
-  if (e == cudaSuccess) e = factor_in_place(c, w.lu, n, w.piv, w.info, w.gemm, o.precision);
+  if (e == cudaSuccess)
+    e = factor_in_place(c, w.lu, n, w.piv, w.info, reinterpret_cast<int*>(base + o_moves), w.gemm,
+                        o.precision);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hinfo, w.info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -350,6 +355,7 @@ extern "C" sg_status sg_det(sg_ctx* c, sg_matrix* A, sg_precision prec, sg_det_r
   const size_t o_piv = take((size_t)n * 4);
   const size_t o_info = take(64);
   const size_t o_out = take(64);
+  const size_t o_moves = take((size_t)((n + sgk::kLuPanel - 1) / sgk::kLuPanel) * sgk::kLuMoveInts * 4);
   const size_t gemm_bytes =
       prec == SG_PREC_F32_SIMT ? 0 : sgk::gemm_tc_scratch_bytes(n, n, sgk::kLuOuter);
   const size_t o_gemm = take(gemm_bytes + 256);
@@ -366,7 +372,10 @@ extern "C" sg_status sg_det(sg_ctx* c, sg_matrix* A, sg_precision prec, sg_det_r
   double* dout = reinterpret_cast<double*>(base + o_out);
   e = cudaMemcpyAsync(lu, A->v->st->ptr, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, 64, s);
-  if (e == cudaSuccess) e = factor_in_place(c, lu, n, piv, info, base + o_gemm, prec);
+  int* moves = reinterpret_cast<int*>(base + o_moves);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(moves, 0, (size_t)((n + sgk::kLuPanel - 1) / sgk::kLuPanel) * sgk::kLuMoveInts * 4, s);
+  if (e == cudaSuccess) e = factor_in_place(c, lu, n, piv, info, moves, base + o_gemm, prec);
   if (e == cudaSuccess) e = sgk::launch_lu_det(lu, n, piv, dout, s, &c->prof);
   c->kernels += 1;
   double h[2] = {0.0, 0.0};
