@@ -4,13 +4,14 @@
 // Right-looking blocked LU, panels of 32 columns:
 //   k_lu_panel   : a cluster of 8 CTAs holds the panel (rows k..n-1) in their
 //                  shared memories and eliminates it column by column.  Each
-//                  column costs one hardware cluster barrier: every CTA
-//                  publishes its best pivot candidate (largest |a|, then the
-//                  lowest current row position) together with that row into
-//                  every CTA's shared memory; after the barrier all pick the
-//                  same winner, find its row in their own shared memory, and
-//                  update their own rows while finding the next column's
-//                  candidate.  Row
+//                  column costs one exchange: every CTA sends its best pivot
+//                  candidate (largest |a|, then the lowest current row
+//                  position) together with that row into every CTA's shared
+//                  memory with asynchronous remote stores that complete on
+//                  the receiver's mbarrier; once its barrier completes a CTA
+//                  picks the winner, finds its row in its own shared memory,
+//                  and updates its own rows while finding the next column's
+//                  candidate.  No cluster-wide barrier per column.  Row
 //                  interchanges are tracked as a replicated position table
 //                  and applied when the panel is written back, so the result
 //                  equals the row-swapping textbook algorithm.
@@ -48,8 +49,45 @@ __device__ __forceinline__ unsigned long long key_of(float v, int pos, int row) 
 }
 
 constexpr int kMaxRowsPerThread = 5;   // ceil(ceil(9216 / 8) / 256)
+// bytes every CTA receives per column: 8 candidates and 8 candidate rows
+constexpr unsigned kColBytes = kPC * (8 + kPB * 4);
 
-// smem: slab[rs][33] floats, cand[2][8] u64, best[2] u64, crow[2][8][32] floats
+__device__ __forceinline__ uint32_t sm_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cl_addr(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+// asynchronous remote stores that complete bytes on the receiver's mbarrier
+__device__ __forceinline__ void st_async_b64(uint32_t raddr, unsigned long long v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+               ::"r"(raddr), "l"(v), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void st_async_v4(uint32_t raddr, float4 v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+               ::"r"(raddr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar) : "memory");
+}
+// bounded wait for phase `parity` of a local mbarrier
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  for (unsigned i = 0; i < kSpin; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// smem: slab[rs][33] floats, cand[2][8] u64, best[2] u64, bar[2] u64,
+// crow[2][8][32] floats
 __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     k_lu_panel(float* __restrict__ LU, int n, int k, int jb, int* __restrict__ piv,
                int* __restrict__ info, int* __restrict__ moves) {
@@ -64,8 +102,9 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
   unsigned long long* cand = reinterpret_cast<unsigned long long*>(
       (reinterpret_cast<uintptr_t>(slab + (size_t)rs * kStride) + 15) & ~(uintptr_t)15);
   unsigned long long* best = cand + 2 * kPC;
+  unsigned long long* bar = best + 2;
   // crow[par][q][c]: CTA q's candidate row for the column of parity par
-  float* crow = reinterpret_cast<float*>(best + 2);
+  float* crow = reinterpret_cast<float*>(bar + 2);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
 
@@ -77,8 +116,13 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     const int r = t / kPB, c = t % kPB;
     slab[r * kStride + c] = c < jb ? LU[(size_t)(k + r0 + r) * n + k + c] : 0.0f;
   }
-  if (tid < 2) best[tid] = 0ull;
-  __syncthreads();
+  if (tid < 2) {
+    best[tid] = 0ull;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&bar[tid])) : "memory");
+  }
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  // every CTA's barriers exist before anyone sends
+  cluster.sync();
   // the first column's candidate
   unsigned long long mine = 0ull;
 #pragma unroll
@@ -90,8 +134,10 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     }
   }
   int my_info = 0;
+  bool failed = false;
   for (int j = 0; j < jb; ++j) {
     const int par = j & 1;
+    const uint32_t mbar = sm_addr(&bar[par]);
     // this CTA's best candidate for column j
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -99,24 +145,34 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
       mine = u > mine ? u : mine;
     }
     if (lane == 0 && mine) atomicMax(&best[par], mine);
+    if (tid == 0)   // this column's bytes from the cluster complete bar[par]
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
+                   "r"(kColBytes) : "memory");
     __syncthreads();
-    // publish the candidate and its row (the pivot row, should it win) in
-    // every CTA of the cluster: one barrier then gives every CTA the winner
-    // and its row from its own shared memory
+    // send the candidate and its row (the pivot row, should it win) to every
+    // CTA of the cluster; the stores complete on the receivers' bar[par].
+    // A CTA sends column j + 2 only after it has all of column j + 1, which
+    // every CTA sends only after reading column j: two slots suffice.
     const unsigned long long bmine = best[par];
-    if (tid < kPC) *cluster.map_shared_rank(&cand[par * kPC + rank], tid) = bmine;
-    if (tid >= 32 && tid < 32 + kPB * kPC / 4 && bmine) {
+    if (tid < kPC) {
+      st_async_b64(cl_addr(sm_addr(&cand[par * kPC + rank]), tid), bmine, cl_addr(mbar, tid));
+    } else if (tid >= 32 && tid < 32 + kPB * kPC / 4) {
       const int q = (tid - 32) / (kPB / 4), cq = ((tid - 32) % (kPB / 4)) * 4;
-      const int lr = (int)(bmine & 0xFFFFu) - r0;
-      float4 v;
-      v.x = (cq >= j && cq < jb) ? slab[lr * kStride + cq] : 0.0f;
-      v.y = (cq + 1 >= j && cq + 1 < jb) ? slab[lr * kStride + cq + 1] : 0.0f;
-      v.z = (cq + 2 >= j && cq + 2 < jb) ? slab[lr * kStride + cq + 2] : 0.0f;
-      v.w = (cq + 3 >= j && cq + 3 < jb) ? slab[lr * kStride + cq + 3] : 0.0f;
-      *reinterpret_cast<float4*>(cluster.map_shared_rank(&crow[(par * kPC + rank) * kPB + cq], q)) = v;
+      const int lr = bmine ? (int)(bmine & 0xFFFFu) - r0 : 0;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (bmine) {
+        v.x = (cq >= j && cq < jb) ? slab[lr * kStride + cq] : 0.0f;
+        v.y = (cq + 1 >= j && cq + 1 < jb) ? slab[lr * kStride + cq + 1] : 0.0f;
+        v.z = (cq + 2 >= j && cq + 2 < jb) ? slab[lr * kStride + cq + 2] : 0.0f;
+        v.w = (cq + 3 >= j && cq + 3 < jb) ? slab[lr * kStride + cq + 3] : 0.0f;
+      }
+      st_async_v4(cl_addr(sm_addr(&crow[(par * kPC + rank) * kPB + cq]), q), v, cl_addr(mbar, q));
     }
     if (tid == kPC) best[par ^ 1] = 0ull;   // next column's slot (its last reader is done)
-    cluster.sync();
+    if (!bar_wait(mbar, (uint32_t)(j >> 1) & 1u)) {
+      failed = true;
+      break;
+    }
     unsigned long long g = 0ull;
     int wq = 0;
 #pragma unroll
@@ -156,13 +212,14 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     }
     if (tid == 0 && rank == 0) piv[k + j] = k + p;
   }
+  if (failed) atomicCAS(info, 0, -1);   // a wait gave up: report, write nothing
   cluster.sync();   // no CTA reads another's shared memory after this
   // write the panel back in its final row order, and list the rows that
   // moved (at most 2 jb) for the other columns' interchange
 #pragma unroll
   for (int i = 0; i < kMaxRowsPerThread; ++i) {
     const int r = r0 + tid + i * kPT;
-    if (r >= r1) continue;
+    if (r >= r1 || failed) continue;
     float* dst = LU + (size_t)(k + lp[i]) * n + k;
     const float* row = slab + (r - r0) * kStride;
     for (int c = 0; c < jb; ++c) dst[c] = row[c];
@@ -466,7 +523,7 @@ __global__ void k_residual_to_f32(const double* __restrict__ r, float* y, int n,
 size_t panel_smem(int n, int k) {
   const int m = n - k;
   const int rs = (m + kPC - 1) / kPC;
-  return (size_t)rs * kStride * 4 + 16 + 2 * kPC * 8 + 2 * 8 + 2 * kPC * kPB * 4 + 64;
+  return (size_t)rs * kStride * 4 + 16 + 2 * kPC * 8 + 2 * 8 + 2 * 8 + 2 * kPC * kPB * 4 + 64;
 }
 
 }  // namespace

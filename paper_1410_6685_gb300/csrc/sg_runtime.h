@@ -129,6 +129,22 @@ struct SchedState {
   ~SchedState();
 };
 
+// The blocked factorisation of one size and precision, captured once as a
+// CUDA graph over a workspace the context keeps (factors, pivots, the
+// panels' interchange lists, tensor-core operand copies).
+struct LuCache {
+  int n = 0, prec = -1;
+  void* base = nullptr;
+  float* lu = nullptr;
+  int* piv = nullptr;
+  int* info = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  int64_t kernels = 0;          // kernel launches in one replay
+  void clear();
+  ~LuCache() { clear(); }
+};
+
 struct sg_ctx {
   int device = -1;
   bool planning_only = true;
@@ -159,6 +175,7 @@ struct sg_ctx {
   sgk::Prof prof;                      // per-kernel event tracing
   BatchPlanCache batch;                // captured batched launches
   SchedState schedst;                  // schedule log and cost model
+  LuCache lu;                          // factorisation workspace + graph
 };
 
 struct sg_vector {

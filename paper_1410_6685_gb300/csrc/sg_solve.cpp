@@ -47,7 +47,6 @@ struct SolveWork {
   int* info;
   double* norms;          // [0] max|r| [1] max|d| [2] max|x| [3] |A|_inf [4] max|b|
   unsigned long long* viol;
-  void* gemm;
 };
 
 // Blocked elimination with partial pivoting of the n x n binary32 matrix in
@@ -57,10 +56,8 @@ struct SolveWork {
 // gemm: tensor-core scratch (gemm_tc_scratch_bytes(n, n, kLuOuter)),
 // unused for binary32 updates.
 cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* info, int* moves,
-                            void* gemm, sg_precision prec) {
+                            void* gemm, sg_precision prec, cudaStream_t s, sgk::Prof* prof) {
   cudaError_t e = cudaSuccess;
-  sgk::Prof* prof = &c->prof;
-  cudaStream_t s = c->stream;
   // two levels: 32-column panels inside 128-column outer blocks; inside an
   // outer block only its own columns are updated (binary32 SIMT, narrow);
   // the trailing matrix is updated once per outer block with K = 128
@@ -105,6 +102,75 @@ cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* info, in
     }
   }
   return e;
+}
+
+// Factors A (n x n binary32) into the context's cached workspace: the first
+// call for a size and precision allocates it and captures the blocked
+// elimination (memsets and about 7 n / 32 kernels) as a CUDA graph on a
+// private stream; every call copies A in and replays the graph on the
+// context's stream.  Afterwards c->lu.lu holds L\U, c->lu.piv the
+// interchanges and c->lu.info the zero-pivot report.
+sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
+  LuCache& L = c->lu;
+  if (L.n != n || L.prec != (int)prec || !L.exec) {
+    L.clear();
+    const int np = (n + sgk::kLuPanel - 1) / sgk::kLuPanel;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      const size_t o2 = off;
+      off = al(off + bytes);
+      return o2;
+    };
+    const size_t o_lu = take((size_t)n * n * 4);
+    const size_t o_piv = take((size_t)n * 4);
+    const size_t o_info = take(64);
+    const size_t o_moves = take((size_t)np * sgk::kLuMoveInts * 4);
+    const size_t o_gemm =
+        take((prec == SG_PREC_F32_SIMT ? 0 : sgk::gemm_tc_scratch_bytes(n, n, sgk::kLuOuter)) + 256);
+    if (cudaMalloc(&L.base, off) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&L.cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      L.clear();
+      return err(c, SG_ERR_OOM, "factorisation workspace allocation failed");
+    }
+    char* base = static_cast<char*>(L.base);
+    L.lu = reinterpret_cast<float*>(base + o_lu);
+    L.piv = reinterpret_cast<int*>(base + o_piv);
+    L.info = reinterpret_cast<int*>(base + o_info);
+    int* moves = reinterpret_cast<int*>(base + o_moves);
+    const int64_t k0 = c->kernels;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(L.cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t le = cudaMemsetAsync(L.info, 0, 64, L.cap);
+      if (le == cudaSuccess) le = cudaMemsetAsync(moves, 0, (size_t)np * sgk::kLuMoveInts * 4, L.cap);
+      if (le == cudaSuccess)
+        le = factor_in_place(c, L.lu, n, L.piv, L.info, moves, base + o_gemm, prec, L.cap, nullptr);
+      e = cudaStreamEndCapture(L.cap, &g);
+      if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&L.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    L.kernels = c->kernels - k0;
+    c->kernels = k0;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      L.clear();
+      return err(c, SG_ERR_CUDA, "factorisation graph capture failed");
+    }
+    L.n = n;
+    L.prec = (int)prec;
+  }
+  cudaError_t e = cudaMemcpyAsync(L.lu, A, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, c->stream);
+  sgk::prof_begin(&c->prof, "lu_factor_graph", c->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(L.exec, c->stream);
+  sgk::prof_end(&c->prof, c->stream);
+  c->kernels += L.kernels;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return err(c, SG_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return SG_OK;
 }
 
 }  // namespace
@@ -156,21 +222,13 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
     off = al(off + bytes);
     return o2;
   };
-  const size_t o_lu = take((size_t)n * n * 4);
-  const size_t o_piv = take((size_t)n * 4);
   const size_t o_y = take((size_t)n * 4);
   const size_t o_r = take((size_t)n * 8);
   const size_t o_flags = take((size_t)2 * nb * 4);
   const size_t o_tk = take(64);
   const size_t o_err = take(64);
-  const size_t o_info = take(64);
-  const size_t o_moves = take((size_t)nb * sgk::kLuMoveInts * 4);
   const size_t o_norms = take(8 * 8);
   const size_t o_viol = take(8);
-  const size_t gemm_bytes = o.precision == SG_PREC_F32_SIMT
-                                ? 0
-                                : sgk::gemm_tc_scratch_bytes(n, n, sgk::kLuOuter);
-  const size_t o_gemm = take(gemm_bytes + 256);
   char* base = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&base, off, c->stream);
   if (e != cudaSuccess) {
@@ -178,17 +236,13 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
     return err(c, SG_ERR_OOM, "solve workspace allocation failed");
   }
   SolveWork w;
-  w.lu = reinterpret_cast<float*>(base + o_lu);
-  w.piv = reinterpret_cast<int*>(base + o_piv);
   w.y = reinterpret_cast<float*>(base + o_y);
   w.r = reinterpret_cast<double*>(base + o_r);
   w.flags = reinterpret_cast<unsigned*>(base + o_flags);
   w.tickets = reinterpret_cast<unsigned*>(base + o_tk);
   w.dev_err = reinterpret_cast<int*>(base + o_err);
-  w.info = reinterpret_cast<int*>(base + o_info);
   w.norms = reinterpret_cast<double*>(base + o_norms);
   w.viol = reinterpret_cast<unsigned long long*>(base + o_viol);
-  w.gemm = base + o_gemm;
 
   // the solution vector (owned by the returned handle)
   auto xv = std::make_shared<Value>();
@@ -225,19 +279,27 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
     return e == cudaSuccess;
   };
 
-  // 1. factorisation of a copy of A
-  e = cudaMemcpyAsync(w.lu, a, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(base + o_flags, 0, o_norms + 64 - o_flags, s);
+  // 1. factorisation of a copy of A (the context's cached graph)
+  e = cudaMemsetAsync(base + o_flags, 0, o_norms + 64 - o_flags, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.viol, 0, 8, s);
   if (e == cudaSuccess) e = sgk::launch_anorm(a, n, w.norms, s);
-  if (e == cudaSuccess)
-    e = factor_in_place(c, w.lu, n, w.piv, w.info, reinterpret_cast<int*>(base + o_moves), w.gemm,
-                        o.precision);
+  if (e == cudaSuccess) {
+    status = lu_factor(c, a, n, o.precision);
+    if (status) {
+      cudaFreeAsync(base, s);
+      return status;
+    }
+  }
+  w.lu = c->lu.lu;
+  w.piv = c->lu.piv;
+  w.info = c->lu.info;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hinfo, w.info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     status = err(c, SG_ERR_CUDA, cudaGetErrorString(e));
     cudaGetLastError();
+  } else if (hinfo < 0) {
+    status = err(c, SG_ERR_TIMEOUT, "panel exchange wait gave up");
   } else if (hinfo) {
     inf.info = hinfo;
     status = err(c, SG_ERR_SINGULAR, "exactly zero pivot");
@@ -345,50 +407,33 @@ extern "C" sg_status sg_det(sg_ctx* c, sg_matrix* A, sg_precision prec, sg_det_r
     *out = sg_det_result{1, 0, 0.0, 1.0};
     return SG_OK;
   }
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    const size_t o2 = off;
-    off = al(off + bytes);
-    return o2;
-  };
-  const size_t o_lu = take((size_t)n * n * 4);
-  const size_t o_piv = take((size_t)n * 4);
-  const size_t o_info = take(64);
-  const size_t o_out = take(64);
-  const size_t o_moves = take((size_t)((n + sgk::kLuPanel - 1) / sgk::kLuPanel) * sgk::kLuMoveInts * 4);
-  const size_t gemm_bytes =
-      prec == SG_PREC_F32_SIMT ? 0 : sgk::gemm_tc_scratch_bytes(n, n, sgk::kLuOuter);
-  const size_t o_gemm = take(gemm_bytes + 256);
-  char* base = nullptr;
   cudaStream_t s = c->stream;
-  cudaError_t e = cudaMallocAsync((void**)&base, off, s);
+  double* dout = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&dout, 64, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return err(c, SG_ERR_OOM, "det workspace allocation failed");
   }
-  float* lu = reinterpret_cast<float*>(base + o_lu);
-  int* piv = reinterpret_cast<int*>(base + o_piv);
-  int* info = reinterpret_cast<int*>(base + o_info);
-  double* dout = reinterpret_cast<double*>(base + o_out);
-  e = cudaMemcpyAsync(lu, A->v->st->ptr, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, 64, s);
-  int* moves = reinterpret_cast<int*>(base + o_moves);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(moves, 0, (size_t)((n + sgk::kLuPanel - 1) / sgk::kLuPanel) * sgk::kLuMoveInts * 4, s);
-  if (e == cudaSuccess) e = factor_in_place(c, lu, n, piv, info, moves, base + o_gemm, prec);
-  if (e == cudaSuccess) e = sgk::launch_lu_det(lu, n, piv, dout, s, &c->prof);
+  sg_status st2 = lu_factor(c, static_cast<const float*>(A->v->st->ptr), n, prec);
+  if (st2) {
+    cudaFreeAsync(dout, s);
+    return st2;
+  }
+  e = sgk::launch_lu_det(c->lu.lu, n, c->lu.piv, dout, s, &c->prof);
   c->kernels += 1;
+  int* info = c->lu.info;
   double h[2] = {0.0, 0.0};
   int hinfo = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (c->prof.on) c->prof.collect();
-  cudaFreeAsync(base, s);
+  cudaFreeAsync(dout, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return err(c, SG_ERR_CUDA, cudaGetErrorString(e));
   }
+  if (hinfo < 0) return err(c, SG_ERR_TIMEOUT, "panel exchange wait gave up");
   sg_det_result r;
   r.info = hinfo;
   if (hinfo) {   // the elimination stopped at an exactly zero pivot
@@ -402,4 +447,19 @@ extern "C" sg_status sg_det(sg_ctx* c, sg_matrix* A, sg_precision prec, sg_det_r
   }
   *out = r;
   return SG_OK;
+}
+
+void LuCache::clear() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (base) cudaFree(base);
+  if (cap) cudaStreamDestroy(cap);
+  exec = nullptr;
+  base = nullptr;
+  cap = nullptr;
+  lu = nullptr;
+  piv = nullptr;
+  info = nullptr;
+  n = 0;
+  prec = -1;
+  kernels = 0;
 }
