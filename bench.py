@@ -63,6 +63,30 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (the slowest rank sets the job's time);
+    x itself with one rank.  device: where the process group's backend
+    reduces ("cuda" for NCCL, "cpu" for gloo)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(world, bytes_per_rank, seconds):
+    """Whole-job throughput: every rank's bytes over the slowest rank's time
+    (weak scaling: each rank sorts its own keys)."""
+    return world * bytes_per_rank / seconds / 1e9
+
+
+def rank_seed(rank):
+    """Each replica sorts different keys: the workload's seed plus its rank."""
+    return 1 + rank
+
+
 class Clocks:
     """SM clock and clock-event reasons sampled during the timed region.
 
@@ -207,7 +231,7 @@ def run_reference(args):
     import oracle
     from paper_1410_6685_gb300 import inputs
     oracle.build()
-    sample = 1 << 22
+    sample = args.ref_sample
     keys = inputs.sort_keys_uniform(sample)
     for _ in range(args.warmup):
         oracle_step(keys)
@@ -221,10 +245,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": sample, "bytes_per_key": BYTES_PER_KEY},
+        "config": {"workload": WORKLOAD, "n": args.n, "bytes_per_key": BYTES_PER_KEY,
+                   "sample_keys_per_step": sample},
         "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": "2^22 uniform int32 keys per step: C qsort + is_sorted + "
-                                   "multiset equality (the oracle as it stands)"},
+                         "sample": "%d uniform int32 keys per step: C qsort + is_sorted + "
+                                   "multiset equality (the oracle as it stands)" % sample},
         "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -450,6 +475,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_KEYS)
+    ap.add_argument("--ref-sample", type=int, default=1 << 22,
+                    help="keys per step of the oracle in --impl reference")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the stream / GEMM / solve / batch figures")
     args = ap.parse_args()
@@ -473,7 +500,7 @@ def main():
     n = args.n
     stream = torch.cuda.current_stream()
     ctx = sg.sg_init(local, stream.cuda_stream)
-    keys = inputs.sort_keys_uniform(n, seed=1 + rank)
+    keys = inputs.sort_keys_uniform(n, seed=rank_seed(rank))
     tk = torch.from_numpy(keys).cuda()
     vk = sg.sg_vector_wrap(ctx, sg.SG_I32, n, tk.data_ptr())
 
@@ -498,12 +525,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         return ms / k
 
     for _ in range(args.warmup):
@@ -547,12 +569,7 @@ def main():
     for _ in range(ke):
         e2e_step()
     torch.cuda.synchronize()
-    t_e2e = (time.perf_counter() - t0) / ke
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / ke, world, "cuda")
     assert np.array_equal(hout_np[:1000], np.sort(keys)[:1000])
 
     if rank != 0:
@@ -560,7 +577,7 @@ def main():
         return
 
     peak, tc_peak, peak_kind = peaks()
-    value = world * BYTES_PER_KEY * n / (ms / 1e3) / 1e9
+    value = job_gbs(world, BYTES_PER_KEY * n, ms / 1e3)
     roof = None
     if "onesweep" in prof:
         cnt, tot = prof["onesweep"]
@@ -597,7 +614,7 @@ def main():
                    "contracts": "pre_post, fused", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": round(world * BYTES_PER_KEY * n / t_e2e / 1e9, 2), "unit": "GB/s",
+        "e2e": {"value": round(job_gbs(world, BYTES_PER_KEY * n, t_e2e), 2), "unit": "GB/s",
                 "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
                 "api": "sg_vector_create(host) -> sg_sort -> sg_vector_read(host), pinned"},
         "clocks": clk,
