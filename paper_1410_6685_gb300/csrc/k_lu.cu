@@ -16,7 +16,7 @@
 //                  and applied when the panel is written back, so the result
 //                  equals the row-swapping textbook algorithm.
 //   k_lu_laswp   : the panel's interchanges on the other columns.
-//   k_lu_trsm    : U12 = L11^-1 A12 (unit lower, 32x32).
+//   k_lu_trsm    : U12 = L11^-1 A12 (unit lower, 32x32), one warp per column.
 //   trailing update A22 -= L21 U12 : the tensor-core product (bf16/fp16
 //                  operands, binary32 accumulate) or the binary32 SIMT form.
 // Solve: pivots on the right-hand side, then forward / backward substitution
@@ -258,48 +258,53 @@ __global__ void __launch_bounds__(128) k_lu_laswp(float* LU, int n, const int* _
     if (t < cnt) LU[(size_t)s_dst[t] * n + c] = v[t];
 }
 
-// U12 = L11^-1 A12 for the columns [c0, c1): one thread per column
-__global__ void k_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1) {
+// U12 = L11^-1 A12 for the columns [c0, c1): one warp per column, lane i
+// holding row k+i; L11 (unit lower, 32x32) staged in shared memory
+__global__ void __launch_bounds__(256) k_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1) {
   __shared__ float L[kPB][kPB + 1];
   for (int t = threadIdx.x; t < jb * jb; t += blockDim.x)
     L[t / jb][t % jb] = LU[(size_t)(k + t / jb) * n + k + t % jb];
   __syncthreads();
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int c = c0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= c1) return;
-  float x[kPB];
+  float x = lane < jb ? LU[(size_t)(k + lane) * n + c] : 0.0f;
 #pragma unroll
-  for (int i = 0; i < kPB; ++i) x[i] = i < jb ? LU[(size_t)(k + i) * n + c] : 0.0f;
-#pragma unroll
-  for (int i = 1; i < kPB; ++i) {
-    if (i >= jb) break;
-    float s = x[i];
-#pragma unroll
-    for (int t = 0; t < i; ++t) s = fmaf(-L[i][t], x[t], s);
-    x[i] = s;
+  for (int i = 0; i < kPB - 1; ++i) {
+    const float xi = __shfl_sync(0xffffffffu, x, i);
+    if (lane > i && lane < jb) x = fmaf(-L[lane][i], xi, x);
   }
-#pragma unroll
-  for (int i = 1; i < kPB; ++i)
-    if (i < jb) LU[(size_t)(k + i) * n + c] = x[i];
+  if (lane >= 1 && lane < jb) LU[(size_t)(k + lane) * n + c] = x;
 }
 
 // ---------------------------------------------------------------------------
 // solve
 
-// y = P rhs (binary64 in, binary32 out): the row interchanges in order
-__global__ void k_apply_piv(const double* __restrict__ rhs, float* y, int n,
-                            const int* __restrict__ piv) {
-  // one CTA: copy, then the interchanges in order by one thread
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (float)rhs[i];
+// perm[i] = the row of A that elimination moved to row i: the interchanges
+// piv[0..n) applied in order to the identity, in shared memory by one thread
+// (once per factorisation)
+__global__ void __launch_bounds__(1024) k_lu_perm(const int* __restrict__ piv, int n, int* perm) {
+  extern __shared__ int s_perm[];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_perm[i] = i;
   __syncthreads();
   if (threadIdx.x == 0)
     for (int j = 0; j < n; ++j) {
       const int p = piv[j];
       if (p != j) {
-        const float t = y[j];
-        y[j] = y[p];
-        y[p] = t;
+        const int t = s_perm[j];
+        s_perm[j] = s_perm[p];
+        s_perm[p] = t;
       }
     }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = s_perm[i];
+}
+
+// y = P rhs (binary64 in, binary32 out): y[i] = rhs[perm[i]]
+__global__ void k_apply_perm(const double* __restrict__ rhs, float* y, int n,
+                             const int* __restrict__ perm) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i] = (float)rhs[perm[i]];
 }
 
 // Triangular solve by 32-row blocks.  LOWER: unit lower L, blocks in
@@ -505,21 +510,6 @@ __global__ void k_update(double* x, const float* __restrict__ d, const double* _
   }
 }
 
-__global__ void k_residual_to_f32(const double* __restrict__ r, float* y, int n,
-                                  const int* __restrict__ piv) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (float)r[i];
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int j = 0; j < n; ++j) {
-      const int p = piv[j];
-      if (p != j) {
-        const float t = y[j];
-        y[j] = y[p];
-        y[p] = t;
-      }
-    }
-}
-
 size_t panel_smem(int n, int k) {
   const int m = n - k;
   const int rs = (m + kPC - 1) / kPC;
@@ -560,20 +550,24 @@ cudaError_t launch_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1, cuda
                            Prof* prof) {
   if (c1 <= c0) return cudaSuccess;
   prof_begin(prof, "lu_trsm", s);
-  k_lu_trsm<<<(c1 - c0 + 127) / 128, 128, 0, s>>>(LU, n, k, jb, c0, c1);
+  k_lu_trsm<<<(c1 - c0 + 7) / 8, 256, 0, s>>>(LU, n, k, jb, c0, c1);
   prof_end(prof, s);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lu_solve(const float* LU, int n, const int* piv, const double* rhs,
+cudaError_t launch_lu_perm(const int* piv, int n, int* perm, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_lu_perm<<<1, 1024, (size_t)n * sizeof(int), s>>>(piv, n, perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_solve(const float* LU, int n, const int* perm, const double* rhs,
                             bool rhs_is_residual, float* y, unsigned* flags, unsigned epoch,
                             unsigned* tickets, int* err, cudaStream_t s, Prof* prof) {
+  (void)rhs_is_residual;
   const int nb = (n + 31) / 32;
   prof_begin(prof, "lu_trsv", s);
-  if (rhs_is_residual)
-    k_residual_to_f32<<<1, 1024, 0, s>>>(rhs, y, n, piv);
-  else
-    k_apply_piv<<<1, 1024, 0, s>>>(rhs, y, n, piv);
+  k_apply_perm<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(rhs, y, n, perm);
   cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s);
   k_trsv<true><<<nb, 256, 0, s>>>(LU, n, y, flags, epoch, tickets, err);
   k_trsv<false><<<nb, 256, 0, s>>>(LU, n, y, flags + nb, epoch, tickets + 1, err);

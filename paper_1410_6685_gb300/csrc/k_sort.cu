@@ -215,7 +215,6 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
 struct SortSmem {
   int keys[kTile];
   unsigned whist[kWarps][kRadix];
-  unsigned start[kRadix];
   int gbase[kRadix];
   unsigned warp[kWarps];
   unsigned tile;
@@ -233,7 +232,6 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
                                               unsigned tile) {
   int* const s_keys = sm.keys;
   unsigned (*const s_whist)[kRadix] = sm.whist;
-  unsigned* const s_start = sm.start;
   int* const s_gbase = sm.gbase;
   unsigned short* const s_rank = sm.rank;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -305,7 +303,11 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
       st_relaxed(&st32[(size_t)tile * kRadix + tid], ((tile == 0 ? kPre : kAgg) << 30) | cnt);
   }
   const unsigned start = block_excl_scan(cnt, sm.warp);
-  if (dig) s_start[tid] = start;
+  if (dig) {
+    // from here s_whist[w][d] is where warp w's keys of digit d start in the tile
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) s_whist[ww][tid] += start;
+  }
   __syncthreads();
 
   // sort the tile in shared memory by digit (stable)
@@ -313,7 +315,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   for (int r = 0; r < kKpt; ++r) {
     if (full || (wbase + r * 32) < n) {
       const unsigned d = digit_of<LAST, FLT>(key[r], dsel);
-      s_keys[s_start[d] + s_whist[w][d] + s_rank[lbase + r * 32]] = key[r];
+      s_keys[s_whist[w][d] + s_rank[lbase + r * 32]] = key[r];
     }
   }
   __syncthreads();

@@ -21,9 +21,12 @@ cudaError_t launch_lu_laswp(float* LU, int n, int k, int jb, const int* moves, c
 // rows k..k+jb of columns [c0, c1) := L11^-1 (them), L11 = unit lower at (k, k)
 cudaError_t launch_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1, cudaStream_t s,
                            Prof* prof);
-// y = U^-1 L^-1 P rhs in binary32; rhs_is_residual only changes the trace
-// name.  flags: 2*ceil(n/32) words that never hold `epoch` before the call.
-cudaError_t launch_lu_solve(const float* LU, int n, const int* piv, const double* rhs,
+// perm[i] = the row of A that the interchanges piv[0..n) moved to row i
+// (dynamic shared memory of n ints: n <= kLuMaxN)
+cudaError_t launch_lu_perm(const int* piv, int n, int* perm, cudaStream_t s);
+// y = U^-1 L^-1 P rhs in binary32 (P rhs gathered through perm).
+// flags: 2*ceil(n/32) words that never hold `epoch` before the call.
+cudaError_t launch_lu_solve(const float* LU, int n, const int* perm, const double* rhs,
                             bool rhs_is_residual, float* y, unsigned* flags, unsigned epoch,
                             unsigned* tickets, int* err, cudaStream_t s, Prof* prof);
 // r = b - A x in binary64; norms[0] = max|r|; rows with |r_i| > thresh

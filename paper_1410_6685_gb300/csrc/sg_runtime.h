@@ -137,6 +137,7 @@ struct LuCache {
   void* base = nullptr;
   float* lu = nullptr;
   int* piv = nullptr;
+  int* perm = nullptr;          // row i of the factors is row perm[i] of A
   int* info = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;

@@ -123,6 +123,7 @@ sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
     };
     const size_t o_lu = take((size_t)n * n * 4);
     const size_t o_piv = take((size_t)n * 4);
+    const size_t o_perm = take((size_t)n * 4);
     const size_t o_info = take(64);
     const size_t o_moves = take((size_t)np * sgk::kLuMoveInts * 4);
     const size_t o_gemm =
@@ -136,6 +137,7 @@ sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
     char* base = static_cast<char*>(L.base);
     L.lu = reinterpret_cast<float*>(base + o_lu);
     L.piv = reinterpret_cast<int*>(base + o_piv);
+    L.perm = reinterpret_cast<int*>(base + o_perm);
     L.info = reinterpret_cast<int*>(base + o_info);
     int* moves = reinterpret_cast<int*>(base + o_moves);
     const int64_t k0 = c->kernels;
@@ -146,6 +148,7 @@ sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
       if (le == cudaSuccess) le = cudaMemsetAsync(moves, 0, (size_t)np * sgk::kLuMoveInts * 4, L.cap);
       if (le == cudaSuccess)
         le = factor_in_place(c, L.lu, n, L.piv, L.info, moves, base + o_gemm, prec, L.cap, nullptr);
+      if (le == cudaSuccess) le = sgk::launch_lu_perm(L.piv, n, L.perm, L.cap);
       e = cudaStreamEndCapture(L.cap, &g);
       if (e == cudaSuccess) e = le;
     }
@@ -308,7 +311,7 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
   // 2. initial solve, 3. refinement
   bool converged = false;
   if (!status) {
-    e = sgk::launch_lu_solve(w.lu, n, w.piv, bb, false, w.y, w.flags, ++epoch, w.tickets,
+    e = sgk::launch_lu_solve(w.lu, n, c->lu.perm, bb, false, w.y, w.flags, ++epoch, w.tickets,
                              w.dev_err, s, prof);
     if (e == cudaSuccess) e = sgk::launch_update(x, w.y, bb, n, true, w.norms, s);
     c->kernels += 4;
@@ -317,7 +320,7 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
       e = cudaMemsetAsync(w.norms, 0, 3 * 8, s);
       if (e == cudaSuccess) e = sgk::launch_residual(a, n, bb, x, w.r, w.norms, 0.0, nullptr, s, prof);
       if (e == cudaSuccess)
-        e = sgk::launch_lu_solve(w.lu, n, w.piv, w.r, true, w.y, w.flags, ++epoch, w.tickets,
+        e = sgk::launch_lu_solve(w.lu, n, c->lu.perm, w.r, true, w.y, w.flags, ++epoch, w.tickets,
                                  w.dev_err, s, prof);
       if (e == cudaSuccess) e = sgk::launch_update(x, w.y, bb, n, false, w.norms, s);
       c->kernels += 5;
@@ -458,6 +461,7 @@ void LuCache::clear() {
   cap = nullptr;
   lu = nullptr;
   piv = nullptr;
+  perm = nullptr;
   info = nullptr;
   n = 0;
   prec = -1;
