@@ -45,6 +45,26 @@ WORKLOAD = ("sort int32 n=2^26 uniform full range, postconditions sorted + permu
             "fused into the last onesweep pass")
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# k_onesweep digit pass over 2^26 keys, from an ncu capture of the sort
+# kernels, valid only for the kernel source it was taken on (its SHA-256
+# prefix); for any other source the roofline reports no traffic.
+ONESWEEP_TRAFFIC = {"k_sort.cu": "527e7e201a0a5313", "n": 1 << 26, "bytes": 269703168 + 224380416}
+
+
+def onesweep_traffic(n):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1410_6685_gb300", "csrc", "k_sort.cu")
+    try:
+        with open(path, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if h != ONESWEEP_TRAFFIC["k_sort.cu"] or n != ONESWEEP_TRAFFIC["n"]:
+        return None
+    return ONESWEEP_TRAFFIC["bytes"]
+
+
 def peaks():
     """(HBM GB/s, bf16 TFLOP/s burst, kind): the measured copy bandwidth and
     cuBLAS bf16 rate of this GPU model, else the fallback figures."""
@@ -584,7 +604,7 @@ def main():
         dur = tot / cnt / 1e3
         achieved = 8.0 * n / dur / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": onesweep_traffic(n),
                 "kernel": "k_onesweep (passes 1-3; 8 bytes/key read+write)",
                 "peak_kind": peak_kind + " hbm_gbs (copy bandwidth)"}
     extras = None
