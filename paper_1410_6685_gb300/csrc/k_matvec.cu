@@ -5,12 +5,13 @@
 //   k_transpose : 64 x 64 tiles staged in shared memory (one padding column
 //                 against bank conflicts); 16-byte loads and stores when both
 //                 extents are multiples of 4, else element by element.
-//   k_matvec    : one warp per row, 16-byte loads of the row, x from L1, four
-//                 loads in flight per lane, binary32 FMA per lane then a warp
-//                 tree.
-//   k_vecmat    : column strips of 1024 (4 columns per thread), the rows split
-//                 into row stripes; each CTA leaves one partial row per stripe,
-//                 which k_vecmat_sum adds in stripe order (deterministic).
+//   k_matvec_cta: rows of 2048 or more aligned columns, one CTA per row,
+//                 eight 16-byte loads in flight per thread, binary32 FMA per
+//                 thread, a warp tree, the eight warp sums added in order.
+//   k_matvec    : narrower or unaligned rows, one warp per row.
+//   k_vecmat    : column strips of 1024 (4 columns per thread, eight rows'
+//                 16-byte loads in flight), the rows split into row stripes; each CTA leaves one partial row per stripe,
+//                 which k_vecmat_sum adds in a fixed order (deterministic).
 #include "sg_linalg_kernels.h"
 
 namespace sgk {
@@ -113,6 +114,58 @@ __global__ void __launch_bounds__(256) k_matvec(const float* __restrict__ A, int
   }
 }
 
+// y[i] = sum_j A[i][j] x[j] for wide rows, one CTA per row: thread t takes
+// the quads t, t + 256, t + 512, ... (the CTA's eight warps read 4 KB of the
+// row at once, eight such loads in flight per thread), a warp tree, then
+// thread 0 adds the eight warp sums in order.  Two slots of warp sums let one
+// barrier per row suffice.
+__global__ void __launch_bounds__(256) k_matvec_cta(const float* __restrict__ A, int rows,
+                                                    int cols, const float* __restrict__ x,
+                                                    float* __restrict__ y) {
+  __shared__ float s_part[2][8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nq = cols >> 2;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  int slot = 0;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const float4* a4 = reinterpret_cast<const float4*>(A + r * (long long)cols);
+    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
+    int q = threadIdx.x;
+    for (; q + 7 * 256 < nq; q += 8 * 256) {
+      float4 av[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        av[u] = __ldcs(a4 + q + 256 * u);
+        xv[u] = __ldg(x4 + q + 256 * u);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        acc0 = fmaf(av[u].x, xv[u].x, acc0);
+        acc1 = fmaf(av[u].y, xv[u].y, acc1);
+        acc2 = fmaf(av[u].z, xv[u].z, acc2);
+        acc3 = fmaf(av[u].w, xv[u].w, acc3);
+      }
+    }
+    for (; q < nq; q += 256) {
+      const float4 av = __ldcs(a4 + q), xv = __ldg(x4 + q);
+      acc0 = fmaf(av.x, xv.x, acc0);
+      acc1 = fmaf(av.y, xv.y, acc1);
+      acc2 = fmaf(av.z, xv.z, acc2);
+      acc3 = fmaf(av.w, xv.w, acc3);
+    }
+    const float sum = warp_sum((acc0 + acc1) + (acc2 + acc3));
+    if (lane == 0) s_part[slot][w] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = s_part[slot][0];
+#pragma unroll
+      for (int k = 1; k < 8; ++k) t += s_part[slot][k];
+      y[r] = t;
+    }
+    slot ^= 1;
+  }
+}
+
 // partial[s][j] = sum over rows i of stripe s of x[i] A[i][j]
 __global__ void __launch_bounds__(256) k_vecmat(const float* __restrict__ x,
                                                 const float* __restrict__ A, int rows, int cols,
@@ -126,16 +179,16 @@ __global__ void __launch_bounds__(256) k_vecmat(const float* __restrict__ x,
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   if (vec) {
     int i = i0;
-    for (; i + 3 < i1; i += 4) {
-      float4 av[4];
-      float xv[4];
+    for (; i + 7 < i1; i += 8) {
+      float4 av[8];
+      float xv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         av[u] = __ldcs(reinterpret_cast<const float4*>(A + (size_t)(i + u) * cols + c));
         xv[u] = __ldg(x + i + u);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         acc.x = fmaf(xv[u], av[u].x, acc.x);
         acc.y = fmaf(xv[u], av[u].y, acc.y);
         acc.z = fmaf(xv[u], av[u].z, acc.z);
@@ -165,13 +218,28 @@ __global__ void __launch_bounds__(256) k_vecmat(const float* __restrict__ x,
   }
 }
 
-__global__ void k_vecmat_sum(const float* __restrict__ partial, int stripes, int cols,
-                             float* __restrict__ y) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= cols) return;
-  float s = 0.0f;
-  for (int k = 0; k < stripes; ++k) s += partial[(size_t)k * cols + j];
-  y[j] = s;
+// y[j] = sum over stripes of partial[s][j]: 32 columns per CTA, its eight
+// warps take the stripes k = w, w + 8, ... and thread row 0 adds the eight
+// sums in order (a fixed order, so the result is deterministic)
+__global__ void __launch_bounds__(256) k_vecmat_sum(const float* __restrict__ partial,
+                                                    int stripes, int cols,
+                                                    float* __restrict__ y) {
+  __shared__ float sp[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + tx;
+  float acc = 0.0f;
+  if (j < cols) {
+#pragma unroll 4
+    for (int k = ty; k < stripes; k += 8) acc += __ldcg(partial + (size_t)k * cols + j);
+  }
+  sp[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && j < cols) {
+    float t = sp[0][tx];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) t += sp[k][tx];
+    y[j] = t;
+  }
 }
 
 int sm_count() {
@@ -216,9 +284,18 @@ cudaError_t launch_matvec(const float* A, int rows, int cols, const float* x, fl
   if (rows <= 0) return cudaSuccess;
   if (cols <= 0) return cudaMemsetAsync(y, 0, (size_t)rows * 4, s);
   const int vec = (cols % 4 == 0 && ((uintptr_t)A % 16) == 0 && ((uintptr_t)x % 16) == 0) ? 1 : 0;
-  const long long blocks = std::min<long long>((rows + 7) / 8, (long long)sm_count() * 8);
   prof_begin(prof, "matvec", s);
-  k_matvec<<<(int)blocks, 256, 0, s>>>(A, rows, cols, x, y, vec);
+  if (vec && cols >= 2048) {
+    static int occ = 0;
+    if (!occ && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_matvec_cta, 256, 0) !=
+                    cudaSuccess)
+      occ = 1;
+    const long long blocks = std::min<long long>(rows, (long long)sm_count() * std::max(occ, 1));
+    k_matvec_cta<<<(int)blocks, 256, 0, s>>>(A, rows, cols, x, y);
+  } else {
+    const long long blocks = std::min<long long>((rows + 7) / 8, (long long)sm_count() * 8);
+    k_matvec<<<(int)blocks, 256, 0, s>>>(A, rows, cols, x, y, vec);
+  }
   prof_end(prof, s);
   return cudaGetLastError();
 }
@@ -240,7 +317,7 @@ cudaError_t launch_vecmat(const float* x, const float* A, int rows, int cols, fl
   float* partial = static_cast<float*>(scratch);
   prof_begin(prof, "vecmat", s);
   k_vecmat<<<dim3((cols + 1023) / 1024, stripes), 256, 0, s>>>(x, A, rows, cols, rps, partial, vec);
-  k_vecmat_sum<<<(cols + 255) / 256, 256, 0, s>>>(partial, stripes, cols, y);
+  k_vecmat_sum<<<(cols + 31) / 32, 256, 0, s>>>(partial, stripes, cols, y);
   prof_end(prof, s);
   return cudaGetLastError();
 }

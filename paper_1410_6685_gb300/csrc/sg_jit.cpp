@@ -270,17 +270,27 @@ __device__ __forceinline__ void sg_elem(const BatchJitArgs& a, float v, long lon
   if (hit & 1u) acc.first[0] = i < acc.first[0] ? i : acc.first[0];
   acc_one(acc, rv, rm);
 }
-__device__ __forceinline__ void sg_quad(const BatchJitArgs& a, float4 t, long long j0,
-                                        long long b, long long e, long long sb, Acc& acc) {
+// one quad wholly inside the collection: the four masked values are added in
+// pairs, (v0 + v1) + (v2 + v3) (error at most 2u of their magnitudes), and the
+// pair sum enters the compensated accumulator once; kept elements counted in
+// 32 bits (a chunk holds far fewer than 2^31)
+__device__ __forceinline__ void sg_quad_in(const BatchJitArgs& a, float4 t, long long i0, Acc& acc,
+                                           int& cnt) {
   const float xv[4] = {t.x, t.y, t.z, t.w};
-  if (j0 >= b && j0 + 3 < e) {
+  float w[4];
 #pragma unroll
-    for (int l = 0; l < 4; ++l) sg_elem(a, xv[l], j0 + l - sb, acc);
-  } else {
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-      if (j0 + l >= b && j0 + l < e) sg_elem(a, xv[l], j0 + l - sb, acc);
+  for (int l = 0; l < 4; ++l) {
+    float x[1] = {xv[l]};
+    float o[1];
+    unsigned hit = 0u;
+    float rv = 0.0f;
+    bool rm = false;
+    sg_body(a, x, i0 + l, o, hit, rv, rm);
+    if (hit & 1u) acc.first[0] = i0 + l < acc.first[0] ? i0 + l : acc.first[0];
+    w[l] = rm ? rv : 0.0f;
+    cnt += rm ? 1 : 0;
   }
+  acc_add(acc, __fadd_rn(__fadd_rn(w[0], w[1]), __fadd_rn(w[2], w[3])));
 }
 // the three fields a chunk's result needs, combined like acc_merge
 __device__ __forceinline__ void batch_warp_reduce(double& sum, long long& cnt, long long& first) {
@@ -316,18 +326,32 @@ extern "C" __global__ void __launch_bounds__(256) sg_batch(const BatchJitArgs a)
     Acc acc;
     acc_init(acc);
     if (a.vec4) {
-      // each thread visits quads q, q + 256, q + 512, ... in that order; four
-      // loads are issued before the four are evaluated
-      const long long q1 = (e + 3) >> 2;
-      long long q = (b >> 2) + threadIdx.x;
-      for (; q + 768 < q1; q += 1024) {
+      // quads [qa, qz) lie wholly in [b, e); the at most three elements before
+      // and after them go one by one.  Each thread visits quads q, q + 256,
+      // q + 512, ... in that order, four loads issued before four are evaluated.
+      const long long qa = (b + 3) >> 2;
+      const long long qz = (e >> 2) > qa ? (e >> 2) : qa;
+      const long long hb = b, he = (qa << 2) < e ? (qa << 2) : e;
+      const long long tb = (qz << 2) > he ? (qz << 2) : he;
+      if (threadIdx.x < he - hb) {
+        const long long i = hb + threadIdx.x;
+        sg_elem(a, __ldcs(a.data + i), i - sb, acc);
+      } else if (threadIdx.x >= 4 && threadIdx.x - 4 < e - tb) {
+        const long long i = tb + threadIdx.x - 4;
+        sg_elem(a, __ldcs(a.data + i), i - sb, acc);
+      }
+      int cnt = 0;
+      long long q = qa + threadIdx.x;
+      const long long ib = -sb;
+      for (; q + 768 < qz; q += 1024) {
         float4 t[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) t[u] = __ldcs(d4 + q + u * 256);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) sg_quad(a, t[u], (q + u * 256) << 2, b, e, sb, acc);
+        for (int u = 0; u < 4; ++u) sg_quad_in(a, t[u], ((q + u * 256) << 2) + ib, acc, cnt);
       }
-      for (; q < q1; q += 256) sg_quad(a, __ldcs(d4 + q), q << 2, b, e, sb, acc);
+      for (; q < qz; q += 256) sg_quad_in(a, __ldcs(d4 + q), (q << 2) + ib, acc, cnt);
+      acc.cnt += cnt;
     } else {
       for (long long i = b + threadIdx.x; i < e; i += 256) sg_elem(a, __ldcs(a.data + i), i - sb, acc);
     }

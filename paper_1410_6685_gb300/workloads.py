@@ -6,7 +6,7 @@ A small command-line driver for measuring and profiling single kernels:
     python -m paper_1410_6685_gb300.workloads stream [--n N] [--reps R]
     python -m paper_1410_6685_gb300.workloads gemm   [--n N] [--reps R] [--prec 0|1|2]
     python -m paper_1410_6685_gb300.workloads solve  [--n N] [--reps R] [--prec 0|1|2]
-    python -m paper_1410_6685_gb300.workloads batch  [--reps R]
+    python -m paper_1410_6685_gb300.workloads batch  [--n collections] [--reps R]
     python -m paper_1410_6685_gb300.workloads filter [--n N] [--reps R]
     python -m paper_1410_6685_gb300.workloads transpose [--n N] [--reps R]
 
@@ -128,7 +128,7 @@ def main(argv=None):
         out["kernels"] = run(step)
         out.update(info_box)
     elif a.case == "batch":
-        L = inputs.batch_lengths()
+        L = inputs.batch_lengths(a.n or 10000)
         off = inputs.batch_offsets(L)
         total = int(off[-1])
         g = torch.Generator(device="cuda").manual_seed(9)

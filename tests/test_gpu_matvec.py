@@ -10,7 +10,7 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(1, 1), (7, 13), (64, 64), (65, 127), (1000, 3), (3, 1000), (513, 2048), (2048, 1031)]
+SHAPES = [(1, 1), (7, 13), (64, 64), (65, 127), (1000, 3), (3, 1000), (513, 2048), (2048, 1031), (300, 3076)]
 
 
 @pytest.fixture(scope="module")
