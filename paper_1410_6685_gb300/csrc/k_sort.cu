@@ -8,7 +8,8 @@
 //      histograms and the input's multiset fingerprint; its last block turns
 //      the histograms into per-digit global start offsets.
 //   2. k_onesweep x4: each CTA takes the next tile (a global atomic ticket,
-//      so tiles start in order; 6144 keys, 24 per thread), ranks its keys
+//      so tiles start in order; 6144 keys, 24 per thread), prefetches the
+//      tile one resident wave ahead into L2 (cp.async.bulk.prefetch), ranks its keys
 //      stably inside the tile (warp-private counters; the lanes sharing a
 //      digit are found by match_any or by ballots), publishes its per-digit tile
 //      counts, finds the exclusive prefix of each digit over the preceding
@@ -432,7 +433,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 template <bool LAST, bool CHECK, bool FLT>
 __global__ void __launch_bounds__(kSortBlock, kSortMinBlocks) k_onesweep(
     const int* __restrict__ in, int* __restrict__ out, long long n, int pass, SortHdr* h,
-    unsigned* st32, unsigned long long* st64, SortResult* res) {
+    unsigned* st32, unsigned long long* st64, SortResult* res, unsigned ahead) {
   __shared__ SortSmem sm;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -442,6 +443,15 @@ __global__ void __launch_bounds__(kSortBlock, kSortMinBlocks) k_onesweep(
   for (int i = tid; i < kWarps * kRadix; i += kSortBlock) (&sm.whist[0][0])[i] = 0;
   __syncthreads();
   const unsigned tile = sm.tile;
+  // tiles are taken in ticket order: the tile one resident wave ahead is
+  // fetched into L2 now, so that its CTA's key loads hit L2
+  if (tid == 0 && ((uintptr_t)in & 15) == 0) {
+    const long long t2 = (long long)tile + ahead;
+    if ((t2 + 1) * kTile <= n)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + t2 * kTile),
+                   "r"((unsigned)(kTile * sizeof(int)))
+                   : "memory");
+  }
   if ((long long)(tile + 1) * kTile <= n)
     onesweep_tile<LAST, CHECK, true, FLT>(sm, in, out, n, pass, h, st32, st64, res, tile);
   else
@@ -546,14 +556,15 @@ cudaError_t sort_impl(const int32_t* in, int32_t* out, long long n, bool contrac
     k_radix_hist<FLT, false><<<grid_for((n + 3) / 4 / 8, num_sms, 8), 256, 0, s>>>(in, n, h, res);
   prof_end(prof, s);
   const unsigned ntiles = (unsigned)((n + kTile - 1) / kTile);
+  const unsigned ahead = (unsigned)num_sms * kSortMinBlocks;
   prof_begin(prof, "onesweep", s);
-  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(in, tmp, n, 0, h, st32[0], st64, res);
+  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(in, tmp, n, 0, h, st32[0], st64, res, ahead);
   prof_end(prof, s);
   prof_begin(prof, "onesweep", s);
-  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 1, h, st32[1], st64, res);
+  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 1, h, st32[1], st64, res, ahead);
   prof_end(prof, s);
   prof_begin(prof, "onesweep", s);
-  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(out, tmp, n, 2, h, st32[2], st64, res);
+  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(out, tmp, n, 2, h, st32[2], st64, res, ahead);
   prof_end(prof, s);
   if (inject && inject->mode == 1 && inject->i < n && inject->j < n) {
     // swap through the (now free) output buffer: stream-ordered host copies
@@ -574,9 +585,9 @@ cudaError_t sort_impl(const int32_t* in, int32_t* out, long long n, bool contrac
   unsigned* st_last = reinterpret_cast<unsigned*>(st64);
   prof_begin(prof, contracts ? "onesweep_last_checked" : "onesweep", s);
   if (contracts)
-    k_onesweep<true, true, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res);
+    k_onesweep<true, true, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res, ahead);
   else
-    k_onesweep<true, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res);
+    k_onesweep<true, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res, ahead);
   prof_end(prof, s);
   *kernels += 5;
   return cudaGetLastError();
