@@ -2,7 +2,8 @@
 // partial pivoting) and the solve with iterative refinement (sm_103a).
 //
 // Right-looking blocked LU, panels of 32 columns:
-//   k_lu_panel   : a cluster of 8 CTAs holds the panel (rows k..n-1) in their
+//   k_lu_panel   : a cluster of 16 CTAs (8 where the device cannot schedule
+//                  16) holds the panel (rows k..n-1) in their
 //                  shared memories and eliminates it column by column.  Each
 //                  column costs one exchange: every CTA sends its best pivot
 //                  candidate (largest |a|, then the lowest current row
@@ -15,10 +16,16 @@
 //                  interchanges are tracked as a replicated position table
 //                  and applied when the panel is written back, so the result
 //                  equals the row-swapping textbook algorithm.
-//   k_lu_laswp   : the panel's interchanges on the other columns.
-//   k_lu_trsm    : U12 = L11^-1 A12 (unit lower, 32x32), one warp per column.
-//   trailing update A22 -= L21 U12 : the tensor-core product (bf16/fp16
-//                  operands, binary32 accumulate) or the binary32 SIMT form.
+//                  At the end it applies its interchanges to the rest of
+//                  its 128-column outer block.
+//   k_lu_inner   : inside the outer block, after each panel, the columns to
+//                  its right: U12 = L11^-1 A12 and A22 -= L21 U12, one launch.
+//   k_lu_laswp_outer : the outer block's interchanges on every other column.
+//   k_lu_trsm_outer  : U12 = L11^-1 A12 for the outer block (128 rows), L11
+//                  and a 32-column strip per CTA in shared memory.
+//   trailing update A22 -= L21 U12 (K = 128) : the tensor-core product
+//                  (bf16/fp16 operands, binary32 accumulate) or the binary32
+//                  SIMT form.
 // Solve: pivots on the right-hand side, then forward / backward substitution
 // by blocks of 32 rows in one launch each: CTAs take row blocks in order
 // (ticket) and wait, with a bounded spin, for the blocks they depend on.
@@ -35,7 +42,8 @@ namespace sgk {
 namespace {
 
 constexpr int kPB = 32;       // panel width
-constexpr int kPC = 8;        // CTAs per cluster
+// CTAs per cluster (PC): 16 where the device schedules clusters of 16
+// (non-portable size), else 8
 constexpr int kPT = 256;      // threads per CTA
 constexpr int kStride = kPB + 1;
 constexpr unsigned kSpin = 1u << 24;
@@ -48,9 +56,12 @@ __device__ __forceinline__ unsigned long long key_of(float v, int pos, int row) 
          ((unsigned long long)(0xFFFFu - (unsigned)pos) << 16) | (unsigned)row;
 }
 
-constexpr int kMaxRowsPerThread = 5;   // ceil(ceil(9216 / 8) / 256)
-// bytes every CTA receives per column: 8 candidates and 8 candidate rows
-constexpr unsigned kColBytes = kPC * (8 + kPB * 4);
+// rows per thread for the largest n: ceil(ceil(kLuMaxN / PC) / kPT)
+template <int PC>
+__host__ __device__ constexpr int max_rows_per_thread() { return (kLuMaxN / PC + kPT - 1) / kPT; }
+// bytes every CTA receives per column: PC candidates and PC candidate rows
+template <int PC>
+__host__ __device__ constexpr unsigned col_bytes() { return PC * (8 + kPB * 4); }
 
 __device__ __forceinline__ uint32_t sm_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -86,32 +97,39 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// smem: slab[rs][33] floats, cand[2][8] u64, best[2] u64, bar[2] u64,
-// crow[2][8][32] floats
-__global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
+// the outer block's columns outside the panel, per cluster CTA (PC >= 8)
+constexpr int kXCols = (kLuOuter - kPB + 7) / 8;
+
+// smem: slab[rs][33] floats, cand[2][PC] u64, best[2] u64, bar[2] u64,
+// crow[2][PC][32] floats, xbuf[64][kXCols] floats
+template <int PC>
+__global__ void __launch_bounds__(kPT)
     k_lu_panel(float* __restrict__ LU, int n, int k, int jb, int* __restrict__ piv,
-               int* __restrict__ info, int* __restrict__ moves) {
+               int* __restrict__ info, int* __restrict__ moves, int c_lo, int c_hi) {
+  constexpr int kRows = max_rows_per_thread<PC>();
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int m = n - k;
-  const int rs = (m + kPC - 1) / kPC;
+  const int rs = (m + PC - 1) / PC;
   const int r0 = rank * rs;
   const int r1 = min(m, r0 + rs);
   float* slab = reinterpret_cast<float*>(smem);
   unsigned long long* cand = reinterpret_cast<unsigned long long*>(
       (reinterpret_cast<uintptr_t>(slab + (size_t)rs * kStride) + 15) & ~(uintptr_t)15);
-  unsigned long long* best = cand + 2 * kPC;
+  unsigned long long* best = cand + 2 * PC;
   unsigned long long* bar = best + 2;
   // crow[par][q][c]: CTA q's candidate row for the column of parity par
   float* crow = reinterpret_cast<float*>(bar + 2);
+  // xbuf[t][i]: moved row t of this CTA's i-th outer-block column
+  float* xbuf = crow + 2 * PC * kPB;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
 
   // my rows: r = r0 + tid + i*kPT; their current positions live in registers
-  int lp[kMaxRowsPerThread];
+  int lp[kRows];
 #pragma unroll
-  for (int i = 0; i < kMaxRowsPerThread; ++i) lp[i] = r0 + tid + i * kPT;
+  for (int i = 0; i < kRows; ++i) lp[i] = r0 + tid + i * kPT;
   for (int t = tid; t < (r1 - r0) * kPB; t += kPT) {
     const int r = t / kPB, c = t % kPB;
     slab[r * kStride + c] = c < jb ? LU[(size_t)(k + r0 + r) * n + k + c] : 0.0f;
@@ -126,7 +144,7 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
   // the first column's candidate
   unsigned long long mine = 0ull;
 #pragma unroll
-  for (int i = 0; i < kMaxRowsPerThread; ++i) {
+  for (int i = 0; i < kRows; ++i) {
     const int r = r0 + tid + i * kPT;
     if (r < r1) {
       const unsigned long long kk = key_of(slab[(r - r0) * kStride], lp[i], r);
@@ -147,16 +165,16 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     if (lane == 0 && mine) atomicMax(&best[par], mine);
     if (tid == 0)   // this column's bytes from the cluster complete bar[par]
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
-                   "r"(kColBytes) : "memory");
+                   "r"(col_bytes<PC>()) : "memory");
     __syncthreads();
     // send the candidate and its row (the pivot row, should it win) to every
     // CTA of the cluster; the stores complete on the receivers' bar[par].
     // A CTA sends column j + 2 only after it has all of column j + 1, which
     // every CTA sends only after reading column j: two slots suffice.
     const unsigned long long bmine = best[par];
-    if (tid < kPC) {
-      st_async_b64(cl_addr(sm_addr(&cand[par * kPC + rank]), tid), bmine, cl_addr(mbar, tid));
-    } else if (tid >= 32 && tid < 32 + kPB * kPC / 4) {
+    if (tid < PC) {
+      st_async_b64(cl_addr(sm_addr(&cand[par * PC + rank]), tid), bmine, cl_addr(mbar, tid));
+    } else if (tid >= 32 && tid < 32 + kPB * PC / 4) {
       const int q = (tid - 32) / (kPB / 4), cq = ((tid - 32) % (kPB / 4)) * 4;
       const int lr = bmine ? (int)(bmine & 0xFFFFu) - r0 : 0;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -166,9 +184,9 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
         v.z = (cq + 2 >= j && cq + 2 < jb) ? slab[lr * kStride + cq + 2] : 0.0f;
         v.w = (cq + 3 >= j && cq + 3 < jb) ? slab[lr * kStride + cq + 3] : 0.0f;
       }
-      st_async_v4(cl_addr(sm_addr(&crow[(par * kPC + rank) * kPB + cq]), q), v, cl_addr(mbar, q));
+      st_async_v4(cl_addr(sm_addr(&crow[(par * PC + rank) * kPB + cq]), q), v, cl_addr(mbar, q));
     }
-    if (tid == kPC) best[par ^ 1] = 0ull;   // next column's slot (its last reader is done)
+    if (tid == PC) best[par ^ 1] = 0ull;   // next column's slot (its last reader is done)
     if (!bar_wait(mbar, (uint32_t)(j >> 1) & 1u)) {
       failed = true;
       break;
@@ -176,16 +194,16 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     unsigned long long g = 0ull;
     int wq = 0;
 #pragma unroll
-    for (int q = 0; q < kPC; ++q) {
-      const unsigned long long cq = cand[par * kPC + q];
+    for (int q = 0; q < PC; ++q) {
+      const unsigned long long cq = cand[par * PC + q];
       if (cq > g) { g = cq; wq = q; }
     }
     const int p = (int)(0xFFFFu - (unsigned)((g >> 16) & 0xFFFFu));   // winning position
     const int gp = (int)(g & 0xFFFFu);                                // its row in the panel
-    const float* prow = crow + (par * kPC + wq) * kPB;
+    const float* prow = crow + (par * PC + wq) * kPB;
     // interchange of positions j and p (each thread for its own rows)
 #pragma unroll
-    for (int i = 0; i < kMaxRowsPerThread; ++i) {
+    for (int i = 0; i < kRows; ++i) {
       const int r = r0 + tid + i * kPT;
       if (lp[i] == j) lp[i] = p;
       if (r == gp) lp[i] = j;
@@ -196,7 +214,7 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     // eliminate below the pivot; find the next column's candidate
     mine = 0ull;
 #pragma unroll
-    for (int i = 0; i < kMaxRowsPerThread; ++i) {
+    for (int i = 0; i < kRows; ++i) {
       const int r = r0 + tid + i * kPT;
       if (r >= r1 || lp[i] <= j) continue;
       float* row = slab + (r - r0) * kStride;
@@ -217,7 +235,7 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
   // write the panel back in its final row order, and list the rows that
   // moved (at most 2 jb) for the other columns' interchange
 #pragma unroll
-  for (int i = 0; i < kMaxRowsPerThread; ++i) {
+  for (int i = 0; i < kRows; ++i) {
     const int r = r0 + tid + i * kPT;
     if (r >= r1 || failed) continue;
     float* dst = LU + (size_t)(k + lp[i]) * n + k;
@@ -232,49 +250,236 @@ __global__ void __cluster_dims__(kPC, 1, 1) __launch_bounds__(kPT)
     }
   }
   if (tid == 0 && rank == 0 && my_info) atomicCAS(info, 0, my_info);
-  cluster.sync();
+  const bool any_failed = __syncthreads_or(failed);
+  cluster.sync();   // every CTA's moves are listed
+  // the interchanges on the outer block's other columns [c_lo, k) and
+  // [k + jb, c_hi) (at most kXCols * PC): CTA `rank` takes the columns
+  // rank, rank + PC, ...; all their moved rows are read into shared memory
+  // before any is written
+  const int nl = k - c_lo, nc = nl + (c_hi - k - jb);
+  const int nci = nc > rank ? (nc - rank + PC - 1) / PC : 0;
+  if (!any_failed && nci > 0) {
+    const int cnt = min(moves[0], 2 * kPB);
+    for (int e = tid; e < cnt * nci; e += kPT) {
+      const int t = e / nci, i = e % nci, g = rank + i * PC;
+      const int c = g < nl ? c_lo + g : k + jb + (g - nl);
+      xbuf[t * kXCols + i] = LU[(size_t)moves[1 + t] * n + c];
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt * nci; e += kPT) {
+      const int t = e / nci, i = e % nci, g = rank + i * PC;
+      const int c = g < nl ? c_lo + g : k + jb + (g - nl);
+      LU[(size_t)moves[1 + 2 * kPB + t] * n + c] = xbuf[t * kXCols + i];
+    }
+  }
 }
 
-// The panel's interchanges on columns [c0, c1) as one permutation: row
-// dst[t] receives old row src[t] (the list the panel kernel left).  Every
-// load of a column is issued before its stores.
-__global__ void __launch_bounds__(128) k_lu_laswp(float* LU, int n, const int* __restrict__ moves,
-                                                  int c0, int c1) {
-  __shared__ int s_src[2 * kPB], s_dst[2 * kPB];
-  const int cnt = min(moves[0], 2 * kPB);
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    s_src[t] = moves[1 + t];
-    s_dst[t] = moves[1 + 2 * kPB + t];
+// The interchanges of an outer block's panels (moves lists m0, m0 + 1, ...,
+// in order) on the columns outside it, [0, K) and [K + KB, n): one thread
+// per column; for each list every load of the column precedes its stores.
+__global__ void __launch_bounds__(128) k_lu_laswp_outer(float* LU, int n, const int* __restrict__ moves,
+                                                        int nlists, int K, int KB) {
+  __shared__ int s_cnt[kLuOuter / kPB], s_src[kLuOuter / kPB][2 * kPB],
+      s_dst[kLuOuter / kPB][2 * kPB];
+  for (int q = 0; q < nlists; ++q) {
+    const int* m = moves + (size_t)q * kLuMoveInts;
+    const int cnt = min(m[0], 2 * kPB);
+    if (threadIdx.x == 0) s_cnt[q] = cnt;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      s_src[q][t] = m[1 + t];
+      s_dst[q][t] = m[1 + 2 * kPB + t];
+    }
   }
   __syncthreads();
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= c1) return;
-  float v[2 * kPB];
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = g < K ? g : g + KB;
+  if (c >= n) return;
+  for (int q = 0; q < nlists; ++q) {
+    const int cnt = s_cnt[q];
+    float v[2 * kPB];
 #pragma unroll
-  for (int t = 0; t < 2 * kPB; ++t)
-    if (t < cnt) v[t] = LU[(size_t)s_src[t] * n + c];
+    for (int t = 0; t < 2 * kPB; ++t)
+      if (t < cnt) v[t] = LU[(size_t)s_src[q][t] * n + c];
 #pragma unroll
-  for (int t = 0; t < 2 * kPB; ++t)
-    if (t < cnt) LU[(size_t)s_dst[t] * n + c] = v[t];
+    for (int t = 0; t < 2 * kPB; ++t)
+      if (t < cnt) LU[(size_t)s_dst[q][t] * n + c] = v[t];
+  }
 }
 
-// U12 = L11^-1 A12 for the columns [c0, c1): one warp per column, lane i
-// holding row k+i; L11 (unit lower, 32x32) staged in shared memory
-__global__ void __launch_bounds__(256) k_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1) {
+// x := L^-1 x for one column x of 32 entries (stride xs) and the unit lower
+// triangle of L (row stride ls), by forward substitution in registers: row i
+// subtracts L[i][0] x[0], L[i][1] x[1], ... in that order
+__device__ __forceinline__ void unit_lower_solve_col(const float* L, int ls, float* x, int xs) {
+  float v[kPB];
+#pragma unroll
+  for (int i = 0; i < kPB; ++i) v[i] = x[i * xs];
+#pragma unroll
+  for (int i = 1; i < kPB; ++i) {
+    float acc = v[i];
+#pragma unroll
+    for (int q = 0; q < i; ++q) acc = fmaf(-L[i * ls + q], v[q], acc);
+    v[i] = acc;
+  }
+#pragma unroll
+  for (int i = 1; i < kPB; ++i) x[i * xs] = v[i];
+}
+
+// After panel j inside an outer block, for its columns [c0, c1) to the right
+// of the panel (at most kLuOuter - kPB):
+//   U12 = L11^-1 A12 (rows j..j+32; L11 the panel's unit lower triangle)
+//   A22 -= L21 U12   (rows j+32..n)
+// Each CTA solves U12 in shared memory (one thread per column) and updates
+// kInRows rows of A22.  U12 replaces A12 in LU only after every
+// CTA has read A12: the CTA that counts last on `counter` (zero before the
+// launch) writes it.
+constexpr int kInRows = 32;
+constexpr int kInCols = kLuOuter - kPB;
+__global__ void __launch_bounds__(256) k_lu_inner(float* LU, int n, int j, int c0, int c1,
+                                                  unsigned* counter) {
   __shared__ float L[kPB][kPB + 1];
-  for (int t = threadIdx.x; t < jb * jb; t += blockDim.x)
-    L[t / jb][t % jb] = LU[(size_t)(k + t / jb) * n + k + t % jb];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int c = c0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (c >= c1) return;
-  float x = lane < jb ? LU[(size_t)(k + lane) * n + c] : 0.0f;
+  __shared__ float U[kPB][kInCols + 1];
+  __shared__ float P[kInRows][kPB + 1];
+  __shared__ bool s_last;
+  const int tid = threadIdx.x;
+  const int N = c1 - c0;
+  const int rb = j + kPB + blockIdx.x * kInRows;
+  const int nr = min(kInRows, n - rb);
+  const int lane = tid & 31, w = tid >> 5;
+  // staging: every thread issues all its loads before its shared stores;
+  // thread (w, lane) owns rows w + 8 i (i < 4) and columns lane + 32 u (u < 3)
+  {
+    float l4[4], p4[4], u12[12];
 #pragma unroll
-  for (int i = 0; i < kPB - 1; ++i) {
-    const float xi = __shfl_sync(0xffffffffu, x, i);
-    if (lane > i && lane < jb) x = fmaf(-L[lane][i], xi, x);
+    for (int i = 0; i < 4; ++i) {
+      const int r = w + 8 * i;
+      l4[i] = __ldg(LU + (size_t)(j + r) * n + j + lane);
+      p4[i] = r < nr ? __ldg(LU + (size_t)(rb + r) * n + j + lane) : 0.0f;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int c = lane + 32 * u;
+        u12[i * 3 + u] = c < N ? __ldg(LU + (size_t)(j + r) * n + c0 + c) : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = w + 8 * i;
+      L[r][lane] = l4[i];
+      P[r][lane] = p4[i];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) U[r][lane + 32 * u] = u12[i * 3 + u];
+    }
   }
-  if (lane >= 1 && lane < jb) LU[(size_t)(k + lane) * n + c] = x;
+  // this thread's A22 entries, loaded while U12 is solved
+  float acc[12];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int r = w + 8 * i, c = lane + 32 * u;
+      acc[i * 3 + u] = (r < nr && c < N) ? LU[(size_t)(rb + r) * n + c0 + c] : 0.0f;
+    }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  if (tid < N) unit_lower_solve_col(&L[0][0], kPB + 1, &U[0][tid], kInCols + 1);
+  __syncthreads();
+  if (s_last)
+    for (int t = tid; t < kPB * N; t += 256) LU[(size_t)(j + t / N) * n + c0 + t % N] = U[t / N][t % N];
+  // A22 -= L21 U12: twelve independent chains per thread, each over q in order
+#pragma unroll 4
+  for (int q = 0; q < kPB; ++q) {
+    float uq[3], pq[4];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) uq[u] = U[q][lane + 32 * u];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pq[i] = P[w + 8 * i][q];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int u = 0; u < 3; ++u) acc[i * 3 + u] = fmaf(-pq[i], uq[u], acc[i * 3 + u]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int r = w + 8 * i, c = lane + 32 * u;
+      if (r < nr && c < N) LU[(size_t)(rb + r) * n + c0 + c] = acc[i * 3 + u];
+    }
+}
+
+// Rows [K, K + KB) of columns [c0, c1) := L11^-1 (them), L11 the unit lower
+// triangle of the KB x KB diagonal block at (K, K) (KB a multiple of 32, at
+// most kLuOuter).  One CTA per 32 columns with L11 and its strip in shared
+// memory; by 32-row blocks: the diagonal block solved one thread per column,
+// then the rows below it updated by all threads.
+__global__ void __launch_bounds__(256) k_lu_trsm_outer(float* LU, int n, int K, int KB, int c0,
+                                                       int c1) {
+  extern __shared__ float sm_t[];
+  const int ls = KB + 1;
+  float* L = sm_t;               // KB x (KB + 1)
+  float* X = sm_t + KB * ls;     // KB x 33
+  const int tid = threadIdx.x;
+  const int cb = c0 + blockIdx.x * kPB;
+  const int nc = min(kPB, c1 - cb);
+  const int lane = tid & 31, w = tid >> 5;
+  // staging, eight loads in flight per thread before their shared stores:
+  // warp w takes rows w, w + 8, ...; lane the column (of L11: lane + 32 u)
+  for (int r0 = 0; r0 < KB; r0 += 32) {
+    float v[4][4], x[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + w + 8 * i;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = lane + 32 * u;
+        v[i][u] = (c < r) ? __ldg(LU + (size_t)(K + r) * n + K + c) : 0.0f;
+      }
+      x[i] = lane < nc ? __ldg(LU + (size_t)(K + r) * n + cb + lane) : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + w + 8 * i;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (lane + 32 * u < KB) L[r * ls + lane + 32 * u] = v[i][u];
+      X[r * 33 + lane] = x[i];
+    }
+  }
+  __syncthreads();
+  for (int b = 0; b < KB; b += kPB) {
+    if (tid < kPB) unit_lower_solve_col(L + b * ls + b, ls, X + b * 33 + tid, 33);
+    __syncthreads();
+    // rows below: warp w takes rows b + 32 + w + 8 i, lane the column;
+    // independent chains over q in order
+    const int below = KB - b - kPB;
+    float acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      const int r = b + kPB + w + 8 * i;
+      acc[i] = (w + 8 * i < below) ? X[r * 33 + lane] : 0.0f;
+    }
+#pragma unroll 4
+    for (int q = 0; q < kPB; ++q) {
+      const float xq = X[(b + q) * 33 + lane];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) {
+        const int r = b + kPB + w + 8 * i;
+        if (w + 8 * i < below) acc[i] = fmaf(-L[r * ls + b + q], xq, acc[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      const int r = b + kPB + w + 8 * i;
+      if (w + 8 * i < below) X[r * 33 + lane] = acc[i];
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < KB * kPB; t += 256) {
+    const int r = t >> 5, c = t & 31;
+    if (c < nc) LU[(size_t)(K + r) * n + cb + c] = X[r * 33 + c];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -510,47 +715,111 @@ __global__ void k_update(double* x, const float* __restrict__ d, const double* _
   }
 }
 
+template <int PC>
 size_t panel_smem(int n, int k) {
   const int m = n - k;
-  const int rs = (m + kPC - 1) / kPC;
-  return (size_t)rs * kStride * 4 + 16 + 2 * kPC * 8 + 2 * 8 + 2 * 8 + 2 * kPC * kPB * 4 + 64;
+  const int rs = (m + PC - 1) / PC;
+  return (size_t)rs * kStride * 4 + 16 + 2 * PC * 8 + 2 * 8 + 2 * 8 + 2 * PC * kPB * 4 +
+         2 * kPB * kXCols * 4 + 64;
+}
+
+template <int PC>
+cudaError_t launch_panel(float* LU, int n, int k, int jb, int* piv, int* info, int* moves,
+                         int c_lo, int c_hi, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(PC);
+  cfg.blockDim = dim3(kPT);
+  cfg.dynamicSmemBytes = panel_smem<PC>(n, k);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = PC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_lu_panel<PC>, LU, n, k, jb, piv, info, moves, c_lo, c_hi);
+}
+
+// 16 when one cluster of 16 CTAs with the largest panel fits the device
+bool use_cluster16() {
+  static int v = -1;
+  if (v < 0) {
+    v = 0;
+    if (cudaFuncSetAttribute(k_lu_panel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_lu_panel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)panel_smem<16>(kLuMaxN, 0)) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(kPT);
+      cfg.dynamicSmemBytes = panel_smem<16>(kLuMaxN, 0);
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 16;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, k_lu_panel<16>, &cfg) == cudaSuccess &&
+          clusters >= 1)
+        v = 1;
+    }
+    cudaGetLastError();
+  }
+  return v == 1;
 }
 
 }  // namespace
 
-size_t lu_panel_max_smem(int n) { return panel_smem(n, 0); }
+size_t lu_panel_max_smem(int n) { return panel_smem<8>(n, 0); }
+
+cudaError_t lu_prepare(int n) {
+  const bool c16 = use_cluster16();
+  const size_t ps = c16 ? panel_smem<16>(n, 0) : panel_smem<8>(n, 0);
+  cudaError_t e = c16 ? cudaFuncSetAttribute(k_lu_panel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps)
+                      : cudaFuncSetAttribute(k_lu_panel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+  if (e != cudaSuccess) return e;
+  const size_t mx = ((size_t)kLuOuter * (kLuOuter + 1) + (size_t)kLuOuter * 33) * sizeof(float);
+  return cudaFuncSetAttribute(k_lu_trsm_outer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+}
 
 cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info, int* moves,
-                            cudaStream_t s, Prof* prof) {
-  const size_t sm = panel_smem(n, k);
-  static size_t attr = 0;
-  if (sm > attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)panel_smem(n, 0));
-    if (e != cudaSuccess) return e;
-    attr = panel_smem(n, 0);
-  }
+                            int c_lo, int c_hi, cudaStream_t s, Prof* prof) {
   prof_begin(prof, "lu_panel", s);
-  k_lu_panel<<<kPC, kPT, sm, s>>>(LU, n, k, jb, piv, info, moves);
+  const cudaError_t e =
+      use_cluster16() ? launch_panel<16>(LU, n, k, jb, piv, info, moves, c_lo, c_hi, s)
+                      : launch_panel<8>(LU, n, k, jb, piv, info, moves, c_lo, c_hi, s);
   prof_end(prof, s);
-  return cudaGetLastError();
+  return e;
 }
 
-cudaError_t launch_lu_laswp(float* LU, int n, int k, int jb, const int* moves, cudaStream_t s,
-                            Prof* prof) {
+cudaError_t launch_lu_laswp_outer(float* LU, int n, const int* moves, int nlists, int K, int KB,
+                                  cudaStream_t s, Prof* prof) {
+  const int cols = n - KB;
+  if (cols <= 0) return cudaSuccess;
   prof_begin(prof, "lu_laswp", s);
-  if (k > 0) k_lu_laswp<<<(k + 127) / 128, 128, 0, s>>>(LU, n, moves, 0, k);
-  const int rest = n - k - jb;
-  if (rest > 0) k_lu_laswp<<<(rest + 127) / 128, 128, 0, s>>>(LU, n, moves, k + jb, n);
+  k_lu_laswp_outer<<<(cols + 127) / 128, 128, 0, s>>>(LU, n, moves, nlists, K, KB);
   prof_end(prof, s);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1, cudaStream_t s,
-                           Prof* prof) {
+cudaError_t launch_lu_inner(float* LU, int n, int j, int c0, int c1, unsigned* counter,
+                            cudaStream_t s, Prof* prof) {
+  if (c1 <= c0 || n - j - kPB <= 0) return cudaSuccess;
+  prof_begin(prof, "lu_inner", s);
+  k_lu_inner<<<(n - j - kPB + kInRows - 1) / kInRows, 256, 0, s>>>(LU, n, j, c0, c1, counter);
+  prof_end(prof, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_trsm_outer(float* LU, int n, int K, int KB, int c0, int c1, cudaStream_t s,
+                                 Prof* prof) {
   if (c1 <= c0) return cudaSuccess;
+  const size_t sm = ((size_t)KB * (KB + 1) + (size_t)KB * 33) * sizeof(float);
   prof_begin(prof, "lu_trsm", s);
-  k_lu_trsm<<<(c1 - c0 + 7) / 8, 256, 0, s>>>(LU, n, k, jb, c0, c1);
+  k_lu_trsm_outer<<<(c1 - c0 + kPB - 1) / kPB, 256, sm, s>>>(LU, n, K, KB, c0, c1);
   prof_end(prof, s);
   return cudaGetLastError();
 }

@@ -9,18 +9,29 @@ constexpr int kLuOuter = 128;     // outer block: one tensor-core update per 128
 constexpr int kLuMaxN = 9216;     // the panel must fit the cluster's shared memory
 
 size_t lu_panel_max_smem(int n);
+// kernel attributes (shared-memory sizes, the panel's cluster size) for
+// factorisations up to n; called before a factorisation is captured
+cudaError_t lu_prepare(int n);
 // moves: the panel's slot of kLuMoveInts ints, zero before the call; the
 // kernel lists there the rows its interchanges moved (count, sources,
-// destinations) for launch_lu_laswp.
+// destinations) and applies them itself to the columns [c_lo, c_hi) of its
+// outer block outside the panel.
 constexpr int kLuMoveInts = 1 + 4 * kLuPanel;
 cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info, int* moves,
+                            int c_lo, int c_hi, cudaStream_t s, Prof* prof);
+// the interchanges of the nlists panels of the outer block [K, K + KB) (their
+// moves slots, consecutive) on every column outside it
+cudaError_t launch_lu_laswp_outer(float* LU, int n, const int* moves, int nlists, int K, int KB,
+                                  cudaStream_t s, Prof* prof);
+// after the panel at j (32 columns) inside an outer block: rows j..j+32 of
+// columns [c0, c1) := L11^-1 (them), then rows j+32..n of those columns -=
+// L21 U12.  counter: one zero word per call.
+cudaError_t launch_lu_inner(float* LU, int n, int j, int c0, int c1, unsigned* counter,
                             cudaStream_t s, Prof* prof);
-// the panel's interchanges on every column outside the panel
-cudaError_t launch_lu_laswp(float* LU, int n, int k, int jb, const int* moves, cudaStream_t s,
-                            Prof* prof);
-// rows k..k+jb of columns [c0, c1) := L11^-1 (them), L11 = unit lower at (k, k)
-cudaError_t launch_lu_trsm(float* LU, int n, int k, int jb, int c0, int c1, cudaStream_t s,
-                           Prof* prof);
+// rows K..K+KB of columns [c0, c1) := L11^-1 (them), L11 = the unit lower
+// triangle at (K, K); KB a multiple of 32, at most kLuOuter
+cudaError_t launch_lu_trsm_outer(float* LU, int n, int K, int KB, int c0, int c1, cudaStream_t s,
+                                 Prof* prof);
 // perm[i] = the row of A that the interchanges piv[0..n) moved to row i
 // (dynamic shared memory of n ints: n <= kLuMaxN)
 cudaError_t launch_lu_perm(const int* piv, int n, int* perm, cudaStream_t s);

@@ -56,49 +56,48 @@ struct SolveWork {
 // gemm: tensor-core scratch (gemm_tc_scratch_bytes(n, n, kLuOuter)),
 // unused for binary32 updates.
 cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* info, int* moves,
-                            void* gemm, sg_precision prec, cudaStream_t s, sgk::Prof* prof) {
+                            unsigned* counters, void* gemm, sg_precision prec, cudaStream_t s,
+                            sgk::Prof* prof) {
   cudaError_t e = cudaSuccess;
-  // two levels: 32-column panels inside 128-column outer blocks; inside an
-  // outer block only its own columns are updated (binary32 SIMT, narrow);
-  // the trailing matrix is updated once per outer block with K = 128
+  // two levels: 32-column panels inside 128-column outer blocks.  Inside an
+  // outer block each panel applies its interchanges to the block's other
+  // columns and one fused kernel updates the block's columns to its right;
+  // per outer block one launch applies its interchanges everywhere else, one
+  // solves U12 for its 128 rows, and the trailing matrix is updated with
+  // K = 128 (tensor cores, or binary32 SIMT)
   const bool tc = prec != SG_PREC_F32_SIMT;
-  auto gemm_sub = [&](float* a_, float* b_, float* c_, int M, int N, int K, bool big) {
-    if (M <= 0 || N <= 0 || K <= 0 || e != cudaSuccess) return;
-    if (big && tc) {
-      e = sgk::launch_gemm_tc(a_, n, b_, n, c_, n, M, N, K, prec == SG_PREC_F16_TC, true,
-                              gemm, s, prof, &c->kernels);
-    } else {
-      e = sgk::launch_gemm_f32(a_, n, b_, n, c_, n, M, N, K, true, s, prof);
-      c->kernels += 1;
-    }
-  };
   auto at = [&](int r, int col) { return lu + (size_t)r * n + col; };
   for (int K = 0; K < n && e == cudaSuccess; K += sgk::kLuOuter) {
     const int KB = std::min(sgk::kLuOuter, n - K);
-    for (int j = K; j < K + KB && e == cudaSuccess; j += sgk::kLuPanel) {
+    int* mv0 = moves + (size_t)(K / sgk::kLuPanel) * sgk::kLuMoveInts;
+    int np = 0;
+    for (int j = K; j < K + KB && e == cudaSuccess; j += sgk::kLuPanel, ++np) {
       const int jb = std::min(sgk::kLuPanel, K + KB - j);
       int* mv = moves + (size_t)(j / sgk::kLuPanel) * sgk::kLuMoveInts;
-      e = sgk::launch_lu_panel(lu, n, j, jb, piv, info, mv, s, prof);
-      if (e == cudaSuccess) e = sgk::launch_lu_laswp(lu, n, j, jb, mv, s, prof);
-      c->kernels += 3;
-      const int right = K + KB - (j + jb);   // columns of this outer block to the right
-      if (right > 0 && e == cudaSuccess) {
-        e = sgk::launch_lu_trsm(lu, n, j, jb, j + jb, K + KB, s, prof);
+      e = sgk::launch_lu_panel(lu, n, j, jb, piv, info, mv, K, K + KB, s, prof);
+      c->kernels += 1;
+      if (e == cudaSuccess && j + jb < K + KB) {
+        e = sgk::launch_lu_inner(lu, n, j, j + jb, K + KB, counters + j / sgk::kLuPanel, s, prof);
         c->kernels += 1;
-        gemm_sub(at(j + jb, j), at(j, j + jb), at(j + jb, j + jb), n - j - jb, right, jb, false);
       }
+    }
+    if (e == cudaSuccess) {
+      e = sgk::launch_lu_laswp_outer(lu, n, mv0, np, K, KB, s, prof);
+      if (n > KB) c->kernels += 1;
     }
     const int rest = n - K - KB;
     if (rest > 0 && e == cudaSuccess) {
-      // U12 = L11^-1 A12 for the outer block, 32 rows at a time
-      for (int i = 0; i < KB && e == cudaSuccess; i += sgk::kLuPanel) {
-        const int ib = std::min(sgk::kLuPanel, KB - i);
-        e = sgk::launch_lu_trsm(lu, n, K + i, ib, K + KB, n, s, prof);
+      e = sgk::launch_lu_trsm_outer(lu, n, K, KB, K + KB, n, s, prof);
+      c->kernels += 1;
+      if (e == cudaSuccess && tc) {
+        e = sgk::launch_gemm_tc(at(K + KB, K), n, at(K, K + KB), n, at(K + KB, K + KB), n, rest,
+                                rest, KB, prec == SG_PREC_F16_TC, true, gemm, s, prof,
+                                &c->kernels);
+      } else if (e == cudaSuccess) {
+        e = sgk::launch_gemm_f32(at(K + KB, K), n, at(K, K + KB), n, at(K + KB, K + KB), n, rest,
+                                 rest, KB, true, s, prof);
         c->kernels += 1;
-        gemm_sub(at(K + i + ib, K + i), at(K + i, K + KB), at(K + i + ib, K + KB), KB - i - ib, rest,
-                 ib, false);
       }
-      gemm_sub(at(K + KB, K), at(K, K + KB), at(K + KB, K + KB), rest, rest, KB, true);
     }
   }
   return e;
@@ -125,7 +124,7 @@ sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
     const size_t o_piv = take((size_t)n * 4);
     const size_t o_perm = take((size_t)n * 4);
     const size_t o_info = take(64);
-    const size_t o_moves = take((size_t)np * sgk::kLuMoveInts * 4);
+    const size_t o_moves = take((size_t)np * sgk::kLuMoveInts * 4 + (size_t)np * 4);
     const size_t o_gemm =
         take((prec == SG_PREC_F32_SIMT ? 0 : sgk::gemm_tc_scratch_bytes(n, n, sgk::kLuOuter)) + 256);
     if (cudaMalloc(&L.base, off) != cudaSuccess ||
@@ -142,12 +141,16 @@ sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
     int* moves = reinterpret_cast<int*>(base + o_moves);
     const int64_t k0 = c->kernels;
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(L.cap, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = sgk::lu_prepare(n);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(L.cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaError_t le = cudaMemsetAsync(L.info, 0, 64, L.cap);
-      if (le == cudaSuccess) le = cudaMemsetAsync(moves, 0, (size_t)np * sgk::kLuMoveInts * 4, L.cap);
       if (le == cudaSuccess)
-        le = factor_in_place(c, L.lu, n, L.piv, L.info, moves, base + o_gemm, prec, L.cap, nullptr);
+        le = cudaMemsetAsync(moves, 0, (size_t)np * sgk::kLuMoveInts * 4 + (size_t)np * 4, L.cap);
+      if (le == cudaSuccess)
+        le = factor_in_place(c, L.lu, n, L.piv, L.info, moves,
+                             reinterpret_cast<unsigned*>(moves + (size_t)np * sgk::kLuMoveInts),
+                             base + o_gemm, prec, L.cap, nullptr);
       if (le == cudaSuccess) le = sgk::launch_lu_perm(L.piv, n, L.perm, L.cap);
       e = cudaStreamEndCapture(L.cap, &g);
       if (e == cudaSuccess) e = le;
