@@ -28,7 +28,9 @@
 //                  SIMT form.
 // Solve: pivots on the right-hand side, then forward / backward substitution
 // by blocks of 32 rows in one launch each: CTAs take row blocks in order
-// (ticket) and wait, with a bounded spin, for the blocks they depend on.
+// (ticket) and wait, with a bounded spin, for the blocks they depend on; the
+// diagonal blocks are applied through their inverses (formed once per
+// factorisation), one short product instead of 32 dependent steps.
 // Refinement: residual r = b - A x in binary64 from the binary32 A, and the
 // update x += d with the norms the stopping test needs.
 #include <cooperative_groups.h>
@@ -275,10 +277,11 @@ __global__ void __launch_bounds__(kPT)
 }
 
 // The interchanges of an outer block's panels (moves lists m0, m0 + 1, ...,
-// in order) on the columns outside it, [0, K) and [K + KB, n): one thread
-// per column; for each list every load of the column precedes its stores.
+// in order) on the columns outside it, [0, K) and [K + KB, n), and on the
+// row permutation perm: one thread per column; for each list every load of
+// the column precedes its stores.
 __global__ void __launch_bounds__(128) k_lu_laswp_outer(float* LU, int n, const int* __restrict__ moves,
-                                                        int nlists, int K, int KB) {
+                                                        int nlists, int K, int KB, int* perm) {
   __shared__ int s_cnt[kLuOuter / kPB], s_src[kLuOuter / kPB][2 * kPB],
       s_dst[kLuOuter / kPB][2 * kPB];
   for (int q = 0; q < nlists; ++q) {
@@ -292,6 +295,20 @@ __global__ void __launch_bounds__(128) k_lu_laswp_outer(float* LU, int n, const 
   }
   __syncthreads();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g == n - KB) {
+    // one more column: the row permutation itself
+    for (int q = 0; q < nlists; ++q) {
+      const int cnt = s_cnt[q];
+      int v[2 * kPB];
+#pragma unroll
+      for (int t = 0; t < 2 * kPB; ++t)
+        if (t < cnt) v[t] = perm[s_src[q][t]];
+#pragma unroll
+      for (int t = 0; t < 2 * kPB; ++t)
+        if (t < cnt) perm[s_dst[q][t]] = v[t];
+    }
+    return;
+  }
   const int c = g < K ? g : g + KB;
   if (c >= n) return;
   for (int q = 0; q < nlists; ++q) {
@@ -485,24 +502,9 @@ __global__ void __launch_bounds__(256) k_lu_trsm_outer(float* LU, int n, int K, 
 // ---------------------------------------------------------------------------
 // solve
 
-// perm[i] = the row of A that elimination moved to row i: the interchanges
-// piv[0..n) applied in order to the identity, in shared memory by one thread
-// (once per factorisation)
-__global__ void __launch_bounds__(1024) k_lu_perm(const int* __restrict__ piv, int n, int* perm) {
-  extern __shared__ int s_perm[];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s_perm[i] = i;
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int j = 0; j < n; ++j) {
-      const int p = piv[j];
-      if (p != j) {
-        const int t = s_perm[j];
-        s_perm[j] = s_perm[p];
-        s_perm[p] = t;
-      }
-    }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = s_perm[i];
+// perm[i] = i (the interchanges are then applied to it like a column)
+__global__ void k_lu_iota(int* perm, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) perm[i] = i;
 }
 
 // y = P rhs (binary64 in, binary32 out): y[i] = rhs[perm[i]]
@@ -510,6 +512,48 @@ __global__ void k_apply_perm(const double* __restrict__ rhs, float* y, int n,
                              const int* __restrict__ perm) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     y[i] = (float)rhs[perm[i]];
+}
+
+// Inverses of the 32x32 diagonal blocks of L (unit lower) and U (upper),
+// once per factorisation, for the blocked substitutions: inv[0][b] = L_bb^-1,
+// inv[1][b] = U_bb^-1, row-major; a block cut by n is padded with the
+// identity.  One CTA per block: thread j < 32 forms column j of L_bb^-1 by
+// forward substitution, thread 32 + j column j of U_bb^-1 by back
+// substitution, both in registers.
+__global__ void __launch_bounds__(64) k_lu_diag_inv(const float* __restrict__ LU, int n,
+                                                    float* __restrict__ inv) {
+  __shared__ float D[32][33];
+  const int b = blockIdx.x, row0 = b * 32, tid = threadIdx.x;
+  for (int t = tid; t < 1024; t += 64) {
+    const int r = t >> 5, c = t & 31;
+    D[r][c] = (row0 + r < n && row0 + c < n) ? LU[(size_t)(row0 + r) * n + row0 + c]
+                                             : (r == c ? 1.0f : 0.0f);
+  }
+  __syncthreads();
+  const int nb = gridDim.x;
+  const int j = tid & 31;
+  float x[32];
+  if (tid < 32) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      float acc = i == j ? 1.0f : 0.0f;
+#pragma unroll
+      for (int q = 0; q < i; ++q) acc = fmaf(-D[i][q], x[q], acc);
+      x[i] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) inv[((size_t)b * 32 + i) * 32 + j] = x[i];
+  } else {
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+      float acc = i == j ? 1.0f : 0.0f;
+#pragma unroll
+      for (int q = i + 1; q < 32; ++q) acc = fmaf(-D[i][q], x[q], acc);
+      x[i] = acc / D[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) inv[((size_t)(nb + b) * 32 + i) * 32 + j] = x[i];
+  }
 }
 
 // Triangular solve by 32-row blocks.  LOWER: unit lower L, blocks in
@@ -520,7 +564,8 @@ __global__ void k_apply_perm(const double* __restrict__ rhs, float* y, int n,
 // lane.  Warp 0 then solves the diagonal block (held in registers from the
 // start) and publishes the flag with a release store.
 template <bool LOWER>
-__global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int n, float* y,
+__global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
+                                              const float* __restrict__ inv, int n, float* y,
                                               unsigned* flags, unsigned epoch, unsigned* ticket,
                                               int* err) {
   __shared__ unsigned s_b;
@@ -537,11 +582,12 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int 
   const float* lrow = LU + (size_t)min(row, n - 1) * n;
   float acc = 0.0f;
   const int ndep = LOWER ? b : nb - 1 - b;
-  // warp 0 keeps its diagonal block's row in registers for the final solve
+  // warp 0 keeps its row of the diagonal block's inverse in registers
   float dg[32];
   if (w == 0) {
+    const float* irow = inv + ((size_t)b * 32 + lane) * 32;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) dg[j] = (row < n && row0 + j < n) ? lrow[row0 + j] : 0.0f;
+    for (int j = 0; j < 32; ++j) dg[j] = irow[j];
   }
   for (int q = w; q < ndep; q += 8) {
     const int c = LOWER ? q : nb - 1 - q;
@@ -560,7 +606,7 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int 
           atomicExch(err, 1);
           break;
         }
-        if (spins > 64) __nanosleep(100);
+        if (spins > 4096) __nanosleep(32);
       }
     }
     __syncwarp();
@@ -578,26 +624,11 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU, int 
       for (int k = 0; k < 8; ++k) sacc += part[k][lane];
       v = __ldcg(&y[row0 + lane]) - sacc;
     }
-    if (LOWER) {
+    // v := (diagonal block)^-1 v, one row of the product per lane
+    float x = 0.0f;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float yi = __shfl_sync(0xffffffffu, v, i);
-        if (lane > i && lane < rows) v = fmaf(-dg[i], yi, v);
-      }
-    } else {
-      // my row's diagonal entry is dg[lane]: select it without dynamic indexing
-      float dii = 1.0f;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) dii = lane == j && lane < rows ? dg[j] : dii;
-#pragma unroll
-      for (int i = 31; i >= 0; --i) {
-        if (i < rows) {
-          if (lane == i) v = v / dii;
-          const float vi = __shfl_sync(0xffffffffu, v, i);
-          if (lane < i) v = fmaf(-dg[i], vi, v);
-        }
-      }
-    }
+    for (int i = 0; i < 32; ++i) x = fmaf(dg[i], __shfl_sync(0xffffffffu, v, i), x);
+    v = x;
     if (lane < rows) y[row0 + lane] = v;
     __threadfence();
     __syncwarp();
@@ -796,11 +827,10 @@ cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info
 }
 
 cudaError_t launch_lu_laswp_outer(float* LU, int n, const int* moves, int nlists, int K, int KB,
-                                  cudaStream_t s, Prof* prof) {
-  const int cols = n - KB;
-  if (cols <= 0) return cudaSuccess;
+                                  int* perm, cudaStream_t s, Prof* prof) {
+  const int cols = n - KB + 1;   // and the permutation
   prof_begin(prof, "lu_laswp", s);
-  k_lu_laswp_outer<<<(cols + 127) / 128, 128, 0, s>>>(LU, n, moves, nlists, K, KB);
+  k_lu_laswp_outer<<<(cols + 127) / 128, 128, 0, s>>>(LU, n, moves, nlists, K, KB, perm);
   prof_end(prof, s);
   return cudaGetLastError();
 }
@@ -824,22 +854,30 @@ cudaError_t launch_lu_trsm_outer(float* LU, int n, int K, int KB, int c0, int c1
   return cudaGetLastError();
 }
 
-cudaError_t launch_lu_perm(const int* piv, int n, int* perm, cudaStream_t s) {
+cudaError_t launch_lu_iota(int* perm, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_lu_perm<<<1, 1024, (size_t)n * sizeof(int), s>>>(piv, n, perm);
+  k_lu_iota<<<(n + 255) / 256 < 256 ? (n + 255) / 256 : 256, 256, 0, s>>>(perm, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lu_solve(const float* LU, int n, const int* perm, const double* rhs,
-                            bool rhs_is_residual, float* y, unsigned* flags, unsigned epoch,
-                            unsigned* tickets, int* err, cudaStream_t s, Prof* prof) {
+cudaError_t launch_lu_diag_inv(const float* LU, int n, float* inv, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_lu_diag_inv<<<(n + 31) / 32, 64, 0, s>>>(LU, n, inv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_solve(const float* LU, const float* inv, int n, const int* perm,
+                            const double* rhs, bool rhs_is_residual, float* y, unsigned* flags,
+                            unsigned epoch, unsigned* tickets, int* err, cudaStream_t s,
+                            Prof* prof) {
   (void)rhs_is_residual;
   const int nb = (n + 31) / 32;
   prof_begin(prof, "lu_trsv", s);
   k_apply_perm<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(rhs, y, n, perm);
   cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s);
-  k_trsv<true><<<nb, 256, 0, s>>>(LU, n, y, flags, epoch, tickets, err);
-  k_trsv<false><<<nb, 256, 0, s>>>(LU, n, y, flags + nb, epoch, tickets + 1, err);
+  k_trsv<true><<<nb, 256, 0, s>>>(LU, inv, n, y, flags, epoch, tickets, err);
+  k_trsv<false><<<nb, 256, 0, s>>>(LU, inv + (size_t)nb * 1024, n, y, flags + nb, epoch,
+                                   tickets + 1, err);
   prof_end(prof, s);
   return cudaGetLastError();
 }

@@ -20,9 +20,9 @@ constexpr int kLuMoveInts = 1 + 4 * kLuPanel;
 cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info, int* moves,
                             int c_lo, int c_hi, cudaStream_t s, Prof* prof);
 // the interchanges of the nlists panels of the outer block [K, K + KB) (their
-// moves slots, consecutive) on every column outside it
+// moves slots, consecutive) on every column outside it and on perm
 cudaError_t launch_lu_laswp_outer(float* LU, int n, const int* moves, int nlists, int K, int KB,
-                                  cudaStream_t s, Prof* prof);
+                                  int* perm, cudaStream_t s, Prof* prof);
 // after the panel at j (32 columns) inside an outer block: rows j..j+32 of
 // columns [c0, c1) := L11^-1 (them), then rows j+32..n of those columns -=
 // L21 U12.  counter: one zero word per call.
@@ -32,14 +32,18 @@ cudaError_t launch_lu_inner(float* LU, int n, int j, int c0, int c1, unsigned* c
 // triangle at (K, K); KB a multiple of 32, at most kLuOuter
 cudaError_t launch_lu_trsm_outer(float* LU, int n, int K, int KB, int c0, int c1, cudaStream_t s,
                                  Prof* prof);
-// perm[i] = the row of A that the interchanges piv[0..n) moved to row i
-// (dynamic shared memory of n ints: n <= kLuMaxN)
-cudaError_t launch_lu_perm(const int* piv, int n, int* perm, cudaStream_t s);
+// perm[i] = i; the outer blocks' interchange launches then turn it into
+// perm[i] = the row of A that elimination moved to row i
+cudaError_t launch_lu_iota(int* perm, int n, cudaStream_t s);
 // y = U^-1 L^-1 P rhs in binary32 (P rhs gathered through perm).
 // flags: 2*ceil(n/32) words that never hold `epoch` before the call.
-cudaError_t launch_lu_solve(const float* LU, int n, const int* perm, const double* rhs,
-                            bool rhs_is_residual, float* y, unsigned* flags, unsigned epoch,
-                            unsigned* tickets, int* err, cudaStream_t s, Prof* prof);
+cudaError_t launch_lu_solve(const float* LU, const float* inv, int n, const int* perm,
+                            const double* rhs, bool rhs_is_residual, float* y, unsigned* flags,
+                            unsigned epoch, unsigned* tickets, int* err, cudaStream_t s,
+                            Prof* prof);
+// inv: 2 * ceil(n/32) blocks of 32x32 floats: the inverses of the diagonal
+// blocks of L (unit lower) then of U, row-major, for launch_lu_solve
+cudaError_t launch_lu_diag_inv(const float* LU, int n, float* inv, cudaStream_t s);
 // r = b - A x in binary64; norms[0] = max|r|; rows with |r_i| > thresh
 // (or NaN) raise ~i into *viol (when viol is not null).
 cudaError_t launch_residual(const float* A, int n, const double* b, const double* x, double* r,

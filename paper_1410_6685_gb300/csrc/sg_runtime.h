@@ -138,6 +138,7 @@ struct LuCache {
   float* lu = nullptr;
   int* piv = nullptr;
   int* perm = nullptr;          // row i of the factors is row perm[i] of A
+  float* inv = nullptr;         // inverses of the factors' 32x32 diagonal blocks
   int* info = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;

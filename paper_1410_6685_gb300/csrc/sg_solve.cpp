@@ -55,9 +55,9 @@ struct SolveWork {
 // pivot.  moves: ceil(n / kLuPanel) * kLuMoveInts ints, zero on entry.
 // gemm: tensor-core scratch (gemm_tc_scratch_bytes(n, n, kLuOuter)),
 // unused for binary32 updates.
-cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* info, int* moves,
-                            unsigned* counters, void* gemm, sg_precision prec, cudaStream_t s,
-                            sgk::Prof* prof) {
+cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* perm, int* info,
+                            int* moves, unsigned* counters, void* gemm, sg_precision prec,
+                            cudaStream_t s, sgk::Prof* prof) {
   cudaError_t e = cudaSuccess;
   // two levels: 32-column panels inside 128-column outer blocks.  Inside an
   // outer block each panel applies its interchanges to the block's other
@@ -82,8 +82,8 @@ cudaError_t factor_in_place(sg_ctx* c, float* lu, int n, int* piv, int* info, in
       }
     }
     if (e == cudaSuccess) {
-      e = sgk::launch_lu_laswp_outer(lu, n, mv0, np, K, KB, s, prof);
-      if (n > KB) c->kernels += 1;
+      e = sgk::launch_lu_laswp_outer(lu, n, mv0, np, K, KB, perm, s, prof);
+      c->kernels += 1;
     }
     const int rest = n - K - KB;
     if (rest > 0 && e == cudaSuccess) {
@@ -123,6 +123,7 @@ sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
     const size_t o_lu = take((size_t)n * n * 4);
     const size_t o_piv = take((size_t)n * 4);
     const size_t o_perm = take((size_t)n * 4);
+    const size_t o_inv = take((size_t)2 * ((n + 31) / 32) * 1024 * 4);
     const size_t o_info = take(64);
     const size_t o_moves = take((size_t)np * sgk::kLuMoveInts * 4 + (size_t)np * 4);
     const size_t o_gemm =
@@ -137,6 +138,7 @@ sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
     L.lu = reinterpret_cast<float*>(base + o_lu);
     L.piv = reinterpret_cast<int*>(base + o_piv);
     L.perm = reinterpret_cast<int*>(base + o_perm);
+    L.inv = reinterpret_cast<float*>(base + o_inv);
     L.info = reinterpret_cast<int*>(base + o_info);
     int* moves = reinterpret_cast<int*>(base + o_moves);
     const int64_t k0 = c->kernels;
@@ -147,11 +149,13 @@ sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
       cudaError_t le = cudaMemsetAsync(L.info, 0, 64, L.cap);
       if (le == cudaSuccess)
         le = cudaMemsetAsync(moves, 0, (size_t)np * sgk::kLuMoveInts * 4 + (size_t)np * 4, L.cap);
+      if (le == cudaSuccess) le = sgk::launch_lu_iota(L.perm, n, L.cap);
       if (le == cudaSuccess)
-        le = factor_in_place(c, L.lu, n, L.piv, L.info, moves,
+        le = factor_in_place(c, L.lu, n, L.piv, L.perm, L.info, moves,
                              reinterpret_cast<unsigned*>(moves + (size_t)np * sgk::kLuMoveInts),
                              base + o_gemm, prec, L.cap, nullptr);
-      if (le == cudaSuccess) le = sgk::launch_lu_perm(L.piv, n, L.perm, L.cap);
+      if (le == cudaSuccess) le = sgk::launch_lu_diag_inv(L.lu, n, L.inv, L.cap);
+      if (le == cudaSuccess) c->kernels += 2;
       e = cudaStreamEndCapture(L.cap, &g);
       if (e == cudaSuccess) e = le;
     }
@@ -314,7 +318,7 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
   // 2. initial solve, 3. refinement
   bool converged = false;
   if (!status) {
-    e = sgk::launch_lu_solve(w.lu, n, c->lu.perm, bb, false, w.y, w.flags, ++epoch, w.tickets,
+    e = sgk::launch_lu_solve(w.lu, c->lu.inv, n, c->lu.perm, bb, false, w.y, w.flags, ++epoch, w.tickets,
                              w.dev_err, s, prof);
     if (e == cudaSuccess) e = sgk::launch_update(x, w.y, bb, n, true, w.norms, s);
     c->kernels += 4;
@@ -323,7 +327,7 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
       e = cudaMemsetAsync(w.norms, 0, 3 * 8, s);
       if (e == cudaSuccess) e = sgk::launch_residual(a, n, bb, x, w.r, w.norms, 0.0, nullptr, s, prof);
       if (e == cudaSuccess)
-        e = sgk::launch_lu_solve(w.lu, n, c->lu.perm, w.r, true, w.y, w.flags, ++epoch, w.tickets,
+        e = sgk::launch_lu_solve(w.lu, c->lu.inv, n, c->lu.perm, w.r, true, w.y, w.flags, ++epoch, w.tickets,
                                  w.dev_err, s, prof);
       if (e == cudaSuccess) e = sgk::launch_update(x, w.y, bb, n, false, w.norms, s);
       c->kernels += 5;
@@ -465,6 +469,7 @@ void LuCache::clear() {
   lu = nullptr;
   piv = nullptr;
   perm = nullptr;
+  inv = nullptr;
   info = nullptr;
   n = 0;
   prec = -1;
