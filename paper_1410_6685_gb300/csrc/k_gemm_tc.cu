@@ -458,19 +458,15 @@ __global__ void __launch_bounds__(256) k_cast_bt_frv(const float* __restrict__ B
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int q = 0; q < 5; ++q) acc[i][q] = 0.0f;
-#pragma unroll 1
-  for (int st = 0; st < kFrvStripeB / 64; ++st) {
-    const int n0 = blockIdx.x * kFrvStripeB + st * 64;
-    if (n0 >= N) break;   // the same for the whole CTA
+  // the next step's 8 x 64 block is loaded while this step's is used
+  auto load = [&](int n0, float* b0, float* b1) {
     const int nc = n0 + 2 * lane;
-    const float4 r0 = frv::ldvec(r4, nc, N), r1 = frv::ldvec(r4, nc + 1, N);
-    float b0[8], b1[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = k0 + w * 8 + i;
       b0[i] = 0.0f;
       b1[i] = 0.0f;
-      if (k < N) {
+      if (k < N && n0 < N) {
         const float* rp = B + (size_t)k * N;
         if (vec2 && nc + 1 < N) {
           const float2 v = __ldcs(reinterpret_cast<const float2*>(rp + nc));
@@ -482,6 +478,22 @@ __global__ void __launch_bounds__(256) k_cast_bt_frv(const float* __restrict__ B
         }
       }
     }
+  };
+  float nb0[8], nb1[8];
+  load(blockIdx.x * kFrvStripeB, nb0, nb1);
+#pragma unroll 1
+  for (int st = 0; st < kFrvStripeB / 64; ++st) {
+    const int n0 = blockIdx.x * kFrvStripeB + st * 64;
+    if (n0 >= N) break;   // the same for the whole CTA
+    const int nc = n0 + 2 * lane;
+    const float4 r0 = frv::ldvec(r4, nc, N), r1 = frv::ldvec(r4, nc + 1, N);
+    float b0[8], b1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      b0[i] = nb0[i];
+      b1[i] = nb1[i];
+    }
+    if (st + 1 < kFrvStripeB / 64) load(n0 + 64, nb0, nb1);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       acc[i][0] = fmaf(b1[i], r1.x, fmaf(b0[i], r0.x, acc[i][0]));
@@ -543,17 +555,25 @@ __global__ void __launch_bounds__(256, 2) k_cast_a_frv(const float* __restrict__
     vt[e] = frv::ldvec(t4, c0 + e, N);
   }
   const int slot = (lane >> 2) & 7;
-#pragma unroll 1
-  for (int it = 0; it < 4; ++it) {
-    const long long row0 = ((long long)blockIdx.y * 4 + it) * 8;
-    if (row0 >= N) break;
-    float4 av[8];
+  // the next step's eight rows are loaded while this step's are used
+  auto load8 = [&](long long row0, float4* av) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const long long row = row0 + i;
       av[i] = row < N ? frv::ldv(A + row * (long long)N, c0, N, vec)
                       : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+  };
+  float4 nxt[8];
+  load8((long long)blockIdx.y * 32, nxt);
+#pragma unroll 1
+  for (int it = 0; it < 4; ++it) {
+    const long long row0 = ((long long)blockIdx.y * 4 + it) * 8;
+    if (row0 >= N) break;
+    float4 av[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) av[i] = nxt[i];
+    if (it < 3) load8(row0 + 8, nxt);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const long long row = row0 + i;
