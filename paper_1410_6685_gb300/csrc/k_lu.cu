@@ -103,7 +103,7 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
 constexpr int kXCols = (kLuOuter - kPB + 7) / 8;
 
 // smem: slab[rs][33] floats, cand[2][PC] u64, best[2] u64, bar[2] u64,
-// crow[2][PC][32] floats, xbuf[64][kXCols] floats
+// crow[2][PC][32] floats, xbuf[64][kXCols] floats, fpos[rs] ints
 template <int PC>
 __global__ void __launch_bounds__(kPT)
     k_lu_panel(float* __restrict__ LU, int n, int k, int jb, int* __restrict__ piv,
@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(kPT)
   float* crow = reinterpret_cast<float*>(bar + 2);
   // xbuf[t][i]: moved row t of this CTA's i-th outer-block column
   float* xbuf = crow + 2 * PC * kPB;
+  // fpos[r]: final position of this CTA's row r (for the write-back)
+  int* fpos = reinterpret_cast<int*>(xbuf + 2 * kPB * kXCols);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
 
@@ -132,9 +134,20 @@ __global__ void __launch_bounds__(kPT)
   int lp[kRows];
 #pragma unroll
   for (int i = 0; i < kRows; ++i) lp[i] = r0 + tid + i * kPT;
-  for (int t = tid; t < (r1 - r0) * kPB; t += kPT) {
-    const int r = t / kPB, c = t % kPB;
-    slab[r * kStride + c] = c < jb ? LU[(size_t)(k + r0 + r) * n + k + c] : 0.0f;
+  // the slab, eight loads in flight per thread (a warp reads one row per load)
+  const int total = (r1 - r0) * kPB;
+  for (int base = 0; base < total; base += 8 * kPT) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = base + u * kPT + tid, r = t >> 5, c = t & 31;
+      v[u] = (t < total && c < jb) ? __ldg(LU + (size_t)(k + r0 + r) * n + k + c) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = base + u * kPT + tid;
+      if (t < total) slab[(t >> 5) * kStride + (t & 31)] = v[u];
+    }
   }
   if (tid < 2) {
     best[tid] = 0ull;
@@ -233,26 +246,34 @@ __global__ void __launch_bounds__(kPT)
     if (tid == 0 && rank == 0) piv[k + j] = k + p;
   }
   if (failed) atomicCAS(info, 0, -1);   // a wait gave up: report, write nothing
+  const bool any_failed = __syncthreads_or(failed);
   cluster.sync();   // no CTA reads another's shared memory after this
-  // write the panel back in its final row order, and list the rows that
-  // moved (at most 2 jb) for the other columns' interchange
+  // list the rows that moved (at most 2 jb) for the other columns'
+  // interchange; keep every row's final position for the write-back
+  if (!any_failed) {
 #pragma unroll
-  for (int i = 0; i < kRows; ++i) {
-    const int r = r0 + tid + i * kPT;
-    if (r >= r1 || failed) continue;
-    float* dst = LU + (size_t)(k + lp[i]) * n + k;
-    const float* row = slab + (r - r0) * kStride;
-    for (int c = 0; c < jb; ++c) dst[c] = row[c];
-    if (lp[i] != r) {
-      const int t = atomicAdd(&moves[0], 1);
-      if (t < 2 * kPB) {
-        moves[1 + t] = k + r;
-        moves[1 + 2 * kPB + t] = k + lp[i];
+    for (int i = 0; i < kRows; ++i) {
+      const int r = r0 + tid + i * kPT;
+      if (r >= r1) continue;
+      fpos[r - r0] = lp[i];
+      if (lp[i] != r) {
+        const int t = atomicAdd(&moves[0], 1);
+        if (t < 2 * kPB) {
+          moves[1 + t] = k + r;
+          moves[1 + 2 * kPB + t] = k + lp[i];
+        }
       }
     }
   }
+  __syncthreads();
+  // write the panel back in its final row order, one row per warp store
+  if (!any_failed) {
+    for (int t = tid; t < total; t += kPT) {
+      const int r = t >> 5, c = t & 31;
+      if (c < jb) LU[(size_t)(k + fpos[r]) * n + k + c] = slab[r * kStride + c];
+    }
+  }
   if (tid == 0 && rank == 0 && my_info) atomicCAS(info, 0, my_info);
-  const bool any_failed = __syncthreads_or(failed);
   cluster.sync();   // every CTA's moves are listed
   // the interchanges on the outer block's other columns [c_lo, k) and
   // [k + jb, c_hi) (at most kXCols * PC): CTA `rank` takes the columns
@@ -751,7 +772,7 @@ size_t panel_smem(int n, int k) {
   const int m = n - k;
   const int rs = (m + PC - 1) / PC;
   return (size_t)rs * kStride * 4 + 16 + 2 * PC * 8 + 2 * 8 + 2 * 8 + 2 * PC * kPB * 4 +
-         2 * kPB * kXCols * 4 + 64;
+         2 * kPB * kXCols * 4 + (size_t)rs * 4 + 64;
 }
 
 template <int PC>
