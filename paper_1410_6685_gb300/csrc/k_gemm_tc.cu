@@ -4,8 +4,10 @@
 // accumulation in tensor memory.
 //
 // Operands are first cast (and B transposed) into K-major 16-bit copies whose
-// K extent is padded to a multiple of 64.  Each CTA computes a 128 x 256 tile
-// of C with 128 threads:
+// K extent is padded to a multiple of 64.  The product runs on CTA pairs
+// (k_gemm_tc2, tcgen05 cta_group::2, 256 x 256 tiles, described there) where
+// the device schedules clusters of two, else on single CTAs (k_gemm_tc), each
+// computing a 128 x 256 tile of C:
 //   warp 0, one lane : TMA producer -- 2-D tiled bulk-tensor loads of a 128x64
 //                      A slice and a 256x64 B slice per stage (128-byte
 //                      swizzle, no multicast), completion on a "full" mbarrier;
@@ -371,6 +373,270 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUte
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same product on CTA pairs (a cluster of 2, tcgen05 cta_group::2): a pair
+// computes a 256 x 256 tile of C, each CTA holding 128 rows of the A slice
+// and 128 rows (half) of the B slice of every stage, so each CTA moves 32 KB
+// per 64-deep K step instead of 48 KB for a 128 x 256 tile of its own.
+//   warp 0, one lane, both CTAs : TMA producer of its CTA's halves; the loads
+//       complete on the leader CTA's "full" barrier (.cta_group::2), which
+//       expects both CTAs' bytes (each producer arrives with its own count);
+//   warp 1, one lane, leader    : MMA issuer, tcgen05.mma.cta_group::2
+//       (M = 256, N = 256, K = 16); commits multicast to both CTAs' "empty",
+//       "accumulator full" and "drain" barriers;
+//   warps 2..5, both CTAs       : epilogue of the CTA's 128 rows from its own
+//       tensor memory; they release an accumulator by arriving on the
+//       leader's "accumulator empty" barrier (eight arrivals, four remote).
+// Six stages of 32 KB.  Every mbarrier wait is bounded, as in k_gemm_tc.
+constexpr int TM2 = 256, TH = 128, STAGES2 = 6;
+constexpr int STAGE2_BYTES = TH * TK * 2 * 2;   // 128 A rows + 128 B rows
+constexpr int SMEM2_BYTES = STAGES2 * STAGE2_BYTES + 1024 + 256 + R_BYTES;
+
+__host__ __device__ constexpr uint32_t idesc2(bool fp16) {
+  return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) |
+         ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM2 >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+// arrive (with a byte count to expect) on a barrier anywhere in the cluster;
+// CTA-scope release: a cluster-scope one would wait for every earlier global
+// store of the thread
+__device__ __forceinline__ void mbar_expect_tx_cl(uint32_t bar_cl, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cluster.b64 _, [%0], %1;" ::"r"(bar_cl),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cl(uint32_t bar_cl) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar_cl) : "memory");
+}
+// TMA load into this CTA's shared memory completing on a barrier of either CTA of the pair
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x,
+                                                 int y, uint32_t bar_cl) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cl)
+      : "memory");
+}
+__device__ __forceinline__ void umma2(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id,
+                                      uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(id), "r"(accumulate)
+      : "memory");
+}
+// arrives once on the barrier at this offset in both CTAs of the pair when
+// every MMA issued before it has completed
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"((unsigned short)3)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1) k_gemm_tc2(const __grid_constant__ CUtensorMap ma,
+                                                     const __grid_constant__ CUtensorMap mb,
+                                                     float* __restrict__ C, int ldc, int M,
+                                                     int N, int KB, uint32_t id, int subtract,
+                                                     int* err, const float4* __restrict__ frv_r,
+                                                     float4* __restrict__ frv_pw, int inj_row,
+                                                     int inj_col, float inj_delta) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES2 * STAGE2_BYTES);
+  // bars[0..S): full (leader's count), [S..2S): empty, [2S, 2S+2): accumulator
+  // full, [2S+2, 2S+4): accumulator empty (leader's count), [2S+4]: drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES2 + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float4* s_r = reinterpret_cast<float4*>(smem + STAGES2 * STAGE2_BYTES + 256);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int nN = (N + TN - 1) / TN, nM = (M + TM2 - 1) / TM2;
+  const int ntiles = nN * nM;
+  const uint32_t tfull0 = smem_u32(&bars[2 * STAGES2]), tempty0 = smem_u32(&bars[2 * STAGES2 + 2]);
+  const uint32_t drain_bar = smem_u32(&bars[2 * STAGES2 + 4]);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES2; ++s) {
+      mbar_init(smem_u32(&bars[s]), 2);
+      mbar_init(smem_u32(&bars[STAGES2 + s]), 1);
+    }
+    mbar_init(tfull0, 1);
+    mbar_init(tfull0 + 8, 1);
+    mbar_init(tempty0, 8);
+    mbar_init(tempty0 + 8, 8);
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(2 * TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync();   // both CTAs' barriers exist, and the tensor memory, before use
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int t = pair; t < ntiles && ok; t += npairs) {
+        int bm, bn;
+        tile_coords(t, nM, nN, &bm, &bn);
+        const int m0 = bm * TM2 + (int)rank * TH, n0 = bn * TN + (int)rank * TH;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % STAGES2;
+          const uint32_t ph = (uint32_t)(it / STAGES2) & 1u;
+          if (it >= STAGES2 &&
+              !mbar_wait_ab(smem_u32(&bars[STAGES2 + s]), ph ^ 1u, err, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t full_cl = map_rank(smem_u32(&bars[s]), 0);
+          mbar_expect_tx_cl(full_cl, STAGE2_BYTES);
+          const uint32_t a_dst = smem_u32(smem + s * STAGE2_BYTES);
+          tma_load_2d_pair(a_dst, &ma, kb * TK, m0, full_cl);
+          tma_load_2d_pair(a_dst + TH * TK * 2, &mb, kb * TK, n0, full_cl);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      int it = 0, tl = 0;
+      bool ok = true;
+      for (int t = pair; t < ntiles && ok; t += npairs, ++tl) {
+        const int acc = tl & 1;
+        if (tl >= 2 && !mbar_wait_ab(tempty0 + 8 * acc, (uint32_t)((tl >> 1) - 1) & 1u, err,
+                                     abort_flag))
+          break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(acc * TN);
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % STAGES2;
+          const uint32_t ph = (uint32_t)(it / STAGES2) & 1u;
+          if (!mbar_wait_ab(smem_u32(&bars[s]), ph, err, abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_base = smem_u32(smem + s * STAGE2_BYTES);
+          const uint64_t da = sdesc(a_base), db = sdesc(a_base + TH * TK * 2);
+#pragma unroll
+          for (int k = 0; k < TK / 16; ++k)
+            umma2(dacc, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), id, (kb | k) != 0);
+          umma_commit_pair(smem_u32(&bars[STAGES2 + s]));
+        }
+        if (ok) umma_commit_pair(tfull0 + 8 * acc);
+      }
+      // completes, in both CTAs, when every MMA issued above has finished
+      umma_commit_pair(drain_bar);
+    }
+  } else {
+    const int q = warp & 3;
+    float4* s_rw = s_r + (warp - 2) * TN;
+    const uint32_t tempty_leader = map_rank(tempty0, 0);
+    int tl = 0;
+    for (int t = pair; t < ntiles; t += npairs, ++tl) {
+      int bm, bn;
+      tile_coords(t, nM, nN, &bm, &bn);
+      const int m0 = bm * TM2 + (int)rank * TH, n0 = bn * TN;
+      const int acc = tl & 1;
+      if (frv_r) {
+        __syncwarp();
+        for (int j = lane; j < TN; j += 32)
+          s_rw[j] = n0 + j < N ? frv_r[n0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+      }
+      if (!mbar_wait_ab(tfull0 + 8 * acc, (uint32_t)(tl >> 1) & 1u, err, abort_flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = m0 + q * 32 + lane;
+      float4 wacc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+      for (int c = 0; c < TN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TN + c * 32), r);
+        if (c == TN / 32 - 1) {
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cl(tempty_leader + 8 * acc);
+        }
+        const int col0 = n0 + c * 32;
+        if (row == inj_row && inj_col >= col0 && inj_col < col0 + 32) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j == inj_col) r[j] = __float_as_uint(__uint_as_float(r[j]) + inj_delta);
+        }
+        if (frv_r) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float4 rj = s_rw[c * 32 + j];
+            const float v = __uint_as_float(r[j]);
+            wacc.x = fmaf(v, rj.x, wacc.x);
+            wacc.y = fmaf(v, rj.y, wacc.y);
+            wacc.z = fmaf(v, rj.z, wacc.z);
+            wacc.w = fmaf(v, rj.w, wacc.w);
+          }
+        }
+        if (row < M) {
+          float* cp = C + (size_t)row * ldc + col0;
+          if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                     __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+              if (subtract) {
+                const float4 o = *reinterpret_cast<const float4*>(cp + j);
+                v = make_float4(o.x - v.x, o.y - v.y, o.z - v.z, o.w - v.w);
+              }
+              *reinterpret_cast<float4*>(cp + j) = v;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (col0 + j < N) {
+                const float v = __uint_as_float(r[j]);
+                cp[j] = subtract ? cp[j] - v : v;
+              }
+            }
+          }
+        }
+      }
+      if (frv_r && row < M) frv_pw[(size_t)bn * M + row] = wacc;
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    mbar_wait(drain_bar, 0, err);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN)
+                 : "memory");
+  }
+  // neither CTA leaves while the other may still signal its barriers
+  cluster_sync();
+}
+
 // binary32 (rows x cols, leading dim ld) -> 16-bit rows x Kp, zero padded
 template <bool FP16>
 __global__ void k_cast_rows(const float* __restrict__ A, int lda, int rows, int cols, int Kp,
@@ -653,7 +919,83 @@ int persistent_grid(int M, int N) {
   return (int)std::max<long long>(1, std::min<long long>(tiles, sms));
 }
 
+// the CTA-pair kernel where the device schedules clusters of two with its
+// shared memory (decided once)
+bool use_pair() {
+  static int v = -1;
+  if (v < 0) {
+    v = 0;
+    if (cudaFuncSetAttribute(k_gemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM2_BYTES) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(2);
+      cfg.blockDim = dim3(192);
+      cfg.dynamicSmemBytes = SMEM2_BYTES;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, k_gemm_tc2, &cfg) == cudaSuccess && nc >= 1) v = 1;
+    }
+    cudaGetLastError();
+  }
+  return v == 1;
+}
+
+// C (+)= A16 Bt16^T on the tensor cores: the CTA-pair kernel, else the
+// one-CTA kernel
+cudaError_t launch_product(const uint16_t* a16, const uint16_t* bt16, int Kp, bool fp16, float* C,
+                           int ldc, int M, int N, bool subtract, int* err, const float4* frv_r,
+                           float4* frv_pw, int inj_row, int inj_col, float inj_delta,
+                           cudaStream_t s) {
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a16, M, Kp, TM, fp16)) return cudaErrorInvalidValue;
+  if (use_pair()) {
+    if (!make_map(&mb, bt16, N, Kp, TH, fp16)) return cudaErrorInvalidValue;
+    const long long tiles = (long long)((M + TM2 - 1) / TM2) * ((N + TN - 1) / TN);
+    const int pairs = (int)std::max<long long>(
+        1, std::min<long long>(tiles, persistent_grid(1 << 30, TN) / 2));   // SMs / 2
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * pairs);
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = SMEM2_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_gemm_tc2, ma, mb, C, ldc, M, N, Kp / TK, idesc2(fp16),
+                              subtract ? 1 : 0, err, frv_r, frv_pw, inj_row, inj_col, inj_delta);
+  }
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  if (!make_map(&mb, bt16, N, Kp, TN, fp16)) return cudaErrorInvalidValue;
+  k_gemm_tc<<<persistent_grid(M, N), 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, Kp / TK,
+                                                           idesc(fp16), subtract ? 1 : 0, err,
+                                                           frv_r, frv_pw, inj_row, inj_col,
+                                                           inj_delta);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+void gemm_tc_prepare() {
+  use_pair();
+  cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaGetLastError();
+}
 
 size_t gemm_tc_scratch_bytes(int M, int N, int K) {
   const size_t Kp = (size_t)((K + TK - 1) / TK) * TK;
@@ -674,13 +1016,6 @@ cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, flo
   int* err = reinterpret_cast<int*>(p);
   uint16_t* a16 = reinterpret_cast<uint16_t*>(p + 256);
   uint16_t* bt16 = reinterpret_cast<uint16_t*>(p + 256 + align256((size_t)M * Kp * 2));
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
   prof_begin(prof, "cast_operands", s);
   const long long ca = (long long)M * (Kp / 8);
   const int ga = (int)std::min<long long>((ca + 255) / 256, 65535LL * 8);
@@ -693,17 +1028,12 @@ cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, flo
     k_cast_transpose<false><<<gt, bt, 0, s>>>(B, ldb, K, N, Kp, bt16);
   }
   prof_end(prof, s);
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, a16, M, Kp, TM, fp16) || !make_map(&mb, bt16, N, Kp, TN, fp16))
-    return cudaErrorInvalidValue;
-  const int grid = persistent_grid(M, N);
   prof_begin(prof, fp16 ? "gemm_tc_f16" : "gemm_tc_bf16", s);
-  k_gemm_tc<<<grid, 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, Kp / TK, idesc(fp16),
-                                          subtract ? 1 : 0, err, nullptr, nullptr, inj_row,
-                                          inj_col, inj_delta);
+  const cudaError_t e = launch_product(a16, bt16, Kp, fp16, C, ldc, M, N, subtract, err, nullptr,
+                                       nullptr, inj_row, inj_col, inj_delta, s);
   prof_end(prof, s);
   *kernels += 3;
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int N, bool fp16,
@@ -718,13 +1048,6 @@ cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int
   uint16_t* a16 = reinterpret_cast<uint16_t*>(p + 256);
   uint16_t* bt16 = reinterpret_cast<uint16_t*>(p + 256 + align256((size_t)N * Kp * 2));
   const FrvFused f = frv_fused_layout(p + gemm_tc_scratch_bytes(N, N, N), N);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
   prof_begin(prof, "cast_operands", s);
   cudaError_t e = launch_frv_vectors(f, N, nvec, seed, s);
   if (e != cudaSuccess) return e;
@@ -737,14 +1060,11 @@ cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int
   if (fp16) k_cast_a_frv<true><<<ga, 256, 0, s>>>(A, N, Kp, a16, f.br4, f.t4, f.pzq);
   else k_cast_a_frv<false><<<ga, 256, 0, s>>>(A, N, Kp, a16, f.br4, f.t4, f.pzq);
   prof_end(prof, s);
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, a16, N, Kp, TM, fp16) || !make_map(&mb, bt16, N, Kp, TN, fp16))
-    return cudaErrorInvalidValue;
-  const int grid = persistent_grid(N, N);
   prof_begin(prof, fp16 ? "gemm_tc_f16" : "gemm_tc_bf16", s);
-  k_gemm_tc<<<grid, 192, SMEM_BYTES, s>>>(ma, mb, C, N, N, N, Kp / TK, idesc(fp16), 0, err, f.r4,
-                                          f.pw, inj_row, inj_col, inj_delta);
+  e = launch_product(a16, bt16, Kp, fp16, C, N, N, N, false, err, f.r4, f.pw, inj_row, inj_col,
+                     inj_delta, s);
   prof_end(prof, s);
+  if (e != cudaSuccess) return e;
   prof_begin(prof, "freivalds_fused", s);
   e = launch_frv_check_fused(f, N, nvec, c, u_eff, res, s);
   prof_end(prof, s);

@@ -828,6 +828,7 @@ bool use_cluster16() {
 size_t lu_panel_max_smem(int n) { return panel_smem<8>(n, 0); }
 
 cudaError_t lu_prepare(int n) {
+  gemm_tc_prepare();
   const bool c16 = use_cluster16();
   const size_t ps = c16 ? panel_smem<16>(n, 0) : panel_smem<8>(n, 0);
   cudaError_t e = c16 ? cudaFuncSetAttribute(k_lu_panel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps)

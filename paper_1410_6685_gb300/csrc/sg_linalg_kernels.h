@@ -17,6 +17,9 @@ cudaError_t launch_gemm_f32(const float* A, int lda, const float* B, int ldb, fl
 // inj_row / inj_col >= 0: contract testing, inj_delta is added to that
 // product element before it is stored.
 size_t gemm_tc_scratch_bytes(int M, int N, int K);
+// kernel attributes and the CTA-pair decision of the tensor-core product;
+// called before a product is captured into a graph
+void gemm_tc_prepare();
 cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
                            int M, int N, int K, bool fp16, bool subtract, void* scratch,
                            cudaStream_t s, Prof* prof, int64_t* kernels, int inj_row = -1,
