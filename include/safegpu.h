@@ -440,6 +440,17 @@ sg_status sg_debug_inject_sort(sg_ctx* ctx, sg_inject_mode mode, int64_t i, int6
  * negative, or above INT32_MAX. */
 sg_status sg_debug_inject_matmul(sg_ctx* ctx, int64_t row, int64_t col, float delta);
 
+/* Testing aid for the portable kernel forms.  On devices that schedule them,
+ * tensor-core products run on CTA pairs (clusters of two, tcgen05
+ * cta_group::2) and the elimination's panel on a 16-CTA cluster; the
+ * one-CTA product and the 8-CTA panel remain for devices that do not.
+ * on != 0 makes every later product and factorisation in this PROCESS use
+ * the portable forms (so that they can be tested where the fast ones run);
+ * 0 restores the choice by the device.  Clears this context's cached
+ * factorisation graph.  Results of both forms are equal up to rounding
+ * order.  Errors: SG_ERR_INVALID_ARG for a null context. */
+sg_status sg_debug_portable_kernels(sg_ctx* ctx, int on);
+
 /* ------------------------------------------------------------------------ */
 /* Batched collections: one persistent launch over many collections of uneven
  * size, each running the chain

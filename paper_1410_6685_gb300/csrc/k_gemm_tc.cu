@@ -954,7 +954,7 @@ cudaError_t launch_product(const uint16_t* a16, const uint16_t* bt16, int Kp, bo
                            cudaStream_t s) {
   CUtensorMap ma, mb;
   if (!make_map(&ma, a16, M, Kp, TM, fp16)) return cudaErrorInvalidValue;
-  if (use_pair()) {
+  if (!portable_kernels() && use_pair()) {
     if (!make_map(&mb, bt16, N, Kp, TH, fp16)) return cudaErrorInvalidValue;
     const long long tiles = (long long)((M + TM2 - 1) / TM2) * ((N + TN - 1) / TN);
     const int pairs = (int)std::max<long long>(
@@ -990,6 +990,12 @@ cudaError_t launch_product(const uint16_t* a16, const uint16_t* bt16, int Kp, bo
 }
 
 }  // namespace
+
+namespace {
+bool g_portable = false;
+}
+void set_portable_kernels(bool on) { g_portable = on; }
+bool portable_kernels() { return g_portable; }
 
 void gemm_tc_prepare() {
   use_pair();

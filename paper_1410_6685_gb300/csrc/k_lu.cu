@@ -829,7 +829,7 @@ size_t lu_panel_max_smem(int n) { return panel_smem<8>(n, 0); }
 
 cudaError_t lu_prepare(int n) {
   gemm_tc_prepare();
-  const bool c16 = use_cluster16();
+  const bool c16 = !portable_kernels() && use_cluster16();
   const size_t ps = c16 ? panel_smem<16>(n, 0) : panel_smem<8>(n, 0);
   cudaError_t e = c16 ? cudaFuncSetAttribute(k_lu_panel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps)
                       : cudaFuncSetAttribute(k_lu_panel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
@@ -842,7 +842,8 @@ cudaError_t launch_lu_panel(float* LU, int n, int k, int jb, int* piv, int* info
                             int c_lo, int c_hi, cudaStream_t s, Prof* prof) {
   prof_begin(prof, "lu_panel", s);
   const cudaError_t e =
-      use_cluster16() ? launch_panel<16>(LU, n, k, jb, piv, info, moves, c_lo, c_hi, s)
+      !portable_kernels() && use_cluster16()
+          ? launch_panel<16>(LU, n, k, jb, piv, info, moves, c_lo, c_hi, s)
                       : launch_panel<8>(LU, n, k, jb, piv, info, moves, c_lo, c_hi, s);
   prof_end(prof, s);
   return e;

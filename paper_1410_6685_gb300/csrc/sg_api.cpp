@@ -15,6 +15,7 @@
 #include <string>
 
 #include "sg_jit.h"
+#include "sg_linalg_kernels.h"
 #include "sg_plan.h"
 #include "sg_runtime.h"
 
@@ -909,6 +910,13 @@ sg_status sg_debug_inject_matmul(sg_ctx* c, int64_t row, int64_t col, float delt
   c->mm_inject.row = row;
   c->mm_inject.col = col;
   c->mm_inject.delta = delta;
+  return SG_OK;
+}
+
+sg_status sg_debug_portable_kernels(sg_ctx* c, int on) {
+  if (!c) return SG_ERR_INVALID_ARG;
+  sgk::set_portable_kernels(on != 0);
+  c->lu.clear();
   return SG_OK;
 }
 

@@ -17,6 +17,10 @@ cudaError_t launch_gemm_f32(const float* A, int lda, const float* B, int ldb, fl
 // inj_row / inj_col >= 0: contract testing, inj_delta is added to that
 // product element before it is stored.
 size_t gemm_tc_scratch_bytes(int M, int N, int K);
+// process-wide: use the portable kernel forms (one-CTA tensor-core product,
+// 8-CTA elimination panel) even where the device schedules the fast ones
+void set_portable_kernels(bool on);
+bool portable_kernels();
 // kernel attributes and the CTA-pair decision of the tensor-core product;
 // called before a product is captured into a graph
 void gemm_tc_prepare();

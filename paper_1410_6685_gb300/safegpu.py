@@ -137,7 +137,7 @@ def _load():
         "sg_last_violation": [vp, P(SgViolation)], "sg_flush": [vp],
         "sg_set_contract_mode": [vp, i32], "sg_set_fusion": [vp, i32],
         "sg_set_scheduler": [vp, i32], "sg_set_codegen": [vp, i32], "sg_plan_describe": [vp, C.c_char_p, sz, P(sz)],
-        "sg_kernel_count": [vp, P(i64)], "sg_profile_enable": [vp, i32], "sg_profile_report": [vp, C.c_char_p, sz, P(sz), i32], "sg_debug_inject_sort": [vp, i32, i64, i64], "sg_debug_inject_matmul": [vp, i64, i64, C.c_float],
+        "sg_kernel_count": [vp, P(i64)], "sg_profile_enable": [vp, i32], "sg_profile_report": [vp, C.c_char_p, sz, P(sz), i32], "sg_debug_inject_sort": [vp, i32, i64, i64], "sg_debug_inject_matmul": [vp, i64, i64, C.c_float], "sg_debug_portable_kernels": [vp, i32],
         "sg_batch_run": [vp, P(SgChain), vp, vp, i64, vp, vp, vp],
         "sg_filter_noalloc": [P(SgExpr), vp, i64, vp, vp, vp],
         "sg_batch_report": [vp, P(SgChain), vp, vp, i64, vp, vp, vp, P(SgSchedReport)],
@@ -476,6 +476,10 @@ def sg_debug_inject_sort(ctx, mode, i, j=0):
 
 def sg_debug_inject_matmul(ctx, row, col, delta):
     _check(lib.sg_debug_inject_matmul(ctx, row, col, delta), ctx)
+
+
+def sg_debug_portable_kernels(ctx, on=True):
+    _check(lib.sg_debug_portable_kernels(ctx, 1 if on else 0), ctx)
 
 
 def sg_profile_enable(ctx, on=True):

@@ -207,3 +207,30 @@ def test_builtin_check_flags_planted_element(env, prec, n, fusion):
     # the injection is consumed: the next product is clean again
     mc, keep = gemm(env, A, B, prec)
     assert np.array_equal(read(env, mc, n, n), C0)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("shape", [(129, 257, 65), (300, 500, 700), (1024, 1024, 1024)])
+def test_portable_one_cta_product(env, prec, shape):
+    """The one-CTA tensor-core product (the form for devices without CTA
+    pairs), forced through the testing switch: within the operand-rounding
+    bound of the oracle, and within binary32 accumulation distance of the
+    CTA-pair form (both accumulate the same bf16/fp16 products in binary32)."""
+    sg, ctx, _ = env
+    M, K, N = shape
+    g = np.random.default_rng(M + 3 * N)
+    A = g.standard_normal((M, K)).astype(np.float32)
+    B = g.standard_normal((K, N)).astype(np.float32)
+    mc, keep = gemm(env, A, B, prec)
+    fast = read(env, mc, M, N)
+    sg.sg_matrix_release(mc)
+    sg.sg_debug_portable_kernels(ctx, True)
+    try:
+        mc, keep2 = gemm(env, A, B, prec)
+        one = read(env, mc, M, N)
+        sg.sg_matrix_release(mc)
+    finally:
+        sg.sg_debug_portable_kernels(ctx, False)
+    ref = oracle.matmul_f64(A, B)
+    assert eta(one, ref) <= TOL[prec]
+    assert eta(one, fast.astype(np.float64)) <= 1e-5

@@ -183,3 +183,29 @@ def test_det_diag_dominant_2048(env, prec):
     assert r.sign == sign and r.info == 0
     assert abs(r.log_abs - ref) <= n * (2.0 ** -20 if prec == 0 else 2.0 ** -12)
     assert r.det == np.inf    # |det| far above the binary64 range
+
+
+@pytest.mark.parametrize("n", [33, 1000, 2048])
+def test_portable_kernel_forms(env, n):
+    """The 8-CTA panel cluster and the one-CTA tensor-core trailing update
+    (the forms for devices without 16-CTA clusters or CTA pairs), forced
+    through the testing switch: a pivoting Gaussian matrix (binary32
+    updates) solved as by the oracle and as by the fast forms, and the
+    diagonally dominant workload with bf16 tensor-core updates."""
+    sg, ctx, _ = env
+    g = np.random.default_rng(n + 5)
+    A = g.standard_normal((n, n)).astype(np.float32)
+    b = A.astype(np.float64) @ g.standard_normal(n)
+    fast, _ = solve(env, A, b, prec=0)
+    sg.sg_debug_portable_kernels(ctx, True)
+    try:
+        x, info = solve(env, A, b, prec=0)
+        Ad, bd = inputs.gepp_inputs(n)
+        xd, infod = solve(env, Ad, bd, prec=1)
+    finally:
+        sg.sg_debug_portable_kernels(ctx, False)
+    ref = oracle.solve(A, b)
+    assert np.max(np.abs(x - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(x - fast)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+    assert info.residual <= 1e-12
+    assert np.max(np.abs(xd - 1.0)) <= 1e-10 and infod.info == 0
