@@ -145,11 +145,39 @@ sg_status sg_vector_wrap(sg_ctx* ctx, sg_dtype dt, int64_t n, void* dev_ptr,
  * then copies n == count elements into host memory and waits for them.
  * SG_ERR_POISONED if the value depends on a failed contract. */
 sg_status sg_vector_read(sg_vector* v, void* host, int64_t n);
+
+/* Asynchronous forms of create and read, for pipelines of many steps (Sec. 3.1:
+ * the data is copied to the device when the collection is created and back
+ * when it is read).  Both return without waiting:
+ *   sg_vector_create_async copies `host` (n elements) on a separate upload
+ *     stream; the first work on the context's stream that uses the vector
+ *     waits for the copy (other work does not, so the copy of the next
+ *     step's input can overlap this step's compute).  `host` must stay
+ *     valid and unchanged until the copy completes
+ *     (sg_sync, or any later call that waits, such as a flush that reads
+ *     back contract results).  Pinned (page-locked) host memory gives the
+ *     full link bandwidth.
+ *   sg_vector_read_async flushes the value's pending work first (like
+ *     sg_vector_read: precondition / postcondition failures are reported
+ *     there) and then enqueues its copy into `host` on a separate download
+ *     stream, after everything enqueued so far on the context's stream.
+ *     `host` holds the data only after sg_sync.  Later work that touches the
+ *     value waits for the copy; a value released right away is freed behind it.
+ * So one step's read can overlap the next step's create and compute.
+ *   sg_sync waits for every copy and kernel the context has enqueued.
+ * Values must be released before sg_destroy.  Errors as for the synchronous
+ * forms; copy failures give SG_ERR_CUDA. */
+sg_status sg_vector_create_async(sg_ctx* ctx, sg_dtype dtype, int64_t n, const void* host,
+                                 sg_vector** out);
+sg_status sg_vector_read_async(sg_vector* v, void* host, int64_t n);
+sg_status sg_sync(sg_ctx* ctx);
 /* count (Table 2): scalar query, no flush.  May be called on a pending
  * filter result only after a flush (its count is data-dependent); before
  * that it flushes. */
 sg_status sg_vector_count(sg_vector* v, int64_t* n);
-/* Device address of the vector's storage after flushing it (for interop). */
+/* Device address of the vector's storage after flushing it (for interop).
+ * Work the caller enqueues on the context's stream afterwards sees the
+ * vector's asynchronous copies completed; on another stream, sg_sync first. */
 sg_status sg_vector_device_ptr(sg_vector* v, void** dev_ptr);
 sg_status sg_vector_release(sg_vector* v);
 /* item (Table 2): element i (0-based) into *value (dtype-sized); flushes the

@@ -1,5 +1,6 @@
-// k_copy.cu -- contiguous device copies for `concatenate` (Table 2): the
-// operands are placed one after the other in a new vector (sm_103a).
+// k_copy.cu -- contiguous copies (sm_103a): `concatenate` (Table 2) places
+// its operands one after the other in a new vector, and a flush stores its
+// pass results into the pinned host buffer (device-addressable) with it.
 // 16-byte loads and stores when both ends are 16-byte aligned and the length
 // is a multiple of 16, else 4-byte, else single bytes; grid-stride.
 #include "sg_internal.h"

@@ -20,7 +20,46 @@
 #include "sg_runtime.h"
 
 Storage::~Storage() {
+  if (ul_event) {
+    // never used: free it behind its copy in
+    if (owned && ptr) cudaStreamWaitEvent(stream, ul_event, 0);
+    cudaEventDestroy(ul_event);
+  }
   if (owned && ptr) cudaFreeAsync(ptr, stream);
+  if (dl_event) cudaEventDestroy(dl_event);
+}
+
+// The storage that owns a view's memory.
+static Storage* root_storage(Storage* st) {
+  while (st && st->parent) st = st->parent.get();
+  return st;
+}
+
+// Work about to be enqueued on the context's stream that touches a storage
+// waits for its asynchronous copy in, and for an asynchronous read in
+// flight (after which the storage is freed on the context's stream again).
+void join_transfers(sg_ctx* c, Storage* st) {
+  st = root_storage(st);
+  if (!st) return;
+  if (st->ul_event) {
+    cudaStreamWaitEvent(c->stream, st->ul_event, 0);
+    cudaEventDestroy(st->ul_event);
+    st->ul_event = nullptr;
+  }
+  if (st->dl_event) {
+    cudaStreamWaitEvent(c->stream, st->dl_event, 0);
+    cudaEventDestroy(st->dl_event);
+    st->dl_event = nullptr;
+    st->stream = c->stream;
+  }
+}
+
+static void join_downloads_of_pending(sg_ctx* c) {
+  for (auto& n : c->pending) {
+    for (int i = 0; i < n->nin; ++i)
+      if (n->in[i] && n->in[i]->st) join_transfers(c, n->in[i]->st.get());
+    if (n->out && n->out->st) join_transfers(c, n->out->st.get());
+  }
 }
 
 struct sg_matrix : public sg_vector {};
@@ -213,6 +252,9 @@ sg_status sg_init(int device, void* stream, sg_ctx** out) {
     c->planning_only = false;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->upload, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->download, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->last_download, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->counter, 64 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(c->counter, 0, 64 * sizeof(unsigned int));
     if (e == cudaSuccess) {
@@ -223,6 +265,12 @@ sg_status sg_init(int device, void* stream, sg_ctx** out) {
       if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t keep = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        // a block freed on one of the context's streams is not handed to an
+        // allocation on another by making that stream wait (it would chain
+        // an asynchronous copy in behind an asynchronous read): such a block
+        // is reused once its free has completed, else a new one is taken
+        int no = 0;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
       }
       cudaGetLastError();
     }
@@ -230,6 +278,9 @@ sg_status sg_init(int device, void* stream, sg_ctx** out) {
     if (e != cudaSuccess) {
       cudaGetLastError();
       if (c->counter) cudaFree(c->counter);
+      if (c->upload) cudaStreamDestroy(c->upload);
+      if (c->download) cudaStreamDestroy(c->download);
+      if (c->last_download) cudaEventDestroy(c->last_download);
       delete c;
       return SG_ERR_CUDA;
     }
@@ -242,7 +293,12 @@ sg_status sg_destroy(sg_ctx* c) {
   if (!c) return SG_ERR_INVALID_ARG;
   c->pending.clear();
   if (!c->planning_only) {
+    cudaStreamSynchronize(c->upload);
+    cudaStreamSynchronize(c->download);
     cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->upload);
+    cudaStreamDestroy(c->download);
+    cudaEventDestroy(c->last_download);
     if (c->scratch) cudaFree(c->scratch);
     if (c->counter) cudaFree(c->counter);
     if (c->host_res) cudaFreeHost(c->host_res);
@@ -311,6 +367,7 @@ static sg_status read_common(sg_vector* h, void* host, int64_t n) {
                                 (long long)n, (long long)h->v->n);
   if (c->planning_only) return fail(c, SG_ERR_UNSUPPORTED, "planning-only context");
   if (n == 0) return SG_OK;
+  join_transfers(c, h->v->st.get());
   cudaError_t e = cudaMemcpyAsync(host, h->v->st->ptr, (size_t)n * dtype_size(h->v->dt),
                                   cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -320,6 +377,81 @@ static sg_status read_common(sg_vector* h, void* host, int64_t n) {
 }
 
 sg_status sg_vector_read(sg_vector* h, void* host, int64_t n) { return read_common(h, host, n); }
+
+sg_status sg_vector_create_async(sg_ctx* c, sg_dtype dt, int64_t n, const void* host,
+                                 sg_vector** out) {
+  if (!c || !out || !valid_dtype(dt) || n < 0 || (!host && n > 0))
+    return fail(c, SG_ERR_INVALID_ARG, "bad create arguments");
+  if (c->planning_only) return fail(c, SG_ERR_UNSUPPORTED, "planning-only context");
+  ValueP v;
+  make_out(c, dt, n, n, 1, &v);
+  auto st = std::make_shared<Storage>();
+  st->bytes = (size_t)n * dtype_size(dt);
+  st->stream = c->stream;   // freed behind the work that uses it
+  if (st->bytes) {
+    cudaError_t e = cudaMallocAsync(&st->ptr, st->bytes, c->upload);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, SG_ERR_OOM, "device allocation of %zu bytes failed", st->bytes);
+    }
+    st->owned = true;
+    e = cudaMemcpyAsync(st->ptr, host, st->bytes, cudaMemcpyHostToDevice, c->upload);
+    // the first work on the context's stream that uses the value waits for it
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->ul_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(st->ul_event, c->upload);
+    if (e != cudaSuccess)
+      return fail(c, SG_ERR_CUDA, "host to device copy failed: %s", cudaGetErrorString(e));
+  }
+  v->st = std::move(st);
+  *out = new_handle(c, v, false);
+  return SG_OK;
+}
+
+sg_status sg_vector_read_async(sg_vector* h, void* host, int64_t n) {
+  if (check_vec(h) || (!host && n > 0)) return SG_ERR_INVALID_ARG;
+  sg_ctx* c = h->ctx;
+  if (h->v->producer || !h->v->count_known || pending_write_to(c, h->v.get())) {
+    sg_status s = sg_flush(c);
+    if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
+  }
+  if (h->v->poisoned) return fail(c, SG_ERR_POISONED, "value depends on a failed contract");
+  if (n != h->v->n) return fail(c, SG_ERR_SHAPE, "read of %lld elements, count is %lld",
+                                (long long)n, (long long)h->v->n);
+  if (c->planning_only) return fail(c, SG_ERR_UNSUPPORTED, "planning-only context");
+  if (n == 0) return SG_OK;
+  Storage* root = root_storage(h->v->st.get());
+  cudaEvent_t made = nullptr, done = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&made, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+  // the copy follows everything enqueued so far on the context's stream
+  if (e == cudaSuccess) e = cudaEventRecord(made, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->download, made, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host, h->v->st->ptr, (size_t)n * dtype_size(h->v->dt),
+                        cudaMemcpyDeviceToHost, c->download);
+  if (e == cudaSuccess) e = cudaEventRecord(done, c->download);
+  if (made) cudaEventDestroy(made);
+  if (e != cudaSuccess) {
+    if (done) cudaEventDestroy(done);
+    return fail(c, SG_ERR_CUDA, "device to host copy failed: %s", cudaGetErrorString(e));
+  }
+  if (root->dl_event) cudaEventDestroy(root->dl_event);
+  root->dl_event = done;
+  cudaEventRecord(c->last_download, c->download);
+  // released before any further use: freed behind the copy
+  root->stream = c->download;
+  return SG_OK;
+}
+
+sg_status sg_sync(sg_ctx* c) {
+  if (!c) return SG_ERR_INVALID_ARG;
+  if (c->planning_only) return SG_OK;
+  cudaError_t e = cudaStreamSynchronize(c->upload);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->download);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, SG_ERR_CUDA, "synchronisation failed: %s", cudaGetErrorString(e));
+  return SG_OK;
+}
 
 sg_status sg_vector_count(sg_vector* h, int64_t* n) {
   if (check_vec(h) || !n) return SG_ERR_INVALID_ARG;
@@ -336,6 +468,8 @@ static sg_status devptr_common(sg_vector* h, void** p) {
     if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
   }
   if (!h->v->st) return fail(h->ctx, SG_ERR_UNSUPPORTED, "value was never materialised");
+  // work the caller enqueues on the context's stream sees its copies done
+  if (!h->ctx->planning_only) join_transfers(h->ctx, h->v->st.get());
   *p = h->v->st->ptr;
   return SG_OK;
 }
@@ -354,6 +488,7 @@ sg_status sg_vector_item(sg_vector* h, int64_t i, void* value) {
     return fail(c, SG_ERR_SHAPE, "item %lld of a vector of %lld", (long long)i, (long long)h->v->n);
   if (c->planning_only) return fail(c, SG_ERR_UNSUPPORTED, "planning-only context");
   const size_t es = dtype_size(h->v->dt);
+  join_transfers(c, h->v->st.get());
   cudaError_t e = cudaMemcpyAsync(value, static_cast<const char*>(h->v->st->ptr) + (size_t)i * es,
                                   es, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -849,6 +984,7 @@ sg_status sg_flush(sg_ctx* c) {
   if (!c) return SG_ERR_INVALID_ARG;
   if (c->pending.empty()) return SG_OK;
   if (c->planning_only) return fail(c, SG_ERR_UNSUPPORTED, "planning-only context cannot execute");
+  join_downloads_of_pending(c);
   return sg_execute_pending(c);
 }
 

@@ -532,6 +532,14 @@ sg_status ensure_host_res(sg_ctx* c, size_t bytes) {
   cudaError_t e = cudaMallocHost(&c->host_res, nb);
   if (e != cudaSuccess) return cuda_fail(c, e, "pinned result buffer");
   c->host_res_bytes = nb;
+  // with unified addressing the pinned buffer has the same address on the
+  // device, so a kernel can store the results into it: the flush does so
+  // while a large asynchronous read of another value is on the copy engine
+  // (a copy would queue behind it)
+  cudaPointerAttributes a{};
+  c->host_res_mapped = cudaPointerGetAttributes(&a, c->host_res) == cudaSuccess &&
+                       a.devicePointer == c->host_res;
+  cudaGetLastError();
   return SG_OK;
 }
 
@@ -565,6 +573,16 @@ void record_violation(sg_ctx* c, Node* n, int64_t first, double observed, bool* 
 }  // namespace
 
 sg_status sg_execute_pending(sg_ctx* c) {
+  // is an asynchronous read still on the copy engine?  (asked before this
+  // flush launches anything; "not ready" is not an error of this flush)
+  bool dl_busy = false;
+  if (c->host_res_mapped && c->last_download) {
+    const cudaError_t q = cudaEventQuery(c->last_download);
+    if (q == cudaErrorNotReady) {
+      dl_busy = true;
+      cudaGetLastError();
+    }
+  }
   Planner pl(c);
   pl.plan();
   std::vector<Pass>& passes = pl.passes;
@@ -800,9 +818,18 @@ sg_status sg_execute_pending(sg_ctx* c) {
       }
     }
   }
-  if (e == cudaSuccess && !status && need_records)
-    e = cudaMemcpyAsync(c->host_res, dres, passes.size() * sgk::kResultBytes,
-                        cudaMemcpyDeviceToHost, c->stream);
+  // while an asynchronous read is still on the copy engine, the records are
+  // stored by a kernel instead of queueing a copy behind it
+  if (e == cudaSuccess && !status && need_records) {
+    if (dl_busy) {
+      e = sgk::launch_copy(c->host_res, dres, passes.size() * sgk::kResultBytes, c->num_sms,
+                           c->stream);
+      c->kernels += 1;
+    } else {
+      e = cudaMemcpyAsync(c->host_res, dres, passes.size() * sgk::kResultBytes,
+                          cudaMemcpyDeviceToHost, c->stream);
+    }
+  }
   if (e == cudaSuccess && !status && need_records) e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess && !status && !need_records) e = cudaGetLastError();
   if (e != cudaSuccess && !status) status = cuda_fail(c, e, "kernel execution");

@@ -18,7 +18,9 @@ struct Storage {
   void* ptr = nullptr;
   size_t bytes = 0;
   bool owned = false;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;     // the stream the allocation is freed on
+  cudaEvent_t ul_event = nullptr;    // the asynchronous create's copy, until first used
+  cudaEvent_t dl_event = nullptr;    // an asynchronous read still in flight
   std::shared_ptr<Storage> parent;   // a subset's view keeps its source alive
   ~Storage();
 };
@@ -151,6 +153,9 @@ struct sg_ctx {
   int device = -1;
   bool planning_only = true;
   cudaStream_t stream = nullptr;
+  cudaStream_t upload = nullptr;       // asynchronous host-to-device creates
+  cudaStream_t download = nullptr;     // asynchronous device-to-host reads
+  cudaEvent_t last_download = nullptr; // the latest of them
   int num_sms = 0;
   int mode = SG_CONTRACTS_PRE_POST;
   int fusion = SG_FUSE_ON;
@@ -169,6 +174,7 @@ struct sg_ctx {
   size_t scratch_bytes = 0;
   void* host_res = nullptr;            // pinned host copy of pass results
   size_t host_res_bytes = 0;
+  bool host_res_mapped = false;        // kernels can store into host_res directly
   sgk::SortInject inject{};            // contract-test fault for the next sort
   struct {
     int64_t row = -1, col = -1;
@@ -179,6 +185,11 @@ struct sg_ctx {
   SchedState schedst;                  // schedule log and cost model
   LuCache lu;                          // factorisation workspace + graph
 };
+
+// Makes work enqueued next on the context's stream wait for the
+// asynchronous copies of `st` (sg_vector_create_async, sg_vector_read_async)
+// still in flight.
+void join_transfers(sg_ctx* c, Storage* st);
 
 struct sg_vector {
   sg_ctx* ctx = nullptr;

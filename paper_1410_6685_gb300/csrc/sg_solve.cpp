@@ -270,6 +270,8 @@ extern "C" sg_status sg_solve(sg_ctx* c, sg_matrix* A, sg_vector* b, const sg_so
   }
   xv->st->owned = true;
   double* x = static_cast<double*>(xv->st->ptr);
+  join_transfers(c, A->v->st.get());
+  join_transfers(c, b->v->st.get());
   const float* a = static_cast<const float*>(A->v->st->ptr);
   const double* bb = static_cast<const double*>(b->v->st->ptr);
   sgk::Prof* prof = &c->prof;
@@ -424,6 +426,7 @@ extern "C" sg_status sg_det(sg_ctx* c, sg_matrix* A, sg_precision prec, sg_det_r
     cudaGetLastError();
     return err(c, SG_ERR_OOM, "det workspace allocation failed");
   }
+  join_transfers(c, A->v->st.get());
   sg_status st2 = lu_factor(c, static_cast<const float*>(A->v->st->ptr), n, prec);
   if (st2) {
     cudaFreeAsync(dout, s);

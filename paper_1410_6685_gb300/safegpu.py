@@ -110,6 +110,8 @@ def _load():
     protos = {
         "sg_init": [i32, vp, P(vp)], "sg_destroy": [vp],
         "sg_vector_create": [vp, i32, i64, vp, P(vp)],
+        "sg_vector_create_async": [vp, i32, i64, vp, P(vp)], "sg_vector_read_async": [vp, vp, i64],
+        "sg_sync": [vp],
         "sg_vector_wrap": [vp, i32, i64, vp, P(vp)],
         "sg_vector_read": [vp, vp, i64], "sg_vector_count": [vp, P(i64)],
         "sg_vector_device_ptr": [vp, P(vp)], "sg_vector_release": [vp],
@@ -251,6 +253,22 @@ def sg_vector_read(ctx, v, out):
     """out: a numpy array with count elements of the vector's dtype."""
     _check(lib.sg_vector_read(v, C.c_void_p(out.ctypes.data), out.size), ctx)
     return out
+
+
+def sg_vector_create_async(ctx, dtype, n, host):
+    """host: a numpy array (contiguous, matching dtype, ideally over pinned
+    memory) that must stay alive and unchanged until sg_sync."""
+    return _out(lib.sg_vector_create_async, ctx, ctx, dtype, n, C.c_void_p(host.ctypes.data))
+
+
+def sg_vector_read_async(ctx, v, out):
+    """Enqueues the copy into `out` (count elements); valid after sg_sync."""
+    _check(lib.sg_vector_read_async(v, C.c_void_p(out.ctypes.data), out.size), ctx)
+    return out
+
+
+def sg_sync(ctx):
+    _check(lib.sg_sync(ctx), ctx)
 
 
 def sg_vector_count(ctx, v) -> int:
