@@ -27,7 +27,7 @@
 //                  (bf16/fp16 operands, binary32 accumulate) or the binary32
 //                  SIMT form.
 // Solve: pivots on the right-hand side, then forward / backward substitution
-// by blocks of 32 rows in one launch each: CTAs take row blocks in order
+// by blocks of 64 rows in one launch each: CTAs take row blocks in order
 // (ticket) and wait, with a bounded spin, for the blocks they depend on; the
 // diagonal blocks are applied through their inverses (formed once per
 // factorisation), one short product instead of 32 dependent steps.
@@ -535,55 +535,58 @@ __global__ void k_apply_perm(const double* __restrict__ rhs, float* y, int n,
     y[i] = (float)rhs[perm[i]];
 }
 
-// Inverses of the 32x32 diagonal blocks of L (unit lower) and U (upper),
+// Inverses of the 64x64 diagonal blocks of L (unit lower) and U (upper),
 // once per factorisation, for the blocked substitutions: inv[0][b] = L_bb^-1,
 // inv[1][b] = U_bb^-1, row-major; a block cut by n is padded with the
-// identity.  One CTA per block: thread j < 32 forms column j of L_bb^-1 by
-// forward substitution, thread 32 + j column j of U_bb^-1 by back
+// identity.  One CTA per block: thread j < 64 forms column j of L_bb^-1 by
+// forward substitution, thread 64 + j column j of U_bb^-1 by back
 // substitution, both in registers.
-__global__ void __launch_bounds__(64) k_lu_diag_inv(const float* __restrict__ LU, int n,
-                                                    float* __restrict__ inv) {
-  __shared__ float D[32][33];
-  const int b = blockIdx.x, row0 = b * 32, tid = threadIdx.x;
-  for (int t = tid; t < 1024; t += 64) {
-    const int r = t >> 5, c = t & 31;
+constexpr int kTB = 64;   // rows of a substitution block
+__global__ void __launch_bounds__(2 * kTB) k_lu_diag_inv(const float* __restrict__ LU, int n,
+                                                         float* __restrict__ inv) {
+  __shared__ float D[kTB][kTB + 1];
+  const int b = blockIdx.x, row0 = b * kTB, tid = threadIdx.x;
+  for (int t = tid; t < kTB * kTB; t += 2 * kTB) {
+    const int r = t / kTB, c = t % kTB;
     D[r][c] = (row0 + r < n && row0 + c < n) ? LU[(size_t)(row0 + r) * n + row0 + c]
                                              : (r == c ? 1.0f : 0.0f);
   }
   __syncthreads();
   const int nb = gridDim.x;
-  const int j = tid & 31;
-  float x[32];
-  if (tid < 32) {
+  const int j = tid % kTB;
+  float x[kTB];
+  if (tid < kTB) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
+    for (int i = 0; i < kTB; ++i) {
       float acc = i == j ? 1.0f : 0.0f;
 #pragma unroll
       for (int q = 0; q < i; ++q) acc = fmaf(-D[i][q], x[q], acc);
       x[i] = acc;
     }
 #pragma unroll
-    for (int i = 0; i < 32; ++i) inv[((size_t)b * 32 + i) * 32 + j] = x[i];
+    for (int i = 0; i < kTB; ++i) inv[((size_t)b * kTB + i) * kTB + j] = x[i];
   } else {
 #pragma unroll
-    for (int i = 31; i >= 0; --i) {
+    for (int i = kTB - 1; i >= 0; --i) {
       float acc = i == j ? 1.0f : 0.0f;
 #pragma unroll
-      for (int q = i + 1; q < 32; ++q) acc = fmaf(-D[i][q], x[q], acc);
+      for (int q = i + 1; q < kTB; ++q) acc = fmaf(-D[i][q], x[q], acc);
       x[i] = acc / D[i][i];
     }
 #pragma unroll
-    for (int i = 0; i < 32; ++i) inv[((size_t)(nb + b) * 32 + i) * 32 + j] = x[i];
+    for (int i = 0; i < kTB; ++i) inv[((size_t)(nb + b) * kTB + i) * kTB + j] = x[i];
   }
 }
 
-// Triangular solve by 32-row blocks.  LOWER: unit lower L, blocks in
+// Triangular solve by 64-row blocks.  LOWER: unit lower L, blocks in
 // increasing order; else upper U with its diagonal, blocks in decreasing
-// order.  Block b's eight warps share its dependencies (warp w takes every
-// eighth one); each loads that 32x32 block into registers, waits, with a
-// bounded spin, for the block's flag and adds its product, one row per
-// lane.  Warp 0 then solves the diagonal block (held in registers from the
-// start) and publishes the flag with a release store.
+// order.  Block b's rows form two halves of 32 (warps 0-3 and 4-7, lane =
+// row); the four warps of a half share the block's dependencies in 32-column
+// pieces (warp w takes every fourth, in the order they are solved), each
+// loading its 32x32 piece before waiting, with a bounded spin, for the flag
+// of the 64-row block that piece belongs to.  Warps 0 and 1 then apply the
+// inverse of the diagonal block (its rows held in registers from the start)
+// to the block's right-hand side and publish the flag with a release store.
 template <bool LOWER>
 __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
                                               const float* __restrict__ inv, int n, float* y,
@@ -591,29 +594,30 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
                                               int* err) {
   __shared__ unsigned s_b;
   __shared__ float part[8][32];
-  const int nb = (n + 31) / 32;
+  __shared__ float vsh[kTB];
+  const int nb = (n + kTB - 1) / kTB;
   if (threadIdx.x == 0) s_b = atomicAdd(ticket, 1u);
   __syncthreads();
   const int t = (int)s_b;
   const int b = LOWER ? t : nb - 1 - t;
-  const int row0 = b * 32;
-  const int rows = min(32, n - row0);
+  const int row0 = b * kTB;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int row = row0 + lane;
+  const int h = w >> 2, wq = w & 3;
+  const int row = row0 + 32 * h + lane;
   const float* lrow = LU + (size_t)min(row, n - 1) * n;
-  float acc = 0.0f;
-  const int ndep = LOWER ? b : nb - 1 - b;
-  // warp 0 keeps its row of the diagonal block's inverse in registers
-  float dg[32];
-  if (w == 0) {
-    const float* irow = inv + ((size_t)b * 32 + lane) * 32;
+  // warps 0 and 1 keep their row of the diagonal block's inverse
+  float dg[kTB];
+  if (w < 2) {
+    const float* irow = inv + ((size_t)b * kTB + 32 * w + lane) * kTB;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) dg[j] = irow[j];
+    for (int j = 0; j < kTB; ++j) dg[j] = irow[j];
   }
-  for (int q = w; q < ndep; q += 8) {
-    const int c = LOWER ? q : nb - 1 - q;
-    const int cb = c * 32;
-    // the 32x32 block does not depend on the flag: load it before waiting
+  float acc = 0.0f;
+  const int ns = (n + 31) / 32;   // 32-column pieces of the matrix
+  const int ndep = LOWER ? 2 * b : ns - 2 * (b + 1);
+  for (int q = wq; q < ndep; q += 4) {
+    const int sp = LOWER ? q : ns - 1 - q;
+    const int cb = sp * 32;
     float m[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) m[j] = (row < n && cb + j < n) ? lrow[cb + j] : 0.0f;
@@ -621,7 +625,7 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
       unsigned spins = 0;
       for (;;) {
         unsigned f;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&flags[c]) : "memory");
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&flags[sp >> 1]) : "memory");
         if (f == epoch) break;
         if (++spins > kSpin) {
           atomicExch(err, 1);
@@ -637,25 +641,25 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
   }
   part[w][lane] = acc;
   __syncthreads();
-  if (w == 0) {
-    float v = 0.0f;
-    if (lane < rows) {
-      float sacc = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) sacc += part[k][lane];
-      v = __ldcg(&y[row0 + lane]) - sacc;
-    }
+  if (w < 2) {
+    const int r = row0 + 32 * w + lane;
+    const float sacc = ((part[4 * w][lane] + part[4 * w + 1][lane]) + part[4 * w + 2][lane]) +
+                       part[4 * w + 3][lane];
+    vsh[32 * w + lane] = r < n ? __ldcg(&y[r]) - sacc : 0.0f;
+  }
+  __syncthreads();
+  if (w < 2) {
     // v := (diagonal block)^-1 v, one row of the product per lane
+    const int r = row0 + 32 * w + lane;
     float x = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) x = fmaf(dg[i], __shfl_sync(0xffffffffu, v, i), x);
-    v = x;
-    if (lane < rows) y[row0 + lane] = v;
+    for (int j = 0; j < kTB; ++j) x = fmaf(dg[j], vsh[j], x);
+    if (r < n) y[r] = x;
     __threadfence();
-    __syncwarp();
-    if (lane == 0)
-      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&flags[b]), "r"(epoch) : "memory");
   }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&flags[b]), "r"(epoch) : "memory");
 }
 
 // r = b - A x (binary64), one warp per row; also |A|_inf rows when asked
@@ -883,9 +887,11 @@ cudaError_t launch_lu_iota(int* perm, int n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+size_t lu_diag_inv_bytes(int n) { return (size_t)2 * ((n + kTB - 1) / kTB) * kTB * kTB * 4; }
+
 cudaError_t launch_lu_diag_inv(const float* LU, int n, float* inv, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_lu_diag_inv<<<(n + 31) / 32, 64, 0, s>>>(LU, n, inv);
+  k_lu_diag_inv<<<(n + kTB - 1) / kTB, 2 * kTB, 0, s>>>(LU, n, inv);
   return cudaGetLastError();
 }
 
@@ -894,12 +900,12 @@ cudaError_t launch_lu_solve(const float* LU, const float* inv, int n, const int*
                             unsigned epoch, unsigned* tickets, int* err, cudaStream_t s,
                             Prof* prof) {
   (void)rhs_is_residual;
-  const int nb = (n + 31) / 32;
+  const int nb = (n + kTB - 1) / kTB;
   prof_begin(prof, "lu_trsv", s);
   k_apply_perm<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(rhs, y, n, perm);
   cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s);
   k_trsv<true><<<nb, 256, 0, s>>>(LU, inv, n, y, flags, epoch, tickets, err);
-  k_trsv<false><<<nb, 256, 0, s>>>(LU, inv + (size_t)nb * 1024, n, y, flags + nb, epoch,
+  k_trsv<false><<<nb, 256, 0, s>>>(LU, inv + (size_t)nb * kTB * kTB, n, y, flags + nb, epoch,
                                    tickets + 1, err);
   prof_end(prof, s);
   return cudaGetLastError();

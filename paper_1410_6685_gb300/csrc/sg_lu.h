@@ -36,13 +36,15 @@ cudaError_t launch_lu_trsm_outer(float* LU, int n, int K, int KB, int c0, int c1
 // perm[i] = the row of A that elimination moved to row i
 cudaError_t launch_lu_iota(int* perm, int n, cudaStream_t s);
 // y = U^-1 L^-1 P rhs in binary32 (P rhs gathered through perm).
-// flags: 2*ceil(n/32) words that never hold `epoch` before the call.
+// flags: 2*ceil(n/64) words (or more) that never hold `epoch` before the call.
 cudaError_t launch_lu_solve(const float* LU, const float* inv, int n, const int* perm,
                             const double* rhs, bool rhs_is_residual, float* y, unsigned* flags,
                             unsigned epoch, unsigned* tickets, int* err, cudaStream_t s,
                             Prof* prof);
-// inv: 2 * ceil(n/32) blocks of 32x32 floats: the inverses of the diagonal
-// blocks of L (unit lower) then of U, row-major, for launch_lu_solve
+// inv: lu_diag_inv_bytes(n): 2 * ceil(n/64) blocks of 64x64 floats, the
+// inverses of the diagonal blocks of L (unit lower) then of U, row-major,
+// for launch_lu_solve
+size_t lu_diag_inv_bytes(int n);
 cudaError_t launch_lu_diag_inv(const float* LU, int n, float* inv, cudaStream_t s);
 // r = b - A x in binary64; norms[0] = max|r|; rows with |r_i| > thresh
 // (or NaN) raise ~i into *viol (when viol is not null).

@@ -123,7 +123,7 @@ sg_status lu_factor(sg_ctx* c, const float* A, int n, sg_precision prec) {
     const size_t o_lu = take((size_t)n * n * 4);
     const size_t o_piv = take((size_t)n * 4);
     const size_t o_perm = take((size_t)n * 4);
-    const size_t o_inv = take((size_t)2 * ((n + 31) / 32) * 1024 * 4);
+    const size_t o_inv = take(sgk::lu_diag_inv_bytes(n));
     const size_t o_info = take(64);
     const size_t o_moves = take((size_t)np * sgk::kLuMoveInts * 4 + (size_t)np * 4);
     const size_t o_gemm =
