@@ -201,13 +201,16 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  if (threadIdx.x < 4) {
-    const int p = threadIdx.x;
-    unsigned run = 0;
-    for (int d = 0; d < kRadix; ++d) {
-      h->offs[p][d] = run;
-      run += __ldcg(&h->hist[p][d]);
-    }
+  // per-digit start offsets: one exclusive scan over the block per histogram
+  // (thread d owns digit d)
+  __shared__ unsigned s_warp[kWarps];
+  unsigned c[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) c[p] = __ldcg(&h->hist[p][threadIdx.x]);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    h->offs[p][threadIdx.x] = block_excl_scan(c[p], s_warp);
+    __syncthreads();
   }
   if (threadIdx.x == 0) res->cnt_in = n;
 }
