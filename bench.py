@@ -5,7 +5,7 @@ A step is one pass of the hot path over one batch: sg_sort of 2^26 uniform
 int32 keys (full signed range) with its built-in postconditions
 (Result.is_sorted and Result is a permutation of the input, Listing 4 of the
 paper) fused into the last radix pass, and the flush that reads the contract
-verdict back.  `value` is whole-job GB/s counted as 36 bytes per key (the
+results back.  `value` is whole-job GB/s counted as 36 bytes per key (the
 algorithmic traffic of an 8-bit LSD onesweep sort: one histogram read plus
 four read+write passes).  Inputs are resident in HBM and larger than L2
 (268 MB > 126 MB), so no L2 flush is needed between steps.
