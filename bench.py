@@ -20,8 +20,9 @@ After the headline, rank 0 also reports the other parts of the metric under
 `extras.secondary` (skip with --no-extras): the fused zip + for_all + sum
 stream at n = 2^28 (GB/s, fraction of HBM, contract overhead), the bf16
 tcgen05 GEMM at 8192^2 with its Freivalds postcondition (TFLOP/s, contract
-overhead), GEPP at n = 8192 with refinement, the transpose of 8192^2 and
-the transposed matrix-vector product of Listing 1, and the batch of 10,000
+overhead), GEPP at n = 8192 with refinement, the sort's second variant
+(2^26 keys from 256 distinct values), the transpose of 8192^2 and the
+transposed matrix-vector product of Listing 1, and the batch of 10,000
 collections.
 """
 from __future__ import annotations
@@ -391,6 +392,22 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
     sg.sg_matrix_release(mA)
     sg.sg_vector_release(vb)
     del ta, tb
+
+    # 3b. the sort's second variant: 2^26 keys from 256 distinct values
+    nk = 1 << 26
+    tk = torch.from_numpy(inputs.sort_keys_distinct(nk)).cuda()
+    vk = sg.sg_vector_wrap(ctx, sg.SG_I32, nk, tk.data_ptr())
+
+    def s_sort_distinct():
+        o = sg.sg_sort(ctx, vk)
+        sg.sg_flush(ctx)
+        sg.sg_vector_release(o)
+    ms_d = time_steps(torch, stream, s_sort_distinct, k)
+    out["sort_256_distinct_2e26"] = {
+        "ms": round(ms_d, 4), "GBps": round(36.0 * nk / (ms_d / 1e3) / 1e9, 1),
+        "keys_per_s": round(nk / (ms_d / 1e3), 1), "bytes_per_key": 36}
+    sg.sg_vector_release(vk)
+    del tk
 
     # 4. Listing 1: transpose of 8192^2 (materialised), and A^T x with the
     #    transpose folded into the left product (A read once)

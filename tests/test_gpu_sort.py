@@ -74,6 +74,18 @@ def test_sort_full_size_workload(env):
     assert np.array_equal(got, oracle.sort_i32(keys))
 
 
+def test_sort_full_size_256_distinct(env):
+    """The workload's second variant at full size: 2^26 keys drawn from 256
+    distinct values (long runs of equal digits in every pass).  Bit-exact
+    against the oracle's sort."""
+    n = 1 << 26
+    keys = inputs.sort_keys_distinct(n)
+    v, out, t = run_sort(env, keys)
+    got = read(env, out, n)
+    assert oracle.first_unsorted_i32(got) == -1
+    assert np.array_equal(got, oracle.sort_i32(keys))
+
+
 def test_sort_input_is_not_modified(env):
     keys = inputs.sort_keys_uniform(50_000, seed=3)
     v, out, t = run_sort(env, keys)
