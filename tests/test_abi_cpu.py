@@ -179,3 +179,34 @@ def test_planning_only_context_cannot_execute(sg, pctx):
     with pytest.raises(sg.SgError) as e:
         sg.sg_flush(pctx)
     assert e.value.status == sg.SG_ERR_UNSUPPORTED
+
+
+def test_async_transfers_on_a_planning_context(sg, pctx):
+    """The asynchronous create / read need a device: a planning-only context
+    refuses them with SG_ERR_UNSUPPORTED (nothing is enqueued) and sg_sync
+    has nothing to wait for; bad arguments are rejected first."""
+    import numpy as np
+    host = np.zeros(16, np.float32)
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_vector_create_async(pctx, sg.SG_F32, 16, host)
+    assert e.value.status == sg.SG_ERR_UNSUPPORTED
+    assert sg.lib.sg_vector_create_async(pctx, sg.SG_F32, -1, None, ctypes.byref(ctypes.c_void_p())) \
+        == sg.SG_ERR_INVALID_ARG
+    assert sg.lib.sg_vector_create_async(None, sg.SG_F32, 4, None, ctypes.byref(ctypes.c_void_p())) \
+        == sg.SG_ERR_INVALID_ARG
+    v = vec(sg, pctx, 16)
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_vector_read_async(pctx, v, host)
+    assert e.value.status == sg.SG_ERR_UNSUPPORTED
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_vector_read_async(pctx, v, np.zeros(3, np.float32))
+    assert e.value.status == sg.SG_ERR_SHAPE
+    sg.sg_sync(pctx)
+    assert sg.lib.sg_sync(None) == sg.SG_ERR_INVALID_ARG
+    sg.sg_vector_release(v)
+
+
+def test_portable_switch_arguments(sg, pctx):
+    assert sg.lib.sg_debug_portable_kernels(None, 1) == sg.SG_ERR_INVALID_ARG
+    sg.sg_debug_portable_kernels(pctx, True)
+    sg.sg_debug_portable_kernels(pctx, False)
