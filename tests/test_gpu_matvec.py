@@ -10,7 +10,8 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(1, 1), (7, 13), (64, 64), (65, 127), (1000, 3), (3, 1000), (513, 2048), (2048, 1031), (300, 3076)]
+SHAPES = [(1, 1), (7, 13), (64, 64), (65, 127), (1000, 3), (3, 1000), (513, 2048), (2048, 1031), (300, 3076),
+          (300, 4096), (1000, 5002), (4099, 4608)]
 
 
 @pytest.fixture(scope="module")
@@ -140,3 +141,8 @@ def test_full_size_transpose_and_products_sampled(env):
     sg.sg_vector_release(y)
     ref = oracle.matvec_f64(A[rows], x)
     assert np.all(np.abs(yv[rows] - ref) <= bound(A[rows], x, False))
+    # x^T A at full size (the clustered left product): every entry
+    z = sg.sg_vecmat(ctx, vx, mA)
+    zv = sg.sg_vector_read(ctx, z, np.empty(n, np.float32))
+    sg.sg_vector_release(z)
+    assert np.all(np.abs(zv - oracle.vecmat_f64(x, A)) <= bound(A, x, True))
