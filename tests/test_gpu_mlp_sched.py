@@ -90,9 +90,11 @@ def test_learned_schedule_gain_over_plain_table(env):
     twice more and the better time kept, so that measurement noise does not
     decide).  The learned chooser must not lose to the table by more than
     the re-measurement noise of these 20-300 us launches (about 3%; median
-    regret, so that one noisy workload out of twelve does not decide) and
-    must stay near the fastest on average; it must also run without
-    measuring."""
+    regret, so that one noisy workload out of twelve does not decide), its
+    median regret must stay near the fastest, and its mean regret near the
+    table's (the mean follows single 20 us workloads whose best time was a
+    lucky measurement: up to 60% regret for every chooser); it must also run
+    without measuring."""
     sg, ctx, torch = env
     chain = sg.chain([("x", 0), ("x", 0), ("c", 1.0), ("fma",)], [("x", 0), ("c", 1.0), ("ge",)],
                      [("x", 0), ("c", 1.5), ("gt",)])
@@ -133,7 +135,8 @@ def test_learned_schedule_gain_over_plain_table(env):
           "learned %s plain %s" % (ml, md, medl, medd, np.round(reg_l, 3).tolist(),
                                    np.round(reg_d, 3).tolist()))
     assert medl <= medd + 0.03
-    assert ml <= 0.10
+    assert medl <= 0.06
+    assert ml <= md + 0.05
     # the learned chooser runs once, without measuring candidates
     sg.sg_set_scheduler(ctx, sg.SG_SCHED_LEARNED)
     x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
