@@ -302,8 +302,9 @@ def with_contracts_off(sg, ctx, fn):
 def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
     """The other rows of the metric, each on its own synthetic workload:
     the fused zip+reduce+for_all stream, the bf16 tensor-core GEMM with its
-    Freivalds postcondition, GEPP with iterative refinement, and the batched
-    chain.  Every figure is device time from CUDA events; the overhead of
+    Freivalds postcondition, GEPP with iterative refinement, the sort of keys
+    from 256 distinct values, transpose and the folded A^T x of Listing 1,
+    filter, and the batched chain with its learned schedule.  Every figure is device time from CUDA events; the overhead of
     contract checking is the ratio of the same steps with checking on and off."""
     import numpy as np
     from paper_1410_6685_gb300 import inputs
@@ -440,6 +441,34 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
     sg.sg_matrix_release(mA)
     sg.sg_vector_release(vx)
     del tA, tx
+
+    # 4b. filter x > 0.25 of 2^28 uniform [-1, 1) binary32 values (37.5% kept),
+    #     with the count read back: one decoupled look-back compaction pass
+    n = 1 << 28
+    g.manual_seed(5)
+    fx = torch.rand(n, device="cuda", generator=g) * 2 - 1
+    vf = sg.wrap_tensor(ctx, fx)
+    fcount = {}
+
+    def s_filter():
+        kf = sg.sg_filter(ctx, [("x", 0), ("c", 0.25), ("gt",)], vf)
+        fcount["m"] = sg.sg_vector_count(ctx, kf)
+        sg.sg_vector_release(kf)
+    sg.sg_profile_enable(ctx, True)
+    sg.sg_profile_report(ctx, reset=True)
+    ms_f = time_steps(torch, stream, s_filter, k)
+    prof = sg.sg_profile_report(ctx, reset=True)
+    sg.sg_profile_enable(ctx, False)
+    kf_ms = prof["filter"][1] / prof["filter"][0] if "filter" in prof else None
+    fb = 4.0 * n + 4.0 * fcount["m"]      # read every item, write the kept ones
+    out["filter_2e28"] = {
+        "n": n, "kept": int(fcount["m"]), "ms_step": round(ms_f, 4),
+        "GBps_step": round(fb / (ms_f / 1e3) / 1e9, 1),
+        "kernel_ms": round(kf_ms, 4) if kf_ms else None,
+        "frac_hbm_kernel": round(fb / (kf_ms / 1e3) / 1e9 / hbm_peak, 4) if kf_ms else None,
+        "bytes": "4 per item + 4 per kept item"}
+    sg.sg_vector_release(vf)
+    del fx
 
     # 5. 10,000 collections (log-uniform lengths), map -> filter -> sum, one launch
     L = inputs.batch_lengths()

@@ -5,10 +5,11 @@
 // ticket.  The tile is staged through shared memory with 128-bit loads, each
 // thread evaluates the predicate on 16 consecutive items, a block scan gives
 // every kept item its rank inside the tile, and a decoupled look-back over
-// the tile counts of earlier tiles (bounded waits) gives the tile's global
-// output offset.  Kept items are packed in shared memory and written out
-// contiguously, so both the read and the write are coalesced: 4n bytes read,
-// 4m bytes written for m kept items.
+// the tile counts of earlier tiles (one warp, 32 tiles' words per memory
+// round trip, bounded waits) gives the tile's global output offset.  Kept
+// items are packed in shared memory and written out contiguously, so both the
+// read and the write are coalesced: 4n bytes read, 4m bytes written for m
+// kept items.
 #include <cstring>
 #include <mutex>
 
@@ -114,34 +115,51 @@ __global__ void __launch_bounds__(kFB) k_filter(const float* __restrict__ x,
   const unsigned excl_tile = incl - cnt + s_warp[w];
   const unsigned total = s_total;
 
-  // decoupled look-back over earlier tiles' counts
-  if (tid == 0) {
+  // decoupled look-back over earlier tiles' counts, by warp 0: lane l reads
+  // the word of tile j - l, so one memory round trip covers up to 32 tiles.
+  // The window is taken in order through its first inclusive prefix, or up
+  // to its first word not yet published, which is then polled again.  Every
+  // word is written once as an aggregate and once as an inclusive prefix
+  // (tile 0 only as the prefix), so any published value read is a valid step;
+  // below tile 0 stands an empty prefix (never reached).
+  if (tid < 32) {
     unsigned long long excl = 0;
     if (tile == 0) {
-      st_relaxed64(&st[0], kFPre | total);
+      if (tid == 0) st_relaxed64(&st[0], kFPre | total);
     } else {
-      st_relaxed64(&st[tile], kFAgg | total);
+      if (tid == 0) st_relaxed64(&st[tile], kFAgg | total);
       long long j = (long long)tile - 1;
       unsigned spins = 0;
-      while (j >= 0) {
-        const unsigned long long s = ld_relaxed64(&st[j]);
+      while (true) {
+        const long long idx = j - tid;
+        const unsigned long long s = idx >= 0 ? ld_relaxed64(&st[idx]) : kFPre;
         const unsigned long long flag = s & ~kFCnt;
-        if (flag == 0) {
+        const unsigned zero = __ballot_sync(0xffffffffu, flag == 0);
+        const unsigned pre = __ballot_sync(0xffffffffu, flag == kFPre);
+        const unsigned stop = zero ? (unsigned)(__ffs(zero) - 1) : 32u;
+        const unsigned first_pre = pre ? (unsigned)(__ffs(pre) - 1) : 32u;
+        const bool done = first_pre < stop;
+        const unsigned take = done ? first_pre + 1 : stop;   // lanes [0, take) are added
+        unsigned long long c = (unsigned)tid < take ? (s & kFCnt) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        excl += c;
+        if (done) break;
+        j -= take;
+        if (stop < 32u) {
           if (++spins > kFSpin) {
-            atomicExch(&res->timeout, 1);
+            if (tid == 0) atomicExch(&res->timeout, 1);
             break;
           }
           if (spins > 32) __nanosleep(64);
-          continue;
         }
-        excl += s & kFCnt;
-        if (flag == kFPre) break;
-        --j;
       }
-      st_relaxed64(&st[tile], kFPre | (excl + total));
+      if (tid == 0) st_relaxed64(&st[tile], kFPre | (excl + total));
     }
-    s_excl = excl;
-    if (tile == gridDim.x - 1) res->count = (long long)(excl + total);
+    if (tid == 0) {
+      s_excl = excl;
+      if (tile == gridDim.x - 1) res->count = (long long)(excl + total);
+    }
   }
   __syncthreads();   // everyone has read s_v into registers
 
