@@ -459,12 +459,13 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
     ms_f = time_steps(torch, stream, s_filter, k)
     prof = sg.sg_profile_report(ctx, reset=True)
     sg.sg_profile_enable(ctx, False)
-    kf_ms = prof["filter"][1] / prof["filter"][0] if "filter" in prof else None
+    fk = "filter_jit" if "filter_jit" in prof else "filter"
+    kf_ms = prof[fk][1] / prof[fk][0] if fk in prof else None
     fb = 4.0 * n + 4.0 * fcount["m"]      # read every item, write the kept ones
     out["filter_2e28"] = {
         "n": n, "kept": int(fcount["m"]), "ms_step": round(ms_f, 4),
         "GBps_step": round(fb / (ms_f / 1e3) / 1e9, 1),
-        "kernel_ms": round(kf_ms, 4) if kf_ms else None,
+        "kernel": fk, "kernel_ms": round(kf_ms, 4) if kf_ms else None,
         "frac_hbm_kernel": round(fb / (kf_ms / 1e3) / 1e9 / hbm_peak, 4) if kf_ms else None,
         "bytes": "4 per item + 4 per kept item"}
     sg.sg_vector_release(vf)

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "sg_eval.cuh"
+#include "sg_jit.h"
 
 namespace sgk {
 namespace {
@@ -208,6 +209,44 @@ cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& p
   return cudaGetLastError();
 }
 
+cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out, long long n,
+                                      const Prog& pred, void* scratch, FilterResult* res,
+                                      cudaStream_t s, int num_sms, int64_t* kernels,
+                                      Prof* prof) {
+  // the scratch is sized for the interpreting kernel's tiles: one look-back
+  // word per tile of kFTile items covers the larger tiles here
+  static_assert(kJitFilterTile % kFTile == 0, "the two filters share the scratch");
+  if (n <= 0) return cudaSuccess;
+  const unsigned ntiles = (unsigned)((n + kJitFilterTile - 1) / kJitFilterTile);
+  FilterHdr* h = static_cast<FilterHdr*>(scratch);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, filter_scratch_bytes(n), s);
+  if (e != cudaSuccess) return e;
+  const void* fn = reinterpret_cast<const void*>(k);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJitFilterSmem);
+  int occ = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFB, kJitFilterSmem);
+  if (e != cudaSuccess) return e;
+  // persistent: every CTA resident at once (tiles are taken from a ticket,
+  // so a CTA that is not resident yet holds none)
+  const long long cap = (long long)(num_sms > 0 ? num_sms : 1) * (occ > 0 ? occ : 1);
+  const int grid = (int)(ntiles < cap ? ntiles : cap);
+  FilterJitArgs a{};
+  a.x = x;
+  a.out = out;
+  a.n = n;
+  for (int i = 0; i < kMaxProg; ++i) a.cst[i] = pred.cst[i];
+  a.st = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + sizeof(FilterHdr));
+  a.tile_ctr = &h->tile_ctr;
+  a.res = res;
+  a.ntiles = ntiles;
+  void* args[] = {&a};
+  prof_begin(prof, "filter_jit", s);
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(kFB), args, kJitFilterSmem, s);
+  prof_end(prof, s);
+  *kernels += 1;
+  return e;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free filter.  Some callers cannot allocate device memory: a

@@ -152,5 +152,10 @@ cudaError_t launch_filter(const float* x, float* out, long long n,
                           const Prog& pred, int pred_depth, void* scratch,
                           FilterResult* res, cudaStream_t s, int num_sms,
                           int64_t* kernels, Prof* prof);
+// the same filter through its run-time specialised kernel (sg_jit.h)
+cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out, long long n,
+                                      const Prog& pred, void* scratch, FilterResult* res,
+                                      cudaStream_t s, int num_sms, int64_t* kernels,
+                                      Prof* prof);
 
 }  // namespace sgk

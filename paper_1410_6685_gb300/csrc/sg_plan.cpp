@@ -729,10 +729,18 @@ sg_status sg_execute_pending(sg_ctx* c) {
           pr.cst[p] = ops[p].cst;
           pr.depth[p] = before[p];
         }
-        e = sgk::launch_filter(static_cast<const float*>(x->st->ptr),
-                               static_cast<float*>(n->out->st->ptr), P.n, pr, md, dwork,
-                               static_cast<sgk::FilterResult*>(rec), c->stream, c->num_sms,
-                               &c->kernels, &c->prof);
+        cudaKernel_t jk = c->codegen == SG_CODEGEN_SPECIALIZE ? sgk::jit_filter_kernel(pr, nullptr)
+                                                              : nullptr;
+        if (jk)
+          e = sgk::launch_filter_specialised(jk, static_cast<const float*>(x->st->ptr),
+                                             static_cast<float*>(n->out->st->ptr), P.n, pr, dwork,
+                                             static_cast<sgk::FilterResult*>(rec), c->stream,
+                                             c->num_sms, &c->kernels, &c->prof);
+        else
+          e = sgk::launch_filter(static_cast<const float*>(x->st->ptr),
+                                 static_cast<float*>(n->out->st->ptr), P.n, pr, md, dwork,
+                                 static_cast<sgk::FilterResult*>(rec), c->stream, c->num_sms,
+                                 &c->kernels, &c->prof);
         break;
       }
       case PK::SORT: {

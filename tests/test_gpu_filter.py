@@ -91,3 +91,65 @@ def test_filter_then_chain(env):
     z = sg.sg_map(ctx, [("x", 0), ("neg",)], k)
     out = sg.sg_vector_read(ctx, z, np.empty(m, f32))
     assert np.array_equal(out, -kept)
+
+
+def kernels_of(env, fn):
+    """Names of the library kernels that ran during fn()."""
+    sg, ctx, _ = env
+    sg.sg_profile_enable(ctx, True)
+    sg.sg_profile_report(ctx, reset=True)
+    try:
+        fn()
+        return set(sg.sg_profile_report(ctx, reset=True))
+    finally:
+        sg.sg_profile_enable(ctx, False)
+
+
+@pytest.mark.parametrize("codegen", ["specialize", "interpret"])
+@pytest.mark.parametrize("n", [5, 4096, 12 * 4096 + 77, 700_001])
+def test_filter_both_kernels(env, codegen, n):
+    """The run-time specialised (persistent, bulk-copy staged) filter and the
+    interpreting one keep the same items in the same order as the oracle."""
+    sg, ctx, _ = env
+    sg.sg_set_codegen(ctx, sg.SG_CODEGEN_SPECIALIZE if codegen == "specialize"
+                      else sg.SG_CODEGEN_INTERPRET)
+    try:
+        x = inputs.uniform_pm1(inputs.rng(3 * n + 1), n)
+        pred = PREDS[2]
+        box = {}
+        names = kernels_of(env, lambda: box.update(got=run_filter(env, x, pred)[0]))
+        assert ("filter_jit" if codegen == "specialize" else "filter") in names
+        ref = oracle.filter(pred, x)
+        assert np.array_equal(box["got"].view(np.uint32), ref.view(np.uint32))
+    finally:
+        sg.sg_set_codegen(ctx, sg.SG_CODEGEN_SPECIALIZE)
+
+
+@pytest.mark.parametrize("n", [4096 * 9 + 3, 333_333])
+def test_filter_unaligned_input(env, n):
+    """An input that starts 4 bytes past a 16-byte boundary: every tile is
+    loaded with plain loads instead of bulk copies."""
+    sg, ctx, torch = env
+    x = inputs.uniform_pm1(inputs.rng(n), n + 1)
+    t = torch.from_numpy(x).cuda()
+    v = sg.sg_vector_wrap(ctx, sg.SG_F32, n, t.data_ptr() + 4)
+    pred = PREDS[0]
+    k = sg.sg_filter(ctx, pred, v)
+    m = sg.sg_vector_count(ctx, k)
+    got = sg.sg_vector_read(ctx, k, np.empty(m, f32))
+    ref = oracle.filter(pred, x[1:])
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_filter_nan_and_signed_zero(env):
+    """NaN items fail `x > c` and pass `x != x`; -0.0 and +0.0 are both kept by
+    `x == 0` and keep their sign bits."""
+    base = inputs.uniform_pm1(inputs.rng(77), 50_000)
+    base[::7] = np.nan
+    base[3::11] = -0.0
+    base[5::13] = 0.0
+    for pred in ([("x", 0), ("c", 0.25), ("gt",)], [("x", 0), ("x", 0), ("ne",)],
+                 [("x", 0), ("c", 0.0), ("eq",)]):
+        got, _ = run_filter(env, base, pred)
+        ref = oracle.filter(pred, base)
+        assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
