@@ -221,16 +221,9 @@ cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out
   FilterHdr* h = static_cast<FilterHdr*>(scratch);
   cudaError_t e = cudaMemsetAsync(scratch, 0, filter_scratch_bytes(n), s);
   if (e != cudaSuccess) return e;
+  (void)num_sms;   // one CTA per tile
   const void* fn = reinterpret_cast<const void*>(k);
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJitFilterSmem);
-  int occ = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFB, kJitFilterSmem);
-  if (e != cudaSuccess) return e;
-  // persistent: every CTA resident at once (tiles are taken from a ticket,
-  // so a CTA that is not resident yet holds none)
-  const long long cap = (long long)(num_sms > 0 ? num_sms : 1) * (occ > 0 ? occ : 1);
-  const int grid = (int)(ntiles < cap ? ntiles : cap);
+  const int grid = (int)ntiles;
   FilterJitArgs a{};
   a.x = x;
   a.out = out;
@@ -242,7 +235,7 @@ cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out
   a.ntiles = ntiles;
   void* args[] = {&a};
   prof_begin(prof, "filter_jit", s);
-  e = cudaLaunchKernel(fn, dim3(grid), dim3(kFB), args, kJitFilterSmem, s);
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(kFB), args, 0, s);
   prof_end(prof, s);
   *kernels += 1;
   return e;

@@ -58,11 +58,8 @@ struct FilterJitArgs {
   int pad;
 };
 static_assert(sizeof(FilterJitArgs) == 248, "FilterJitArgs layout changed: update the template");
-// tile of the specialised filter (items), its pipeline depth, and the bytes
-// of dynamic shared memory it needs
+// tile of the specialised filter (items); its shared memory is static
 constexpr int kJitFilterTile = 8192;
-constexpr int kJitFilterStages = 2;
-constexpr size_t kJitFilterSmem = (size_t)kJitFilterStages * kJitFilterTile * 4 + 64;
 
 bool jit_available();
 // minmax: the pass also tracks min / max / NaN (a min, max or avg is asked)
@@ -70,8 +67,8 @@ cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, boo
                                bool minmax, uint32_t pred_exists, std::string* log);
 // the batched map -> for_all -> masked sum chain of one program (k_batch.cu)
 cudaKernel_t jit_batch_kernel(const Prog& pr, std::string* log);
-// the stable compaction of one predicate (one input slot), persistent, with
-// bulk-copy staged tiles (k_filter.cu launches it)
+// the stable compaction of one predicate (one input slot), one CTA per
+// 8192-item tile (k_filter.cu launches it)
 cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log);
 cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,
                               cudaStream_t st, Prof* prof);

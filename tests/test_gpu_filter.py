@@ -108,8 +108,9 @@ def kernels_of(env, fn):
 @pytest.mark.parametrize("codegen", ["specialize", "interpret"])
 @pytest.mark.parametrize("n", [5, 4096, 12 * 4096 + 77, 700_001])
 def test_filter_both_kernels(env, codegen, n):
-    """The run-time specialised (persistent, bulk-copy staged) filter and the
-    interpreting one keep the same items in the same order as the oracle."""
+    """The run-time specialised filter (one CTA per 8192-item tile) and the
+    interpreting one (4096-item tiles) keep the same items in the same order
+    as the oracle."""
     sg, ctx, _ = env
     sg.sg_set_codegen(ctx, sg.SG_CODEGEN_SPECIALIZE if codegen == "specialize"
                       else sg.SG_CODEGEN_INTERPRET)
@@ -128,7 +129,7 @@ def test_filter_both_kernels(env, codegen, n):
 @pytest.mark.parametrize("n", [4096 * 9 + 3, 333_333])
 def test_filter_unaligned_input(env, n):
     """An input that starts 4 bytes past a 16-byte boundary: every tile is
-    loaded with plain loads instead of bulk copies."""
+    loaded with 4-byte loads instead of 16-byte ones."""
     sg, ctx, torch = env
     x = inputs.uniform_pm1(inputs.rng(n), n + 1)
     t = torch.from_numpy(x).cuda()
