@@ -417,16 +417,27 @@ typedef enum { SG_SCHED_AUTOTUNE = 0, SG_SCHED_LEARNED = 1 } sg_sched;
 sg_status sg_set_scheduler(sg_ctx* ctx, sg_sched s);
 
 /* Code generation for fused element-wise passes (Sec. 5 generates a kernel
- * per plan).  SG_CODEGEN_SPECIALIZE (default): the fused program is compiled
- * once per program structure into straight-line code inside the streaming
- * kernel template (NVRTC, sm_103a) and cached for the process;
- * SG_CODEGEN_INTERPRET: the precompiled streaming kernel evaluates the
- * program.  Both give identical results.  SG_ERR_UNSUPPORTED if
+ * per plan).  SG_CODEGEN_SPECIALIZE (default): the fused program (and a
+ * filter's predicate) is compiled once per program structure into
+ * straight-line code inside the streaming (or filter) kernel template
+ * (NVRTC, sm_103a) and cached for the process; a program whose kernel does
+ * not compile is interpreted instead.  SG_CODEGEN_INTERPRET: the
+ * precompiled kernels evaluate the program.  Both give identical results.  SG_ERR_UNSUPPORTED if
  * specialisation was requested but NVRTC cannot be loaded (the context keeps
  * interpreting).  The environment variable SG_CODEGEN=interpret sets the
  * default of new contexts. */
 typedef enum { SG_CODEGEN_INTERPRET = 0, SG_CODEGEN_SPECIALIZE = 1 } sg_codegen;
 sg_status sg_set_codegen(sg_ctx* ctx, sg_codegen g);
+
+/* Compiles, and only compiles, the run-time specialised filter kernel of
+ * `pred` (a predicate over slot 0, as for sg_filter) with NVRTC for sm_103a;
+ * nothing is loaded, so no GPU is needed.  SG_OK when it compiles;
+ * SG_ERR_UNSUPPORTED when NVRTC cannot be loaded or the compile fails (the
+ * reason or the compiler's log, truncated to cap - 1 bytes and terminated,
+ * goes to `log` unless it is NULL); SG_ERR_INVALID_ARG for a malformed
+ * predicate.  A predicate whose kernel does not compile still filters
+ * correctly: sg_filter then uses the interpreting kernel. */
+sg_status sg_debug_jit_check_filter(const sg_expr* pred, char* log, size_t cap);
 
 /* Writes a one-line-per-kernel description of what sg_flush would launch
  * for the currently queued work (no execution; works on a planning-only

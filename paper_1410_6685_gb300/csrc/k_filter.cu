@@ -268,15 +268,14 @@ void* g_noalloc_ptr[kNoAllocMaxDevices];   // device address of the array, per d
 }  // namespace
 }  // namespace sgk
 
-extern "C" sg_status sg_filter_noalloc(const sg_expr* pred, const float* dev_x, int64_t n,
-                                       float* dev_out, int64_t* dev_count, void* stream) {
-  using namespace sgk;
-  if (!pred || n < 0 || (n > 0 && (!dev_x || !dev_out)) || !dev_count) return SG_ERR_INVALID_ARG;
-  if (n > SG_FILTER_NOALLOC_MAX_N) return SG_ERR_SHAPE;
-  // the predicate: one input slot, checked and given its stack depths here
-  if (pred->nops <= 0 || pred->nops > SG_MAX_EXPR_OPS) return SG_ERR_INVALID_ARG;
-  Prog pr;
-  memset(&pr, 0, sizeof pr);
+namespace sgk {
+namespace {
+
+// the program of a filter predicate over input slot 0, with its stack
+// depths; SG_ERR_INVALID_ARG when it is malformed
+sg_status filter_prog(const sg_expr* pred, Prog* pr, int* max_depth) {
+  if (!pred || pred->nops <= 0 || pred->nops > SG_MAX_EXPR_OPS) return SG_ERR_INVALID_ARG;
+  memset(pr, 0, sizeof *pr);
   int d = 0, md = 0;
   for (int p = 0; p < pred->nops; ++p) {
     const int op = pred->ops[p].op;
@@ -297,16 +296,52 @@ extern "C" sg_status sg_filter_noalloc(const sg_expr* pred, const float* dev_x, 
         delta = -1;
     }
     if (d < need) return SG_ERR_INVALID_ARG;
-    pr.op[p] = (uint8_t)op;
-    pr.arg[p] = 0;
-    pr.cst[p] = pred->ops[p].value;
-    pr.depth[p] = (uint8_t)d;
+    pr->op[p] = (uint8_t)op;
+    pr->arg[p] = 0;
+    pr->cst[p] = pred->ops[p].value;
+    pr->depth[p] = (uint8_t)d;
     d += delta;
     md = d > md ? d : md;
     if (md > SG_MAX_EXPR_DEPTH) return SG_ERR_INVALID_ARG;
   }
   if (d != 1) return SG_ERR_INVALID_ARG;
-  pr.nops = pred->nops;
+  pr->nops = pred->nops;
+  *max_depth = md;
+  return SG_OK;
+}
+
+}  // namespace
+}  // namespace sgk
+
+extern "C" sg_status sg_debug_jit_check_filter(const sg_expr* pred, char* log, size_t cap) {
+  using namespace sgk;
+  if (log && cap > 0) log[0] = '\0';
+  Prog pr;
+  int md = 0;
+  const sg_status st = filter_prog(pred, &pr, &md);
+  if (st != SG_OK) return st;
+  std::string l;
+  if (jit_check_filter(pr, &l)) return SG_OK;
+  if (log && cap > 0) {
+    const size_t k = l.size() < cap - 1 ? l.size() : cap - 1;
+    memcpy(log, l.data(), k);
+    log[k] = '\0';
+  }
+  return SG_ERR_UNSUPPORTED;
+}
+
+extern "C" sg_status sg_filter_noalloc(const sg_expr* pred, const float* dev_x, int64_t n,
+                                       float* dev_out, int64_t* dev_count, void* stream) {
+  using namespace sgk;
+  if (!pred || n < 0 || (n > 0 && (!dev_x || !dev_out)) || !dev_count) return SG_ERR_INVALID_ARG;
+  if (n > SG_FILTER_NOALLOC_MAX_N) return SG_ERR_SHAPE;
+  // the predicate: one input slot, checked and given its stack depths here
+  Prog pr;
+  int md = 0;
+  {
+    const sg_status st = filter_prog(pred, &pr, &md);
+    if (st != SG_OK) return st;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // set-up, once per device, with that device current: the array's device

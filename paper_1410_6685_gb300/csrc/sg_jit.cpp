@@ -531,7 +531,7 @@ extern "C" __global__ void __launch_bounds__(256, 4) sg_filter(const FilterJitAr
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const unsigned bit = (keep >> (4 * q + l)) & 1u;
-      *(bit ? s_pack + r : s_spare + tid) = v[4 * q + l];
+      *(bit ? s_pack + r : s_spare + tid) = v[4 * q + l];   // no predicated store
       r += bit;
     }
   }
@@ -791,14 +791,18 @@ cudaKernel_t jit_batch_kernel(const Prog& pr, std::string* log) {
   return compile_cached(src, "sg_batch", log);
 }
 
-cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log) {
+namespace {
+
+// the source of the specialised filter for `pred`; false (with a reason in
+// *log) when it cannot be specialised
+bool filter_source(const Prog& pred, std::string* src, std::string* log) {
   if (!nvrtc().ok) {
     if (log) *log = "NVRTC library not found";
-    return nullptr;
+    return false;
   }
   if (pred.nops <= 0 || pred.nops >= kMaxProg) {
     if (log) *log = "program could not be specialised";
-    return nullptr;
+    return false;
   }
   // the predicate's value is the program's result: a trailing reduce sink
   // hands it to the template as rv
@@ -810,11 +814,41 @@ cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log) {
   std::string body;
   if (!gen_body(pr, 0u, &body)) {
     if (log) *log = "program could not be specialised";
-    return nullptr;
+    return false;
   }
-  const std::string src =
-      std::string("#define SG_MINMAX 0\n") + kTemplateHead + body_fn(body) + kTemplateFilter;
+  *src = std::string("#define SG_MINMAX 0\n") + kTemplateHead + body_fn(body) + kTemplateFilter;
+  return true;
+}
+
+}  // namespace
+
+cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log) {
+  std::string src;
+  if (!filter_source(pred, &src, log)) return nullptr;
   return compile_cached(src, "sg_filter", log);
+}
+
+bool jit_check_filter(const Prog& pred, std::string* log) {
+  std::string src;
+  if (!filter_source(pred, &src, log)) return false;
+  Nvrtc& nv = nvrtc();
+  void* prog = nullptr;
+  if (nv.create(&prog, src.c_str(), "sg_filter.cu", 0, nullptr, nullptr) != 0) {
+    if (log) *log = "NVRTC could not create the program";
+    return false;
+  }
+  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-default-device",
+                        "-fmad=false"};
+  const bool ok = nv.compile(prog, 4, opts) == 0;
+  if (!ok && log) {
+    size_t ls = 0;
+    nv.log_size(prog, &ls);
+    std::string l(ls, '\0');
+    nv.log(prog, &l[0]);
+    *log = l;
+  }
+  nv.destroy(&prog);
+  return ok;
 }
 
 cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,

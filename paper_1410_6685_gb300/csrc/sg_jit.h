@@ -70,6 +70,9 @@ cudaKernel_t jit_batch_kernel(const Prog& pr, std::string* log);
 // the stable compaction of one predicate (one input slot), one CTA per
 // 8192-item tile (k_filter.cu launches it)
 cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log);
+// compiles that kernel's source with NVRTC without loading it (no device
+// needed); false with the compiler's log when it does not compile
+bool jit_check_filter(const Prog& pred, std::string* log);
 cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,
                               cudaStream_t st, Prof* prof);
 

@@ -142,6 +142,7 @@ def _load():
         "sg_kernel_count": [vp, P(i64)], "sg_profile_enable": [vp, i32], "sg_profile_report": [vp, C.c_char_p, sz, P(sz), i32], "sg_debug_inject_sort": [vp, i32, i64, i64], "sg_debug_inject_matmul": [vp, i64, i64, C.c_float], "sg_debug_portable_kernels": [vp, i32],
         "sg_batch_run": [vp, P(SgChain), vp, vp, i64, vp, vp, vp],
         "sg_filter_noalloc": [P(SgExpr), vp, i64, vp, vp, vp],
+        "sg_debug_jit_check_filter": [P(SgExpr), C.c_char_p, sz],
         "sg_batch_report": [vp, P(SgChain), vp, vp, i64, vp, vp, vp, P(SgSchedReport)],
         "sg_sched_train": [vp, i32, C.c_float, C.c_uint64, P(C.c_float)],
         "sg_sched_log_size": [vp, P(i64), P(C.c_int32)],
@@ -522,6 +523,15 @@ SG_CODEGEN_INTERPRET, SG_CODEGEN_SPECIALIZE = 0, 1
 
 def sg_set_codegen(ctx, g):
     _check(lib.sg_set_codegen(ctx, g), ctx)
+
+
+def sg_debug_jit_check_filter(pred):
+    """Compile (only) the specialised filter kernel of `pred` with NVRTC.
+    Returns (status, log): status 0 when it compiles."""
+    e = expr(pred)
+    buf = C.create_string_buffer(1 << 14)
+    st = lib.sg_debug_jit_check_filter(C.byref(e), buf, len(buf))
+    return int(st), buf.value.decode(errors="replace")
 
 
 SG_FILTER_NOALLOC_MAX_N = 1 << 28
