@@ -106,7 +106,7 @@ def kernels_of(env, fn):
 
 
 @pytest.mark.parametrize("codegen", ["specialize", "interpret"])
-@pytest.mark.parametrize("n", [5, 4096, 12 * 4096 + 77, 700_001])
+@pytest.mark.parametrize("n", [5, 4096, 8192, 8193, 3 * 8192, 12 * 4096 + 77, 700_001])
 def test_filter_both_kernels(env, codegen, n):
     """The run-time specialised filter (one CTA per 8192-item tile) and the
     interpreting one (4096-item tiles) keep the same items in the same order
