@@ -373,6 +373,8 @@ extern "C" sg_status sg_filter_noalloc(const sg_expr* pred, const float* dev_x, 
   cudaError_t e = cudaMemsetAsync(res, 0, sizeof(FilterResult), s);
   if (e == cudaSuccess && n > 0) {
     int64_t kernels = 0;
+    // the interpreting kernel: the specialised one would need a module
+    // load, which allocates device memory
     e = launch_filter(dev_x, dev_out, n, pr, md, scratch, res, s, 0, &kernels, nullptr);
   }
   if (e == cudaSuccess)
