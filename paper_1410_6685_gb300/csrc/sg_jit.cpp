@@ -421,9 +421,10 @@ extern "C" __global__ void __launch_bounds__(256) sg_batch(const BatchJitArgs a)
 // once, every warp packs its kept items into shared memory (unpredicated
 // stores), warp 0 does the decoupled look-back over the tiles' words, 32
 // tiles per memory round trip, and the packed items are written out
-// contiguously.  Four CTAs per SM (64 registers).  Measured at 2^28 items:
-// 0.49 ms, against 0.55 ms at three CTAs per SM (80 registers), 0.57 ms with
-// 512 threads of 16 items, 0.65 ms with 4096-item tiles, 0.71 / 0.85 ms with
+// contiguously.  Five CTAs per SM (48 registers, a few spilled).  Measured
+// at 2^28 items: 0.41 ms, against 0.48 / 0.49 / 0.55 ms at six / four / three
+// CTAs per SM (40 / 64 / 80 registers), 0.57 ms with 512 threads of 16
+// items, 0.65 ms with 4096-item tiles, 0.71 / 0.85 ms with
 // 64- / 128-tile look-back windows (more words re-polled while a predecessor
 // is unpublished), and 0.92 ms for a persistent form prefetching its next
 // tile by bulk copy (its tickets run ahead of the tiles it is still working
@@ -450,7 +451,7 @@ __device__ __forceinline__ void sg_st_relaxed(unsigned long long* p, unsigned lo
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-extern "C" __global__ void __launch_bounds__(256, 4) sg_filter(const FilterJitArgs a) {
+extern "C" __global__ void __launch_bounds__(256, 5) sg_filter(const FilterJitArgs a) {
   __shared__ __align__(16) float s_pack[SG_FT];
   __shared__ float s_spare[256];
   __shared__ unsigned s_cnt[SG_FQ * 8];
