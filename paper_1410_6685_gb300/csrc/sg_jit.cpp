@@ -482,7 +482,7 @@ extern "C" __global__ void __launch_bounds__(256, 5) sg_filter(const FilterJitAr
         v[4 * q + l] = li < valid ? a.x[base + li] : 0.0f;
       }
   }
-  // predicate on the thread's 16 items, masked to the valid ones
+  // predicate on the thread's 32 items, masked to the valid ones
   unsigned keep = 0, vmask = 0;
 #pragma unroll
   for (int q = 0; q < SG_FQ; ++q) {
