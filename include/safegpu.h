@@ -593,9 +593,19 @@ sg_status sg_mlp_adam(sg_ctx* ctx, float* params, const float* grad, float* m,
  *               call waits for the stream before it returns
  * Errors: n > SG_FILTER_NOALLOC_MAX_N (2^28) gives SG_ERR_SHAPE; a malformed
  * predicate or a null buffer SG_ERR_INVALID_ARG; a look-back wait that gave
- * up SG_ERR_TIMEOUT; a CUDA failure SG_ERR_CUDA.
+ * up SG_ERR_TIMEOUT, with *dev_count set to -1 (the kept items written so far
+ * are not a result); a CUDA failure SG_ERR_CUDA.
  * The first call on each device looks up the array's device address, with
  * that device current: make that first call before any stream capture.
+ * Loading is the one exception to "allocates nothing": under CUDA's default
+ * lazy module loading, that first call loads the library's device code on
+ * the device, and the loader then takes the array's 513 KB (and the code's
+ * own memory) from the device; the first call with a predicate whose stack
+ * is deeper than 4 loads a second kernel the same way.  A caller that is
+ * about to reserve all of HBM should make one call with a shallow and one
+ * with a deep predicate first (or run with CUDA_MODULE_LOADING=EAGER, which
+ * loads everything when the process starts); after that no call takes
+ * device memory.
  * All calls on a device share the one array, which keeps the last call's
  * contents (each call clears what it needs first): calls whose GPU work
  * overlaps -- from several host threads or streams -- race on it, so the

@@ -272,41 +272,18 @@ namespace sgk {
 namespace {
 
 // the program of a filter predicate over input slot 0, with its stack
-// depths; SG_ERR_INVALID_ARG when it is malformed
+// depths; SG_ERR_INVALID_ARG when it is malformed (the library's one
+// expression validator, as sg_filter uses)
 sg_status filter_prog(const sg_expr* pred, Prog* pr, int* max_depth) {
-  if (!pred || pred->nops <= 0 || pred->nops > SG_MAX_EXPR_OPS) return SG_ERR_INVALID_ARG;
   memset(pr, 0, sizeof *pr);
-  int d = 0, md = 0;
+  const sg_status st = validate_expr(pred, 1, max_depth, pr->depth, nullptr, 0);
+  if (st != SG_OK) return st;
   for (int p = 0; p < pred->nops; ++p) {
-    const int op = pred->ops[p].op;
-    int need = 0, delta = 0;
-    switch (op) {
-      case SG_OP_LOAD:
-        if (pred->ops[p].arg != 0) return SG_ERR_INVALID_ARG;
-        delta = 1;
-        break;
-      case SG_OP_CONST: case SG_OP_INDEX: delta = 1; break;
-      case SG_OP_FMA: case SG_OP_SELECT: need = 3; delta = -2; break;
-      case SG_OP_NEG: case SG_OP_ABS: case SG_OP_SQRT: case SG_OP_NOT: need = 1; break;
-      case SG_OP_DUP: need = 1; delta = 1; break;
-      case SG_OP_SWAP: need = 2; break;
-      default:
-        if (op < SG_OP_ADD || op > SG_OP_INDEX) return SG_ERR_INVALID_ARG;
-        need = 2;
-        delta = -1;
-    }
-    if (d < need) return SG_ERR_INVALID_ARG;
-    pr->op[p] = (uint8_t)op;
+    pr->op[p] = (uint8_t)pred->ops[p].op;
     pr->arg[p] = 0;
     pr->cst[p] = pred->ops[p].value;
-    pr->depth[p] = (uint8_t)d;
-    d += delta;
-    md = d > md ? d : md;
-    if (md > SG_MAX_EXPR_DEPTH) return SG_ERR_INVALID_ARG;
   }
-  if (d != 1) return SG_ERR_INVALID_ARG;
   pr->nops = pred->nops;
-  *max_depth = md;
   return SG_OK;
 }
 
@@ -383,6 +360,11 @@ extern "C" sg_status sg_filter_noalloc(const sg_expr* pred, const float* dev_x, 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&h, res, sizeof h, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && h.timeout) {
+    // the count of a compaction whose look-back gave up is not a count
+    e = cudaMemsetAsync(dev_count, 0xff, sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return SG_ERR_CUDA;

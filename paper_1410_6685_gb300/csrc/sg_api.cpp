@@ -111,42 +111,9 @@ sg_status alloc_storage(sg_ctx* c, size_t bytes, std::shared_ptr<Storage>* out) 
 
 // Validates a user expression over `nin` input slots; returns its max depth.
 sg_status check_expr(sg_ctx* c, const sg_expr* f, int nin, int* depth_out) {
-  if (!f) return fail(c, SG_ERR_INVALID_ARG, "null expression");
-  if (f->nops <= 0 || f->nops > SG_MAX_EXPR_OPS)
-    return fail(c, SG_ERR_INVALID_ARG, "expression has %d ops (1..%d allowed)", f->nops,
-                SG_MAX_EXPR_OPS);
-  int d = 0, mx = 0;
-  for (int p = 0; p < f->nops; ++p) {
-    const sg_expr_op& o = f->ops[p];
-    int need = 0, delta = 0;
-    switch (o.op) {
-      case SG_OP_LOAD:
-        if (o.arg < 0 || o.arg >= nin)
-          return fail(c, SG_ERR_INVALID_ARG, "op %d loads slot %d of %d", p, o.arg, nin);
-        delta = 1;
-        break;
-      case SG_OP_CONST: case SG_OP_INDEX: delta = 1; break;
-      case SG_OP_ADD: case SG_OP_SUB: case SG_OP_MUL: case SG_OP_DIV: case SG_OP_MIN:
-      case SG_OP_MAX: case SG_OP_LT: case SG_OP_LE: case SG_OP_GT: case SG_OP_GE:
-      case SG_OP_EQ: case SG_OP_NE: case SG_OP_AND: case SG_OP_OR:
-        need = 2; delta = -1; break;
-      case SG_OP_FMA: case SG_OP_SELECT: need = 3; delta = -2; break;
-      case SG_OP_NEG: case SG_OP_ABS: case SG_OP_SQRT: case SG_OP_NOT: need = 1; break;
-      case SG_OP_DUP: need = 1; delta = 1; break;
-      case SG_OP_SWAP: need = 2; break;
-      default:
-        return fail(c, SG_ERR_INVALID_ARG, "op %d has unknown opcode %d", p, o.op);
-    }
-    if (d < need)
-      return fail(c, SG_ERR_INVALID_ARG, "op %d needs %d operands, stack has %d", p, need, d);
-    d += delta;
-    mx = std::max(mx, d);
-    if (mx > SG_MAX_EXPR_DEPTH)
-      return fail(c, SG_ERR_INVALID_ARG, "expression stack deeper than %d", SG_MAX_EXPR_DEPTH);
-  }
-  if (d != 1)
-    return fail(c, SG_ERR_INVALID_ARG, "expression leaves %d values (must be 1)", d);
-  if (depth_out) *depth_out = mx;
+  char msg[160];
+  const sg_status s = sgk::validate_expr(f, nin, depth_out, nullptr, msg, sizeof msg);
+  if (s) return fail(c, s, "%s", msg);
   return SG_OK;
 }
 
@@ -1063,3 +1030,61 @@ sg_status sg_kernel_count(sg_ctx* c, int64_t* count) {
 }
 
 }  // extern "C"
+
+namespace sgk {
+
+static sg_status expr_error(char* msg, size_t cap, const char* fmt, ...)
+    __attribute__((format(printf, 3, 4)));
+
+static sg_status expr_error(char* msg, size_t cap, const char* fmt, ...) {
+  if (msg && cap) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, cap, fmt, ap);
+    va_end(ap);
+  }
+  return SG_ERR_INVALID_ARG;
+}
+
+sg_status validate_expr(const sg_expr* f, int nin, int* max_depth, uint8_t* depth_before,
+                        char* msg, size_t cap) {
+  if (!f) return expr_error(msg, cap, "null expression");
+  if (f->nops <= 0 || f->nops > SG_MAX_EXPR_OPS)
+    return expr_error(msg, cap, "expression has %d ops (1..%d allowed)", f->nops,
+                      SG_MAX_EXPR_OPS);
+  int d = 0, mx = 0;
+  for (int p = 0; p < f->nops; ++p) {
+    const sg_expr_op& o = f->ops[p];
+    int need = 0, delta = 0;
+    switch (o.op) {
+      case SG_OP_LOAD:
+        if (o.arg < 0 || o.arg >= nin)
+          return expr_error(msg, cap, "op %d loads slot %d of %d", p, o.arg, nin);
+        delta = 1;
+        break;
+      case SG_OP_CONST: case SG_OP_INDEX: delta = 1; break;
+      case SG_OP_ADD: case SG_OP_SUB: case SG_OP_MUL: case SG_OP_DIV: case SG_OP_MIN:
+      case SG_OP_MAX: case SG_OP_LT: case SG_OP_LE: case SG_OP_GT: case SG_OP_GE:
+      case SG_OP_EQ: case SG_OP_NE: case SG_OP_AND: case SG_OP_OR:
+        need = 2; delta = -1; break;
+      case SG_OP_FMA: case SG_OP_SELECT: need = 3; delta = -2; break;
+      case SG_OP_NEG: case SG_OP_ABS: case SG_OP_SQRT: case SG_OP_NOT: need = 1; break;
+      case SG_OP_DUP: need = 1; delta = 1; break;
+      case SG_OP_SWAP: need = 2; break;
+      default:
+        return expr_error(msg, cap, "op %d has unknown opcode %d", p, o.op);
+    }
+    if (d < need)
+      return expr_error(msg, cap, "op %d needs %d operands, stack has %d", p, need, d);
+    if (depth_before) depth_before[p] = (uint8_t)d;
+    d += delta;
+    mx = std::max(mx, d);
+    if (mx > SG_MAX_EXPR_DEPTH)
+      return expr_error(msg, cap, "expression stack deeper than %d", SG_MAX_EXPR_DEPTH);
+  }
+  if (d != 1) return expr_error(msg, cap, "expression leaves %d values (must be 1)", d);
+  if (max_depth) *max_depth = mx;
+  return SG_OK;
+}
+
+}  // namespace sgk

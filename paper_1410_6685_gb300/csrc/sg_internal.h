@@ -90,6 +90,13 @@ struct StreamArgs {
   int vec4;              // every pointer 16-byte aligned: use 128-bit accesses
 };
 
+// Stack check of a postfix expression over `nin` input slots (the one
+// validator of every entry point that takes an sg_expr).  SG_OK with the
+// largest stack depth in *max_depth and, when `depth_before` is given, the
+// depth before each op; else SG_ERR_INVALID_ARG with a message in msg.
+sg_status validate_expr(const sg_expr* f, int nin, int* max_depth, uint8_t* depth_before,
+                        char* msg, size_t cap);
+
 cudaError_t launch_stream(const StreamArgs& a, int grid, int block,
                           cudaStream_t s, Prof* prof);
 int stream_max_blocks_per_sm(int nin, int depth, int block);

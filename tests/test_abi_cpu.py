@@ -210,3 +210,26 @@ def test_portable_switch_arguments(sg, pctx):
     assert sg.lib.sg_debug_portable_kernels(None, 1) == sg.SG_ERR_INVALID_ARG
     sg.sg_debug_portable_kernels(pctx, True)
     sg.sg_debug_portable_kernels(pctx, False)
+
+
+MALFORMED = [
+    [("x", 0), ("gt",)],                                   # too few operands
+    [("x", 0), ("x", 0)],                                  # two values left
+    [("x", 1), ("c", 0.0), ("gt",)],                       # slot 1 of a one-input filter
+    [("x", 0)] * 7 + [("add",)] * 6,                       # stack deeper than 6
+]
+
+
+@pytest.mark.parametrize("k", range(len(MALFORMED)))
+def test_malformed_predicates_refused_alike(sg, pctx, k):
+    """sg_filter and the allocation-free filter share one expression
+    validator: every malformed predicate is refused by both, before any
+    device work (the allocation-free call gets fake pointers here)."""
+    pred = MALFORMED[k]
+    v = vec(sg, pctx, 100)
+    with pytest.raises(sg.SgError) as e1:
+        sg.sg_filter(pctx, pred, v)
+    with pytest.raises(sg.SgError) as e2:
+        sg.sg_filter_noalloc(pred, 16, 100, 16, 16)
+    assert e1.value.status == e2.value.status == sg.SG_ERR_INVALID_ARG
+    sg.sg_vector_release(v)

@@ -69,11 +69,14 @@ def test_diag_dominant_workload(env, n, prec):
     assert 1 <= info.iterations <= 30
 
 
-def test_full_size_8192(env):
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_full_size_8192(env, prec):
+    """The n = 8192 elimination workload with binary32, bf16 and fp16
+    trailing updates: refinement reaches the all-ones solution to 1e-10."""
     A, b = inputs.gepp_inputs(8192)
-    x, info = solve(env, A, b, prec=1)
+    x, info = solve(env, A, b, prec=prec)
     assert np.max(np.abs(x - 1.0)) <= 1e-10
-    assert info.residual <= 1e-12
+    assert info.residual <= 1e-12 and info.info == 0
 
 
 def test_row_interchanges_match_oracle(env):
@@ -108,13 +111,34 @@ def test_singular_matrix(env):
 
 
 def test_residual_postcondition_reports_first_row(env):
+    """The residual postcondition names the smallest row i with
+    |b_i - (A x)_i| above its bound.  One refinement step (refine_tol = 1)
+    leaves residuals far above binary64 rounding, so the host's binary64
+    residual of the returned x ranks the rows as the GPU's does; the bound is
+    put in the widest gap between sorted residuals, and the row the
+    postcondition reports must be the first row above it."""
     sg, ctx, _ = env
     n = 300
     A, b = inputs.gepp_inputs(n)
-    # an impossible bound: every row violates it, the first one is reported
+    x, info = solve(env, A, b, prec=1, refine_tol=1.0, residual_tol=1.0)
+    assert info.iterations == 1
+    r = np.abs(b - A.astype(np.float64) @ x)
+    denom = np.abs(A.astype(np.float64)).sum(axis=1).max() * np.abs(x).max() + np.abs(b).max()
+    srt = np.sort(r)
+    hi = srt[n // 2:]
+    k = int(np.argmax(hi[1:] / hi[:-1]))
+    assert hi[k + 1] / hi[k] > 1.01
+    thresh = float(np.sqrt(hi[k] * hi[k + 1]))
+    expect = int(np.flatnonzero(r > thresh)[0])
+    solve(env, A, b, prec=1, refine_tol=1.0, residual_tol=thresh / denom,
+          expect=sg.SG_ERR_POSTCONDITION)
+    v = sg.sg_last_violation(ctx)
+    assert v.kind == sg.SG_C_RESIDUAL and v.role == sg.SG_POST
+    assert v.first_index == expect
+    # an impossible bound: the first row whose residual is not exactly zero
     solve(env, A, b, prec=1, residual_tol=1e-300, expect=sg.SG_ERR_POSTCONDITION)
     v = sg.sg_last_violation(ctx)
-    assert v.kind == sg.SG_C_RESIDUAL and v.role == sg.SG_POST and 0 <= v.first_index < n
+    assert v.kind == sg.SG_C_RESIDUAL and 0 <= v.first_index < n
 
 
 def test_not_converged(env):
