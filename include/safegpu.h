@@ -468,6 +468,21 @@ sg_status sg_profile_report(sg_ctx* ctx, char* buf, size_t cap, size_t* len,
 typedef enum { SG_INJECT_NONE = 0, SG_INJECT_SWAP = 1, SG_INJECT_OVERWRITE = 2 } sg_inject_mode;
 sg_status sg_debug_inject_sort(sg_ctx* ctx, sg_inject_mode mode, int64_t i, int64_t j);
 
+/* Failure-detection testing of the bounded waits (no counterpart in the
+ * paper; its kernels have no inter-block waits).  The sort passes and the
+ * filter find their tiles' output offsets by a decoupled look-back: a tile
+ * waits for words that earlier tiles publish, and every wait gives up after
+ * a bounded number of polls, marks the flush SG_ERR_TIMEOUT and leaves the
+ * context usable.  For the sorts and filters of this context's later
+ * flushes: spin_limit bounds each wait (0 restores the default of 2^22
+ * polls), and skip_tile >= 0 makes that tile of every look-back pass publish
+ * nothing, so that the tiles after it wait until the limit (the planted
+ * fault is on the host side: a kernel argument).  (0, -1) switches both off.
+ * A timed-out pass writes nothing at unknown offsets and later passes of
+ * the same sort do nothing; the outputs of the flush are undefined.
+ * Errors: SG_ERR_INVALID_ARG for skip_tile < -1 or > INT32_MAX. */
+sg_status sg_debug_lookback(sg_ctx* ctx, uint32_t spin_limit, int64_t skip_tile);
+
 /* Contract testing of `multiply` (Sec. 3.4): plant an error in the NEXT
  * tensor-core product (SG_PREC_BF16_TC / SG_PREC_F16_TC) of this context:
  * `delta` is added to element (row, col) of the product as the kernel's

@@ -45,7 +45,8 @@ template <int DEPTH>
 __global__ void __launch_bounds__(kFB) k_filter(const float* __restrict__ x,
                                                 float* __restrict__ out, long long n,
                                                 const StreamArgs a, unsigned long long* st,
-                                                FilterHdr* h, FilterResult* res) {
+                                                FilterHdr* h, FilterResult* res,
+                                                const LookbackCtl lb) {
   __shared__ float s_v[kFTile];
   __shared__ unsigned s_warp[kFB / 32];
   __shared__ unsigned s_tile;
@@ -125,10 +126,12 @@ __global__ void __launch_bounds__(kFB) k_filter(const float* __restrict__ x,
   // below tile 0 stands an empty prefix (never reached).
   if (tid < 32) {
     unsigned long long excl = 0;
+    const bool publish = (int)tile != lb.skip_tile;
+    const unsigned limit = lb.spin_limit ? lb.spin_limit : kFSpin;
     if (tile == 0) {
-      if (tid == 0) st_relaxed64(&st[0], kFPre | total);
+      if (tid == 0 && publish) st_relaxed64(&st[0], kFPre | total);
     } else {
-      if (tid == 0) st_relaxed64(&st[tile], kFAgg | total);
+      if (tid == 0 && publish) st_relaxed64(&st[tile], kFAgg | total);
       long long j = (long long)tile - 1;
       unsigned spins = 0;
       while (true) {
@@ -148,14 +151,14 @@ __global__ void __launch_bounds__(kFB) k_filter(const float* __restrict__ x,
         if (done) break;
         j -= take;
         if (stop < 32u) {
-          if (++spins > kFSpin) {
+          if (++spins > limit) {
             if (tid == 0) atomicExch(&res->timeout, 1);
             break;
           }
           if (spins > 32) __nanosleep(64);
         }
       }
-      if (tid == 0) st_relaxed64(&st[tile], kFPre | (excl + total));
+      if (tid == 0 && publish) st_relaxed64(&st[tile], kFPre | (excl + total));
     }
     if (tid == 0) {
       s_excl = excl;
@@ -186,7 +189,7 @@ size_t filter_scratch_bytes(long long n) {
 
 cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& pred,
                           int pred_depth, void* scratch, FilterResult* res, cudaStream_t s,
-                          int num_sms, int64_t* kernels, Prof* prof) {
+                          int num_sms, int64_t* kernels, Prof* prof, const LookbackCtl& lb) {
   (void)num_sms;
   if (n <= 0) return cudaSuccess;   // count stays 0 (result record was zeroed)
   const unsigned ntiles = (unsigned)((n + kFTile - 1) / kFTile);
@@ -201,9 +204,9 @@ cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& p
   a.depth = pred_depth;
   prof_begin(prof, "filter", s);
   if (pred_depth > 4)
-    k_filter<8><<<ntiles, kFB, 0, s>>>(x, out, n, a, st, h, res);
+    k_filter<8><<<ntiles, kFB, 0, s>>>(x, out, n, a, st, h, res, lb);
   else
-    k_filter<4><<<ntiles, kFB, 0, s>>>(x, out, n, a, st, h, res);
+    k_filter<4><<<ntiles, kFB, 0, s>>>(x, out, n, a, st, h, res, lb);
   prof_end(prof, s);
   *kernels += 1;
   return cudaGetLastError();
@@ -212,7 +215,7 @@ cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& p
 cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out, long long n,
                                       const Prog& pred, void* scratch, FilterResult* res,
                                       cudaStream_t s, int num_sms, int64_t* kernels,
-                                      Prof* prof) {
+                                      Prof* prof, const LookbackCtl& lb) {
   // the scratch is sized for the interpreting kernel's tiles: one look-back
   // word per tile of kFTile items covers the larger tiles here
   static_assert(kJitFilterTile % kFTile == 0, "the two filters share the scratch");
@@ -233,6 +236,8 @@ cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out
   a.tile_ctr = &h->tile_ctr;
   a.res = res;
   a.ntiles = ntiles;
+  a.skip_tile = lb.skip_tile;
+  a.spin_limit = lb.spin_limit ? lb.spin_limit : kFSpin;
   void* args[] = {&a};
   prof_begin(prof, "filter_jit", s);
   e = cudaLaunchKernel(fn, dim3(grid), dim3(kFB), args, 0, s);
@@ -352,7 +357,8 @@ extern "C" sg_status sg_filter_noalloc(const sg_expr* pred, const float* dev_x, 
     int64_t kernels = 0;
     // the interpreting kernel: the specialised one would need a module
     // load, which allocates device memory
-    e = launch_filter(dev_x, dev_out, n, pr, md, scratch, res, s, 0, &kernels, nullptr);
+    e = launch_filter(dev_x, dev_out, n, pr, md, scratch, res, s, 0, &kernels, nullptr,
+                      LookbackCtl{0, -1});
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dev_count, &res->count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);

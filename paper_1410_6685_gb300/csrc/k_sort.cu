@@ -241,7 +241,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
                                               int* __restrict__ out, long long n, int pass,
                                               SortHdr* h, unsigned* st32,
                                               unsigned long long* st64, SortResult* res,
-                                              unsigned tile) {
+                                              unsigned tile, const LookbackCtl lb) {
   int* const s_keys = sm.keys;
   unsigned (*const s_whist)[kRadix] = sm.whist;
   int* const s_gbase = sm.gbase;
@@ -250,6 +250,9 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   const long long base = (long long)tile * kTile;
   const unsigned dsel = 0x4440u | (unsigned)pass;   // digit selector of this pass
   const int valid_cnt = FULL ? kTile : (int)(n - base < kTile ? n - base : kTile);
+  // the look-back testing switch: a tile that publishes nothing, a short wait
+  const bool publish = (int)tile != lb.skip_tile;
+  const unsigned spin_limit = lb.spin_limit ? lb.spin_limit : kSpinLimit;
 
   // load: warp w owns keys [w*kWarpKeys, (w+1)*kWarpKeys) of the tile, 32
   // consecutive per round
@@ -311,7 +314,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
       cnt += t;
     }
     // publish the tile aggregate as early as possible
-    if (!(LAST && CHECK))
+    if (!(LAST && CHECK) && publish)
       st_relaxed(&st32[(size_t)tile * kRadix + tid], ((tile == 0 ? kPre : kAgg) << 30) | cnt);
   }
   const unsigned start = block_excl_scan(cnt, sm.warp);
@@ -368,13 +371,13 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
         if (done) break;
         if (u < kLook) {
           j -= u;
-          if (++spins > kSpinLimit) { timeout = true; break; }
+          if (++spins > spin_limit) { timeout = true; break; }
           if (spins > 32) __nanosleep(64);
         } else {
           j -= kLook;
         }
       }
-      st_relaxed(&st32[(size_t)tile * kRadix + d], (kPre << 30) | (unsigned)(excl + cnt));
+      if (publish) st_relaxed(&st32[(size_t)tile * kRadix + d], (kPre << 30) | (unsigned)(excl + cnt));
     }
   } else {
     // 64-bit words: flag(2) | count(30) | last key of the digit run (32)
@@ -386,9 +389,9 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
     bool found = false;
     int pred_last = 0;
     if (tile == 0) {
-      st_relaxed64(&st64[d], word(kPre, cnt, last_key));
+      if (publish) st_relaxed64(&st64[d], word(kPre, cnt, last_key));
     } else {
-      st_relaxed64(&st64[(size_t)tile * kRadix + d], word(kAgg, cnt, last_key));
+      if (publish) st_relaxed64(&st64[(size_t)tile * kRadix + d], word(kAgg, cnt, last_key));
       // the same windowed walk as above; the first run met with keys
       // gives the last key before this tile's run
       long long j = (long long)tile - 1;
@@ -420,14 +423,14 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
         if (done) break;
         if (u < kLookWide) {
           j -= u;
-          if (++spins > kSpinLimit) { timeout = true; break; }
+          if (++spins > spin_limit) { timeout = true; break; }
           if (spins > 32) __nanosleep(64);
         } else {
           j -= kLookWide;
         }
       }
       const int carry = cnt ? last_key : pred_last;
-      st_relaxed64(&st64[(size_t)tile * kRadix + d], word(kPre, (unsigned)(excl + cnt), carry));
+      if (publish) st_relaxed64(&st64[(size_t)tile * kRadix + d], word(kPre, (unsigned)(excl + cnt), carry));
     }
     // the first key of this run must not be below the last key before it
     if (cnt && found && okey<FLT>(first_key) < okey<FLT>(pred_last)) {
@@ -452,7 +455,9 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
     const int k = s_keys[i];
     const unsigned dk = digit_of<LAST, FLT>(k, dsel);
     const int pos = s_gbase[dk] + i;
-    if (write) __stcs(out + pos, k);
+    // a planted fault (a key changed between passes) can carry a digit run
+    // past the histogram's offsets: never write outside the output
+    if (write && (unsigned)pos < (unsigned)n) __stcs(out + pos, k);
     if (LAST && CHECK) {
       fp_add(f1, f2, k);
       if (i + 1 < valid_cnt) {
@@ -481,15 +486,19 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 template <bool LAST, bool CHECK, bool FLT>
 __global__ void __launch_bounds__(kSortBlock, kSortMinBlocks) k_onesweep(
     const int* __restrict__ in, int* __restrict__ out, long long n, int pass, SortHdr* h,
-    unsigned* st32, unsigned long long* st64, SortResult* res, unsigned ahead) {
+    unsigned* st32, unsigned long long* st64, SortResult* res, unsigned ahead,
+    const LookbackCtl lb) {
   __shared__ SortSmem sm;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    sm.tile = atomicAdd(&h->tile_ctr[pass], 1u);
-    sm.timeout = 0;
+    // an earlier pass whose look-back gave up left its output incomplete:
+    // this pass does nothing
+    sm.timeout = pass > 0 ? *reinterpret_cast<volatile int*>(&res->timeout) : 0;
+    if (!sm.timeout) sm.tile = atomicAdd(&h->tile_ctr[pass], 1u);
   }
   for (int i = tid; i < kWarps * kRadix; i += kSortBlock) (&sm.whist[0][0])[i] = 0;
   __syncthreads();
+  if (sm.timeout) return;
   const unsigned tile = sm.tile;
   // tiles are taken in ticket order: the tile one resident wave ahead is
   // fetched into L2 now, so that its CTA's key loads hit L2
@@ -501,9 +510,9 @@ __global__ void __launch_bounds__(kSortBlock, kSortMinBlocks) k_onesweep(
                    : "memory");
   }
   if ((long long)(tile + 1) * kTile <= n)
-    onesweep_tile<LAST, CHECK, true, FLT>(sm, in, out, n, pass, h, st32, st64, res, tile);
+    onesweep_tile<LAST, CHECK, true, FLT>(sm, in, out, n, pass, h, st32, st64, res, tile, lb);
   else
-    onesweep_tile<LAST, CHECK, false, FLT>(sm, in, out, n, pass, h, st32, st64, res, tile);
+    onesweep_tile<LAST, CHECK, false, FLT>(sm, in, out, n, pass, h, st32, st64, res, tile, lb);
 }
 
 // ---------------------------------------------------------------------------
@@ -586,7 +595,8 @@ namespace {
 template <bool FLT>
 cudaError_t sort_impl(const int32_t* in, int32_t* out, long long n, bool contracts,
                         void* scratch, SortResult* res, cudaStream_t s, int num_sms,
-                        int64_t* kernels, const SortInject* inject, Prof* prof) {
+                        int64_t* kernels, const SortInject* inject, Prof* prof,
+                        const LookbackCtl lb) {
   if (n <= 0) return cudaSuccess;
   const Layout L = layout(n);
   char* base = static_cast<char*>(scratch);
@@ -606,13 +616,13 @@ cudaError_t sort_impl(const int32_t* in, int32_t* out, long long n, bool contrac
   const unsigned ntiles = (unsigned)((n + kTile - 1) / kTile);
   const unsigned ahead = (unsigned)num_sms * kSortMinBlocks;
   prof_begin(prof, "onesweep", s);
-  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(in, tmp, n, 0, h, st32[0], st64, res, ahead);
+  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(in, tmp, n, 0, h, st32[0], st64, res, ahead, lb);
   prof_end(prof, s);
   prof_begin(prof, "onesweep", s);
-  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 1, h, st32[1], st64, res, ahead);
+  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 1, h, st32[1], st64, res, ahead, lb);
   prof_end(prof, s);
   prof_begin(prof, "onesweep", s);
-  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(out, tmp, n, 2, h, st32[2], st64, res, ahead);
+  k_onesweep<false, false, FLT><<<ntiles, kSortBlock, 0, s>>>(out, tmp, n, 2, h, st32[2], st64, res, ahead, lb);
   prof_end(prof, s);
   if (inject && inject->mode == 1 && inject->i < n && inject->j < n) {
     // swap through the (now free) output buffer: stream-ordered host copies
@@ -633,9 +643,9 @@ cudaError_t sort_impl(const int32_t* in, int32_t* out, long long n, bool contrac
   unsigned* st_last = reinterpret_cast<unsigned*>(st64);
   prof_begin(prof, contracts ? "onesweep_last_checked" : "onesweep", s);
   if (contracts)
-    k_onesweep<true, true, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res, ahead);
+    k_onesweep<true, true, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res, ahead, lb);
   else
-    k_onesweep<true, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res, ahead);
+    k_onesweep<true, false, FLT><<<ntiles, kSortBlock, 0, s>>>(tmp, out, n, 3, h, st_last, st64, res, ahead, lb);
   prof_end(prof, s);
   *kernels += 5;
   return cudaGetLastError();
@@ -645,11 +655,12 @@ cudaError_t sort_impl(const int32_t* in, int32_t* out, long long n, bool contrac
 
 cudaError_t launch_sort(const int32_t* in, int32_t* out, long long n, bool contracts,
                         void* scratch, SortResult* res, cudaStream_t s, int num_sms,
-                        int64_t* kernels, const SortInject* inject, Prof* prof, bool flt) {
+                        int64_t* kernels, const SortInject* inject, Prof* prof, bool flt,
+                        const LookbackCtl& lb) {
   return flt ? sort_impl<true>(in, out, n, contracts, scratch, res, s, num_sms, kernels, inject,
-                               prof)
+                               prof, lb)
              : sort_impl<false>(in, out, n, contracts, scratch, res, s, num_sms, kernels, inject,
-                                prof);
+                                prof, lb);
 }
 
 size_t check_scratch_bytes() { return 0; }

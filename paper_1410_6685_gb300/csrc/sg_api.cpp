@@ -1007,6 +1007,13 @@ sg_status sg_debug_inject_sort(sg_ctx* c, sg_inject_mode mode, int64_t i, int64_
   return SG_OK;
 }
 
+sg_status sg_debug_lookback(sg_ctx* c, uint32_t spin_limit, int64_t skip_tile) {
+  if (!c || skip_tile < -1 || skip_tile > INT32_MAX) return SG_ERR_INVALID_ARG;
+  c->lookback.spin_limit = spin_limit;
+  c->lookback.skip_tile = (int)skip_tile;
+  return SG_OK;
+}
+
 sg_status sg_debug_inject_matmul(sg_ctx* c, int64_t row, int64_t col, float delta) {
   if (!c || row < -1 || col < -1 || (row < 0) != (col < 0) || row > INT32_MAX || col > INT32_MAX)
     return SG_ERR_INVALID_ARG;

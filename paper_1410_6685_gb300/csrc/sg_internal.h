@@ -119,6 +119,15 @@ struct SortResult {
 };
 static_assert(sizeof(SortResult) <= kResultBytes, "result too large");
 
+// Bounds of the decoupled look-back waits (sort passes, filter).  The
+// default (spin_limit 0, skip_tile -1) is the kernels' own limit and every
+// tile publishing; the testing switch sg_debug_lookback sets a short limit
+// and a tile that publishes nothing, so that its successors' waits run out.
+struct LookbackCtl {
+  unsigned spin_limit;   // polls before a wait gives up (0 = the kernel's default)
+  int skip_tile;         // this tile publishes no look-back word (-1 = none)
+};
+
 // bytes from src to dst (no overlap), on stream s
 cudaError_t launch_copy(void* dst, const void* src, size_t bytes, int num_sms, cudaStream_t s);
 
@@ -134,7 +143,8 @@ struct SortInject {
 cudaError_t launch_sort(const int32_t* in, int32_t* out, long long n,
                         bool contracts, void* scratch, SortResult* res,
                         cudaStream_t s, int num_sms, int64_t* kernels,
-                        const SortInject* inject, Prof* prof, bool flt);
+                        const SortInject* inject, Prof* prof, bool flt,
+                        const LookbackCtl& lb);
 // Stand-alone checks on any 32-bit vector (re-read).  `res` must be zeroed
 // by the caller's conventions: these kernels set only their own fields.
 size_t check_scratch_bytes();
@@ -158,11 +168,11 @@ size_t filter_scratch_bytes(long long n);
 cudaError_t launch_filter(const float* x, float* out, long long n,
                           const Prog& pred, int pred_depth, void* scratch,
                           FilterResult* res, cudaStream_t s, int num_sms,
-                          int64_t* kernels, Prof* prof);
+                          int64_t* kernels, Prof* prof, const LookbackCtl& lb);
 // the same filter through its run-time specialised kernel (sg_jit.h)
 cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out, long long n,
                                       const Prog& pred, void* scratch, FilterResult* res,
                                       cudaStream_t s, int num_sms, int64_t* kernels,
-                                      Prof* prof);
+                                      Prof* prof, const LookbackCtl& lb);
 
 }  // namespace sgk

@@ -435,7 +435,8 @@ const char* kTemplateFilter = R"SGJIT(
 struct FilterResult { long long count; int timeout; int pad; };
 struct FilterJitArgs {
   const float* x; float* out; long long n; float cst[48];
-  unsigned long long* st; unsigned* tile_ctr; FilterResult* res; unsigned ntiles; int pad;
+  unsigned long long* st; unsigned* tile_ctr; FilterResult* res; unsigned ntiles; int skip_tile;
+  unsigned spin_limit; int pad;
 };
 #define SG_FT 8192
 #define SG_FQ 8
@@ -524,7 +525,8 @@ extern "C" __global__ void __launch_bounds__(256, 5) sg_filter(const FilterJitAr
   }
   const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
   const unsigned e0 = incl - c0 - c1;
-  if (tid == 0 && t > 0) sg_st_relaxed(&a.st[t], SG_AGG | total);
+  const bool publish = (int)t != a.skip_tile;
+  if (tid == 0 && t > 0 && publish) sg_st_relaxed(&a.st[t], SG_AGG | total);
 #pragma unroll
   for (int q = 0; q < SG_FQ; ++q) {
     const int entry = q * 8 + w;
@@ -539,7 +541,7 @@ extern "C" __global__ void __launch_bounds__(256, 5) sg_filter(const FilterJitAr
   if (w == 0) {
     unsigned long long excl = 0;
     if (t == 0) {
-      if (lane == 0) sg_st_relaxed(&a.st[0], SG_PRE | total);
+      if (lane == 0 && publish) sg_st_relaxed(&a.st[0], SG_PRE | total);
     } else {
       long long j = (long long)t - 1;
       unsigned spins = 0;
@@ -560,14 +562,14 @@ extern "C" __global__ void __launch_bounds__(256, 5) sg_filter(const FilterJitAr
         if (done) break;
         j -= take;
         if (stop < 32u) {
-          if (++spins > (1u << 22)) {
+          if (++spins > a.spin_limit) {
             if (lane == 0) atomicExch(&a.res->timeout, 1);
             break;
           }
           if (spins > 32) __nanosleep(64);
         }
       }
-      if (lane == 0) sg_st_relaxed(&a.st[t], SG_PRE | (excl + total));
+      if (lane == 0 && publish) sg_st_relaxed(&a.st[t], SG_PRE | (excl + total));
     }
     if (lane == 0) {
       s_excl = excl;

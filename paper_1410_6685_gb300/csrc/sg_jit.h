@@ -55,9 +55,11 @@ struct FilterJitArgs {
   unsigned* tile_ctr;       // tile tickets
   FilterResult* res;
   unsigned ntiles;
+  int skip_tile;            // look-back testing switch: this tile publishes nothing
+  unsigned spin_limit;      // polls before a look-back wait gives up
   int pad;
 };
-static_assert(sizeof(FilterJitArgs) == 248, "FilterJitArgs layout changed: update the template");
+static_assert(sizeof(FilterJitArgs) == 256, "FilterJitArgs layout changed: update the template");
 // tile of the specialised filter (items); its shared memory is static
 constexpr int kJitFilterTile = 8192;
 

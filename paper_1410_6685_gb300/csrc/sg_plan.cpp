@@ -735,12 +735,12 @@ sg_status sg_execute_pending(sg_ctx* c) {
           e = sgk::launch_filter_specialised(jk, static_cast<const float*>(x->st->ptr),
                                              static_cast<float*>(n->out->st->ptr), P.n, pr, dwork,
                                              static_cast<sgk::FilterResult*>(rec), c->stream,
-                                             c->num_sms, &c->kernels, &c->prof);
+                                             c->num_sms, &c->kernels, &c->prof, c->lookback);
         else
           e = sgk::launch_filter(static_cast<const float*>(x->st->ptr),
                                  static_cast<float*>(n->out->st->ptr), P.n, pr, md, dwork,
                                  static_cast<sgk::FilterResult*>(rec), c->stream, c->num_sms,
-                                 &c->kernels, &c->prof);
+                                 &c->kernels, &c->prof, c->lookback);
         break;
       }
       case PK::SORT: {
@@ -751,7 +751,8 @@ sg_status sg_execute_pending(sg_ctx* c) {
                              static_cast<int32_t*>(n->out->st->ptr), P.n,
                              P.chk_sorted || P.chk_perm, dwork,
                              static_cast<sgk::SortResult*>(rec), c->stream, c->num_sms,
-                             &c->kernels, &c->inject, &c->prof, n->in[0]->dt == SG_F32);
+                             &c->kernels, &c->inject, &c->prof, n->in[0]->dt == SG_F32,
+                             c->lookback);
         c->inject = sgk::SortInject{};
         break;
       }
@@ -887,6 +888,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
           if (r.timeout) {
             status = SG_ERR_TIMEOUT;
             c->err = "filter look-back wait gave up";
+            r.count = 0;   // the kept items of a timed-out compaction are no result
           }
           P.main->out->n = r.count;
           P.main->out->rows = r.count;

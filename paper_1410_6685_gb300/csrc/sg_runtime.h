@@ -176,6 +176,7 @@ struct sg_ctx {
   size_t host_res_bytes = 0;
   bool host_res_mapped = false;        // kernels can store into host_res directly
   sgk::SortInject inject{};            // contract-test fault for the next sort
+  sgk::LookbackCtl lookback{0, -1};    // testing switch of the look-back waits
   struct {
     int64_t row = -1, col = -1;
     float delta = 0.0f;

@@ -139,7 +139,7 @@ def _load():
         "sg_last_violation": [vp, P(SgViolation)], "sg_flush": [vp],
         "sg_set_contract_mode": [vp, i32], "sg_set_fusion": [vp, i32],
         "sg_set_scheduler": [vp, i32], "sg_set_codegen": [vp, i32], "sg_plan_describe": [vp, C.c_char_p, sz, P(sz)],
-        "sg_kernel_count": [vp, P(i64)], "sg_profile_enable": [vp, i32], "sg_profile_report": [vp, C.c_char_p, sz, P(sz), i32], "sg_debug_inject_sort": [vp, i32, i64, i64], "sg_debug_inject_matmul": [vp, i64, i64, C.c_float], "sg_debug_portable_kernels": [vp, i32],
+        "sg_kernel_count": [vp, P(i64)], "sg_profile_enable": [vp, i32], "sg_profile_report": [vp, C.c_char_p, sz, P(sz), i32], "sg_debug_inject_sort": [vp, i32, i64, i64], "sg_debug_lookback": [vp, C.c_uint32, i64], "sg_debug_inject_matmul": [vp, i64, i64, C.c_float], "sg_debug_portable_kernels": [vp, i32],
         "sg_batch_run": [vp, P(SgChain), vp, vp, i64, vp, vp, vp],
         "sg_filter_noalloc": [P(SgExpr), vp, i64, vp, vp, vp],
         "sg_debug_jit_check_filter": [P(SgExpr), C.c_char_p, sz],
@@ -487,6 +487,10 @@ def wrap_tensor(ctx, t):
 
 
 SG_INJECT_NONE, SG_INJECT_SWAP, SG_INJECT_OVERWRITE = 0, 1, 2
+
+
+def sg_debug_lookback(ctx, spin_limit=0, skip_tile=-1):
+    _check(lib.sg_debug_lookback(ctx, spin_limit, skip_tile), ctx)
 
 
 def sg_debug_inject_sort(ctx, mode, i, j=0):

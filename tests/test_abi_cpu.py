@@ -233,3 +233,11 @@ def test_malformed_predicates_refused_alike(sg, pctx, k):
         sg.sg_filter_noalloc(pred, 16, 100, 16, 16)
     assert e1.value.status == e2.value.status == sg.SG_ERR_INVALID_ARG
     sg.sg_vector_release(v)
+
+
+def test_lookback_switch_arguments(sg, pctx):
+    sg.sg_debug_lookback(pctx, 100, 3)
+    sg.sg_debug_lookback(pctx, 0, -1)
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_debug_lookback(pctx, 0, -2)
+    assert e.value.status == sg.SG_ERR_INVALID_ARG
