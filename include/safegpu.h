@@ -354,7 +354,9 @@ typedef enum {
   SG_C_SORTED = 2,      /* target ascending; first i with t[i] > t[i+1]   */
   SG_C_PERMUTATION = 3, /* target is a permutation of other[0]            */
   SG_C_FREIVALDS = 4,   /* target C = other[0] (A) x other[1] (B), matrices */
-  SG_C_RESIDUAL = 5     /* target x solves other[0] (A) x = other[1] (b)    */
+  SG_C_RESIDUAL = 5,    /* target x solves other[0] (A) x = other[1] (b)    */
+  SG_C_UNCHANGED = 6    /* target equals its value when other[0] was taken
+                           by sg_old (Listing 3: Current = old Current)   */
 } sg_contract_kind;
 
 typedef struct {
@@ -371,8 +373,22 @@ typedef struct {
 
 sg_status sg_require(sg_ctx* ctx, void* target, const sg_contract* c,
                      int32_t* contract_id);
+
 sg_status sg_ensure(sg_ctx* ctx, void* target, const sg_contract* c,
                     int32_t* contract_id);
+
+/* Eiffel's `old` (Sec. 4, Listing 3's postcondition Current = old Current):
+ * takes the state of `target` (a vector or a matrix) at this point of the
+ * queue, kept as a position-dependent fingerprint -- two 64-bit sums of
+ * mix64(i 2^32 + unit_i) over its 16-bit (bf16, fp16) or 32-bit units, mix64
+ * being SplitMix64's output function -- instead of a copy: one read of the
+ * target when the queue reaches it, 16 bytes kept.  *old is a new SG_I64
+ * vector of 2 elements (owned by the caller) holding the fingerprint; pass
+ * it as other[0] of an SG_C_UNCHANGED contract on the same target.  A
+ * change of any single unit always changes the fingerprint (mix64 is a
+ * bijection); several changes go unseen only if their sums cancel mod 2^64
+ * in both sums.  Errors: SG_ERR_INVALID_ARG, SG_ERR_POISONED. */
+sg_status sg_old(sg_ctx* ctx, void* target, sg_vector** old);
 
 typedef enum { SG_PRE = 0, SG_POST = 1 } sg_contract_role;
 

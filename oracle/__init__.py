@@ -80,6 +80,8 @@ def lib():
             "or_vecmat_f64": (None, [vp, vp, i64, i64, vp]),
             "or_matmul_rows_f64": (None, [vp, vp, i64, i64, i64, vp, i64, vp]),
             "or_splitmix64": (u64, [u64]),
+            "or_first_changed": (i64, [vp, vp, i64, i32]),
+            "or_fingerprint_old": (None, [vp, i64, i32, vp]),
             "or_rademacher": (dbl, [u64, i64, i64, i64]),
             "or_freivalds": (i64, [vp, vp, vp, i64, u64, i32, dbl, dbl, vp, vp]),
             "or_gepp_f64": (i32, [vp, i64, vp]),
@@ -283,6 +285,28 @@ def matmul_rows_f64(A, B, rows) -> np.ndarray:
     Cm = np.empty((len(rows), N), dtype=np.float64)
     lib().or_matmul_rows_f64(_p(A), _p(B), M, K, N, _p(rows), len(rows), _p(Cm))
     return Cm
+
+
+def _units(x):
+    x = np.ascontiguousarray(x)
+    ub = 2 if x.dtype.itemsize == 2 else 4
+    return x, x.nbytes // ub, ub
+
+
+def first_changed(before, after) -> int:
+    """Listing 3's Current = old Current: first unit whose bits differ, -1."""
+    a, units, ub = _units(before)
+    b = np.ascontiguousarray(after)
+    assert a.dtype == b.dtype and a.shape == b.shape
+    return int(lib().or_first_changed(_p(a), _p(b), units, ub))
+
+
+def fingerprint_old(x) -> tuple:
+    """The (F1, F2) fingerprint that stands for `old` of a collection."""
+    a, units, ub = _units(x)
+    f = np.zeros(2, dtype=np.uint64)
+    lib().or_fingerprint_old(_p(a), units, ub, _p(f))
+    return int(f[0]), int(f[1])
 
 
 def splitmix64(z: int) -> int:

@@ -341,6 +341,46 @@ uint64_t or_splitmix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+/* Listing 3's postcondition Current = old Current (Sec. 4): the collection
+ * after the routine equals, unit for unit (bit patterns, so a NaN equals
+ * itself and -0 differs from +0), the collection when the routine was
+ * entered.  The plain definition: the first index of a unit (16- or 32-bit)
+ * whose bits differ, or -1.                                                 */
+int64_t or_first_changed(const void* before, const void* after, int64_t units,
+                         int unit_bytes) {
+  const unsigned char* a = (const unsigned char*)before;
+  const unsigned char* b = (const unsigned char*)after;
+  for (int64_t i = 0; i < units; ++i)
+    if (memcmp(a + i * unit_bytes, b + i * unit_bytes, (size_t)unit_bytes) != 0) return i;
+  return -1;
+}
+
+/* The library keeps `old` as a fingerprint instead of a copy.  Its
+ * definition, written out: unit i (its bits w, zero-extended) contributes
+ * h_i = SplitMix64's output function applied to i * 2^32 + w; f[0] = sum h_i
+ * and f[1] = sum (h_i >> 32) * (h_i mod 2^32), both mod 2^64, i ascending. */
+void or_fingerprint_old(const void* x, int64_t units, int unit_bytes, uint64_t* f) {
+  const unsigned char* p = (const unsigned char*)x;
+  uint64_t f1 = 0, f2 = 0;
+  for (int64_t i = 0; i < units; ++i) {
+    uint64_t w = 0;
+    if (unit_bytes == 2) {
+      uint16_t u;
+      memcpy(&u, p + 2 * i, 2);
+      w = u;
+    } else {
+      uint32_t u;
+      memcpy(&u, p + 4 * i, 4);
+      w = u;
+    }
+    const uint64_t h = or_splitmix64(((uint64_t)i << 32) | w);
+    f1 += h;
+    f2 += (h >> 32) * (h & 0xFFFFFFFFull);
+  }
+  f[0] = f1;
+  f[1] = f2;
+}
+
 /* Rademacher entry j of check vector v (0-based) for an n-vector: the t-th
  * SplitMix64 draw of the stream `seed`, t = v*n + j + 1; its top bit picks
  * the sign (1 -> -1.0, 0 -> +1.0). */

@@ -75,6 +75,9 @@ void    or_matvec_f64(const float* A, int64_t rows, int64_t cols, const float* x
 void    or_vecmat_f64(const float* x, const float* A, int64_t rows, int64_t cols,
                       double* y);
 uint64_t or_splitmix64(uint64_t state_after_increment);
+/* ---- `old` (Sec. 4, Listing 3: Current = old Current) ---- */
+int64_t or_first_changed(const void* before, const void* after, int64_t units, int unit_bytes);
+void    or_fingerprint_old(const void* x, int64_t units, int unit_bytes, uint64_t* f);
 double  or_rademacher(uint64_t seed, int64_t v, int64_t n, int64_t j);
 int64_t or_freivalds(const float* A, const float* B, const float* C, int64_t N,
                      uint64_t seed, int nvec, double c, double u_eff,

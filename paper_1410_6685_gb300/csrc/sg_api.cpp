@@ -922,10 +922,41 @@ static sg_status attach(sg_ctx* c, void* target, const sg_contract* k, int32_t* 
       use(n.get(), 2, b->v);
       break;
     }
+    case SG_C_UNCHANGED: {
+      // Listing 3: Current = old Current, against the fingerprint sg_old took
+      if (k->nother != 1) return fail(c, SG_ERR_INVALID_ARG, "unchanged needs other[0] from sg_old");
+      sg_vector* o = static_cast<sg_vector*>(k->other[0]);
+      if (o->v->dt != SG_I64 || o->v->n != 2)
+        return fail(c, SG_ERR_INVALID_ARG, "other[0] must be the 2-element vector sg_old returns");
+      sg_status s = known_count(t);
+      if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
+      if (!active) return SG_OK;
+      n->nin = 2;
+      use(n.get(), 0, t->v);
+      use(n.get(), 1, o->v);
+      break;
+    }
     default:
       return fail(c, SG_ERR_INVALID_ARG, "contract kind %d not supported here", k->kind);
   }
   enqueue(c, std::move(n));
+  return SG_OK;
+}
+
+sg_status sg_old(sg_ctx* c, void* target, sg_vector** old) {
+  if (!c || !target || !old) return fail(c, SG_ERR_INVALID_ARG, "bad sg_old arguments");
+  sg_vector* t = static_cast<sg_vector*>(target);
+  if (check_vec(t) || t->ctx != c) return fail(c, SG_ERR_INVALID_ARG, "bad sg_old target");
+  sg_status s = known_count(t);
+  if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
+  if (t->v->poisoned) return fail(c, SG_ERR_POISONED, "sg_old of a value that failed a contract");
+  NodeP n = new_node(c, NK::SNAPSHOT);
+  n->nin = 1;
+  use(n.get(), 0, t->v);
+  make_out(c, SG_I64, 2, 2, 1, &n->out);
+  sg_vector* h = new_handle(c, n->out, false);
+  enqueue(c, std::move(n));
+  *old = h;
   return SG_OK;
 }
 

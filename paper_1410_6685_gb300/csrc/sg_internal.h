@@ -156,6 +156,13 @@ cudaError_t launch_check_perm(const int32_t* x, const int32_t* ref, long long n,
                               SortResult* res, void* scratch, cudaStream_t s,
                               int num_sms, int64_t* kernels, Prof* prof);
 
+// Position-dependent fingerprint of `bytes` bytes at x, read in units of
+// unit_bytes (2 or 4): out[0] = sum of h_i, out[1] = sum of hi32(h_i)
+// lo32(h_i) mod 2^64 with h_i = mix64(i 2^32 + unit_i) (k_fprint.cu); out is
+// cleared first.  The `old` of a postcondition (Sec. 4, Listing 3).
+cudaError_t launch_fprint(const void* x, size_t bytes, int unit_bytes, unsigned long long* out,
+                          cudaStream_t s, int num_sms, int64_t* kernels, Prof* prof);
+
 // ---------------------------------------------------------------------------
 // Filter (k_filter.cu): stable stream compaction with a decoupled look-back
 // scan of tile counts.

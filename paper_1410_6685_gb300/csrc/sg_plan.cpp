@@ -41,7 +41,15 @@ struct Op {
 };
 
 enum class PK { STREAM, FILTER, SORT, CHECK_SORTED, CHECK_PERM, MATMUL, FREIVALDS, TRANSPOSE, MATVEC,
-                CONCAT };
+                CONCAT, FPRINT, CHECK_SAME };
+
+// bytes of a value, and the unit its fingerprint reads (2 for bf16 / fp16)
+size_t value_bytes(const Value* v) {
+  const size_t es = (v->dt == SG_F64 || v->dt == SG_I64) ? 8
+                    : (v->dt == SG_BF16 || v->dt == SG_F16) ? 2 : 4;
+  return (size_t)v->n * es;
+}
+int fprint_unit(const Value* v) { return (v->dt == SG_BF16 || v->dt == SG_F16) ? 2 : 4; }
 
 struct Pass {
   PK kind = PK::STREAM;
@@ -326,6 +334,7 @@ struct Planner {
           P.kind = PK::TRANSPOSE;
           break;
         case NK::CONCAT: P.kind = PK::CONCAT; break;
+        case NK::SNAPSHOT: P.kind = PK::FPRINT; break;
         case NK::MATVEC:
           P.kind = PK::MATVEC;
           if (!n->left && n->in[0]->producer && virtual_t.count(n->in[0]->producer))
@@ -350,6 +359,8 @@ struct Planner {
               continue;
             }
             P.kind = PK::CHECK_PERM;
+          } else if (n->ckind == SG_C_UNCHANGED) {
+            P.kind = PK::CHECK_SAME;
           } else {
             // fold into the tensor-core product that produced the checked value
             if (c->fusion == SG_FUSE_ON && !passes.empty() && passes.back().kind == PK::MATMUL &&
@@ -604,7 +615,9 @@ sg_status sg_execute_pending(sg_ctx* c) {
       case PK::MATMUL:
       case PK::FREIVALDS: work = std::max(work, sg_linalg_scratch(c, P.main, P.chk_frv)); break;
       case PK::TRANSPOSE:
-      case PK::CONCAT: break;
+      case PK::CONCAT:
+      case PK::FPRINT:
+      case PK::CHECK_SAME: break;
       case PK::MATVEC: {
         const Node* n = P.main;
         const Value* A = P.vtrans ? P.vtrans->in[0].get() : n->left ? n->in[1].get() : nullptr;
@@ -776,6 +789,28 @@ sg_status sg_execute_pending(sg_ctx* c) {
       case PK::FREIVALDS:
         status = sg_exec_linalg(c, P.main, P.chk_frv, rec, dwork, &e);
         break;
+      case PK::FPRINT: {
+        Node* n = P.main;
+        status = ensure_storage(c, n->out.get());
+        if (status) break;
+        const Value* x = n->in[0].get();
+        e = sgk::launch_fprint(x->st ? x->st->ptr : nullptr, value_bytes(x), fprint_unit(x),
+                               static_cast<unsigned long long*>(n->out->st->ptr), c->stream,
+                               c->num_sms, &c->kernels, &c->prof);
+        break;
+      }
+      case PK::CHECK_SAME: {
+        // the fingerprint now, beside the one sg_old took, in the record
+        Node* n = P.main;
+        const Value* x = n->in[0].get();
+        auto* r = static_cast<sgk::SortResult*>(rec);
+        e = sgk::launch_fprint(x->st ? x->st->ptr : nullptr, value_bytes(x), fprint_unit(x),
+                               r->fp_out, c->stream, c->num_sms, &c->kernels, &c->prof);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(r->fp_in, n->in[1]->st->ptr, sizeof r->fp_in,
+                              cudaMemcpyDeviceToDevice, c->stream);
+        break;
+      }
       case PK::CONCAT: {
         Node* n = P.main;
         status = ensure_storage(c, n->out.get());
@@ -913,9 +948,17 @@ sg_status sg_execute_pending(sg_ctx* c) {
             record_violation(c, kp, -1, 0.0, &have, &cstatus);
           break;
         }
+        case PK::CHECK_SAME: {
+          sgk::SortResult r;
+          memcpy(&r, rec, sizeof r);
+          if (r.fp_in[0] != r.fp_out[0] || r.fp_in[1] != r.fp_out[1])
+            record_violation(c, P.main, -1, 0.0, &have, &cstatus);
+          break;
+        }
         case PK::TRANSPOSE:
         case PK::MATVEC:
         case PK::CONCAT:
+        case PK::FPRINT:
           break;
         case PK::MATMUL:
         case PK::FREIVALDS: {
@@ -993,6 +1036,12 @@ sg_status sg_describe_pending(sg_ctx* c, std::string* out) {
       case PK::CONCAT:
         snprintf(buf, sizeof buf, "concat %lld+%lld\n", (long long)P.main->in[0]->n,
                  (long long)P.main->in[1]->n);
+        break;
+      case PK::FPRINT:
+        snprintf(buf, sizeof buf, "fingerprint(old) n=%lld\n", (long long)P.main->in[0]->n);
+        break;
+      case PK::CHECK_SAME:
+        snprintf(buf, sizeof buf, "check_unchanged n=%lld\n", (long long)P.main->in[0]->n);
         break;
       case PK::MATVEC: {
         const Node* n = P.main;

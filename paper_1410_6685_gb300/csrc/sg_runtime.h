@@ -56,7 +56,8 @@ struct ScalarVal {
 };
 using ScalarP = std::shared_ptr<ScalarVal>;
 
-enum class NK { MAP, REDUCE, QUANT, CHECK, FILTER, SORT, MATMUL, TRANSPOSE, MATVEC, CONCAT };
+enum class NK { MAP, REDUCE, QUANT, CHECK, FILTER, SORT, MATMUL, TRANSPOSE, MATVEC, CONCAT,
+                SNAPSHOT };
 
 struct Node {
   int id = 0;

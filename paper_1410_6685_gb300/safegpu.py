@@ -30,7 +30,8 @@ for _i, _n in enumerate(STATUS):
 SG_F32, SG_F64, SG_BF16, SG_F16, SG_I32, SG_I64 = range(6)
 SG_REDUCE_SUM, SG_REDUCE_MIN, SG_REDUCE_MAX, SG_REDUCE_AVG, SG_REDUCE_COUNT = range(5)
 SG_PREC_F32_SIMT, SG_PREC_BF16_TC, SG_PREC_F16_TC = range(3)
-SG_C_FOR_ALL, SG_C_EXISTS, SG_C_SORTED, SG_C_PERMUTATION, SG_C_FREIVALDS, SG_C_RESIDUAL = range(6)
+(SG_C_FOR_ALL, SG_C_EXISTS, SG_C_SORTED, SG_C_PERMUTATION, SG_C_FREIVALDS, SG_C_RESIDUAL,
+ SG_C_UNCHANGED) = range(7)
 SG_PRE, SG_POST = 0, 1
 SG_CONTRACTS_OFF, SG_CONTRACTS_PRE, SG_CONTRACTS_PRE_POST, SG_CONTRACTS_FULL = range(4)
 SG_FUSE_OFF, SG_FUSE_ON = 0, 1
@@ -135,7 +136,7 @@ def _load():
         "sg_solve": [vp, vp, vp, P(SgSolveOpts), P(vp), P(SgSolveInfo)],
         "sg_det": [vp, vp, i32, P(SgDetResult)],
         "sg_require": [vp, vp, P(SgContract), P(C.c_int32)],
-        "sg_ensure": [vp, vp, P(SgContract), P(C.c_int32)],
+        "sg_ensure": [vp, vp, P(SgContract), P(C.c_int32)], "sg_old": [vp, vp, P(vp)],
         "sg_last_violation": [vp, P(SgViolation)], "sg_flush": [vp],
         "sg_set_contract_mode": [vp, i32], "sg_set_fusion": [vp, i32],
         "sg_set_scheduler": [vp, i32], "sg_set_codegen": [vp, i32], "sg_plan_describe": [vp, C.c_char_p, sz, P(sz)],
@@ -448,6 +449,11 @@ def sg_require(ctx, target, c: SgContract) -> int:
     cid = C.c_int32()
     _check(lib.sg_require(ctx, target, C.byref(c), C.byref(cid)), ctx)
     return cid.value
+
+
+def sg_old(ctx, target):
+    """Eiffel's `old`: the fingerprint of target at this point of the queue."""
+    return _out(lib.sg_old, ctx, ctx, target)
 
 
 def sg_ensure(ctx, target, c: SgContract) -> int:
