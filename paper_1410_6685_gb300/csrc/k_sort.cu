@@ -21,10 +21,12 @@
 //   (b) carries the last key of every digit run through the look-back words
 //   so each run's first key is compared with its predecessor in the output,
 //   and (c) accumulates the output's multiset fingerprint (sum of mix(k),
-//   sum of mix(k)^2 mod 2^64, count; mix = MurmurHash3's 32-bit finalizer, a
-//   bijection) for comparison with the input's.  No extra pass over the keys
-//   is needed.
+//   sum of mix(k)^2 mod 2^64, count; mix(k) = rot16(k * c1) * c2 with odd
+//   c1, c2, a bijection of 32-bit words) for comparison with the input's.  No
+//   extra pass over the keys is needed.
 #include <stdint.h>
+
+#include <climits>
 
 #include "sg_internal.h"
 
@@ -35,7 +37,7 @@ constexpr int kSortBlock = 256;
 constexpr int kSortMinBlocks = 4;   // resident CTAs per SM the registers are sized for
 constexpr int kKpt = 24;
 constexpr int kTile = kSortBlock * kKpt;   // 6144 keys
-constexpr int kMatchEvery = 4;
+constexpr int kMatchEvery = 8;
 constexpr int kRadix = 256;
 constexpr int kWarps = kSortBlock / 32;
 constexpr int kWarpKeys = 32 * kKpt;
@@ -59,8 +61,14 @@ struct SortHdr {
   unsigned offs[4][kRadix];
   unsigned tile_ctr[4];
   unsigned done_ctr;
-  unsigned pad[59];
+  unsigned pad[27];
+  // a look-back wait gave up (also recorded in the result record); on a line
+  // of its own, away from the tickets and the result record's atomics, since
+  // every CTA of a later pass reads it when it starts
+  int failed;
+  unsigned pad2[31];
 };
+static_assert(sizeof(SortHdr) % 128 == 0, "header lines");
 
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
   unsigned v;
@@ -128,33 +136,75 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* s_warp
   return x - v + s_warp[w];
 }
 
-// MurmurHash3's 32-bit finalizer (Appleby): a bijection of 32-bit words, so
-// replacing one key by another always changes the sums below.
-__device__ __forceinline__ unsigned fmix32(unsigned h) {
-  h ^= h >> 16;
-  h *= 0x85ebca6bu;
-  h ^= h >> 13;
-  h *= 0xc2b2ae35u;
-  h ^= h >> 16;
-  return h;
+// The key mix of the multiset fingerprint: multiply by an odd constant,
+// rotate by 16, multiply by another odd constant.  Each step is a bijection
+// of 32-bit words, so replacing one key by another always changes the sums
+// below; the rotation makes the map non-linear in the key.  Two multiplies
+// and one byte permute: cheap enough for a pass bound by instruction issue.
+__device__ __forceinline__ unsigned key_mix(unsigned k) {
+  return __byte_perm(k * 0x9E3779B1u, 0u, 0x1032) * 0x85EBCA77u;
 }
 
+// f1 += m, f2 += m * m as 64-bit sums, both as multiply-adds (the FMA pipe,
+// which the ranking leaves idle)
 __device__ __forceinline__ void fp_add(unsigned long long& f1, unsigned long long& f2, int k) {
-  const unsigned m = fmix32((unsigned)k);
-  f1 += m;
-  f2 += (unsigned long long)m * m;
+  const unsigned m = key_mix((unsigned)k);
+  asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(f1) : "r"(m));
+  asm("mad.wide.u32 %0, %1, %1, %0;" : "+l"(f2) : "r"(m));
 }
 
+// 64-bit look-back word of the checked last pass: flag (2 bits) | count (30)
+// | the last key before the end of this tile's run of the digit (32)
+__device__ __forceinline__ unsigned long long lb_word(unsigned flag, unsigned c, int k) {
+  return ((unsigned long long)((flag << 30) | c) << 32) | (unsigned)k;
+}
+
+// The lanes holding the same 8-bit digit: one ballot per digit bit; a lane
+// keeps the ballot where its own bit is set and its complement where it is
+// clear.  Written as PTX so that each bit costs a predicate, a vote, a
+// predicated complement and an AND (the compiler's code for the same C was
+// measured 9% slower per pass).
+__device__ __forceinline__ unsigned digit_peers(unsigned d) {
+  unsigned peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    asm("{\n\t.reg .pred p;\n\t.reg .b32 m, t;\n\t"
+        "and.b32 t, %1, %2;\n\t"
+        "setp.ne.u32 p, t, 0;\n\t"
+        "vote.sync.ballot.b32 m, p, 0xffffffff;\n\t"
+        "@!p not.b32 m, m;\n\t"
+        "and.b32 %0, %0, m;\n\t}"
+        : "+r"(peers)
+        : "r"(d), "r"(1u << b));
+  }
+  return peers;
+}
+
+// The block's fingerprint sums into dst with one pair of atomics per CTA
+// (one pair per warp put some 10^5 same-address atomics on one L2 line per
+// pass).  s_fp: 2 x (blockDim.x / 32) words of shared memory.  Contains
+// __syncthreads: every thread of the block calls it.
 __device__ __forceinline__ void fp_flush(unsigned long long f1, unsigned long long f2,
-                                         unsigned long long* dst) {
+                                         unsigned long long* dst, unsigned long long* s_fp) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     f1 += __shfl_xor_sync(0xffffffffu, f1, o);
     f2 += __shfl_xor_sync(0xffffffffu, f2, o);
   }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(dst, f1);
-    atomicAdd(dst + 1, f2);
+    s_fp[w] = f1;
+    s_fp[nw + w] = f2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, b = 0;
+    for (int i = 0; i < nw; ++i) {
+      a += s_fp[i];
+      b += s_fp[nw + i];
+    }
+    atomicAdd(dst, a);
+    atomicAdd(dst + 1, b);
   }
 }
 
@@ -196,7 +246,8 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
     }
   }
   for (long long i = start + tid; i < n; i += stride) count(in[i]);
-  if (FP) fp_flush(f1, f2, res->fp_in);
+  __shared__ unsigned long long s_fp[2 * 8];
+  if (FP) fp_flush(f1, f2, res->fp_in, s_fp);
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
     const unsigned c = (&sh[0][0])[i];
@@ -224,20 +275,26 @@ __global__ void __launch_bounds__(256) k_radix_hist(const int* __restrict__ in, 
 }
 
 // ---------------------------------------------------------------------------
+template <bool CK>
 struct SortSmem {
-  int keys[kTile];
+  int keys[kTile + 1];   // + a sentinel after the tile's keys (checked pass)
   unsigned whist[kWarps][kRadix];
+  // checked pass: the last key of each warp's keys of each digit, so that a
+  // tile's digit runs know their last keys before the tile is sorted in
+  // shared memory
+  int lastk[CK ? kWarps : 1][kRadix];
   int gbase[kRadix];
   unsigned warp[kWarps];
   unsigned tile;
   int timeout;
+  unsigned long long fp[2 * kWarps];
   unsigned short rank[kTile];
 };
 
 // One tile of one pass.  FULL: the tile holds kTile keys (every tile but the
 // last), so no index is checked against n.
 template <bool LAST, bool CHECK, bool FULL, bool FLT>
-__device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restrict__ in,
+__device__ __forceinline__ void onesweep_tile(SortSmem<LAST && CHECK>& sm, const int* __restrict__ in,
                                               int* __restrict__ out, long long n, int pass,
                                               SortHdr* h, unsigned* st32,
                                               unsigned long long* st64, SortResult* res,
@@ -269,25 +326,19 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   // stable rank of each key among the warp's keys of the same digit; the
   // lanes holding the same digit are found with match_any, or with eight
   // ballots (one per digit bit) and a ninth that separates the padding lanes
-  // of a partial tile
+  // of a partial tile.  match_any costs grow with the number of distinct
+  // digits among the lanes (uniform keys: about 28 of 32), so it takes one
+  // round in kMatchEvery, where it overlaps the ballots of the others
   const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int r = 0; r < kKpt; ++r) {
     const bool ok = full || (wbase + r * 32) < n;
     const unsigned d = digit_of<LAST, FLT>(key[r], dsel);
     unsigned peers;
-    if (r % kMatchEvery == 0) {
-      // one round in kMatchEvery on the match unit, the others on ballots,
-      // so that the two kinds of instruction overlap
+    if (r % kMatchEvery == kMatchEvery - 1) {
       peers = __match_any_sync(0xffffffffu, ok ? d : 0x1000u);
     } else {
-      peers = 0xffffffffu;
-#pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const unsigned bit = (d >> b) & 1u;
-        const unsigned bal = __ballot_sync(0xffffffffu, bit);
-        peers &= bal ^ (bit - 1u);        // lanes whose bit b equals mine
-      }
+      peers = digit_peers(d);
       if (!full) {
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
         peers &= ok ? bal : ~bal;
@@ -297,6 +348,9 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
     const unsigned prev = ok ? s_whist[w][d] : 0u;
     __syncwarp();
     if (ok && before == 0) s_whist[w][d] = prev + __popc(peers);
+    // checked pass: the highest lane of the group holds the warp's latest
+    // key of this digit (rounds are in key order)
+    if (LAST && CHECK && ok && (peers >> lane) == 1u) sm.lastk[w][d] = key[r];
     __syncwarp();
     s_rank[lbase + r * 32] = (unsigned short)(prev + before);
   }
@@ -305,6 +359,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   // per digit (threads 0..255): tile count and exclusive offsets of the warps
   const bool dig = kSortBlock == kRadix || tid < kRadix;
   unsigned cnt = 0;
+  int last_key = 0;   // checked pass: last key of this tile's run of digit tid
   if (dig) {
     const int d = tid;
 #pragma unroll
@@ -312,10 +367,15 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
       const unsigned t = s_whist[ww][d];
       s_whist[ww][d] = cnt;
       cnt += t;
+      if (LAST && CHECK && t) last_key = sm.lastk[ww][d];
     }
     // publish the tile aggregate as early as possible
-    if (!(LAST && CHECK) && publish)
-      st_relaxed(&st32[(size_t)tile * kRadix + tid], ((tile == 0 ? kPre : kAgg) << 30) | cnt);
+    if (publish) {
+      if (!(LAST && CHECK))
+        st_relaxed(&st32[(size_t)tile * kRadix + tid], ((tile == 0 ? kPre : kAgg) << 30) | cnt);
+      else
+        st_relaxed64(&st64[(size_t)tile * kRadix + tid], lb_word(tile == 0 ? kPre : kAgg, cnt, last_key));
+    }
   }
   const unsigned start = block_excl_scan(cnt, sm.warp);
   if (dig) {
@@ -333,6 +393,9 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
       s_keys[s_whist[w][d] + s_rank[lbase + r * 32]] = key[r];
     }
   }
+  // checked pass: a sentinel above every key (okey 0xFFFFFFFF) after the
+  // last one, so that every key has a successor to be compared with
+  if (LAST && CHECK && tid == 0) s_keys[valid_cnt] = FLT ? 0x7FFFFFFF : INT_MAX;
   __syncthreads();
 
   // decoupled look-back: exclusive prefix of digit `tid` over earlier tiles
@@ -380,18 +443,13 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
       if (publish) st_relaxed(&st32[(size_t)tile * kRadix + d], (kPre << 30) | (unsigned)(excl + cnt));
     }
   } else {
-    // 64-bit words: flag(2) | count(30) | last key of the digit run (32)
+    // 64-bit words: flag(2) | count(30) | last key of the digit run (32),
+    // the aggregate published above with the run's last key
     const int first_key = cnt ? s_keys[start] : 0;
-    const int last_key = cnt ? s_keys[start + cnt - 1] : 0;
-    auto word = [](unsigned flag, unsigned c, int k) {
-      return ((unsigned long long)((flag << 30) | c) << 32) | (unsigned)k;
-    };
+    auto word = lb_word;
     bool found = false;
     int pred_last = 0;
-    if (tile == 0) {
-      if (publish) st_relaxed64(&st64[d], word(kPre, cnt, last_key));
-    } else {
-      if (publish) st_relaxed64(&st64[(size_t)tile * kRadix + d], word(kAgg, cnt, last_key));
+    if (tile > 0) {
       // the same windowed walk as above; the first run met with keys
       // gives the last key before this tile's run
       long long j = (long long)tile - 1;
@@ -440,6 +498,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
   }
   if (timeout) {
     atomicExch(&res->timeout, 1);
+    atomicExch(&h->failed, 1);
     sm.timeout = 1;
   }
   if (dig) s_gbase[d] = (int)h->offs[pass][d] + (int)excl - (int)start;
@@ -449,27 +508,31 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
 
   // write the tile out in digit runs
   unsigned long long f1 = 0, f2 = 0;
-  long long bad = -1;
+  int bad = INT_MAX;
 #pragma unroll 4
   for (int i = tid; i < valid_cnt; i += kSortBlock) {
     const int k = s_keys[i];
     const unsigned dk = digit_of<LAST, FLT>(k, dsel);
     const int pos = s_gbase[dk] + i;
-    // a planted fault (a key changed between passes) can carry a digit run
-    // past the histogram's offsets: never write outside the output
-    if (write && (unsigned)pos < (unsigned)n) __stcs(out + pos, k);
+    // the last pass runs after the host's contract-test fault planting (a key
+    // changed between passes can carry a digit run past the histogram's
+    // offsets): there, never write outside the output.  Earlier passes read
+    // what the previous pass wrote, whose digit counts are the histogram's.
+    if (write && (!LAST || (unsigned)pos < (unsigned)n)) __stcs(out + pos, k);
     if (LAST && CHECK) {
       fp_add(f1, f2, k);
-      if (i + 1 < valid_cnt) {
-        const int k2 = s_keys[i + 1];
-        if (digit_of<LAST, FLT>(k2, dsel) == dk && okey<FLT>(k) > okey<FLT>(k2) && bad < 0)
-          bad = pos;
-      }
+      // the tile is sorted by the most significant digit and each digit
+      // run by the lower ones: every adjacent pair of the tile is in order
+      // (runs of different digits trivially), and pairs inside a run are
+      // adjacent in the output too
+      const int k2 = s_keys[i + 1];
+      const bool desc = FLT ? okey<true>(k) > okey<true>(k2) : k > k2;
+      if (desc) bad = min(bad, pos);
     }
   }
   if (LAST && CHECK) {
-    fp_flush(f1, f2, res->fp_out);
-    unsigned long long enc = bad >= 0 ? ~(unsigned long long)bad : 0ull;
+    fp_flush(f1, f2, res->fp_out, sm.fp);
+    unsigned long long enc = bad != INT_MAX ? ~(unsigned long long)(long long)bad : 0ull;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long e2 = __shfl_xor_sync(0xffffffffu, enc, o);
@@ -478,7 +541,7 @@ __device__ __forceinline__ void onesweep_tile(SortSmem& sm, const int* __restric
     if (lane == 0 && enc) atomicMax(&res->unsorted_enc, enc);
     if (tid == 0) {
       atomicAdd((unsigned long long*)&res->cnt_out, (unsigned long long)valid_cnt);
-      res->checked = 1;
+      if (tile == 0) res->checked = 1;
     }
   }
 }
@@ -488,12 +551,12 @@ __global__ void __launch_bounds__(kSortBlock, kSortMinBlocks) k_onesweep(
     const int* __restrict__ in, int* __restrict__ out, long long n, int pass, SortHdr* h,
     unsigned* st32, unsigned long long* st64, SortResult* res, unsigned ahead,
     const LookbackCtl lb) {
-  __shared__ SortSmem sm;
+  __shared__ SortSmem<LAST && CHECK> sm;
   const int tid = threadIdx.x;
   if (tid == 0) {
     // an earlier pass whose look-back gave up left its output incomplete:
     // this pass does nothing
-    sm.timeout = pass > 0 ? *reinterpret_cast<volatile int*>(&res->timeout) : 0;
+    sm.timeout = pass > 0 ? *reinterpret_cast<volatile int*>(&h->failed) : 0;
     if (!sm.timeout) sm.tile = atomicAdd(&h->tile_ctr[pass], 1u);
   }
   for (int i = tid; i < kWarps * kRadix; i += kSortBlock) (&sm.whist[0][0])[i] = 0;
@@ -548,7 +611,8 @@ __global__ void __launch_bounds__(256) k_fingerprint(const int* __restrict__ x, 
   const long long stride = (long long)gridDim.x * blockDim.x;
   unsigned long long f1 = 0, f2 = 0;
   for (long long i = tid; i < n; i += stride) fp_add(f1, f2, __ldg(x + i));
-  fp_flush(f1, f2, fp);
+  __shared__ unsigned long long s_fp[2 * 8];
+  fp_flush(f1, f2, fp, s_fp);
   if (tid == 0) *cnt = n;
 }
 

@@ -2,7 +2,7 @@
 
 A small command-line driver for measuring and profiling single kernels:
 
-    python -m paper_1410_6685_gb300.workloads sort   [--n N] [--reps R]
+    python -m paper_1410_6685_gb300.workloads sort   [--n N] [--reps R] [--contracts on|off]
     python -m paper_1410_6685_gb300.workloads stream [--n N] [--reps R]
     python -m paper_1410_6685_gb300.workloads gemm   [--n N] [--reps R] [--prec 0|1|2]
     python -m paper_1410_6685_gb300.workloads solve  [--n N] [--reps R] [--prec 0|1|2]
@@ -32,6 +32,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--prec", type=int, default=1)
+    ap.add_argument("--contracts", choices=["on", "off"], default="on",
+                    help="off: contract mode SG_CONTRACTS_OFF (the unchecked schedule)")
     a = ap.parse_args(argv)
 
     import torch
@@ -44,6 +46,8 @@ def main(argv=None):
     from paper_1410_6685_gb300 import safegpu as sg
 
     ctx = sg.sg_init(0, torch.cuda.current_stream().cuda_stream)
+    if a.contracts == "off":
+        sg.sg_set_contract_mode(ctx, sg.SG_CONTRACTS_OFF)
     keep = []
     out = {"case": a.case}
 
