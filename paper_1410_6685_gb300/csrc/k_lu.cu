@@ -2,9 +2,10 @@
 // partial pivoting) and the solve with iterative refinement (sm_103a).
 //
 // Right-looking blocked LU, panels of 32 columns:
-//   k_lu_panel   : a cluster of 16 CTAs (8 where the device cannot schedule
-//                  16) holds the panel (rows k..n-1) in their
-//                  shared memories and eliminates it column by column.  Each
+//   k_lu_panel_reg / k_lu_panel : a cluster of 16 CTAs (8 where the device
+//                  cannot schedule 16) holds the panel (rows k..n-1) -- in
+//                  registers (16 CTAs) or in shared memory (8 CTAs) -- and
+//                  eliminates it column by column.  Each
 //                  column costs one exchange: every CTA sends its best pivot
 //                  candidate (largest |a|, then the lowest current row
 //                  position) together with that row into every CTA's shared
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(kPT)
     const float d = prow[j];
     const bool zero = d == 0.0f;
     if (zero && my_info == 0) my_info = k + j + 1;
+    const float rd = 1.0f / d;
     // eliminate below the pivot; find the next column's candidate
     mine = 0ull;
 #pragma unroll
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(kPT)
       if (r >= r1 || lp[i] <= j) continue;
       float* row = slab + (r - r0) * kStride;
       if (!zero) {
-        const float l = row[j] / d;
+        const float l = row[j] * rd;   // a product with the reciprocal, as in the register form
         row[j] = l;
         for (int c = j + 1; c < jb; ++c) row[c] = fmaf(-l, prow[c], row[c]);
       }
@@ -292,6 +294,243 @@ __global__ void __launch_bounds__(kPT)
     for (int e = tid; e < cnt * nci; e += kPT) {
       const int t = e / nci, i = e % nci, g = rank + i * PC;
       const int c = g < nl ? c_lo + g : k + jb + (g - nl);
+      LU[(size_t)moves[1 + 2 * kPB + t] * n + c] = xbuf[t * kXCols + i];
+    }
+  }
+}
+
+// The 16-CTA panel with each thread's rows in registers.  Shared memory
+// traffic bounds the slab form above at large heights: every column reads
+// and writes the whole remaining panel there.  Here a thread keeps its rows
+// (at most kRows of them) as 32 registers each, in a layout shifted by one
+// per column: at step j, register c of a row holds column j + c, so every
+// register index is a compile-time constant although j is not.  An L entry
+// goes to shared memory (lbuf, stride 33) when it is formed; a row chosen as
+// the pivot writes its U part there and retires.  Per column: each warp's
+// best candidate (two redux.sync maxima: magnitude, then position and row)
+// stages its row (in the same shifted layout); one CTA barrier; every
+// thread finds the CTA's best among the warps' keys by a lane-parallel
+// maximum; the CTA's key and staged row go to every CTA of the cluster by
+// asynchronous remote stores (as in the slab form); the cluster's winner is
+// again a lane-parallel maximum, and its row arrives pre-shifted.  The
+// interchanges, the zero-pivot rule and the write-back are the slab form's.
+template <int PC>
+__global__ void __launch_bounds__(kPT, 1)
+    k_lu_panel_reg(float* __restrict__ LU, int n, int k, int jb, int* __restrict__ piv,
+                   int* __restrict__ info, int* __restrict__ moves, int c_lo, int c_hi) {
+  constexpr int kRows = max_rows_per_thread<PC>();
+  constexpr int kW = kPT / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int m = n - k;
+  const int rs = (m + PC - 1) / PC;
+  const int r0 = rank * rs;
+  const int r1 = min(m, r0 + rs);
+  float* lbuf = reinterpret_cast<float*>(smem);   // [rs][kStride]: the slab, then L\U
+  float* stage = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(lbuf + (size_t)rs * kStride) + 15) & ~(uintptr_t)15);  // [2][kW][32]
+  float* crow = stage + 2 * kW * kPB;                                                    // [2][PC][32]
+  unsigned long long* wkey = reinterpret_cast<unsigned long long*>(crow + 2 * PC * kPB);  // [2][kW]
+  unsigned long long* cand = wkey + 2 * kW;                                              // [2][PC]
+  unsigned long long* bar = cand + 2 * PC;                                               // [2]
+  float* xbuf = reinterpret_cast<float*>(bar + 2);                                       // [2 kPB][kXCols]
+  int* fpos = reinterpret_cast<int*>(xbuf + 2 * kPB * kXCols);                           // [rs]
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, w = tid >> 5;
+
+  // the slab, eight loads in flight per thread (a warp reads one row per load)
+  const int total = (r1 - r0) * kPB;
+  for (int base = 0; base < total; base += 8 * kPT) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = base + u * kPT + tid, r = t >> 5, c = t & 31;
+      v[u] = (t < total && c < jb) ? __ldg(LU + (size_t)(k + r0 + r) * n + k + c) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = base + u * kPT + tid;
+      if (t < total) lbuf[(t >> 5) * kStride + (t & 31)] = v[u];
+    }
+  }
+  if (tid < 2) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&bar[tid])) : "memory");
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  // every CTA's barriers exist before anyone sends; the slab is complete
+  cluster.sync();
+  // my rows: r = r0 + tid + i * kPT; positions and values in registers
+  float x[kRows][kPB];
+  int lp[kRows];
+  bool act[kRows];
+#pragma unroll
+  for (int i = 0; i < kRows; ++i) {
+    const int r = r0 + tid + i * kPT;
+    lp[i] = r;
+    act[i] = r < r1;
+#pragma unroll
+    for (int c = 0; c < kPB; ++c) x[i][c] = act[i] ? lbuf[(r - r0) * kStride + c] : 0.0f;
+  }
+  int my_info = 0;
+  bool failed = false;
+  for (int j = 0; j < jb; ++j) {
+    const int par = j & 1;
+    const uint32_t mbar = sm_addr(&bar[par]);
+    // this thread's and this warp's best candidate for column j (register 0)
+    unsigned long long mine = 0ull;
+    int mi = -1;
+#pragma unroll
+    for (int i = 0; i < kRows; ++i)
+      if (act[i]) {
+        const unsigned long long kk = key_of(x[i][0], lp[i], r0 + tid + i * kPT);
+        if (kk > mine) { mine = kk; mi = i; }
+      }
+    const unsigned mh = __reduce_max_sync(0xffffffffu, (unsigned)(mine >> 32));
+    const unsigned ml = __reduce_max_sync(0xffffffffu, (unsigned)(mine >> 32) == mh ? (unsigned)mine : 0u);
+    const unsigned long long wk = ((unsigned long long)mh << 32) | ml;
+    // the warp's winner stages its row (keys carry the row: the winner is unique)
+    if (wk != 0ull && mine == wk) {
+      float4* st = reinterpret_cast<float4*>(stage + (par * kW + w) * kPB);
+#pragma unroll
+      for (int i = 0; i < kRows; ++i)
+        if (i == mi) {
+#pragma unroll
+          for (int q = 0; q < kPB / 4; ++q)
+            st[q] = make_float4(x[i][4 * q], x[i][4 * q + 1], x[i][4 * q + 2], x[i][4 * q + 3]);
+        }
+    }
+    if (lane == 0) wkey[par * kW + w] = wk;
+    if (tid == 0)   // this column's bytes from the cluster complete bar[par]
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
+                   "r"(col_bytes<PC>()) : "memory");
+    __syncthreads();
+    // the CTA's best: lane q looks at warp q's key
+    unsigned long long b;
+    int bw;
+    {
+      const unsigned long long u = lane < kW ? wkey[par * kW + lane] : 0ull;
+      const unsigned uh = (unsigned)(u >> 32);
+      const unsigned bh = __reduce_max_sync(0xffffffffu, uh);
+      const unsigned bl = __reduce_max_sync(0xffffffffu, uh == bh ? (unsigned)u : 0u);
+      b = ((unsigned long long)bh << 32) | bl;
+      const unsigned hit = __ballot_sync(0xffffffffu, b != 0ull && u == b);
+      bw = hit ? __ffs(hit) - 1 : 0;
+    }
+    // send the key and its row to every CTA of the cluster; the stores
+    // complete on the receivers' bar[par].  A CTA sends column j + 2 only
+    // after it has all of column j + 1, which every CTA sends only after
+    // reading column j: two slots suffice (for stage too).
+    if (tid < PC) {
+      st_async_b64(cl_addr(sm_addr(&cand[par * PC + rank]), tid), b, cl_addr(mbar, tid));
+    } else if (tid >= 32) {
+      const float4* srow = reinterpret_cast<const float4*>(stage + (par * kW + bw) * kPB);
+      for (int e = tid - 32; e < PC * (kPB / 4); e += kPT - 32) {
+        const int q = e / (kPB / 4), part = e % (kPB / 4);
+        st_async_v4(cl_addr(sm_addr(&crow[(par * PC + rank) * kPB + 4 * part]), q),
+                    b ? srow[part] : make_float4(0.f, 0.f, 0.f, 0.f), cl_addr(mbar, q));
+      }
+    }
+    // after a wait gave up nothing is written back; later columns do not wait
+    if (!failed && !bar_wait(mbar, (uint32_t)(j >> 1) & 1u)) failed = true;
+    unsigned long long g;
+    int wq;
+    {
+      const unsigned long long u = lane < PC ? cand[par * PC + lane] : 0ull;
+      const unsigned uh = (unsigned)(u >> 32);
+      const unsigned gh = __reduce_max_sync(0xffffffffu, uh);
+      const unsigned gl = __reduce_max_sync(0xffffffffu, uh == gh ? (unsigned)u : 0u);
+      g = ((unsigned long long)gh << 32) | gl;
+      const unsigned hit = __ballot_sync(0xffffffffu, g != 0ull && u == g);
+      wq = hit ? __ffs(hit) - 1 : 0;
+    }
+    const int p = (int)(0xFFFFu - (unsigned)((g >> 16) & 0xFFFFu));   // winning position
+    const int gp = (int)(g & 0xFFFFu);                                // its row in the panel
+    // the pivot row, shifted: pv[c] is column j + c
+    float pv[kPB];
+    {
+      const float4* pr = reinterpret_cast<const float4*>(crow + (par * PC + wq) * kPB);
+#pragma unroll
+      for (int q = 0; q < kPB / 4; ++q) {
+        const float4 v = pr[q];
+        pv[4 * q] = v.x; pv[4 * q + 1] = v.y; pv[4 * q + 2] = v.z; pv[4 * q + 3] = v.w;
+      }
+    }
+    const float d = pv[0];
+    const bool zero = d == 0.0f;
+    if (zero && my_info == 0) my_info = k + j + 1;
+    const float rd = 1.0f / d;
+    // interchange of positions j and p; the pivot row writes its U part
+    // (columns j..jb-1) and retires
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+      const int r = r0 + tid + i * kPT;
+      if (lp[i] == j) lp[i] = p;
+      if (act[i] && r == gp) {
+        lp[i] = j;
+        act[i] = false;
+        float* dst = lbuf + (r - r0) * kStride + j;
+#pragma unroll
+        for (int c = 0; c < kPB; ++c)
+          if (c < jb - j) dst[c] = x[i][c];
+      }
+    }
+    // eliminate below the pivot: l = a_ij / u_jj (as a product with the
+    // reciprocal), then shift the row by one column while updating it
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+      if (!act[i]) continue;
+      const int r = r0 + tid + i * kPT;
+      const float l = zero ? x[i][0] : x[i][0] * rd;
+      lbuf[(r - r0) * kStride + j] = l;
+#pragma unroll
+      for (int c = 0; c + 1 < kPB; ++c) x[i][c] = zero ? x[i][c + 1] : fmaf(-l, pv[c + 1], x[i][c + 1]);
+      x[i][kPB - 1] = 0.0f;
+    }
+    if (tid == 0 && rank == 0) piv[k + j] = k + p;
+  }
+  if (failed) atomicCAS(info, 0, -1);   // a wait gave up: report, write nothing
+  const bool any_failed = __syncthreads_or(failed);
+  cluster.sync();   // no CTA reads another's shared memory after this
+  // list the rows that moved (at most 2 jb) for the other columns'
+  // interchange; keep every row's final position for the write-back
+  if (!any_failed) {
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+      const int r = r0 + tid + i * kPT;
+      if (r >= r1) continue;
+      fpos[r - r0] = lp[i];
+      if (lp[i] != r) {
+        const int t = atomicAdd(&moves[0], 1);
+        if (t < 2 * kPB) {
+          moves[1 + t] = k + r;
+          moves[1 + 2 * kPB + t] = k + lp[i];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // write the panel back in its final row order, one row per warp store
+  if (!any_failed) {
+    for (int t = tid; t < total; t += kPT) {
+      const int r = t >> 5, c = t & 31;
+      if (c < jb) LU[(size_t)(k + fpos[r]) * n + k + c] = lbuf[r * kStride + c];
+    }
+  }
+  if (tid == 0 && rank == 0 && my_info) atomicCAS(info, 0, my_info);
+  cluster.sync();   // every CTA's moves are listed
+  // the interchanges on the outer block's other columns, as in the slab form
+  const int nl = k - c_lo, nc = nl + (c_hi - k - jb);
+  const int nci = nc > rank ? (nc - rank + PC - 1) / PC : 0;
+  if (!any_failed && nci > 0) {
+    const int cnt = min(moves[0], 2 * kPB);
+    for (int e = tid; e < cnt * nci; e += kPT) {
+      const int t = e / nci, i = e % nci, gg = rank + i * PC;
+      const int c = gg < nl ? c_lo + gg : k + jb + (gg - nl);
+      xbuf[t * kXCols + i] = LU[(size_t)moves[1 + t] * n + c];
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt * nci; e += kPT) {
+      const int t = e / nci, i = e % nci, gg = rank + i * PC;
+      const int c = gg < nl ? c_lo + gg : k + jb + (gg - nl);
       LU[(size_t)moves[1 + 2 * kPB + t] * n + c] = xbuf[t * kXCols + i];
     }
   }
@@ -780,12 +1019,23 @@ size_t panel_smem(int n, int k) {
 }
 
 template <int PC>
+size_t panel_reg_smem(int n, int k) {
+  const int m = n - k;
+  const int rs = (m + PC - 1) / PC;
+  constexpr int kW = kPT / 32;
+  return (size_t)rs * kStride * 4 + 16 + 2 * kW * kPB * 4 + 2 * PC * kPB * 4 + 2 * kW * 8 +
+         2 * PC * 8 + 2 * 8 + 2 * kPB * kXCols * 4 + (size_t)rs * 4 + 64;
+}
+
+// the 16-CTA form keeps rows in registers (k_lu_panel_reg); the 8-CTA
+// portable form keeps the slab in shared memory (k_lu_panel)
+template <int PC>
 cudaError_t launch_panel(float* LU, int n, int k, int jb, int* piv, int* info, int* moves,
                          int c_lo, int c_hi, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(PC);
   cfg.blockDim = dim3(kPT);
-  cfg.dynamicSmemBytes = panel_smem<PC>(n, k);
+  cfg.dynamicSmemBytes = PC == 16 ? panel_reg_smem<PC>(n, k) : panel_smem<PC>(n, k);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -794,7 +1044,10 @@ cudaError_t launch_panel(float* LU, int n, int k, int jb, int* piv, int* info, i
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_lu_panel<PC>, LU, n, k, jb, piv, info, moves, c_lo, c_hi);
+  if constexpr (PC == 16)
+    return cudaLaunchKernelEx(&cfg, k_lu_panel_reg<PC>, LU, n, k, jb, piv, info, moves, c_lo, c_hi);
+  else
+    return cudaLaunchKernelEx(&cfg, k_lu_panel<PC>, LU, n, k, jb, piv, info, moves, c_lo, c_hi);
 }
 
 // 16 when one cluster of 16 CTAs with the largest panel fits the device
@@ -802,14 +1055,14 @@ bool use_cluster16() {
   static int v = -1;
   if (v < 0) {
     v = 0;
-    if (cudaFuncSetAttribute(k_lu_panel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+    if (cudaFuncSetAttribute(k_lu_panel_reg<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess &&
-        cudaFuncSetAttribute(k_lu_panel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)panel_smem<16>(kLuMaxN, 0)) == cudaSuccess) {
+        cudaFuncSetAttribute(k_lu_panel_reg<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)panel_reg_smem<16>(kLuMaxN, 0)) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(16);
       cfg.blockDim = dim3(kPT);
-      cfg.dynamicSmemBytes = panel_smem<16>(kLuMaxN, 0);
+      cfg.dynamicSmemBytes = panel_reg_smem<16>(kLuMaxN, 0);
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = 16;
@@ -818,7 +1071,7 @@ bool use_cluster16() {
       cfg.attrs = at;
       cfg.numAttrs = 1;
       int clusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&clusters, k_lu_panel<16>, &cfg) == cudaSuccess &&
+      if (cudaOccupancyMaxActiveClusters(&clusters, k_lu_panel_reg<16>, &cfg) == cudaSuccess &&
           clusters >= 1)
         v = 1;
     }
@@ -834,8 +1087,8 @@ size_t lu_panel_max_smem(int n) { return panel_smem<8>(n, 0); }
 cudaError_t lu_prepare(int n) {
   gemm_tc_prepare();
   const bool c16 = !portable_kernels() && use_cluster16();
-  const size_t ps = c16 ? panel_smem<16>(n, 0) : panel_smem<8>(n, 0);
-  cudaError_t e = c16 ? cudaFuncSetAttribute(k_lu_panel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps)
+  const size_t ps = c16 ? panel_reg_smem<16>(n, 0) : panel_smem<8>(n, 0);
+  cudaError_t e = c16 ? cudaFuncSetAttribute(k_lu_panel_reg<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps)
                       : cudaFuncSetAttribute(k_lu_panel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
   if (e != cudaSuccess) return e;
   const size_t mx = ((size_t)kLuOuter * (kLuOuter + 1) + (size_t)kLuOuter * 33) * sizeof(float);
