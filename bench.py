@@ -77,6 +77,17 @@ def peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+def sustained_tc_peak():
+    """bf16 TFLOP/s of a seconds-long cuBLAS loop (for kernels timed inside a
+    long step), else the burst figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p.get("bf16_tflops_sustained", p["bf16_tflops"]))
+    except Exception:
+        return 1700.0
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -380,14 +391,22 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
         xs, info = sg.sg_solve(ctx, mA, vb, o)
         info_box["it"] = info.iterations
         sg.sg_vector_release(xs)
-    ms = time_steps(torch, stream, s_solve, 2)
+    ms, kern = profiled(sg, ctx, lambda: time_steps(torch, stream, s_solve, 2))
     it_bf16 = info_box.get("it")
     # the plain form: every update in binary32 on the CUDA cores
     o.precision = sg.SG_PREC_F32_SIMT
-    ms32 = time_steps(torch, stream, s_solve, 2)
+    ms32, kern32 = profiled(sg, ctx, lambda: time_steps(torch, stream, s_solve, 2))
+    fl = 2 / 3 * n ** 3
+    f_ms, f32_ms = kern.get("lu_factor_graph"), kern32.get("lu_factor_graph")
     out["solve_gepp_8192"] = {"ms": round(ms, 3), "iterations": it_bf16,
-                              "GFLOPs": round(2 / 3 * n ** 3 / (ms / 1e3) / 1e9, 1),
+                              "GFLOPs": round(fl / (ms / 1e3) / 1e9, 1),
+                              "factor_ms": round(f_ms, 3) if f_ms else None,
+                              "LU_TFLOPs": round(fl / (f_ms / 1e3) / 1e12, 2) if f_ms else None,
+                              "LU_frac_of_sustained_bf16":
+                                  round(fl / (f_ms / 1e3) / 1e12 / sustained_tc_peak(), 4)
+                                  if f_ms else None,
                               "plain_f32_ms": round(ms32, 3),
+                              "plain_f32_factor_ms": round(f32_ms, 3) if f32_ms else None,
                               "plain_f32_iterations": info_box.get("it"),
                               "speedup_mixed_over_plain": round(ms32 / ms, 3)}
     sg.sg_matrix_release(mA)
@@ -533,6 +552,234 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
         "train_records": int(sg.sg_sched_log(ctx)[1].shape[0]), "train_loss": round(loss, 5),
         "train_s": round(t_train, 2)}
     return out
+
+
+def profiled(sg, ctx, fn):
+    """Runs fn with per-kernel event tracing: (result, {kernel: mean ms})."""
+    sg.sg_profile_enable(ctx, True)
+    sg.sg_profile_report(ctx, reset=True)
+    try:
+        r = fn()
+        prof = sg.sg_profile_report(ctx, reset=True)
+    finally:
+        sg.sg_profile_enable(ctx, False)
+    return r, {kk: v[1] / v[0] for kk, v in prof.items()}
+
+
+def cpu_time(fn, reps=1):
+    """Seconds of one call of a CPU oracle function (best of reps)."""
+    best = 1e300
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+def per_config_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak, tc_sustained):
+    """Every configuration of the benchmark plan as stated (vector add + sum
+    at 2^20 on the plain unfused path; GEMM at N = 1024 / 4096 / 8192 in the
+    three forms; GEPP + refinement at n = 2048 / 8192 in the three update
+    precisions; the batched chain and the filter with and without their
+    contracts), each with its contract overhead (the same steps with checking
+    off) and the oracle timed on one host core on a stated sample."""
+    import numpy as np
+    import oracle
+    from paper_1410_6685_gb300 import inputs
+    oracle.build()
+    res = {}
+
+    # config 1: a + b, ensure for_all(z = a + b), sum; n = 2^20, plain unfused
+    # path (one kernel per call; the postcondition re-reads a, b and z)
+    n = 1 << 20
+    a, b = inputs.vadd_inputs(n)
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    va, vb = sg.wrap_tensor(ctx, ta), sg.wrap_tensor(ctx, tb)
+    add = [("x", 0), ("x", 1), ("add",)]
+    post = sg.contract(sg.SG_C_FOR_ALL, [("x", 0), ("x", 1), ("x", 2), ("add",), ("eq",)],
+                       other=[va, vb])
+
+    def s_vadd():
+        z = sg.sg_zip(ctx, add, va, vb)
+        sg.sg_ensure(ctx, z, post)
+        r = sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, z)
+        sg.sg_scalar_get(ctx, r)
+        sg.sg_vector_release(z)
+        sg.sg_scalar_release(r)
+    row = {}
+    for fusion, name in ((sg.SG_FUSE_OFF, "unfused"), (sg.SG_FUSE_ON, "fused")):
+        sg.sg_set_fusion(ctx, fusion)
+        try:
+            ms = time_steps(torch, stream, s_vadd, 4 * k)
+            ms_off = with_contracts_off(sg, ctx, lambda: time_steps(torch, stream, s_vadd, 4 * k))
+        finally:
+            sg.sg_set_fusion(ctx, sg.SG_FUSE_ON)
+        row[name] = {"ms": round(ms, 4), "GBps_12B": round(12.0 * n / (ms / 1e3) / 1e9, 1),
+                     "ms_contracts_off": round(ms_off, 4),
+                     "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2)}
+    t_cpu = cpu_time(lambda: (oracle.sum(oracle.map(add, a, b)),
+                              oracle.first_false([("x", 0), ("x", 1), ("x", 2), ("add",), ("eq",)],
+                                                 a, b, oracle.map(add, a, b))), 3)
+    row["oracle"] = {"ms": round(t_cpu * 1e3, 3), "cores": 1,
+                     "sample": "the same n = 2^20 (map, for_all, binary64 sum)"}
+    row["note"] = "12.6 MB working set: L2-resident, launch-bound; HBM fractions are claimed at 2^28"
+    res["1_vadd_sum_2e20"] = row
+    sg.sg_vector_release(va)
+    sg.sg_vector_release(vb)
+    del ta, tb
+
+    # config 2 (second variant): the oracle on keys from 256 distinct values
+    ks = inputs.sort_keys_distinct(1 << 22)
+    t_cpu = cpu_time(lambda: oracle_step(ks))
+    res["2_sort_256_distinct_oracle"] = {
+        "GBps": round(BYTES_PER_KEY * len(ks) / t_cpu / 1e9, 4), "cores": 1,
+        "sample": "2^22 keys: C qsort + is_sorted + multiset equality"}
+
+    # config 3: C = A B, N(0,1), N in {1024, 4096, 8192}, binary32 SIMT and
+    # bf16 / fp16 operands on the tensor cores; built-in Freivalds check
+    names = {sg.SG_PREC_F32_SIMT: ("f32_simt", "gemm_f32_simt"),
+             sg.SG_PREC_BF16_TC: ("bf16_tc", "gemm_tc_bf16"),
+             sg.SG_PREC_F16_TC: ("f16_tc", "gemm_tc_f16")}
+    for N in (1024, 4096, 8192):
+        A, B = inputs.matmul_inputs(N)
+        tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        ma, mb = sg.wrap_tensor(ctx, tA), sg.wrap_tensor(ctx, tB)
+        for prec, (pname, kname) in names.items():
+            def s_mm():
+                c = sg.sg_matmul(ctx, ma, mb, prec)
+                sg.sg_flush(ctx)
+                sg.sg_matrix_release(c)
+            kk = k if N > 1024 else 4 * k
+            ms, kern = profiled(sg, ctx, lambda: time_steps(torch, stream, s_mm, kk))
+            ms_off = with_contracts_off(sg, ctx, lambda: time_steps(torch, stream, s_mm, kk))
+            g_ms = kern.get(kname)
+            fl = 2.0 * N ** 3
+            ent = {"ms_step": round(ms, 4), "TFLOPs_step": round(fl / (ms / 1e3) / 1e12, 1),
+                   "kernel_ms": round(g_ms, 4) if g_ms else None,
+                   "TFLOPs_kernel": round(fl / (g_ms / 1e3) / 1e12, 1) if g_ms else None,
+                   "ms_contracts_off": round(ms_off, 4),
+                   "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2),
+                   "per_kernel_ms": {x: round(v, 4) for x, v in kern.items()}}
+            if prec != sg.SG_PREC_F32_SIMT and g_ms:
+                # fp16 and bf16 share the nominal dense rate: the measured bf16 peak
+                ent["frac_tensor_kernel"] = round(fl / (g_ms / 1e3) / 1e12 / tc_peak, 4)
+            res["3_gemm_%d_%s" % (N, pname)] = ent
+        # the binary64 oracle on one core: the whole product at 1024, 16 rows above
+        rows = np.arange(N) if N == 1024 else np.arange(16)
+        t_cpu = cpu_time(lambda: oracle.matmul_rows_f64(A, B, rows))
+        res["3_gemm_%d_oracle" % N] = {
+            "GFLOPs": round(2.0 * len(rows) * N * N / t_cpu / 1e9, 3), "cores": 1,
+            "sample": "%d of %d rows of C, binary64" % (len(rows), N)}
+        sg.sg_matrix_release(ma)
+        sg.sg_matrix_release(mb)
+        del tA, tB
+
+    # config 4: GEPP + binary64 refinement, diagonally dominant, b = A 1,
+    # n in {2048, 8192}, trailing updates in binary32 / bf16 / fp16; the
+    # residual postcondition on and off
+    for n in (2048, 8192):
+        An, bn = inputs.gepp_inputs(n)
+        tA, tb = torch.from_numpy(An).cuda(), torch.from_numpy(bn).cuda()
+        mA, vb = sg.wrap_tensor(ctx, tA), sg.wrap_tensor(ctx, tb)
+        for prec, pname in ((sg.SG_PREC_F32_SIMT, "f32_simt"), (sg.SG_PREC_BF16_TC, "bf16_tc"),
+                            (sg.SG_PREC_F16_TC, "f16_tc")):
+            o = sg.SgSolveOpts()
+            o.precision, o.max_iter, o.refine_tol, o.residual_tol = prec, 30, 1e-14, 1e-12
+            box = {}
+
+            def s_solve():
+                xs, info = sg.sg_solve(ctx, mA, vb, o)
+                box["it"] = info.iterations
+                box["x"] = xs
+            def s_solve_rel():
+                s_solve()
+                sg.sg_vector_release(box.pop("x"))
+            kk = 3 if n > 2048 else 6
+            ms, kern = profiled(sg, ctx, lambda: time_steps(torch, stream, s_solve_rel, kk))
+            ms_off = with_contracts_off(sg, ctx, lambda: time_steps(torch, stream, s_solve_rel, kk))
+            s_solve()
+            xs = sg.sg_vector_read(ctx, box["x"], np.empty(n))
+            sg.sg_vector_release(box.pop("x"))
+            f_ms = kern.get("lu_factor_graph")
+            fl = 2.0 / 3.0 * n ** 3
+            res["4_solve_%d_%s" % (n, pname)] = {
+                "ms": round(ms, 3), "iterations": box.get("it"),
+                "max_abs_x_minus_1": float(np.max(np.abs(xs - 1.0))),
+                "factor_ms": round(f_ms, 3) if f_ms else None,
+                "LU_TFLOPs": round(fl / (f_ms / 1e3) / 1e12, 2) if f_ms else None,
+                "LU_frac_of_sustained_bf16": round(fl / (f_ms / 1e3) / 1e12 / tc_sustained, 4)
+                if f_ms else None,
+                "ms_contracts_off": round(ms_off, 3),
+                "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2),
+                "per_kernel_ms": {x: round(v, 4) for x, v in kern.items()}}
+        sg.sg_matrix_release(mA)
+        sg.sg_vector_release(vb)
+        del tA, tb
+    # the binary64 oracle (textbook GEPP + substitution) on one core at n = 1024
+    A1, b1 = inputs.gepp_inputs(1024)
+    t_cpu = cpu_time(lambda: oracle.solve(A1, b1))
+    res["4_solve_oracle"] = {"GFLOPs": round(2.0 / 3.0 * 1024 ** 3 / t_cpu / 1e9, 3), "cores": 1,
+                             "ms_n1024": round(t_cpu * 1e3, 1),
+                             "sample": "n = 1024 (2048 and 8192 are pinned by x = 1)"}
+
+    # config 5: the batched chain with its precondition and without (mode OFF)
+    L = inputs.batch_lengths()
+    off = inputs.batch_offsets(L)
+    total = int(off[-1])
+    g = torch.Generator(device="cuda").manual_seed(9)
+    xb = torch.rand(total, device="cuda", generator=g) * 2 - 1
+    to = torch.from_numpy(off).cuda()
+    nseg = len(L)
+    outs = (torch.empty(nseg, dtype=torch.float64, device="cuda"),
+            torch.empty(nseg, dtype=torch.int64, device="cuda"),
+            torch.empty(nseg, dtype=torch.int64, device="cuda"))
+    mp = [("x", 0), ("x", 0), ("c", 1.0), ("fma",)]
+    pre = [("x", 0), ("c", 1.0), ("ge",)]
+    kp = [("x", 0), ("c", 1.5), ("gt",)]
+    ch = sg.chain(mp, pre, kp)
+
+    def s_batch():
+        sg.sg_batch_run(ctx, ch, xb.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
+    ms = time_steps(torch, stream, s_batch, k)
+    ms_off = with_contracts_off(sg, ctx, lambda: time_steps(torch, stream, s_batch, k))
+    ns = 200
+    xs = inputs.batch_data(int(off[ns]), seed=9)
+    t_cpu = cpu_time(lambda: oracle.batch_chain(mp, pre, kp, xs, off[:ns + 1]))
+    res["5_batch_10000"] = {
+        "ms": round(ms, 4), "GBps": round((4.0 * total + 24 * nseg) / (ms / 1e3) / 1e9, 1),
+        "ms_contracts_off": round(ms_off, 4),
+        "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2),
+        "oracle": {"elements_per_s": round(int(off[ns]) / t_cpu, 1), "cores": 1,
+                   "sample": "the first %d collections (%d elements)" % (ns, int(off[ns]))}}
+    del xb, to, outs
+
+    # the filter x > 0.25 of 2^28 items, and the same with the postcondition
+    # Result.for_all(x > 0.25) on its output (one more pass over the kept items)
+    n = 1 << 28
+    g.manual_seed(5)
+    fx = torch.rand(n, device="cuda", generator=g) * 2 - 1
+    vf = sg.wrap_tensor(ctx, fx)
+    pr = [("x", 0), ("c", 0.25), ("gt",)]
+    fpost = sg.contract(sg.SG_C_FOR_ALL, pr)
+
+    def s_filter():
+        kf = sg.sg_filter(ctx, pr, vf)
+        sg.sg_ensure(ctx, kf, fpost)
+        sg.sg_vector_count(ctx, kf)
+        sg.sg_flush(ctx)
+        sg.sg_vector_release(kf)
+    ms = time_steps(torch, stream, s_filter, k)
+    ms_off = with_contracts_off(sg, ctx, lambda: time_steps(torch, stream, s_filter, k))
+    xh = inputs.uniform_pm1(inputs.rng(5), 1 << 24)
+    t_cpu = cpu_time(lambda: oracle.filter(pr, xh))
+    res["filter_2e28_with_postcondition"] = {
+        "ms": round(ms, 4), "ms_contracts_off": round(ms_off, 4),
+        "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2),
+        "oracle": {"items_per_s": round((1 << 24) / t_cpu, 1), "cores": 1,
+                   "sample": "2^24 items"}}
+    sg.sg_vector_release(vf)
+    del fx
+    return res
 
 
 def main():
@@ -687,9 +934,12 @@ def main():
                 "kernel": "k_onesweep (passes 1-3; 8 bytes/key read+write)",
                 "peak_kind": peak_kind + " hbm_gbs (copy bandwidth)"}
     extras = None
+    per_config = None
     if not args.no_extras:
         extras = secondary_workloads(torch, sg, ctx, stream, max(3, min(args.steps, 10)), peak,
                                      tc_peak)
+        per_config = per_config_workloads(torch, sg, ctx, stream, max(3, min(args.steps, 10)),
+                                          peak, tc_peak, sustained_tc_peak())
     cpu = None
     if world == 1:
         import oracle
@@ -733,6 +983,7 @@ def main():
             "per_kernel_ms": {k: round(v[1] / v[0], 5) for k, v in prof.items()},
             "per_kernel_launches": {k: v[0] for k, v in prof.items()},
             "secondary": extras,
+            "per_config": per_config,
         },
     }
     print(json.dumps(line), flush=True)

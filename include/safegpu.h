@@ -535,7 +535,8 @@ sg_status sg_debug_portable_kernels(sg_ctx* ctx, int on);
  *               fails, -1 if none
  *   kept     : nseg int64 counts of kept elements
  * Returns SG_ERR_PRECONDITION if any collection violated `pre` (outputs are
- * still written). */
+ * still written).  In contract mode SG_CONTRACTS_OFF the precondition is not
+ * evaluated (it is not compiled into the pass) and every first_viol is -1. */
 typedef struct {
   sg_expr map;
   sg_expr pre;

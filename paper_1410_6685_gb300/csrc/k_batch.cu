@@ -233,11 +233,13 @@ int stack_delta(uint8_t op, int* need) {
 
 }  // namespace
 
-bool build_chain_prog(const sg_chain& ch, Prog* pr, int* depth) {
+bool build_chain_prog(const sg_chain& ch, Prog* pr, int* depth, bool with_pre) {
   std::vector<HostOp> x{{SG_OP_LOAD, 0.0f}}, y, prog;
   append_with(y, ch.map, x);                       // y = map(x)
-  append_with(prog, ch.pre, y);                    // pre(y)
-  prog.push_back(HostOp{K_PRED, 0.0f});
+  if (with_pre) {
+    append_with(prog, ch.pre, y);                  // pre(y)
+    prog.push_back(HostOp{K_PRED, 0.0f});
+  }
   append_with(prog, ch.keep, y);                   // keep(y)
   prog.push_back(HostOp{K_MASK, 0.0f});
   prog.insert(prog.end(), y.begin(), y.end());     // y

@@ -62,6 +62,7 @@ struct Job {
   sgk::Prog prog;
   int depth;
   int occ;          // resident CTAs per SM of the kernel that will run
+  bool with_pre;    // the precondition is checked (contract mode PRE or above)
   BatchStats stats;
 };
 
@@ -111,7 +112,7 @@ sg_status run_with(sg_ctx* c, const Job& j, const sg_sched_choice& sch, double* 
   key.kept = j.kept;
   key.chunk = sch.chunk;
   key.grid_per_sm = sch.blocks_per_sm;
-  key.pad = c->codegen;
+  key.pad = c->codegen | (j.with_pre ? 0x100 : 0);
   BatchPlanCache& cache = c->batch;
   if (!cache.capture_stream) {
     if (cudaStreamCreateWithFlags(&cache.capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -218,7 +219,10 @@ sg_status prepare(sg_ctx* c, const sg_chain* ch, const float* data, const int64_
   j->sums = sums;
   j->first = first;
   j->kept = kept;
-  if (!sgk::build_chain_prog(*ch, &j->prog, &j->depth))
+  // contract mode OFF (Sec. 6.3): the precondition is not compiled in, and
+  // every first-violation index comes back -1
+  j->with_pre = c->mode >= SG_CONTRACTS_PRE;
+  if (!sgk::build_chain_prog(*ch, &j->prog, &j->depth, j->with_pre))
     return bad(c, SG_ERR_INVALID_ARG, "chain program too long or too deep");
   // the candidates' CTAs per SM follow the kernel that will run: the
   // specialised one when code generation is on, else the interpreter

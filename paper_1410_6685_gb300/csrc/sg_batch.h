@@ -22,7 +22,8 @@ struct BatchLaunch {
   cudaKernel_t jit;         // run-time specialised kernel, or nullptr (interpreter)
 };
 
-bool build_chain_prog(const sg_chain& ch, Prog* pr, int* depth);
+// with_pre: the precondition is evaluated (contract mode PRE or above)
+bool build_chain_prog(const sg_chain& ch, Prog* pr, int* depth, bool with_pre = true);
 size_t batch_scratch_bytes(long long nseg, long long capacity);
 cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, Prof* prof);
 int batch_blocks_per_sm(int depth);

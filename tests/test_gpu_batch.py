@@ -82,6 +82,33 @@ def test_precondition_violations_reported_per_collection(env):
     assert np.array_equal(fv, rf) and np.array_equal(kept, rk)
 
 
+def test_contracts_off_skips_the_precondition(env):
+    """Contract mode OFF (Sec. 6.3): the precondition is not evaluated, so
+    the planted NaNs are not reported (every first index -1, no error); the
+    kept counts and sums are the oracle's all the same.  Back in PRE_POST
+    the same batch reports them again (a separately captured graph)."""
+    sg, ctx, _ = env
+    L = np.array([100, 20000, 50000, 10, 33333])
+    off = inputs.batch_offsets(L)
+    x = inputs.batch_data(int(off[-1]), seed=33)
+    x[off[1] + 5] = np.nan
+    x[off[4]] = np.nan
+    sg.sg_set_contract_mode(ctx, sg.SG_CONTRACTS_OFF)
+    try:
+        sums, fv, kept, _ = run(env, x, off)
+    finally:
+        sg.sg_set_contract_mode(ctx, sg.SG_CONTRACTS_PRE_POST)
+    rs, rf, rk = oracle.batch_chain(MAP, PRE, KEEP, x, off)
+    assert list(fv) == [-1] * 5
+    assert np.array_equal(kept, rk)
+    for s in range(len(L)):     # a NaN is never kept (NaN > 1.5 is false)
+        seg = x[off[s]:off[s + 1]].astype(np.float64)
+        scale = np.nansum(np.abs(seg * seg + 1))
+        assert abs(sums[s] - rs[s]) <= max(1e-5 * abs(rs[s]), 2.0 ** -22 * scale), s
+    sums2, fv2, kept2, _ = run(env, x, off, expect_status=sg.SG_ERR_PRECONDITION)
+    assert np.array_equal(fv2, rf) and list(rf) == [-1, 5, -1, -1, 0]
+
+
 def test_graph_replay_is_deterministic(env):
     sg, ctx, _ = env
     L = inputs.batch_lengths(500, seed=40, hi_log2=16)
