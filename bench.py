@@ -512,17 +512,17 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
                           "frac_hbm": round(gbs / hbm_peak, 4)}
 
     # 6. schedule of that batch: the 2x64 MLP cost model, trained on the GPU on
-    #    autotuner sweeps of 56 smaller synthetic batches (never this one),
-    #    against the plain table and the autotuner's measured best
+    #    autotuner sweeps of 40 other synthetic batches of the family it serves
+    #    (1,000-10,000 collections, log-uniform lengths, at most 4e8 elements;
+    #    never this one), against the plain table and the autotuner's best
     rng = np.random.default_rng(12)
     sg.sg_set_scheduler(ctx, sg.SG_SCHED_AUTOTUNE)
-    keep = []
-    for _ in range(56):
-        lo = int(rng.integers(4, 9))
-        hi = int(rng.integers(lo + 2, 19))
-        ns = int(rng.integers(100, 3000))
-        while ns * 2.0 ** ((lo + hi) / 2) > 2.5e7:
-            ns //= 2
+    for _ in range(40):
+        lo = int(rng.integers(6, 10))
+        hi = int(rng.integers(14, 21))
+        ns = int(rng.integers(1000, 10001))
+        while ns * (2.0 ** hi - 2.0 ** lo) / ((hi - lo) * np.log(2)) > 4e8:
+            ns = ns * 3 // 4
         ns = max(ns, 16)
         Ls = np.floor(2.0 ** (lo + (hi - lo) * rng.random(ns))).astype(np.int64)
         offs = inputs.batch_offsets(Ls)
@@ -532,11 +532,10 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
                torch.empty(ns, dtype=torch.int64, device="cuda"),
                torch.empty(ns, dtype=torch.int64, device="cuda"))
         sg.sg_batch_run(ctx, ch, xs.data_ptr(), ts.data_ptr(), ns, *(t.data_ptr() for t in os_))
-        keep.append((xs, ts, os_))
+        del xs, ts, os_
     t0 = time.perf_counter()
     loss = sg.sg_sched_train(ctx, epochs=400, lr=3e-3, seed=7)
     t_train = time.perf_counter() - t0
-    del keep
     r = sg.sg_batch_report(ctx, ch, xb.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
     t_us = np.array(r.measured_us[:r.ncand])
     best = float(t_us.min())

@@ -84,37 +84,35 @@ def make_workload(torch, rng, nseg, lo, hi):
 
 
 def test_learned_schedule_gain_over_plain_table(env):
-    """Train the cost model on autotuner sweeps of 56 synthetic workloads, then
-    compare, on 12 held-out workloads, the regret of the learned choice and
-    of the plain table's choice (time / fastest - 1, each candidate measured
-    twice more and the better time kept, so that measurement noise does not
-    decide).  The learned chooser must not lose to the table by more than
-    the re-measurement noise of these 20-300 us launches (about 3%; median
-    regret, so that one noisy workload out of twelve does not decide), its
-    median regret must stay near the fastest, and its mean regret near the
-    table's (the mean follows single 20 us workloads whose best time was a
-    lucky measurement: up to 60% regret for every chooser); it must also run
-    without measuring."""
+    """Train the cost model on autotuner sweeps of 40 synthetic batches drawn
+    from the family the chooser serves (1,000-10,000 collections, lengths
+    log-uniform from 2^6-2^9 up to 2^14-2^20, at most 4e8 elements), then
+    compare, on 12 held-out batches of the same family, the regret of the
+    learned choice and of the plain table's choice (time / fastest - 1; every
+    candidate measured twice and the better time kept, so that measurement
+    noise does not decide).  The learned chooser must gain: lower median and
+    lower mean regret than the table; it must also run without measuring."""
     sg, ctx, torch = env
     chain = sg.chain([("x", 0), ("x", 0), ("c", 1.0), ("fma",)], [("x", 0), ("c", 1.0), ("ge",)],
                      [("x", 0), ("c", 1.5), ("gt",)])
     rng = np.random.default_rng(12)
 
     def spec(r):
-        lo = int(r.integers(4, 9))
-        hi = int(r.integers(lo + 2, 19))
-        nseg = int(r.integers(100, 3000))
-        while nseg * 2.0 ** ((lo + hi) / 2) > 2.5e7:
-            nseg //= 2
+        lo = int(r.integers(6, 10))
+        hi = int(r.integers(14, 21))
+        nseg = int(r.integers(1000, 10001))
+        while nseg * (2.0 ** hi - 2.0 ** lo) / ((hi - lo) * np.log(2)) > 4e8:
+            nseg = nseg * 3 // 4
         return max(nseg, 16), lo, hi
 
     # training: the autotuner measures every candidate of each workload
     sg.sg_set_scheduler(ctx, sg.SG_SCHED_AUTOTUNE)
-    for _ in range(56):
+    for _ in range(40):
         x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
         sg.sg_batch_run(ctx, chain, x.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
+        del x, to, outs
     Xlog, ylog = sg.sg_sched_log(ctx)
-    assert len(ylog) >= 56 * 8 and Xlog.shape == (len(ylog), D_IN)
+    assert len(ylog) >= 40 * 8 and Xlog.shape == (len(ylog), D_IN)
     loss = sg.sg_sched_train(ctx, epochs=400, lr=3e-3, seed=7)
     assert loss < 0.5          # standardised relative log-time: well below its variance (1.0)
     # held-out workloads
@@ -129,14 +127,14 @@ def test_learned_schedule_gain_over_plain_table(env):
         assert r1.learned_index >= 0 and r1.default_index >= 0
         reg_l.append(t[r1.learned_index] / best - 1)
         reg_d.append(t[r1.default_index] / best - 1)
+        del x, to, outs
     ml, md = float(np.mean(reg_l)), float(np.mean(reg_d))
     medl, medd = float(np.median(reg_l)), float(np.median(reg_d))
     print("\nmean regret learned %.3f, plain table %.3f; median %.3f, %.3f; per workload "
           "learned %s plain %s" % (ml, md, medl, medd, np.round(reg_l, 3).tolist(),
                                    np.round(reg_d, 3).tolist()))
-    assert medl <= medd + 0.03
-    assert medl <= 0.06
-    assert ml <= md + 0.05
+    assert medl < medd
+    assert ml < md
     # the learned chooser runs once, without measuring candidates
     sg.sg_set_scheduler(ctx, sg.SG_SCHED_LEARNED)
     x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
