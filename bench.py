@@ -50,7 +50,7 @@ WORKLOAD = ("sort int32 n=2^26 uniform full range, postconditions sorted + permu
 # k_onesweep digit pass over 2^26 keys, from an ncu capture of the sort
 # kernels, valid only for the kernel source it was taken on (its SHA-256
 # prefix); for any other source the roofline reports no traffic.
-ONESWEEP_TRAFFIC = {"k_sort.cu": "58c93f8c08147dcb", "n": 1 << 26, "bytes": 271510528 + 223193088}
+ONESWEEP_TRAFFIC = {"k_sort.cu": "6b00e4b654c0ca82", "n": 1 << 26, "bytes": 269313280 + 222068736}
 
 
 def onesweep_traffic(n):
@@ -843,19 +843,24 @@ def main():
 
     for _ in range(args.warmup):
         step()
-    # timed region (kernel tracing on: events bracket each launch on `stream`)
+    # timed region: the K steps, untraced
     clocks = Clocks(local, torch)
-    sg.sg_profile_enable(ctx, True)
-    sg.sg_profile_report(ctx, reset=True)
     k0 = sg.sg_kernel_count(ctx)
     clocks.start()
     ms = timed(args.steps)
     clk = clocks.stop()
     launches = sg.sg_kernel_count(ctx) - k0
+    # the same K steps again with kernel tracing (CUDA events bracket each
+    # launch on `stream`): the per-kernel durations of the roofline; tracing
+    # adds its event records to the step, so the step time comes from the
+    # untraced region above
+    sg.sg_profile_enable(ctx, True)
+    sg.sg_profile_report(ctx, reset=True)
+    ms_traced = timed(args.steps)
     prof = sg.sg_profile_report(ctx, reset=True)
     sg.sg_profile_enable(ctx, False)
 
-    # contract overhead: the same steps with checking off
+    # contract overhead: the same steps with checking off, untraced too
     sg.sg_set_contract_mode(ctx, sg.SG_CONTRACTS_OFF)
     for _ in range(2):
         step()
@@ -959,7 +964,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "bytes_per_key": BYTES_PER_KEY,
                    "l2": "inputs larger than L2 (268 MB keys vs 126 MB L2), no flush",
-                   "contracts": "pre_post, fused", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "contracts": "pre_post, fused", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "timing": "CUDA events around K untraced steps; the roofline's kernel "
+                             "durations from K further steps with per-launch events"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": round(job_gbs(world, BYTES_PER_KEY * n, t_e2e), 2), "unit": "GB/s",
@@ -979,6 +986,7 @@ def main():
             "keys_per_s": round(world * n / (ms / 1e3), 1),
             "contract_overhead_pct": round((ms / ms_off - 1.0) * 100.0, 2),
             "ms_per_step_contracts_off": round(ms_off, 4),
+            "ms_per_step_traced": round(ms_traced, 4),
             "per_kernel_ms": {k: round(v[1] / v[0], 5) for k, v in prof.items()},
             "per_kernel_launches": {k: v[0] for k, v in prof.items()},
             "secondary": extras,
