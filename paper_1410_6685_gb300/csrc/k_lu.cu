@@ -312,13 +312,18 @@ __global__ void __launch_bounds__(kPT)
 // thread finds the CTA's best among the warps' keys by a lane-parallel
 // maximum; the CTA's key and staged row go to every CTA of the cluster by
 // asynchronous remote stores (as in the slab form); the cluster's winner is
-// again a lane-parallel maximum, and its row arrives pre-shifted.  The
-// interchanges, the zero-pivot rule and the write-back are the slab form's.
-template <int PC>
+// again a lane-parallel maximum, and its row arrives pre-shifted.  Once the
+// pivot row is known a row forms its multiplier and only its next column
+// (the next candidate); the rest of its update is done while the next
+// exchange is in flight (a warp's winner completes its own row first, since
+// that row is staged and sent).  The interchanges, the zero-pivot rule and
+// the write-back are the slab form's.  KR: row slots per thread (2 when a
+// CTA holds at most 2 kPT rows: fewer registers, measured 6% faster).
+template <int PC, int KR>
 __global__ void __launch_bounds__(kPT, 1)
     k_lu_panel_reg(float* __restrict__ LU, int n, int k, int jb, int* __restrict__ piv,
                    int* __restrict__ info, int* __restrict__ moves, int c_lo, int c_hi) {
-  constexpr int kRows = max_rows_per_thread<PC>();
+  constexpr int kRows = KR;
   constexpr int kW = kPT / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
@@ -360,16 +365,31 @@ __global__ void __launch_bounds__(kPT, 1)
   cluster.sync();
   // my rows: r = r0 + tid + i * kPT; positions and values in registers
   float x[kRows][kPB];
+  float lr[kRows];       // a row's pending multiplier
   int lp[kRows];
-  bool act[kRows];
+  bool act[kRows], pend[kRows];
+  float pv[kPB];         // the last pivot row, shifted (pv[c] is column j + c of its step)
+  bool pzero = false;
+#pragma unroll
+  for (int c = 0; c < kPB; ++c) pv[c] = 0.0f;
 #pragma unroll
   for (int i = 0; i < kRows; ++i) {
     const int r = r0 + tid + i * kPT;
     lp[i] = r;
     act[i] = r < r1;
+    pend[i] = false;
+    lr[i] = 0.0f;
 #pragma unroll
     for (int c = 0; c < kPB; ++c) x[i][c] = act[i] ? lbuf[(r - r0) * kStride + c] : 0.0f;
   }
+  // the deferred part of a row's update: registers 1..30 of the shifted row
+  // (register 0, the next column, was updated when the multiplier was formed)
+  auto finish = [&](int i) {
+#pragma unroll
+    for (int c = 1; c + 1 < kPB; ++c) x[i][c] = pzero ? x[i][c + 1] : fmaf(-lr[i], pv[c + 1], x[i][c + 1]);
+    x[i][kPB - 1] = 0.0f;
+    pend[i] = false;
+  };
   int my_info = 0;
   bool failed = false;
   for (int j = 0; j < jb; ++j) {
@@ -387,12 +407,14 @@ __global__ void __launch_bounds__(kPT, 1)
     const unsigned mh = __reduce_max_sync(0xffffffffu, (unsigned)(mine >> 32));
     const unsigned ml = __reduce_max_sync(0xffffffffu, (unsigned)(mine >> 32) == mh ? (unsigned)mine : 0u);
     const unsigned long long wk = ((unsigned long long)mh << 32) | ml;
-    // the warp's winner stages its row (keys carry the row: the winner is unique)
+    // the warp's winner completes and stages its row (keys carry the row:
+    // the winner is unique)
     if (wk != 0ull && mine == wk) {
       float4* st = reinterpret_cast<float4*>(stage + (par * kW + w) * kPB);
 #pragma unroll
       for (int i = 0; i < kRows; ++i)
         if (i == mi) {
+          if (pend[i]) finish(i);
 #pragma unroll
           for (int q = 0; q < kPB / 4; ++q)
             st[q] = make_float4(x[i][4 * q], x[i][4 * q + 1], x[i][4 * q + 2], x[i][4 * q + 3]);
@@ -429,6 +451,10 @@ __global__ void __launch_bounds__(kPT, 1)
                     b ? srow[part] : make_float4(0.f, 0.f, 0.f, 0.f), cl_addr(mbar, q));
       }
     }
+    // the deferred updates, while the exchange is in flight
+#pragma unroll
+    for (int i = 0; i < kRows; ++i)
+      if (pend[i]) finish(i);
     // after a wait gave up nothing is written back; later columns do not wait
     if (!failed && !bar_wait(mbar, (uint32_t)(j >> 1) & 1u)) failed = true;
     unsigned long long g;
@@ -444,8 +470,8 @@ __global__ void __launch_bounds__(kPT, 1)
     }
     const int p = (int)(0xFFFFu - (unsigned)((g >> 16) & 0xFFFFu));   // winning position
     const int gp = (int)(g & 0xFFFFu);                                // its row in the panel
-    // the pivot row, shifted: pv[c] is column j + c
-    float pv[kPB];
+    // the pivot row, shifted: pv[c] is column j + c (every pending update,
+    // which used the previous one, is done)
     {
       const float4* pr = reinterpret_cast<const float4*>(crow + (par * PC + wq) * kPB);
 #pragma unroll
@@ -455,8 +481,8 @@ __global__ void __launch_bounds__(kPT, 1)
       }
     }
     const float d = pv[0];
-    const bool zero = d == 0.0f;
-    if (zero && my_info == 0) my_info = k + j + 1;
+    pzero = d == 0.0f;
+    if (pzero && my_info == 0) my_info = k + j + 1;
     const float rd = 1.0f / d;
     // interchange of positions j and p; the pivot row writes its U part
     // (columns j..jb-1) and retires
@@ -474,16 +500,17 @@ __global__ void __launch_bounds__(kPT, 1)
       }
     }
     // eliminate below the pivot: l = a_ij / u_jj (as a product with the
-    // reciprocal), then shift the row by one column while updating it
+    // reciprocal); register 0 becomes the next column now, the rest of the
+    // shifted update waits for the next exchange
 #pragma unroll
     for (int i = 0; i < kRows; ++i) {
       if (!act[i]) continue;
       const int r = r0 + tid + i * kPT;
-      const float l = zero ? x[i][0] : x[i][0] * rd;
+      const float l = pzero ? x[i][0] : x[i][0] * rd;
       lbuf[(r - r0) * kStride + j] = l;
-#pragma unroll
-      for (int c = 0; c + 1 < kPB; ++c) x[i][c] = zero ? x[i][c + 1] : fmaf(-l, pv[c + 1], x[i][c + 1]);
-      x[i][kPB - 1] = 0.0f;
+      lr[i] = l;
+      x[i][0] = pzero ? x[i][1] : fmaf(-l, pv[1], x[i][1]);
+      pend[i] = true;
     }
     if (tid == 0 && rank == 0) piv[k + j] = k + p;
   }
@@ -1044,9 +1071,13 @@ cudaError_t launch_panel(float* LU, int n, int k, int jb, int* piv, int* info, i
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if constexpr (PC == 16)
-    return cudaLaunchKernelEx(&cfg, k_lu_panel_reg<PC>, LU, n, k, jb, piv, info, moves, c_lo, c_hi);
-  else
+  if constexpr (PC == 16) {
+    if ((n - k + PC - 1) / PC <= 2 * kPT)
+      return cudaLaunchKernelEx(&cfg, k_lu_panel_reg<PC, 2>, LU, n, k, jb, piv, info, moves, c_lo,
+                                c_hi);
+    return cudaLaunchKernelEx(&cfg, k_lu_panel_reg<PC, max_rows_per_thread<PC>()>, LU, n, k, jb,
+                              piv, info, moves, c_lo, c_hi);
+  } else
     return cudaLaunchKernelEx(&cfg, k_lu_panel<PC>, LU, n, k, jb, piv, info, moves, c_lo, c_hi);
 }
 
@@ -1055,9 +1086,9 @@ bool use_cluster16() {
   static int v = -1;
   if (v < 0) {
     v = 0;
-    if (cudaFuncSetAttribute(k_lu_panel_reg<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+    if (cudaFuncSetAttribute(k_lu_panel_reg<16, max_rows_per_thread<16>()>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess &&
-        cudaFuncSetAttribute(k_lu_panel_reg<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_lu_panel_reg<16, max_rows_per_thread<16>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)panel_reg_smem<16>(kLuMaxN, 0)) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(16);
@@ -1071,7 +1102,7 @@ bool use_cluster16() {
       cfg.attrs = at;
       cfg.numAttrs = 1;
       int clusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&clusters, k_lu_panel_reg<16>, &cfg) == cudaSuccess &&
+      if (cudaOccupancyMaxActiveClusters(&clusters, k_lu_panel_reg<16, max_rows_per_thread<16>()>, &cfg) == cudaSuccess &&
           clusters >= 1)
         v = 1;
     }
@@ -1088,8 +1119,17 @@ cudaError_t lu_prepare(int n) {
   gemm_tc_prepare();
   const bool c16 = !portable_kernels() && use_cluster16();
   const size_t ps = c16 ? panel_reg_smem<16>(n, 0) : panel_smem<8>(n, 0);
-  cudaError_t e = c16 ? cudaFuncSetAttribute(k_lu_panel_reg<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps)
-                      : cudaFuncSetAttribute(k_lu_panel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+  cudaError_t e;
+  if (c16) {
+    e = cudaFuncSetAttribute(k_lu_panel_reg<16, max_rows_per_thread<16>()>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_lu_panel_reg<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_lu_panel_reg<16, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  } else {
+    e = cudaFuncSetAttribute(k_lu_panel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+  }
   if (e != cudaSuccess) return e;
   const size_t mx = ((size_t)kLuOuter * (kLuOuter + 1) + (size_t)kLuOuter * 33) * sizeof(float);
   return cudaFuncSetAttribute(k_lu_trsm_outer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);

@@ -79,6 +79,20 @@ def test_full_size_8192(env, prec):
     assert info.residual <= 1e-12 and info.info == 0
 
 
+def test_maximum_size_9216(env):
+    """The largest n the elimination takes (the 16-CTA panel then holds three
+    rows per thread): the diagonally dominant workload reaches x = 1, and a
+    larger n is refused with SG_ERR_SHAPE."""
+    sg, ctx, _ = env
+    A, b = inputs.gepp_inputs(9216)
+    x, info = solve(env, A, b, prec=1)
+    assert np.max(np.abs(x - 1.0)) <= 1e-10
+    assert info.residual <= 1e-12 and info.info == 0
+    n = 9217
+    A = np.eye(n, dtype=np.float32)
+    solve(env, A, np.ones(n), prec=1, expect=sg.SG_ERR_SHAPE)
+
+
 def test_row_interchanges_match_oracle(env):
     """A matrix whose elimination needs interchanges at every step, and ties
     in |a_ik| (the lowest row wins)."""
