@@ -550,6 +550,21 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
                            "ctas_per_sm": int(r.ctas_per_sm[r.learned_index])},
         "train_records": int(sg.sg_sched_log(ctx)[1].shape[0]), "train_loss": round(loss, 5),
         "train_s": round(t_train, 2)}
+
+    # 7. the other decision families -- the stream pass's launch shape, the
+    #    filter's tile, the product's tile form: held-out regret of the
+    #    learned choice and of the plain table (sched_study: 40 swept training
+    #    workloads per family, 16 held-out ones each timed by two sweeps), in
+    #    a context of its own
+    from paper_1410_6685_gb300 import sched_study
+    sctx = sg.sg_init(torch.cuda.current_device(), stream.cuda_stream)
+    try:
+        t0 = time.perf_counter()
+        fam = sched_study.study(sg, sctx, torch, train=40, heldout=16)
+        fam["study_s"] = round(time.perf_counter() - t0, 1)
+    finally:
+        sg.sg_destroy(sctx)
+    out["schedule_families"] = fam
     return out
 
 

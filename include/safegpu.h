@@ -427,8 +427,8 @@ sg_status sg_set_contract_mode(sg_ctx* ctx, sg_contract_mode m);
 typedef enum { SG_FUSE_OFF = 0, SG_FUSE_ON = 1 } sg_fusion;
 sg_status sg_set_fusion(sg_ctx* ctx, sg_fusion f);
 
-/* Schedule choice for launch shapes (blocks per SM, items per thread, sort
- * tile): the autotuned plain table, or the learned MLP cost model. */
+/* Schedule choice for launch and tile shapes (the families below): the
+ * autotuned plain table, or the learned MLP cost model. */
 typedef enum { SG_SCHED_AUTOTUNE = 0, SG_SCHED_LEARNED = 1 } sg_sched;
 sg_status sg_set_scheduler(sg_ctx* ctx, sg_sched s);
 
@@ -446,8 +446,9 @@ typedef enum { SG_CODEGEN_INTERPRET = 0, SG_CODEGEN_SPECIALIZE = 1 } sg_codegen;
 sg_status sg_set_codegen(sg_ctx* ctx, sg_codegen g);
 
 /* Compiles, and only compiles, the run-time specialised filter kernel of
- * `pred` (a predicate over slot 0, as for sg_filter) with NVRTC for sm_103a;
- * nothing is loaded, so no GPU is needed.  SG_OK when it compiles;
+ * `pred` (a predicate over slot 0, as for sg_filter) in each of its tile
+ * sizes (2048, 4096, 8192 items) with NVRTC for sm_103a; nothing is
+ * loaded, so no GPU is needed.  SG_OK when it compiles;
  * SG_ERR_UNSUPPORTED when NVRTC cannot be loaded or the compile fails (the
  * reason or the compiler's log, truncated to cap - 1 bytes and terminated,
  * goes to `log` unless it is NULL); SG_ERR_INVALID_ARG for a malformed
@@ -548,29 +549,59 @@ sg_status sg_batch_run(sg_ctx* ctx, const sg_chain* chain, const float* data,
                        int64_t* first_viol, int64_t* kept);
 
 /* ------------------------------------------------------------------------ */
-/* Schedule choice for the batched launch: a schedule is (elements per work
- * item, CTAs per SM).  SG_SCHED_AUTOTUNE measures every candidate the first
- * time a workload (offsets pointer, count, chain) is seen -- a warm-up run,
- * then the better of two runs timed with CUDA events -- and keeps the
- * fastest; each measurement is logged as (12 features, log microseconds,
- * log of the time relative to the plain table's choice on that workload).
- * sg_sched_train fits the 2x64 MLP cost model to the relative log-times on
- * the GPU with the kernels below.  SG_SCHED_LEARNED then runs, without
- * measuring, the candidate the model predicts fastest when it is predicted
- * to beat the plain table's choice by more than 2%, else that choice (while
- * no model is trained it behaves as SG_SCHED_AUTOTUNE).  In the report,
+/* Schedule choice.  A decision family is a point where the library picks a
+ * launch or tile shape from a candidate list; a schedule is one candidate,
+ * given as (chunk, ctas_per_sm):
+ *   SG_SCHED_BATCH    the batched launch (sg_batch_run): chunk = elements
+ *                     per work item, ctas_per_sm = persistent CTAs per SM;
+ *                     plain table (16384, 8)
+ *   SG_SCHED_STREAM   a fused element-wise pass (Sec. 5's generated kernel,
+ *                     specialised code): chunk = threads per CTA (64, 128,
+ *                     256), ctas_per_sm = CTAs per SM of the grid-stride
+ *                     grid (1, 2, 4, 8; the grid never exceeds one float4
+ *                     per thread); plain table (256, 8)
+ *   SG_SCHED_FILTER   the specialised filter (Table 2): chunk = items per
+ *                     tile (2048, 4096, 8192), ctas_per_sm = 0; plain
+ *                     table 8192
+ *   SG_SCHED_PRODUCT  the tensor-core product (Sec. 3.4 multiply, sg_matmul
+ *                     in bf16 / fp16): chunk = tile rows, ctas_per_sm =
+ *                     CTAs per tile (256, 2: a CTA pair; 128, 1: one CTA);
+ *                     plain table the pair (on devices that schedule pairs)
+ * SG_SCHED_AUTOTUNE measures every candidate the first time a workload is
+ * seen -- a warm-up run, then the better of two runs timed with CUDA
+ * events -- and keeps the fastest (the batch: per offsets pointer, count
+ * and chain; a stream pass: per length, program shape and alignment; the
+ * filter: per length and predicate shape; the product: per M, N, K and
+ * precision).  A stream pass that writes over one of its inputs is not
+ * re-run: it takes the plain table's choice.  Each measurement is logged
+ * as (family, 12 features, log microseconds, log of the time relative to
+ * the plain table's choice on that workload).  sg_sched_train fits one 2x64
+ * MLP cost model per family to the relative log-times on the GPU with the
+ * kernels below.  SG_SCHED_LEARNED then runs, without measuring, the
+ * candidate the family's model predicts fastest when it is predicted to
+ * beat the plain table's choice by more than 2%, else that choice (a family
+ * with no trained model behaves as under SG_SCHED_AUTOTUNE).  In a report,
  * predicted_us is the model's relative prediction times the plain choice's
- * measured time.                                                            */
+ * measured time (0 where nothing was measured).                          */
+typedef enum {
+  SG_SCHED_BATCH = 0,
+  SG_SCHED_STREAM = 1,
+  SG_SCHED_FILTER = 2,
+  SG_SCHED_PRODUCT = 3
+} sg_sched_family;
 #define SG_SCHED_MAX_CANDIDATES 32
 typedef struct {
-  int32_t ncand;          /* candidates measured                               */
-  int32_t best_index;     /* fastest measured (the autotuner's choice)         */
+  int32_t ncand;          /* candidates                                        */
+  int32_t best_index;     /* fastest measured (the autotuner's choice), -1 when
+                             nothing was measured                              */
   int32_t default_index;  /* the plain table's choice                          */
   int32_t learned_index;  /* the model's choice, -1 when no model is trained   */
   int64_t chunk[SG_SCHED_MAX_CANDIDATES];
   int32_t ctas_per_sm[SG_SCHED_MAX_CANDIDATES];
-  double measured_us[SG_SCHED_MAX_CANDIDATES];
+  double measured_us[SG_SCHED_MAX_CANDIDATES];   /* 0: not measured         */
   double predicted_us[SG_SCHED_MAX_CANDIDATES];
+  int32_t family;         /* sg_sched_family                                   */
+  int32_t chosen_index;   /* the candidate that ran                            */
 } sg_sched_report;
 
 /* Runs the batch once under every candidate schedule (the outputs hold the
@@ -579,15 +610,33 @@ typedef struct {
 sg_status sg_batch_report(sg_ctx* ctx, const sg_chain* chain, const float* data,
                           const int64_t* offsets, int64_t nseg, double* sums,
                           int64_t* first_viol, int64_t* kept, sg_sched_report* out);
-/* Trains the cost model on the context's log (at least 8 records): features
- * and targets standardised, minibatches of up to 512, Adam(lr), `epochs`
- * passes, initial weights from `seed`.  *final_loss: mean squared error on
- * the standardised log-time. */
+/* Trains the cost models on the context's log: every family with at least 8
+ * sweep records gets its own model (SG_ERR_INVALID_ARG when none has),
+ * features and targets standardised per family, minibatches of up to 512,
+ * Adam(lr), `epochs` passes, initial weights from `seed`.  *final_loss:
+ * mean squared error on the standardised log-time over the trained
+ * families' records. */
 sg_status sg_sched_train(sg_ctx* ctx, int32_t epochs, float lr, uint64_t seed,
                          float* final_loss);
+/* The log: records x 12 features, log microseconds, and (family may be
+ * NULL) each record's sg_sched_family; host buffers of the caller. */
 sg_status sg_sched_log_size(sg_ctx* ctx, int64_t* records, int32_t* features);
 sg_status sg_sched_log_read(sg_ctx* ctx, float* features, float* log_us,
-                            int64_t records);
+                            int32_t* family, int64_t records);
+/* The last decision the context took in `family` (its candidates, the
+ * measured times of a sweep, the plain, autotuned, learned and chosen
+ * indices).  SG_ERR_INVALID_ARG when that family has decided nothing yet. */
+sg_status sg_sched_last(sg_ctx* ctx, int32_t family, sg_sched_report* out);
+/* Drops the autotuned choices of `family` (-1: of every family), so that the
+ * next workload of each kind is measured again (after a change of
+ * conditions: another process on the device, other clocks).  The log and
+ * the models are kept. */
+sg_status sg_sched_forget(sg_ctx* ctx, int32_t family);
+/* Testing aid: every later decision of `family` takes candidate `index` (in
+ * the order sg_sched_last lists them) when the workload has that many
+ * candidates, without measuring or predicting; -1 restores the scheduler.
+ * Lets a test check each candidate's results. */
+sg_status sg_sched_force(sg_ctx* ctx, int32_t family, int32_t index);
 
 /* The cost model's network on caller device buffers (binary32), stream of
  * ctx: yhat = W3 relu(W2 relu(W1 x + b1) + b2) + b3, hidden width 64, flat

@@ -10,6 +10,7 @@
 // items are packed in shared memory and written out contiguously, so both the
 // read and the write are coalesced: 4n bytes read, 4m bytes written for m
 // kept items.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -187,6 +188,11 @@ size_t filter_scratch_bytes(long long n) {
   return sizeof(FilterHdr) + ntiles * sizeof(unsigned long long) + 256;
 }
 
+size_t filter_jit_scratch_bytes(long long n) {
+  const size_t ntiles = (size_t)((n + kJitFilterMinTile - 1) / kJitFilterMinTile);
+  return std::max(filter_scratch_bytes(n), sizeof(FilterHdr) + ntiles * sizeof(unsigned long long) + 256);
+}
+
 cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& pred,
                           int pred_depth, void* scratch, FilterResult* res, cudaStream_t s,
                           int num_sms, int64_t* kernels, Prof* prof, const LookbackCtl& lb) {
@@ -215,14 +221,15 @@ cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& p
 cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out, long long n,
                                       const Prog& pred, void* scratch, FilterResult* res,
                                       cudaStream_t s, int num_sms, int64_t* kernels,
-                                      Prof* prof, const LookbackCtl& lb) {
-  // the scratch is sized for the interpreting kernel's tiles: one look-back
-  // word per tile of kFTile items covers the larger tiles here
-  static_assert(kJitFilterTile % kFTile == 0, "the two filters share the scratch");
+                                      Prof* prof, const LookbackCtl& lb, int tile) {
+  // the scratch (filter_jit_scratch_bytes) holds one look-back word per tile
+  // of the smallest tile
   if (n <= 0) return cudaSuccess;
-  const unsigned ntiles = (unsigned)((n + kJitFilterTile - 1) / kJitFilterTile);
+  if (tile < kJitFilterMinTile) return cudaErrorInvalidValue;
+  const unsigned ntiles = (unsigned)((n + tile - 1) / tile);
   FilterHdr* h = static_cast<FilterHdr*>(scratch);
-  cudaError_t e = cudaMemsetAsync(scratch, 0, filter_scratch_bytes(n), s);
+  cudaError_t e = cudaMemsetAsync(
+      scratch, 0, sizeof(FilterHdr) + (size_t)ntiles * sizeof(unsigned long long) + 256, s);
   if (e != cudaSuccess) return e;
   (void)num_sms;   // one CTA per tile
   const void* fn = reinterpret_cast<const void*>(k);

@@ -947,15 +947,15 @@ bool use_pair() {
   return v == 1;
 }
 
-// C (+)= A16 Bt16^T on the tensor cores: the CTA-pair kernel, else the
-// one-CTA kernel
+// C (+)= A16 Bt16^T on the tensor cores: the CTA-pair kernel (form 2, or 0
+// where the device schedules pairs), else the one-CTA kernel
 cudaError_t launch_product(const uint16_t* a16, const uint16_t* bt16, int Kp, bool fp16, float* C,
                            int ldc, int M, int N, bool subtract, int* err, const float4* frv_r,
                            float4* frv_pw, int inj_row, int inj_col, float inj_delta,
-                           cudaStream_t s) {
+                           cudaStream_t s, int form) {
   CUtensorMap ma, mb;
   if (!make_map(&ma, a16, M, Kp, TM, fp16)) return cudaErrorInvalidValue;
-  if (!portable_kernels() && use_pair()) {
+  if (form != 1 && !portable_kernels() && use_pair()) {
     if (!make_map(&mb, bt16, N, Kp, TH, fp16)) return cudaErrorInvalidValue;
     const long long tiles = (long long)((M + TM2 - 1) / TM2) * ((N + TN - 1) / TN);
     const int pairs = (int)std::max<long long>(
@@ -1004,15 +1004,71 @@ void gemm_tc_prepare() {
   cudaGetLastError();
 }
 
+bool gemm_pair_available() { return !portable_kernels() && use_pair(); }
+
 size_t gemm_tc_scratch_bytes(int M, int N, int K) {
   const size_t Kp = (size_t)((K + TK - 1) / TK) * TK;
   return 256 + align256((size_t)M * Kp * 2) + align256((size_t)N * Kp * 2);
 }
 
+namespace {
+
+// the bf16 / fp16 operand copies: A by rows, B transposed (K padded to Kp)
+void cast_operands(const float* A, int lda, const float* B, int ldb, int M, int N, int K, int Kp,
+                   bool fp16, uint16_t* a16, uint16_t* bt16, cudaStream_t s) {
+  const long long ca = (long long)M * (Kp / 8);
+  const int ga = (int)std::min<long long>((ca + 255) / 256, 65535LL * 8);
+  dim3 gt((N + 31) / 32, (Kp + 31) / 32), bt(32, 8);
+  if (fp16) {
+    k_cast_rows<true><<<ga, 256, 0, s>>>(A, lda, M, K, Kp, a16);
+    k_cast_transpose<true><<<gt, bt, 0, s>>>(B, ldb, K, N, Kp, bt16);
+  } else {
+    k_cast_rows<false><<<ga, 256, 0, s>>>(A, lda, M, K, Kp, a16);
+    k_cast_transpose<false><<<gt, bt, 0, s>>>(B, ldb, K, N, Kp, bt16);
+  }
+}
+
+}  // namespace
+
+cudaError_t time_gemm_forms(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                            int M, int N, int K, bool fp16, void* scratch, cudaStream_t s,
+                            const int* forms, int nforms, double* us, int64_t* kernels) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  const int Kp = ((K + TK - 1) / TK) * TK;
+  char* p = static_cast<char*>(scratch);
+  int* err = reinterpret_cast<int*>(p);
+  uint16_t* a16 = reinterpret_cast<uint16_t*>(p + 256);
+  uint16_t* bt16 = reinterpret_cast<uint16_t*>(p + 256 + align256((size_t)M * Kp * 2));
+  cast_operands(A, lda, B, ldb, M, N, K, Kp, fp16, a16, bt16, s);
+  *kernels += 2;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  for (int f = 0; f < nforms && e == cudaSuccess; ++f) {
+    double best = 1e300;
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {   // a warm-up, then two timed
+      e = cudaEventRecord(ev[0], s);
+      if (e == cudaSuccess)
+        e = launch_product(a16, bt16, Kp, fp16, C, ldc, M, N, false, err, nullptr, nullptr, -1,
+                           -1, 0.0f, s, forms[f]);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (e == cudaSuccess && r > 0) best = std::min(best, 1000.0 * ms);
+      *kernels += 1;
+    }
+    us[f] = best;
+  }
+  for (cudaEvent_t v : ev)
+    if (v) cudaEventDestroy(v);
+  return e;
+}
+
 cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
                            int M, int N, int K, bool fp16, bool subtract, void* scratch,
                            cudaStream_t s, Prof* prof, int64_t* kernels, int inj_row,
-                           int inj_col, float inj_delta) {
+                           int inj_col, float inj_delta, int form) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (K <= 0) {   // empty inner dimension: C = 0 (or C unchanged for C - A B)
     if (subtract) return cudaSuccess;
@@ -1024,20 +1080,11 @@ cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, flo
   uint16_t* a16 = reinterpret_cast<uint16_t*>(p + 256);
   uint16_t* bt16 = reinterpret_cast<uint16_t*>(p + 256 + align256((size_t)M * Kp * 2));
   prof_begin(prof, "cast_operands", s);
-  const long long ca = (long long)M * (Kp / 8);
-  const int ga = (int)std::min<long long>((ca + 255) / 256, 65535LL * 8);
-  dim3 gt((N + 31) / 32, (Kp + 31) / 32), bt(32, 8);
-  if (fp16) {
-    k_cast_rows<true><<<ga, 256, 0, s>>>(A, lda, M, K, Kp, a16);
-    k_cast_transpose<true><<<gt, bt, 0, s>>>(B, ldb, K, N, Kp, bt16);
-  } else {
-    k_cast_rows<false><<<ga, 256, 0, s>>>(A, lda, M, K, Kp, a16);
-    k_cast_transpose<false><<<gt, bt, 0, s>>>(B, ldb, K, N, Kp, bt16);
-  }
+  cast_operands(A, lda, B, ldb, M, N, K, Kp, fp16, a16, bt16, s);
   prof_end(prof, s);
   prof_begin(prof, fp16 ? "gemm_tc_f16" : "gemm_tc_bf16", s);
   const cudaError_t e = launch_product(a16, bt16, Kp, fp16, C, ldc, M, N, subtract, err, nullptr,
-                                       nullptr, inj_row, inj_col, inj_delta, s);
+                                       nullptr, inj_row, inj_col, inj_delta, s, form);
   prof_end(prof, s);
   *kernels += 3;
   return e != cudaSuccess ? e : cudaGetLastError();
@@ -1047,7 +1094,7 @@ cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int
                                    unsigned long long seed, int nvec, float c, float u_eff,
                                    void* scratch, FreivaldsResult* res, cudaStream_t s,
                                    Prof* prof, int64_t* kernels, int inj_row, int inj_col,
-                                   float inj_delta) {
+                                   float inj_delta, int form) {
   if (N <= 0) return cudaSuccess;
   const int Kp = ((N + TK - 1) / TK) * TK;
   char* p = static_cast<char*>(scratch);
@@ -1069,7 +1116,7 @@ cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int
   prof_end(prof, s);
   prof_begin(prof, fp16 ? "gemm_tc_f16" : "gemm_tc_bf16", s);
   e = launch_product(a16, bt16, Kp, fp16, C, N, N, N, false, err, f.r4, f.pw, inj_row, inj_col,
-                     inj_delta, s);
+                     inj_delta, s, form);
   prof_end(prof, s);
   if (e != cudaSuccess) return e;
   prof_begin(prof, "freivalds_fused", s);

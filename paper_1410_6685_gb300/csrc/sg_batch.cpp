@@ -246,8 +246,8 @@ sg_status prepare(sg_ctx* c, const sg_chain* ch, const float* data, const int64_
 // Autotune: measure every candidate -- a warm-up run (graph capture, cold
 // caches), then the better of two timed runs -- and log the sweep with each
 // time relative to the plain table's choice.
-sg_status autotune(sg_ctx* c, const Job& j, std::vector<double>* times, int* best) {
-  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.occ);
+sg_status autotune(sg_ctx* c, const Job& j, const std::vector<sg_sched_choice>& cand,
+                   const std::vector<float>& X, int def, std::vector<double>* times, int* best) {
   times->assign(cand.size(), 0.0);
   double bt = 1e300;
   *best = 0;
@@ -265,17 +265,21 @@ sg_status autotune(sg_ctx* c, const Job& j, std::vector<double>* times, int* bes
       *best = (int)i;
     }
   }
-  const sg_sched_choice def = sg_batch_default(j.occ);
-  double tdef = 0.0;
-  for (size_t i = 0; i < cand.size(); ++i)
-    if (cand[i].chunk == def.chunk && cand[i].blocks_per_sm == def.blocks_per_sm) tdef = (*times)[i];
-  for (size_t i = 0; i < cand.size(); ++i) {
-    float f[kSchedFeatures];
-    sg_batch_features(j.stats, cand[i], c->num_sms, f);
-    const float rel = tdef > 0.0 ? (float)std::log((*times)[i] / tdef) : NAN;
-    sg_sched_log_add(c, f, (*times)[i], rel);
-  }
+  sg_sched_log_sweep(c, SG_SCHED_BATCH, X, *times, def);
   return SG_OK;
+}
+
+// candidates, their features and the plain choice's index
+void batch_candidates(sg_ctx* c, const Job& j, std::vector<sg_sched_choice>* cand,
+                      std::vector<float>* X, int* def) {
+  *cand = sg_batch_candidates(j.occ);
+  const sg_sched_choice d = sg_batch_default(j.occ);
+  X->assign(cand->size() * kSchedFeatures, 0.0f);
+  *def = 0;
+  for (size_t i = 0; i < cand->size(); ++i) {
+    sg_batch_features(j.stats, (*cand)[i], c->num_sms, &(*X)[i * kSchedFeatures]);
+    if ((*cand)[i].chunk == d.chunk && (*cand)[i].blocks_per_sm == d.blocks_per_sm) *def = (int)i;
+  }
 }
 
 }  // namespace
@@ -298,33 +302,29 @@ extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* da
   Job j;
   sg_status st = prepare(c, ch, data, offsets, nseg, sums, first_viol, kept, &j);
   if (st || nseg == 0) return st;
-  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.occ);
-  sg_sched_choice pick = sg_batch_default(j.occ);
-  bool chosen = false;
-  if (c->sched == SG_SCHED_LEARNED) {
-    const int li = sg_sched_learned_index(c, j.stats, cand, pick, nullptr);
-    if (li >= 0) {
-      pick = cand[li];
-      chosen = true;
-    }
+  std::vector<sg_sched_choice> cand;
+  std::vector<float> X;
+  int def = 0;
+  batch_candidates(c, j, &cand, &X, &def);
+  // the autotuned table is kept per workload (offsets, count, lengths) and
+  // chain
+  uint64_t mb;
+  memcpy(&mb, &j.stats.mean_log, 8);
+  const uint64_t key =
+      sg_sched_key(SG_SCHED_BATCH, {(uint64_t)(uintptr_t)offsets, (uint64_t)nseg,
+                                    (uint64_t)j.stats.total, mb, chain_hash(*ch)});
+  int learned = -1;
+  std::vector<float> pred;
+  int idx = sg_sched_lookup(c, SG_SCHED_BATCH, key, X, def, &learned, &pred);
+  std::vector<double> times;
+  if (idx < 0) {
+    st = autotune(c, j, cand, X, def, &times, &idx);
+    if (st) return st;
+    sg_sched_set_tuned(c, SG_SCHED_BATCH, key, idx);
   }
-  if (!chosen) {
-    // the autotuned table (measured once per workload and chain)
-    auto wkey = std::make_pair((const void*)offsets, (long long)nseg);
-    const uint64_t h = chain_hash(*ch);
-    int idx = -1;
-    for (auto& t : c->schedst.tuned)
-      if (t.first == wkey && t.second.first == h) idx = t.second.second;
-    if (idx < 0) {
-      std::vector<double> times;
-      st = autotune(c, j, &times, &idx);
-      if (st) return st;
-      c->schedst.tuned.push_back({wkey, {h, idx}});
-    }
-    pick = cand[idx];
-  }
+  sg_sched_note(c, SG_SCHED_BATCH, cand, times, def, learned, idx, pred);
   bool viol = false;
-  st = run_with(c, j, pick, nullptr, &viol);
+  st = run_with(c, j, cand[idx], nullptr, &viol);
   if (st) return st;
   if (viol) {
     c->err = "a collection violated the batch precondition";
@@ -341,33 +341,18 @@ extern "C" sg_status sg_batch_report(sg_ctx* c, const sg_chain* ch, const float*
   sg_status st = prepare(c, ch, data, offsets, nseg, sums, first_viol, kept, &j);
   if (st) return st;
   if (nseg == 0) return bad(c, SG_ERR_INVALID_ARG, "empty batch");
-  const std::vector<sg_sched_choice> cand = sg_batch_candidates(j.occ);
-  memset(out, 0, sizeof *out);
-  out->ncand = (int32_t)std::min<size_t>(cand.size(), SG_SCHED_MAX_CANDIDATES);
+  std::vector<sg_sched_choice> cand;
+  std::vector<float> X;
+  int def = 0;
+  batch_candidates(c, j, &cand, &X, &def);
   std::vector<double> times;
   int best = 0;
-  st = autotune(c, j, &times, &best);
+  st = autotune(c, j, cand, X, def, &times, &best);
   if (st) return st;
-  const sg_sched_choice def = sg_batch_default(j.occ);
-  out->default_index = -1;
-  for (int i = 0; i < out->ncand; ++i) {
-    out->chunk[i] = cand[i].chunk;
-    out->ctas_per_sm[i] = cand[i].blocks_per_sm;
-    out->measured_us[i] = times[i];
-    if (cand[i].chunk == def.chunk && cand[i].blocks_per_sm == def.blocks_per_sm)
-      out->default_index = i;
-  }
-  out->best_index = best;
-  out->learned_index = -1;
   std::vector<float> pred;
-  const int li = sg_sched_learned_index(c, j.stats, cand, def, &pred);
-  if (li >= 0) {
-    out->learned_index = li;
-    // the model predicts times relative to the plain choice: scale by its
-    // measured time
-    const double tdef = out->default_index >= 0 ? times[out->default_index] : 0.0;
-    for (int i = 0; i < out->ncand; ++i) out->predicted_us[i] = std::exp((double)pred[i]) * tdef;
-  }
+  const int li = sg_sched_learned_index(c, SG_SCHED_BATCH, X, def, &pred);
+  sg_sched_note(c, SG_SCHED_BATCH, cand, times, def, li, best, pred);
+  *out = c->schedst.last[SG_SCHED_BATCH];
   return SG_OK;
 }
 
@@ -385,10 +370,37 @@ extern "C" sg_status sg_sched_log_size(sg_ctx* c, int64_t* records, int32_t* fea
   return SG_OK;
 }
 
-extern "C" sg_status sg_sched_log_read(sg_ctx* c, float* features, float* log_us, int64_t records) {
+extern "C" sg_status sg_sched_log_read(sg_ctx* c, float* features, float* log_us,
+                                       int32_t* family, int64_t records) {
   if (!c || records < 0 || records > (int64_t)c->schedst.log_y.size()) return SG_ERR_INVALID_ARG;
   if (records && (!features || !log_us)) return SG_ERR_INVALID_ARG;
+  if (records == 0) return SG_OK;
   memcpy(features, c->schedst.log_x.data(), (size_t)records * kSchedFeatures * 4);
   memcpy(log_us, c->schedst.log_y.data(), (size_t)records * 4);
+  if (family)
+    for (int64_t r = 0; r < records; ++r) family[r] = (int32_t)c->schedst.log_fam[r];
+  return SG_OK;
+}
+
+extern "C" sg_status sg_sched_last(sg_ctx* c, int32_t family, sg_sched_report* out) {
+  if (!c || !out || family < 0 || family >= kSchedFamilies) return SG_ERR_INVALID_ARG;
+  if (!c->schedst.has_last[family]) return bad(c, SG_ERR_INVALID_ARG, "no decision of that family yet");
+  *out = c->schedst.last[family];
+  return SG_OK;
+}
+
+extern "C" sg_status sg_sched_forget(sg_ctx* c, int32_t family) {
+  if (!c || family < -1 || family >= kSchedFamilies) return SG_ERR_INVALID_ARG;
+  auto& t = c->schedst.tuned;
+  t.erase(std::remove_if(t.begin(), t.end(),
+                         [&](const SchedState::Tuned& x) { return family < 0 || x.family == family; }),
+          t.end());
+  return SG_OK;
+}
+
+extern "C" sg_status sg_sched_force(sg_ctx* c, int32_t family, int32_t index) {
+  if (!c || family < 0 || family >= kSchedFamilies || index < -1 || index >= SG_SCHED_MAX_CANDIDATES)
+    return SG_ERR_INVALID_ARG;
+  c->schedst.forced[family] = index;
   return SG_OK;
 }

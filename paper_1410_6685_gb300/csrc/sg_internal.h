@@ -176,10 +176,12 @@ cudaError_t launch_filter(const float* x, float* out, long long n,
                           const Prog& pred, int pred_depth, void* scratch,
                           FilterResult* res, cudaStream_t s, int num_sms,
                           int64_t* kernels, Prof* prof, const LookbackCtl& lb);
-// the same filter through its run-time specialised kernel (sg_jit.h)
+// the same filter through its run-time specialised kernel (sg_jit.h), whose
+// tiles hold `tile` items; scratch: filter_jit_scratch_bytes(n)
+size_t filter_jit_scratch_bytes(long long n);
 cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out, long long n,
                                       const Prog& pred, void* scratch, FilterResult* res,
                                       cudaStream_t s, int num_sms, int64_t* kernels,
-                                      Prof* prof, const LookbackCtl& lb);
+                                      Prof* prof, const LookbackCtl& lb, int tile);
 
 }  // namespace sgk

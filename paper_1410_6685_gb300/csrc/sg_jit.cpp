@@ -412,7 +412,8 @@ extern "C" __global__ void __launch_bounds__(256) sg_batch(const BatchJitArgs a)
 )SGJIT";
 
 // The filter (Table 2), specialised: a stable compaction, one CTA per tile
-// of 8192 items taken from a ticket counter when the CTA starts (so tiles
+// of 8192 items (or 2048 / 4096: SG_FQ = 2 / 4 float4s per thread, the
+// schedule chooser's filter family) taken from a ticket counter when the CTA starts (so tiles
 // start in ticket order and a look-back seldom waits on a tile that has not
 // started).  Thread t loads float4s t + 256 q (q < 8) of the tile straight
 // into registers; the order of kept items (round q, warp, lane, component)
@@ -438,8 +439,6 @@ struct FilterJitArgs {
   unsigned long long* st; unsigned* tile_ctr; FilterResult* res; unsigned ntiles; int skip_tile;
   unsigned spin_limit; int pad;
 };
-#define SG_FT 8192
-#define SG_FQ 8
 #define SG_AGG (1ull << 62)
 #define SG_PRE (2ull << 62)
 #define SG_CNT ((1ull << 62) - 1)
@@ -452,7 +451,7 @@ __device__ __forceinline__ void sg_st_relaxed(unsigned long long* p, unsigned lo
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-extern "C" __global__ void __launch_bounds__(256, 5) sg_filter(const FilterJitArgs a) {
+extern "C" __global__ void __launch_bounds__(256, SG_FMINB) sg_filter(const FilterJitArgs a) {
   __shared__ __align__(16) float s_pack[SG_FT];
   __shared__ float s_spare[256];
   __shared__ unsigned s_cnt[SG_FQ * 8];
@@ -515,8 +514,13 @@ extern "C" __global__ void __launch_bounds__(256, 5) sg_filter(const FilterJitAr
     if (lane == 0) s_cnt[q * 8 + w] = cnt;
   }
   __syncthreads();
-  // every warp scans the 64 (round, warp) counts, two per lane
+  // every warp scans the 8 SG_FQ (round, warp) counts, two per lane when
+  // there are 64
+#if SG_FQ == 8
   const unsigned c0 = s_cnt[2 * lane], c1 = s_cnt[2 * lane + 1];
+#else
+  const unsigned c0 = lane < SG_FQ * 8 ? s_cnt[lane] : 0u, c1 = 0u;
+#endif
   unsigned incl = c0 + c1;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -530,7 +534,11 @@ extern "C" __global__ void __launch_bounds__(256, 5) sg_filter(const FilterJitAr
 #pragma unroll
   for (int q = 0; q < SG_FQ; ++q) {
     const int entry = q * 8 + w;
+#if SG_FQ == 8
     unsigned r = __shfl_sync(0xffffffffu, (entry & 1) ? e0 + c0 : e0, entry >> 1) + rbase[q];
+#else
+    unsigned r = __shfl_sync(0xffffffffu, e0, entry) + rbase[q];
+#endif
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const unsigned bit = (keep >> (4 * q + l)) & 1u;
@@ -796,9 +804,13 @@ cudaKernel_t jit_batch_kernel(const Prog& pr, std::string* log) {
 
 namespace {
 
-// the source of the specialised filter for `pred`; false (with a reason in
-// *log) when it cannot be specialised
-bool filter_source(const Prog& pred, std::string* src, std::string* log) {
+// the source of the specialised filter for `pred` with `tile`-item tiles;
+// false (with a reason in *log) when it cannot be specialised
+bool filter_source(const Prog& pred, int tile, std::string* src, std::string* log) {
+  if (tile != 2048 && tile != 4096 && tile != 8192) {
+    if (log) *log = "unsupported filter tile";
+    return false;
+  }
   if (!nvrtc().ok) {
     if (log) *log = "NVRTC library not found";
     return false;
@@ -819,39 +831,49 @@ bool filter_source(const Prog& pred, std::string* src, std::string* log) {
     if (log) *log = "program could not be specialised";
     return false;
   }
-  *src = std::string("#define SG_MINMAX 0\n") + kTemplateHead + body_fn(body) + kTemplateFilter;
+  // resident CTAs per SM the compiler plans for: 48 registers at 8192
+  // items, 40 at 4096, 32 at 2048
+  char defs[128];
+  snprintf(defs, sizeof defs, "#define SG_MINMAX 0\n#define SG_FT %d\n#define SG_FQ %d\n"
+           "#define SG_FMINB %d\n", tile, tile / 1024, filter_tile_occupancy(tile));
+  *src = std::string(defs) + kTemplateHead + body_fn(body) + kTemplateFilter;
   return true;
 }
 
 }  // namespace
 
-cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log) {
+int filter_tile_occupancy(int tile) { return tile >= 8192 ? 5 : tile >= 4096 ? 6 : 8; }
+
+cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log, int tile) {
   std::string src;
-  if (!filter_source(pred, &src, log)) return nullptr;
+  if (!filter_source(pred, tile, &src, log)) return nullptr;
   return compile_cached(src, "sg_filter", log);
 }
 
 bool jit_check_filter(const Prog& pred, std::string* log) {
-  std::string src;
-  if (!filter_source(pred, &src, log)) return false;
   Nvrtc& nv = nvrtc();
-  void* prog = nullptr;
-  if (nv.create(&prog, src.c_str(), "sg_filter.cu", 0, nullptr, nullptr) != 0) {
-    if (log) *log = "NVRTC could not create the program";
-    return false;
+  for (int tile : {2048, 4096, 8192}) {
+    std::string src;
+    if (!filter_source(pred, tile, &src, log)) return false;
+    void* prog = nullptr;
+    if (nv.create(&prog, src.c_str(), "sg_filter.cu", 0, nullptr, nullptr) != 0) {
+      if (log) *log = "NVRTC could not create the program";
+      return false;
+    }
+    const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-default-device",
+                          "-fmad=false"};
+    const bool ok = nv.compile(prog, 4, opts) == 0;
+    if (!ok && log) {
+      size_t ls = 0;
+      nv.log_size(prog, &ls);
+      std::string l(ls, '\0');
+      nv.log(prog, &l[0]);
+      *log = l;
+    }
+    nv.destroy(&prog);
+    if (!ok) return false;
   }
-  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-default-device",
-                        "-fmad=false"};
-  const bool ok = nv.compile(prog, 4, opts) == 0;
-  if (!ok && log) {
-    size_t ls = 0;
-    nv.log_size(prog, &ls);
-    std::string l(ls, '\0');
-    nv.log(prog, &l[0]);
-    *log = l;
-  }
-  nv.destroy(&prog);
-  return ok;
+  return true;
 }
 
 cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,

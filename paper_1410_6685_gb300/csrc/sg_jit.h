@@ -70,8 +70,12 @@ cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, boo
 // the batched map -> for_all -> masked sum chain of one program (k_batch.cu)
 cudaKernel_t jit_batch_kernel(const Prog& pr, std::string* log);
 // the stable compaction of one predicate (one input slot), one CTA per
-// 8192-item tile (k_filter.cu launches it)
-cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log);
+// tile of `tile` items: 2048, 4096 or 8192 (k_filter.cu launches it)
+cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log, int tile = kJitFilterTile);
+// resident CTAs per SM that filter kernel is compiled for
+int filter_tile_occupancy(int tile);
+// the smallest tile of the specialised filter (sizes its look-back scratch)
+constexpr int kJitFilterMinTile = 2048;
 // compiles that kernel's source with NVRTC without loading it (no device
 // needed); false with the compiler's log when it does not compile
 bool jit_check_filter(const Prog& pred, std::string* log);

@@ -1,11 +1,13 @@
 // sg_linalg.cpp -- matrix product (Sec. 3.4 `multiply`) and its Freivalds
 // postcondition, dispatched from the executor.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
 #include "sg_linalg_kernels.h"
 #include "sg_plan.h"
 #include "sg_runtime.h"
+#include "sg_sched.h"
 
 namespace {
 
@@ -18,6 +20,50 @@ float u_eff_for(int prec, long long n) {
     case SG_PREC_F16_TC: return (float)(std::ldexp(1.0, -10) + acc);
     default: return (float)acc;
   }
+}
+
+// The product's tile form (SG_SCHED_PRODUCT): 1 one CTA per 128 x 256
+// tile, 2 a CTA pair per 256 x 256 tile.  Learned or autotuned; a sweep
+// times both forms' products the first time (M, N, K, precision) is seen,
+// unless the stream is being captured.
+int product_form(sg_ctx* c, int M, int N, int K, bool fp16, const float* a, const float* b,
+                 float* cc, void* work, cudaError_t* e) {
+  const std::vector<sg_sched_choice> cand = sg_product_candidates(sgk::gemm_pair_available());
+  if (cand.size() < 2 || M <= 0 || N <= 0 || K <= 0) return 0;
+  const ProductWork w{M, N, K, fp16};
+  std::vector<float> X(cand.size() * kSchedFeatures);
+  const sg_sched_choice d = sg_product_default(true);
+  int def = 0;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    sg_product_features(w, cand[i], c->num_sms, &X[i * kSchedFeatures]);
+    if (cand[i].chunk == d.chunk) def = (int)i;
+  }
+  const uint64_t key = sg_sched_key(SG_SCHED_PRODUCT, {(uint64_t)M, (uint64_t)N, (uint64_t)K,
+                                                       (uint64_t)fp16});
+  int learned = -1;
+  std::vector<float> pred;
+  int idx = sg_sched_lookup(c, SG_SCHED_PRODUCT, key, X, def, &learned, &pred);
+  std::vector<double> us;
+  if (idx < 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      idx = def;
+    } else {
+      std::vector<int> forms;
+      for (auto& ch : cand) forms.push_back(ch.blocks_per_sm == 2 ? 2 : 1);
+      us.assign(cand.size(), 0.0);
+      *e = sgk::time_gemm_forms(a, K, b, N, cc, N, M, N, K, fp16, work, c->stream, forms.data(),
+                                (int)forms.size(), us.data(), &c->kernels);
+      if (*e != cudaSuccess) return 0;
+      idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
+      sg_sched_log_sweep(c, SG_SCHED_PRODUCT, X, us, def);
+      sg_sched_set_tuned(c, SG_SCHED_PRODUCT, key, idx);
+      learned = sg_sched_learned_index(c, SG_SCHED_PRODUCT, X, def, &pred);
+    }
+  }
+  sg_sched_note(c, SG_SCHED_PRODUCT, cand, us, def, learned, idx, pred);
+  return cand[idx].blocks_per_sm == 2 ? 2 : 1;
 }
 
 }  // namespace
@@ -69,19 +115,23 @@ sg_status sg_exec_linalg(sg_ctx* c, Node* n, Node* fused, void* rec, void* work,
     const int ir = (int)c->mm_inject.row, ic = (int)c->mm_inject.col;
     const float id = c->mm_inject.delta;
     if (n->prec != SG_PREC_F32_SIMT) c->mm_inject.row = c->mm_inject.col = -1;
+    const bool fp16 = n->prec == SG_PREC_F16_TC;
+    const int form =
+        n->prec == SG_PREC_F32_SIMT ? 0 : product_form(c, M, N, K, fp16, a, b, cc, work, e);
+    if (*e != cudaSuccess) return SG_OK;
     if (fused) {
-      *e = sgk::launch_gemm_tc_checked(a, b, cc, N, n->prec == SG_PREC_F16_TC, fused->seed,
-                                       fused->nvec, (float)fused->tol, u_eff_for(n->prec, N),
-                                       work, static_cast<sgk::FreivaldsResult*>(rec), c->stream,
-                                       &c->prof, &c->kernels, ir, ic, id);
+      *e = sgk::launch_gemm_tc_checked(a, b, cc, N, fp16, fused->seed, fused->nvec,
+                                       (float)fused->tol, u_eff_for(n->prec, N), work,
+                                       static_cast<sgk::FreivaldsResult*>(rec), c->stream,
+                                       &c->prof, &c->kernels, ir, ic, id, form);
       return SG_OK;
     }
     if (n->prec == SG_PREC_F32_SIMT) {
       *e = sgk::launch_gemm_f32(a, K, b, N, cc, N, M, N, K, false, c->stream, &c->prof);
       c->kernels += 1;
     } else {
-      *e = sgk::launch_gemm_tc(a, K, b, N, cc, N, M, N, K, n->prec == SG_PREC_F16_TC, false,
-                               work, c->stream, &c->prof, &c->kernels, ir, ic, id);
+      *e = sgk::launch_gemm_tc(a, K, b, N, cc, N, M, N, K, fp16, false, work, c->stream,
+                               &c->prof, &c->kernels, ir, ic, id, form);
     }
     return SG_OK;
   }

@@ -24,10 +24,19 @@ bool portable_kernels();
 // kernel attributes and the CTA-pair decision of the tensor-core product;
 // called before a product is captured into a graph
 void gemm_tc_prepare();
+// form: 0 the CTA-pair kernel where the device schedules pairs, else the
+// one-CTA kernel; 1 the one-CTA kernel; 2 the pair where available
 cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
                            int M, int N, int K, bool fp16, bool subtract, void* scratch,
                            cudaStream_t s, Prof* prof, int64_t* kernels, int inj_row = -1,
-                           int inj_col = -1, float inj_delta = 0.0f);
+                           int inj_col = -1, float inj_delta = 0.0f, int form = 0);
+bool gemm_pair_available();
+// Casts the operands once, then times the product C = A B in each of `forms`
+// (a warm-up, then the better of two runs, CUDA events on s; waits for s):
+// us[f] microseconds.  C holds the last form's result.
+cudaError_t time_gemm_forms(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                            int M, int N, int K, bool fp16, void* scratch, cudaStream_t s,
+                            const int* forms, int nforms, double* us, int64_t* kernels);
 
 // Freivalds' check of C = A B for square N x N matrices with `nvec`
 // Rademacher vectors drawn from SplitMix64 (seed); tau_i = c u_eff sigma_i.
@@ -74,7 +83,7 @@ cudaError_t launch_gemm_tc_checked(const float* A, const float* B, float* C, int
                                    unsigned long long seed, int nvec, float c, float u_eff,
                                    void* scratch, FreivaldsResult* res, cudaStream_t s,
                                    Prof* prof, int64_t* kernels, int inj_row = -1,
-                                   int inj_col = -1, float inj_delta = 0.0f);
+                                   int inj_col = -1, float inj_delta = 0.0f, int form = 0);
 
 // Sec. 3.4 `transpose`, `right_multiply`, `left_multiply` (binary32,
 // row-major).  At: cols x rows.  matvec: y = A x (x: cols, y: rows); vecmat:

@@ -29,6 +29,7 @@
 #include "sg_jit.h"
 #include "sg_linalg_kernels.h"
 #include "sg_plan.h"
+#include "sg_sched.h"
 
 namespace {
 
@@ -581,6 +582,180 @@ void record_violation(sg_ctx* c, Node* n, int64_t first, double observed, bool* 
   *status = n->role == SG_PRE ? SG_ERR_PRECONDITION : SG_ERR_POSTCONDITION;
 }
 
+// One launch's time: a warm-up, then the better of two runs (CUDA events on
+// the context's stream; waits for it).
+template <class F>
+cudaError_t time_launch(sg_ctx* c, F&& launch, double* us) {
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  double best = 1e300;
+  for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(ev[0], c->stream);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (e == cudaSuccess && r > 0) best = std::min(best, 1000.0 * ms);
+  }
+  for (cudaEvent_t v : ev)
+    if (v) cudaEventDestroy(v);
+  *us = best;
+  return e;
+}
+
+// a sweep would wait for the stream: not while it is being captured
+bool stream_capturing(sg_ctx* c) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bytes && y < x + bytes;
+}
+
+// the structure of a program (operators, operand slots, depths), not its
+// constants
+uint64_t prog_shape(const sgk::Prog& pr) {
+  uint64_t h = 1469598103934665603ull;
+  for (int p = 0; p < pr.nops; ++p) {
+    h = (h ^ pr.op[p]) * 1099511628211ull;
+    h = (h ^ pr.arg[p]) * 1099511628211ull;
+    h = (h ^ pr.depth[p]) * 1099511628211ull;
+  }
+  return h;
+}
+
+// The launch shape of a specialised stream pass (SG_SCHED_STREAM): learned,
+// autotuned (a sweep the first time the workload is seen, unless the pass
+// writes over one of its inputs or the stream is being captured), else the
+// plain table's.
+cudaError_t launch_stream_scheduled(sg_ctx* c, cudaKernel_t jk, const sgk::StreamArgs& a,
+                                    int nout, bool minmax) {
+  StreamWork w;
+  w.n = a.n;
+  w.nin = a.nin;
+  w.nout = nout;
+  w.ops = a.prog.nops;
+  w.depth = a.depth;
+  w.npred = a.npred;
+  w.reduce = a.has_reduce != 0;
+  w.minmax = minmax;
+  w.vec4 = a.vec4 != 0;
+  const std::vector<sg_sched_choice> cand = sg_stream_candidates(w.n, c->num_sms);
+  const sg_sched_choice d = sg_stream_default();
+  const int gd = sg_stream_grid(w.n, d, c->num_sms);
+  std::vector<float> X(cand.size() * kSchedFeatures);
+  int def = -1;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    sg_stream_features(w, cand[i], c->num_sms, &X[i * kSchedFeatures]);
+    if (def < 0 && cand[i].chunk == d.chunk && sg_stream_grid(w.n, cand[i], c->num_sms) == gd)
+      def = (int)i;
+  }
+  if (def < 0) def = 0;
+  const uint64_t key =
+      sg_sched_key(SG_SCHED_STREAM, {(uint64_t)w.n, prog_shape(a.prog), (uint64_t)w.nin,
+                                     (uint64_t)w.nout, (uint64_t)w.npred, a.pred_exists,
+                                     (uint64_t)(w.reduce + 2 * w.minmax + 4 * w.vec4)});
+  int learned = -1;
+  std::vector<float> pred;
+  int idx = sg_sched_lookup(c, SG_SCHED_STREAM, key, X, def, &learned, &pred);
+  std::vector<double> us;
+  cudaError_t e = cudaSuccess;
+  if (idx < 0) {
+    bool in_place = false;
+    for (int k = 0; k < a.nin; ++k)
+      for (int o = 0; o < nout; ++o)
+        in_place |= ranges_overlap(a.in[k], a.out[o], (size_t)w.n * 4);
+    if (in_place || cand.size() < 2 || stream_capturing(c)) {
+      idx = def;
+    } else {
+      us.assign(cand.size(), 0.0);
+      for (size_t i = 0; i < cand.size() && e == cudaSuccess; ++i) {
+        const int g = sg_stream_grid(w.n, cand[i], c->num_sms), b = (int)cand[i].chunk;
+        e = time_launch(c, [&]() { return sgk::launch_jit_stream(jk, a, g, b, c->stream, nullptr); },
+                        &us[i]);
+        c->kernels += 3;
+      }
+      if (e != cudaSuccess) return e;
+      idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
+      sg_sched_log_sweep(c, SG_SCHED_STREAM, X, us, def);
+      sg_sched_set_tuned(c, SG_SCHED_STREAM, key, idx);
+      learned = sg_sched_learned_index(c, SG_SCHED_STREAM, X, def, &pred);
+    }
+  }
+  sg_sched_note(c, SG_SCHED_STREAM, cand, us, def, learned, idx, pred);
+  return sgk::launch_jit_stream(jk, a, sg_stream_grid(w.n, cand[idx], c->num_sms),
+                                (int)cand[idx].chunk, c->stream, &c->prof);
+}
+
+// The tile of the specialised filter (SG_SCHED_FILTER): learned, autotuned
+// (a sweep the first time the length and predicate shape are seen, unless
+// the look-back testing controls are set or the stream is being captured),
+// else the plain table's 8192 items.  *ran is false when no specialised
+// kernel could be built (the caller interprets).
+cudaError_t launch_filter_scheduled(sg_ctx* c, const sgk::Prog& pr, const float* x, float* out,
+                                    long long n, void* dwork, sgk::FilterResult* rec, bool* ran) {
+  *ran = false;
+  const std::vector<sg_sched_choice> cand = sg_filter_candidates();
+  const sg_sched_choice d = sg_filter_default();
+  FilterWork w;
+  w.n = n;
+  w.ops = pr.nops;
+  std::vector<float> X(cand.size() * kSchedFeatures);
+  int def = 0;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    sg_filter_features(w, cand[i], sgk::filter_tile_occupancy((int)cand[i].chunk), c->num_sms,
+                       &X[i * kSchedFeatures]);
+    if (cand[i].chunk == d.chunk) def = (int)i;
+  }
+  const uint64_t key = sg_sched_key(SG_SCHED_FILTER, {(uint64_t)n, prog_shape(pr)});
+  int learned = -1;
+  std::vector<float> pred;
+  int idx = sg_sched_lookup(c, SG_SCHED_FILTER, key, X, def, &learned, &pred);
+  std::vector<double> us;
+  cudaError_t e = cudaSuccess;
+  auto kernel = [&](int i) { return sgk::jit_filter_kernel(pr, nullptr, (int)cand[i].chunk); };
+  auto launch = [&](cudaKernel_t k, int i, sgk::Prof* prof) {
+    return sgk::launch_filter_specialised(k, x, out, n, pr, dwork, rec, c->stream, c->num_sms,
+                                          &c->kernels, prof, c->lookback, (int)cand[i].chunk);
+  };
+  if (idx < 0) {
+    const bool debug = c->lookback.spin_limit != 0 || c->lookback.skip_tile >= 0;
+    bool all = true;
+    for (size_t i = 0; i < cand.size() && !debug; ++i) all &= kernel((int)i) != nullptr;
+    if (debug || !all || n <= 0 || stream_capturing(c)) {
+      idx = def;
+    } else {
+      us.assign(cand.size(), 0.0);
+      for (size_t i = 0; i < cand.size() && e == cudaSuccess; ++i) {
+        cudaKernel_t k = kernel((int)i);
+        e = time_launch(c, [&]() { return launch(k, (int)i, nullptr); }, &us[i]);
+      }
+      if (e != cudaSuccess) return e;
+      idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
+      sg_sched_log_sweep(c, SG_SCHED_FILTER, X, us, def);
+      sg_sched_set_tuned(c, SG_SCHED_FILTER, key, idx);
+      learned = sg_sched_learned_index(c, SG_SCHED_FILTER, X, def, &pred);
+    }
+  }
+  cudaKernel_t k = kernel(idx);
+  if (!k && idx != def) {
+    idx = def;
+    k = kernel(idx);
+  }
+  if (!k) return cudaSuccess;
+  sg_sched_note(c, SG_SCHED_FILTER, cand, us, def, learned, idx, pred);
+  *ran = true;
+  return launch(k, idx, &c->prof);
+}
+
 }  // namespace
 
 sg_status sg_execute_pending(sg_ctx* c) {
@@ -609,7 +784,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
                                   sizeof(sgk::PassResult));
         break;
       case PK::SORT: work = std::max(work, sgk::sort_scratch_bytes(P.n)); break;
-      case PK::FILTER: work = std::max(work, sgk::filter_scratch_bytes(P.n)); break;
+      case PK::FILTER: work = std::max(work, sgk::filter_jit_scratch_bytes(P.n)); break;
       case PK::CHECK_SORTED:
       case PK::CHECK_PERM: work = std::max(work, sgk::check_scratch_bytes()); break;
       case PK::MATMUL:
@@ -708,11 +883,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
           jk = sgk::jit_stream_kernel(a.prog, a.nin, (int)P.stores.size(), a.npred,
                                       a.has_reduce != 0, minmax, a.pred_exists, nullptr);
         if (jk) {
-          const long long units = std::max<long long>(1, (P.n + 3) / 4);
-          const long long want = (units + kStreamBlock - 1) / kStreamBlock;
-          const int grid = (int)std::max<long long>(
-              1, std::min<long long>(want, (long long)c->num_sms * 8));
-          e = sgk::launch_jit_stream(jk, a, grid, kStreamBlock, c->stream, &c->prof);
+          e = launch_stream_scheduled(c, jk, a, (int)P.stores.size(), minmax);
         } else {
           e = sgk::launch_stream(a, stream_grid(c, P), kStreamBlock, c->stream, &c->prof);
         }
@@ -742,14 +913,12 @@ sg_status sg_execute_pending(sg_ctx* c) {
           pr.cst[p] = ops[p].cst;
           pr.depth[p] = before[p];
         }
-        cudaKernel_t jk = c->codegen == SG_CODEGEN_SPECIALIZE ? sgk::jit_filter_kernel(pr, nullptr)
-                                                              : nullptr;
-        if (jk)
-          e = sgk::launch_filter_specialised(jk, static_cast<const float*>(x->st->ptr),
-                                             static_cast<float*>(n->out->st->ptr), P.n, pr, dwork,
-                                             static_cast<sgk::FilterResult*>(rec), c->stream,
-                                             c->num_sms, &c->kernels, &c->prof, c->lookback);
-        else
+        bool ran = false;
+        if (c->codegen == SG_CODEGEN_SPECIALIZE)
+          e = launch_filter_scheduled(c, pr, static_cast<const float*>(x->st->ptr),
+                                      static_cast<float*>(n->out->st->ptr), P.n, dwork,
+                                      static_cast<sgk::FilterResult*>(rec), &ran);
+        if (!ran && e == cudaSuccess)
           e = sgk::launch_filter(static_cast<const float*>(x->st->ptr),
                                  static_cast<float*>(n->out->st->ptr), P.n, pr, md, dwork,
                                  static_cast<sgk::FilterResult*>(rec), c->stream, c->num_sms,

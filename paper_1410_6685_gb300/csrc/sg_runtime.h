@@ -114,22 +114,39 @@ struct BatchPlanCache {
   ~BatchPlanCache();
 };
 
-// Timing log and learned cost model of the schedule chooser.
+// Timing log and learned cost models of the schedule chooser: one 2x64
+// MLP per decision family (sg_sched_family).
 constexpr int kSchedFeatures = 12;
 constexpr int kSchedMaxCand = 64;
-struct SchedState {
-  std::vector<float> log_x;   // records x kSchedFeatures
-  std::vector<float> log_y;   // log microseconds
-  std::vector<float> log_rel; // log(us / us of the plain choice), NaN outside sweeps
+constexpr int kSchedFamilies = 4;
+struct SchedModel {
   bool trained = false;
   std::vector<float> mu, sd;  // feature normalisation
   float ymu = 0.0f, ysd = 1.0f;
   void* dev = nullptr;        // params, grads, Adam moments, data (device)
   float* params = nullptr;
   float* pred = nullptr;
-  // autotuned choices: (offsets, nseg, chain hash) -> candidate index
-  std::vector<std::pair<std::pair<const void*, long long>, std::pair<uint64_t, int>>> tuned;
-  ~SchedState();
+  ~SchedModel();
+};
+struct SchedState {
+  std::vector<float> log_x;   // records x kSchedFeatures
+  std::vector<float> log_y;   // log microseconds
+  std::vector<float> log_rel; // log(us / us of the plain choice), NaN outside sweeps
+  std::vector<int> log_fam;   // the record's decision family
+  SchedModel model[kSchedFamilies];
+  // autotuned choices: hash of (family, workload) -> candidate index
+  struct Tuned {
+    uint64_t key;
+    int idx, family;
+  };
+  std::vector<Tuned> tuned;
+  // learned choices under the current models (cleared when they are trained)
+  std::vector<std::pair<uint64_t, int>> learned_memo;
+  // sg_sched_force: a candidate index every decision of the family takes
+  int forced[kSchedFamilies] = {-1, -1, -1, -1};
+  // the last decision of each family (sg_sched_last)
+  sg_sched_report last[kSchedFamilies];
+  bool has_last[kSchedFamilies] = {false, false, false, false};
 };
 
 // The blocked factorisation of one size and precision, captured once as a

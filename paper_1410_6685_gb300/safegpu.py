@@ -36,6 +36,7 @@ SG_PRE, SG_POST = 0, 1
 SG_CONTRACTS_OFF, SG_CONTRACTS_PRE, SG_CONTRACTS_PRE_POST, SG_CONTRACTS_FULL = range(4)
 SG_FUSE_OFF, SG_FUSE_ON = 0, 1
 SG_SCHED_AUTOTUNE, SG_SCHED_LEARNED = 0, 1
+SG_SCHED_BATCH, SG_SCHED_STREAM, SG_SCHED_FILTER, SG_SCHED_PRODUCT = 0, 1, 2, 3
 
 SG_MAX_EXPR_OPS = 24
 OPCODES = {
@@ -87,7 +88,8 @@ class SgSchedReport(C.Structure):
                 ("learned_index", C.c_int32), ("chunk", C.c_int64 * SG_SCHED_MAX_CANDIDATES),
                 ("ctas_per_sm", C.c_int32 * SG_SCHED_MAX_CANDIDATES),
                 ("measured_us", C.c_double * SG_SCHED_MAX_CANDIDATES),
-                ("predicted_us", C.c_double * SG_SCHED_MAX_CANDIDATES)]
+                ("predicted_us", C.c_double * SG_SCHED_MAX_CANDIDATES),
+                ("family", C.c_int32), ("chosen_index", C.c_int32)]
 
 
 class SgChain(C.Structure):
@@ -147,7 +149,10 @@ def _load():
         "sg_batch_report": [vp, P(SgChain), vp, vp, i64, vp, vp, vp, P(SgSchedReport)],
         "sg_sched_train": [vp, i32, C.c_float, C.c_uint64, P(C.c_float)],
         "sg_sched_log_size": [vp, P(i64), P(C.c_int32)],
-        "sg_sched_log_read": [vp, vp, vp, i64],
+        "sg_sched_log_read": [vp, vp, vp, vp, i64],
+        "sg_sched_last": [vp, i32, P(SgSchedReport)],
+        "sg_sched_forget": [vp, i32],
+        "sg_sched_force": [vp, i32, i32],
         "sg_mlp_forward": [vp, vp, i32, vp, i64, vp],
         "sg_mlp_loss_grad": [vp, vp, i32, vp, vp, i64, vp, vp],
         "sg_mlp_adam": [vp, vp, vp, vp, vp, i64, i64, C.c_float, C.c_float, C.c_float, C.c_float],
@@ -570,14 +575,33 @@ def sg_sched_train(ctx, epochs=200, lr=1e-3, seed=1) -> float:
 
 
 def sg_sched_log(ctx):
+    """The timing log: features (records x 12), log microseconds, family."""
     import numpy as np
     n, d = C.c_int64(), C.c_int32()
     _check(lib.sg_sched_log_size(ctx, C.byref(n), C.byref(d)), ctx)
     X = np.empty((n.value, d.value), np.float32)
     y = np.empty(n.value, np.float32)
+    fam = np.empty(n.value, np.int32)
     _check(lib.sg_sched_log_read(ctx, C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data),
-                                 n.value), ctx)
-    return X, y
+                                 C.c_void_p(fam.ctypes.data), n.value), ctx)
+    return X, y, fam
+
+
+def sg_sched_forget(ctx, family=-1):
+    """Drops the autotuned choices of `family` (-1: all) so they are measured again."""
+    _check(lib.sg_sched_forget(ctx, family), ctx)
+
+
+def sg_sched_force(ctx, family, index):
+    """Every later decision of `family` takes candidate `index` (-1: none)."""
+    _check(lib.sg_sched_force(ctx, family, index), ctx)
+
+
+def sg_sched_last(ctx, family) -> SgSchedReport:
+    """The last decision the context took in `family` (SG_SCHED_*)."""
+    r = SgSchedReport()
+    _check(lib.sg_sched_last(ctx, family, C.byref(r)), ctx)
+    return r
 
 
 def sg_mlp_forward(ctx, p_ptr, d_in, x_ptr, B, yhat_ptr):

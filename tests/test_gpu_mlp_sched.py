@@ -111,7 +111,7 @@ def test_learned_schedule_gain_over_plain_table(env):
         x, to, outs, nseg = make_workload(torch, rng, *spec(rng))
         sg.sg_batch_run(ctx, chain, x.data_ptr(), to.data_ptr(), nseg, *(t.data_ptr() for t in outs))
         del x, to, outs
-    Xlog, ylog = sg.sg_sched_log(ctx)
+    Xlog, ylog, _ = sg.sg_sched_log(ctx)
     assert len(ylog) >= 40 * 8 and Xlog.shape == (len(ylog), D_IN)
     loss = sg.sg_sched_train(ctx, epochs=400, lr=3e-3, seed=7)
     assert loss < 0.5          # standardised relative log-time: well below its variance (1.0)
