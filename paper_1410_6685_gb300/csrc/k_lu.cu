@@ -344,34 +344,18 @@ __global__ void __launch_bounds__(kPT, 1)
   const int tid = threadIdx.x;
   const int lane = tid & 31, w = tid >> 5;
 
-  // the slab, eight loads in flight per thread (a warp reads one row per load)
   const int total = (r1 - r0) * kPB;
-  for (int base = 0; base < total; base += 8 * kPT) {
-    float v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = base + u * kPT + tid, r = t >> 5, c = t & 31;
-      v[u] = (t < total && c < jb) ? __ldg(LU + (size_t)(k + r0 + r) * n + k + c) : 0.0f;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = base + u * kPT + tid;
-      if (t < total) lbuf[(t >> 5) * kStride + (t & 31)] = v[u];
-    }
-  }
-  if (tid < 2) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&bar[tid])) : "memory");
-  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  // every CTA's barriers exist before anyone sends; the slab is complete
-  cluster.sync();
-  // my rows: r = r0 + tid + i * kPT; positions and values in registers
+  // my rows: r = r0 + tid + i * kPT, loaded whole into registers with every
+  // load of the thread in flight at once (float4 where the rows start on 16
+  // bytes); lbuf only receives the L and U entries as they form
   float x[kRows][kPB];
-  float lr[kRows];       // a row's pending multiplier
+  float lr[kRows];       // a row's pending multiplier (0 after a zero pivot)
   int lp[kRows];
   bool act[kRows], pend[kRows];
   float pv[kPB];         // the last pivot row, shifted (pv[c] is column j + c of its step)
-  bool pzero = false;
 #pragma unroll
   for (int c = 0; c < kPB; ++c) pv[c] = 0.0f;
+  const bool vec = ((n | k) & 3) == 0;   // then jb is a multiple of 4 too
 #pragma unroll
   for (int i = 0; i < kRows; ++i) {
     const int r = r0 + tid + i * kPT;
@@ -379,14 +363,31 @@ __global__ void __launch_bounds__(kPT, 1)
     act[i] = r < r1;
     pend[i] = false;
     lr[i] = 0.0f;
+    const float* src = LU + (size_t)(k + (act[i] ? r : 0)) * n + k;
+    if (vec) {
 #pragma unroll
-    for (int c = 0; c < kPB; ++c) x[i][c] = act[i] ? lbuf[(r - r0) * kStride + c] : 0.0f;
+      for (int q = 0; q < kPB / 4; ++q) {
+        const float4 v = act[i] && 4 * q < jb ? __ldg(reinterpret_cast<const float4*>(src) + q)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[i][4 * q] = v.x; x[i][4 * q + 1] = v.y; x[i][4 * q + 2] = v.z; x[i][4 * q + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < kPB; ++c) x[i][c] = act[i] && c < jb ? __ldg(src + c) : 0.0f;
+    }
   }
+  if (tid < 2) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&bar[tid])) : "memory");
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  // every CTA's barriers exist before anyone sends
+  cluster.sync();
   // the deferred part of a row's update: registers 1..30 of the shifted row
-  // (register 0, the next column, was updated when the multiplier was formed)
+  // (register 0, the next column, was updated when the multiplier was formed).
+  // After a zero pivot the multiplier and the pivot row are +0, and
+  // x + (-0)(+0) = x for every x (signed zeros, infinities, NaN): the row is
+  // only shifted, as the zero-pivot rule wants, without a select per entry.
   auto finish = [&](int i) {
 #pragma unroll
-    for (int c = 1; c + 1 < kPB; ++c) x[i][c] = pzero ? x[i][c + 1] : fmaf(-lr[i], pv[c + 1], x[i][c + 1]);
+    for (int c = 1; c + 1 < kPB; ++c) x[i][c] = fmaf(-lr[i], pv[c + 1], x[i][c + 1]);
     x[i][kPB - 1] = 0.0f;
     pend[i] = false;
   };
@@ -481,7 +482,11 @@ __global__ void __launch_bounds__(kPT, 1)
       }
     }
     const float d = pv[0];
-    pzero = d == 0.0f;
+    const bool pzero = d == 0.0f;
+    if (pzero) {
+#pragma unroll
+      for (int c = 0; c < kPB; ++c) pv[c] = 0.0f;
+    }
     if (pzero && my_info == 0) my_info = k + j + 1;
     const float rd = 1.0f / d;
     // interchange of positions j and p; the pivot row writes its U part
@@ -508,8 +513,8 @@ __global__ void __launch_bounds__(kPT, 1)
       const int r = r0 + tid + i * kPT;
       const float l = pzero ? x[i][0] : x[i][0] * rd;
       lbuf[(r - r0) * kStride + j] = l;
-      lr[i] = l;
-      x[i][0] = pzero ? x[i][1] : fmaf(-l, pv[1], x[i][1]);
+      lr[i] = pzero ? 0.0f : l;
+      x[i][0] = fmaf(-lr[i], pv[1], x[i][1]);
       pend[i] = true;
     }
     if (tid == 0 && rank == 0) piv[k + j] = k + p;
