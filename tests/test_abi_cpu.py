@@ -241,3 +241,25 @@ def test_lookback_switch_arguments(sg, pctx):
     with pytest.raises(sg.SgError) as e:
         sg.sg_debug_lookback(pctx, 0, -2)
     assert e.value.status == sg.SG_ERR_INVALID_ARG
+
+
+def test_schedule_family_arguments(sg, pctx):
+    """The schedule chooser's per-family calls: nothing decided yet, bad
+    families and indices refused, forgetting and forcing accepted."""
+    for fam in (sg.SG_SCHED_BATCH, sg.SG_SCHED_STREAM, sg.SG_SCHED_FILTER, sg.SG_SCHED_PRODUCT):
+        with pytest.raises(sg.SgError) as e:
+            sg.sg_sched_last(pctx, fam)
+        assert e.value.status == sg.SG_ERR_INVALID_ARG
+        sg.sg_sched_forget(pctx, fam)
+        sg.sg_sched_force(pctx, fam, 0)
+        sg.sg_sched_force(pctx, fam, -1)
+    sg.sg_sched_forget(pctx, -1)
+    for bad in ((4, 0), (-1, 0), (0, -2), (0, sg.SG_SCHED_MAX_CANDIDATES)):
+        with pytest.raises(sg.SgError) as e:
+            sg.sg_sched_force(pctx, *bad)
+        assert e.value.status == sg.SG_ERR_INVALID_ARG
+    with pytest.raises(sg.SgError):
+        sg.sg_sched_forget(pctx, 4)
+    # an empty log trains nothing
+    X, y, fam = sg.sg_sched_log(pctx)
+    assert X.shape == (0, 12) and y.shape == (0,) and fam.shape == (0,)
