@@ -302,6 +302,16 @@ def time_steps(torch, stream, step, k):
     return e0.elapsed_time(e1) / k
 
 
+def fusion_plan(sg, ctx):
+    """The plan the last fusion-boundary decision ran: "fused" (Sec. 5's
+    merges) or "unfused (autotuned)"."""
+    try:
+        r = sg.sg_sched_last(ctx, sg.SG_SCHED_FUSION)
+    except sg.SgError:
+        return "fused"
+    return "fused" if r.chosen_index == 0 else "unfused (autotuned)"
+
+
 def with_contracts_off(sg, ctx, fn):
     sg.sg_set_contract_mode(ctx, sg.SG_CONTRACTS_OFF)
     try:
@@ -340,11 +350,12 @@ def secondary_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak):
         sg.sg_vector_release(z)
         sg.sg_scalar_release(r)
     ms = time_steps(torch, stream, s_stream, k)
+    plan = fusion_plan(sg, ctx)
     ms_off = with_contracts_off(sg, ctx, lambda: time_steps(torch, stream, s_stream, k))
     gbs = 12.0 * n / (ms / 1e3) / 1e9     # read x, y; write z
     out["stream_zip_sum_forall"] = {
         "n": n, "ms": round(ms, 4), "GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4),
-        "bytes_per_elem": 12, "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2)}
+        "bytes_per_elem": 12, "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2), "plan": plan}
     sg.sg_vector_release(vx)
     sg.sg_vector_release(vy)
     del x, y
@@ -625,11 +636,12 @@ def per_config_workloads(torch, sg, ctx, stream, k, hbm_peak, tc_peak, tc_sustai
         sg.sg_set_fusion(ctx, fusion)
         try:
             ms = time_steps(torch, stream, s_vadd, 4 * k)
+            plan = "unfused" if fusion == sg.SG_FUSE_OFF else fusion_plan(sg, ctx)
             ms_off = with_contracts_off(sg, ctx, lambda: time_steps(torch, stream, s_vadd, 4 * k))
         finally:
             sg.sg_set_fusion(ctx, sg.SG_FUSE_ON)
         row[name] = {"ms": round(ms, 4), "GBps_12B": round(12.0 * n / (ms / 1e3) / 1e9, 1),
-                     "ms_contracts_off": round(ms_off, 4),
+                     "plan": plan, "ms_contracts_off": round(ms_off, 4),
                      "contract_overhead_pct": round((ms / ms_off - 1) * 100, 2)}
     t_cpu = cpu_time(lambda: (oracle.sum(oracle.map(add, a, b)),
                               oracle.first_false([("x", 0), ("x", 1), ("x", 2), ("add",), ("eq",)],

@@ -567,12 +567,23 @@ sg_status sg_batch_run(sg_ctx* ctx, const sg_chain* chain, const float* data,
  *                     in bf16 / fp16): chunk = tile rows, ctas_per_sm =
  *                     CTAs per tile (256, 2: a CTA pair; 128, 1: one CTA);
  *                     plain table the pair (on devices that schedule pairs)
+ *   SG_SCHED_FUSION   the fusion boundaries of a flush whose work is only
+ *                     element-wise passes (maps, zips, reductions, for_all /
+ *                     exists and range contracts, no call writing in place)
+ *                     and whose fused and unfused plans differ: chunk = the
+ *                     candidate plan's kernels, ctas_per_sm = 1 for the
+ *                     fused plan (Sec. 5's merges), 0 for one kernel per
+ *                     queued call; plain table the fused plan.  Under
+ *                     SG_FUSE_OFF nothing is decided.  The autotuner takes
+ *                     the unfused plan only when it measured more than 3%
+ *                     faster
  * SG_SCHED_AUTOTUNE measures every candidate the first time a workload is
  * seen -- a warm-up run, then the better of two runs timed with CUDA
  * events -- and keeps the fastest (the batch: per offsets pointer, count
  * and chain; a stream pass: per length, program shape and alignment; the
  * filter: per length and predicate shape; the product: per M, N, K and
- * precision).  A stream pass that writes over one of its inputs is not
+ * precision; the fusion boundaries: per shape of the queued calls, timing
+ * each plan's kernels over the whole flush).  A stream pass that writes over one of its inputs is not
  * re-run: it takes the plain table's choice.  Each measurement is logged
  * as (family, 12 features, log microseconds, log of the time relative to
  * the plain table's choice on that workload).  sg_sched_train fits one 2x64
@@ -587,7 +598,8 @@ typedef enum {
   SG_SCHED_BATCH = 0,
   SG_SCHED_STREAM = 1,
   SG_SCHED_FILTER = 2,
-  SG_SCHED_PRODUCT = 3
+  SG_SCHED_PRODUCT = 3,
+  SG_SCHED_FUSION = 4
 } sg_sched_family;
 #define SG_SCHED_MAX_CANDIDATES 32
 typedef struct {

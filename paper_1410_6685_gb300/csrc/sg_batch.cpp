@@ -315,12 +315,12 @@ extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* da
                                     (uint64_t)j.stats.total, mb, chain_hash(*ch)});
   int learned = -1;
   std::vector<float> pred;
-  int idx = sg_sched_lookup(c, SG_SCHED_BATCH, key, X, def, &learned, &pred);
   std::vector<double> times;
+  int idx = sg_sched_lookup(c, SG_SCHED_BATCH, key, X, def, &learned, &pred, &times);
   if (idx < 0) {
     st = autotune(c, j, cand, X, def, &times, &idx);
     if (st) return st;
-    sg_sched_set_tuned(c, SG_SCHED_BATCH, key, idx);
+    sg_sched_set_tuned(c, SG_SCHED_BATCH, key, idx, times);
   }
   sg_sched_note(c, SG_SCHED_BATCH, cand, times, def, learned, idx, pred);
   bool viol = false;

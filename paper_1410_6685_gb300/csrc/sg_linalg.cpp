@@ -42,8 +42,8 @@ int product_form(sg_ctx* c, int M, int N, int K, bool fp16, const float* a, cons
                                                        (uint64_t)fp16});
   int learned = -1;
   std::vector<float> pred;
-  int idx = sg_sched_lookup(c, SG_SCHED_PRODUCT, key, X, def, &learned, &pred);
   std::vector<double> us;
+  int idx = sg_sched_lookup(c, SG_SCHED_PRODUCT, key, X, def, &learned, &pred, &us);
   if (idx < 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -58,7 +58,7 @@ int product_form(sg_ctx* c, int M, int N, int K, bool fp16, const float* a, cons
       if (*e != cudaSuccess) return 0;
       idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
       sg_sched_log_sweep(c, SG_SCHED_PRODUCT, X, us, def);
-      sg_sched_set_tuned(c, SG_SCHED_PRODUCT, key, idx);
+      sg_sched_set_tuned(c, SG_SCHED_PRODUCT, key, idx, us);
       learned = sg_sched_learned_index(c, SG_SCHED_PRODUCT, X, def, &pred);
     }
   }

@@ -120,12 +120,14 @@ bool program_depths(const std::vector<Op>& ops, std::vector<uint8_t>* before, in
 
 struct Planner {
   sg_ctx* c;
+  bool fuse;                    // merge passes (Sec. 5), else one pass per call
   std::vector<Node*> nodes;
   std::set<Node*> unmaskable;   // filters that must be compacted
   std::vector<Pass> passes;
   std::map<Value*, std::vector<Node*>> consumers;
 
-  explicit Planner(sg_ctx* ctx) : c(ctx) {
+  explicit Planner(sg_ctx* ctx) : Planner(ctx, ctx->fusion == SG_FUSE_ON) {}
+  Planner(sg_ctx* ctx, bool f) : c(ctx), fuse(f) {
     for (auto& n : c->pending) nodes.push_back(n.get());
     for (Node* n : nodes)
       for (int k = 0; k < n->nin; ++k)
@@ -135,7 +137,7 @@ struct Planner {
   // A filter can become a mask when only reductions consume its result and
   // no handle refers to it.
   bool maskable(Node* f) {
-    if (c->fusion != SG_FUSE_ON || unmaskable.count(f)) return false;
+    if (!fuse || unmaskable.count(f)) return false;
     Value* y = f->out.get();
     if (y->handles > 0) return false;
     auto it = consumers.find(y);
@@ -158,7 +160,7 @@ struct Planner {
   // never materialised: y = A^T x is computed as x^T A on the source.
   std::set<Node*> virtual_t;
   bool virtual_transpose(Node* n) {
-    if (c->fusion != SG_FUSE_ON || n->kind != NK::TRANSPOSE) return false;
+    if (!fuse || n->kind != NK::TRANSPOSE) return false;
     Value* v = n->out.get();
     if (v->handles > 0) return false;
     auto it = consumers.find(v);
@@ -300,7 +302,7 @@ struct Planner {
       const bool streamable = is_f32_stream_node(n) || (n->kind == NK::FILTER && maskable(n));
       if (streamable) {
         const int64_t len = node_len(n);
-        if (open && c->fusion == SG_FUSE_ON && passes.back().n == len && try_add(passes.back(), n))
+        if (open && fuse && passes.back().n == len && try_add(passes.back(), n))
           continue;
         Pass P;
         P.kind = PK::STREAM;
@@ -344,7 +346,7 @@ struct Planner {
         case NK::CHECK:
           if (n->ckind == SG_C_SORTED) {
             // fuse into the sort that produced the checked value
-            if (c->fusion == SG_FUSE_ON && !passes.empty() && passes.back().kind == PK::SORT &&
+            if (fuse && !passes.empty() && passes.back().kind == PK::SORT &&
                 passes.back().main->out.get() == n->in[0].get() && !passes.back().chk_sorted) {
               passes.back().chk_sorted = n;
               passes.back().nodes.push_back(n);
@@ -352,7 +354,7 @@ struct Planner {
             }
             P.kind = PK::CHECK_SORTED;
           } else if (n->ckind == SG_C_PERMUTATION) {
-            if (c->fusion == SG_FUSE_ON && !passes.empty() && passes.back().kind == PK::SORT &&
+            if (fuse && !passes.empty() && passes.back().kind == PK::SORT &&
                 passes.back().main->out.get() == n->in[0].get() &&
                 passes.back().main->in[0].get() == n->in[1].get() && !passes.back().chk_perm) {
               passes.back().chk_perm = n;
@@ -364,7 +366,7 @@ struct Planner {
             P.kind = PK::CHECK_SAME;
           } else {
             // fold into the tensor-core product that produced the checked value
-            if (c->fusion == SG_FUSE_ON && !passes.empty() && passes.back().kind == PK::MATMUL &&
+            if (fuse && !passes.empty() && passes.back().kind == PK::MATMUL &&
                 !passes.back().chk_frv && sg_linalg_can_fuse(passes.back().main, n)) {
               passes.back().chk_frv = n;
               passes.back().nodes.push_back(n);
@@ -665,8 +667,8 @@ cudaError_t launch_stream_scheduled(sg_ctx* c, cudaKernel_t jk, const sgk::Strea
                                      (uint64_t)(w.reduce + 2 * w.minmax + 4 * w.vec4)});
   int learned = -1;
   std::vector<float> pred;
-  int idx = sg_sched_lookup(c, SG_SCHED_STREAM, key, X, def, &learned, &pred);
   std::vector<double> us;
+  int idx = sg_sched_lookup(c, SG_SCHED_STREAM, key, X, def, &learned, &pred, &us);
   cudaError_t e = cudaSuccess;
   if (idx < 0) {
     bool in_place = false;
@@ -686,7 +688,7 @@ cudaError_t launch_stream_scheduled(sg_ctx* c, cudaKernel_t jk, const sgk::Strea
       if (e != cudaSuccess) return e;
       idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
       sg_sched_log_sweep(c, SG_SCHED_STREAM, X, us, def);
-      sg_sched_set_tuned(c, SG_SCHED_STREAM, key, idx);
+      sg_sched_set_tuned(c, SG_SCHED_STREAM, key, idx, us);
       learned = sg_sched_learned_index(c, SG_SCHED_STREAM, X, def, &pred);
     }
   }
@@ -718,8 +720,8 @@ cudaError_t launch_filter_scheduled(sg_ctx* c, const sgk::Prog& pr, const float*
   const uint64_t key = sg_sched_key(SG_SCHED_FILTER, {(uint64_t)n, prog_shape(pr)});
   int learned = -1;
   std::vector<float> pred;
-  int idx = sg_sched_lookup(c, SG_SCHED_FILTER, key, X, def, &learned, &pred);
   std::vector<double> us;
+  int idx = sg_sched_lookup(c, SG_SCHED_FILTER, key, X, def, &learned, &pred, &us);
   cudaError_t e = cudaSuccess;
   auto kernel = [&](int i) { return sgk::jit_filter_kernel(pr, nullptr, (int)cand[i].chunk); };
   auto launch = [&](cudaKernel_t k, int i, sgk::Prof* prof) {
@@ -741,7 +743,7 @@ cudaError_t launch_filter_scheduled(sg_ctx* c, const sgk::Prog& pr, const float*
       if (e != cudaSuccess) return e;
       idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
       sg_sched_log_sweep(c, SG_SCHED_FILTER, X, us, def);
-      sg_sched_set_tuned(c, SG_SCHED_FILTER, key, idx);
+      sg_sched_set_tuned(c, SG_SCHED_FILTER, key, idx, us);
       learned = sg_sched_learned_index(c, SG_SCHED_FILTER, X, def, &pred);
     }
   }
@@ -758,7 +760,14 @@ cudaError_t launch_filter_scheduled(sg_ctx* c, const sgk::Prog& pr, const float*
 
 }  // namespace
 
-sg_status sg_execute_pending(sg_ctx* c) {
+namespace {
+
+// One execution of the queued work under the fused (Sec. 5) or the unfused
+// plan.  commit: the results go to the handles and the queue is emptied (the
+// flush itself); otherwise (a measurement of the fusion boundaries) only the
+// kernels run, and *us receives their device time (CUDA events on the
+// context's stream).
+sg_status run_flush(sg_ctx* c, bool fuse, bool commit, double* us) {
   // is an asynchronous read still on the copy engine?  (asked before this
   // flush launches anything; "not ready" is not an error of this flush)
   bool dl_busy = false;
@@ -769,7 +778,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
       cudaGetLastError();
     }
   }
-  Planner pl(c);
+  Planner pl(c, fuse);
   pl.plan();
   std::vector<Pass>& passes = pl.passes;
   c->has_violation = false;
@@ -804,7 +813,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
   sg_status st = ensure_scratch(c, res_bytes + work);
   if (!st) st = ensure_host_res(c, res_bytes);
   if (st) {
-    c->pending.clear();
+    if (commit) c->pending.clear();
     return st;
   }
   char* dres = static_cast<char*>(c->scratch);
@@ -828,6 +837,12 @@ sg_status sg_execute_pending(sg_ctx* c) {
   }
   cudaError_t e = need_records ? cudaMemsetAsync(dres, 0, res_bytes, c->stream) : cudaSuccess;
   sg_status status = SG_OK;
+  cudaEvent_t tev[2] = {nullptr, nullptr};
+  if (us && e == cudaSuccess) {
+    e = cudaEventCreate(&tev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&tev[1]);
+    if (e == cudaSuccess) e = cudaEventRecord(tev[0], c->stream);
+  }
 
   for (size_t i = 0; i < passes.size() && e == cudaSuccess && !status; ++i) {
     Pass& P = passes[i];
@@ -1031,6 +1046,7 @@ sg_status sg_execute_pending(sg_ctx* c) {
       }
     }
   }
+  if (us && e == cudaSuccess && !status) e = cudaEventRecord(tev[1], c->stream);
   // while an asynchronous read is still on the copy engine, the records are
   // stored by a kernel instead of queueing a copy behind it
   if (e == cudaSuccess && !status && need_records) {
@@ -1045,8 +1061,17 @@ sg_status sg_execute_pending(sg_ctx* c) {
   }
   if (e == cudaSuccess && !status && need_records) e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess && !status && !need_records) e = cudaGetLastError();
+  if (us) {
+    float ms = 0.0f;
+    if (e == cudaSuccess && !status) e = cudaEventSynchronize(tev[1]);
+    if (e == cudaSuccess && !status) e = cudaEventElapsedTime(&ms, tev[0], tev[1]);
+    *us = 1000.0 * ms;
+    for (cudaEvent_t v : tev)
+      if (v) cudaEventDestroy(v);
+  }
   if (e != cudaSuccess && !status) status = cuda_fail(c, e, "kernel execution");
   if (e == cudaSuccess) c->prof.collect();
+  if (!commit) return status;
 
   bool have = false;
   sg_status cstatus = SG_OK;
@@ -1166,6 +1191,132 @@ sg_status sg_execute_pending(sg_ctx* c) {
   c->pending.clear();
   if (status) return status;
   return cstatus;
+}
+
+// The fusion boundaries (SG_SCHED_FUSION) of a flush whose work is only
+// element-wise passes: true for the fused plan.  The fused plan unless a
+// forced choice, the learned model or the autotuner's measurement of both
+// plans over the whole flush (a warm-up, then the better of two runs, each
+// plan's kernels timed by CUDA events) prefers one kernel per queued call.
+bool choose_fusion(sg_ctx* c) {
+  // the shape of the queued calls: kinds, programs (not their constants),
+  // which call feeds which, lengths, and which results a handle keeps
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  std::map<const Value*, int> ext;
+  std::map<const Value*, int> made;
+  int idx_node = 0;
+  for (auto& np : c->pending) {
+    const Node* nd = np.get();
+    const bool elementwise = (nd->kind == NK::MAP && !nd->inplace) || nd->kind == NK::REDUCE ||
+                             nd->kind == NK::QUANT || nd->kind == NK::CHECK;
+    if (!elementwise) return true;
+    mix((uint64_t)nd->kind);
+    mix((uint64_t)nd->nin);
+    mix((uint64_t)nd->rop);
+    mix((uint64_t)nd->ckind * 2 + (nd->exists ? 1 : 0));
+    for (int p = 0; p < nd->expr.nops; ++p) {
+      mix((uint64_t)nd->expr.ops[p].op);
+      mix((uint64_t)(uint32_t)nd->expr.ops[p].arg);
+    }
+    for (int k = 0; k < nd->nin; ++k) {
+      const Value* v = nd->in[k].get();
+      if (!v) continue;
+      mix((uint64_t)v->n);
+      auto m = made.find(v);
+      if (m != made.end()) {
+        mix(0x100000000ull + (uint64_t)m->second);
+      } else {
+        auto e = ext.find(v);
+        const int id = e == ext.end() ? (int)ext.size() : e->second;
+        if (e == ext.end()) ext[v] = id;
+        mix(0x200000000ull + (uint64_t)id);
+      }
+    }
+    if (nd->out) {
+      made[nd->out.get()] = idx_node;
+      mix(nd->out->handles > 0 ? 1 : 2);
+    }
+    ++idx_node;
+  }
+  const uint64_t key = sg_sched_key(SG_SCHED_FUSION, {h});
+  const int forced = c->schedst.forced[SG_SCHED_FUSION];
+  SchedState& ss = c->schedst;
+  if (forced < 0 || forced > 1) {
+    if (c->sched == SG_SCHED_LEARNED && ss.model[SG_SCHED_FUSION].trained)
+      for (auto& t : ss.learned_memo)
+        if (t.first == key) return t.second == 0;
+    const int tuned = sg_sched_tuned(c, key);
+    if (tuned >= 0 && !(c->sched == SG_SCHED_LEARNED && ss.model[SG_SCHED_FUSION].trained))
+      return tuned == 0;
+  }
+  // first sight: both plans, which must be element-wise passes alone and differ
+  Planner pf(c, true), pu(c, false);
+  pf.plan();
+  pu.plan();
+  FusionWork w;
+  w.nodes = (int)c->pending.size();
+  bool ok = true;
+  Planner* pls[2] = {&pf, &pu};
+  for (int k = 0; k < 2; ++k)
+    for (const Pass& P : pls[k]->passes) {
+      if (P.kind != PK::STREAM) {
+        ok = false;
+        continue;
+      }
+      if (P.prog.empty()) continue;
+      w.passes[k] += 1;
+      w.bytes[k] += 4.0 * (double)P.n * (double)(P.inputs.size() + P.stores.size());
+      w.n = std::max<long long>(w.n, P.n);
+    }
+  for (auto& np : c->pending) {
+    const Node* nd = np.get();
+    w.reduces += nd->kind == NK::REDUCE;
+    w.preds += nd->kind == NK::QUANT || nd->kind == NK::CHECK;
+    w.ops += nd->expr.nops;
+  }
+  if (!ok || w.passes[0] == w.passes[1]) {
+    if (forced < 0) sg_sched_set_tuned(c, SG_SCHED_FUSION, key, 0);
+    return true;
+  }
+  const std::vector<sg_sched_choice> cand = sg_fusion_candidates(w);
+  std::vector<float> X(2 * kSchedFeatures);
+  for (int k = 0; k < 2; ++k) sg_fusion_features(w, k, &X[(size_t)k * kSchedFeatures]);
+  std::vector<float> pred;
+  std::vector<double> us;
+  int learned = -1, idx = 0;
+  if (forced == 0 || forced == 1) {
+    idx = forced;
+  } else if (c->sched == SG_SCHED_LEARNED && ss.model[SG_SCHED_FUSION].trained) {
+    learned = sg_sched_learned_index(c, SG_SCHED_FUSION, X, 0, &pred);
+    idx = learned >= 0 ? learned : 0;
+    ss.learned_memo.push_back({key, idx});
+  } else if (!stream_capturing(c)) {
+    us.assign(2, 0.0);
+    for (int k = 0; k < 2; ++k) {
+      double best = 1e300;
+      for (int r = 0; r < 3; ++r) {
+        double t = 0.0;
+        if (run_flush(c, k == 0, false, &t) != SG_OK) return true;
+        if (r > 0) best = std::min(best, t);
+      }
+      us[k] = best;
+    }
+    idx = us[1] < kFusionMargin * us[0] ? 1 : 0;
+    sg_sched_log_sweep(c, SG_SCHED_FUSION, X, us, 0);
+    sg_sched_set_tuned(c, SG_SCHED_FUSION, key, idx, us);
+    learned = sg_sched_learned_index(c, SG_SCHED_FUSION, X, 0, &pred);
+  }
+  sg_sched_note(c, SG_SCHED_FUSION, cand, us, 0, learned, idx, pred);
+  return idx == 0;
+}
+
+}  // namespace
+
+sg_status sg_execute_pending(sg_ctx* c) {
+  bool fuse = c->fusion == SG_FUSE_ON;
+  if (fuse && !c->pending.empty()) fuse = choose_fusion(c);
+  return run_flush(c, fuse, true, nullptr);
 }
 
 sg_status sg_describe_pending(sg_ctx* c, std::string* out) {

@@ -118,7 +118,7 @@ struct BatchPlanCache {
 // MLP per decision family (sg_sched_family).
 constexpr int kSchedFeatures = 12;
 constexpr int kSchedMaxCand = 64;
-constexpr int kSchedFamilies = 4;
+constexpr int kSchedFamilies = 5;
 struct SchedModel {
   bool trained = false;
   std::vector<float> mu, sd;  // feature normalisation
@@ -138,15 +138,16 @@ struct SchedState {
   struct Tuned {
     uint64_t key;
     int idx, family;
+    std::vector<double> us;   // the sweep's times, for sg_sched_last
   };
   std::vector<Tuned> tuned;
   // learned choices under the current models (cleared when they are trained)
   std::vector<std::pair<uint64_t, int>> learned_memo;
   // sg_sched_force: a candidate index every decision of the family takes
-  int forced[kSchedFamilies] = {-1, -1, -1, -1};
+  int forced[kSchedFamilies] = {-1, -1, -1, -1, -1};
   // the last decision of each family (sg_sched_last)
   sg_sched_report last[kSchedFamilies];
-  bool has_last[kSchedFamilies] = {false, false, false, false};
+  bool has_last[kSchedFamilies] = {};
 };
 
 // The blocked factorisation of one size and precision, captured once as a

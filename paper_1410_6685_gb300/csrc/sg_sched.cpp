@@ -16,6 +16,10 @@
 //   product  [log2 M, log2 N, log2 K, fp16, CTAs per tile, log2 tiles,
 //             SMs busy / SMs, row and column padding of the tiles, log2
 //             flops, tiles per busy SM (log2), 0]
+//   fusion   [log2 n, queued calls, the plan's kernels, the unfused plan's
+//             extra kernels, reductions, predicates, ops / 48, unfused,
+//             log2 of the plan's bytes, its bytes / the fused plan's, log2
+//             bytes per kernel, 0]
 // The autotuner measures every candidate of a workload (a warm-up run, then
 // the better of two timed runs, CUDA events) and keeps the fastest; each
 // measurement is logged as (family, features, log microseconds, log of the
@@ -183,6 +187,27 @@ void sg_product_features(const ProductWork& w, const sg_sched_choice& ch, int nu
   f[11] = 0.0f;
 }
 
+// ---- the fusion boundaries ------------------------------------------------------
+
+std::vector<sg_sched_choice> sg_fusion_candidates(const FusionWork& w) {
+  return {sg_sched_choice{w.passes[0], 1}, sg_sched_choice{w.passes[1], 0}};
+}
+
+void sg_fusion_features(const FusionWork& w, int cand, float* f) {
+  f[0] = lg2((double)w.n);
+  f[1] = (float)w.nodes;
+  f[2] = (float)w.passes[cand];
+  f[3] = (float)(w.passes[1] - w.passes[0]);
+  f[4] = (float)w.reduces;
+  f[5] = (float)w.preds;
+  f[6] = (float)w.ops / 48.0f;
+  f[7] = (float)cand;
+  f[8] = lg2(w.bytes[cand]);
+  f[9] = (float)(w.bytes[cand] / std::max(1.0, w.bytes[0]));
+  f[10] = lg2(w.bytes[cand] / std::max(1.0, (double)w.passes[cand]));
+  f[11] = 0.0f;
+}
+
 // ---- the log, the tuned table and the last decisions --------------------------
 
 void sg_sched_log_add(sg_ctx* c, int family, const float* f, double us, float rel) {
@@ -208,19 +233,24 @@ uint64_t sg_sched_key(int family, std::initializer_list<uint64_t> parts) {
   return h;
 }
 
-int sg_sched_tuned(const sg_ctx* c, uint64_t key) {
+int sg_sched_tuned(const sg_ctx* c, uint64_t key, std::vector<double>* us) {
   for (auto& t : c->schedst.tuned)
-    if (t.key == key) return t.idx;
+    if (t.key == key) {
+      if (us) *us = t.us;
+      return t.idx;
+    }
   return -1;
 }
 
-void sg_sched_set_tuned(sg_ctx* c, int family, uint64_t key, int idx) {
+void sg_sched_set_tuned(sg_ctx* c, int family, uint64_t key, int idx,
+                        const std::vector<double>& us) {
   for (auto& t : c->schedst.tuned)
     if (t.key == key) {
       t.idx = idx;
+      t.us = us;
       return;
     }
-  c->schedst.tuned.push_back({key, idx, family});
+  c->schedst.tuned.push_back({key, idx, family, us});
 }
 
 void sg_sched_note(sg_ctx* c, int family, const std::vector<sg_sched_choice>& cand,
@@ -257,7 +287,7 @@ void sg_sched_note(sg_ctx* c, int family, const std::vector<sg_sched_choice>& ca
 }
 
 int sg_sched_lookup(sg_ctx* c, int family, uint64_t key, const std::vector<float>& X, int def,
-                    int* learned, std::vector<float>* pred) {
+                    int* learned, std::vector<float>* pred, std::vector<double>* us) {
   *learned = -1;
   const int f = c->schedst.forced[family];
   if (f >= 0 && f < (int)(X.size() / kSchedFeatures)) return f;
@@ -271,7 +301,7 @@ int sg_sched_lookup(sg_ctx* c, int family, uint64_t key, const std::vector<float
       return *learned;
     }
   }
-  return sg_sched_tuned(c, key);
+  return sg_sched_tuned(c, key, us);
 }
 
 // ---------------------------------------------------------------------------

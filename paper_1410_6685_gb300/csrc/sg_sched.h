@@ -40,6 +40,14 @@ struct ProductWork {
   bool fp16 = false;
 };
 
+// A flush of element-wise passes, under its fused and its unfused plan
+struct FusionWork {
+  long long n = 0;           // the longest pass
+  int nodes = 0, reduces = 0, preds = 0, ops = 0;
+  int passes[2] = {0, 0};    // kernels of the fused / unfused plan
+  double bytes[2] = {0, 0};  // bytes those kernels read and write
+};
+
 // occ: resident CTAs per SM of the batch kernel that will run
 std::vector<sg_sched_choice> sg_batch_candidates(int occ);
 sg_sched_choice sg_batch_default(int occ);
@@ -63,6 +71,13 @@ std::vector<sg_sched_choice> sg_product_candidates(bool pair_available);
 sg_sched_choice sg_product_default(bool pair_available);
 void sg_product_features(const ProductWork& w, const sg_sched_choice& ch, int num_sms, float* f);
 
+// The fusion boundaries: candidate 0 the fused plan (kernels, 1), candidate
+// 1 one kernel per queued call (kernels, 0)
+std::vector<sg_sched_choice> sg_fusion_candidates(const FusionWork& w);
+void sg_fusion_features(const FusionWork& w, int cand, float* f);
+// the autotuner takes the unfused plan only when it measured this much faster
+constexpr double kFusionMargin = 0.97;
+
 // One timing record: family, features, microseconds, and log(us / us of the
 // plain table's choice on the same workload) when the record comes from a
 // sweep of every candidate (NaN otherwise).
@@ -83,9 +98,11 @@ constexpr float kLearnedMargin = 0.02f;
 int sg_sched_learned_index(sg_ctx* c, int family, const std::vector<float>& X, int def,
                            std::vector<float>* pred);
 
-// A workload's autotuned choice: the candidate index, or -1 when none yet
-int sg_sched_tuned(const sg_ctx* c, uint64_t key);
-void sg_sched_set_tuned(sg_ctx* c, int family, uint64_t key, int idx);
+// A workload's autotuned choice: the candidate index (and, when us is not
+// null, the times its sweep measured), or -1 when none yet
+int sg_sched_tuned(const sg_ctx* c, uint64_t key, std::vector<double>* us = nullptr);
+void sg_sched_set_tuned(sg_ctx* c, int family, uint64_t key, int idx,
+                        const std::vector<double>& us = {});
 uint64_t sg_sched_key(int family, std::initializer_list<uint64_t> parts);
 
 // Records a decision for sg_sched_last: the candidates, the measured times
@@ -99,6 +116,7 @@ void sg_sched_note(sg_ctx* c, int family, const std::vector<sg_sched_choice>& ca
 // (sg_sched_force) when it names a candidate; under SG_SCHED_LEARNED with
 // a trained model the learned index; otherwise the autotuned index when
 // `key` was swept before, else -1 (the caller sweeps when it can, or takes
-// `def`).  *pred receives the model's predictions when there is a model.
+// `def`).  *pred receives the model's predictions when there is a model,
+// *us an autotuned choice's measured times.
 int sg_sched_lookup(sg_ctx* c, int family, uint64_t key, const std::vector<float>& X, int def,
-                    int* learned, std::vector<float>* pred);
+                    int* learned, std::vector<float>* pred, std::vector<double>* us);

@@ -36,7 +36,7 @@ SG_PRE, SG_POST = 0, 1
 SG_CONTRACTS_OFF, SG_CONTRACTS_PRE, SG_CONTRACTS_PRE_POST, SG_CONTRACTS_FULL = range(4)
 SG_FUSE_OFF, SG_FUSE_ON = 0, 1
 SG_SCHED_AUTOTUNE, SG_SCHED_LEARNED = 0, 1
-SG_SCHED_BATCH, SG_SCHED_STREAM, SG_SCHED_FILTER, SG_SCHED_PRODUCT = 0, 1, 2, 3
+SG_SCHED_BATCH, SG_SCHED_STREAM, SG_SCHED_FILTER, SG_SCHED_PRODUCT, SG_SCHED_FUSION = 0, 1, 2, 3, 4
 
 SG_MAX_EXPR_OPS = 24
 OPCODES = {

@@ -1,7 +1,7 @@
 """Regret study of the schedule chooser's decision families.
 
-For the stream pass's launch shape, the filter's tile and the product's tile
-form (sg_sched_family), sweeps of every candidate on training workloads fill
+For the stream pass's launch shape, the filter's tile, the product's tile
+form and the fusion boundaries (sg_sched_family), sweeps of every candidate on training workloads fill
 the context's timing log; sg_sched_train fits each family's 2x64 cost model
 to it; then, on held-out workloads drawn from the same distribution with
 another seed, the learned choice (predicted before the workload is measured)
@@ -20,6 +20,10 @@ Workloads (seeded, synthetic; uniform binary32 data in [-1, 1)):
            20% and 95% kept) over n elements, u uniform in [11, 27]
   product  C = A B in bf16 or fp16 with M, N, K each drawn from
            {128, 192, 256, 384, 512, 640, 768, 1024, 1536, 2048, 3072, 4096}
+  fusion   one of three chains whose intermediates no handle keeps -- a + b
+           summed; (2x + 1)^2 summed; a * b range-checked and summed -- over
+           n elements, u uniform in [10, 27]: fused, one kernel; unfused, one
+           kernel per call
 
     python -m paper_1410_6685_gb300.sched_study [--train T] [--heldout H]
 """
@@ -46,6 +50,8 @@ def draw(family, count, seed):
     for _ in range(count):
         if family == "stream":
             out.append((int(g.integers(STREAM_CHAINS)), int(2.0 ** g.uniform(10, 27))))
+        elif family == "fusion":
+            out.append((4 + int(g.integers(3)), int(2.0 ** g.uniform(10, 27))))
         elif family == "filter":
             out.append((int(g.integers(len(FILTER_PREDS))), int(2.0 ** g.uniform(11, 27))))
         else:
@@ -96,14 +102,39 @@ class Runner:
             f = sg.sg_for_all(ctx, [("x", 0), ("c", -2.0), ("gt",)], [a])
             sg.sg_scalar_get(ctx, f)
             sg.sg_scalar_release(f)
-        else:
+        elif chain == 3:
             y = sg.sg_mapn(ctx, [("x", 0), ("x", 1), ("mul",), ("x", 2), ("add",)], [a, b, c])
             s = sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, y)
             sg.sg_scalar_get(ctx, s)
             sg.sg_scalar_release(s)
             rel.append(y)
+        else:
+            # the fusion family's chains: intermediates released before the
+            # flush, so the fused plan stores nothing
+            if chain == 4:
+                z = sg.sg_zip(ctx, [("x", 0), ("x", 1), ("add",)], a, b)
+                outs = [sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, z)]
+                mids = [z]
+            elif chain == 5:
+                y1 = sg.sg_map(ctx, [("x", 0), ("c", 2.0), ("mul",), ("c", 1.0), ("add",)], a)
+                y2 = sg.sg_map(ctx, [("x", 0), ("x", 0), ("mul",)], y1)
+                outs = [sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, y2)]
+                mids = [y1, y2]
+            else:
+                z = sg.sg_zip(ctx, [("x", 0), ("x", 1), ("mul",)], a, b)
+                outs = [sg.sg_for_all(ctx, [("x", 0), ("c", -2.0), ("gt",)], [z]),
+                        sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, z)]
+                mids = [z]
+            for v in mids:
+                sg.sg_vector_release(v)
+            for o in outs:
+                sg.sg_scalar_get(ctx, o)
+                sg.sg_scalar_release(o)
         for v in rel:
             sg.sg_vector_release(v)
+
+    def fusion(self, chain, n):
+        self.stream(chain, n)
 
     def filter(self, pred, n):
         sg, ctx = self.sg, self.ctx
@@ -127,7 +158,7 @@ class Runner:
         getattr(self, family)(*w)
 
 
-FAMILY_ID = {"stream": 1, "filter": 2, "product": 3}
+FAMILY_ID = {"stream": 1, "filter": 2, "product": 3, "fusion": 4}
 
 
 def sweep(runner, family, w):
@@ -147,7 +178,7 @@ def sweep(runner, family, w):
     return (ts[0] + ts[1]) / 2, rep.default_index, rep.learned_index, rep
 
 
-def study(sg, ctx, torch, families=("stream", "filter", "product"), train=48, heldout=24,
+def study(sg, ctx, torch, families=("stream", "filter", "product", "fusion"), train=48, heldout=24,
           seed=5, epochs=400):
     """Trains on `train` swept workloads per family and reports the held-out
     regrets.  The context's scheduler is set to SG_SCHED_AUTOTUNE."""
@@ -188,7 +219,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=48)
     ap.add_argument("--heldout", type=int, default=24)
-    ap.add_argument("--families", default="stream,filter,product")
+    ap.add_argument("--families", default="stream,filter,product,fusion")
     ap.add_argument("--dump", default="", help="write every held-out sweep to this JSON file")
     a = ap.parse_args(argv)
     import torch

@@ -246,7 +246,8 @@ def test_lookback_switch_arguments(sg, pctx):
 def test_schedule_family_arguments(sg, pctx):
     """The schedule chooser's per-family calls: nothing decided yet, bad
     families and indices refused, forgetting and forcing accepted."""
-    for fam in (sg.SG_SCHED_BATCH, sg.SG_SCHED_STREAM, sg.SG_SCHED_FILTER, sg.SG_SCHED_PRODUCT):
+    for fam in (sg.SG_SCHED_BATCH, sg.SG_SCHED_STREAM, sg.SG_SCHED_FILTER, sg.SG_SCHED_PRODUCT,
+                sg.SG_SCHED_FUSION):
         with pytest.raises(sg.SgError) as e:
             sg.sg_sched_last(pctx, fam)
         assert e.value.status == sg.SG_ERR_INVALID_ARG
@@ -254,12 +255,12 @@ def test_schedule_family_arguments(sg, pctx):
         sg.sg_sched_force(pctx, fam, 0)
         sg.sg_sched_force(pctx, fam, -1)
     sg.sg_sched_forget(pctx, -1)
-    for bad in ((4, 0), (-1, 0), (0, -2), (0, sg.SG_SCHED_MAX_CANDIDATES)):
+    for bad in ((5, 0), (-1, 0), (0, -2), (0, sg.SG_SCHED_MAX_CANDIDATES)):
         with pytest.raises(sg.SgError) as e:
             sg.sg_sched_force(pctx, *bad)
         assert e.value.status == sg.SG_ERR_INVALID_ARG
     with pytest.raises(sg.SgError):
-        sg.sg_sched_forget(pctx, 4)
+        sg.sg_sched_forget(pctx, 5)
     # an empty log trains nothing
     X, y, fam = sg.sg_sched_log(pctx)
     assert X.shape == (0, 12) and y.shape == (0,) and fam.shape == (0,)

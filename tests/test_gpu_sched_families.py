@@ -1,5 +1,6 @@
 """The schedule chooser's decision families beyond the batched launch: the
-stream pass's launch shape, the filter's tile and the product's tile form.
+stream pass's launch shape, the filter's tile, the product's tile form and
+the fusion boundaries.
 
 Every candidate must give the oracle's results (element-wise and filter
 outputs bit-exact; sums within 1e-5; products within the normwise bound of
@@ -14,7 +15,7 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-STREAM, FILTER, PRODUCT = 1, 2, 3
+STREAM, FILTER, PRODUCT, FUSION = 1, 2, 3, 4
 
 
 @pytest.fixture(scope="module")
@@ -184,10 +185,87 @@ def test_product_both_forms(env, shape, prec):
     sg.sg_matrix_release(mc)
 
 
+@pytest.mark.parametrize("n", [3, 4099, (1 << 22) + 5])
+def test_fusion_boundaries_both_plans_exact(env, n):
+    """a * b range-checked and summed, the product released before the flush:
+    the fused plan is one kernel, the unfused one a kernel per call (three);
+    both give the oracle's results, and a sweep measures both."""
+    sg, ctx, torch = env
+    g = np.random.default_rng(n + 5)
+    a = g.uniform(-1, 1, n).astype(np.float32)
+    b = g.uniform(-1, 1, n).astype(np.float32)
+    ta, va = dev(env, a)
+    tb, vb = dev(env, b)
+    prod = oracle.map([("x", 0), ("x", 1), ("mul",)], a, b)
+    want_sum = oracle.sum(prod)
+    bound = 1e-5 * np.abs(prod.astype(np.float64)).sum() + 1e-30
+
+    def run():
+        z = sg.sg_zip(ctx, [("x", 0), ("x", 1), ("mul",)], va, vb)
+        f = sg.sg_for_all(ctx, [("x", 0), ("c", -2.0), ("gt",)], [z])
+        s = sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, z)
+        sg.sg_vector_release(z)
+        k0 = sg.sg_kernel_count(ctx)
+        ok = sg.sg_scalar_get(ctx, f)
+        got = sg.sg_scalar_get(ctx, s)
+        k = sg.sg_kernel_count(ctx) - k0
+        sg.sg_scalar_release(f)
+        sg.sg_scalar_release(s)
+        assert ok == 1.0 and abs(got - want_sum) <= bound
+        return k
+
+    sg.sg_sched_forget(ctx, -1)
+    run()
+    rep = sg.sg_sched_last(ctx, FUSION)
+    assert rep.ncand == 2 and rep.default_index == 0
+    assert (rep.chunk[0], rep.ctas_per_sm[0], rep.chunk[1], rep.ctas_per_sm[1]) == (1, 1, 3, 0)
+    assert rep.measured_us[0] > 0 and rep.measured_us[1] > 0
+    fused_wins = rep.measured_us[1] >= 0.97 * rep.measured_us[0]
+    assert rep.chosen_index == (0 if fused_wins else 1)
+    for i, kernels in ((0, 1), (1, 3)):
+        sg.sg_sched_force(ctx, FUSION, i)
+        try:
+            assert run() == kernels
+            assert sg.sg_sched_last(ctx, FUSION).chosen_index == i
+        finally:
+            sg.sg_sched_force(ctx, FUSION, -1)
+
+
+def test_fusion_not_decided_when_off_or_in_place(env):
+    sg, ctx, torch = env
+    n = 1 << 16
+    x = np.random.default_rng(1).uniform(-1, 1, n).astype(np.float32)
+    tx, vx = dev(env, x)
+    # in place: the flush is not measured (a re-run would apply it twice)
+    sg.sg_sched_forget(ctx, -1)
+    sg.sg_for_each(ctx, MAP, vx)
+    s = sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, vx)
+    got = sg.sg_scalar_get(ctx, s)
+    want = oracle.map(MAP, x)
+    assert np.array_equal(bits(sg.sg_vector_read(ctx, vx, np.empty(n, np.float32))), bits(want))
+    assert abs(got - oracle.sum(want)) <= 1e-5 * np.abs(want.astype(np.float64)).sum()
+    sg.sg_scalar_release(s)
+    # fusion off: one kernel per call, nothing decided
+    sg.sg_set_fusion(ctx, sg.SG_FUSE_OFF)
+    try:
+        k0 = sg.sg_kernel_count(ctx)
+        z = sg.sg_zip(ctx, [("x", 0), ("x", 0), ("mul",)], vx, vx)
+        s = sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, z)
+        sg.sg_vector_release(z)
+        sg.sg_scalar_get(ctx, s)
+        assert sg.sg_kernel_count(ctx) - k0 >= 2
+        sg.sg_scalar_release(s)
+    finally:
+        sg.sg_set_fusion(ctx, sg.SG_FUSE_ON)
+
+
 def test_learned_families_against_the_plain_table(env):
     """Held-out regret of the learned choice and of the plain table, per
     family (sched_study: trained on 40 swept workloads per family, 16
-    held-out ones, each timed by two independent sweeps)."""
+    held-out ones, each timed by two independent sweeps).  The learned
+    choice beats the plain table where the plain table can be beaten (launch
+    shape, filter tile, product tile form) and does not lose to it on the
+    fusion boundaries."""
     sg, ctx, torch = env
     from paper_1410_6685_gb300 import sched_study
     sctx = sg.sg_init(0, torch.cuda.current_stream().cuda_stream)
@@ -200,3 +278,7 @@ def test_learned_families_against_the_plain_table(env):
         r = res[fam]
         assert r["learned_mean_regret"] < r["plain_mean_regret"], (fam, r)
         assert r["learned_median_regret"] <= r["plain_median_regret"], (fam, r)
+    # the fused plan is the plain choice and mostly the fastest: the learned
+    # choice must not lose to it
+    r = res["fusion"]
+    assert r["learned_mean_regret"] <= r["plain_mean_regret"], r
