@@ -261,7 +261,7 @@ def test_fusion_not_decided_when_off_or_in_place(env):
 
 def test_learned_families_against_the_plain_table(env):
     """Held-out regret of the learned choice and of the plain table, per
-    family (sched_study: trained on 40 swept workloads per family, 16
+    family (sched_study: trained on 64 swept workloads per family, 24
     held-out ones, each timed by two independent sweeps).  The learned
     choice beats the plain table where the plain table can be beaten (launch
     shape, filter tile, product tile form) and does not lose to it on the
@@ -270,7 +270,7 @@ def test_learned_families_against_the_plain_table(env):
     from paper_1410_6685_gb300 import sched_study
     sctx = sg.sg_init(0, torch.cuda.current_stream().cuda_stream)
     try:
-        res = sched_study.study(sg, sctx, torch, train=40, heldout=16)
+        res = sched_study.study(sg, sctx, torch, train=64, heldout=24)
     finally:
         sg.sg_destroy(sctx)
     print(res)
