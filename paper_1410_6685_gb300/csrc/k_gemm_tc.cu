@@ -25,6 +25,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "sg_frv.cuh"
 #include "sg_linalg_kernels.h"
@@ -1045,18 +1046,26 @@ cudaError_t time_gemm_forms(const float* A, int lda, const float* B, int ldb, fl
   cudaError_t e = cudaEventCreate(&ev[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
   for (int f = 0; f < nforms && e == cudaSuccess; ++f) {
+    // a warm-up, then the better of two timed runs; a product shorter than
+    // 16 us is repeated within each run (the events resolve about 0.5 us)
     double best = 1e300;
-    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {   // a warm-up, then two timed
+    int reps = 1;
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
       e = cudaEventRecord(ev[0], s);
-      if (e == cudaSuccess)
+      for (int k = 0; k < reps && e == cudaSuccess; ++k) {
         e = launch_product(a16, bt16, Kp, fp16, C, ldc, M, N, false, err, nullptr, nullptr, -1,
                            -1, 0.0f, s, forms[f]);
+        *kernels += 1;
+      }
       if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
       if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
       float ms = 0.0f;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-      if (e == cudaSuccess && r > 0) best = std::min(best, 1000.0 * ms);
-      *kernels += 1;
+      const double t = 1000.0 * ms / reps;
+      if (r == 0)
+        reps = t >= 16.0 ? 1 : (int)std::min(64.0, std::ceil(16.0 / std::max(t, 0.25)));
+      else if (e == cudaSuccess)
+        best = std::min(best, t);
     }
     us[f] = best;
   }

@@ -32,8 +32,9 @@ cudaError_t launch_gemm_tc(const float* A, int lda, const float* B, int ldb, flo
                            int inj_col = -1, float inj_delta = 0.0f, int form = 0);
 bool gemm_pair_available();
 // Casts the operands once, then times the product C = A B in each of `forms`
-// (a warm-up, then the better of two runs, CUDA events on s; waits for s):
-// us[f] microseconds.  C holds the last form's result.
+// (a warm-up, then the better of two runs, CUDA events on s, a product
+// under 16 us repeated within a run; waits for s): us[f] microseconds.  C
+// holds the last form's result.
 cudaError_t time_gemm_forms(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
                             int M, int N, int K, bool fp16, void* scratch, cudaStream_t s,
                             const int* forms, int nforms, double* us, int64_t* kernels);

@@ -585,21 +585,28 @@ void record_violation(sg_ctx* c, Node* n, int64_t first, double observed, bool* 
 }
 
 // One launch's time: a warm-up, then the better of two runs (CUDA events on
-// the context's stream; waits for it).
+// the context's stream; waits for it).  A launch shorter than 16 us is
+// repeated within each timed run (up to 64 times) and the run divided: the
+// events resolve about half a microsecond, too coarse for one short launch.
 template <class F>
 cudaError_t time_launch(sg_ctx* c, F&& launch, double* us) {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   cudaError_t e = cudaEventCreate(&ev[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
   double best = 1e300;
+  int reps = 1;
   for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
     e = cudaEventRecord(ev[0], c->stream);
-    if (e == cudaSuccess) e = launch();
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch();
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
     float ms = 0.0f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-    if (e == cudaSuccess && r > 0) best = std::min(best, 1000.0 * ms);
+    const double t = 1000.0 * ms / reps;
+    if (r == 0)
+      reps = t >= 16.0 ? 1 : (int)std::min(64.0, std::ceil(16.0 / std::max(t, 0.25)));
+    else
+      best = std::min(best, t);
   }
   for (cudaEvent_t v : ev)
     if (v) cudaEventDestroy(v);
@@ -681,9 +688,12 @@ cudaError_t launch_stream_scheduled(sg_ctx* c, cudaKernel_t jk, const sgk::Strea
       us.assign(cand.size(), 0.0);
       for (size_t i = 0; i < cand.size() && e == cudaSuccess; ++i) {
         const int g = sg_stream_grid(w.n, cand[i], c->num_sms), b = (int)cand[i].chunk;
-        e = time_launch(c, [&]() { return sgk::launch_jit_stream(jk, a, g, b, c->stream, nullptr); },
+        e = time_launch(c,
+                        [&]() {
+                          c->kernels += 1;
+                          return sgk::launch_jit_stream(jk, a, g, b, c->stream, nullptr);
+                        },
                         &us[i]);
-        c->kernels += 3;
       }
       if (e != cudaSuccess) return e;
       idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
