@@ -24,7 +24,11 @@ __global__ void __launch_bounds__(256) k_stream(const StreamArgs a) {
   constexpr int NX = NIN > 0 ? NIN : 1;
   Acc acc;
   acc_init(acc);
-  const long long n = a.n;
+  long long n = a.n;
+  if (a.count) {
+    const long long c = *a.count;
+    n = c < 0 ? 0 : c < n ? c : n;
+  }
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long tail_start = 0;

@@ -88,6 +88,9 @@ struct StreamArgs {
   unsigned int* counter; // last-block-done counter; zero before and after
   PassResult* result;    // final record (scratch or caller memory)
   int vec4;              // every pointer 16-byte aligned: use 128-bit accesses
+  // when set, the pass covers min(n, *count) elements: a compacted filter's
+  // count, which the filter kernel earlier in the stream wrote on the device
+  const long long* count;
 };
 
 // Stack check of a postfix expression over `nin` input slots (the one

@@ -72,7 +72,8 @@ struct PassResult {
 };
 struct JitArgs {
   const float* in[4]; float* out[4]; long long n; float cst[48];
-  PassResult* partials; unsigned* counter; PassResult* result; int vec4; int pad;
+  PassResult* partials; unsigned* counter; PassResult* result; const long long* count;
+  int vec4; int pad;
 };
 #define SG_NONE 0x7fffffffffffffffLL
 __device__ __forceinline__ bool sg_nan(float v) { return v != v; }
@@ -149,7 +150,11 @@ const char* kTemplateKernel = R"SGJIT(
 extern "C" __global__ void __launch_bounds__(256) sg_fused(const JitArgs a) {
   Acc acc;
   acc_init(acc);
-  const long long n = a.n;
+  long long n = a.n;
+  if (a.count) {
+    const long long c = *a.count;
+    n = c < 0 ? 0 : c < n ? c : n;
+  }
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long tail = 0;
@@ -886,6 +891,7 @@ cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int
   a.partials = s.partials;
   a.counter = s.counter;
   a.result = s.result;
+  a.count = s.count;
   a.vec4 = s.vec4;
   void* args[] = {&a};
   prof_begin(prof, "stream_jit", st);

@@ -16,12 +16,13 @@ struct JitArgs {
   PassResult* partials;
   unsigned* counter;
   PassResult* result;
+  const long long* count;   // StreamArgs::count
   int vec4;
   int pad;
 };
 static_assert(kMaxIn == 4 && kMaxOut == 4 && kMaxProg == 48 && kMaxPred == 4,
               "the kernel template hard-codes these sizes");
-static_assert(sizeof(JitArgs) == 296, "JitArgs layout changed: update the template");
+static_assert(sizeof(JitArgs) == 304, "JitArgs layout changed: update the template");
 
 // Kernel argument block of the specialised batch kernel (k_batch.cu holds the
 // interpreting twin); repeated verbatim in the template source.

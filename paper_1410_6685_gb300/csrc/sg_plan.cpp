@@ -74,6 +74,9 @@ struct Pass {
   Node* chk_perm = nullptr;
   Node* chk_frv = nullptr;    // MATMUL: built-in Freivalds check folded in
   Node* vtrans = nullptr;     // MATVEC y = A x with A the pending transpose of vtrans->in[0]
+  // STREAM over a compacted filter's result of the same flush: that filter,
+  // whose count (on the device) bounds the pass
+  Node* count_src = nullptr;
 };
 
 bool is_f32_stream_node(const Node* n) {
@@ -169,6 +172,18 @@ struct Planner {
       if (u->kind != NK::MATVEC || u->left || u->in[0].get() != v || u->in[1].get() == v)
         return false;
     return true;
+  }
+
+  // the filter whose compacted result (count not yet known) node n reads,
+  // when that filter runs as its own pass earlier in this plan
+  Node* counted_source(const Node* n) const {
+    for (int k = 0; k < n->nin; ++k) {
+      const Value* v = n->in[k].get();
+      if (!v || v->count_known || !v->producer || v->producer->kind != NK::FILTER) continue;
+      for (const Pass& Q : passes)
+        if (Q.kind == PK::FILTER && Q.main == v->producer) return v->producer;
+    }
+    return nullptr;
   }
 
   int slot_of(Pass& P, Value* v, bool add) {
@@ -302,11 +317,16 @@ struct Planner {
       const bool streamable = is_f32_stream_node(n) || (n->kind == NK::FILTER && maskable(n));
       if (streamable) {
         const int64_t len = node_len(n);
-        if (open && fuse && passes.back().n == len && try_add(passes.back(), n))
+        // a reduction over a compacted filter's result of this flush covers
+        // the filter's count, known only on the device: a pass of its own
+        Node* csrc = counted_source(n);
+        if (!csrc && open && fuse && passes.back().n == len && !passes.back().count_src &&
+            try_add(passes.back(), n))
           continue;
         Pass P;
         P.kind = PK::STREAM;
         P.n = len;
+        P.count_src = csrc;
         if (!try_add(P, n)) {
           // cannot fail for a lone node with loaded inputs unless the node
           // consumes a masked value produced in a closed pass
@@ -317,7 +337,7 @@ struct Planner {
           try_add(P, n);
         }
         passes.push_back(std::move(P));
-        open = true;
+        open = csrc == nullptr;
         continue;
       }
       open = false;
@@ -423,6 +443,7 @@ struct Planner {
       Pass E;
       E.kind = PK::STREAM;
       E.n = P.n;
+      E.count_src = P.count_src;
       E.nodes = P.nodes;
       for (Node* n : P.nodes) {
         switch (n->kind) {
@@ -877,6 +898,10 @@ sg_status run_flush(sg_ctx* c, bool fuse, bool commit, double* us) {
         }
         if (status) break;
         a.n = P.n;
+        if (P.count_src)
+          for (size_t q = 0; q < i; ++q)
+            if (passes[q].kind == PK::FILTER && passes[q].main == P.count_src)
+              a.count = reinterpret_cast<const long long*>(dres + q * sgk::kResultBytes);
         a.prog.nops = (int)P.prog.size();
         std::vector<uint8_t> before;
         int md = 0;
@@ -1338,9 +1363,9 @@ sg_status sg_describe_pending(sg_ctx* c, std::string* out) {
     switch (P.kind) {
       case PK::STREAM:
         if (P.prog.empty()) continue;
-        snprintf(buf, sizeof buf, "stream n=%lld in=%zu store=%zu pred=%zu reduce=%d ops=%zu\n",
-                 (long long)P.n, P.inputs.size(), P.stores.size(), P.preds.size(),
-                 P.reduce_of ? 1 : 0, P.prog.size());
+        snprintf(buf, sizeof buf, "stream n=%lld%s in=%zu store=%zu pred=%zu reduce=%d ops=%zu\n",
+                 (long long)P.n, P.count_src ? " (the filter's count)" : "", P.inputs.size(),
+                 P.stores.size(), P.preds.size(), P.reduce_of ? 1 : 0, P.prog.size());
         break;
       case PK::FILTER: snprintf(buf, sizeof buf, "filter n=%lld\n", (long long)P.n); break;
       case PK::SORT:

@@ -121,12 +121,17 @@ def test_filter_then_sum_becomes_masked_reduce(sg, pctx):
 
 
 def test_filter_kept_by_handle_is_compacted(sg, pctx):
+    """A reduction of a kept filter result runs after the compaction, over
+    the filter's count (read on the device), in a pass of its own."""
     x = vec(sg, pctx, 10000)
     k = sg.sg_filter(pctx, [("x", 0), ("c", 0.0), ("gt",)], x)
     s = sg.sg_reduce(pctx, sg.SG_REDUCE_SUM, k)
+    s2 = sg.sg_reduce(pctx, sg.SG_REDUCE_MAX, k)
     L = lines(sg, pctx)
-    assert L[0].startswith("filter n=10000") and L[1].startswith("stream"), L
+    assert L[0].startswith("filter n=10000") and len(L) == 3, L
+    assert all(l.startswith("stream n=10000 (the filter's count)") for l in L[1:]), L
     sg.sg_scalar_release(s)
+    sg.sg_scalar_release(s2)
 
 
 def test_contract_mode_off_plans_no_check(sg, pctx):

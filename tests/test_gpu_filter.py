@@ -73,6 +73,39 @@ def test_filter_large_full_size(env):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("n", [5, 300_007, (1 << 22) + 3])
+def test_reductions_of_a_kept_filter_result(env, n):
+    """Reductions queued over a filter's result that a handle keeps (so it is
+    compacted, not masked) cover the filter's count, which only the device
+    knows when they are planned: count, sum and max against the oracle, after
+    a flush that leaves large stale values in the allocator's memory."""
+    sg, ctx, torch = env
+    big = torch.full((n,), 1000.0, device="cuda")
+    vb = sg.sg_vector_wrap(ctx, sg.SG_F32, n, big.data_ptr())
+    kb = sg.sg_filter(ctx, [("x", 0), ("c", 0.0), ("gt",)], vb)
+    sg.sg_flush(ctx)
+    sg.sg_vector_release(kb)
+    x = inputs.uniform_pm1(inputs.rng(n % 97), n)
+    t = torch.from_numpy(x).cuda()
+    v = sg.sg_vector_wrap(ctx, sg.SG_F32, n, t.data_ptr())
+    pred = [("x", 0), ("c", 0.5), ("gt",)]
+    k = sg.sg_filter(ctx, pred, v)
+    rc = sg.sg_reduce(ctx, sg.SG_REDUCE_COUNT, k)
+    rs = sg.sg_reduce(ctx, sg.SG_REDUCE_SUM, k)
+    rm = sg.sg_reduce(ctx, sg.SG_REDUCE_MAX, k)
+    kept = oracle.filter(pred, x)
+    assert sg.sg_scalar_get(ctx, rc) == len(kept)
+    assert sg.sg_vector_count(ctx, k) == len(kept)
+    s = sg.sg_scalar_get(ctx, rs)
+    assert abs(s - oracle.sum(kept)) <= 1e-5 * np.abs(kept.astype(np.float64)).sum() + 1e-30
+    m = sg.sg_scalar_get(ctx, rm)
+    assert (np.isnan(m) and len(kept) == 0) or m == oracle.max(kept)
+    for h in (rc, rs, rm):
+        sg.sg_scalar_release(h)
+    for h in (k, v, vb):
+        sg.sg_vector_release(h)
+
+
 def test_filter_then_chain(env):
     """A filtered collection feeds further deferred operations."""
     sg, ctx, torch = env
