@@ -607,7 +607,8 @@ typedef struct {
   int32_t best_index;     /* fastest measured (the autotuner's choice), -1 when
                              nothing was measured                              */
   int32_t default_index;  /* the plain table's choice                          */
-  int32_t learned_index;  /* the model's choice, -1 when no model is trained   */
+  int32_t learned_index;  /* the model's choice, -1 when no model is trained
+                             (for an autotuned choice: when it was measured)  */
   int64_t chunk[SG_SCHED_MAX_CANDIDATES];
   int32_t ctas_per_sm[SG_SCHED_MAX_CANDIDATES];
   double measured_us[SG_SCHED_MAX_CANDIDATES];   /* 0: not measured         */

@@ -320,7 +320,8 @@ extern "C" sg_status sg_batch_run(sg_ctx* c, const sg_chain* ch, const float* da
   if (idx < 0) {
     st = autotune(c, j, cand, X, def, &times, &idx);
     if (st) return st;
-    sg_sched_set_tuned(c, SG_SCHED_BATCH, key, idx, times);
+    learned = sg_sched_learned_index(c, SG_SCHED_BATCH, X, def, &pred);
+    sg_sched_set_tuned(c, SG_SCHED_BATCH, key, idx, times, learned);
   }
   sg_sched_note(c, SG_SCHED_BATCH, cand, times, def, learned, idx, pred);
   bool viol = false;

@@ -58,8 +58,8 @@ int product_form(sg_ctx* c, int M, int N, int K, bool fp16, const float* a, cons
       if (*e != cudaSuccess) return 0;
       idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
       sg_sched_log_sweep(c, SG_SCHED_PRODUCT, X, us, def);
-      sg_sched_set_tuned(c, SG_SCHED_PRODUCT, key, idx, us);
       learned = sg_sched_learned_index(c, SG_SCHED_PRODUCT, X, def, &pred);
+      sg_sched_set_tuned(c, SG_SCHED_PRODUCT, key, idx, us, learned);
     }
   }
   sg_sched_note(c, SG_SCHED_PRODUCT, cand, us, def, learned, idx, pred);

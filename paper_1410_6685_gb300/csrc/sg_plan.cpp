@@ -719,8 +719,8 @@ cudaError_t launch_stream_scheduled(sg_ctx* c, cudaKernel_t jk, const sgk::Strea
       if (e != cudaSuccess) return e;
       idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
       sg_sched_log_sweep(c, SG_SCHED_STREAM, X, us, def);
-      sg_sched_set_tuned(c, SG_SCHED_STREAM, key, idx, us);
       learned = sg_sched_learned_index(c, SG_SCHED_STREAM, X, def, &pred);
+      sg_sched_set_tuned(c, SG_SCHED_STREAM, key, idx, us, learned);
     }
   }
   sg_sched_note(c, SG_SCHED_STREAM, cand, us, def, learned, idx, pred);
@@ -774,8 +774,8 @@ cudaError_t launch_filter_scheduled(sg_ctx* c, const sgk::Prog& pr, const float*
       if (e != cudaSuccess) return e;
       idx = (int)(std::min_element(us.begin(), us.end()) - us.begin());
       sg_sched_log_sweep(c, SG_SCHED_FILTER, X, us, def);
-      sg_sched_set_tuned(c, SG_SCHED_FILTER, key, idx, us);
       learned = sg_sched_learned_index(c, SG_SCHED_FILTER, X, def, &pred);
+      sg_sched_set_tuned(c, SG_SCHED_FILTER, key, idx, us, learned);
     }
   }
   cudaKernel_t k = kernel(idx);
@@ -1339,8 +1339,8 @@ bool choose_fusion(sg_ctx* c) {
     }
     idx = us[1] < kFusionMargin * us[0] ? 1 : 0;
     sg_sched_log_sweep(c, SG_SCHED_FUSION, X, us, 0);
-    sg_sched_set_tuned(c, SG_SCHED_FUSION, key, idx, us);
     learned = sg_sched_learned_index(c, SG_SCHED_FUSION, X, 0, &pred);
+    sg_sched_set_tuned(c, SG_SCHED_FUSION, key, idx, us, learned);
   }
   sg_sched_note(c, SG_SCHED_FUSION, cand, us, 0, learned, idx, pred);
   return idx == 0;

@@ -139,6 +139,7 @@ struct SchedState {
     uint64_t key;
     int idx, family;
     std::vector<double> us;   // the sweep's times, for sg_sched_last
+    int learned;              // the model's choice when the sweep ran, or -1
   };
   std::vector<Tuned> tuned;
   // learned choices under the current models (cleared when they are trained)

@@ -233,24 +233,26 @@ uint64_t sg_sched_key(int family, std::initializer_list<uint64_t> parts) {
   return h;
 }
 
-int sg_sched_tuned(const sg_ctx* c, uint64_t key, std::vector<double>* us) {
+int sg_sched_tuned(const sg_ctx* c, uint64_t key, std::vector<double>* us, int* learned) {
   for (auto& t : c->schedst.tuned)
     if (t.key == key) {
       if (us) *us = t.us;
+      if (learned) *learned = t.learned;
       return t.idx;
     }
   return -1;
 }
 
 void sg_sched_set_tuned(sg_ctx* c, int family, uint64_t key, int idx,
-                        const std::vector<double>& us) {
+                        const std::vector<double>& us, int learned) {
   for (auto& t : c->schedst.tuned)
     if (t.key == key) {
       t.idx = idx;
       t.us = us;
+      t.learned = learned;
       return;
     }
-  c->schedst.tuned.push_back({key, idx, family, us});
+  c->schedst.tuned.push_back({key, idx, family, us, learned});
 }
 
 void sg_sched_note(sg_ctx* c, int family, const std::vector<sg_sched_choice>& cand,
@@ -301,7 +303,7 @@ int sg_sched_lookup(sg_ctx* c, int family, uint64_t key, const std::vector<float
       return *learned;
     }
   }
-  return sg_sched_tuned(c, key, us);
+  return sg_sched_tuned(c, key, us, learned);
 }
 
 // ---------------------------------------------------------------------------

@@ -100,9 +100,11 @@ int sg_sched_learned_index(sg_ctx* c, int family, const std::vector<float>& X, i
 
 // A workload's autotuned choice: the candidate index (and, when us is not
 // null, the times its sweep measured), or -1 when none yet
-int sg_sched_tuned(const sg_ctx* c, uint64_t key, std::vector<double>* us = nullptr);
+int sg_sched_tuned(const sg_ctx* c, uint64_t key, std::vector<double>* us = nullptr,
+                   int* learned = nullptr);
+// learned: the model's choice for the workload when it was swept (-1: none)
 void sg_sched_set_tuned(sg_ctx* c, int family, uint64_t key, int idx,
-                        const std::vector<double>& us = {});
+                        const std::vector<double>& us = {}, int learned = -1);
 uint64_t sg_sched_key(int family, std::initializer_list<uint64_t> parts);
 
 // Records a decision for sg_sched_last: the candidates, the measured times
@@ -117,6 +119,7 @@ void sg_sched_note(sg_ctx* c, int family, const std::vector<sg_sched_choice>& ca
 // a trained model the learned index; otherwise the autotuned index when
 // `key` was swept before, else -1 (the caller sweeps when it can, or takes
 // `def`).  *pred receives the model's predictions when there is a model,
-// *us an autotuned choice's measured times.
+// *us and *learned an autotuned choice's measured times and the model's
+// choice when it was measured.
 int sg_sched_lookup(sg_ctx* c, int family, uint64_t key, const std::vector<float>& X, int def,
                     int* learned, std::vector<float>* pred, std::vector<double>* us);

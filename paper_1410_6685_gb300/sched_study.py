@@ -168,6 +168,9 @@ def sweep(runner, family, w):
     fid = FAMILY_ID[family]
     ts = []
     rep = None
+    # a first run settles the other families' decisions in the same flush
+    # (the fusion boundaries of a stream chain are measured on first sight)
+    runner.run(family, w)
     for k in range(2):
         sg.sg_sched_forget(ctx, fid)
         runner.run(family, w)
