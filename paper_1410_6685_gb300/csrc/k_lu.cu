@@ -851,11 +851,11 @@ __global__ void __launch_bounds__(2 * kTB) k_lu_diag_inv(const float* __restrict
 
 // Triangular solve by 64-row blocks.  LOWER: unit lower L, blocks in
 // increasing order; else upper U with its diagonal, blocks in decreasing
-// order.  Block b's rows form two halves of 32 (warps 0-3 and 4-7, lane =
-// row); the four warps of a half share the block's dependencies in 32-column
-// pieces (warp w takes every fourth, in the order they are solved), each
-// loading its 32x32 piece before waiting, with a bounded spin, for the flag
-// of the 64-row block that piece belongs to.  Warps 0 and 1 then apply the
+// order.  Block b's rows form two halves of 32 (warps 0-3 and 4-7); the four
+// warps of a half share the block's dependencies in 32-column pieces (warp w
+// takes every fourth, in the order they are solved), each loading its 32x32
+// piece, row by row and coalesced (lane = column), before waiting, with a
+// bounded spin, for the flag of the 64-row block that piece belongs to.  Warps 0 and 1 then apply the
 // inverse of the diagonal block (its rows held in registers from the start)
 // to the block's right-hand side and publish the flag with a release store.
 template <bool LOWER>
@@ -874,8 +874,6 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
   const int row0 = b * kTB;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int h = w >> 2, wq = w & 3;
-  const int row = row0 + 32 * h + lane;
-  const float* lrow = LU + (size_t)min(row, n - 1) * n;
   // warps 0 and 1 keep their row of the diagonal block's inverse
   float dg[kTB];
   if (w < 2) {
@@ -883,15 +881,23 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
 #pragma unroll
     for (int j = 0; j < kTB; ++j) dg[j] = irow[j];
   }
-  float acc = 0.0f;
+  // lane = column: a piece's 32 rows are read as 32 coalesced 128-byte rows,
+  // and lane j accumulates column j's terms of every row of the half; one
+  // transposing reduction at the end gives lane r the sum of row r
+  float acc[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) acc[r] = 0.0f;
+  const int rh = row0 + 32 * h;                  // the half's first row
   const int ns = (n + 31) / 32;   // 32-column pieces of the matrix
   const int ndep = LOWER ? 2 * b : ns - 2 * (b + 1);
   for (int q = wq; q < ndep; q += 4) {
     const int sp = LOWER ? q : ns - 1 - q;
     const int cb = sp * 32;
+    const bool colok = cb + lane < n;
     float m[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) m[j] = (row < n && cb + j < n) ? lrow[cb + j] : 0.0f;
+    for (int r = 0; r < 32; ++r)
+      m[r] = (colok && rh + r < n) ? LU[(size_t)(rh + r) * n + cb + lane] : 0.0f;
     if (lane == 0) {
       unsigned spins = 0;
       for (;;) {
@@ -906,11 +912,23 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
       }
     }
     __syncwarp();
-    const float yc = cb + lane < n ? __ldcg(&y[cb + lane]) : 0.0f;
+    const float yc = colok ? __ldcg(&y[cb + lane]) : 0.0f;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc = fmaf(m[j], __shfl_sync(0xffffffffu, yc, j), acc);
+    for (int r = 0; r < 32; ++r) acc[r] = fmaf(m[r], yc, acc[r]);
   }
-  part[w][lane] = acc;
+  // transposing reduction: after the step of width o, a lane keeps the half
+  // of its rows that its bit o selects, added to its partner's
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int r = 0; r < o; ++r) {
+      const float send = up ? acc[r] : acc[r + o];
+      const float keep = up ? acc[r + o] : acc[r];
+      acc[r] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  part[w][lane] = acc[0];
   __syncthreads();
   if (w < 2) {
     const int r = row0 + 32 * w + lane;
