@@ -466,35 +466,27 @@ extern "C" __global__ void __launch_bounds__(256, SG_FMINB) sg_filter(const Filt
   const long long n = a.n;
   unsigned lt;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-  float v[4 * SG_FQ];
-  auto load_tile = [&](unsigned tt, long long& base, int& valid) {
-    base = (long long)tt * SG_FT;
-    valid = (int)(n - base < SG_FT ? n - base : SG_FT);
-    if (valid == SG_FT && (((unsigned long long)(a.x + base)) & 15ull) == 0) {
-#pragma unroll
-      for (int q = 0; q < SG_FQ; ++q) {
-        const float4 f = __ldcs(reinterpret_cast<const float4*>(a.x + base) + q * 256 + tid);
-        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < SG_FQ; ++q)
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          const int li = 4 * (q * 256 + tid) + l;
-          v[4 * q + l] = li < valid ? a.x[base + li] : 0.0f;
-        }
-    }
-  };
-  // the loads of the tile of this CTA's index (usually its ticket as well)
-  // are in flight while the ticket is fetched; another ticket reloads
-  long long base;
-  int valid;
-  load_tile(blockIdx.x, base, valid);
   if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
   __syncthreads();
   const unsigned t = s_tile;
-  if (t != blockIdx.x) load_tile(t, base, valid);
+  const long long base = (long long)t * SG_FT;
+  const int valid = (int)(n - base < SG_FT ? n - base : SG_FT);
+  float v[4 * SG_FQ];
+  if (valid == SG_FT && (((unsigned long long)(a.x + base)) & 15ull) == 0) {
+#pragma unroll
+    for (int q = 0; q < SG_FQ; ++q) {
+      const float4 f = __ldcs(reinterpret_cast<const float4*>(a.x + base) + q * 256 + tid);
+      v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < SG_FQ; ++q)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int li = 4 * (q * 256 + tid) + l;
+        v[4 * q + l] = li < valid ? a.x[base + li] : 0.0f;
+      }
+  }
   // predicate on the thread's 32 items, masked to the valid ones
   unsigned keep = 0, vmask = 0;
 #pragma unroll
