@@ -689,8 +689,9 @@ sg_status sg_mlp_adam(sg_ctx* ctx, float* params, const float* grad, float* m,
  * predicate or a null buffer SG_ERR_INVALID_ARG; a look-back wait that gave
  * up SG_ERR_TIMEOUT, with *dev_count set to -1 (the kept items written so far
  * are not a result); a CUDA failure SG_ERR_CUDA.
- * The first call on each device looks up the array's device address, with
- * that device current: make that first call before any stream capture.
+ * Every call waits for its stream (it reads the look-back's timeout flag
+ * back), so no call can be captured in a CUDA graph.  The first call on each
+ * device looks up the array's device address, with that device current.
  * Loading is the one exception to "allocates nothing": under CUDA's default
  * lazy module loading, that first call loads the library's device code on
  * the device, and the loader then takes the array's 513 KB (and the code's
