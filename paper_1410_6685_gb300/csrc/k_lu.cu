@@ -28,10 +28,11 @@
 //                  (bf16/fp16 operands, binary32 accumulate) or the binary32
 //                  SIMT form.
 // Solve: pivots on the right-hand side, then forward / backward substitution
-// by blocks of 64 rows in one launch each: CTAs take row blocks in order
-// (ticket) and wait, with a bounded spin, for the blocks they depend on; the
-// diagonal blocks are applied through their inverses (formed once per
-// factorisation), one short product instead of 32 dependent steps.
+// by steps of 128 rows in one launch each: CTAs take steps in order
+// (ticket) and wait, with a bounded spin, for the steps they depend on; each
+// step's diagonal block is applied through its inverse (assembled from the
+// 64 x 64 inverses formed once per factorisation), one short product
+// instead of 128 dependent steps.
 // Refinement: residual r = b - A x in binary64 from the binary32 A, and the
 // update x += d with the norms the stopping test needs.
 #include <cooperative_groups.h>
@@ -849,47 +850,117 @@ __global__ void __launch_bounds__(2 * kTB) k_lu_diag_inv(const float* __restrict
   }
 }
 
-// Triangular solve by 64-row blocks.  LOWER: unit lower L, blocks in
-// increasing order; else upper U with its diagonal, blocks in decreasing
-// order.  Block b's rows form two halves of 32 (warps 0-3 and 4-7); the four
-// warps of a half share the block's dependencies in 32-column pieces (warp w
-// takes every fourth, in the order they are solved), each loading its 32x32
-// piece, row by row and coalesced (lane = column), before waiting, with a
-// bounded spin, for the flag of the 64-row block that piece belongs to.  Warps 0 and 1 then apply the
-// inverse of the diagonal block (its rows held in registers from the start)
-// to the block's right-hand side and publish the flag with a release store.
+// Triangular solve by steps of 128 rows (two 64-row blocks).  LOWER: unit
+// lower L, steps in increasing order; else upper U with its diagonal, in
+// decreasing order.  Each step first forms, in shared memory, the inverse of
+// its 128 x 128 diagonal block from the two 64 x 64 inverses: with f the
+// block solved first (the upper one for L, the lower one for U), s the
+// other and X the rows of s over the columns of f, the inverse holds f's and
+// s's inverses on its diagonal and -inv_s X inv_f in place of X.  This is
+// done while earlier steps run, and each thread then keeps a 32-column
+// quarter of one row of it in registers.  A step's 128 rows form four
+// groups of 32, four warps per group sharing the step's dependencies in
+// 32-column pieces (warp q of a group takes every fourth, in the order they
+// are solved), each loading its piece row by row, coalesced (lane =
+// column), before waiting, with a bounded spin, for the flag of the step the
+// piece belongs to; one transposing warp reduction then gives lane r the sum
+// of row r.  The right-hand sides minus those sums times the inverse give
+// the step's solution, published with one flag (a release store).  The
+// chain of global waits from step to step (a few microseconds each, the
+// same at every size) bounds the solve.
+constexpr int kRB = 2 * kTB;         // rows of a step
+constexpr int kTrsvThreads = 512;
+constexpr int kTS = kTB + 1;         // shared row strides (conflict-free lane = row reads)
+constexpr int kRS = kRB + 1;
+constexpr size_t kTrsvSmem =
+    (kRB * kRS + 2 * kTB * kTS + (kTrsvThreads / 32) * 32 + kRB + 4 * kRB) * sizeof(float) + 16;
 template <bool LOWER>
-__global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
-                                              const float* __restrict__ inv, int n, float* y,
-                                              unsigned* flags, unsigned epoch, unsigned* ticket,
-                                              int* err) {
-  __shared__ unsigned s_b;
-  __shared__ float part[8][32];
-  __shared__ float vsh[kTB];
+__global__ void __launch_bounds__(kTrsvThreads, 1) k_trsv(const float* __restrict__ LU,
+                                                          const float* __restrict__ inv, int n,
+                                                          float* y, unsigned* flags,
+                                                          unsigned epoch, unsigned* ticket,
+                                                          int* err) {
+  extern __shared__ float tsm[];
+  float* ib = tsm;                                     // [kRB][kRS] the step's inverse
+  float* xa = ib + kRB * kRS;                          // [kTB][kTS] X
+  float* xb = xa + kTB * kTS;                          // [kTB][kTS] X inv_f
+  float* part = xb + kTB * kTS;                        // [16][32]
+  float* vsh = part + (kTrsvThreads / 32) * 32;        // [kRB]
+  float* xp = vsh + kRB;                               // [4][kRB] quarter sums
+  unsigned* s_b = reinterpret_cast<unsigned*>(xp + 4 * kRB);
+  const int tid = threadIdx.x;
   const int nb = (n + kTB - 1) / kTB;
-  if (threadIdx.x == 0) s_b = atomicAdd(ticket, 1u);
+  const int nst = (n + kRB - 1) / kRB;
+  if (tid == 0) *s_b = atomicAdd(ticket, 1u);
   __syncthreads();
-  const int t = (int)s_b;
-  const int b = LOWER ? t : nb - 1 - t;
-  const int row0 = b * kTB;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int h = w >> 2, wq = w & 3;
-  // warps 0 and 1 keep their row of the diagonal block's inverse
-  float dg[kTB];
-  if (w < 2) {
-    const float* irow = inv + ((size_t)b * kTB + 32 * w + lane) * kTB;
-#pragma unroll
-    for (int j = 0; j < kTB; ++j) dg[j] = irow[j];
+  const int t = (int)*s_b;
+  const int c = LOWER ? t : nst - 1 - t;
+  const int row0 = c * kRB;
+  const int lane = tid & 31, w = tid >> 5;
+  const int g = w >> 2, wq = w & 3;              // row group, and the warp's share of it
+  const bool two = 2 * c + 1 < nb;
+  const int nblk = two ? 2 : 1;
+  const int kf = LOWER || !two ? 0 : 1, ks = 1 - kf;
+  // warps 0-3 (lane + 32 w = row of the step) read their right-hand side now
+  const int rs = 32 * (w & 3) + lane;
+  const float bv = (w < 4 && row0 + rs < n) ? __ldcg(&y[row0 + rs]) : 0.0f;
+  // the diagonal inverses (zero elsewhere), and X
+  for (int e = tid; e < kRB * kRB; e += kTrsvThreads) {
+    const int r = e / kRB, jj = e % kRB, kr = r / kTB;
+    ib[r * kRS + jj] = (kr == jj / kTB && kr < nblk)
+                           ? inv[((size_t)(2 * c + kr) * kTB + r % kTB) * kTB + jj % kTB]
+                           : 0.0f;
   }
-  // lane = column: a piece's 32 rows are read as 32 coalesced 128-byte rows,
-  // and lane j accumulates column j's terms of every row of the half; one
-  // transposing reduction at the end gives lane r the sum of row r
+  if (two)
+    for (int e = tid; e < kTB * kTB; e += kTrsvThreads) {
+      const int r = e / kTB, jj = e % kTB;
+      const int gr = row0 + kTB * ks + r, gc = (2 * c + kf) * kTB + jj;
+      xa[r * kTS + jj] = (gr < n && gc < n) ? LU[(size_t)gr * n + gc] : 0.0f;
+    }
+  __syncthreads();
+  if (two) {
+    // X inv_f, then -inv_s (X inv_f): thread = one column, eight rows
+    const int jj = tid % kTB, r8 = (tid / kTB) * 8;
+    const float* fi = ib + (kTB * kf) * kRS + kTB * kf + jj;
+    float a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = 0.0f;
+#pragma unroll 8
+    for (int m = 0; m < kTB; ++m) {
+      const float bm = fi[m * kRS];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = fmaf(xa[(r8 + i) * kTS + m], bm, a[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xb[(r8 + i) * kTS + jj] = a[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = 0.0f;
+    const float* si = ib + (kTB * ks) * kRS + kTB * ks;
+#pragma unroll 8
+    for (int m = 0; m < kTB; ++m) {
+      const float bm = xb[m * kTS + jj];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = fmaf(si[(r8 + i) * kRS + m], bm, a[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) ib[(kTB * ks + r8 + i) * kRS + kTB * kf + jj] = -a[i];
+    __syncthreads();
+  }
+  // this thread's quarter of row rs of the inverse
+  float iv[32];
+  {
+    const float* ir = ib + rs * kRS + 32 * g;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) iv[jj] = ir[jj];
+  }
+  // the dependencies: lane = column, one transposing reduction at the end
   float acc[32];
 #pragma unroll
   for (int r = 0; r < 32; ++r) acc[r] = 0.0f;
-  const int rh = row0 + 32 * h;                  // the half's first row
+  const int rh = row0 + 32 * g;                  // the group's first row
   const int ns = (n + 31) / 32;   // 32-column pieces of the matrix
-  const int ndep = LOWER ? 2 * b : ns - 2 * (b + 1);
+  const int ndep = LOWER ? 4 * c : max(0, ns - 4 * (c + 1));
   for (int q = wq; q < ndep; q += 4) {
     const int sp = LOWER ? q : ns - 1 - q;
     const int cb = sp * 32;
@@ -902,7 +973,7 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
       unsigned spins = 0;
       for (;;) {
         unsigned f;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&flags[sp >> 1]) : "memory");
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&flags[sp >> 2]) : "memory");
         if (f == epoch) break;
         if (++spins > kSpin) {
           atomicExch(err, 1);
@@ -916,8 +987,8 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
 #pragma unroll
     for (int r = 0; r < 32; ++r) acc[r] = fmaf(m[r], yc, acc[r]);
   }
-  // transposing reduction: after the step of width o, a lane keeps the half
-  // of its rows that its bit o selects, added to its partner's
+  // after the step of width o a lane keeps the half of its rows that its
+  // bit o selects, added to its partner's: lane r ends with row r
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     const bool up = (lane & o) != 0;
@@ -928,27 +999,35 @@ __global__ void __launch_bounds__(256) k_trsv(const float* __restrict__ LU,
       acc[r] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  part[w][lane] = acc[0];
+  part[w * 32 + lane] = acc[0];
   __syncthreads();
-  if (w < 2) {
-    const int r = row0 + 32 * w + lane;
-    const float sacc = ((part[4 * w][lane] + part[4 * w + 1][lane]) + part[4 * w + 2][lane]) +
-                       part[4 * w + 3][lane];
-    vsh[32 * w + lane] = r < n ? __ldcg(&y[r]) - sacc : 0.0f;
+  if (w < 4) {
+    const float* p = part + 4 * w * 32 + lane;
+    vsh[rs] = row0 + rs < n ? bv - (((p[0] + p[32]) + p[64]) + p[96]) : 0.0f;
   }
   __syncthreads();
-  if (w < 2) {
-    // v := (diagonal block)^-1 v, one row of the product per lane
-    const int r = row0 + 32 * w + lane;
-    float x = 0.0f;
+  {
+    const float4* v4 = reinterpret_cast<const float4*>(vsh + 32 * g);
+    float x0 = 0.0f, x1 = 0.0f;
 #pragma unroll
-    for (int j = 0; j < kTB; ++j) x = fmaf(dg[j], vsh[j], x);
-    if (r < n) y[r] = x;
+    for (int k = 0; k < 8; ++k) {
+      const float4 v = v4[k];
+      x0 = fmaf(iv[4 * k], v.x, x0);
+      x1 = fmaf(iv[4 * k + 1], v.y, x1);
+      x0 = fmaf(iv[4 * k + 2], v.z, x0);
+      x1 = fmaf(iv[4 * k + 3], v.w, x1);
+    }
+    xp[g * kRB + rs] = x0 + x1;
+  }
+  __syncthreads();
+  if (w < 4) {
+    const float x = ((xp[rs] + xp[kRB + rs]) + xp[2 * kRB + rs]) + xp[3 * kRB + rs];
+    if (row0 + rs < n) y[row0 + rs] = x;
     __threadfence();
   }
   __syncthreads();
-  if (threadIdx.x == 0)
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&flags[b]), "r"(epoch) : "memory");
+  if (tid == 0)
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&flags[c]), "r"(epoch) : "memory");
 }
 
 // binary32 -> binary64, exactly, by the two formats' encodings: sign kept,
@@ -1235,12 +1314,23 @@ cudaError_t launch_lu_solve(const float* LU, const float* inv, int n, const int*
                             Prof* prof) {
   (void)rhs_is_residual;
   const int nb = (n + kTB - 1) / kTB;
+  const int nst = (n + kRB - 1) / kRB;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_trsv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTrsvSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_trsv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTrsvSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   prof_begin(prof, "lu_trsv", s);
   k_apply_perm<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(rhs, y, n, perm);
   cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), s);
-  k_trsv<true><<<nb, 256, 0, s>>>(LU, inv, n, y, flags, epoch, tickets, err);
-  k_trsv<false><<<nb, 256, 0, s>>>(LU, inv + (size_t)nb * kTB * kTB, n, y, flags + nb, epoch,
-                                   tickets + 1, err);
+  k_trsv<true><<<nst, kTrsvThreads, kTrsvSmem, s>>>(LU, inv, n, y, flags, epoch, tickets, err);
+  k_trsv<false><<<nst, kTrsvThreads, kTrsvSmem, s>>>(LU, inv + (size_t)nb * kTB * kTB, n, y,
+                                                     flags + nb, epoch, tickets + 1, err);
   prof_end(prof, s);
   return cudaGetLastError();
 }
