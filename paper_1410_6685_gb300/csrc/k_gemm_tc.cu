@@ -34,12 +34,26 @@ namespace sgk {
 namespace {
 
 constexpr int TM = 128, TN = 256, TK = 64, STAGES = 4;
-static_assert(kFrvTileC == TN, "the fused check keeps one C r partial per column tile");
+static_assert(kFrvTileC == TN / 2, "the fused check keeps one C r partial per epilogue warp's column half");
 constexpr int A_BYTES = TM * TK * 2;            // 16 KB
 constexpr int B_BYTES = TN * TK * 2;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
-constexpr int R_BYTES = 4 * TN * 16;            // the fused check's r entries, one copy per epilogue warp
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + R_BYTES;
+// Eight epilogue warps, two per quarter of the tensor memory's lanes, each
+// draining one 128-column half of a tile (with four, each alone on its SM
+// sub-partition, the dependent steps of the epilogue bounded short-K
+// products such as the elimination's updates)
+constexpr int kEpiWarps = 8;
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;   // producer, MMA issuer, epilogue
+constexpr int R_BYTES = kEpiWarps * (TN / 2) * 16;  // the fused check's r entries of each warp's half
+// The epilogue turns each 32 x 32 chunk (lane = row, from the tensor
+// memory) around in shared memory, 16 rows at a time, so that eight lanes
+// cover one row's 128 bytes: a warp's access touches 4 rows instead of 32,
+// and the L1 handles 4 lines per request instead of 32.  The 16-byte group
+// g of row r sits at group g ^ (r & 7): conflict-free writes (lane = row)
+// and reads (eight lanes = one row).
+constexpr int T_BYTES = kEpiWarps * 16 * 32 * 4;    // one 16 x 32 buffer per epilogue warp
+constexpr int SMEM_BYTES =
+    STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + R_BYTES + T_BYTES;
 constexpr unsigned kWaitLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -156,6 +170,152 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, int*
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// arrive on a barrier anywhere in the cluster
+__device__ __forceinline__ void mbar_arrive_cl(uint32_t bar_cl) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar_cl) : "memory");
+}
+
+// C rows m0q .. m0q + 31, columns col0 .. col0 + 31, as the epilogue's
+// stores take them: access it, lane l: row m0q + 4 it + l / 8, columns
+// col0 + 4 (l % 8) .. + 3 (zero outside M x N)
+__device__ __forceinline__ void load_c(const float* __restrict__ C, int ldc, int M, int N, int m0q,
+                                       int col0, int lane, float4 (&cv)[8]) {
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int grow = m0q + it * 4 + (lane >> 3), gcol = col0 + (lane & 7) * 4;
+    const float* cp = C + (size_t)grow * ldc + gcol;
+    if (grow < M && gcol + 4 <= N && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
+      cv[it] = *reinterpret_cast<const float4*>(cp);
+    } else {
+      float e[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) e[u] = grow < M && gcol + u < N ? cp[u] : 0.0f;
+      cv[it] = make_float4(e[0], e[1], e[2], e[3]);
+    }
+  }
+}
+
+// Row `row`, columns c0 .. c0 + w - 1 of C (clipped to N) into L2: the
+// subtracting product's epilogue reads them a tile later
+__device__ __forceinline__ void prefetch_c_row(const float* C, int ldc, int M, int N, int row,
+                                               int c0, int w) {
+  if (row >= M || c0 >= N) return;
+  const float* p = C + (size_t)row * ldc + c0;
+  const unsigned bytes = (unsigned)(min(w, N - c0) * 4) & ~15u;
+  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0 && bytes)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// One 32 x 32 chunk of the epilogue: lane l holds row m0q + l, columns
+// col0 .. col0 + 31 (r); C := chunk, or C := cv - chunk when subtracting (cv
+// from load_c), through the warp's transpose buffer s_tw (16 x 32 floats,
+// rows 16 h .. 16 h + 15 in turn); rows outside M and columns outside N are
+// left alone.
+__device__ __forceinline__ void store_chunk(float* __restrict__ C, int ldc, int M, int N, int m0q,
+                                            int col0, const uint32_t (&r)[32], float* s_tw,
+                                            int lane, int subtract, const float4 (&cv)[8]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if ((lane >> 4) == h) {
+      const int rw = lane & 15;
+      float4* dst = reinterpret_cast<float4*>(s_tw + rw * 32);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        dst[j ^ (rw & 7)] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                        __uint_as_float(r[4 * j + 2]),
+                                        __uint_as_float(r[4 * j + 3]));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int rr = it * 4 + (lane >> 3), g = lane & 7;
+      const float4 v = reinterpret_cast<const float4*>(s_tw + rr * 32)[g ^ (rr & 7)];
+      const int grow = m0q + 16 * h + rr, gcol = col0 + 4 * g;
+      if (grow >= M) continue;
+      const float4 c4 = cv[4 * h + it];
+      const float4 o =
+          subtract ? make_float4(c4.x - v.x, c4.y - v.y, c4.z - v.z, c4.w - v.w) : v;
+      float* cp = C + (size_t)grow * ldc + gcol;
+      if (gcol + 4 <= N && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
+        *reinterpret_cast<float4*>(cp) = o;
+      } else {
+        const float oe[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (gcol + u < N) cp[u] = oe[u];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// The epilogue of one tile by one epilogue warp: tensor-memory lane quarter
+// q (rows m0q .. m0q + 31), column half hh (columns n0 + 128 hh .. + 127,
+// four 32-column chunks) of accumulator acc.  The warp releases the
+// accumulator with one arrival on `tempty` (a cluster address when CL) once
+// its last chunk is read; the fused check's partial C r of its rows over its
+// half goes to column tile 2 bn + hh of frv_pw.  false: the wait for the
+// accumulator gave up.
+template <bool CL>
+__device__ __forceinline__ bool epilogue_tile(
+    uint32_t tmem, int acc, int tl, uint32_t tfull, uint32_t tempty, int q, int hh, int m0q,
+    int n0, int bn, float* __restrict__ C, int ldc, int M, int N, int subtract,
+    const float4* __restrict__ frv_r, float4* __restrict__ frv_pw, int inj_row, int inj_col,
+    float inj_delta, float4* s_rw, float* s_tw, int lane, int* err, volatile int* abort_flag) {
+  const int c0 = n0 + hh * (TN / 2);
+  if (frv_r) {
+    // each epilogue warp keeps its own copy, so no barrier spans the warps
+    __syncwarp();
+    for (int j = lane; j < TN / 2; j += 32)
+      s_rw[j] = c0 + j < N ? frv_r[c0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+  }
+  if (!mbar_wait_ab(tfull, (uint32_t)(tl >> 1) & 1u, err, abort_flag)) return false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0q + lane;
+  float4 wacc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+  for (int c = 0; c < TN / 64; ++c) {
+    const int col0 = c0 + c * 32;
+    float4 cv[8];
+    if (subtract) load_c(C, ldc, M, N, m0q, col0, lane, cv);
+    uint32_t r[32];
+    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TN + col0 - n0), r);
+    if (c == TN / 64 - 1) {
+      // this warp's part of the accumulator is drained
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        if (CL)
+          mbar_arrive_cl(tempty);
+        else
+          mbar_arrive(tempty);
+      }
+    }
+    // contract testing: a planted error in one product element, applied
+    // before it is stored (and before the fused check sees it)
+    if (row == inj_row && inj_col >= col0 && inj_col < col0 + 32) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (col0 + j == inj_col) r[j] = __float_as_uint(__uint_as_float(r[j]) + inj_delta);
+    }
+    if (frv_r) {
+      // r of columns past N is zero in s_r (their accumulator entries are too)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float4 rj = s_rw[c * 32 + j];
+        const float v = __uint_as_float(r[j]);
+        wacc.x = fmaf(v, rj.x, wacc.x);
+        wacc.y = fmaf(v, rj.y, wacc.y);
+        wacc.z = fmaf(v, rj.z, wacc.z);
+        wacc.w = fmaf(v, rj.w, wacc.w);
+      }
+    }
+    store_chunk(C, ldc, M, N, m0q, col0, r, s_tw, lane, subtract, cv);
+  }
+  if (frv_r && row < M && c0 < N) frv_pw[(size_t)(2 * bn + hh) * M + row] = wacc;
+  return true;
+}
 
 // Tile t of the persistent order: groups of kGroupM row blocks; inside a
 // group the row block varies fastest.  The 76 pairs' concurrent 256 x 256
@@ -179,10 +339,11 @@ __device__ __forceinline__ void tile_coords(int t, int nM, int nN, int* mb, int*
 //   warp 1, one lane : MMA issuer; accumulators alternate between two
 //                      256-column halves of the 512 TMEM columns, so the
 //                      epilogue of one tile overlaps the main loop of the next;
-//   warps 2..5       : epilogue, warp w reads TMEM lanes 32 (w % 4) .. + 31;
+//   warps 2..9       : epilogue, warp w reads TMEM lanes 32 (w % 4) .. + 31
+//                      and the 128-column half (w - 2) / 4 of the tile;
 //                      after draining an accumulator they release it to the
 //                      MMA issuer through an mbarrier.
-__global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ma,
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ma,
                                                     const __grid_constant__ CUtensorMap mb,
                                                     float* __restrict__ C, int ldc, int M,
                                                     int N, int KB, uint32_t id, int subtract,
@@ -199,6 +360,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUte
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float4* s_r = reinterpret_cast<float4*>(smem + STAGES * STAGE_BYTES + 256);
+  float* s_t = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256 + R_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nN = (N + TN - 1) / TN, nM = (M + TM - 1) / TM;
   const int ntiles = nN * nM;
@@ -209,8 +371,8 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUte
     for (int s = 0; s < 2 * STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
     mbar_init(tfull0, 1);
     mbar_init(tfull0 + 8, 1);
-    mbar_init(tempty0, 4);
-    mbar_init(tempty0 + 8, 4);
+    mbar_init(tempty0, kEpiWarps);
+    mbar_init(tempty0 + 8, kEpiWarps);
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -288,81 +450,25 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUte
       umma_commit(drain_bar);
     }
   } else {
-    // epilogue warps 2..5
-    const int q = warp & 3;                 // TMEM lane quarter of this warp
-    float4* s_rw = s_r + (warp - 2) * TN;
+    // epilogue warps 2..9: lane quarter warp % 4, column half (warp - 2) / 4
+    const int q = warp & 3, hh = (warp - 2) >> 2;
+    float4* s_rw = s_r + (warp - 2) * (TN / 2);
+    float* s_tw = s_t + (warp - 2) * 16 * 32;
     int tl = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       int bm, bn;
       tile_coords(t, nM, nN, &bm, &bn);
-      const int m0 = bm * TM, n0 = bn * TN;
       const int acc = tl & 1;
-      if (frv_r) {
-        // each epilogue warp keeps its own copy, so no barrier spans the warps
-        __syncwarp();
-        for (int j = lane; j < TN; j += 32)
-          s_rw[j] = n0 + j < N ? frv_r[n0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncwarp();
+      if (subtract && t + (int)gridDim.x < ntiles) {
+        int bm2, bn2;
+        tile_coords(t + (int)gridDim.x, nM, nN, &bm2, &bn2);
+        prefetch_c_row(C, ldc, M, N, bm2 * TM + q * 32 + lane, bn2 * TN + hh * (TN / 2), TN / 2);
       }
-      if (!mbar_wait_ab(tfull0 + 8 * acc, (uint32_t)(tl >> 1) & 1u, err, abort_flag)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = m0 + q * 32 + lane;
-      float4 wacc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 1
-      for (int c = 0; c < TN / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TN + c * 32), r);
-        if (c == TN / 32 - 1) {
-          // the accumulator is drained: hand it back to the MMA issuer
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
-        }
-        const int col0 = n0 + c * 32;
-        // contract testing: a planted error in one product element, applied
-        // before it is stored (and before the fused check sees it)
-        if (row == inj_row && inj_col >= col0 && inj_col < col0 + 32) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (col0 + j == inj_col) r[j] = __float_as_uint(__uint_as_float(r[j]) + inj_delta);
-        }
-        if (frv_r) {
-          // r of columns past N is zero in s_r (their accumulator entries are too)
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float4 rj = s_rw[c * 32 + j];
-            const float v = __uint_as_float(r[j]);
-            wacc.x = fmaf(v, rj.x, wacc.x);
-            wacc.y = fmaf(v, rj.y, wacc.y);
-            wacc.z = fmaf(v, rj.z, wacc.z);
-            wacc.w = fmaf(v, rj.w, wacc.w);
-          }
-        }
-        if (row < M) {
-          float* cp = C + (size_t)row * ldc + col0;
-          if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                     __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-              if (subtract) {
-                const float4 o = *reinterpret_cast<const float4*>(cp + j);
-                v = make_float4(o.x - v.x, o.y - v.y, o.z - v.z, o.w - v.w);
-              }
-              *reinterpret_cast<float4*>(cp + j) = v;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (col0 + j < N) {
-                const float v = __uint_as_float(r[j]);
-                cp[j] = subtract ? cp[j] - v : v;
-              }
-            }
-          }
-        }
-      }
-      if (frv_r && row < M) frv_pw[(size_t)bn * M + row] = wacc;
+      if (!epilogue_tile<false>(tmem, acc, tl, tfull0 + 8 * acc, tempty0 + 8 * acc, q, hh,
+                                bm * TM + q * 32, bn * TN, bn, C, ldc, M, N, subtract, frv_r,
+                                frv_pw, inj_row, inj_col, inj_delta, s_rw, s_tw, lane, err,
+                                abort_flag))
+        break;
     }
   }
   __syncthreads();
@@ -386,13 +492,14 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc(const __grid_constant__ CUte
 //   warp 1, one lane, leader    : MMA issuer, tcgen05.mma.cta_group::2
 //       (M = 256, N = 256, K = 16); commits multicast to both CTAs' "empty",
 //       "accumulator full" and "drain" barriers;
-//   warps 2..5, both CTAs       : epilogue of the CTA's 128 rows from its own
-//       tensor memory; they release an accumulator by arriving on the
-//       leader's "accumulator empty" barrier (eight arrivals, four remote).
+//   warps 2..9, both CTAs       : epilogue of the CTA's 128 rows from its own
+//       tensor memory (two warps per lane quarter, one per column half); they
+//       release an accumulator by arriving on the leader's "accumulator
+//       empty" barrier (sixteen arrivals, eight remote).
 // Six stages of 32 KB.  Every mbarrier wait is bounded, as in k_gemm_tc.
 constexpr int TM2 = 256, TH = 128, STAGES2 = 6;
 constexpr int STAGE2_BYTES = TH * TK * 2 * 2;   // 128 A rows + 128 B rows
-constexpr int SMEM2_BYTES = STAGES2 * STAGE2_BYTES + 1024 + 256 + R_BYTES;
+constexpr int SMEM2_BYTES = STAGES2 * STAGE2_BYTES + 1024 + 256 + R_BYTES + T_BYTES;
 
 __host__ __device__ constexpr uint32_t idesc2(bool fp16) {
   return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) |
@@ -419,9 +526,6 @@ __device__ __forceinline__ void cluster_sync() {
 __device__ __forceinline__ void mbar_expect_tx_cl(uint32_t bar_cl, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cluster.b64 _, [%0], %1;" ::"r"(bar_cl),
                "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_cl(uint32_t bar_cl) {
-  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar_cl) : "memory");
 }
 // TMA load into this CTA's shared memory completing on a barrier of either CTA of the pair
 __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x,
@@ -450,7 +554,7 @@ __device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
       : "memory");
 }
 
-__global__ void __launch_bounds__(192, 1) k_gemm_tc2(const __grid_constant__ CUtensorMap ma,
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc2(const __grid_constant__ CUtensorMap ma,
                                                      const __grid_constant__ CUtensorMap mb,
                                                      float* __restrict__ C, int ldc, int M,
                                                      int N, int KB, uint32_t id, int subtract,
@@ -466,6 +570,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc2(const __grid_constant__ CUt
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES2 + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float4* s_r = reinterpret_cast<float4*>(smem + STAGES2 * STAGE2_BYTES + 256);
+  float* s_t = reinterpret_cast<float*>(smem + STAGES2 * STAGE2_BYTES + 256 + R_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
   const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
@@ -481,8 +586,8 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc2(const __grid_constant__ CUt
     }
     mbar_init(tfull0, 1);
     mbar_init(tfull0 + 8, 1);
-    mbar_init(tempty0, 8);
-    mbar_init(tempty0 + 8, 8);
+    mbar_init(tempty0, 2 * kEpiWarps);
+    mbar_init(tempty0 + 8, 2 * kEpiWarps);
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -556,76 +661,27 @@ __global__ void __launch_bounds__(192, 1) k_gemm_tc2(const __grid_constant__ CUt
       umma_commit_pair(drain_bar);
     }
   } else {
-    const int q = warp & 3;
-    float4* s_rw = s_r + (warp - 2) * TN;
+    // epilogue warps 2..9: lane quarter warp % 4, column half (warp - 2) / 4
+    const int q = warp & 3, hh = (warp - 2) >> 2;
+    float4* s_rw = s_r + (warp - 2) * (TN / 2);
+    float* s_tw = s_t + (warp - 2) * 16 * 32;
     const uint32_t tempty_leader = map_rank(tempty0, 0);
     int tl = 0;
     for (int t = pair; t < ntiles; t += npairs, ++tl) {
       int bm, bn;
       tile_coords(t, nM, nN, &bm, &bn);
-      const int m0 = bm * TM2 + (int)rank * TH, n0 = bn * TN;
       const int acc = tl & 1;
-      if (frv_r) {
-        __syncwarp();
-        for (int j = lane; j < TN; j += 32)
-          s_rw[j] = n0 + j < N ? frv_r[n0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncwarp();
+      if (subtract && t + npairs < ntiles) {
+        int bm2, bn2;
+        tile_coords(t + npairs, nM, nN, &bm2, &bn2);
+        prefetch_c_row(C, ldc, M, N, bm2 * TM2 + (int)rank * TH + q * 32 + lane,
+                       bn2 * TN + hh * (TN / 2), TN / 2);
       }
-      if (!mbar_wait_ab(tfull0 + 8 * acc, (uint32_t)(tl >> 1) & 1u, err, abort_flag)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = m0 + q * 32 + lane;
-      float4 wacc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 1
-      for (int c = 0; c < TN / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TN + c * 32), r);
-        if (c == TN / 32 - 1) {
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive_cl(tempty_leader + 8 * acc);
-        }
-        const int col0 = n0 + c * 32;
-        if (row == inj_row && inj_col >= col0 && inj_col < col0 + 32) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (col0 + j == inj_col) r[j] = __float_as_uint(__uint_as_float(r[j]) + inj_delta);
-        }
-        if (frv_r) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float4 rj = s_rw[c * 32 + j];
-            const float v = __uint_as_float(r[j]);
-            wacc.x = fmaf(v, rj.x, wacc.x);
-            wacc.y = fmaf(v, rj.y, wacc.y);
-            wacc.z = fmaf(v, rj.z, wacc.z);
-            wacc.w = fmaf(v, rj.w, wacc.w);
-          }
-        }
-        if (row < M) {
-          float* cp = C + (size_t)row * ldc + col0;
-          if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                     __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-              if (subtract) {
-                const float4 o = *reinterpret_cast<const float4*>(cp + j);
-                v = make_float4(o.x - v.x, o.y - v.y, o.z - v.z, o.w - v.w);
-              }
-              *reinterpret_cast<float4*>(cp + j) = v;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (col0 + j < N) {
-                const float v = __uint_as_float(r[j]);
-                cp[j] = subtract ? cp[j] - v : v;
-              }
-            }
-          }
-        }
-      }
-      if (frv_r && row < M) frv_pw[(size_t)bn * M + row] = wacc;
+      if (!epilogue_tile<true>(tmem, acc, tl, tfull0 + 8 * acc, tempty_leader + 8 * acc, q, hh,
+                               bm * TM2 + (int)rank * TH + q * 32, bn * TN, bn, C, ldc, M, N,
+                               subtract, frv_r, frv_pw, inj_row, inj_col, inj_delta, s_rw, s_tw,
+                               lane, err, abort_flag))
+        break;
     }
   }
   __syncthreads();
@@ -931,7 +987,7 @@ bool use_pair() {
                              SMEM2_BYTES) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(2);
-      cfg.blockDim = dim3(192);
+      cfg.blockDim = dim3(kGemmThreads);
       cfg.dynamicSmemBytes = SMEM2_BYTES;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
@@ -963,7 +1019,7 @@ cudaError_t launch_product(const uint16_t* a16, const uint16_t* bt16, int Kp, bo
         1, std::min<long long>(tiles, persistent_grid(1 << 30, TN) / 2));   // SMs / 2
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * pairs);
-    cfg.blockDim = dim3(192);
+    cfg.blockDim = dim3(kGemmThreads);
     cfg.dynamicSmemBytes = SMEM2_BYTES;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -984,7 +1040,7 @@ cudaError_t launch_product(const uint16_t* a16, const uint16_t* bt16, int Kp, bo
     attr_done = true;
   }
   if (!make_map(&mb, bt16, N, Kp, TN, fp16)) return cudaErrorInvalidValue;
-  k_gemm_tc<<<persistent_grid(M, N), 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, Kp / TK,
+  k_gemm_tc<<<persistent_grid(M, N), kGemmThreads, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, Kp / TK,
                                                            idesc(fp16), subtract ? 1 : 0, err,
                                                            frv_r, frv_pw, inj_row, inj_col,
                                                            inj_delta);

@@ -60,7 +60,7 @@ cudaError_t launch_freivalds(const float* A, const float* B, const float* C, int
 // added in a fixed order by the final per-row test.
 constexpr int kFrvStripeB = 512;
 constexpr int kFrvStripeA = 1024;
-constexpr int kFrvTileC = 256;
+constexpr int kFrvTileC = 128;
 struct FrvFused {
   float4* r4;      // [N] the nvec Rademacher vectors, entry j of each
   float4* br4;     // [N] B r
