@@ -246,6 +246,8 @@ __global__ void k_frv_check_fused(const float* __restrict__ pzq, int nsa,
       o[0] += z.x; o[1] += z.y; o[2] += z.z; o[3] += z.w;
       o[4] += q.x; o[5] += q.y; o[6] += q.z; o[7] += q.w;
     }
+    // several partials in flight at once (the sums keep their order)
+#pragma unroll 8
     for (int t = 0; t < nsc; ++t) {
       const float4 w = pw[(long long)t * N + i];
       o[8] += w.x; o[9] += w.y; o[10] += w.z; o[11] += w.w;
@@ -342,8 +344,9 @@ cudaError_t launch_frv_b_reduce(const FrvFused& f, int N, cudaStream_t st) {
 
 cudaError_t launch_frv_check_fused(const FrvFused& f, int N, int nvec, float c, float u_eff,
                                    FreivaldsResult* res, cudaStream_t st) {
-  k_frv_check_fused<<<(N + 255) / 256, 256, 0, st>>>(f.pzq, f.nsa, f.pw, f.nsc, N, nvec, c, u_eff,
-                                                     res);
+  // one row per thread, 64-thread blocks: some 128 CTAs at N = 8192
+  k_frv_check_fused<<<(N + 63) / 64, 64, 0, st>>>(f.pzq, f.nsa, f.pw, f.nsc, N, nvec, c, u_eff,
+                                                  res);
   return cudaGetLastError();
 }
 
