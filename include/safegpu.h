@@ -456,6 +456,17 @@ sg_status sg_set_codegen(sg_ctx* ctx, sg_codegen g);
  * correctly: sg_filter then uses the interpreting kernel. */
 sg_status sg_debug_jit_check_filter(const sg_expr* pred, char* log, size_t cap);
 
+/* The same compile check for the specialised filter that also evaluates a
+ * for_all postcondition `post` (one input slot, as for sg_filter's
+ * predicate; NULL: none) on each kept item as it writes it -- the form
+ * sg_flush uses when a `Result.for_all` contract (sg_ensure) on a filter's
+ * result of the same flush is folded into the filter (Sec. 4: contracts
+ * checked on the device; no pass over the result).  Status and log as for
+ * sg_debug_jit_check_filter; SG_ERR_UNSUPPORTED also when the two programs
+ * together have more than 46 operations. */
+sg_status sg_debug_jit_check_filter_post(const sg_expr* pred, const sg_expr* post, char* log,
+                                         size_t cap);
+
 /* Writes a one-line-per-kernel description of what sg_flush would launch
  * for the currently queued work (no execution; works on a planning-only
  * context).  *len receives the length needed, including the terminator. */

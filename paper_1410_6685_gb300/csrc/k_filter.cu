@@ -221,7 +221,8 @@ cudaError_t launch_filter(const float* x, float* out, long long n, const Prog& p
 cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out, long long n,
                                       const Prog& pred, void* scratch, FilterResult* res,
                                       cudaStream_t s, int num_sms, int64_t* kernels,
-                                      Prof* prof, const LookbackCtl& lb, int tile) {
+                                      Prof* prof, const LookbackCtl& lb, int tile,
+                                      const Prog* post) {
   // the scratch (filter_jit_scratch_bytes) holds one look-back word per tile
   // of the smallest tile
   if (n <= 0) return cudaSuccess;
@@ -239,6 +240,12 @@ cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out
   a.out = out;
   a.n = n;
   for (int i = 0; i < kMaxProg; ++i) a.cst[i] = pred.cst[i];
+  if (post) {
+    // the postcondition's constants follow the predicate's and its sink
+    const int b = jit_filter_post_base(pred);
+    if (b + post->nops > kMaxProg) return cudaErrorInvalidValue;
+    for (int i = 0; i < post->nops; ++i) a.cst[b + i] = post->cst[i];
+  }
   a.st = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + sizeof(FilterHdr));
   a.tile_ctr = &h->tile_ctr;
   a.res = res;
@@ -302,21 +309,30 @@ sg_status filter_prog(const sg_expr* pred, Prog* pr, int* max_depth) {
 }  // namespace
 }  // namespace sgk
 
-extern "C" sg_status sg_debug_jit_check_filter(const sg_expr* pred, char* log, size_t cap) {
+extern "C" sg_status sg_debug_jit_check_filter_post(const sg_expr* pred, const sg_expr* post,
+                                                     char* log, size_t cap) {
   using namespace sgk;
   if (log && cap > 0) log[0] = '\0';
-  Prog pr;
+  Prog pr, pp;
   int md = 0;
-  const sg_status st = filter_prog(pred, &pr, &md);
+  sg_status st = filter_prog(pred, &pr, &md);
   if (st != SG_OK) return st;
+  if (post) {
+    st = filter_prog(post, &pp, &md);
+    if (st != SG_OK) return st;
+  }
   std::string l;
-  if (jit_check_filter(pr, &l)) return SG_OK;
+  if (jit_check_filter(pr, &l, post ? &pp : nullptr)) return SG_OK;
   if (log && cap > 0) {
     const size_t k = l.size() < cap - 1 ? l.size() : cap - 1;
     memcpy(log, l.data(), k);
     log[k] = '\0';
   }
   return SG_ERR_UNSUPPORTED;
+}
+
+extern "C" sg_status sg_debug_jit_check_filter(const sg_expr* pred, char* log, size_t cap) {
+  return sg_debug_jit_check_filter_post(pred, nullptr, log, cap);
 }
 
 extern "C" sg_status sg_filter_noalloc(const sg_expr* pred, const float* dev_x, int64_t n,

@@ -861,7 +861,12 @@ static sg_status attach(sg_ctx* c, void* target, const sg_contract* k, int32_t* 
     case SG_C_EXISTS: {
       const int nin = 1 + k->nother;
       if (t->v->dt != SG_F32) return fail(c, SG_ERR_DTYPE, "for_all/exists need SG_F32");
-      sg_status s = known_count(t);
+      // a contract on a queued filter's result alone needs no count now: it
+      // runs in the same flush, over the count the filter finds on the device
+      // (checked by the filter itself where the plan folds it in)
+      const bool behind_filter = !t->v->count_known && k->nother == 0 && t->v->producer &&
+                                 t->v->producer->kind == NK::FILTER;
+      sg_status s = behind_filter ? SG_OK : known_count(t);
       if (s && s != SG_ERR_PRECONDITION && s != SG_ERR_POSTCONDITION) return s;
       for (int i = 0; i < k->nother; ++i) {
         sg_vector* o = static_cast<sg_vector*>(k->other[i]);

@@ -173,6 +173,10 @@ struct FilterResult {
   long long count;
   int timeout;
   int pad;
+  // a for_all postcondition on the kept items checked as they are written
+  // (the specialised kernel's folded check): ~(first violating position), 0
+  // when none
+  unsigned long long post_enc;
 };
 size_t filter_scratch_bytes(long long n);
 cudaError_t launch_filter(const float* x, float* out, long long n,
@@ -182,9 +186,12 @@ cudaError_t launch_filter(const float* x, float* out, long long n,
 // the same filter through its run-time specialised kernel (sg_jit.h), whose
 // tiles hold `tile` items; scratch: filter_jit_scratch_bytes(n)
 size_t filter_jit_scratch_bytes(long long n);
+// post: the folded postcondition's program (its constants follow the
+// predicate's), or null; the kernel must have been built with it
 cudaError_t launch_filter_specialised(cudaKernel_t k, const float* x, float* out, long long n,
                                       const Prog& pred, void* scratch, FilterResult* res,
                                       cudaStream_t s, int num_sms, int64_t* kernels,
-                                      Prof* prof, const LookbackCtl& lb, int tile);
+                                      Prof* prof, const LookbackCtl& lb, int tile,
+                                      const Prog* post = nullptr);
 
 }  // namespace sgk

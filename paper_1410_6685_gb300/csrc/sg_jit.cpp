@@ -438,7 +438,7 @@ extern "C" __global__ void __launch_bounds__(256) sg_batch(const BatchJitArgs a)
 // Layouts below must match FilterResult (sg_internal.h) and FilterJitArgs
 // (sg_jit.h).
 const char* kTemplateFilter = R"SGJIT(
-struct FilterResult { long long count; int timeout; int pad; };
+struct FilterResult { long long count; int timeout; int pad; unsigned long long post_enc; };
 struct FilterJitArgs {
   const float* x; float* out; long long n; float cst[48];
   unsigned long long* st; unsigned* tile_ctr; FilterResult* res; unsigned ntiles; int skip_tile;
@@ -591,15 +591,41 @@ extern "C" __global__ void __launch_bounds__(256, SG_FMINB) sg_filter(const Filt
   }
   __syncthreads();
   const unsigned long long gb = s_excl;
+#if SG_POST
+  unsigned long long bad = 0ull;   // ~(lowest violating position), 0: none
+#endif
   for (unsigned i = tid; i < total; i += 256) {
     const unsigned long long pos = gb + i;
-    if (pos < (unsigned long long)n) a.out[pos] = s_pack[i];
+    if (pos < (unsigned long long)n) {
+      const float kv = s_pack[i];
+      a.out[pos] = kv;
+#if SG_POST
+      // the folded postcondition on the kept item at its output position
+      float x[1], o[1];
+      x[0] = kv;
+      unsigned hit = 0u;
+      float rv = 0.0f;
+      bool rm = false;
+      sg_post(a, x, (long long)pos, o, hit, rv, rm);
+      if (!(rv != 0.0f) && ~pos > bad) bad = ~pos;
+#endif
+    }
   }
+#if SG_POST
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, bad, o2);
+    bad = b2 > bad ? b2 : bad;
+  }
+  if (lane == 0 && bad) atomicMax(&a.res->post_enc, bad);
+#endif
 }
 )SGJIT";
 
 // ---- body generation: symbolic execution of the postfix program -----------
-bool gen_body(const Prog& pr, uint32_t pred_exists, std::string* body) {
+// cst_base: where the program's constants start in the argument block's
+// cst array (a second program shares it)
+bool gen_body(const Prog& pr, uint32_t pred_exists, std::string* body, int cst_base = 0) {
   std::vector<std::string> st;
   std::string b;
   int t = 0;
@@ -624,7 +650,7 @@ bool gen_body(const Prog& pr, uint32_t pred_exists, std::string* body) {
         st.push_back(buf);
         break;
       case SG_OP_CONST:
-        snprintf(buf, sizeof buf, "a.cst[%d]", pc);
+        snprintf(buf, sizeof buf, "a.cst[%d]", cst_base + pc);
         st.push_back(buf);
         break;
       case SG_OP_INDEX: st.push_back(tmp("__ll2float_rn(i)")); break;
@@ -757,8 +783,9 @@ cudaKernel_t compile_cached(const std::string& src, const char* name, std::strin
   return k;
 }
 
-std::string body_fn(const std::string& body) {
-  return "template <class A> __device__ __forceinline__ void sg_body(const A& a, const float* x, "
+std::string body_fn(const std::string& body, const char* name = "sg_body") {
+  return std::string("template <class A> __device__ __forceinline__ void ") + name +
+         "(const A& a, const float* x, "
          "long long i, float* o, unsigned& hit, float& rv, bool& rm) {\n"
          "  bool mask = true;\n  (void)x; (void)i; (void)o; (void)hit; (void)rv; "
          "(void)rm; (void)a;\n" +
@@ -811,7 +838,8 @@ namespace {
 
 // the source of the specialised filter for `pred` with `tile`-item tiles;
 // false (with a reason in *log) when it cannot be specialised
-bool filter_source(const Prog& pred, int tile, std::string* src, std::string* log) {
+bool filter_source(const Prog& pred, int tile, std::string* src, std::string* log,
+                   const Prog* post = nullptr) {
   if (tile != 2048 && tile != 4096 && tile != 8192) {
     if (log) *log = "unsupported filter tile";
     return false;
@@ -836,12 +864,33 @@ bool filter_source(const Prog& pred, int tile, std::string* src, std::string* lo
     if (log) *log = "program could not be specialised";
     return false;
   }
+  // the folded postcondition: the same form, its constants after the
+  // predicate's and its sink
+  std::string post_body;
+  if (post) {
+    const int b = jit_filter_post_base(pred);
+    if (post->nops <= 0 || b + post->nops + 1 > kMaxProg) {
+      if (log) *log = "postcondition could not be folded";
+      return false;
+    }
+    Prog pp = *post;
+    pp.op[pp.nops] = K_REDUCE;
+    pp.arg[pp.nops] = 0;
+    pp.cst[pp.nops] = 0.0f;
+    pp.nops += 1;
+    if (!gen_body(pp, 0u, &post_body, b)) {
+      if (log) *log = "postcondition could not be specialised";
+      return false;
+    }
+  }
   // resident CTAs per SM the compiler plans for: 48 registers at 8192
   // items, 40 at 4096, 32 at 2048
-  char defs[128];
+  char defs[160];
   snprintf(defs, sizeof defs, "#define SG_MINMAX 0\n#define SG_FT %d\n#define SG_FQ %d\n"
-           "#define SG_FMINB %d\n", tile, tile / 1024, filter_tile_occupancy(tile));
-  *src = std::string(defs) + kTemplateHead + body_fn(body) + kTemplateFilter;
+           "#define SG_FMINB %d\n#define SG_POST %d\n", tile, tile / 1024,
+           filter_tile_occupancy(tile), post ? 1 : 0);
+  *src = std::string(defs) + kTemplateHead + body_fn(body) +
+         (post ? body_fn(post_body, "sg_post") : std::string()) + kTemplateFilter;
   return true;
 }
 
@@ -849,17 +898,21 @@ bool filter_source(const Prog& pred, int tile, std::string* src, std::string* lo
 
 int filter_tile_occupancy(int tile) { return tile >= 8192 ? 5 : tile >= 4096 ? 6 : 8; }
 
-cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log, int tile) {
+cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log, int tile, const Prog* post) {
   std::string src;
-  if (!filter_source(pred, tile, &src, log)) return nullptr;
+  if (!filter_source(pred, tile, &src, log, post)) return nullptr;
   return compile_cached(src, "sg_filter", log);
 }
 
-bool jit_check_filter(const Prog& pred, std::string* log) {
+bool jit_check_filter(const Prog& pred, std::string* log, const Prog* post) {
   Nvrtc& nv = nvrtc();
+  if (!nv.ok) {
+    if (log) *log = "NVRTC library not found";
+    return false;
+  }
   for (int tile : {2048, 4096, 8192}) {
     std::string src;
-    if (!filter_source(pred, tile, &src, log)) return false;
+    if (!filter_source(pred, tile, &src, log, post)) return false;
     void* prog = nullptr;
     if (nv.create(&prog, src.c_str(), "sg_filter.cu", 0, nullptr, nullptr) != 0) {
       if (log) *log = "NVRTC could not create the program";

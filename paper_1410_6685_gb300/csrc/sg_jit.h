@@ -72,14 +72,19 @@ cudaKernel_t jit_stream_kernel(const Prog& pr, int nin, int nout, int npred, boo
 cudaKernel_t jit_batch_kernel(const Prog& pr, std::string* log);
 // the stable compaction of one predicate (one input slot), one CTA per
 // tile of `tile` items: 2048, 4096 or 8192 (k_filter.cu launches it)
-cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log, int tile = kJitFilterTile);
+// post: a for_all postcondition (one input slot) on the kept items, checked
+// as they are written (FilterResult::post_enc), or null
+cudaKernel_t jit_filter_kernel(const Prog& pred, std::string* log, int tile = kJitFilterTile,
+                               const Prog* post = nullptr);
+// index of the postcondition's first constant in FilterJitArgs::cst
+inline int jit_filter_post_base(const Prog& pred) { return pred.nops + 1; }
 // resident CTAs per SM that filter kernel is compiled for
 int filter_tile_occupancy(int tile);
 // the smallest tile of the specialised filter (sizes its look-back scratch)
 constexpr int kJitFilterMinTile = 2048;
 // compiles that kernel's source with NVRTC without loading it (no device
 // needed); false with the compiler's log when it does not compile
-bool jit_check_filter(const Prog& pred, std::string* log);
+bool jit_check_filter(const Prog& pred, std::string* log, const Prog* post = nullptr);
 cudaError_t launch_jit_stream(cudaKernel_t k, const StreamArgs& s, int grid, int block,
                               cudaStream_t st, Prof* prof);
 

@@ -73,6 +73,7 @@ struct Pass {
   Node* chk_sorted = nullptr;
   Node* chk_perm = nullptr;
   Node* chk_frv = nullptr;    // MATMUL: built-in Freivalds check folded in
+  Node* chk_post = nullptr;   // FILTER: a for_all postcondition on its result folded in
   Node* vtrans = nullptr;     // MATVEC y = A x with A the pending transpose of vtrans->in[0]
   // STREAM over a compacted filter's result of the same flush: that filter,
   // whose count (on the device) bounds the pass
@@ -121,6 +122,29 @@ bool program_depths(const std::vector<Op>& ops, std::vector<uint8_t>* before, in
   return mx <= sgk::kMaxDepth;
 }
 
+// The program of an element-wise expression whose value is read off the
+// stack (a filter predicate, a contract): depths are computed with a trailing
+// pop that is not part of the program.
+sgk::Prog value_prog(const sg_expr& ex, int* max_depth = nullptr) {
+  sgk::Prog pr{};
+  std::vector<Op> ops;
+  for (int p = 0; p < ex.nops; ++p) ops.push_back(Op{(uint8_t)ex.ops[p].op, 0, ex.ops[p].value});
+  ops.push_back(Op{sgk::K_POP, 0, 0.0f});
+  std::vector<uint8_t> before;
+  int md = 0;
+  program_depths(ops, &before, &md);
+  ops.pop_back();
+  pr.nops = (int)ops.size();
+  for (size_t p = 0; p < ops.size(); ++p) {
+    pr.op[p] = ops[p].op;
+    pr.arg[p] = ops[p].arg;
+    pr.cst[p] = ops[p].cst;
+    pr.depth[p] = before[p];
+  }
+  if (max_depth) *max_depth = md;
+  return pr;
+}
+
 struct Planner {
   sg_ctx* c;
   bool fuse;                    // merge passes (Sec. 5), else one pass per call
@@ -148,6 +172,24 @@ struct Planner {
     for (Node* u : it->second)
       if (u->kind != NK::REDUCE) return false;
     return true;
+  }
+
+  // A for_all postcondition whose only operand is the compacted result of a
+  // filter of this plan is checked by the specialised filter on each kept
+  // item as it is written (no pass over the result): the filter's pass.
+  int post_fold_target(Node* n) {
+    if (!fuse || c->codegen != SG_CODEGEN_SPECIALIZE || !sgk::jit_available()) return -1;
+    if (n->kind != NK::CHECK || n->ckind != SG_C_FOR_ALL || n->nin != 1 || !n->in[0]) return -1;
+    Node* f = n->in[0]->producer;
+    if (!f || f->kind != NK::FILTER || n->in[0]->dt != SG_F32) return -1;
+    for (int p = 0; p < n->expr.nops; ++p)
+      if (n->expr.ops[p].op == SG_OP_LOAD && n->expr.ops[p].arg != 0) return -1;
+    if (f->expr.nops + 1 + n->expr.nops + 1 > sgk::kMaxProg) return -1;
+    for (size_t i = passes.size(); i-- > 0;) {
+      const Pass& P = passes[i];
+      if (P.kind == PK::FILTER && P.main == f) return P.chk_post ? -1 : (int)i;
+    }
+    return -1;
   }
 
   bool dead(Node* n) {
@@ -314,6 +356,12 @@ struct Planner {
     bool open = false;
     for (Node* n : nodes) {
       if (dead(n)) continue;
+      const int pf = post_fold_target(n);
+      if (pf >= 0) {
+        passes[pf].chk_post = n;
+        passes[pf].nodes.push_back(n);
+        continue;
+      }
       const bool streamable = is_f32_stream_node(n) || (n->kind == NK::FILTER && maskable(n));
       if (streamable) {
         const int64_t len = node_len(n);
@@ -734,7 +782,8 @@ cudaError_t launch_stream_scheduled(sg_ctx* c, cudaKernel_t jk, const sgk::Strea
 // else the plain table's 8192 items.  *ran is false when no specialised
 // kernel could be built (the caller interprets).
 cudaError_t launch_filter_scheduled(sg_ctx* c, const sgk::Prog& pr, const float* x, float* out,
-                                    long long n, void* dwork, sgk::FilterResult* rec, bool* ran) {
+                                    long long n, void* dwork, sgk::FilterResult* rec, bool* ran,
+                                    const sgk::Prog* post) {
   *ran = false;
   const std::vector<sg_sched_choice> cand = sg_filter_candidates();
   const sg_sched_choice d = sg_filter_default();
@@ -748,16 +797,20 @@ cudaError_t launch_filter_scheduled(sg_ctx* c, const sgk::Prog& pr, const float*
                        &X[i * kSchedFeatures]);
     if (cand[i].chunk == d.chunk) def = (int)i;
   }
-  const uint64_t key = sg_sched_key(SG_SCHED_FILTER, {(uint64_t)n, prog_shape(pr)});
+  const uint64_t key = sg_sched_key(SG_SCHED_FILTER, {(uint64_t)n, prog_shape(pr),
+                                                      post ? prog_shape(*post) + 1 : 0});
   int learned = -1;
   std::vector<float> pred;
   std::vector<double> us;
   int idx = sg_sched_lookup(c, SG_SCHED_FILTER, key, X, def, &learned, &pred, &us);
   cudaError_t e = cudaSuccess;
-  auto kernel = [&](int i) { return sgk::jit_filter_kernel(pr, nullptr, (int)cand[i].chunk); };
+  auto kernel = [&](int i) {
+    return sgk::jit_filter_kernel(pr, nullptr, (int)cand[i].chunk, post);
+  };
   auto launch = [&](cudaKernel_t k, int i, sgk::Prof* prof) {
     return sgk::launch_filter_specialised(k, x, out, n, pr, dwork, rec, c->stream, c->num_sms,
-                                          &c->kernels, prof, c->lookback, (int)cand[i].chunk);
+                                          &c->kernels, prof, c->lookback, (int)cand[i].chunk,
+                                          post);
   };
   if (idx < 0) {
     const bool debug = c->lookback.spin_limit != 0 || c->lookback.skip_tile >= 0;
@@ -945,29 +998,22 @@ sg_status run_flush(sg_ctx* c, bool fuse, bool commit, double* us) {
         Value* x = n->in[0].get();
         status = ensure_storage(c, n->out.get());
         if (status) break;
-        sgk::Prog pr{};
-        std::vector<Op> ops;
-        for (int p = 0; p < n->expr.nops; ++p)
-          ops.push_back(Op{(uint8_t)n->expr.ops[p].op, 0, n->expr.ops[p].value});
-        // the predicate's value is read off the stack (no sink): depths are
-        // computed with a trailing pop that is not executed
-        ops.push_back(Op{sgk::K_POP, 0, 0.0f});
-        std::vector<uint8_t> before;
         int md = 0;
-        program_depths(ops, &before, &md);
-        ops.pop_back();
-        pr.nops = (int)ops.size();
-        for (size_t p = 0; p < ops.size(); ++p) {
-          pr.op[p] = ops[p].op;
-          pr.arg[p] = ops[p].arg;
-          pr.cst[p] = ops[p].cst;
-          pr.depth[p] = before[p];
-        }
+        const sgk::Prog pr = value_prog(n->expr, &md);
+        sgk::Prog post{};
+        if (P.chk_post) post = value_prog(P.chk_post->expr);
         bool ran = false;
         if (c->codegen == SG_CODEGEN_SPECIALIZE)
           e = launch_filter_scheduled(c, pr, static_cast<const float*>(x->st->ptr),
                                       static_cast<float*>(n->out->st->ptr), P.n, dwork,
-                                      static_cast<sgk::FilterResult*>(rec), &ran);
+                                      static_cast<sgk::FilterResult*>(rec), &ran,
+                                      P.chk_post ? &post : nullptr);
+        if (!ran && P.chk_post && e == cudaSuccess) {
+          // the folded postcondition exists only in the specialised kernel
+          status = SG_ERR_UNSUPPORTED;
+          c->err = "the specialised filter with its folded postcondition could not be built";
+          break;
+        }
         if (!ran && e == cudaSuccess)
           e = sgk::launch_filter(static_cast<const float*>(x->st->ptr),
                                  static_cast<float*>(n->out->st->ptr), P.n, pr, md, dwork,
@@ -1157,6 +1203,8 @@ sg_status run_flush(sg_ctx* c, bool fuse, bool commit, double* us) {
           P.main->out->n = r.count;
           P.main->out->rows = r.count;
           P.main->out->count_known = true;
+          if (P.chk_post && !r.timeout && r.post_enc != 0)
+            record_violation(c, P.chk_post, (int64_t)~r.post_enc, 0.0, &have, &cstatus);
           break;
         }
         case PK::SORT:
@@ -1367,7 +1415,10 @@ sg_status sg_describe_pending(sg_ctx* c, std::string* out) {
                  (long long)P.n, P.count_src ? " (the filter's count)" : "", P.inputs.size(),
                  P.stores.size(), P.preds.size(), P.reduce_of ? 1 : 0, P.prog.size());
         break;
-      case PK::FILTER: snprintf(buf, sizeof buf, "filter n=%lld\n", (long long)P.n); break;
+      case PK::FILTER:
+        snprintf(buf, sizeof buf, "filter n=%lld%s\n", (long long)P.n,
+                 P.chk_post ? " for_all=1" : "");
+        break;
       case PK::SORT:
         snprintf(buf, sizeof buf, "sort n=%lld sorted=%d perm=%d\n", (long long)P.n,
                  P.chk_sorted ? 1 : 0, P.chk_perm ? 1 : 0);

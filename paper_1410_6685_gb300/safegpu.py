@@ -146,6 +146,7 @@ def _load():
         "sg_batch_run": [vp, P(SgChain), vp, vp, i64, vp, vp, vp],
         "sg_filter_noalloc": [P(SgExpr), vp, i64, vp, vp, vp],
         "sg_debug_jit_check_filter": [P(SgExpr), C.c_char_p, sz],
+        "sg_debug_jit_check_filter_post": [P(SgExpr), P(SgExpr), C.c_char_p, sz],
         "sg_batch_report": [vp, P(SgChain), vp, vp, i64, vp, vp, vp, P(SgSchedReport)],
         "sg_sched_train": [vp, i32, C.c_float, C.c_uint64, P(C.c_float)],
         "sg_sched_log_size": [vp, P(i64), P(C.c_int32)],
@@ -546,6 +547,15 @@ def sg_debug_jit_check_filter(pred):
     e = expr(pred)
     buf = C.create_string_buffer(1 << 14)
     st = lib.sg_debug_jit_check_filter(C.byref(e), buf, len(buf))
+    return int(st), buf.value.decode(errors="replace")
+
+
+def sg_debug_jit_check_filter_post(pred, post):
+    """Compile (only) the specialised filter of `pred` with the for_all
+    postcondition `post` folded in.  Returns (status, log)."""
+    e, q = expr(pred), expr(post)
+    buf = C.create_string_buffer(1 << 14)
+    st = lib.sg_debug_jit_check_filter_post(C.byref(e), C.byref(q), buf, len(buf))
     return int(st), buf.value.decode(errors="replace")
 
 

@@ -120,6 +120,35 @@ def test_filter_then_sum_becomes_masked_reduce(sg, pctx):
     sg.sg_scalar_release(s)
 
 
+def test_filter_postcondition_folded_into_the_filter(sg, pctx):
+    """`Result.for_all(p)` (Sec. 4) on a queued filter's result runs in the
+    same flush: folded into the specialised filter, which checks each kept
+    item as it writes it, else as a pass over the filter's count."""
+    if sg.sg_debug_jit_check_filter([("x", 0)])[0] != sg.SG_OK:
+        pytest.skip("no NVRTC on this machine")
+    x = vec(sg, pctx, 10000)
+    pred = [("x", 0), ("c", 0.0), ("gt",)]
+    post = sg.contract(sg.SG_C_FOR_ALL, [("x", 0), ("c", -1.0), ("gt",)])
+    k = sg.sg_filter(pctx, pred, x)
+    sg.sg_ensure(pctx, k, post)
+    assert lines(sg, pctx) == ["filter n=10000 for_all=1"]
+    sg.sg_set_fusion(pctx, sg.SG_FUSE_OFF)
+    L = lines(sg, pctx)
+    assert L[0] == "filter n=10000" and len(L) == 2, L
+    assert L[1].startswith("stream n=10000 (the filter's count)") and "pred=1" in L[1], L
+    sg.sg_set_fusion(pctx, sg.SG_FUSE_ON)
+    sg.sg_set_codegen(pctx, sg.SG_CODEGEN_INTERPRET)
+    L = lines(sg, pctx)
+    assert L[0] == "filter n=10000" and len(L) == 2, L
+    sg.sg_set_codegen(pctx, sg.SG_CODEGEN_SPECIALIZE)
+    # exists, and a second filter's contract, are not folded into the first
+    k2 = sg.sg_filter(pctx, pred, x)
+    sg.sg_ensure(pctx, k2, sg.contract(sg.SG_C_EXISTS, [("x", 0), ("c", 0.5), ("gt",)]))
+    L = lines(sg, pctx)
+    assert L[0] == "filter n=10000 for_all=1" and L[1] == "filter n=10000", L
+    assert L[2].startswith("stream n=10000 (the filter's count)") and len(L) == 3, L
+
+
 def test_filter_kept_by_handle_is_compacted(sg, pctx):
     """A reduction of a kept filter result runs after the compaction, over
     the filter's count (read on the device), in a pass of its own."""

@@ -187,3 +187,80 @@ def test_filter_nan_and_signed_zero(env):
         got, _ = run_filter(env, base, pred)
         ref = oracle.filter(pred, base)
         assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+# (filter predicate, postcondition on the kept items): one that holds, one
+# that fails at the first kept item <= 0.5, one on output positions (fails
+# at position 1000 when more than 1000 items are kept)
+POSTS = [
+    ([("x", 0), ("c", 0.25), ("gt",)], [("x", 0), ("c", 0.25), ("gt",)]),
+    ([("x", 0), ("c", 0.25), ("gt",)], [("x", 0), ("c", 0.5), ("gt",)]),
+    ([("x", 0), ("c", 0.0), ("lt",)], [("index",), ("c", 1000.0), ("lt",)]),
+]
+
+
+@pytest.mark.parametrize("mode", ["folded", "unfused", "interpret"])
+@pytest.mark.parametrize("n", [5, 4097, 300_007, (1 << 22) + 3])
+@pytest.mark.parametrize("k", range(len(POSTS)))
+def test_filter_postcondition_on_the_kept_items(env, mode, n, k):
+    """`Result.for_all(p)` on a filter's result (Sec. 4) runs in the filter's
+    flush: folded into the specialised filter (each kept item checked as it
+    is written), or as a pass over the filter's count.  Either way the
+    outcome, and the first violating position of the result, are the
+    oracle's; when it holds the kept items are the oracle's, bit for bit."""
+    sg, ctx, torch = env
+    pred, post = POSTS[k]
+    x = inputs.uniform_pm1(inputs.rng(n + 31 * k), n)
+    ref = oracle.filter(pred, x)
+    want = oracle.first_false(post, ref)
+    t = torch.from_numpy(x).cuda()
+    v = sg.sg_vector_wrap(ctx, sg.SG_F32, n, t.data_ptr())
+    if mode == "unfused":
+        sg.sg_set_fusion(ctx, sg.SG_FUSE_OFF)
+    if mode == "interpret":
+        sg.sg_set_codegen(ctx, sg.SG_CODEGEN_INTERPRET)
+    try:
+        kf = sg.sg_filter(ctx, pred, v)
+        cid = sg.sg_ensure(ctx, kf, sg.contract(sg.SG_C_FOR_ALL, post))
+        plan = sg.sg_plan_describe(ctx).splitlines()
+        if mode == "folded":
+            assert plan == ["filter n=%d for_all=1" % n], plan
+        else:
+            assert len(plan) == 2 and "(the filter's count)" in plan[1], plan
+        if want < 0:
+            m = sg.sg_vector_count(ctx, kf)
+            out = sg.sg_vector_read(ctx, kf, np.empty(m, f32))
+            assert m == len(ref)
+            assert np.array_equal(out.view(np.uint32), ref.view(np.uint32))
+        else:
+            with pytest.raises(sg.SgError) as e:
+                sg.sg_flush(ctx)
+            assert e.value.status == sg.SG_ERR_POSTCONDITION
+            viol = sg.sg_last_violation(ctx)
+            assert viol.first_index == want and viol.contract_id == cid and viol.role == sg.SG_POST
+        sg.sg_vector_release(kf)
+    finally:
+        sg.sg_set_fusion(ctx, sg.SG_FUSE_ON)
+        sg.sg_set_codegen(ctx, sg.SG_CODEGEN_SPECIALIZE)
+        sg.sg_vector_release(v)
+
+
+def test_folded_postcondition_is_one_kernel(env):
+    """With the postcondition folded in, the filter and its check are one
+    kernel launch (after the first flush of the workload, which measures the
+    filter's tiles)."""
+    sg, ctx, torch = env
+    n = 1 << 20
+    x = inputs.uniform_pm1(inputs.rng(77), n)
+    t = torch.from_numpy(x).cuda()
+    v = sg.sg_vector_wrap(ctx, sg.SG_F32, n, t.data_ptr())
+    pred = [("x", 0), ("c", 0.25), ("gt",)]
+    for _ in range(2):
+        k0 = sg.sg_kernel_count(ctx)
+        kf = sg.sg_filter(ctx, pred, v)
+        sg.sg_ensure(ctx, kf, sg.contract(sg.SG_C_FOR_ALL, pred))
+        m = sg.sg_vector_count(ctx, kf)
+        sg.sg_vector_release(kf)
+    assert sg.sg_kernel_count(ctx) - k0 == 1
+    assert m == len(oracle.filter(pred, x))
+    sg.sg_vector_release(v)

@@ -44,3 +44,33 @@ def test_malformed_predicate_rejected(sg):
     assert st == sg.SG_ERR_INVALID_ARG
     st, _ = sg.sg_debug_jit_check_filter([("x", 1), ("c", 0.0), ("gt",)])
     assert st == sg.SG_ERR_INVALID_ARG
+
+
+POSTS = [
+    [("x", 0), ("c", 0.25), ("gt",)],
+    [("index",), ("c", 100.0), ("lt",)],
+    [("x", 0), ("x", 0), ("eq",), ("x", 0), ("abs",), ("c", 2.0), ("le",), ("and",)],
+]
+
+
+@pytest.mark.parametrize("k", range(len(POSTS)))
+def test_specialised_filter_with_folded_postcondition_compiles(sg, k):
+    st, log = sg.sg_debug_jit_check_filter_post(PREDICATES[k], POSTS[k])
+    if st == sg.SG_ERR_UNSUPPORTED and "NVRTC library not found" in log:
+        pytest.skip("no NVRTC on this machine")
+    assert st == sg.SG_OK, log
+
+
+def test_folded_postcondition_size_limit(sg):
+    # the two programs share the 48 constant slots: 46 operations together
+    pred = [("x", 0), ("abs",)] + [("c", 1.0), ("add",)] * 10 + [("c", 0.0), ("gt",)]
+    post = [("x", 0)] + [("c", 1.0), ("add",)] * 10 + [("c", 0.0), ("gt",)]
+    assert (len(pred), len(post)) == (24, 23)
+    st, log = sg.sg_debug_jit_check_filter_post(pred, post[:-4] + [("c", 0.0), ("gt",)])
+    if st == sg.SG_ERR_UNSUPPORTED and "NVRTC library not found" in log:
+        pytest.skip("no NVRTC on this machine")
+    assert st == sg.SG_OK, log          # 24 + 21 operations fold
+    st, log = sg.sg_debug_jit_check_filter_post(pred, post)
+    if st == sg.SG_ERR_UNSUPPORTED and "NVRTC library not found" in log:
+        pytest.skip("no NVRTC on this machine")
+    assert st == sg.SG_ERR_UNSUPPORTED and "folded" in log, log
