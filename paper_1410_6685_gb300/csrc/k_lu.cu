@@ -617,17 +617,28 @@ __global__ void __launch_bounds__(128) k_lu_laswp_outer(float* LU, int n, const 
 }
 
 // x := L^-1 x for one column x of 32 entries (stride xs) and the unit lower
-// triangle of L (row stride ls), by forward substitution in registers: row i
-// subtracts L[i][0] x[0], L[i][1] x[1], ... in that order
-__device__ __forceinline__ void unit_lower_solve_col(const float* L, int ls, float* x, int xs) {
+// triangle of L (row stride ls, a multiple of 4; L 16-byte aligned), by
+// forward substitution in registers: row i subtracts L[i][0] x[0], L[i][1]
+// x[1], ... in that order, reading L's row four entries per shared-memory
+// load.
+__device__ __forceinline__ void unit_lower_solve_col4(const float* L, int ls, float* x, int xs) {
   float v[kPB];
 #pragma unroll
   for (int i = 0; i < kPB; ++i) v[i] = x[i * xs];
 #pragma unroll
   for (int i = 1; i < kPB; ++i) {
     float acc = v[i];
+    const float4* Li = reinterpret_cast<const float4*>(L + i * ls);
 #pragma unroll
-    for (int q = 0; q < i; ++q) acc = fmaf(-L[i * ls + q], v[q], acc);
+    for (int g = 0; g < i / 4; ++g) {
+      const float4 l = Li[g];
+      acc = fmaf(-l.x, v[4 * g], acc);
+      acc = fmaf(-l.y, v[4 * g + 1], acc);
+      acc = fmaf(-l.z, v[4 * g + 2], acc);
+      acc = fmaf(-l.w, v[4 * g + 3], acc);
+    }
+#pragma unroll
+    for (int q = (i / 4) * 4; q < i; ++q) acc = fmaf(-L[i * ls + q], v[q], acc);
     v[i] = acc;
   }
 #pragma unroll
@@ -646,9 +657,10 @@ constexpr int kInRows = 32;
 constexpr int kInCols = kLuOuter - kPB;
 __global__ void __launch_bounds__(256) k_lu_inner(float* LU, int n, int j, int c0, int c1,
                                                   unsigned* counter) {
-  __shared__ float L[kPB][kPB + 1];
+  // rows of L and P padded to 36 floats: 16-byte loads of four entries
+  __shared__ __align__(16) float L[kPB][kPB + 4];
   __shared__ float U[kPB][kInCols + 1];
-  __shared__ float P[kInRows][kPB + 1];
+  __shared__ __align__(16) float P[kInRows][kPB + 4];
   __shared__ bool s_last;
   const int tid = threadIdx.x;
   const int N = c1 - c0;
@@ -693,22 +705,29 @@ __global__ void __launch_bounds__(256) k_lu_inner(float* LU, int n, int j, int c
     __threadfence();
     s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
-  if (tid < N) unit_lower_solve_col(&L[0][0], kPB + 1, &U[0][tid], kInCols + 1);
+  if (tid < N) unit_lower_solve_col4(&L[0][0], kPB + 4, &U[0][tid], kInCols + 1);
   __syncthreads();
   if (s_last)
     for (int t = tid; t < kPB * N; t += 256) LU[(size_t)(j + t / N) * n + c0 + t % N] = U[t / N][t % N];
-  // A22 -= L21 U12: twelve independent chains per thread, each over q in order
-#pragma unroll 4
-  for (int q = 0; q < kPB; ++q) {
-    float uq[3], pq[4];
+  // A22 -= L21 U12: twelve independent chains per thread, each over q in
+  // order; four entries of each of the thread's P rows per load
+#pragma unroll 2
+  for (int q = 0; q < kPB; q += 4) {
+    float4 p4[4];
 #pragma unroll
-    for (int u = 0; u < 3; ++u) uq[u] = U[q][lane + 32 * u];
+    for (int i = 0; i < 4; ++i) p4[i] = *reinterpret_cast<const float4*>(&P[w + 8 * i][q]);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) pq[i] = P[w + 8 * i][q];
+    for (int e = 0; e < 4; ++e) {
+      float uq[3];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int u = 0; u < 3; ++u) uq[u] = U[q + e][lane + 32 * u];
 #pragma unroll
-      for (int u = 0; u < 3; ++u) acc[i * 3 + u] = fmaf(-pq[i], uq[u], acc[i * 3 + u]);
+      for (int i = 0; i < 4; ++i) {
+        const float pq = e == 0 ? p4[i].x : e == 1 ? p4[i].y : e == 2 ? p4[i].z : p4[i].w;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) acc[i * 3 + u] = fmaf(-pq, uq[u], acc[i * 3 + u]);
+      }
+    }
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -724,11 +743,11 @@ __global__ void __launch_bounds__(256) k_lu_inner(float* LU, int n, int j, int c
 // most kLuOuter).  One CTA per 32 columns with L11 and its strip in shared
 // memory; by 32-row blocks: the diagonal block solved one thread per column,
 // then the rows below it updated by all threads.
-__global__ void __launch_bounds__(256) k_lu_trsm_outer(float* LU, int n, int K, int KB, int c0,
-                                                       int c1) {
-  extern __shared__ float sm_t[];
-  const int ls = KB + 1;
-  float* L = sm_t;               // KB x (KB + 1)
+__global__ void __launch_bounds__(256, 2) k_lu_trsm_outer(float* LU, int n, int K, int KB,
+                                                          int c0, int c1) {
+  extern __shared__ __align__(16) float sm_t[];
+  const int ls = KB + 4;         // rows padded to a multiple of 4: 16-byte loads
+  float* L = sm_t;               // KB x (KB + 4)
   float* X = sm_t + KB * ls;     // KB x 33
   const int tid = threadIdx.x;
   const int cb = c0 + blockIdx.x * kPB;
@@ -759,7 +778,7 @@ __global__ void __launch_bounds__(256) k_lu_trsm_outer(float* LU, int n, int K, 
   }
   __syncthreads();
   for (int b = 0; b < KB; b += kPB) {
-    if (tid < kPB) unit_lower_solve_col(L + b * ls + b, ls, X + b * 33 + tid, 33);
+    if (tid < kPB) unit_lower_solve_col4(L + b * ls + b, ls, X + b * 33 + tid, 33);
     __syncthreads();
     // rows below: warp w takes rows b + 32 + w + 8 i, lane the column;
     // independent chains over q in order
@@ -770,13 +789,21 @@ __global__ void __launch_bounds__(256) k_lu_trsm_outer(float* LU, int n, int K, 
       const int r = b + kPB + w + 8 * i;
       acc[i] = (w + 8 * i < below) ? X[r * 33 + lane] : 0.0f;
     }
-#pragma unroll 4
-    for (int q = 0; q < kPB; ++q) {
-      const float xq = X[(b + q) * 33 + lane];
+#pragma unroll 2
+    for (int q = 0; q < kPB; q += 4) {
+      float xq[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) xq[e] = X[(b + q + e) * 33 + lane];
 #pragma unroll
       for (int i = 0; i < 12; ++i) {
         const int r = b + kPB + w + 8 * i;
-        if (w + 8 * i < below) acc[i] = fmaf(-L[r * ls + b + q], xq, acc[i]);
+        if (w + 8 * i < below) {
+          const float4 l = *reinterpret_cast<const float4*>(L + r * ls + b + q);
+          acc[i] = fmaf(-l.x, xq[0], acc[i]);
+          acc[i] = fmaf(-l.y, xq[1], acc[i]);
+          acc[i] = fmaf(-l.z, xq[2], acc[i]);
+          acc[i] = fmaf(-l.w, xq[3], acc[i]);
+        }
       }
     }
 #pragma unroll
@@ -1251,7 +1278,7 @@ cudaError_t lu_prepare(int n) {
     e = cudaFuncSetAttribute(k_lu_panel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
   }
   if (e != cudaSuccess) return e;
-  const size_t mx = ((size_t)kLuOuter * (kLuOuter + 1) + (size_t)kLuOuter * 33) * sizeof(float);
+  const size_t mx = ((size_t)kLuOuter * (kLuOuter + 4) + (size_t)kLuOuter * 33) * sizeof(float);
   return cudaFuncSetAttribute(k_lu_trsm_outer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
 
@@ -1287,7 +1314,7 @@ cudaError_t launch_lu_inner(float* LU, int n, int j, int c0, int c1, unsigned* c
 cudaError_t launch_lu_trsm_outer(float* LU, int n, int K, int KB, int c0, int c1, cudaStream_t s,
                                  Prof* prof) {
   if (c1 <= c0) return cudaSuccess;
-  const size_t sm = ((size_t)KB * (KB + 1) + (size_t)KB * 33) * sizeof(float);
+  const size_t sm = ((size_t)KB * (KB + 4) + (size_t)KB * 33) * sizeof(float);
   prof_begin(prof, "lu_trsm", s);
   k_lu_trsm_outer<<<(c1 - c0 + kPB - 1) / kPB, 256, sm, s>>>(LU, n, K, KB, c0, c1);
   prof_end(prof, s);

@@ -44,7 +44,7 @@ def solve(env, A, b, prec=1, expect=None, **kw):
     return xs, info
 
 
-@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 100, 257, 1000])
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 100, 129, 191, 257, 1000])
 def test_general_matrix_fp32_lu(env, n):
     """Random Gaussian matrices: pivoting is exercised; binary32 LU + refinement."""
     g = np.random.default_rng(n)
