@@ -196,6 +196,8 @@ POSTS = [
     ([("x", 0), ("c", 0.25), ("gt",)], [("x", 0), ("c", 0.25), ("gt",)]),
     ([("x", 0), ("c", 0.25), ("gt",)], [("x", 0), ("c", 0.5), ("gt",)]),
     ([("x", 0), ("c", 0.0), ("lt",)], [("index",), ("c", 1000.0), ("lt",)]),
+    # nothing kept: the postcondition holds on the empty result
+    ([("x", 0), ("c", 2.0), ("gt",)], [("x", 0), ("c", 5.0), ("gt",)]),
 ]
 
 
@@ -264,3 +266,34 @@ def test_folded_postcondition_is_one_kernel(env):
     assert sg.sg_kernel_count(ctx) - k0 == 1
     assert m == len(oracle.filter(pred, x))
     sg.sg_vector_release(v)
+
+
+@pytest.mark.parametrize("fuse", [True, False])
+def test_filter_postcondition_nan_kept(env, fuse):
+    """NaN items kept by the filter (x > 0.5 or x != x) fail `x > 0.5` (an
+    IEEE comparison with NaN is false): the first NaN's position in the
+    result is the violation, folded or not."""
+    sg, ctx, torch = env
+    n = 300_007
+    x = inputs.uniform_pm1(inputs.rng(41), n)
+    x[[1234, 5678, 200_001]] = np.nan
+    pred = [("x", 0), ("c", 0.5), ("gt",), ("x", 0), ("x", 0), ("ne",), ("or",)]
+    post = [("x", 0), ("c", 0.5), ("gt",)]
+    ref = oracle.filter(pred, x)
+    want = oracle.first_false(post, ref)
+    assert want >= 0 and np.isnan(ref[want])
+    t = torch.from_numpy(x).cuda()
+    v = sg.sg_vector_wrap(ctx, sg.SG_F32, n, t.data_ptr())
+    sg.sg_set_fusion(ctx, sg.SG_FUSE_ON if fuse else sg.SG_FUSE_OFF)
+    try:
+        kf = sg.sg_filter(ctx, pred, v)
+        cid = sg.sg_ensure(ctx, kf, sg.contract(sg.SG_C_FOR_ALL, post))
+        with pytest.raises(sg.SgError) as e:
+            sg.sg_flush(ctx)
+        assert e.value.status == sg.SG_ERR_POSTCONDITION
+        viol = sg.sg_last_violation(ctx)
+        assert viol.first_index == want and viol.contract_id == cid
+        sg.sg_vector_release(kf)
+    finally:
+        sg.sg_set_fusion(ctx, sg.SG_FUSE_ON)
+        sg.sg_vector_release(v)
