@@ -346,8 +346,13 @@ sg_status sg_det(sg_ctx* ctx, sg_matrix* A, sg_precision precision, sg_det_resul
  * postcondition, to the current (possibly pending) value of `target`.  They
  * are evaluated at the next flush, fused into the pass that produces the
  * target whenever possible.  Scalar parts (counts, shapes) are checked at
- * the call.  Returns an id in *contract_id (may be NULL) that
- * sg_last_violation() reports.                                              */
+ * the call; a FOR_ALL or EXISTS with no other[] operand on a pending filter
+ * result has none, so it does not flush the filter: it runs in the filter's
+ * flush, over the count the filter finds (a FOR_ALL there is checked by the
+ * run-time specialised filter itself, on each kept item as it is written,
+ * when fusion is on), and its first index is a position in the result.
+ * Returns an id in *contract_id (may be NULL) that sg_last_violation()
+ * reports.                                                                  */
 typedef enum {
   SG_C_FOR_ALL = 0,     /* expr over slots: 0 = target, 1.. = other[]   */
   SG_C_EXISTS = 1,
