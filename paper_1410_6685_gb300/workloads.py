@@ -34,6 +34,8 @@ def main(argv=None):
     ap.add_argument("--prec", type=int, default=1)
     ap.add_argument("--contracts", choices=["on", "off"], default="on",
                     help="off: contract mode SG_CONTRACTS_OFF (the unchecked schedule)")
+    ap.add_argument("--post", action="store_true",
+                    help="filter: also ensure Result.for_all(x > 0.25) on its result")
     a = ap.parse_args(argv)
 
     import torch
@@ -95,8 +97,13 @@ def main(argv=None):
             out["kernels"] = run(step)
             out["bytes_per_launch"] = 12 * n
         else:
+            pred = [("x", 0), ("c", 0.25), ("gt",)]
+            fpost = sg.contract(sg.SG_C_FOR_ALL, pred)
+
             def step():
-                k = sg.sg_filter(ctx, [("x", 0), ("c", 0.25), ("gt",)], vx)
+                k = sg.sg_filter(ctx, pred, vx)
+                if a.post:
+                    sg.sg_ensure(ctx, k, fpost)
                 sg.sg_vector_count(ctx, k)
                 sg.sg_vector_release(k)
             out["kernels"] = run(step)
