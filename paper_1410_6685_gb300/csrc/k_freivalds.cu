@@ -230,28 +230,41 @@ __global__ void k_frv_check(const float* __restrict__ pac, int N, int nstripes, 
 // The same test when the partial sums come from the fused product (the cast
 // kernels and the GEMM epilogue): pzq[s][i] = (z_0..3, q_0..3) over column
 // stripe s of A, pw[t][i] = (C r)_i over column tile t of C.
-__global__ void k_frv_check_fused(const float* __restrict__ pzq, int nsa,
-                                  const float4* __restrict__ pw, int nsc, int N, int nvec,
-                                  float c, float u_eff, FreivaldsResult* res) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  float worst = 0.0f;
-  bool bad = false;
-  if (i < N) {
-    float o[12];
+// Four threads per row: thread p of row i sums partials p, p + 4, p + 8,
+// ... in order, then the four sums are added in a fixed order ((0 + 1) +
+// (2 + 3)), so the result does not depend on the schedule.
+__global__ void __launch_bounds__(256) k_frv_check_fused(const float* __restrict__ pzq, int nsa,
+                                                         const float4* __restrict__ pw, int nsc,
+                                                         int N, int nvec, float c, float u_eff,
+                                                         FreivaldsResult* res) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long i = g >> 2;
+  const int part = (int)(g & 3);
+  float o[12];
 #pragma unroll
-    for (int t = 0; t < 12; ++t) o[t] = 0.0f;
-    for (int s = 0; s < nsa; ++s) {
+  for (int t = 0; t < 12; ++t) o[t] = 0.0f;
+  if (i < N) {
+    for (int s = part; s < nsa; s += 4) {
       const float4* p = reinterpret_cast<const float4*>(pzq + ((long long)s * N + i) * 8);
       const float4 z = p[0], q = p[1];
       o[0] += z.x; o[1] += z.y; o[2] += z.z; o[3] += z.w;
       o[4] += q.x; o[5] += q.y; o[6] += q.z; o[7] += q.w;
     }
-    // several partials in flight at once (the sums keep their order)
-#pragma unroll 8
-    for (int t = 0; t < nsc; ++t) {
+    // several partials in flight at once (each sum keeps its order)
+#pragma unroll 4
+    for (int t = part; t < nsc; t += 4) {
       const float4 w = pw[(long long)t * N + i];
       o[8] += w.x; o[9] += w.y; o[10] += w.z; o[11] += w.w;
     }
+  }
+#pragma unroll
+  for (int t = 0; t < 12; ++t) {
+    o[t] += __shfl_xor_sync(0xffffffffu, o[t], 1);
+    o[t] += __shfl_xor_sync(0xffffffffu, o[t], 2);
+  }
+  float worst = 0.0f;
+  bool bad = false;
+  if (i < N && part == 0) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       if (v >= nvec) continue;
@@ -344,9 +357,9 @@ cudaError_t launch_frv_b_reduce(const FrvFused& f, int N, cudaStream_t st) {
 
 cudaError_t launch_frv_check_fused(const FrvFused& f, int N, int nvec, float c, float u_eff,
                                    FreivaldsResult* res, cudaStream_t st) {
-  // one row per thread, 64-thread blocks: some 128 CTAs at N = 8192
-  k_frv_check_fused<<<(N + 63) / 64, 64, 0, st>>>(f.pzq, f.nsa, f.pw, f.nsc, N, nvec, c, u_eff,
-                                                  res);
+  // four threads per row: 128 CTAs of 256 threads at N = 8192
+  k_frv_check_fused<<<(int)((4LL * N + 255) / 256), 256, 0, st>>>(f.pzq, f.nsa, f.pw, f.nsc, N,
+                                                                  nvec, c, u_eff, res);
   return cudaGetLastError();
 }
 
